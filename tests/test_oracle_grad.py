@@ -1,0 +1,93 @@
+"""Pins of the oracle's gradients: autograd of the brute-force definition
+against central finite differences in fp64 (8x8 and 12x10 images, few
+curves, parameters away from the threshold decisions)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle.curves import SampleCfg
+from oracle.pipeline import CURVE_KEYS, as_curves, loss_only, step
+from paper_2503_16424_gb300 import synth
+
+
+def _case(seed, W, H, n_open, n_closed, cfg):
+    c = synth.make_curves(seed, W, H, n_open, n_closed, style="uniform",
+                          width_range=(1.5, 3.0), opac_range=(0.3, 0.85))
+    curves = as_curves(c.as_dict())
+    target = torch.as_tensor(np.random.default_rng(seed + 100).uniform(0, 1, (3, H, W)))
+    return curves, target
+
+
+@pytest.mark.parametrize("seed,W,H,n_open,n_closed", [(0, 8, 8, 2, 0), (1, 8, 8, 0, 1),
+                                                      (2, 12, 10, 2, 1)])
+def test_autograd_equals_central_fd(seed, W, H, n_open, n_closed):
+    cfg = SampleCfg(g_open=6, rows_closed=3, k_closed=4, eps=0.3)
+    curves, target = _case(seed, W, H, n_open, n_closed, cfg)
+    bg = (0.2, 0.1, 0.4)
+    res = step(curves, cfg, W, H, target, bg)
+    # no pixel close to a threshold decision, so the loss is smooth here
+    from oracle.raster import render_pixels
+    ys, xs = torch.meshgrid(torch.arange(H, dtype=torch.float64), torch.arange(W, dtype=torch.float64),
+                            indexing="ij")
+    fl = render_pixels(res["table"], xs.reshape(-1), ys.reshape(-1), bg, margin=1e-4)["flag"]
+    assert not bool(fl.any())
+    checked = 0
+    for key in CURVE_KEYS:
+        base = curves[key]
+        g_auto = res["dcurves"][key].reshape(-1)
+        flat = base.reshape(-1)
+        gmax = float(g_auto.abs().max()) if g_auto.numel() else 0.0
+        for i in range(flat.numel()):
+            h = 1e-6 * max(1.0, abs(float(flat[i])))
+            plus = {k: v.clone() for k, v in curves.items()}
+            minus = {k: v.clone() for k, v in curves.items()}
+            plus[key].view(-1)[i] += h
+            minus[key].view(-1)[i] -= h
+            fd = (loss_only(plus, cfg, W, H, target, bg) - loss_only(minus, cfg, W, H, target, bg)) / (2 * h)
+            err = abs(fd - float(g_auto[i]))
+            # FD rounding error is about eps * L / h; allow 50x that
+            fd_round = 50 * 2.2e-16 * res["loss"] / h
+            assert err <= 1e-5 * max(abs(fd), 1e-3 * gmax) + fd_round, (key, i, fd, float(g_auto[i]))
+            checked += 1
+    assert checked > 20
+
+
+def test_per_gaussian_grads_fd():
+    """dL/d(table) of render_grads against FD in the table entries."""
+    cfg = SampleCfg(g_open=5, rows_closed=3, k_closed=4)
+    curves, target = _case(3, 8, 8, 2, 1, cfg)
+    res = step(curves, cfg, 8, 8, target)
+    tab = {k: v.detach().clone() for k, v in res["table"].items() if k in
+           ("mx", "my", "ca", "cb", "cc", "o", "col")}
+
+    def loss_of(t):
+        img = oracle.render_image(t, 8, 8)["img"]
+        return float(oracle.l2_loss(img, target)[0])
+
+    rng = np.random.default_rng(0)
+    for key in ("mx", "my", "ca", "cb", "cc", "o", "col"):
+        g = res["dtable"][key].reshape(-1)
+        for i in rng.choice(g.numel(), size=min(6, g.numel()), replace=False):
+            h = 1e-6 * max(1.0, abs(float(tab[key].reshape(-1)[i])))
+            tp = {k: v.clone() for k, v in tab.items()}
+            tm = {k: v.clone() for k, v in tab.items()}
+            tp[key].view(-1)[i] += h
+            tm[key].view(-1)[i] -= h
+            fd = (loss_of(tp) - loss_of(tm)) / (2 * h)
+            fd_round = 50 * 2.2e-16 * res["loss"] / h
+            assert abs(fd - float(g[i])) <= 1e-5 * max(abs(fd), 1e-3 * float(g.abs().max())) + fd_round
+
+
+def test_l2_loss_gradient():
+    rng = np.random.default_rng(1)
+    a, b = rng.uniform(0, 1, (3, 4, 5)), rng.uniform(0, 1, (3, 4, 5))
+    L, g = oracle.l2_loss(a, b)
+    assert abs(float(L) - ((a - b) ** 2).sum() / 60) < 1e-15
+    i = (1, 2, 3)
+    h = 1e-7
+    ap = a.copy(); ap[i] += h
+    am = a.copy(); am[i] -= h
+    fd = (float(oracle.l2_loss(ap, b)[0]) - float(oracle.l2_loss(am, b)[0])) / (2 * h)
+    assert abs(fd - float(g[i])) < 1e-8
