@@ -1,0 +1,367 @@
+"""Throughput of the Bezier Splatting rasterizer: fwd+bwd raster steps/s.
+
+One step = the whole hot path over one synthetic problem:
+  curve order -> sample Gaussians -> bin (count, emit, onesweep sort, ranges)
+  -> blend forward -> L2 loss gradient -> blend backward -> sampling backward.
+Workload (default): 2048x2048 RGB target, 2048 open + 2048 closed cubic
+curves, 64 Gaussians per curve (262,144 Gaussians), 16x16 tiles.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload.  Under torchrun every rank runs an
+independent replica (the single-image path has no exchange step).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "hires_2048_4096"
+METRIC = "fwd+bwd raster steps/s at 2048² (4096 curves); batched vs plain, same PSNR"
+UNIT = "steps/s"
+FP32_FLOP_PER_FWD_EVAL = 22     # per (pixel, list entry) evaluation, forward
+FP32_FLOP_PER_BWD_EVAL = 55     # per (pixel, list entry) evaluation, backward
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """FMA = 2 FLOP on 128 FP32 lanes per SM."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem(device):
+    import torch
+    from paper_2503_16424_gb300 import bs, synth
+    w = synth.WORKLOADS[WORKLOAD]
+    arrays = synth.make_curves(w["seed"], w["W"], w["H"], w["n_open"], w["n_closed"], style=w["style"]).as_dict()
+    target = synth.procedural_target(w["seed"] + 1, w["W"], w["H"], w["n_shapes"])
+    cfg = bs.SampleCfg(g_open=w["g_open"], rows_closed=w["rows_closed"], k_closed=w["k_closed"])
+    canvas = bs.Canvas(w["W"], w["H"], w["tile"])
+    return w, arrays, target, cfg, canvas
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2503_16424_gb300 import bs
+    from paper_2503_16424_gb300.raster import Rasterizer
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w, arrays, target_np, cfg, canvas = make_problem(dev)
+    curves = bs.CurveSet.from_arrays(arrays, device=dev)
+    target = torch.as_tensor(target_np, device=dev)
+    r = Rasterizer(canvas, cfg, curves.n_open, curves.n_closed, device=dev, pair_capacity=1 << 25)
+    grad = curves.zeros_like()
+    stream = torch.cuda.current_stream()
+
+    def mk():
+        return torch.cuda.Event(enable_timing=True)
+    ev = [[mk() for _ in range(4)] for _ in range(args.steps)]
+
+    def step(e=None):
+        # forward: order, sample, bin, blend
+        r.rank, r.first = bs.curve_order(curves, cfg)
+        bs.sample_curves(curves, cfg, r.first, out=r.gauss)
+        r.binning.run(r.gauss)
+        if e:
+            e[0].record(stream)
+        bs.render_fwd(r.gauss, canvas, r.binning, out=(r.img, r.T, r.nc))
+        if e:
+            e[1].record(stream)
+        bs.l2_loss_grad(r.img, target, dimg=r.dimg, loss=r.loss)
+        if e:
+            e[2].record(stream)
+        bs.render_bwd(r.gauss, canvas, r.binning, r.T, r.nc, r.dimg, r.dgauss)
+        if e:
+            e[3].record(stream)
+        bs.sample_curves_bwd(curves, cfg, r.first, r.dgauss, grad)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # work counters of this problem (untimed)
+    stats = bs.render_stats(r.gauss, canvas, r.binning)
+    n_pairs = r.binning.n_pairs
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            step(ev[i])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    bwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs (curves + target) from pinned memory, D2H of loss and gradients
+    host_in = {k: torch.as_tensor(v).pin_memory() for k, v in arrays.items()}
+    host_target = torch.as_tensor(target_np).pin_memory()
+    host_out = {k: torch.empty_like(getattr(grad, k), device="cpu").pin_memory() for k in bs.CURVE_FIELDS}
+    host_loss = torch.empty((), dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values()) + host_target.numel() * 4
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 8
+
+    def e2e_step():
+        for k in bs.CURVE_FIELDS:
+            getattr(curves, k).copy_(host_in[k], non_blocking=True)
+        target.copy_(host_target, non_blocking=True)
+        step()
+        for k in bs.CURVE_FIELDS:
+            host_out[k].copy_(getattr(grad, k), non_blocking=True)
+        host_loss.copy_(r.loss, non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e_ms = (time.perf_counter() - e0) * 1e3
+    if world > 1:
+        t = torch.tensor([e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e_ms = float(t.item())
+    e2e_value = world * args.steps / (e_ms / 1e3)
+
+    peaks, src = load_peaks()
+    clocks = clk.summary()
+    fwd_avg, bwd_avg = float(np.mean(fwd_ms)), float(np.mean(bwd_ms))
+    e_fwd, e_bwd = stats["evals"], stats["n_contrib_sum"]
+    fwd_tf = FP32_FLOP_PER_FWD_EVAL * e_fwd / (fwd_avg * 1e-3) / 1e12
+    bwd_tf = FP32_FLOP_PER_BWD_EVAL * e_bwd / (bwd_avg * 1e-3) / 1e12
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    if bwd_avg >= fwd_avg:
+        dom, ach = "render_bwd_kernel", bwd_tf
+    else:
+        dom, ach = "render_fwd_kernel", fwd_tf
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "W": w["W"], "H": w["H"], "n_open": w["n_open"],
+                   "n_closed": w["n_closed"], "gaussians_per_curve": w["g_open"],
+                   "n_gaussians": r.n_gauss, "tile": w["tile"], "n_pairs": n_pairs,
+                   "curve_init": w["style"], "l2": "working set larger than L2 (no flush)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": round(ach, 3),
+                     "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                     "traffic": None,
+                     "peak_source": f"FP32 {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                    f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)"},
+        "kernels_ms": {"render_fwd": round(fwd_avg, 4), "render_bwd": round(bwd_avg, 4)},
+        "work": {"fwd_evals": e_fwd, "bwd_evals": e_bwd, "blended": stats["blended"],
+                 "fwd_tflops": round(fwd_tf, 3), "bwd_tflops": round(bwd_tf, 3)},
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    # kernels launched per step: curve_order 1, sample 1, bin (count, scan,
+    # zero, emit, passes x onesweep, ranges), render_fwd 1, l2 1, render_bwd 1,
+    # sample_bwd 1 (memsets are not kernels)
+    passes = -(-max(1, (canvas.n_tiles - 1).bit_length()) // 8)
+    per_step = 1 + 1 + (5 + passes) + 1 + 1 + 1 + 1
+    out["gpu_launches"] = per_step * args.steps
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(side=8)
+    return out
+
+
+_PROBLEM = {}
+
+
+def _oracle_problem():
+    """The workload's curves and target for the oracle (made once)."""
+    if not _PROBLEM:
+        w, arrays, target_np, _, _ = make_problem(None)
+        _PROBLEM.update(w=w, arrays=arrays, target=target_np)
+    return _PROBLEM
+
+
+def cpu_baseline(side=16):
+    """The fp64 CPU oracle on a bounded sample of the workload: sampling of
+    all curves, the brute-force blend (every Gaussian at every pixel) and its
+    gradient at a side x side pixel crop extrapolated to the full image by
+    pixel count, and the sampling backward of all curves."""
+    import torch
+    import oracle
+    from oracle.curves import SampleCfg as OCfg
+    from oracle.pipeline import as_curves, sample_vjp
+    pb = _oracle_problem()
+    w, arrays, target_np = pb["w"], pb["arrays"], pb["target"]
+    cfg = OCfg(g_open=w["g_open"], rows_closed=w["rows_closed"], k_closed=w["k_closed"])
+    threads = torch.get_num_threads()
+    t0 = time.perf_counter()
+    cur = as_curves(arrays)
+    _, first = oracle.draw_order(arrays["open_ctrl"], arrays["open_width"], arrays["closed_ctrl"], cfg)
+    with torch.no_grad():
+        tab = oracle.gaussian_table(cur, cfg, first)
+    t_sample = time.perf_counter() - t0
+    y0 = x0 = w["W"] // 2 - side // 2
+    ys, xs = torch.meshgrid(torch.arange(y0, y0 + side, dtype=torch.float64),
+                            torch.arange(x0, x0 + side, dtype=torch.float64), indexing="ij")
+    xs, ys = xs.reshape(-1), ys.reshape(-1)
+    t1 = time.perf_counter()
+    with torch.no_grad():
+        px = oracle.render_pixels(tab, xs, ys)
+    tgt = torch.as_tensor(target_np[:, y0:y0 + side, x0:x0 + side]).permute(1, 2, 0).reshape(-1, 3)
+    n_full = 3 * w["W"] * w["H"]
+    dC = 2.0 * (px["C"] - tgt.double()) / n_full
+    dtab = oracle.render_grads(tab, xs, ys, dC)
+    t_pix = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    sample_vjp(cur, cfg, dtab, first)
+    t_vjp = time.perf_counter() - t2
+    frac = (side * side) / (w["W"] * w["H"])
+    step_s = t_sample + t_vjp + t_pix / frac
+    return {"value": round(1.0 / step_s, 9), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"sampling of all {w['n_open'] + w['n_closed']} curves, brute-force blend and its "
+                      f"gradient at a {side}x{side} pixel crop ({side * side} of {w['W'] * w['H']} pixels, "
+                      f"time extrapolated by pixel count), sampling backward of all curves",
+            "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    _oracle_problem()
+    for _ in range(max(1, args.warmup)):
+        cpu_baseline(side=8)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(side=8)["value"])
+    total = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    w = _PROBLEM["w"]
+    cb = cpu_baseline(side=8)
+    cb["value"] = round(value, 9)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 9), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / value, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "W": w["W"], "H": w["H"],
+                                            "n_open": w["n_open"], "n_closed": w["n_closed"],
+                                            "gaussians_per_curve": w["g_open"], "tile": w["tile"]},
+            "cpu_baseline": cb, "wall_s": round(total, 2),
+            "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,265 @@
+/*
+ * bs.h -- C ABI of the GB300 Bezier Splatting rasterizer (libbs.so).
+ *
+ * The library implements the differentiable splatting rasterizer of
+ * "Bezier Splatting for Fast and Differentiable Vector Graphics Rendering"
+ * (Liu, Zhou, Zhao, Huang): 2D Gaussians sampled along cubic Bezier curves
+ * and inside closed curves (Section 3.3, Eq. 3-8), binned into screen tiles
+ * by (tile, depth) keys (Section 3.4), alpha-blended front to back
+ * (Eq. 9-12), and the reverse-order backward to the curve parameters.
+ *
+ * Conventions for every call
+ *   - All array pointers are DEVICE pointers owned by the caller, unless a
+ *     parameter says "host".  The library never allocates device memory.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t; NULL is
+ *     the legacy default stream).  The only call that synchronises is
+ *     bs_bin_tiles (one 8-byte read-back of the pair count) and
+ *     bs_device_status.
+ *   - Every call returns a bs_status.  Arguments are validated on the host
+ *     before anything is launched; an invalid argument returns
+ *     BS_ERR_INVALID_ARG and launches nothing.  bs_last_error() gives a
+ *     thread-local message for the last non-OK status.
+ *   - Errors found by a kernel (a bounded wait that ran out, a count that
+ *     overflowed) are recorded in a status word inside the binning
+ *     workspace; bs_device_status reads it.
+ *   - Coordinates are pixels: pixel (x, y) covers [x, x+1) x [y, y+1) and
+ *     its centre is (x + 0.5, y + 0.5).  Colours and opacities are the
+ *     activated values in [0, 1].
+ *   - Images are planar float32 [3][H][W]; per-pixel maps are [H][W].
+ *   - Only sm_103a is supported; other devices return BS_ERR_UNSUPPORTED.
+ */
+#ifndef BEZIER_SPLATTING_BS_H
+#define BEZIER_SPLATTING_BS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t, spelled without the CUDA headers. */
+typedef struct CUstream_st *bs_stream;
+
+typedef enum {
+  BS_OK = 0,
+  BS_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported parameter value */
+  BS_ERR_CUDA = 2,          /* a CUDA runtime call failed (message in bs_last_error) */
+  BS_ERR_CAPACITY = 3,      /* pair_capacity too small; *n_pairs_out holds the need  */
+  BS_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out (device status)    */
+  BS_ERR_NOT_FINITE = 5,    /* reserved: non-finite values detected                 */
+  BS_ERR_UNSUPPORTED = 6    /* device or configuration the library does not support */
+} bs_status;
+
+/*
+ * A set of curves (Section 3.2).  Open curves are 3 chained cubic segments
+ * (10 control points, the end of one segment is the start of the next) with
+ * a stroke width and one opacity per segment (Appendix D); closed curves are
+ * 4 chained cubic segments whose 13th point is the first one, stored as 12
+ * points, with one colour and one opacity (Appendix D).
+ * Curve i < n_open is open curve i; curve n_open + j is closed curve j.
+ */
+typedef struct {
+  int32_t n_open;
+  int32_t n_closed;
+  const float *open_ctrl;     /* [n_open][10][2] px                                  */
+  const float *open_width;    /* [n_open]        px, the y-scale of its Gaussians    */
+  const float *open_color;    /* [n_open][3]                                         */
+  const float *open_opac;     /* [n_open][3]     one per segment                     */
+  const float *closed_ctrl;   /* [n_closed][12][2] px                                */
+  const float *closed_color;  /* [n_closed][3]                                       */
+  const float *closed_opac;   /* [n_closed]                                          */
+  const uint32_t *draw_first; /* [n_open + n_closed] index of each curve's first
+                                 Gaussian in the draw-ordered table (bs_curve_order) */
+} bs_curves;
+
+/* Gradients in the layout of bs_curves (device, written by the callee). */
+typedef struct {
+  float *open_ctrl;     /* [n_open][10][2] */
+  float *open_width;    /* [n_open]        */
+  float *open_color;    /* [n_open][3]     */
+  float *open_opac;     /* [n_open][3]     */
+  float *closed_ctrl;   /* [n_closed][12][2] */
+  float *closed_color;  /* [n_closed][3]   */
+  float *closed_opac;   /* [n_closed]      */
+} bs_curves_grad;
+
+/* Sampling of Gaussians on curves (Section 3.3, Eq. 3-8). */
+typedef struct {
+  int32_t g_open;      /* K: samples per open curve, 2..1024                      */
+  int32_t rows_closed; /* R + 2: rows of a closed curve incl. both boundaries, >= 2 */
+  int32_t k_closed;    /* K: samples per row of a closed curve, >= 2;
+                          rows_closed * k_closed <= 4096                           */
+  float rho;           /* the density constant of Eq. 7, > 0                      */
+  float cov_eps;       /* isotropic covariance floor in px^2 (Sigma += eps I), >= 0 */
+} bs_sample_cfg;
+
+/* The canvas and its tiling (Section 3.4). */
+typedef struct {
+  int32_t width;   /* W px, 1..32768 */
+  int32_t height;  /* H px, 1..32768 */
+  int32_t tile;    /* tile side in px; 16 */
+  float bg[3];     /* background colour blended with the final transmittance */
+} bs_canvas;
+
+/*
+ * Gaussian table record: 12 float32 per Gaussian, in draw order (front
+ * first), 16-byte aligned rows:
+ *   [0] mx  [1] my              mean (px)
+ *   [2] ca  [3] cb  [4] cc      conic Sigma^-1 = [[ca, cb], [cb, cc]]
+ *   [5] o                       opacity
+ *   [6] r   [7] g   [8] b       colour
+ *   [9] ext_x [10] ext_y        half extents of the box holding every pixel
+ *                               centre with alpha >= 1/255; < 0: never binned
+ *   [11] 0
+ * Per-Gaussian gradient record: 12 float32, d/d(mx, my, ca, cb, cc, o, r, g, b)
+ * in [0..8], [9..11] = 0.  cb is the single off-diagonal entry, so
+ * d/d(cb) counts both of its appearances in d^T Sigma^-1 d.
+ */
+#define BS_GAUSS_FLOATS 12
+#define BS_DGAUSS_FLOATS 12
+
+/* Number of Gaussians the curves produce: n_open*g_open + n_closed*rows*k.
+ * Host arithmetic only.  Returns -1 on invalid arguments. */
+int64_t bs_num_gaussians(int32_t n_open, int32_t n_closed, const bs_sample_cfg *cfg);
+
+/*
+ * Draw order (Section 3.3: depth from curve area, small curves in front).
+ * The area key is computed in float32 with a fixed operation order: for a
+ * closed curve half the absolute shoelace sum of its 12-point control
+ * polygon, for an open curve the length of its 10-point control polygon
+ * times its width.  Curves are ranked by ascending key, equal keys by index.
+ *   rank_out  [n_open + n_closed]  0 = front-most        (device, written)
+ *   first_out [n_open + n_closed]  first Gaussian index   (device, written)
+ * curves->draw_first is not read.
+ */
+bs_status bs_curve_order(const bs_curves *curves, const bs_sample_cfg *cfg,
+                         uint32_t *rank_out, uint32_t *first_out, bs_stream stream);
+
+/*
+ * Sample Gaussians on curves (Section 3.3, Eq. 3-8; covariance Eq. 11-12).
+ * Open curve: K samples uniform in u = k/(K-1) over the 3-segment chain;
+ * sigma_x = |X_{k+1} - X_k| / rho (last sample: previous pair),
+ * sigma_y = width, theta from the central difference (ends: one-sided).
+ * Closed curve: rows r = 0..R+1 interpolate the control points of boundary
+ * A = P0..P6 and boundary B = P0,P11,...,P7,P6 with weights
+ * tau_r = (1 - cos(pi r/(R+1)))/2; K samples per row; sigma_y is the distance
+ * to the next row (last row: previous).  Sigma = R S S^T R^T + eps I.
+ *   gauss [n_gauss][12]  (device, written; n_gauss = bs_num_gaussians)
+ */
+bs_status bs_sample_curves(const bs_curves *curves, const bs_sample_cfg *cfg,
+                           float *gauss, bs_stream stream);
+
+/*
+ * Backward of bs_sample_curves: given dL/d(table record) [n_gauss][12],
+ * write dL/d(curve parameters).  Every array of grad is overwritten.
+ */
+bs_status bs_sample_curves_bwd(const bs_curves *curves, const bs_sample_cfg *cfg,
+                               const float *dgauss, const bs_curves_grad *grad,
+                               bs_stream stream);
+
+/* Workspace bytes bs_bin_tiles needs for n_gauss Gaussians and up to
+ * pair_capacity (tile, Gaussian) pairs.  Host arithmetic only. */
+bs_status bs_bin_tiles_workspace(int64_t n_gauss, const bs_canvas *canvas,
+                                 int64_t pair_capacity, size_t *bytes);
+
+/*
+ * Tile binning (Section 3.4, the tile pipeline of 3D Gaussian splatting).
+ * A Gaussian is listed in every tile that holds a pixel whose centre lies in
+ * its box [mx - ext_x, mx + ext_x] x [my - ext_y, my + ext_y], decided in
+ * float32 as: xlo = (mx - ext_x) - 0.5, xhi = (mx + ext_x) - 0.5,
+ * x0 = max(ceil(xlo), 0), x1 = min(floor(xhi), W - 1) (same for y).  Keys are
+ *     key = tile_id << gbits | g,  tile_id = ty * tiles_x + tx,
+ *     gbits = max(1, bit length of n_gauss - 1),
+ * and are sorted ascending by a hand-written stable LSD radix sort of the
+ * tile bits (decoupled look-back), so each tile's list is front to back.
+ * tile bits + gbits must be <= 32 (else BS_ERR_UNSUPPORTED).
+ *   ws, ws_bytes    scratch of bs_bin_tiles_workspace bytes (device)
+ *   pair_capacity   room in tile_keys and ws
+ *   n_pairs_out     (HOST) the number of pairs P; on BS_ERR_CAPACITY the
+ *                   number needed (nothing else is valid then)
+ *   tile_keys       [pair_capacity] sorted keys (device, written [0, P))
+ *   tile_ranges     [n_tiles][2] (start, end) into tile_keys (device, written)
+ * Synchronises the stream once to read P.
+ */
+bs_status bs_bin_tiles(const float *gauss, int64_t n_gauss, const bs_canvas *canvas,
+                       void *ws, size_t ws_bytes, int64_t pair_capacity,
+                       int64_t *n_pairs_out, uint32_t *tile_keys, uint32_t *tile_ranges,
+                       bs_stream stream);
+
+/*
+ * Forward blend (Eq. 9-10).  Per pixel, over its tile's list in order:
+ * alpha = min(0.99, o exp(-0.5 d^T Sigma^-1 d)); skipped if alpha < 1/255;
+ * the pixel stops at the first Gaussian that would bring its transmittance
+ * T below 1e-4 (not blended); C += c alpha T, T *= 1 - alpha; finally
+ * C += T bg.
+ *   img       [3][H][W]  (device, written)
+ *   T_final   [H][W]     final transmittance (device, written)
+ *   n_contrib [H][W]     entries of the tile list up to and including the
+ *                        last blended Gaussian, 0 if none (device, written)
+ */
+bs_status bs_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas *canvas,
+                        const uint32_t *tile_keys, const uint32_t *tile_ranges,
+                        float *img, float *T_final, uint32_t *n_contrib, bs_stream stream);
+
+/*
+ * bs_render_fwd plus work counters, for measurement: stats_out (device,
+ * 4 x uint64, zeroed and written) receives [0] the (pixel, list entry)
+ * evaluations performed, [1] the entries blended, [2] the sum over tiles of
+ * list length x 256 pixels, [3] 0.
+ */
+bs_status bs_render_stats(const float *gauss, int64_t n_gauss, const bs_canvas *canvas,
+                          const uint32_t *tile_keys, const uint32_t *tile_ranges,
+                          float *img, float *T_final, uint32_t *n_contrib,
+                          unsigned long long *stats_out, bs_stream stream);
+
+/*
+ * L2 term of Eq. 13 with lambda_1 = 1 averaged over the n entries:
+ * loss = mean((img - target)^2) (device double, written), and
+ * dL_dimg = 2 (img - target) / n (device, written).
+ */
+bs_status bs_l2_loss_grad(const float *img, const float *target, int64_t n,
+                          float *dL_dimg, double *loss_out, bs_stream stream);
+
+/*
+ * Backward of bs_render_fwd, then of bs_sample_curves.  Per pixel, walks its
+ * tile list from its last blended Gaussian to the front, recovering
+ * T_i = T_{i+1} / (1 - alpha_i) from T_final (no per-Gaussian state is
+ * stored), and accumulates dL/d(mean, conic, opacity, colour) per Gaussian.
+ *   dgauss [n_gauss][12]  per-Gaussian gradients (device, zeroed and written)
+ *   curves, cfg, grad     if grad is non-NULL, the curve gradients are
+ *                         written as by bs_sample_curves_bwd; if NULL only
+ *                         dgauss is produced and curves/cfg may be NULL.
+ */
+bs_status bs_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas *canvas,
+                        const uint32_t *tile_keys, const uint32_t *tile_ranges,
+                        const float *T_final, const uint32_t *n_contrib,
+                        const float *dL_dimg, float *dgauss,
+                        const bs_curves *curves, const bs_sample_cfg *cfg,
+                        const bs_curves_grad *grad, bs_stream stream);
+
+/* Synchronise the stream and read the device status word of a binning
+ * workspace: BS_OK or the first kernel-side error recorded since the
+ * workspace's last bs_bin_tiles call. */
+bs_status bs_device_status(const void *ws, size_t ws_bytes, int32_t *status_out,
+                           bs_stream stream);
+
+/* Test hook for the bounded waits of the sort.  Partition
+ * never_publish_partition (-1: none) never publishes its digit counts, and
+ * every look-back wait gives up after spin_limit polls (0: the default
+ * bound).  Applies to later bs_bin_tiles calls in this process; while a
+ * partition is held back the sorted keys are invalid and bs_device_status
+ * reports BS_ERR_TIMEOUT.  No wait is unbounded either way. */
+bs_status bs_debug_sort_fault(int32_t never_publish_partition, uint32_t spin_limit);
+
+/* Message of the last non-OK status on this thread ("" if none). */
+const char *bs_last_error(void);
+
+/* Name of a status code. */
+const char *bs_status_string(bs_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEZIER_SPLATTING_BS_H */

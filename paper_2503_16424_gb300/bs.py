@@ -1,0 +1,349 @@
+"""Thin ctypes binding of libbs.so with the C ABI's names.
+
+Argument marshalling only: every function takes torch CUDA tensors, checks
+their dtype/shape/contiguity, passes raw device pointers and the current
+stream to the library, and raises on a non-OK status.  All computation runs
+in the library's CUDA kernels; there is no fallback path.  Importing this
+module raises ImportError when libbs.so has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int32, c_int64, c_size_t, c_uint32, c_void_p
+from dataclasses import dataclass
+
+import torch
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libbs.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                      "(python -m paper_2503_16424_gb300.build_lib)")
+lib = ctypes.CDLL(LIB_PATH)
+
+GAUSS_FLOATS = 12
+DGAUSS_FLOATS = 12
+
+BS_OK, BS_ERR_INVALID_ARG, BS_ERR_CUDA, BS_ERR_CAPACITY, BS_ERR_TIMEOUT, BS_ERR_NOT_FINITE, \
+    BS_ERR_UNSUPPORTED = range(7)
+
+
+class bs_curves(ctypes.Structure):
+    _fields_ = [("n_open", c_int32), ("n_closed", c_int32),
+                ("open_ctrl", c_void_p), ("open_width", c_void_p), ("open_color", c_void_p),
+                ("open_opac", c_void_p), ("closed_ctrl", c_void_p), ("closed_color", c_void_p),
+                ("closed_opac", c_void_p), ("draw_first", c_void_p)]
+
+
+class bs_curves_grad(ctypes.Structure):
+    _fields_ = [("open_ctrl", c_void_p), ("open_width", c_void_p), ("open_color", c_void_p),
+                ("open_opac", c_void_p), ("closed_ctrl", c_void_p), ("closed_color", c_void_p),
+                ("closed_opac", c_void_p)]
+
+
+class bs_sample_cfg(ctypes.Structure):
+    _fields_ = [("g_open", c_int32), ("rows_closed", c_int32), ("k_closed", c_int32),
+                ("rho", c_float), ("cov_eps", c_float)]
+
+
+class bs_canvas(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("tile", c_int32), ("bg", c_float * 3)]
+
+
+def _sig(name, *args):
+    f = getattr(lib, name)
+    f.argtypes = list(args)
+    f.restype = c_int
+    return f
+
+
+_P = c_void_p
+lib.bs_num_gaussians.argtypes = [c_int32, c_int32, POINTER(bs_sample_cfg)]
+lib.bs_num_gaussians.restype = c_int64
+lib.bs_last_error.restype = c_char_p
+lib.bs_status_string.argtypes = [c_int]
+lib.bs_status_string.restype = c_char_p
+_sig("bs_curve_order", POINTER(bs_curves), POINTER(bs_sample_cfg), _P, _P, _P)
+_sig("bs_sample_curves", POINTER(bs_curves), POINTER(bs_sample_cfg), _P, _P)
+_sig("bs_sample_curves_bwd", POINTER(bs_curves), POINTER(bs_sample_cfg), _P, POINTER(bs_curves_grad), _P)
+_sig("bs_bin_tiles_workspace", c_int64, POINTER(bs_canvas), c_int64, POINTER(c_size_t))
+_sig("bs_bin_tiles", _P, c_int64, POINTER(bs_canvas), _P, c_size_t, c_int64, POINTER(c_int64), _P, _P, _P)
+_sig("bs_render_fwd", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P)
+_sig("bs_l2_loss_grad", _P, _P, c_int64, _P, _P, _P)
+_sig("bs_render_stats", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P, _P)
+_sig("bs_render_bwd", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P,
+     POINTER(bs_curves), POINTER(bs_sample_cfg), POINTER(bs_curves_grad), _P)
+_sig("bs_device_status", _P, c_size_t, POINTER(c_int32), _P)
+_sig("bs_debug_sort_fault", c_int32, c_uint32)
+
+
+class BSError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        name = lib.bs_status_string(status).decode()
+        super().__init__(f"{fn}: {name}: {lib.bs_last_error().decode()}")
+
+
+def _check(fn, status):
+    if status != BS_OK:
+        raise BSError(fn, status)
+
+
+def _stream():
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else c_void_p(0)
+
+
+def _want(t, dtype, shape=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+@dataclass
+class SampleCfg:
+    g_open: int = 16
+    rows_closed: int = 4
+    k_closed: int = 8
+    rho: float = 1.0
+    cov_eps: float = 0.3
+
+    def c(self):
+        return bs_sample_cfg(self.g_open, self.rows_closed, self.k_closed, self.rho, self.cov_eps)
+
+
+@dataclass
+class Canvas:
+    width: int
+    height: int
+    tile: int = 16
+    bg: tuple = (0.0, 0.0, 0.0)
+
+    def c(self):
+        return bs_canvas(self.width, self.height, self.tile, (c_float * 3)(*self.bg))
+
+    @property
+    def n_tiles(self):
+        t = self.tile
+        return ((self.width + t - 1) // t) * ((self.height + t - 1) // t)
+
+
+CURVE_FIELDS = ("open_ctrl", "open_width", "open_color", "open_opac",
+                "closed_ctrl", "closed_color", "closed_opac")
+
+
+@dataclass
+class CurveSet:
+    """Device curve parameters (float32, contiguous) in pixel space with
+    activated attributes; layouts as in bs.h."""
+    open_ctrl: torch.Tensor     # [No,10,2]
+    open_width: torch.Tensor    # [No]
+    open_color: torch.Tensor    # [No,3]
+    open_opac: torch.Tensor     # [No,3]
+    closed_ctrl: torch.Tensor   # [Nc,12,2]
+    closed_color: torch.Tensor  # [Nc,3]
+    closed_opac: torch.Tensor   # [Nc]
+
+    @property
+    def n_open(self):
+        return int(self.open_ctrl.shape[0])
+
+    @property
+    def n_closed(self):
+        return int(self.closed_ctrl.shape[0])
+
+    def check(self):
+        no, nc = self.n_open, self.n_closed
+        shapes = dict(open_ctrl=(no, 10, 2), open_width=(no,), open_color=(no, 3), open_opac=(no, 3),
+                      closed_ctrl=(nc, 12, 2), closed_color=(nc, 3), closed_opac=(nc,))
+        for k, s in shapes.items():
+            _want(getattr(self, k), torch.float32, s, k)
+        return self
+
+    def c(self, draw_first=None):
+        return bs_curves(self.n_open, self.n_closed, *(_ptr(getattr(self, k)) for k in CURVE_FIELDS),
+                         _ptr(draw_first))
+
+    @staticmethod
+    def from_arrays(arrays: dict, device="cuda"):
+        return CurveSet(**{k: torch.as_tensor(arrays[k], dtype=torch.float32, device=device).contiguous()
+                           for k in CURVE_FIELDS})
+
+    def zeros_like(self):
+        return CurveSet(**{k: torch.zeros_like(getattr(self, k)) for k in CURVE_FIELDS})
+
+    def grad_c(self):
+        return bs_curves_grad(*(_ptr(getattr(self, k)) for k in CURVE_FIELDS))
+
+
+def num_gaussians(n_open, n_closed, cfg: SampleCfg) -> int:
+    c = cfg.c()
+    n = lib.bs_num_gaussians(n_open, n_closed, ctypes.byref(c))
+    if n < 0:
+        raise ValueError("invalid sample configuration")
+    return int(n)
+
+
+def curve_order(curves: CurveSet, cfg: SampleCfg):
+    """rank [N] (0 = front) and first [N] Gaussian index, uint32 as int32."""
+    curves.check()
+    n = curves.n_open + curves.n_closed
+    dev = curves.open_ctrl.device
+    rank = torch.empty(n, dtype=torch.int32, device=dev)
+    first = torch.empty(n, dtype=torch.int32, device=dev)
+    c, k = curves.c(), cfg.c()
+    _check("bs_curve_order", lib.bs_curve_order(ctypes.byref(c), ctypes.byref(k), _ptr(rank), _ptr(first),
+                                                 _stream()))
+    return rank, first
+
+
+def sample_curves(curves: CurveSet, cfg: SampleCfg, first: torch.Tensor, out=None):
+    ng = num_gaussians(curves.n_open, curves.n_closed, cfg)
+    gauss = out if out is not None else torch.empty(ng, GAUSS_FLOATS, dtype=torch.float32,
+                                                    device=curves.open_ctrl.device)
+    _want(gauss, torch.float32, (ng, GAUSS_FLOATS), "gauss")
+    c, k = curves.c(first), cfg.c()
+    _check("bs_sample_curves", lib.bs_sample_curves(ctypes.byref(c), ctypes.byref(k), _ptr(gauss), _stream()))
+    return gauss
+
+
+def sample_curves_bwd(curves: CurveSet, cfg: SampleCfg, first: torch.Tensor, dgauss: torch.Tensor, grad=None):
+    grad = grad if grad is not None else curves.zeros_like()
+    c, k, g = curves.c(first), cfg.c(), grad.grad_c()
+    _want(dgauss, torch.float32, None, "dgauss")
+    _check("bs_sample_curves_bwd", lib.bs_sample_curves_bwd(ctypes.byref(c), ctypes.byref(k), _ptr(dgauss),
+                                                             ctypes.byref(g), _stream()))
+    return grad
+
+
+def bin_tiles_workspace(n_gauss: int, canvas: Canvas, pair_capacity: int) -> int:
+    cv = canvas.c()
+    nb = c_size_t(0)
+    _check("bs_bin_tiles_workspace", lib.bs_bin_tiles_workspace(n_gauss, ctypes.byref(cv), pair_capacity,
+                                                                 ctypes.byref(nb)))
+    return int(nb.value)
+
+
+class Binning:
+    """Device buffers of one binning: workspace, sorted keys, tile ranges.
+    Grows its capacity when a call reports BS_ERR_CAPACITY."""
+
+    def __init__(self, canvas: Canvas, device="cuda", pair_capacity: int = 1 << 20):
+        self.canvas = canvas
+        self.device = device
+        self.capacity = 0
+        self.n_gauss = -1
+        self.ws = None
+        self.keys = None
+        self.ranges = torch.empty(canvas.n_tiles, 2, dtype=torch.int32, device=device)
+        self._want_capacity = pair_capacity
+        self.n_pairs = 0
+
+    def _alloc(self, n_gauss, capacity):
+        nbytes = bin_tiles_workspace(n_gauss, self.canvas, capacity)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.keys = torch.empty(max(1, capacity), dtype=torch.int32, device=self.device)
+        self.capacity = capacity
+        self.n_gauss = n_gauss
+
+    def run(self, gauss: torch.Tensor):
+        n_gauss = int(gauss.shape[0])
+        _want(gauss, torch.float32, (n_gauss, GAUSS_FLOATS), "gauss")
+        if self.ws is None or n_gauss != self.n_gauss or self.capacity < self._want_capacity:
+            self._alloc(n_gauss, max(self._want_capacity, self.capacity))
+        cv = self.canvas.c()
+        for _ in range(2):
+            n_pairs = c_int64(0)
+            st = lib.bs_bin_tiles(_ptr(gauss), n_gauss, ctypes.byref(cv), _ptr(self.ws), self.ws.numel(),
+                                  self.capacity, ctypes.byref(n_pairs), _ptr(self.keys), _ptr(self.ranges),
+                                  _stream())
+            if st == BS_ERR_CAPACITY:
+                self._want_capacity = int(n_pairs.value * 1.25) + 1024
+                self._alloc(n_gauss, self._want_capacity)
+                continue
+            _check("bs_bin_tiles", st)
+            self.n_pairs = int(n_pairs.value)
+            return self
+        raise BSError("bs_bin_tiles", BS_ERR_CAPACITY)
+
+    def device_status(self) -> int:
+        out = c_int32(0)
+        _check("bs_device_status", lib.bs_device_status(_ptr(self.ws), self.ws.numel(), ctypes.byref(out),
+                                                         _stream()))
+        return int(out.value)
+
+
+def render_fwd(gauss: torch.Tensor, canvas: Canvas, binning: Binning, out=None):
+    W, H = canvas.width, canvas.height
+    dev = gauss.device
+    if out is None:
+        out = (torch.empty(3, H, W, dtype=torch.float32, device=dev),
+               torch.empty(H, W, dtype=torch.float32, device=dev),
+               torch.empty(H, W, dtype=torch.int32, device=dev))
+    img, T, nc = out
+    cv = canvas.c()
+    _check("bs_render_fwd", lib.bs_render_fwd(_ptr(gauss), int(gauss.shape[0]), ctypes.byref(cv),
+                                               _ptr(binning.keys), _ptr(binning.ranges), _ptr(img), _ptr(T),
+                                               _ptr(nc), _stream()))
+    return img, T, nc
+
+
+def render_stats(gauss: torch.Tensor, canvas: Canvas, binning: Binning):
+    """Work counters of a forward blend: dict(evals, blended, tile_px_entries)."""
+    W, H = canvas.width, canvas.height
+    dev = gauss.device
+    img = torch.empty(3, H, W, dtype=torch.float32, device=dev)
+    T = torch.empty(H, W, dtype=torch.float32, device=dev)
+    nc = torch.empty(H, W, dtype=torch.int32, device=dev)
+    st = torch.zeros(4, dtype=torch.int64, device=dev)
+    cv = canvas.c()
+    _check("bs_render_stats", lib.bs_render_stats(_ptr(gauss), int(gauss.shape[0]), ctypes.byref(cv),
+                                                   _ptr(binning.keys), _ptr(binning.ranges), _ptr(img), _ptr(T),
+                                                   _ptr(nc), _ptr(st), _stream()))
+    v = st.cpu().tolist()
+    return dict(evals=v[0], blended=v[1], tile_px_entries=v[2], n_contrib_sum=int(nc.sum().item()))
+
+
+def l2_loss_grad(img: torch.Tensor, target: torch.Tensor, dimg=None, loss=None):
+    _want(img, torch.float32, None, "img")
+    _want(target, torch.float32, tuple(img.shape), "target")
+    dimg = dimg if dimg is not None else torch.empty_like(img)
+    loss = loss if loss is not None else torch.empty((), dtype=torch.float64, device=img.device)
+    _check("bs_l2_loss_grad", lib.bs_l2_loss_grad(_ptr(img), _ptr(target), img.numel(), _ptr(dimg),
+                                                   c_void_p(loss.data_ptr()), _stream()))
+    return loss, dimg
+
+
+def render_bwd(gauss, canvas: Canvas, binning: Binning, T_final, n_contrib, dimg, dgauss=None,
+               curves: CurveSet = None, cfg: SampleCfg = None, first=None, grad: CurveSet = None):
+    """Per-Gaussian gradients, and (when curves is given) curve gradients."""
+    ng = int(gauss.shape[0])
+    dgauss = dgauss if dgauss is not None else torch.empty(ng, DGAUSS_FLOATS, dtype=torch.float32,
+                                                           device=gauss.device)
+    cv = canvas.c()
+    if curves is not None:
+        grad = grad if grad is not None else curves.zeros_like()
+        c, k, g = curves.c(first), cfg.c(), grad.grad_c()
+        cp, kp, gp = ctypes.byref(c), ctypes.byref(k), ctypes.byref(g)
+    else:
+        cp = kp = gp = None
+    _check("bs_render_bwd", lib.bs_render_bwd(_ptr(gauss), ng, ctypes.byref(cv), _ptr(binning.keys),
+                                               _ptr(binning.ranges), _ptr(T_final), _ptr(n_contrib),
+                                               _ptr(dimg), _ptr(dgauss), cp, kp, gp, _stream()))
+    return dgauss, grad
+
+
+def debug_sort_fault(never_publish_partition: int = -1, spin_limit: int = 0):
+    """Test hook: make one sort partition never publish its counts, with a
+    short bound on the look-back wait (-1 restores normal operation)."""
+    _check("bs_debug_sort_fault", lib.bs_debug_sort_fault(never_publish_partition, spin_limit))

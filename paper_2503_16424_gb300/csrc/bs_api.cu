@@ -1,0 +1,260 @@
+// The C ABI of libbs.so: argument validation on the host, then the launchers.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+
+#include "bs_internal.cuh"
+
+namespace bs {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+const char *last_error_cstr() { return g_last_error.c_str(); }
+
+void set_error(const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+bs_status cuda_status(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return BS_OK;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return BS_ERR_CUDA;
+}
+
+// sm_103 only; checked once per device.
+bs_status check_device() {
+  int dev = 0;
+  BS_CUDA(cudaGetDevice(&dev));
+  static int checked[64] = {0};  // 0 unknown, 1 ok, 2 unsupported
+  if (dev >= 0 && dev < 64 && checked[dev] == 1) return BS_OK;
+  int major = 0, minor = 0;
+  BS_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  BS_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+  const bool ok = major == 10 && minor == 3;
+  if (dev >= 0 && dev < 64) checked[dev] = ok ? 1 : 2;
+  if (!ok) {
+    set_error("device %d is sm_%d%d; this library is built for sm_103a only", dev, major, minor);
+    return BS_ERR_UNSUPPORTED;
+  }
+  return BS_OK;
+}
+
+void debug_set_sort_fault(int never_publish_part, uint32_t spin_limit);
+const char *last_error_cstr();
+
+}  // namespace bs
+
+using namespace bs;
+
+namespace {
+
+bs_status invalid(const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  set_error("%s", buf);
+  return BS_ERR_INVALID_ARG;
+}
+
+bs_status check_cfg(const bs_sample_cfg *cfg) {
+  if (!cfg) return invalid("cfg is NULL");
+  if (cfg->g_open < 2 || cfg->g_open > 1024) return invalid("g_open %d not in [2, 1024]", cfg->g_open);
+  if (cfg->rows_closed < 2 || cfg->k_closed < 2) return invalid("rows_closed and k_closed must be >= 2");
+  if ((int64_t)cfg->rows_closed * cfg->k_closed > kMaxSamplesPerCurve)
+    return invalid("rows_closed * k_closed > %d", kMaxSamplesPerCurve);
+  if (!(cfg->rho > 0.f)) return invalid("rho must be > 0");
+  if (!(cfg->cov_eps >= 0.f)) return invalid("cov_eps must be >= 0");
+  return BS_OK;
+}
+
+bs_status check_curves(const bs_curves *c, bool need_first) {
+  if (!c) return invalid("curves is NULL");
+  if (c->n_open < 0 || c->n_closed < 0) return invalid("negative curve count");
+  if (c->n_open > 0 && (!c->open_ctrl || !c->open_width || !c->open_color || !c->open_opac))
+    return invalid("open curve arrays must be non-NULL when n_open > 0");
+  if (c->n_closed > 0 && (!c->closed_ctrl || !c->closed_color || !c->closed_opac))
+    return invalid("closed curve arrays must be non-NULL when n_closed > 0");
+  if (need_first && c->n_open + c->n_closed > 0 && !c->draw_first) return invalid("draw_first is NULL");
+  if ((int64_t)c->n_open + c->n_closed > (1 << 30)) return invalid("too many curves");
+  return BS_OK;
+}
+
+bs_status check_canvas(const bs_canvas *cv) {
+  if (!cv) return invalid("canvas is NULL");
+  if (cv->width < 1 || cv->height < 1 || cv->width > 32768 || cv->height > 32768)
+    return invalid("canvas %dx%d out of range", cv->width, cv->height);
+  if (cv->tile != 16) {
+    set_error("tile side %d not supported (16)", cv->tile);
+    return BS_ERR_UNSUPPORTED;
+  }
+  return BS_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int64_t bs_num_gaussians(int32_t n_open, int32_t n_closed, const bs_sample_cfg *cfg) {
+  if (n_open < 0 || n_closed < 0 || check_cfg(cfg) != BS_OK) return -1;
+  return (int64_t)n_open * cfg->g_open + (int64_t)n_closed * cfg->rows_closed * cfg->k_closed;
+}
+
+bs_status bs_curve_order(const bs_curves *curves, const bs_sample_cfg *cfg, uint32_t *rank_out,
+                         uint32_t *first_out, bs_stream stream) {
+  BS_TRY(check_curves(curves, false));
+  BS_TRY(check_cfg(cfg));
+  const int64_t n = (int64_t)curves->n_open + curves->n_closed;
+  if (n > 0 && (!rank_out || !first_out)) return invalid("rank_out/first_out is NULL");
+  if (bs_num_gaussians(curves->n_open, curves->n_closed, cfg) > (1ll << 31) - 1)
+    return invalid("too many Gaussians");
+  BS_TRY(check_device());
+  return launch_curve_order(*curves, *cfg, rank_out, first_out, (cudaStream_t)stream);
+}
+
+bs_status bs_sample_curves(const bs_curves *curves, const bs_sample_cfg *cfg, float *gauss, bs_stream stream) {
+  BS_TRY(check_curves(curves, true));
+  BS_TRY(check_cfg(cfg));
+  const int64_t ng = bs_num_gaussians(curves->n_open, curves->n_closed, cfg);
+  if (ng > (1ll << 31) - 1) return invalid("too many Gaussians");
+  if (ng > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  BS_TRY(check_device());
+  return launch_sample_fwd(*curves, *cfg, gauss, (cudaStream_t)stream);
+}
+
+bs_status bs_sample_curves_bwd(const bs_curves *curves, const bs_sample_cfg *cfg, const float *dgauss,
+                               const bs_curves_grad *grad, bs_stream stream) {
+  BS_TRY(check_curves(curves, true));
+  BS_TRY(check_cfg(cfg));
+  if (!grad) return invalid("grad is NULL");
+  if (curves->n_open > 0 && (!grad->open_ctrl || !grad->open_width || !grad->open_color || !grad->open_opac))
+    return invalid("open gradient arrays must be non-NULL");
+  if (curves->n_closed > 0 && (!grad->closed_ctrl || !grad->closed_color || !grad->closed_opac))
+    return invalid("closed gradient arrays must be non-NULL");
+  const int64_t ng = bs_num_gaussians(curves->n_open, curves->n_closed, cfg);
+  if (ng > 0 && (!dgauss || !aligned16(dgauss))) return invalid("dgauss must be a 16-byte aligned device pointer");
+  BS_TRY(check_device());
+  return launch_sample_bwd(*curves, *cfg, dgauss, *grad, (cudaStream_t)stream);
+}
+
+bs_status bs_bin_tiles_workspace(int64_t n_gauss, const bs_canvas *canvas, int64_t pair_capacity, size_t *bytes) {
+  BS_TRY(check_canvas(canvas));
+  if (!bytes) return invalid("bytes is NULL");
+  BinPlan p;
+  BS_TRY(plan_binning(n_gauss, *canvas, pair_capacity, &p));
+  *bytes = p.bytes;
+  return BS_OK;
+}
+
+bs_status bs_bin_tiles(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, void *ws, size_t ws_bytes,
+                       int64_t pair_capacity, int64_t *n_pairs_out, uint32_t *tile_keys, uint32_t *tile_ranges,
+                       bs_stream stream) {
+  BS_TRY(check_canvas(canvas));
+  if (!n_pairs_out) return invalid("n_pairs_out is NULL");
+  *n_pairs_out = 0;
+  BinPlan p;
+  BS_TRY(plan_binning(n_gauss, *canvas, pair_capacity, &p));
+  if (!ws || ws_bytes < p.bytes || !aligned16(ws))
+    return invalid("workspace needs %zu bytes (16-byte aligned), got %zu", p.bytes, ws_bytes);
+  if (n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  if (!tile_ranges || !aligned16(tile_ranges)) return invalid("tile_ranges must be an 8-byte aligned device pointer");
+  if (pair_capacity > 0 && !tile_keys) return invalid("tile_keys is NULL");
+  BS_TRY(check_device());
+  return run_binning(p, gauss, *canvas, ws, n_pairs_out, tile_keys, tile_ranges, (cudaStream_t)stream);
+}
+
+bs_status bs_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, const uint32_t *tile_keys,
+                        const uint32_t *tile_ranges, float *img, float *T_final, uint32_t *n_contrib,
+                        bs_stream stream) {
+  BS_TRY(check_canvas(canvas));
+  if (n_gauss < 0 || n_gauss > (1ll << 31) - 1) return invalid("n_gauss out of range");
+  if (n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  if (!tile_ranges || !img || !T_final || !n_contrib) return invalid("NULL output or tile_ranges");
+  BS_TRY(check_device());
+  return launch_render_fwd(gauss, n_gauss, *canvas, gauss_bits(n_gauss), tile_keys, tile_ranges, img, T_final, n_contrib,
+                           (cudaStream_t)stream);
+}
+
+bs_status bs_render_stats(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, const uint32_t *tile_keys,
+                          const uint32_t *tile_ranges, float *img, float *T_final, uint32_t *n_contrib,
+                          unsigned long long *stats_out, bs_stream stream) {
+  BS_TRY(check_canvas(canvas));
+  if (n_gauss < 0 || n_gauss > (1ll << 31) - 1) return invalid("n_gauss out of range");
+  if (n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  if (!tile_ranges || !img || !T_final || !n_contrib || !stats_out) return invalid("NULL output or tile_ranges");
+  BS_TRY(check_device());
+  return launch_render_fwd(gauss, n_gauss, *canvas, gauss_bits(n_gauss), tile_keys, tile_ranges, img, T_final,
+                           n_contrib, (cudaStream_t)stream, stats_out);
+}
+
+bs_status bs_l2_loss_grad(const float *img, const float *target, int64_t n, float *dL_dimg, double *loss_out,
+                          bs_stream stream) {
+  if (n < 0) return invalid("n < 0");
+  if (!loss_out || (n > 0 && (!img || !target || !dL_dimg))) return invalid("NULL pointer");
+  BS_TRY(check_device());
+  return launch_l2(img, target, n, dL_dimg, loss_out, (cudaStream_t)stream);
+}
+
+bs_status bs_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, const uint32_t *tile_keys,
+                        const uint32_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
+                        const float *dL_dimg, float *dgauss, const bs_curves *curves, const bs_sample_cfg *cfg,
+                        const bs_curves_grad *grad, bs_stream stream) {
+  BS_TRY(check_canvas(canvas));
+  if (n_gauss < 0 || n_gauss > (1ll << 31) - 1) return invalid("n_gauss out of range");
+  if (n_gauss > 0 && (!gauss || !aligned16(gauss) || !dgauss || !aligned16(dgauss)))
+    return invalid("gauss/dgauss must be 16-byte aligned device pointers");
+  if (!tile_ranges || !T_final || !n_contrib || !dL_dimg) return invalid("NULL input");
+  if (grad) {
+    BS_TRY(check_curves(curves, true));
+    BS_TRY(check_cfg(cfg));
+    if (bs_num_gaussians(curves->n_open, curves->n_closed, cfg) != n_gauss)
+      return invalid("n_gauss does not match the curves and cfg");
+  }
+  BS_TRY(check_device());
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (n_gauss > 0)
+    BS_TRY(launch_render_bwd(gauss, n_gauss, *canvas, gauss_bits(n_gauss), tile_keys, tile_ranges, T_final,
+                             n_contrib, dL_dimg, dgauss, s));
+  if (grad) return bs_sample_curves_bwd(curves, cfg, dgauss, grad, stream);
+  return BS_OK;
+}
+
+bs_status bs_device_status(const void *ws, size_t ws_bytes, int32_t *status_out, bs_stream stream) {
+  if (!ws || !status_out) return invalid("NULL pointer");
+  return read_device_status(ws, ws_bytes, status_out, (cudaStream_t)stream);
+}
+
+bs_status bs_debug_sort_fault(int32_t never_publish_partition, uint32_t spin_limit) {
+  debug_set_sort_fault(never_publish_partition, spin_limit);
+  return BS_OK;
+}
+
+const char *bs_last_error(void) { return last_error_cstr(); }
+
+const char *bs_status_string(bs_status status) {
+  switch (status) {
+    case BS_OK: return "BS_OK";
+    case BS_ERR_INVALID_ARG: return "BS_ERR_INVALID_ARG";
+    case BS_ERR_CUDA: return "BS_ERR_CUDA";
+    case BS_ERR_CAPACITY: return "BS_ERR_CAPACITY";
+    case BS_ERR_TIMEOUT: return "BS_ERR_TIMEOUT";
+    case BS_ERR_NOT_FINITE: return "BS_ERR_NOT_FINITE";
+    case BS_ERR_UNSUPPORTED: return "BS_ERR_UNSUPPORTED";
+  }
+  return "BS_ERR_UNKNOWN";
+}
+
+}  // extern "C"

@@ -1,0 +1,461 @@
+// Curves -> Gaussians: draw order (Section 3.3 "depth from area"), sampling
+// (Section 3.3, Eq. 3-8, covariance Eq. 11-12) and its backward.
+//
+// One CTA per curve.  The CTA evaluates the curve's sample points X into
+// shared memory, then each thread turns one sample and its neighbours into
+// a Gaussian record (forward) or pushes one Gaussian's gradient back to the
+// sample points and from there, with the Bernstein weights of Eq. 1-2, to the
+// control points (backward).  A curve's Gaussians are contiguous in the
+// draw-ordered table, so the backward needs no global atomics.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "bs_internal.cuh"
+
+namespace bs {
+namespace {
+
+constexpr int kCurveThreads = 128;
+
+struct Cfg {
+  int g_open, rows, kc;
+  float rho, eps;
+};
+
+__device__ __forceinline__ void bern3(float t, float w[4]) {
+  const float u = 1.0f - t;
+  w[0] = u * u * u;
+  w[1] = 3.0f * u * u * t;
+  w[2] = 3.0f * u * t * t;
+  w[3] = t * t * t;
+}
+
+// Segment and local parameter of sample k of K on a chain of S segments:
+// u = k/(K-1), s = min(floor(S u), S-1), t = S u - s (integer decisions).
+__device__ __forceinline__ void chain_param(int k, int K, int S, int *seg, float *t) {
+  int s = (S * k) / (K - 1);
+  if (s > S - 1) s = S - 1;
+  *seg = s;
+  *t = __fdiv_rn((float)(S * k - s * (K - 1)), (float)(K - 1));
+}
+
+// Boundary groups of a closed curve: A = P0..P6, B = P0, P11, ..., P7, P6.
+__device__ __forceinline__ int closed_b_index(int j) { return (j == 0 || j == 6) ? j : 12 - j; }
+
+// tau_r = (1 - cos(pi r/(R+1)))/2 with rows = R + 2.
+__device__ __forceinline__ float closed_tau(int r, int rows) {
+  return 0.5f * (1.0f - cospif((float)r / (float)(rows - 1)));
+}
+
+__device__ __forceinline__ float2 ld2(const float *p, int i) { return make_float2(p[2 * i], p[2 * i + 1]); }
+
+// Sample point X of a curve into shared memory; returns the number of samples.
+__device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, float2 *X) {
+  if (curve < c.n_open) {
+    const float *P = c.open_ctrl + (size_t)curve * 20;
+    const int K = cfg.g_open;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      int s;
+      float t, w[4];
+      chain_param(k, K, 3, &s, &t);
+      bern3(t, w);
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 p = ld2(P, 3 * s + i);
+        acc.x += w[i] * p.x;
+        acc.y += w[i] * p.y;
+      }
+      X[k] = acc;
+    }
+    return K;
+  }
+  const float *P = c.closed_ctrl + (size_t)(curve - c.n_open) * 24;
+  const int K = cfg.kc, R2 = cfg.rows, n = R2 * K;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int r = idx / K, k = idx - r * K;
+    const float tau = closed_tau(r, R2);
+    int s;
+    float t, w[4];
+    chain_param(k, K, 2, &s, &t);
+    bern3(t, w);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = 3 * s + i;
+      const float2 a = ld2(P, j), b = ld2(P, closed_b_index(j));
+      const float qx = (1.0f - tau) * a.x + tau * b.x;   // Eq. 4
+      const float qy = (1.0f - tau) * a.y + tau * b.y;
+      acc.x += w[i] * qx;
+      acc.y += w[i] * qy;
+    }
+    X[idx] = acc;
+  }
+  return n;
+}
+
+// Local geometry of one sample (Eq. 7-8): the along-row difference e, the
+// tangent difference t, the across-row difference f (closed only), the
+// scales and the unit tangent (c, s).
+struct Local {
+  float2 e, t, f;
+  int e_hi, e_lo, t_hi, t_lo, f_hi, f_lo;  // sample indices the differences use
+  float le, lt, lf;                         // their lengths
+  float sx, sy, c, s;
+};
+
+__device__ __forceinline__ Local local_geometry(const float2 *X, int idx, int K, int R2, bool closed,
+                                                float width, float rho) {
+  Local L;
+  const int r = closed ? idx / K : 0;
+  const int k = idx - r * K;
+  const int row = r * K;
+  if (k + 1 < K) { L.e_hi = row + k + 1; L.e_lo = row + k; }
+  else { L.e_hi = row + k; L.e_lo = row + k - 1; }
+  if (k == 0) { L.t_hi = row + 1; L.t_lo = row; }
+  else if (k == K - 1) { L.t_hi = row + k; L.t_lo = row + k - 1; }
+  else { L.t_hi = row + k + 1; L.t_lo = row + k - 1; }
+  L.e = make_float2(X[L.e_hi].x - X[L.e_lo].x, X[L.e_hi].y - X[L.e_lo].y);
+  L.t = make_float2(X[L.t_hi].x - X[L.t_lo].x, X[L.t_hi].y - X[L.t_lo].y);
+  L.le = sqrtf(L.e.x * L.e.x + L.e.y * L.e.y);
+  L.lt = sqrtf(L.t.x * L.t.x + L.t.y * L.t.y);
+  L.sx = L.le / rho;
+  if (closed) {
+    if (r + 1 < R2) { L.f_hi = idx + K; L.f_lo = idx; }
+    else { L.f_hi = idx; L.f_lo = idx - K; }
+    L.f = make_float2(X[L.f_hi].x - X[L.f_lo].x, X[L.f_hi].y - X[L.f_lo].y);
+    L.lf = sqrtf(L.f.x * L.f.x + L.f.y * L.f.y);
+    L.sy = L.lf / rho;
+  } else {
+    L.f = make_float2(0.f, 0.f);
+    L.f_hi = L.f_lo = idx;
+    L.lf = 0.f;
+    L.sy = width;
+  }
+  if (L.lt > 0.f) { L.c = L.t.x / L.lt; L.s = L.t.y / L.lt; }
+  else { L.c = 1.f; L.s = 0.f; }
+  return L;
+}
+
+// Sigma = R S S^T R^T + eps I (Eq. 11-12) with R from the unit tangent.
+__device__ __forceinline__ void covariance(const Local &L, float eps, float *sxx, float *sxy, float *syy) {
+  const float a = L.sx * L.sx, b = L.sy * L.sy;
+  *sxx = a * L.c * L.c + b * L.s * L.s + eps;
+  *sxy = (a - b) * L.c * L.s;
+  *syy = a * L.s * L.s + b * L.c * L.c + eps;
+}
+
+// Sigma^-1 from the same eigen-decomposition, without a 2x2 determinant:
+// Q = u u^T / (sx^2 + eps) + v v^T / (sy^2 + eps), u = (c, s), v = (-s, c).
+__device__ __forceinline__ void conic(const Local &L, float eps, float *qa, float *qb, float *qc) {
+  const float ix = 1.0f / (L.sx * L.sx + eps), iy = 1.0f / (L.sy * L.sy + eps);
+  *qa = ix * L.c * L.c + iy * L.s * L.s;
+  *qb = (ix - iy) * L.c * L.s;
+  *qc = ix * L.s * L.s + iy * L.c * L.c;
+}
+
+struct CurveAttr {
+  float width;
+  float opac;
+  float3 col;
+};
+
+__device__ __forceinline__ CurveAttr curve_attr(const bs_curves &c, int curve, int seg) {
+  CurveAttr a;
+  if (curve < c.n_open) {
+    a.width = c.open_width[curve];
+    a.opac = c.open_opac[curve * 3 + seg];
+    a.col = make_float3(c.open_color[curve * 3], c.open_color[curve * 3 + 1], c.open_color[curve * 3 + 2]);
+  } else {
+    const int j = curve - c.n_open;
+    a.width = 0.f;
+    a.opac = c.closed_opac[j];
+    a.col = make_float3(c.closed_color[j * 3], c.closed_color[j * 3 + 1], c.closed_color[j * 3 + 2]);
+  }
+  return a;
+}
+
+__global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss) {
+  extern __shared__ float2 X[];  // [max samples per curve]
+  const int curve = blockIdx.x;
+  const bool closed = curve >= c.n_open;
+  const int n = eval_samples(c, cfg, curve, X);
+  __syncthreads();
+  const int K = closed ? cfg.kc : cfg.g_open;
+  const uint32_t first = c.draw_first[curve];
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    int seg = 0;
+    if (!closed) {
+      float t;
+      chain_param(idx, K, 3, &seg, &t);
+    }
+    const CurveAttr at = curve_attr(c, curve, seg);
+    const Local L = local_geometry(X, idx, K, cfg.rows, closed, at.width, cfg.rho);
+    float sxx, sxy, syy, qa, qb, qc;
+    covariance(L, cfg.eps, &sxx, &sxy, &syy);
+    conic(L, cfg.eps, &qa, &qb, &qc);
+    float ex = -1.f, ey = -1.f;
+    if (at.opac >= kAlphaMin) {
+      const float lth = logf(255.0f * at.opac);  // alpha >= 1/255 <=> 0.5 d^T Q d <= lth
+      ex = sqrtf(2.0f * lth * sxx) + kExtPad;
+      ey = sqrtf(2.0f * lth * syy) + kExtPad;
+    }
+    float4 *rec = reinterpret_cast<float4 *>(gauss + (size_t)(first + idx) * BS_GAUSS_FLOATS);
+    rec[0] = make_float4(X[idx].x, X[idx].y, qa, qb);
+    rec[1] = make_float4(qc, at.opac, at.col.x, at.col.y);
+    rec[2] = make_float4(at.col.z, ex, ey, 0.f);
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void sadd2(float2 *p, float x, float y) {
+  atomicAdd(&p->x, x);
+  atomicAdd(&p->y, y);
+}
+
+__global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
+                                                                   bs_curves_grad g, int n_max) {
+  extern __shared__ float2 X[];  // [n_max] sample points, then [n_max] their gradients
+  float2 *dX = X + n_max;
+  __shared__ float2 dP[12];
+  __shared__ float sAttr[8];  // opac[3] (open) or opac (closed), colour[3], width
+  const int curve = blockIdx.x;
+  const bool closed = curve >= c.n_open;
+  for (int i = threadIdx.x; i < 12; i += blockDim.x) dP[i] = make_float2(0.f, 0.f);
+  if (threadIdx.x < 8) sAttr[threadIdx.x] = 0.f;
+  const int n = eval_samples(c, cfg, curve, X);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dX[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int K = closed ? cfg.kc : cfg.g_open;
+  const uint32_t first = c.draw_first[curve];
+  const int lane = threadIdx.x & 31;
+  const int n_rounds = div_up(n, blockDim.x);
+  for (int round = 0; round < n_rounds; ++round) {
+    const int idx = round * blockDim.x + threadIdx.x;
+    float d_op[3] = {0.f, 0.f, 0.f}, d_col[3] = {0.f, 0.f, 0.f}, d_w = 0.f;
+    if (idx < n) {
+      int seg = 0;
+      if (!closed) {
+        float t;
+        chain_param(idx, K, 3, &seg, &t);
+      }
+      const CurveAttr at = curve_attr(c, curve, seg);
+      const Local L = local_geometry(X, idx, K, cfg.rows, closed, at.width, cfg.rho);
+      float qa, qb, qc;
+      conic(L, cfg.eps, &qa, &qb, &qc);
+      const float *dg = dgauss + (size_t)(first + idx) * BS_DGAUSS_FLOATS;
+      const float4 d0 = *reinterpret_cast<const float4 *>(dg);
+      const float4 d1 = *reinterpret_cast<const float4 *>(dg + 4);
+      const float d8 = dg[8];
+      // dL/dSigma = -Q G Q with G the symmetric gradient of the conic.
+      const float ga = d0.z, gb = 0.5f * d0.w, gc = d1.x;
+      const float t00 = qa * ga + qb * gb, t01 = qa * gb + qb * gc;  // T = Q G
+      const float t10 = qb * ga + qc * gb, t11 = qb * gb + qc * gc;
+      const float mxx = -(t00 * qa + t01 * qb);
+      const float mxy = -(t00 * qb + t01 * qc);
+      const float myy = -(t10 * qb + t11 * qc);
+      const float cc = L.c * L.c, ss = L.s * L.s, cs = L.c * L.s;
+      const float dsx = 2.0f * L.sx * (mxx * cc + 2.0f * mxy * cs + myy * ss);
+      const float dsy = 2.0f * L.sy * (mxx * ss - 2.0f * mxy * cs + myy * cc);
+      const float dth = (L.sx * L.sx - L.sy * L.sy) * (2.0f * cs * (myy - mxx) + 2.0f * (cc - ss) * mxy);
+      // mean
+      sadd2(&dX[idx], d0.x, d0.y);
+      // sigma_x = |e| / rho
+      if (L.le > 0.f) {
+        const float k = dsx / (L.le * cfg.rho);
+        sadd2(&dX[L.e_hi], k * L.e.x, k * L.e.y);
+        sadd2(&dX[L.e_lo], -k * L.e.x, -k * L.e.y);
+      }
+      // theta = atan2(t_y, t_x)
+      if (L.lt > 0.f) {
+        const float k = dth / (L.lt * L.lt);
+        sadd2(&dX[L.t_hi], -k * L.t.y, k * L.t.x);
+        sadd2(&dX[L.t_lo], k * L.t.y, -k * L.t.x);
+      }
+      if (closed) {
+        if (L.lf > 0.f) {
+          const float k = dsy / (L.lf * cfg.rho);
+          sadd2(&dX[L.f_hi], k * L.f.x, k * L.f.y);
+          sadd2(&dX[L.f_lo], -k * L.f.x, -k * L.f.y);
+        }
+        d_op[0] = d1.y;
+      } else {
+        d_w = dsy;
+        d_op[seg] = d1.y;
+      }
+      d_col[0] = d1.z;
+      d_col[1] = d1.w;
+      d_col[2] = d8;
+    }
+    // per-curve scalars: warp sums, then one shared atomic per warp
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float a = warp_sum(d_op[i]);
+      const float b = warp_sum(d_col[i]);
+      if (lane == 0) {
+        atomicAdd(&sAttr[i], a);
+        atomicAdd(&sAttr[3 + i], b);
+      }
+    }
+    const float w = warp_sum(d_w);
+    if (lane == 0) atomicAdd(&sAttr[6], w);
+  }
+  __syncthreads();
+  // sample points -> control points (Eq. 1-2; closed rows also Eq. 4)
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const float2 d = dX[idx];
+    if (!closed) {
+      int s;
+      float t, w[4];
+      chain_param(idx, K, 3, &s, &t);
+      bern3(t, w);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) sadd2(&dP[3 * s + i], w[i] * d.x, w[i] * d.y);
+    } else {
+      const int r = idx / K, k = idx - r * K;
+      const float tau = closed_tau(r, cfg.rows);
+      int s;
+      float t, w[4];
+      chain_param(k, K, 2, &s, &t);
+      bern3(t, w);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = 3 * s + i;
+        const float wa = w[i] * (1.0f - tau), wb = w[i] * tau;
+        sadd2(&dP[j], wa * d.x, wa * d.y);
+        sadd2(&dP[closed_b_index(j)], wb * d.x, wb * d.y);
+      }
+    }
+  }
+  __syncthreads();
+  if (!closed) {
+    float *gp = g.open_ctrl + (size_t)curve * 20;
+    for (int i = threadIdx.x; i < 10; i += blockDim.x) {
+      gp[2 * i] = dP[i].x;
+      gp[2 * i + 1] = dP[i].y;
+    }
+    if (threadIdx.x < 3) {
+      g.open_opac[curve * 3 + threadIdx.x] = sAttr[threadIdx.x];
+      g.open_color[curve * 3 + threadIdx.x] = sAttr[3 + threadIdx.x];
+    }
+    if (threadIdx.x == 0) g.open_width[curve] = sAttr[6];
+  } else {
+    const int j = curve - c.n_open;
+    float *gp = g.closed_ctrl + (size_t)j * 24;
+    for (int i = threadIdx.x; i < 12; i += blockDim.x) {
+      gp[2 * i] = dP[i].x;
+      gp[2 * i + 1] = dP[i].y;
+    }
+    if (threadIdx.x < 3) g.closed_color[j * 3 + threadIdx.x] = sAttr[3 + threadIdx.x];
+    if (threadIdx.x == 0) g.closed_opac[j] = sAttr[0];
+  }
+}
+
+// ---- draw order ----
+__device__ __forceinline__ float area_key(const bs_curves &c, int i) {
+  if (i < c.n_open) {
+    const float *P = c.open_ctrl + (size_t)i * 20;
+    float acc = 0.f;
+    for (int j = 0; j < 9; ++j) {
+      const float dx = __fsub_rn(P[2 * j + 2], P[2 * j]);
+      const float dy = __fsub_rn(P[2 * j + 3], P[2 * j + 1]);
+      acc = __fadd_rn(acc, __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy))));
+    }
+    return __fmul_rn(acc, c.open_width[i]);
+  }
+  const float *P = c.closed_ctrl + (size_t)(i - c.n_open) * 24;
+  float acc = 0.f;
+  for (int j = 0; j < 12; ++j) {
+    const int jn = j == 11 ? 0 : j + 1;
+    const float cross = __fsub_rn(__fmul_rn(P[2 * j], P[2 * jn + 1]), __fmul_rn(P[2 * jn], P[2 * j + 1]));
+    acc = __fadd_rn(acc, cross);
+  }
+  return __fmul_rn(fabsf(acc), 0.5f);
+}
+
+// Order-preserving integer image of a float key (NaN last, -0 == +0).
+__device__ __forceinline__ uint32_t key_order(float k) {
+  if (k != k) return 0xffffffffu;
+  k = __fadd_rn(k, 0.0f);
+  const uint32_t b = __float_as_uint(k);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+constexpr int kOrderThreads = 256;
+
+__global__ void __launch_bounds__(kOrderThreads) curve_order_kernel(bs_curves c, int g_open, int g_closed,
+                                                                   uint32_t *rank, uint32_t *first) {
+  __shared__ uint32_t sk[kOrderThreads];
+  const int n = c.n_open + c.n_closed;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t mine = i < n ? key_order(area_key(c, i)) : 0u;
+  uint32_t before = 0, open_before = 0;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int j = base + threadIdx.x;
+    sk[threadIdx.x] = j < n ? key_order(area_key(c, j)) : 0u;
+    __syncthreads();
+    const int m = min((int)blockDim.x, n - base);
+    for (int q = 0; q < m; ++q) {
+      const uint32_t kq = sk[q];
+      const int jq = base + q;
+      const bool prec = kq < mine || (kq == mine && jq < i);
+      before += prec;
+      open_before += prec && jq < c.n_open;
+    }
+    __syncthreads();
+  }
+  if (i < n) {
+    rank[i] = before;
+    first[i] = open_before * (uint32_t)g_open + (before - open_before) * (uint32_t)g_closed;
+  }
+}
+
+Cfg to_cfg(const bs_sample_cfg &s) { return Cfg{s.g_open, s.rows_closed, s.k_closed, s.rho, s.cov_eps}; }
+
+int max_samples(const bs_curves &c, const bs_sample_cfg &cfg) {
+  int m = 0;
+  if (c.n_open > 0) m = cfg.g_open;
+  if (c.n_closed > 0) m = max(m, cfg.rows_closed * cfg.k_closed);
+  return m;
+}
+
+}  // namespace
+
+bs_status launch_curve_order(const bs_curves &c, const bs_sample_cfg &cfg, uint32_t *rank, uint32_t *first,
+                             cudaStream_t s) {
+  const int n = c.n_open + c.n_closed;
+  if (n == 0) return BS_OK;
+  curve_order_kernel<<<div_up(n, kOrderThreads), kOrderThreads, 0, s>>>(c, cfg.g_open,
+                                                                        cfg.rows_closed * cfg.k_closed, rank, first);
+  BS_LAUNCHED("curve_order_kernel");
+  return BS_OK;
+}
+
+bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float *gauss, cudaStream_t s) {
+  const int n = c.n_open + c.n_closed;
+  if (n == 0) return BS_OK;
+  const size_t smem = (size_t)max_samples(c, cfg) * sizeof(float2);
+  BS_CUDA(cudaFuncSetAttribute(sample_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), gauss);
+  BS_LAUNCHED("sample_fwd_kernel");
+  return BS_OK;
+}
+
+bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const float *dgauss,
+                            const bs_curves_grad &g, cudaStream_t s) {
+  const int n = c.n_open + c.n_closed;
+  if (n == 0) return BS_OK;
+  const int n_max = max_samples(c, cfg);
+  const size_t smem = 2 * (size_t)n_max * sizeof(float2);
+  BS_CUDA(cudaFuncSetAttribute(sample_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), dgauss, g, n_max);
+  BS_LAUNCHED("sample_bwd_kernel");
+  return BS_OK;
+}
+
+}  // namespace bs

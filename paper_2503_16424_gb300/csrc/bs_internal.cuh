@@ -1,0 +1,90 @@
+// Internal declarations shared by the translation units of libbs.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "bs.h"
+
+namespace bs {
+
+// ---- thresholds of the blend (Eq. 9-10 with the tile rasterizer's rules) ----
+constexpr float kAlphaMin = 1.0f / 255.0f;  // skip a Gaussian below this alpha
+constexpr float kAlphaMax = 0.99f;          // alpha clamp
+constexpr float kTMin = 1e-4f;              // stop a pixel before T drops below
+constexpr float kExtPad = 0.01f;            // px added to support half extents
+
+constexpr int kMaxSamplesPerCurve = 4096;
+
+// ---- status plumbing ----
+void set_error(const char *fmt, ...);
+bs_status cuda_status(cudaError_t e, const char *what);
+bs_status check_device();
+
+#define BS_TRY(expr)                      \
+  do {                                    \
+    bs_status _s = (expr);                \
+    if (_s != BS_OK) return _s;           \
+  } while (0)
+
+#define BS_CUDA(expr) BS_TRY(::bs::cuda_status((expr), #expr))
+
+#define BS_LAUNCHED(what) BS_TRY(::bs::cuda_status(cudaGetLastError(), what))
+
+// ---- device status word (inside the binning workspace) ----
+constexpr uint32_t kDevErrTimeout = 1u;
+constexpr uint32_t kDevErrCapacity = 2u;
+
+// ---- small math helpers usable on host and device ----
+__host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t div_up64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int bit_length(uint64_t v) {
+  int n = 0;
+  while (v) { ++n; v >>= 1; }
+  return n;
+}
+inline int gauss_bits(int64_t n_gauss) { return n_gauss > 1 ? bit_length((uint64_t)(n_gauss - 1)) : 1; }
+
+// ---- launchers (one per translation unit) ----
+// curves (bs_curves.cu)
+bs_status launch_curve_order(const bs_curves &c, const bs_sample_cfg &cfg, uint32_t *rank,
+                             uint32_t *first, cudaStream_t s);
+bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float *gauss,
+                            cudaStream_t s);
+bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const float *dgauss,
+                            const bs_curves_grad &g, cudaStream_t s);
+
+// binning (bs_bin.cu)
+struct BinPlan {
+  int64_t n_gauss;
+  int tiles_x, tiles_y, n_tiles;
+  int gbits, tbits;
+  int passes, digit_bits;
+  int64_t capacity;
+  int64_t count_blocks;    // blocks of the count/emit kernels
+  int64_t parts;           // onesweep partitions for `capacity` keys
+  // byte offsets inside the workspace
+  size_t off_hdr, off_local, off_partial, off_keys_tmp, off_hist, off_counter, off_lookback;
+  size_t bytes;
+};
+bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, BinPlan *p);
+bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv, void *ws,
+                      int64_t *n_pairs, uint32_t *tile_keys, uint32_t *tile_ranges,
+                      cudaStream_t s);
+bs_status read_device_status(const void *ws, size_t ws_bytes, int32_t *out, cudaStream_t s);
+
+// render (bs_render.cu)
+bs_status launch_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas &cv, int gbits,
+                            const uint32_t *keys, const uint32_t *ranges, float *img,
+                            float *T_final, uint32_t *n_contrib, cudaStream_t s,
+                            unsigned long long *stats = nullptr);
+bs_status launch_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas &cv, int gbits,
+                            const uint32_t *keys, const uint32_t *ranges, const float *T_final,
+                            const uint32_t *n_contrib, const float *dL_dimg, float *dgauss,
+                            cudaStream_t s);
+bs_status launch_l2(const float *img, const float *target, int64_t n, float *dimg, double *loss,
+                    cudaStream_t s);
+
+}  // namespace bs

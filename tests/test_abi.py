@@ -1,0 +1,78 @@
+"""The C ABI library loads and exports every function include/bs.h declares;
+host-side argument validation and pure host arithmetic work without a GPU
+(no compute call is made here)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bs.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|bs_status|int64_t)\s*(bs_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_2503_16424_gb300 import build_lib
+    build_lib.build()
+    from paper_2503_16424_gb300 import bs as _bs
+    return _bs
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for f in ("bs_sample_curves", "bs_bin_tiles", "bs_render_fwd", "bs_render_bwd", "bs_curve_order",
+              "bs_l2_loss_grad", "bs_sample_curves_bwd", "bs_last_error"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(bs):
+    lib = ctypes.CDLL(bs.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_num_gaussians_host_arithmetic(bs):
+    cfg = bs.SampleCfg(g_open=64, rows_closed=8, k_closed=8)
+    assert bs.num_gaussians(2048, 2048, cfg) == 262144
+    assert bs.num_gaussians(64, 0, bs.SampleCfg(g_open=16)) == 1024
+    c = bs.SampleCfg(g_open=1).c()
+    assert bs.lib.bs_num_gaussians(1, 0, ctypes.byref(c)) == -1
+
+
+def test_workspace_size_host_arithmetic(bs):
+    n1 = bs.bin_tiles_workspace(1000, bs.Canvas(256, 256), 10000)
+    n2 = bs.bin_tiles_workspace(1000, bs.Canvas(256, 256), 20000)
+    assert n2 > n1 > 10000 * 4
+
+
+def test_invalid_arguments_are_rejected_on_the_host(bs):
+    cfg = bs.SampleCfg(g_open=16).c()
+    curves = bs.bs_curves(5, 0, None, None, None, None, None, None, None, None)
+    st = bs.lib.bs_curve_order(ctypes.byref(curves), ctypes.byref(cfg), None, None, None)
+    assert st == bs.BS_ERR_INVALID_ARG
+    assert b"open curve arrays" in bs.lib.bs_last_error()
+    cv = bs.Canvas(0, 10).c()
+    nb = ctypes.c_size_t(0)
+    assert bs.lib.bs_bin_tiles_workspace(10, ctypes.byref(cv), 100, ctypes.byref(nb)) == bs.BS_ERR_INVALID_ARG
+    cv = bs.Canvas(64, 64, tile=12).c()
+    assert bs.lib.bs_bin_tiles_workspace(10, ctypes.byref(cv), 100, ctypes.byref(nb)) == bs.BS_ERR_UNSUPPORTED
+    # keys wider than 32 bits
+    cv = bs.Canvas(32768, 32768).c()
+    assert bs.lib.bs_bin_tiles_workspace(1 << 20, ctypes.byref(cv), 100, ctypes.byref(nb)) == bs.BS_ERR_UNSUPPORTED
+    assert bs.lib.bs_status_string(bs.BS_ERR_TIMEOUT) == b"BS_ERR_TIMEOUT"
+    bad = bs.SampleCfg(g_open=16, rho=0.0).c()
+    assert bs.lib.bs_sample_curves(ctypes.byref(curves), ctypes.byref(bad), None, None) == bs.BS_ERR_INVALID_ARG
+
+
+def test_binding_refuses_cpu_tensors(bs):
+    import torch
+    with pytest.raises(TypeError):
+        bs.CurveSet(*(torch.zeros(0, 10, 2),) * 7).check()

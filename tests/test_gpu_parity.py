@@ -1,0 +1,201 @@
+"""Parity of every hot-path call of the CUDA library with the CPU oracle, on
+the same seeded inputs, element by element.
+
+Bars: integer results (draw order, tile keys, tile ranges) bit-exact;
+forward pixels within 1e-5 absolute except pixels the oracle flags as being
+within 1e-4 (relative) of a threshold decision; per-Gaussian and curve
+gradients within 1e-3 relative error, the relative error of an entry being
+measured against max(|reference|, 1e-3 * max |reference| of that array)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle.pipeline import as_curves, sample_vjp
+from tests.gpu_cases import CASES, arrays, grad_rel_err, ocfg, oracle_table, target, table_to_f32, table_from_f32
+
+pytestmark = pytest.mark.gpu
+
+FIELD_SLICES = {"mx": 0, "my": 1, "ca": 2, "cb": 3, "cc": 4, "o": 5}
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_2503_16424_gb300 import bs as _bs
+    return _bs
+
+
+def _gpu_curves(bs, arr):
+    return bs.CurveSet.from_arrays(arr, device="cuda")
+
+
+def _cfg(bs, case):
+    return bs.SampleCfg(g_open=case.g_open, rows_closed=case.rows, k_closed=case.kc)
+
+
+def _canvas(bs, case):
+    return bs.Canvas(case.W, case.H, 16, case.bg)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_curve_order_bit_exact(bs, name):
+    case = CASES[name]
+    arr = arrays(case)
+    rank, first = bs.curve_order(_gpu_curves(bs, arr), _cfg(bs, case))
+    o_rank, o_first = oracle.draw_order(arr["open_ctrl"], arr["open_width"], arr["closed_ctrl"], ocfg(case))
+    assert np.array_equal(rank.cpu().numpy(), o_rank)
+    assert np.array_equal(first.cpu().numpy(), o_first)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_sample_matches_oracle(bs, name):
+    case = CASES[name]
+    arr = arrays(case)
+    curves = _gpu_curves(bs, arr)
+    _, first = bs.curve_order(curves, _cfg(bs, case))
+    gauss = bs.sample_curves(curves, _cfg(bs, case), first).cpu().numpy().astype(np.float64)
+    tab, _, _ = oracle_table(case, arr)
+    ref = table_to_f32(tab).astype(np.float64)
+    ref64 = np.stack([tab["mx"].numpy(), tab["my"].numpy(), tab["ca"].detach().numpy(),
+                      tab["cb"].detach().numpy(), tab["cc"].detach().numpy(), tab["o"].numpy()], 1)
+    # positions relative to the canvas size, conic entries relative to the
+    # Gaussian's largest conic entry, the rest relative to 1
+    scale_pos = max(case.W, case.H)
+    assert np.abs(gauss[:, 0:2] - ref64[:, 0:2]).max() <= 1e-5 * scale_pos
+    qmax = np.abs(ref64[:, 2:5]).max(1, keepdims=True)
+    assert (np.abs(gauss[:, 2:5] - ref64[:, 2:5]) / qmax).max() <= 1e-5
+    assert np.array_equal(gauss[:, 5:9], ref[:, 5:9])           # opacity and colour are copied
+    ext_ok = ref[:, 9] >= 0
+    assert np.array_equal(gauss[:, 9] >= 0, ext_ok)
+    assert (np.abs(gauss[ext_ok, 9:11] - ref[ext_ok, 9:11]) / np.maximum(ref[ext_ok, 9:11], 1.0)).max() <= 1e-5
+
+
+def _bin(bs, case, rec):
+    gauss = torch.as_tensor(rec, device="cuda")
+    b = bs.Binning(_canvas(bs, case), "cuda", pair_capacity=1024).run(gauss)
+    assert b.device_status() == 0
+    return gauss, b
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_bin_bit_exact(bs, name):
+    case = CASES[name]
+    tab, _, _ = oracle_table(case)
+    rec = table_to_f32(tab)
+    keys, ranges, counts = oracle.tile_keys(rec, case.W, case.H, 16)
+    _, b = _bin(bs, case, rec)
+    assert b.n_pairs == keys.shape[0]
+    assert np.array_equal(b.keys[:b.n_pairs].cpu().numpy().view(np.uint32), keys)
+    assert np.array_equal(b.ranges.cpu().numpy().view(np.uint32), ranges)
+
+
+def test_bin_bit_exact_many_partitions_and_degenerate(bs):
+    """About 10^5 pairs (dozens of sort partitions), plus Gaussians that are
+    culled, non-finite, far off-screen or cover the whole canvas."""
+    rng = np.random.default_rng(7)
+    W, H, n = 333, 217, 6000
+    rec = np.zeros((n, 12), dtype=np.float32)
+    rec[:, 0] = rng.uniform(-40, W + 40, n)
+    rec[:, 1] = rng.uniform(-40, H + 40, n)
+    rec[:, 9] = rng.uniform(0, 30, n)
+    rec[:, 10] = rng.uniform(0, 30, n)
+    rec[::97, 9] = -1.0
+    rec[1::97, 0] = np.nan
+    rec[2::97, 1] = 1e30
+    rec[3::97, 9] = np.inf
+    rec[4, 9:11] = 1e4
+    rec[5, 0:2] = [W + 0.4999, H + 0.5]
+    rec[6, 0:2] = [0.5, 0.5]
+    rec[6, 9:11] = 0.0
+    keys, ranges, _ = oracle.tile_keys(rec, W, H, 16)
+    assert keys.shape[0] > 50000
+
+    class C:
+        pass
+    case = C()
+    case.W, case.H, case.bg = W, H, (0, 0, 0)
+    _, b = _bin(bs, case, rec)
+    assert b.n_pairs == keys.shape[0]
+    assert np.array_equal(b.keys[:b.n_pairs].cpu().numpy().view(np.uint32), keys)
+    assert np.array_equal(b.ranges.cpu().numpy().view(np.uint32), ranges)
+
+
+def _render(bs, case, rec):
+    gauss, b = _bin(bs, case, rec)
+    img, T, nc = bs.render_fwd(gauss, _canvas(bs, case), b)
+    return gauss, b, img, T, nc
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_render_fwd_matches_oracle(bs, name):
+    case = CASES[name]
+    tab, _, _ = oracle_table(case)
+    rec = table_to_f32(tab)
+    gauss, b, img, T, nc = _render(bs, case, rec)
+    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg)
+    ok = ~ref["flag"].numpy()
+    assert ok.mean() > 1 - 1e-3
+    err = np.abs(img.cpu().numpy().astype(np.float64) - ref["img"].numpy()).max(0)
+    assert err[ok].max() <= 1e-5
+    assert np.abs(T.cpu().numpy() - ref["T"].numpy())[ok].max() <= 1e-5
+    # the last blended Gaussian of every pixel, through the tile list
+    keys = b.keys[:b.n_pairs].cpu().numpy().view(np.uint32).astype(np.int64)
+    ranges = b.ranges.cpu().numpy().view(np.uint32).astype(np.int64)
+    gbits = max(1, (rec.shape[0] - 1).bit_length())
+    nc = nc.cpu().numpy().astype(np.int64)
+    ys, xs = np.mgrid[0:case.H, 0:case.W]
+    tiles_x = -(-case.W // 16)
+    start = ranges[(ys // 16) * tiles_x + xs // 16, 0]
+    last = np.where(nc > 0, keys[np.maximum(start + nc - 1, 0)] & ((1 << gbits) - 1), -1)
+    assert np.array_equal(last[ok], ref["last"].numpy()[ok])
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_render_bwd_matches_oracle(bs, name):
+    case = CASES[name]
+    tab, _, _ = oracle_table(case)
+    rec = table_to_f32(tab)
+    gauss, b, img, T, nc = _render(bs, case, rec)
+    tgt = torch.as_tensor(target(case), device="cuda")
+    _, dimg = bs.l2_loss_grad(img, tgt)
+    dgauss, _ = bs.render_bwd(gauss, _canvas(bs, case), b, T, nc, dimg)
+    ys, xs = torch.meshgrid(torch.arange(case.H, dtype=torch.float64),
+                            torch.arange(case.W, dtype=torch.float64), indexing="ij")
+    dC = dimg.cpu().double().permute(1, 2, 0).reshape(-1, 3)
+    ref = oracle.render_grads(table_from_f32(rec), xs.reshape(-1), ys.reshape(-1), dC, bg=case.bg)
+    got = dgauss.cpu().double()
+    for key, col in FIELD_SLICES.items():
+        assert grad_rel_err(got[:, col], ref[key]) <= 1e-3, key
+    assert grad_rel_err(got[:, 6:9], ref["col"]) <= 1e-3
+    assert torch.all(got[:, 9:] == 0)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_sample_bwd_matches_oracle(bs, name):
+    case = CASES[name]
+    arr = arrays(case)
+    tab, _, first = oracle_table(case, arr)
+    rng = np.random.default_rng(case.seed)
+    n = tab["mx"].shape[0]
+    dg = np.zeros((n, 12), dtype=np.float32)
+    dg[:, 0:9] = rng.normal(0, 1, (n, 9)).astype(np.float32)
+    dg[:, 2:5] *= 10.0
+    dtab = dict(mx=dg[:, 0], my=dg[:, 1], ca=dg[:, 2], cb=dg[:, 3], cc=dg[:, 4], o=dg[:, 5], col=dg[:, 6:9])
+    dtab = {k: torch.as_tensor(v.astype(np.float64)) for k, v in dtab.items()}
+    ref = sample_vjp(as_curves(arr), ocfg(case), dtab, first)
+    curves = _gpu_curves(bs, arr)
+    grad = bs.sample_curves_bwd(curves, _cfg(bs, case), torch.as_tensor(first.astype(np.int32), device="cuda"),
+                                torch.as_tensor(dg, device="cuda"))
+    for k in ("open_ctrl", "open_width", "open_color", "open_opac", "closed_ctrl", "closed_color", "closed_opac"):
+        assert grad_rel_err(getattr(grad, k).cpu(), ref[k]) <= 1e-3, k
+
+
+def test_l2_matches_oracle(bs):
+    rng = np.random.default_rng(0)
+    a = rng.uniform(0, 1, (3, 37, 29)).astype(np.float32)
+    t = rng.uniform(0, 1, (3, 37, 29)).astype(np.float32)
+    loss, dimg = bs.l2_loss_grad(torch.as_tensor(a, device="cuda"), torch.as_tensor(t, device="cuda"))
+    L, g = oracle.l2_loss(a, t)
+    assert abs(loss.item() - float(L)) <= 1e-12 + 1e-9 * float(L)
+    assert np.abs(dimg.cpu().numpy() - g.numpy()).max() <= 1e-7 * np.abs(g.numpy()).max()
