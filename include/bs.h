@@ -104,17 +104,18 @@ typedef struct {
 
 /*
  * Gaussian table record: 12 float32 per Gaussian, in draw order (front
- * first), 16-byte aligned rows:
+ * first), 16-byte aligned rows.  A Gaussian is kept in the eigen-frame of
+ * Eq. 11-12: Sigma = R diag(sx^2 + eps, sy^2 + eps) R^T, R = [[ux, -uy], [uy, ux]],
+ * so Sigma^-1 = R diag(isx^2, isy^2) R^T.
  *   [0] mx  [1] my              mean (px)
- *   [2] ca  [3] cb  [4] cc      conic Sigma^-1 = [[ca, cb], [cb, cc]]
- *   [5] o                       opacity
- *   [6] r   [7] g   [8] b       colour
- *   [9] ext_x [10] ext_y        half extents of the box holding every pixel
+ *   [2] ux  [3] uy              unit tangent: first column of R
+ *   [4] isx [5] isy             (sx^2 + eps)^-1/2, (sy^2 + eps)^-1/2
+ *   [6] o                       opacity
+ *   [7] r   [8] g   [9] b       colour
+ *   [10] ext_x [11] ext_y       half extents of the box holding every pixel
  *                               centre with alpha >= 1/255; < 0: never binned
- *   [11] 0
- * Per-Gaussian gradient record: 12 float32, d/d(mx, my, ca, cb, cc, o, r, g, b)
- * in [0..8], [9..11] = 0.  cb is the single off-diagonal entry, so
- * d/d(cb) counts both of its appearances in d^T Sigma^-1 d.
+ * Per-Gaussian gradient record: 12 float32,
+ * d/d(mx, my, ux, uy, isx, isy, o, r, g, b) in [0..9], [10..11] = 0.
  */
 #define BS_GAUSS_FLOATS 12
 #define BS_DGAUSS_FLOATS 12
@@ -179,7 +180,8 @@ bs_status bs_bin_tiles_workspace(int64_t n_gauss, const bs_canvas *canvas,
  *   n_pairs_out     (HOST) the number of pairs P; on BS_ERR_CAPACITY the
  *                   number needed (nothing else is valid then)
  *   tile_keys       [pair_capacity] sorted keys (device, written [0, P))
- *   tile_ranges     [n_tiles][2] (start, end) into tile_keys (device, written)
+ *   tile_ranges     [n_tiles][2] (start, end) into tile_keys; an empty tile
+ *                   has (0, 0) (device, written)
  * Synchronises the stream once to read P.
  */
 bs_status bs_bin_tiles(const float *gauss, int64_t n_gauss, const bs_canvas *canvas,

@@ -41,7 +41,7 @@ def tile_rects_f32(rec: np.ndarray, W: int, H: int, tile: int):
     f = np.float32
     rec = np.asarray(rec, dtype=f)
     mx, my = rec[:, 0], rec[:, 1]
-    ex, ey = rec[:, 9], rec[:, 10]
+    ex, ey = rec[:, 10], rec[:, 11]
     half = f(0.5)
     with np.errstate(invalid="ignore", over="ignore"):
         xlo = (mx - ex) - half
@@ -62,7 +62,8 @@ def tile_rects_f32(rec: np.ndarray, W: int, H: int, tile: int):
 
 def tile_keys(rec: np.ndarray, W: int, H: int, tile: int):
     """All (tile, Gaussian) keys sorted ascending, the tile ranges [n_tiles, 2]
-    (start, end) into them, and the per-Gaussian pair counts."""
+    (start, end) into them (an empty tile has (0, 0)), and the per-Gaussian
+    pair counts."""
     ng = rec.shape[0]
     tiles_x = -(-W // tile)
     tiles_y = -(-H // tile)
@@ -85,4 +86,5 @@ def tile_keys(rec: np.ndarray, W: int, H: int, tile: int):
     t = np.arange(n_tiles, dtype=np.uint32)
     ranges = np.stack([np.searchsorted(tile_of, t, side="left"),
                        np.searchsorted(tile_of, t, side="right")], axis=1).astype(np.uint32)
+    ranges[ranges[:, 0] == ranges[:, 1]] = 0       # an empty tile is (0, 0)
     return keys, ranges, counts

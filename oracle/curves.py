@@ -28,7 +28,8 @@ Readings of the paper used here (the paper is silent or garbled):
     theta = 0 (Eq. 7-8 "nearest available neighbour").
   * open curves: sigma_y = width (Section 3.3, width is the y-scale).
   * Sigma = (R S)(R S)^T + eps I (Eq. 11-12 plus a small isotropic floor eps,
-    which keeps Sigma invertible when two samples coincide).
+    which keeps Sigma invertible when two samples coincide); a Gaussian is
+    stored by R and the inverse scales of Sigma (see gaussian_table).
 """
 
 from __future__ import annotations
@@ -243,8 +244,15 @@ EXT_PAD = 0.01              # px added to the support half-extents
 
 def gaussian_table(curves: dict, cfg: SampleCfg, first=None):
     """All Gaussians in draw order as a dict of fp64 tensors [Ng] (colour
-    [Ng,3]): mx, my, ca, cb, cc (conic = Sigma^-1), o, col, ext_x, ext_y,
-    plus sigma_x/sigma_y/theta for inspection.
+    [Ng,3]).
+
+    Each Gaussian is kept in the eigen-frame of Eq. 11-12: with the eps
+    floor, Sigma = (R S)(R S)^T + eps I = R diag(sx^2 + eps, sy^2 + eps) R^T,
+    so Sigma^-1 = R diag(isx^2, isy^2) R^T with
+        R = [[ux, -uy], [uy, ux]],  (ux, uy) = (cos theta, sin theta),
+        isx = (sx^2 + eps)^-1/2,    isy = (sy^2 + eps)^-1/2.
+    Fields: mx, my, ux, uy, isx, isy, o, col, ext_x, ext_y, and for
+    inspection sigma_x, sigma_y, theta, Sigma.
 
     ext_x/ext_y are the half extents of the axis-aligned box around the
     ellipse where alpha >= 1/255, i.e. 0.5 d^T Sigma^-1 d <= ln(255 o):
@@ -274,15 +282,19 @@ def gaussian_table(curves: dict, cfg: SampleCfg, first=None):
         idx_all.append(idx.reshape(-1))
         for k, v in samp.items():
             fields.setdefault(k, []).append(v.reshape((n * per,) + tuple(v.shape[2:])))
+    if not idx_all:
+        z = torch.zeros(0, dtype=F64)
+        return dict(mx=z, my=z, ux=z, uy=z, isx=z, isy=z, o=z, col=torch.zeros(0, 3, dtype=F64),
+                    ext_x=z, ext_y=z, sigma_x=z, sigma_y=z, theta=z, Sigma=torch.zeros(0, 2, 2, dtype=F64))
     idx = torch.cat(idx_all)
     inv = torch.empty(n_g, dtype=torch.int64)
     inv[idx] = torch.arange(n_g)
     g = {k: torch.cat(v)[inv] for k, v in fields.items()}
 
     Sigma = covariance(g["theta"], g["sigma_x"], g["sigma_y"], cfg.eps)
-    conic = torch.linalg.inv(Sigma)
     out = dict(mx=g["mu"][:, 0], my=g["mu"][:, 1],
-               ca=conic[:, 0, 0], cb=conic[:, 0, 1], cc=conic[:, 1, 1],
+               ux=torch.cos(g["theta"]), uy=torch.sin(g["theta"]),
+               isx=(g["sigma_x"] ** 2 + cfg.eps) ** -0.5, isy=(g["sigma_y"] ** 2 + cfg.eps) ** -0.5,
                o=g["o"], col=g["col"], sigma_x=g["sigma_x"], sigma_y=g["sigma_y"],
                theta=g["theta"], Sigma=Sigma)
     with torch.no_grad():
@@ -297,16 +309,16 @@ def gaussian_table(curves: dict, cfg: SampleCfg, first=None):
 
 
 TABLE_FIELDS = 12
+RECORD = ("mx", "my", "ux", "uy", "isx", "isy", "o", "r", "g", "b", "ext_x", "ext_y")
 
 
 def table_to_f32(tab: dict) -> np.ndarray:
     """Pack a table into the float32 record of the CUDA library,
-    [Ng, 12] = mx, my, ca, cb, cc, o, r, g, b, ext_x, ext_y, 0."""
+    [Ng, 12] = mx, my, ux, uy, isx, isy, o, r, g, b, ext_x, ext_y."""
     n = tab["mx"].shape[0]
     rec = np.zeros((n, TABLE_FIELDS), dtype=np.float32)
-    cols = [tab["mx"], tab["my"], tab["ca"], tab["cb"], tab["cc"], tab["o"],
-            tab["col"][:, 0], tab["col"][:, 1], tab["col"][:, 2],
-            tab["ext_x"], tab["ext_y"]]
+    cols = [tab["mx"], tab["my"], tab["ux"], tab["uy"], tab["isx"], tab["isy"], tab["o"],
+            tab["col"][:, 0], tab["col"][:, 1], tab["col"][:, 2], tab["ext_x"], tab["ext_y"]]
     for i, c in enumerate(cols):
         rec[:, i] = c.detach().numpy().astype(np.float32)
     return rec
@@ -315,5 +327,5 @@ def table_to_f32(tab: dict) -> np.ndarray:
 def table_from_f32(rec: np.ndarray) -> dict:
     """The inverse of table_to_f32, as fp64 tensors (exact)."""
     r = torch.as_tensor(np.asarray(rec, dtype=np.float32).astype(np.float64))
-    return dict(mx=r[:, 0], my=r[:, 1], ca=r[:, 2], cb=r[:, 3], cc=r[:, 4],
-                o=r[:, 5], col=r[:, 6:9], ext_x=r[:, 9], ext_y=r[:, 10])
+    return dict(mx=r[:, 0], my=r[:, 1], ux=r[:, 2], uy=r[:, 3], isx=r[:, 4], isy=r[:, 5],
+                o=r[:, 6], col=r[:, 7:10], ext_x=r[:, 10], ext_y=r[:, 11])

@@ -33,7 +33,7 @@ def as_curves(d: dict, requires_grad=False):
 
 def sample_vjp(curves: dict, cfg: SampleCfg, dtab: dict, first=None):
     """dL/d(curve parameters) given dL/d(table field) for the fields of
-    GRAD_KEYS (mx, my, ca, cb, cc, o, col)."""
+    GRAD_KEYS (mx, my, ux, uy, isx, isy, o, col)."""
     cv = {k: v.detach().clone().requires_grad_(True) for k, v in curves.items()}
     tab = gaussian_table(cv, cfg, first)
     outs = [tab[k] for k in GRAD_KEYS]

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 For every requested pixel and EVERY Gaussian, in draw order (no culling):
   d     = p - mu,  p = (x + 0.5, y + 0.5) the pixel centre
-  s     = 0.5 d^T Sigma^-1 d                      (Eq. 10)
+  s     = 0.5 d^T Sigma^-1 d                      (Eq. 10, Sigma from Eq. 11-12)
   alpha = min(0.99, o exp(-s))                    (Eq. 10 with the clamp below)
   C     = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j) + T_final bg      (Eq. 9)
 
@@ -30,21 +30,25 @@ T_MIN = 1e-4
 
 
 def _alpha_raw(tab, px, py):
+    """o exp(-0.5 d^T Sigma^-1 d) with Sigma^-1 = R diag(isx^2, isy^2) R^T,
+    R = [[ux, -uy], [uy, ux]] (Eq. 10-12), so d^T Sigma^-1 d = |S^-1 R^T d|^2."""
     dx = px[:, None] - tab["mx"][None, :]
     dy = py[:, None] - tab["my"][None, :]
-    s = 0.5 * (tab["ca"][None] * dx * dx + 2.0 * tab["cb"][None] * dx * dy
-               + tab["cc"][None] * dy * dy)
+    a = (tab["ux"][None] * dx + tab["uy"][None] * dy) * tab["isx"][None]      # along the curve
+    b = (-tab["uy"][None] * dx + tab["ux"][None] * dy) * tab["isy"][None]     # across it
+    s = 0.5 * (a * a + b * b)
     return tab["o"][None] * torch.exp(-s)
 
 
-def render_pixels(tab: dict, xs, ys, bg=(0.0, 0.0, 0.0), margin: float = 1e-4):
+def render_pixels(tab: dict, xs, ys, bg=(0.0, 0.0, 0.0), margin: float = 1e-4, margin_T=None):
     """Blend all Gaussians of ``tab`` at pixels (xs[i], ys[i]).
 
     Returns dict(C [n,3], T [n] final transmittance, last [n] index of the
     last blended Gaussian or -1, n_blend [n], flag [n]).  ``flag`` marks a
     pixel where some threshold decision (the 1/255 skip, the 1e-4 stop, the
-    0.99 clamp) lies within a relative ``margin`` of its threshold, so that an
-    fp32 evaluation may legitimately decide it the other way.
+    0.99 clamp) lies within a relative ``margin`` of its threshold (``margin_T``
+    for the transmittance stop, default ``margin``), so that an fp32
+    evaluation may legitimately decide it the other way.
     Differentiable in the table entries."""
     xs = torch.as_tensor(xs, dtype=torch.float64)
     ys = torch.as_tensor(ys, dtype=torch.float64)
@@ -73,7 +77,8 @@ def render_pixels(tab: dict, xs, ys, bg=(0.0, 0.0, 0.0), margin: float = 1e-4):
         considered = idx <= first_stop[:, None]
         near_skip = (torch.abs(a_raw - ALPHA_MIN) <= margin * ALPHA_MIN) & considered
         near_clamp = (torch.abs(a_raw - ALPHA_MAX) <= margin) & considered & (a_raw >= ALPHA_MIN)
-        near_stop = (torch.abs(T_after - T_MIN) <= margin * T_MIN) & considered & (alpha > 0)
+        mT = margin if margin_T is None else margin_T
+        near_stop = (torch.abs(T_after - T_MIN) <= mT * T_MIN) & considered & (alpha > 0)
         flag = (near_skip | near_clamp | near_stop).any(dim=1)
     return dict(C=C, T=T_final, last=last, n_blend=n_blend, flag=flag)
 
@@ -83,7 +88,7 @@ def _chunks(n, size):
         yield s, min(n, s + size)
 
 
-def render_image(tab: dict, W: int, H: int, bg=(0.0, 0.0, 0.0), margin=1e-4,
+def render_image(tab: dict, W: int, H: int, bg=(0.0, 0.0, 0.0), margin=1e-4, margin_T=None,
                  max_entries: int = 1 << 22):
     """Brute-force render of a W x H image.  Returns planar img [3,H,W],
     T [H,W], last [H,W], flag [H,W] (no autograd)."""
@@ -95,14 +100,14 @@ def render_image(tab: dict, W: int, H: int, bg=(0.0, 0.0, 0.0), margin=1e-4,
     C, T, last, flag = [], [], [], []
     with torch.no_grad():
         for s, e in _chunks(xs.shape[0], chunk):
-            r = render_pixels(tab, xs[s:e], ys[s:e], bg, margin)
+            r = render_pixels(tab, xs[s:e], ys[s:e], bg, margin, margin_T)
             C.append(r["C"]); T.append(r["T"]); last.append(r["last"]); flag.append(r["flag"])
     C = torch.cat(C).reshape(H, W, 3).permute(2, 0, 1).contiguous()
     return dict(img=C, T=torch.cat(T).reshape(H, W), last=torch.cat(last).reshape(H, W),
                 flag=torch.cat(flag).reshape(H, W))
 
 
-GRAD_KEYS = ("mx", "my", "ca", "cb", "cc", "o", "col")
+GRAD_KEYS = ("mx", "my", "ux", "uy", "isx", "isy", "o", "col")
 
 
 def render_grads(tab: dict, xs, ys, dC, bg=(0.0, 0.0, 0.0), max_entries: int = 1 << 21):

@@ -52,7 +52,7 @@ struct Rect {
 __device__ __forceinline__ bool tile_rect(const float *gauss, int64_t g, int W, int H, int tile, Rect *r) {
   const float4 a = __ldg(reinterpret_cast<const float4 *>(gauss + g * BS_GAUSS_FLOATS));
   const float4 c = __ldg(reinterpret_cast<const float4 *>(gauss + g * BS_GAUSS_FLOATS + 8));
-  const float mx = a.x, my = a.y, ex = c.y, ey = c.z;
+  const float mx = a.x, my = a.y, ex = c.z, ey = c.w;
   if (!(ex >= 0.f) || !(ey >= 0.f)) return false;
   const float xlo = __fsub_rn(__fsub_rn(mx, ex), 0.5f);
   const float xhi = __fsub_rn(__fadd_rn(mx, ex), 0.5f);

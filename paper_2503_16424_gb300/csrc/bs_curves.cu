@@ -1,12 +1,18 @@
 // Curves -> Gaussians: draw order (Section 3.3 "depth from area"), sampling
-// (Section 3.3, Eq. 3-8, covariance Eq. 11-12) and its backward.
+// (Section 3.3, Eq. 3-8, Eq. 11-12) and its backward.
 //
 // One CTA per curve.  The CTA evaluates the curve's sample points X into
 // shared memory, then each thread turns one sample and its neighbours into
-// a Gaussian record (forward) or pushes one Gaussian's gradient back to the
+// a Gaussian record (forward), or pushes one Gaussian's gradient back to the
 // sample points and from there, with the Bernstein weights of Eq. 1-2, to the
 // control points (backward).  A curve's Gaussians are contiguous in the
 // draw-ordered table, so the backward needs no global atomics.
+//
+// Precision: the sample points and the differences of neighbouring samples
+// (Eq. 7-8) are computed in double, relative to the curve's first control
+// point.  Subtracting two float32 positions loses the digits that a short
+// tangent or a thin row spacing needs; the difference vectors, once formed,
+// are well conditioned and everything after them runs in float32.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -22,7 +28,15 @@ struct Cfg {
   float rho, eps;
 };
 
-__device__ __forceinline__ void bern3(float t, float w[4]) {
+__device__ __forceinline__ void bern3(double t, double w[4]) {
+  const double u = 1.0 - t;
+  w[0] = u * u * u;
+  w[1] = 3.0 * u * u * t;
+  w[2] = 3.0 * u * t * t;
+  w[3] = t * t * t;
+}
+
+__device__ __forceinline__ void bern3f(float t, float w[4]) {
   const float u = 1.0f - t;
   w[0] = u * u * u;
   w[1] = 3.0f * u * u * t;
@@ -30,81 +44,89 @@ __device__ __forceinline__ void bern3(float t, float w[4]) {
   w[3] = t * t * t;
 }
 
-// Segment and local parameter of sample k of K on a chain of S segments:
-// u = k/(K-1), s = min(floor(S u), S-1), t = S u - s (integer decisions).
-__device__ __forceinline__ void chain_param(int k, int K, int S, int *seg, float *t) {
-  int s = (S * k) / (K - 1);
-  if (s > S - 1) s = S - 1;
-  *seg = s;
-  *t = __fdiv_rn((float)(S * k - s * (K - 1)), (float)(K - 1));
+// Segment of sample k of K on a chain of S segments, u = k/(K-1):
+// s = min(floor(S u), S-1) decided in integers; local parameter t = S u - s.
+__device__ __forceinline__ int chain_seg(int k, int K, int S) {
+  const int s = (S * k) / (K - 1);
+  return s > S - 1 ? S - 1 : s;
+}
+__device__ __forceinline__ double chain_t(int k, int K, int S, int s) {
+  return (double)(S * k - s * (K - 1)) / (double)(K - 1);
 }
 
 // Boundary groups of a closed curve: A = P0..P6, B = P0, P11, ..., P7, P6.
 __device__ __forceinline__ int closed_b_index(int j) { return (j == 0 || j == 6) ? j : 12 - j; }
 
 // tau_r = (1 - cos(pi r/(R+1)))/2 with rows = R + 2.
-__device__ __forceinline__ float closed_tau(int r, int rows) {
-  return 0.5f * (1.0f - cospif((float)r / (float)(rows - 1)));
+__device__ __forceinline__ double closed_tau(int r, int rows) {
+  return 0.5 * (1.0 - cospi((double)r / (double)(rows - 1)));
 }
 
 __device__ __forceinline__ float2 ld2(const float *p, int i) { return make_float2(p[2 * i], p[2 * i + 1]); }
 
-// Sample point X of a curve into shared memory; returns the number of samples.
-__device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, float2 *X) {
+__device__ __forceinline__ const float *curve_ctrl(const bs_curves &c, int curve) {
+  return curve < c.n_open ? c.open_ctrl + (size_t)curve * 20 : c.closed_ctrl + (size_t)(curve - c.n_open) * 24;
+}
+
+// Sample points X of a curve relative to its first control point, into
+// shared memory; returns the number of samples.
+__device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, double2 *X) {
+  const float *P = curve_ctrl(c, curve);
+  const double ox = P[0], oy = P[1];
   if (curve < c.n_open) {
-    const float *P = c.open_ctrl + (size_t)curve * 20;
     const int K = cfg.g_open;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      int s;
-      float t, w[4];
-      chain_param(k, K, 3, &s, &t);
-      bern3(t, w);
-      float2 acc = make_float2(0.f, 0.f);
+      const int s = chain_seg(k, K, 3);
+      double w[4];
+      bern3(chain_t(k, K, 3, s), w);
+      double ax = 0.0, ay = 0.0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const float2 p = ld2(P, 3 * s + i);
-        acc.x += w[i] * p.x;
-        acc.y += w[i] * p.y;
+        ax += w[i] * ((double)p.x - ox);
+        ay += w[i] * ((double)p.y - oy);
       }
-      X[k] = acc;
+      X[k] = make_double2(ax, ay);
     }
     return K;
   }
-  const float *P = c.closed_ctrl + (size_t)(curve - c.n_open) * 24;
   const int K = cfg.kc, R2 = cfg.rows, n = R2 * K;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int r = idx / K, k = idx - r * K;
-    const float tau = closed_tau(r, R2);
-    int s;
-    float t, w[4];
-    chain_param(k, K, 2, &s, &t);
-    bern3(t, w);
-    float2 acc = make_float2(0.f, 0.f);
+    const double tau = closed_tau(r, R2);
+    const int s = chain_seg(k, K, 2);
+    double w[4];
+    bern3(chain_t(k, K, 2, s), w);
+    double ax = 0.0, ay = 0.0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int j = 3 * s + i;
       const float2 a = ld2(P, j), b = ld2(P, closed_b_index(j));
-      const float qx = (1.0f - tau) * a.x + tau * b.x;   // Eq. 4
-      const float qy = (1.0f - tau) * a.y + tau * b.y;
-      acc.x += w[i] * qx;
-      acc.y += w[i] * qy;
+      const double qx = (1.0 - tau) * ((double)a.x - ox) + tau * ((double)b.x - ox);  // Eq. 4
+      const double qy = (1.0 - tau) * ((double)a.y - oy) + tau * ((double)b.y - oy);
+      ax += w[i] * qx;
+      ay += w[i] * qy;
     }
-    X[idx] = acc;
+    X[idx] = make_double2(ax, ay);
   }
   return n;
 }
 
-// Local geometry of one sample (Eq. 7-8): the along-row difference e, the
-// tangent difference t, the across-row difference f (closed only), the
-// scales and the unit tangent (c, s).
+__device__ __forceinline__ float2 diff(const double2 *X, int hi, int lo) {
+  return make_float2((float)(X[hi].x - X[lo].x), (float)(X[hi].y - X[lo].y));
+}
+
+// Local geometry of one sample (Eq. 7-8): the along-row difference e (for
+// sigma_x), the tangent difference t (for the rotation), the across-row
+// difference f (closed curves, for sigma_y); the scales; the unit tangent u.
 struct Local {
   float2 e, t, f;
   int e_hi, e_lo, t_hi, t_lo, f_hi, f_lo;  // sample indices the differences use
   float le, lt, lf;                         // their lengths
-  float sx, sy, c, s;
+  float sx, sy, ux, uy;
 };
 
-__device__ __forceinline__ Local local_geometry(const float2 *X, int idx, int K, int R2, bool closed,
+__device__ __forceinline__ Local local_geometry(const double2 *X, int idx, int K, int R2, bool closed,
                                                 float width, float rho) {
   Local L;
   const int r = closed ? idx / K : 0;
@@ -115,15 +137,15 @@ __device__ __forceinline__ Local local_geometry(const float2 *X, int idx, int K,
   if (k == 0) { L.t_hi = row + 1; L.t_lo = row; }
   else if (k == K - 1) { L.t_hi = row + k; L.t_lo = row + k - 1; }
   else { L.t_hi = row + k + 1; L.t_lo = row + k - 1; }
-  L.e = make_float2(X[L.e_hi].x - X[L.e_lo].x, X[L.e_hi].y - X[L.e_lo].y);
-  L.t = make_float2(X[L.t_hi].x - X[L.t_lo].x, X[L.t_hi].y - X[L.t_lo].y);
+  L.e = diff(X, L.e_hi, L.e_lo);
+  L.t = diff(X, L.t_hi, L.t_lo);
   L.le = sqrtf(L.e.x * L.e.x + L.e.y * L.e.y);
   L.lt = sqrtf(L.t.x * L.t.x + L.t.y * L.t.y);
   L.sx = L.le / rho;
   if (closed) {
     if (r + 1 < R2) { L.f_hi = idx + K; L.f_lo = idx; }
     else { L.f_hi = idx; L.f_lo = idx - K; }
-    L.f = make_float2(X[L.f_hi].x - X[L.f_lo].x, X[L.f_hi].y - X[L.f_lo].y);
+    L.f = diff(X, L.f_hi, L.f_lo);
     L.lf = sqrtf(L.f.x * L.f.x + L.f.y * L.f.y);
     L.sy = L.lf / rho;
   } else {
@@ -132,26 +154,9 @@ __device__ __forceinline__ Local local_geometry(const float2 *X, int idx, int K,
     L.lf = 0.f;
     L.sy = width;
   }
-  if (L.lt > 0.f) { L.c = L.t.x / L.lt; L.s = L.t.y / L.lt; }
-  else { L.c = 1.f; L.s = 0.f; }
+  if (L.lt > 0.f) { L.ux = L.t.x / L.lt; L.uy = L.t.y / L.lt; }
+  else { L.ux = 1.f; L.uy = 0.f; }
   return L;
-}
-
-// Sigma = R S S^T R^T + eps I (Eq. 11-12) with R from the unit tangent.
-__device__ __forceinline__ void covariance(const Local &L, float eps, float *sxx, float *sxy, float *syy) {
-  const float a = L.sx * L.sx, b = L.sy * L.sy;
-  *sxx = a * L.c * L.c + b * L.s * L.s + eps;
-  *sxy = (a - b) * L.c * L.s;
-  *syy = a * L.s * L.s + b * L.c * L.c + eps;
-}
-
-// Sigma^-1 from the same eigen-decomposition, without a 2x2 determinant:
-// Q = u u^T / (sx^2 + eps) + v v^T / (sy^2 + eps), u = (c, s), v = (-s, c).
-__device__ __forceinline__ void conic(const Local &L, float eps, float *qa, float *qb, float *qc) {
-  const float ix = 1.0f / (L.sx * L.sx + eps), iy = 1.0f / (L.sy * L.sy + eps);
-  *qa = ix * L.c * L.c + iy * L.s * L.s;
-  *qb = (ix - iy) * L.c * L.s;
-  *qc = ix * L.s * L.s + iy * L.c * L.c;
 }
 
 struct CurveAttr {
@@ -176,34 +181,33 @@ __device__ __forceinline__ CurveAttr curve_attr(const bs_curves &c, int curve, i
 }
 
 __global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss) {
-  extern __shared__ float2 X[];  // [max samples per curve]
+  extern __shared__ double2 X[];  // [max samples per curve]
   const int curve = blockIdx.x;
   const bool closed = curve >= c.n_open;
   const int n = eval_samples(c, cfg, curve, X);
   __syncthreads();
   const int K = closed ? cfg.kc : cfg.g_open;
   const uint32_t first = c.draw_first[curve];
+  const float *P = curve_ctrl(c, curve);
+  const double ox = P[0], oy = P[1];
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    int seg = 0;
-    if (!closed) {
-      float t;
-      chain_param(idx, K, 3, &seg, &t);
-    }
+    const int seg = closed ? 0 : chain_seg(idx, K, 3);
     const CurveAttr at = curve_attr(c, curve, seg);
     const Local L = local_geometry(X, idx, K, cfg.rows, closed, at.width, cfg.rho);
-    float sxx, sxy, syy, qa, qb, qc;
-    covariance(L, cfg.eps, &sxx, &sxy, &syy);
-    conic(L, cfg.eps, &qa, &qb, &qc);
+    // Sigma = R diag(lx, ly) R^T (Eq. 11-12 with the eps floor)
+    const float lx = L.sx * L.sx + cfg.eps, ly = L.sy * L.sy + cfg.eps;
     float ex = -1.f, ey = -1.f;
     if (at.opac >= kAlphaMin) {
-      const float lth = logf(255.0f * at.opac);  // alpha >= 1/255 <=> 0.5 d^T Q d <= lth
+      const float lth = logf(255.0f * at.opac);  // alpha >= 1/255 <=> 0.5 d^T Sigma^-1 d <= lth
+      const float sxx = L.ux * L.ux * lx + L.uy * L.uy * ly;
+      const float syy = L.uy * L.uy * lx + L.ux * L.ux * ly;
       ex = sqrtf(2.0f * lth * sxx) + kExtPad;
       ey = sqrtf(2.0f * lth * syy) + kExtPad;
     }
     float4 *rec = reinterpret_cast<float4 *>(gauss + (size_t)(first + idx) * BS_GAUSS_FLOATS);
-    rec[0] = make_float4(X[idx].x, X[idx].y, qa, qb);
-    rec[1] = make_float4(qc, at.opac, at.col.x, at.col.y);
-    rec[2] = make_float4(at.col.z, ex, ey, 0.f);
+    rec[0] = make_float4((float)(ox + X[idx].x), (float)(oy + X[idx].y), L.ux, L.uy);
+    rec[1] = make_float4(rsqrtf(lx), rsqrtf(ly), at.opac, at.col.x);
+    rec[2] = make_float4(at.col.y, at.col.z, ex, ey);
   }
 }
 
@@ -220,8 +224,8 @@ __device__ __forceinline__ void sadd2(float2 *p, float x, float y) {
 
 __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
                                                                    bs_curves_grad g, int n_max) {
-  extern __shared__ float2 X[];  // [n_max] sample points, then [n_max] their gradients
-  float2 *dX = X + n_max;
+  extern __shared__ double2 X[];                       // [n_max] sample points
+  float2 *dX = reinterpret_cast<float2 *>(X + n_max);  // [n_max] their gradients
   __shared__ float2 dP[12];
   __shared__ float sAttr[8];  // opac[3] (open) or opac (closed), colour[3], width
   const int curve = blockIdx.x;
@@ -239,30 +243,17 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
     const int idx = round * blockDim.x + threadIdx.x;
     float d_op[3] = {0.f, 0.f, 0.f}, d_col[3] = {0.f, 0.f, 0.f}, d_w = 0.f;
     if (idx < n) {
-      int seg = 0;
-      if (!closed) {
-        float t;
-        chain_param(idx, K, 3, &seg, &t);
-      }
+      const int seg = closed ? 0 : chain_seg(idx, K, 3);
       const CurveAttr at = curve_attr(c, curve, seg);
       const Local L = local_geometry(X, idx, K, cfg.rows, closed, at.width, cfg.rho);
-      float qa, qb, qc;
-      conic(L, cfg.eps, &qa, &qb, &qc);
       const float *dg = dgauss + (size_t)(first + idx) * BS_DGAUSS_FLOATS;
-      const float4 d0 = *reinterpret_cast<const float4 *>(dg);
-      const float4 d1 = *reinterpret_cast<const float4 *>(dg + 4);
-      const float d8 = dg[8];
-      // dL/dSigma = -Q G Q with G the symmetric gradient of the conic.
-      const float ga = d0.z, gb = 0.5f * d0.w, gc = d1.x;
-      const float t00 = qa * ga + qb * gb, t01 = qa * gb + qb * gc;  // T = Q G
-      const float t10 = qb * ga + qc * gb, t11 = qb * gb + qc * gc;
-      const float mxx = -(t00 * qa + t01 * qb);
-      const float mxy = -(t00 * qb + t01 * qc);
-      const float myy = -(t10 * qb + t11 * qc);
-      const float cc = L.c * L.c, ss = L.s * L.s, cs = L.c * L.s;
-      const float dsx = 2.0f * L.sx * (mxx * cc + 2.0f * mxy * cs + myy * ss);
-      const float dsy = 2.0f * L.sy * (mxx * ss - 2.0f * mxy * cs + myy * cc);
-      const float dth = (L.sx * L.sx - L.sy * L.sy) * (2.0f * cs * (myy - mxx) + 2.0f * (cc - ss) * mxy);
+      const float4 d0 = *reinterpret_cast<const float4 *>(dg);      // mx, my, ux, uy
+      const float4 d1 = *reinterpret_cast<const float4 *>(dg + 4);  // isx, isy, o, r
+      const float4 d2 = *reinterpret_cast<const float4 *>(dg + 8);  // g, b, -, -
+      // isx = (sx^2 + eps)^-1/2  ->  d isx / d sx = -sx isx^3
+      const float isx = rsqrtf(L.sx * L.sx + cfg.eps), isy = rsqrtf(L.sy * L.sy + cfg.eps);
+      const float dsx = -d1.x * L.sx * isx * isx * isx;
+      const float dsy = -d1.y * L.sy * isy * isy * isy;
       // mean
       sadd2(&dX[idx], d0.x, d0.y);
       // sigma_x = |e| / rho
@@ -271,11 +262,12 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
         sadd2(&dX[L.e_hi], k * L.e.x, k * L.e.y);
         sadd2(&dX[L.e_lo], -k * L.e.x, -k * L.e.y);
       }
-      // theta = atan2(t_y, t_x)
+      // u = t / |t|  ->  dL/dt = (du - u (u . du)) / |t|
       if (L.lt > 0.f) {
-        const float k = dth / (L.lt * L.lt);
-        sadd2(&dX[L.t_hi], -k * L.t.y, k * L.t.x);
-        sadd2(&dX[L.t_lo], k * L.t.y, -k * L.t.x);
+        const float proj = L.ux * d0.z + L.uy * d0.w;
+        const float gx = (d0.z - L.ux * proj) / L.lt, gy = (d0.w - L.uy * proj) / L.lt;
+        sadd2(&dX[L.t_hi], gx, gy);
+        sadd2(&dX[L.t_lo], -gx, -gy);
       }
       if (closed) {
         if (L.lf > 0.f) {
@@ -283,14 +275,14 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
           sadd2(&dX[L.f_hi], k * L.f.x, k * L.f.y);
           sadd2(&dX[L.f_lo], -k * L.f.x, -k * L.f.y);
         }
-        d_op[0] = d1.y;
+        d_op[0] = d1.z;
       } else {
         d_w = dsy;
-        d_op[seg] = d1.y;
+        d_op[seg] = d1.z;
       }
-      d_col[0] = d1.z;
-      d_col[1] = d1.w;
-      d_col[2] = d8;
+      d_col[0] = d1.w;
+      d_col[1] = d2.x;
+      d_col[2] = d2.y;
     }
     // per-curve scalars: warp sums, then one shared atomic per warp
 #pragma unroll
@@ -310,19 +302,17 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const float2 d = dX[idx];
     if (!closed) {
-      int s;
-      float t, w[4];
-      chain_param(idx, K, 3, &s, &t);
-      bern3(t, w);
+      const int s = chain_seg(idx, K, 3);
+      float w[4];
+      bern3f((float)chain_t(idx, K, 3, s), w);
 #pragma unroll
       for (int i = 0; i < 4; ++i) sadd2(&dP[3 * s + i], w[i] * d.x, w[i] * d.y);
     } else {
       const int r = idx / K, k = idx - r * K;
-      const float tau = closed_tau(r, cfg.rows);
-      int s;
-      float t, w[4];
-      chain_param(k, K, 2, &s, &t);
-      bern3(t, w);
+      const float tau = (float)closed_tau(r, cfg.rows);
+      const int s = chain_seg(k, K, 2);
+      float w[4];
+      bern3f((float)chain_t(k, K, 2, s), w);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int j = 3 * s + i;
@@ -439,7 +429,7 @@ bs_status launch_curve_order(const bs_curves &c, const bs_sample_cfg &cfg, uint3
 bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float *gauss, cudaStream_t s) {
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
-  const size_t smem = (size_t)max_samples(c, cfg) * sizeof(float2);
+  const size_t smem = (size_t)max_samples(c, cfg) * sizeof(double2);
   BS_CUDA(cudaFuncSetAttribute(sample_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), gauss);
   BS_LAUNCHED("sample_fwd_kernel");
@@ -451,7 +441,7 @@ bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const 
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
   const int n_max = max_samples(c, cfg);
-  const size_t smem = 2 * (size_t)n_max * sizeof(float2);
+  const size_t smem = (size_t)n_max * (sizeof(double2) + sizeof(float2));
   BS_CUDA(cudaFuncSetAttribute(sample_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), dgauss, g, n_max);
   BS_LAUNCHED("sample_bwd_kernel");

@@ -2,12 +2,18 @@
 // backward, plus the L2 term of Eq. 13.
 //
 // One CTA per 16x16 tile, one pixel per thread.  The tile's list is staged
-// into shared memory 256 Gaussians at a time; each Gaussian is staged as a
-// log2-domain quadratic form so that a pixel evaluates
-//     p = qa dx^2 + qb2 dx dy + qc dy^2 + log2(o),    alpha = min(0.99, 2^p)
-// with qa = -a log2(e)/2, qb2 = -b log2(e), qc = -c log2(e)/2 for the conic
-// [[a, b], [b, c]].  The forward and the backward stage and evaluate alpha
-// with the same code, so both take the same skip decisions bit for bit.
+// into shared memory 256 Gaussians at a time.  A Gaussian is stored by its
+// eigen-frame (Eq. 11-12): Sigma^-1 = R diag(isx^2, isy^2) R^T with
+// R = [[ux, -uy], [uy, ux]], and is staged as the two scaled axes
+//     (A1, B1) = k isx (ux, uy),   (A2, B2) = k isy (-uy, ux),   k^2 = log2(e)/2,
+// so that a pixel at offset (dx, dy) from the mean evaluates
+//     t1 = A1 dx + B1 dy,  t2 = A2 dx + B2 dy,
+//     p  = log2(o) - t1^2 - t2^2 = log2(o exp(-0.5 d^T Sigma^-1 d)),
+//     alpha = min(0.99, 2^p).
+// A sum of two squares has no cancellation, unlike the conic form
+// a dx^2 + 2 b dx dy + c dy^2 of a thin, rotated Gaussian far along its
+// axis.  The forward and the backward stage and evaluate alpha with the same
+// code, so both take the same skip decisions bit for bit.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -20,9 +26,8 @@ namespace {
 
 constexpr int kTile = 16;
 constexpr int kThreads = kTile * kTile;
-constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
-constexpr float kQ = -0.5f * kLog2e;
+constexpr float kKappa = 0.84932180028801907f;  // sqrt(log2(e) / 2)
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -31,9 +36,10 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 struct Staged {
-  float4 a;  // mx, my, qa, qb2
-  float4 b;  // qc, lo, r, g
-  float2 c;  // b, o
+  float4 a;    // mx, my, A1, B1
+  float4 b;    // A2, B2, log2(o), r
+  float4 c;    // g, b, o, 0
+  float4 raw;  // ux, uy, isx, isy
 };
 
 // Stage Gaussian g; an index past the table (only possible after a sort that
@@ -42,28 +48,31 @@ __device__ __forceinline__ Staged stage(const float *__restrict__ gauss, uint32_
   Staged s;
   if (g >= n_gauss) {
     s.a = make_float4(0.f, 0.f, 0.f, 0.f);
-    s.b = make_float4(0.f, -INFINITY, 0.f, 0.f);
-    s.c = make_float2(0.f, 0.f);
+    s.b = make_float4(0.f, 0.f, -INFINITY, 0.f);
+    s.c = make_float4(0.f, 0.f, 0.f, 0.f);
+    s.raw = make_float4(1.f, 0.f, 0.f, 0.f);
     return s;
   }
   const float4 *rec = reinterpret_cast<const float4 *>(gauss + (size_t)g * BS_GAUSS_FLOATS);
-  const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
-  const float blue = __ldg(gauss + (size_t)g * BS_GAUSS_FLOATS + 8);
-  const float o = r1.y;
-  s.a = make_float4(r0.x, r0.y, __fmul_rn(kQ, r0.z), __fmul_rn(2.0f * kQ, r0.w));
-  s.b = make_float4(__fmul_rn(kQ, r1.x), o > 0.f ? log2f(o) : -INFINITY, r1.z, r1.w);
-  s.c = make_float2(blue, o);
+  const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+  const float ux = r0.z, uy = r0.w, isx = r1.x, isy = r1.y, o = r1.z;
+  const float kx = __fmul_rn(kKappa, isx), ky = __fmul_rn(kKappa, isy);
+  s.a = make_float4(r0.x, r0.y, __fmul_rn(kx, ux), __fmul_rn(kx, uy));
+  s.b = make_float4(__fmul_rn(ky, -uy), __fmul_rn(ky, ux), o > 0.f ? log2f(o) : -INFINITY, r1.w);
+  s.c = make_float4(r2.x, r2.y, o, 0.f);
+  s.raw = make_float4(ux, uy, isx, isy);
   return s;
 }
 
-// log2 of the unclamped alpha of a staged Gaussian at pixel centre (px, py).
+// log2 of the unclamped alpha of a staged Gaussian at pixel centre (px, py),
+// with the offsets and the two axis projections.
 __device__ __forceinline__ float log2_alpha(const float4 &a, const float4 &b, float px, float py, float &dx,
-                                            float &dy) {
+                                            float &dy, float &t1, float &t2) {
   dx = __fsub_rn(px, a.x);
   dy = __fsub_rn(py, a.y);
-  const float u = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));
-  const float v = __fmul_rn(b.x, dy);
-  return __fmaf_rn(dx, u, __fmaf_rn(dy, v, b.y));
+  t1 = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));
+  t2 = __fmaf_rn(b.x, dx, __fmul_rn(b.y, dy));
+  return __fmaf_rn(-t1, t1, __fmaf_rn(-t2, t2, b.z));
 }
 
 // kStats: also count, per pixel, the list entries evaluated (E), the entries
@@ -80,7 +89,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const float *__res
                                                               unsigned long long *__restrict__ stats) {
   __shared__ float4 s_a[kThreads];
   __shared__ float4 s_b[kThreads];
-  __shared__ float s_c[kThreads];
+  __shared__ float2 s_c[kThreads];
   uint32_t n_eval = 0, n_blend = 0;
   const int tile = blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -99,15 +108,15 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const float *__res
       const Staged s = stage(gauss, keys[i] & gmask, n_gauss);
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
-      s_c[threadIdx.x] = s.c.x;
+      s_c[threadIdx.x] = make_float2(s.c.x, s.c.y);
     }
     __syncthreads();
     if (!done) {
       const int n = (int)min((uint32_t)kThreads, r.y - base);
       for (int j = 0; j < n; ++j) {
         const float4 a = s_a[j], b = s_b[j];
-        float dx, dy;
-        const float al = fminf(kAlphaMax, ex2_approx(log2_alpha(a, b, px, py, dx, dy)));
+        float dx, dy, t1, t2;
+        const float al = fminf(kAlphaMax, ex2_approx(log2_alpha(a, b, px, py, dx, dy, t1, t2)));
         if (kStats) ++n_eval;
         if (al < kAlphaMin) continue;
         const float Tn = T * (1.f - al);
@@ -116,9 +125,10 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const float *__res
           break;
         }
         const float w = al * T;
-        c0 = __fmaf_rn(w, b.z, c0);
-        c1 = __fmaf_rn(w, b.w, c1);
-        c2 = __fmaf_rn(w, s_c[j], c2);
+        const float2 gb = s_c[j];
+        c0 = __fmaf_rn(w, b.w, c0);
+        c1 = __fmaf_rn(w, gb.x, c1);
+        c2 = __fmaf_rn(w, gb.y, c2);
         T = Tn;
         last = base - r.x + (uint32_t)j + 1;
         if (kStats) ++n_blend;
@@ -154,6 +164,16 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Reverse walk.  With S the colour behind Gaussian j as seen through it,
+// S <- alpha_j c_j + (1 - alpha_j) S (starting from bg behind the last
+// blended Gaussian), the colour derivative is
+//     dC/dalpha_j = T_j (c_j - S),
+// which keeps the (1 - alpha_j)^-1 of the recovered transmittance out of the
+// gradient.  Per Gaussian and pixel the walk accumulates
+//   q1 = dp t1, q2 = dp t2 (dp = dL/dlog2(alpha)), q1 dx, q1 dy, q2 dx,
+//   q2 dy, dp and w g (w = alpha T),
+// and the chain rule through the staging turns their tile sums into
+// d/d(mx, my, ux, uy, isx, isy, o, r, g, b).
 __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__restrict__ gauss,
                                                               const uint32_t *__restrict__ keys,
                                                               const uint2 *__restrict__ ranges, int W, int H,
@@ -164,7 +184,8 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__res
                                                               float *__restrict__ dgauss) {
   __shared__ float4 s_a[kThreads];
   __shared__ float4 s_b[kThreads];
-  __shared__ float2 s_c[kThreads];
+  __shared__ float4 s_c[kThreads];
+  __shared__ float4 s_raw[kThreads];
   __shared__ uint32_t s_g[kThreads];
   __shared__ uint32_t s_max_last;
   const int tile = blockIdx.x;
@@ -188,8 +209,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__res
     g2 = dimg[2 * plane + p];
     atomicMax(&s_max_last, last);
   }
-  // g . A, A = colour accumulated behind the current Gaussian, starts at T_final bg
-  float gA = T * (g0 * bg.x + g1 * bg.y + g2 * bg.z);
+  float gS = g0 * bg.x + g1 * bg.y + g2 * bg.z;  // g . S, S = bg behind the last blended Gaussian
   __syncthreads();
   const uint32_t max_last = min(s_max_last, r.y - r.x);
   for (uint32_t end = max_last; end > 0;) {
@@ -202,58 +222,67 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__res
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
+      s_raw[threadIdx.x] = s.raw;
       s_g[threadIdx.x] = g;
     }
     __syncthreads();
     for (int j = (int)(end - start) - 1; j >= 0; --j) {
       const uint32_t pos = start + (uint32_t)j;
-      float v[9];
+      float v[10];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) v[q] = 0.f;
+      for (int q = 0; q < 10; ++q) v[q] = 0.f;
       bool contrib = false;
       if (pos < last) {
         const float4 a = s_a[j], b = s_b[j];
-        float dx, dy;
-        const float raw = ex2_approx(log2_alpha(a, b, px, py, dx, dy));
+        float dx, dy, t1, t2;
+        const float raw = ex2_approx(log2_alpha(a, b, px, py, dx, dy, t1, t2));
         const float al = fminf(kAlphaMax, raw);
         if (al >= kAlphaMin) {
           contrib = true;
+          const float4 c = s_c[j];
           const float one_m = 1.f - al;
-          const float inv = 1.f / one_m;
-          T = T * inv;                         // T before this Gaussian
+          T = __fdividef(T, one_m);             // T before this Gaussian
           const float w = al * T;
-          const float cb = s_c[j].x;
-          const float gc = g0 * b.z + g1 * b.w + g2 * cb;
-          const float dal = T * gc - gA * inv;  // dL/dalpha
-          gA = __fmaf_rn(gc, w, gA);
-          v[6] = w * g0;
-          v[7] = w * g1;
-          v[8] = w * g2;
+          const float gc = g0 * b.w + g1 * c.x + g2 * c.y;
+          const float dal = T * (gc - gS);      // dL/dalpha
+          gS = __fmaf_rn(al, gc, one_m * gS);
+          v[7] = w * g0;
+          v[8] = w * g1;
+          v[9] = w * g2;
           if (raw <= kAlphaMax) {
-            const float dp = dal * al * kLn2;   // dL/d(log2 alpha)
-            const float t1 = dp * dx, t2 = dp * dy;
-            v[0] = -(t1 * (2.f * a.z) + t2 * a.w);  // sum dp (2qa dx + qb2 dy), negated: d/dmx
-            v[1] = -(t1 * a.w + t2 * (2.f * b.x));  // d/dmy
-            v[2] = t1 * dx;                         // sum dp dx^2
-            v[3] = t1 * dy;                         // sum dp dx dy
-            v[4] = t2 * dy;                         // sum dp dy^2
-            v[5] = dp;                              // sum dp
+            const float dp = dal * al * kLn2;   // dL/dlog2(alpha)
+            const float q1 = dp * t1, q2 = dp * t2;
+            v[0] = q1;
+            v[1] = q2;
+            v[2] = q1 * dx;
+            v[3] = q1 * dy;
+            v[4] = q2 * dx;
+            v[5] = q2 * dy;
+            v[6] = dp;
           }
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) v[q] = warp_sum(v[q]);
-        if (lane < 9) {
-          float val = v[0];
-#pragma unroll
-          for (int q = 1; q < 9; ++q)
-            if (lane == q) val = v[q];
-          const float o = s_c[j].y;
-          // constant factors of the chain rule (see the staging above)
-          if (lane == 2 || lane == 4) val *= kQ;
-          else if (lane == 3) val *= 2.f * kQ;
-          else if (lane == 5) val = o > 0.f ? val / (o * kLn2) : 0.f;
+        for (int q = 0; q < 10; ++q) v[q] = warp_sum(v[q]);
+        if (lane < 10) {
+          const float4 a = s_a[j], b = s_b[j], u = s_raw[j];
+          const float o = s_c[j].z;
+          // dL/dA1 = -2 sum q1 dx, dL/dB1 = -2 sum q1 dy, dL/dA2 = -2 sum q2 dx, dL/dB2 = -2 sum q2 dy
+          const float dA1 = -2.f * v[2], dB1 = -2.f * v[3], dA2 = -2.f * v[4], dB2 = -2.f * v[5];
+          float val;
+          switch (lane) {
+            case 0: val = 2.f * (a.z * v[0] + b.x * v[1]); break;                // mx
+            case 1: val = 2.f * (a.w * v[0] + b.y * v[1]); break;                // my
+            case 2: val = kKappa * (u.z * dA1 + u.w * dB2); break;               // ux
+            case 3: val = kKappa * (u.z * dB1 - u.w * dA2); break;               // uy
+            case 4: val = kKappa * (u.x * dA1 + u.y * dB1); break;               // isx
+            case 5: val = kKappa * (u.x * dB2 - u.y * dA2); break;               // isy
+            case 6: val = o > 0.f ? v[6] / (o * kLn2) : 0.f; break;              // o
+            case 7: val = v[7]; break;
+            case 8: val = v[8]; break;
+            default: val = v[9]; break;
+          }
           if (val != 0.f && s_g[j] < n_gauss) atomicAdd(dgauss + (size_t)s_g[j] * BS_DGAUSS_FLOATS + lane, val);
         }
       }
@@ -269,9 +298,9 @@ __global__ void l2_kernel(const float *__restrict__ img, const float *__restrict
   const float scale = (float)(2.0 / (double)n);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const float d = img[i] - target[i];
-    dimg[i] = scale * d;
-    acc += (double)d * (double)d;
+    const double d = (double)img[i] - (double)target[i];   // exact
+    dimg[i] = scale * (float)d;
+    acc += d * d;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

@@ -1,0 +1,134 @@
+"""Parity at the full benchmark size (2048x2048, 2048 open + 2048 closed
+curves, 64 Gaussians per curve = 262,144 Gaussians, about 10^7 tile pairs),
+in the launch configuration bench.py times: draw order and every tile key
+bit-exact, all Gaussians of the sampling, sampled pixels of the blend, and
+the backward of a loss on a 32x32 crop."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle.curves import SampleCfg as OCfg, table_to_f32, table_from_f32
+from oracle.pipeline import as_curves
+from paper_2503_16424_gb300 import synth
+from tests.gpu_cases import grad_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def problem():
+    from paper_2503_16424_gb300 import bs
+    from paper_2503_16424_gb300.raster import Rasterizer
+    w = synth.WORKLOADS["hires_2048_4096"]
+    arr = synth.make_curves(w["seed"], w["W"], w["H"], w["n_open"], w["n_closed"], style=w["style"]).as_dict()
+    ocfg = OCfg(g_open=w["g_open"], rows_closed=w["rows_closed"], k_closed=w["k_closed"])
+    rank, first = oracle.draw_order(arr["open_ctrl"], arr["open_width"], arr["closed_ctrl"], ocfg)
+    with torch.no_grad():
+        tab = oracle.gaussian_table(as_curves(arr), ocfg, first)
+    cfg = bs.SampleCfg(g_open=w["g_open"], rows_closed=w["rows_closed"], k_closed=w["k_closed"])
+    curves = bs.CurveSet.from_arrays(arr, device="cuda")
+    r = Rasterizer(bs.Canvas(w["W"], w["H"], w["tile"]), cfg, curves.n_open, curves.n_closed,
+                   pair_capacity=1 << 25)
+    return dict(bs=bs, w=w, arr=arr, rank=rank, first=first, tab=tab, rec=table_to_f32(tab), r=r,
+                curves=curves)
+
+
+def test_full_order_and_sampling(problem):
+    p = problem
+    r = p["r"]
+    r.forward(p["curves"])
+    assert np.array_equal(r.rank.cpu().numpy(), p["rank"])
+    assert np.array_equal(r.first.cpu().numpy(), p["first"])
+    got = r.gauss.cpu().numpy().astype(np.float64)
+    tab = p["tab"]
+    ref64 = np.stack([tab[k].numpy() for k in ("mx", "my", "ux", "uy", "isx", "isy")], 1)
+    pos = np.abs(got[:, 0:2] - ref64[:, 0:2]).max() / 2048
+    u = np.abs(got[:, 2:4] - ref64[:, 2:4]).max()
+    sc = (np.abs(got[:, 4:6] - ref64[:, 4:6]) / ref64[:, 4:6]).max()
+    print(f"full sampling: position err {pos:.1e} of canvas, direction err {u:.1e}, scale err {sc:.1e}")
+    assert pos <= 1e-5 and u <= 1e-5 and sc <= 1e-5
+
+
+def test_full_binning_bit_exact(problem):
+    p = problem
+    bs = p["bs"]
+    rec = p["rec"]
+    keys, ranges, _ = oracle.tile_keys(rec, 2048, 2048, 16)
+    gauss = torch.as_tensor(rec, device="cuda")
+    b = bs.Binning(bs.Canvas(2048, 2048), "cuda", pair_capacity=1 << 25).run(gauss)
+    print(f"full binning: {keys.shape[0]} pairs")
+    assert b.device_status() == 0
+    assert b.n_pairs == keys.shape[0]
+    assert np.array_equal(b.keys[:b.n_pairs].cpu().numpy().view(np.uint32), keys)
+    assert np.array_equal(b.ranges.cpu().numpy().view(np.uint32), ranges)
+    p["binning"] = b
+    p["gauss_in"] = gauss
+
+
+def test_full_blend_sampled_pixels(problem):
+    p = problem
+    bs = p["bs"]
+    if "binning" not in p:
+        pytest.skip("needs the binning test")
+    canvas = bs.Canvas(2048, 2048)
+    img, T, nc = bs.render_fwd(p["gauss_in"], canvas, p["binning"])
+    rng = np.random.default_rng(0)
+    n = 192
+    xs = rng.integers(0, 2048, n)
+    ys = rng.integers(0, 2048, n)
+    tab = table_from_f32(p["rec"])
+    ref = {"C": [], "T": [], "flag": []}
+    for s in range(0, n, 16):
+        rr = oracle.render_pixels(tab, xs[s:s + 16].astype(np.float64), ys[s:s + 16].astype(np.float64),
+                                  margin=4e-6, margin_T=1e-4)
+        for k in ref:
+            ref[k].append(rr[k])
+    C = torch.cat(ref["C"]).numpy()
+    flag = torch.cat(ref["flag"]).numpy()
+    got = img.cpu().numpy()[:, ys, xs].T.astype(np.float64)
+    err = np.abs(got - C).max(1)
+    print(f"full blend: {n} pixels, flagged {flag.sum()}, max err {err[~flag].max():.1e}")
+    assert flag.mean() <= 0.02
+    assert err[~flag].max() <= 1e-5
+    p["fwd"] = (img, T, nc)
+
+
+def test_full_backward_crop(problem):
+    p = problem
+    bs = p["bs"]
+    if "fwd" not in p:
+        pytest.skip("needs the blend test")
+    img, T, nc = p["fwd"]
+    x0, y0, side = 1008, 1008, 32
+    tab = table_from_f32(p["rec"])
+    ys, xs = torch.meshgrid(torch.arange(y0, y0 + side, dtype=torch.float64),
+                            torch.arange(x0, x0 + side, dtype=torch.float64), indexing="ij")
+    xs, ys = xs.reshape(-1), ys.reshape(-1)
+    # Gaussians whose support box touches the crop (all others have alpha < 1/255 there)
+    ex, ey = tab["ext_x"], tab["ext_y"]
+    near = ((ex >= 0) & (tab["mx"] + ex >= x0 + 0.5) & (tab["mx"] - ex <= x0 + side - 0.5)
+            & (tab["my"] + ey >= y0 + 0.5) & (tab["my"] - ey <= y0 + side - 0.5))
+    idx = torch.nonzero(near)[:, 0]
+    sub = {k: v[idx] for k, v in tab.items()}
+    pf = oracle.render_pixels(sub, xs, ys, margin=1e-4)
+    rng = np.random.default_rng(1)
+    dC = torch.as_tensor(rng.normal(0, 1e-6, (side * side, 3)))
+    dC[pf["flag"]] = 0.0
+    dimg = torch.zeros(3, 2048, 2048, dtype=torch.float32)
+    dimg[:, y0:y0 + side, x0:x0 + side] = dC.float().reshape(side, side, 3).permute(2, 0, 1)
+    dgauss, _ = bs.render_bwd(p["gauss_in"], bs.Canvas(2048, 2048), p["binning"], T, nc, dimg.cuda())
+    ref = oracle.render_grads(sub, xs, ys, dC.float().double())
+    got = dgauss.cpu().double()
+    others = torch.ones(got.shape[0], dtype=torch.bool)
+    others[idx] = False
+    assert float(got[others].abs().max()) == 0.0
+    g = got[idx]
+    cols = {"mx": 0, "my": 1, "ux": 2, "uy": 3, "isx": 4, "isy": 5, "o": 6}
+    errs = {k: grad_rel_err(g[:, c], ref[k]) for k, c in cols.items()}
+    errs["col"] = grad_rel_err(g[:, 7:10], ref["col"])
+    print(f"full backward crop: {idx.numel()} Gaussians near the crop, rel errs " +
+          ", ".join(f"{k} {v:.1e}" for k, v in errs.items()))
+    for k, e in errs.items():
+        assert e <= 1e-3, k

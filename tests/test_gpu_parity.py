@@ -17,7 +17,7 @@ from tests.gpu_cases import CASES, arrays, grad_rel_err, ocfg, oracle_table, tar
 
 pytestmark = pytest.mark.gpu
 
-FIELD_SLICES = {"mx": 0, "my": 1, "ca": 2, "cb": 3, "cc": 4, "o": 5}
+FIELD_SLICES = {"mx": 0, "my": 1, "ux": 2, "uy": 3, "isx": 4, "isy": 5, "o": 6}
 
 
 @pytest.fixture(scope="module")
@@ -57,18 +57,21 @@ def test_sample_matches_oracle(bs, name):
     gauss = bs.sample_curves(curves, _cfg(bs, case), first).cpu().numpy().astype(np.float64)
     tab, _, _ = oracle_table(case, arr)
     ref = table_to_f32(tab).astype(np.float64)
-    ref64 = np.stack([tab["mx"].numpy(), tab["my"].numpy(), tab["ca"].detach().numpy(),
-                      tab["cb"].detach().numpy(), tab["cc"].detach().numpy(), tab["o"].numpy()], 1)
-    # positions relative to the canvas size, conic entries relative to the
-    # Gaussian's largest conic entry, the rest relative to 1
+    ref64 = np.stack([tab[k].detach().numpy() for k in ("mx", "my", "ux", "uy", "isx", "isy")], 1)
+    # positions relative to the canvas size, the rest relative to 1 (the
+    # direction) or to the value (the inverse scales)
     scale_pos = max(case.W, case.H)
-    assert np.abs(gauss[:, 0:2] - ref64[:, 0:2]).max() <= 1e-5 * scale_pos
-    qmax = np.abs(ref64[:, 2:5]).max(1, keepdims=True)
-    assert (np.abs(gauss[:, 2:5] - ref64[:, 2:5]) / qmax).max() <= 1e-5
-    assert np.array_equal(gauss[:, 5:9], ref[:, 5:9])           # opacity and colour are copied
-    ext_ok = ref[:, 9] >= 0
-    assert np.array_equal(gauss[:, 9] >= 0, ext_ok)
-    assert (np.abs(gauss[ext_ok, 9:11] - ref[ext_ok, 9:11]) / np.maximum(ref[ext_ok, 9:11], 1.0)).max() <= 1e-5
+    pos_err = np.abs(gauss[:, 0:2] - ref64[:, 0:2]).max() / scale_pos
+    u_err = np.abs(gauss[:, 2:4] - ref64[:, 2:4]).max()
+    s_err = (np.abs(gauss[:, 4:6] - ref64[:, 4:6]) / ref64[:, 4:6]).max()
+    print(f"{name}: position err {pos_err:.1e} (of canvas), direction err {u_err:.1e}, scale err {s_err:.1e}")
+    assert pos_err <= 1e-5
+    assert u_err <= 1e-5
+    assert s_err <= 1e-5
+    assert np.array_equal(gauss[:, 6:10], ref[:, 6:10])          # opacity and colour are copied
+    ext_ok = ref[:, 10] >= 0
+    assert np.array_equal(gauss[:, 10] >= 0, ext_ok)
+    assert (np.abs(gauss[ext_ok, 10:12] - ref[ext_ok, 10:12]) / np.maximum(ref[ext_ok, 10:12], 1.0)).max() <= 1e-5
 
 
 def _bin(bs, case, rec):
@@ -98,16 +101,16 @@ def test_bin_bit_exact_many_partitions_and_degenerate(bs):
     rec = np.zeros((n, 12), dtype=np.float32)
     rec[:, 0] = rng.uniform(-40, W + 40, n)
     rec[:, 1] = rng.uniform(-40, H + 40, n)
-    rec[:, 9] = rng.uniform(0, 30, n)
-    rec[:, 10] = rng.uniform(0, 30, n)
-    rec[::97, 9] = -1.0
+    rec[:, 10] = rng.uniform(0, 60, n)
+    rec[:, 11] = rng.uniform(0, 60, n)
+    rec[::97, 10] = -1.0
     rec[1::97, 0] = np.nan
     rec[2::97, 1] = 1e30
-    rec[3::97, 9] = np.inf
-    rec[4, 9:11] = 1e4
+    rec[3::97, 10] = np.inf
+    rec[4, 10:12] = 1e4
     rec[5, 0:2] = [W + 0.4999, H + 0.5]
     rec[6, 0:2] = [0.5, 0.5]
-    rec[6, 9:11] = 0.0
+    rec[6, 10:12] = 0.0
     keys, ranges, _ = oracle.tile_keys(rec, W, H, 16)
     assert keys.shape[0] > 50000
 
@@ -133,12 +136,16 @@ def test_render_fwd_matches_oracle(bs, name):
     tab, _, _ = oracle_table(case)
     rec = table_to_f32(tab)
     gauss, b, img, T, nc = _render(bs, case, rec)
-    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg)
+    # flag decisions within 4e-6 (alpha) / 1e-4 (transmittance) of a threshold
+    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg, margin=4e-6, margin_T=1e-4)
     ok = ~ref["flag"].numpy()
-    assert ok.mean() > 1 - 1e-3
     err = np.abs(img.cpu().numpy().astype(np.float64) - ref["img"].numpy()).max(0)
+    terr = np.abs(T.cpu().numpy() - ref["T"].numpy())
+    print(f"{name}: flagged {1 - ok.mean():.2e}, max err {err[ok].max():.2e}, "
+          f"max err incl. flagged {err.max():.2e}, T err {terr[ok].max():.2e}")
+    assert 1 - ok.mean() <= 1e-4
     assert err[ok].max() <= 1e-5
-    assert np.abs(T.cpu().numpy() - ref["T"].numpy())[ok].max() <= 1e-5
+    assert terr[ok].max() <= 1e-5
     # the last blended Gaussian of every pixel, through the tile list
     keys = b.keys[:b.n_pairs].cpu().numpy().view(np.uint32).astype(np.int64)
     ranges = b.ranges.cpu().numpy().view(np.uint32).astype(np.int64)
@@ -159,16 +166,23 @@ def test_render_bwd_matches_oracle(bs, name):
     gauss, b, img, T, nc = _render(bs, case, rec)
     tgt = torch.as_tensor(target(case), device="cuda")
     _, dimg = bs.l2_loss_grad(img, tgt)
+    # pixels near a threshold decision (incl. the 0.99 clamp kink) get no
+    # gradient on either side
+    ref_f = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg, margin=1e-4)["flag"]
+    dimg = dimg * (~ref_f).to(dimg.device)[None].float()
     dgauss, _ = bs.render_bwd(gauss, _canvas(bs, case), b, T, nc, dimg)
     ys, xs = torch.meshgrid(torch.arange(case.H, dtype=torch.float64),
                             torch.arange(case.W, dtype=torch.float64), indexing="ij")
     dC = dimg.cpu().double().permute(1, 2, 0).reshape(-1, 3)
     ref = oracle.render_grads(table_from_f32(rec), xs.reshape(-1), ys.reshape(-1), dC, bg=case.bg)
     got = dgauss.cpu().double()
-    for key, col in FIELD_SLICES.items():
-        assert grad_rel_err(got[:, col], ref[key]) <= 1e-3, key
-    assert grad_rel_err(got[:, 6:9], ref["col"]) <= 1e-3
-    assert torch.all(got[:, 9:] == 0)
+    errs = {key: grad_rel_err(got[:, col], ref[key]) for key, col in FIELD_SLICES.items()}
+    errs["col"] = grad_rel_err(got[:, 7:10], ref["col"])
+    print(f"{name}: flagged {float(ref_f.double().mean()):.2e}, rel errs " +
+          ", ".join(f"{k} {v:.1e}" for k, v in errs.items()))
+    for key, e in errs.items():
+        assert e <= 1e-3, key
+    assert torch.all(got[:, 10:] == 0)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -179,16 +193,20 @@ def test_sample_bwd_matches_oracle(bs, name):
     rng = np.random.default_rng(case.seed)
     n = tab["mx"].shape[0]
     dg = np.zeros((n, 12), dtype=np.float32)
-    dg[:, 0:9] = rng.normal(0, 1, (n, 9)).astype(np.float32)
-    dg[:, 2:5] *= 10.0
-    dtab = dict(mx=dg[:, 0], my=dg[:, 1], ca=dg[:, 2], cb=dg[:, 3], cc=dg[:, 4], o=dg[:, 5], col=dg[:, 6:9])
+    dg[:, 0:10] = rng.normal(0, 1, (n, 10)).astype(np.float32)
+    dg[:, 2:6] *= 10.0
+    dtab = dict(mx=dg[:, 0], my=dg[:, 1], ux=dg[:, 2], uy=dg[:, 3], isx=dg[:, 4], isy=dg[:, 5], o=dg[:, 6],
+                col=dg[:, 7:10])
     dtab = {k: torch.as_tensor(v.astype(np.float64)) for k, v in dtab.items()}
     ref = sample_vjp(as_curves(arr), ocfg(case), dtab, first)
     curves = _gpu_curves(bs, arr)
     grad = bs.sample_curves_bwd(curves, _cfg(bs, case), torch.as_tensor(first.astype(np.int32), device="cuda"),
                                 torch.as_tensor(dg, device="cuda"))
-    for k in ("open_ctrl", "open_width", "open_color", "open_opac", "closed_ctrl", "closed_color", "closed_opac"):
-        assert grad_rel_err(getattr(grad, k).cpu(), ref[k]) <= 1e-3, k
+    errs = {k: grad_rel_err(getattr(grad, k).cpu(), ref[k]) for k in
+            ("open_ctrl", "open_width", "open_color", "open_opac", "closed_ctrl", "closed_color", "closed_opac")}
+    print(f"{name}: " + ", ".join(f"{k} {v:.1e}" for k, v in errs.items()))
+    for k, e in errs.items():
+        assert e <= 1e-3, k
 
 
 def test_l2_matches_oracle(bs):

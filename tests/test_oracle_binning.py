@@ -23,13 +23,13 @@ def test_rects_equal_per_pixel_enumeration():
     [xlo, xhi] (float32 bounds), enumerated pixel by pixel."""
     W, H, T = 53, 37, 8
     rec = _table_f32(1, W, H, 4, 2, SampleCfg(g_open=9, rows_closed=3, k_closed=4))
-    rec[0, 9] = -1.0                     # culled
+    rec[0, 10] = -1.0                    # culled
     rec[1, 0] = np.float32(np.nan)       # non-finite
     rec[2, 0] = 1e30                     # far away
     tx0, tx1, ty0, ty1, ok = tile_rects_f32(rec, W, H, T)
     f = np.float32
     for g in range(rec.shape[0]):
-        mx, my, ex, ey = rec[g, 0], rec[g, 1], rec[g, 9], rec[g, 10]
+        mx, my, ex, ey = rec[g, 0], rec[g, 1], rec[g, 10], rec[g, 11]
         with np.errstate(invalid="ignore", over="ignore"):
             xlo, xhi = (mx - ex) - f(0.5), (mx + ex) - f(0.5)
             ylo, yhi = (my - ey) - f(0.5), (my + ey) - f(0.5)
@@ -57,10 +57,8 @@ def test_culling_is_exact(W, H, T):
     tiles_x = -(-W // T)
     ys, xs = np.mgrid[0:H, 0:W]
     px, py = torch.as_tensor(xs.ravel() + 0.5), torch.as_tensor(ys.ravel() + 0.5)
-    dx = px[:, None] - tab["mx"][None]
-    dy = py[:, None] - tab["my"][None]
-    s = 0.5 * (tab["ca"] * dx * dx + 2 * tab["cb"] * dx * dy + tab["cc"] * dy * dy)
-    a = tab["o"] * torch.exp(-s)
+    from oracle.raster import _alpha_raw
+    a = _alpha_raw(tab, px, py)
     hit = torch.nonzero(a >= 1 / 255)
     assert hit.shape[0] > 100
     for p, g in hit.tolist():

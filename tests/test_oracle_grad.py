@@ -60,14 +60,14 @@ def test_per_gaussian_grads_fd():
     curves, target = _case(3, 8, 8, 2, 1, cfg)
     res = step(curves, cfg, 8, 8, target)
     tab = {k: v.detach().clone() for k, v in res["table"].items() if k in
-           ("mx", "my", "ca", "cb", "cc", "o", "col")}
+           ("mx", "my", "ux", "uy", "isx", "isy", "o", "col")}
 
     def loss_of(t):
         img = oracle.render_image(t, 8, 8)["img"]
         return float(oracle.l2_loss(img, target)[0])
 
     rng = np.random.default_rng(0)
-    for key in ("mx", "my", "ca", "cb", "cc", "o", "col"):
+    for key in ("mx", "my", "ux", "uy", "isx", "isy", "o", "col"):
         g = res["dtable"][key].reshape(-1)
         for i in rng.choice(g.numel(), size=min(6, g.numel()), replace=False):
             h = 1e-6 * max(1.0, abs(float(tab[key].reshape(-1)[i])))

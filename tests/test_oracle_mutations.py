@@ -15,12 +15,12 @@ def _expect_fail(fn, *args):
         fn(*args)
 
 
-def test_flipped_conic_offdiagonal_is_caught(monkeypatch):
+def test_flipped_rotation_is_caught(monkeypatch):
     orig = raster_mod._alpha_raw
 
     def bad(tab, px, py):
         t = dict(tab)
-        t["cb"] = -tab["cb"]
+        t["uy"] = -tab["uy"]
         return orig(t, px, py)
     monkeypatch.setattr(raster_mod, "_alpha_raw", bad)
     _expect_fail(tr.test_single_rotated_gaussian_matches_density_ratio)
@@ -46,6 +46,17 @@ def test_reversed_boundary_is_caught(monkeypatch):
     monkeypatch.setattr(curves_mod, "closed_boundaries", bad)
     monkeypatch.setattr(tg.oracle, "closed_boundaries", bad)
     _expect_fail(tg.test_closed_boundaries_order)
+
+
+def test_swapped_scales_are_caught(monkeypatch):
+    orig = raster_mod._alpha_raw
+
+    def bad(tab, px, py):
+        t = dict(tab)
+        t["isx"], t["isy"] = tab["isy"], tab["isx"]
+        return orig(t, px, py)
+    monkeypatch.setattr(raster_mod, "_alpha_raw", bad)
+    _expect_fail(tr.test_single_rotated_gaussian_matches_density_ratio)
 
 
 def test_swapped_sigma_axes_is_caught(monkeypatch):

@@ -17,11 +17,12 @@ F64 = torch.float64
 
 
 def _table(mx, my, Sig, o, col):
+    """A table from covariances: R and the inverse scales from eigh."""
     Sig = np.asarray(Sig, dtype=np.float64)
-    inv = np.linalg.inv(Sig)
+    w, v = np.linalg.eigh(Sig)
     t = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64))
-    return dict(mx=t(mx), my=t(my), ca=t(inv[:, 0, 0]), cb=t(inv[:, 0, 1]), cc=t(inv[:, 1, 1]),
-                o=t(o), col=t(col))
+    return dict(mx=t(mx), my=t(my), ux=t(v[:, 0, 0]), uy=t(v[:, 1, 0]), isx=t(w[:, 0] ** -0.5),
+                isy=t(w[:, 1] ** -0.5), o=t(o), col=t(col), Sig=Sig)
 
 
 def test_single_rotated_gaussian_matches_density_ratio():
@@ -51,8 +52,8 @@ def sequential_blend(tab, x, y, bg):
     last = -1
     px, py = x + 0.5, y + 0.5
     for i in range(tab["mx"].shape[0]):
-        dx, dy = px - float(tab["mx"][i]), py - float(tab["my"][i])
-        q = float(tab["ca"][i]) * dx * dx + 2 * float(tab["cb"][i]) * dx * dy + float(tab["cc"][i]) * dy * dy
+        d = np.array([px - float(tab["mx"][i]), py - float(tab["my"][i])])
+        q = d @ np.linalg.solve(tab["Sig"][i], d)
         a = min(0.99, float(tab["o"][i]) * math.exp(-0.5 * q))
         if a < 1 / 255:
             continue
@@ -165,4 +166,4 @@ def test_rotation_symmetry_of_sample_and_render():
 def test_render_of_f32_table_roundtrip():
     rec = np.random.default_rng(9).uniform(0, 1, (5, 12)).astype(np.float32)
     t = table_from_f32(rec)
-    assert t["mx"].dtype == F64 and np.array_equal(t["col"].numpy().astype(np.float32), rec[:, 6:9])
+    assert t["mx"].dtype == F64 and np.array_equal(t["col"].numpy().astype(np.float32), rec[:, 7:10])
