@@ -1,9 +1,10 @@
 // Per-tile alpha blending (Section 3.4, Eq. 9-10) and its reverse-order
 // backward, plus the L2 term of Eq. 13.
 //
-// One CTA per 16x16 tile, one pixel per thread.  The tile's list is staged
-// into shared memory 256 Gaussians at a time.  A Gaussian is stored by its
-// eigen-frame (Eq. 11-12): Sigma^-1 = R diag(isx^2, isy^2) R^T with
+// One CTA of 64 threads per 16x16 tile; each thread owns 4 neighbouring
+// pixels of one row, so a warp covers a 16x8 half tile.  The tile's list is
+// staged into shared memory 64 Gaussians at a time.  A Gaussian is stored by
+// its eigen-frame (Eq. 11-12): Sigma^-1 = R diag(isx^2, isy^2) R^T with
 // R = [[ux, -uy], [uy, ux]], and is staged as the two scaled axes
 //     (A1, B1) = k isx (ux, uy),   (A2, B2) = k isy (-uy, ux),   k^2 = log2(e)/2,
 // so that a pixel at offset (dx, dy) from the mean evaluates
@@ -12,8 +13,9 @@
 //     alpha = min(0.99, 2^p).
 // A sum of two squares has no cancellation, unlike the conic form
 // a dx^2 + 2 b dx dy + c dy^2 of a thin, rotated Gaussian far along its
-// axis.  The forward and the backward stage and evaluate alpha with the same
-// code, so both take the same skip decisions bit for bit.
+// axis.  B1 dy and B2 dy are shared by a thread's 4 pixels.  The forward and
+// the backward stage and evaluate alpha with the same code, so both take the
+// same skip decisions bit for bit.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -25,9 +27,11 @@ namespace bs {
 namespace {
 
 constexpr int kTile = 16;
-constexpr int kThreads = kTile * kTile;
+constexpr int kPix = 4;                             // pixels per thread, along a row
+constexpr int kThreads = kTile * kTile / kPix;      // 64
+constexpr int kBatch = kThreads;                    // Gaussians staged per round
 constexpr float kLn2 = 0.6931471805599453f;
-constexpr float kKappa = 0.84932180028801907f;  // sqrt(log2(e) / 2)
+constexpr float kKappa = 0.84932180028801907f;      // sqrt(log2(e) / 2)
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -36,11 +40,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 struct Staged {
-  float4 a;    // mx, my, A1, B1
-  float4 b;    // A2, B2, log2(o), r
-  float4 c;    // g, b, o, 0
-  float4 raw;  // ux, uy, isx, isy
+  float4 a;  // mx, my, A1, B1
+  float4 b;  // A2, B2, log2(o), r
+  float2 c;  // g, b
 };
+
+__device__ __forceinline__ void scaled_axes(float ux, float uy, float isx, float isy, float &A1, float &B1,
+                                            float &A2, float &B2) {
+  const float kx = __fmul_rn(kKappa, isx), ky = __fmul_rn(kKappa, isy);
+  A1 = __fmul_rn(kx, ux);
+  B1 = __fmul_rn(kx, uy);
+  A2 = __fmul_rn(ky, -uy);
+  B2 = __fmul_rn(ky, ux);
+}
 
 // Stage Gaussian g; an index past the table (only possible after a sort that
 // gave up waiting) stages an invisible Gaussian.
@@ -49,33 +61,51 @@ __device__ __forceinline__ Staged stage(const float *__restrict__ gauss, uint32_
   if (g >= n_gauss) {
     s.a = make_float4(0.f, 0.f, 0.f, 0.f);
     s.b = make_float4(0.f, 0.f, -INFINITY, 0.f);
-    s.c = make_float4(0.f, 0.f, 0.f, 0.f);
-    s.raw = make_float4(1.f, 0.f, 0.f, 0.f);
+    s.c = make_float2(0.f, 0.f);
     return s;
   }
   const float4 *rec = reinterpret_cast<const float4 *>(gauss + (size_t)g * BS_GAUSS_FLOATS);
   const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
-  const float ux = r0.z, uy = r0.w, isx = r1.x, isy = r1.y, o = r1.z;
-  const float kx = __fmul_rn(kKappa, isx), ky = __fmul_rn(kKappa, isy);
-  s.a = make_float4(r0.x, r0.y, __fmul_rn(kx, ux), __fmul_rn(kx, uy));
-  s.b = make_float4(__fmul_rn(ky, -uy), __fmul_rn(ky, ux), o > 0.f ? log2f(o) : -INFINITY, r1.w);
-  s.c = make_float4(r2.x, r2.y, o, 0.f);
-  s.raw = make_float4(ux, uy, isx, isy);
+  float A1, B1, A2, B2;
+  scaled_axes(r0.z, r0.w, r1.x, r1.y, A1, B1, A2, B2);
+  const float o = r1.z;
+  s.a = make_float4(r0.x, r0.y, A1, B1);
+  s.b = make_float4(A2, B2, o > 0.f ? log2f(o) : -INFINITY, r1.w);
+  s.c = make_float2(r2.x, r2.y);
   return s;
 }
 
-// log2 of the unclamped alpha of a staged Gaussian at pixel centre (px, py),
-// with the offsets and the two axis projections.
-__device__ __forceinline__ float log2_alpha(const float4 &a, const float4 &b, float px, float py, float &dx,
-                                            float &dy, float &t1, float &t2) {
-  dx = __fsub_rn(px, a.x);
-  dy = __fsub_rn(py, a.y);
-  t1 = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));
-  t2 = __fmaf_rn(b.x, dx, __fmul_rn(b.y, dy));
+// log2 of the unclamped alpha at one pixel of a row: dx = px - mx, and the
+// row's shared b1dy = B1 dy, b2dy = B2 dy.
+__device__ __forceinline__ float pixel_log2_alpha(const float4 &a, const float4 &b, float dx, float b1dy,
+                                                  float b2dy, float &t1, float &t2) {
+  t1 = __fmaf_rn(a.z, dx, b1dy);
+  t2 = __fmaf_rn(b.x, dx, b2dy);
   return __fmaf_rn(-t1, t1, __fmaf_rn(-t2, t2, b.z));
 }
 
-// kStats: also count, per pixel, the list entries evaluated (E), the entries
+struct TilePixels {
+  int x0, y;        // first pixel of the thread's row segment
+  float px[kPix], py;
+  unsigned inside;  // bit i: pixel i lies on the canvas
+};
+
+__device__ __forceinline__ TilePixels tile_pixels(int tile, int tiles_x, int W, int H) {
+  TilePixels t;
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  t.y = ty * kTile + (threadIdx.x >> 2);
+  t.x0 = tx * kTile + (threadIdx.x & 3) * kPix;
+  t.py = (float)t.y + 0.5f;
+  t.inside = 0;
+#pragma unroll
+  for (int i = 0; i < kPix; ++i) {
+    t.px[i] = (float)(t.x0 + i) + 0.5f;
+    if (t.x0 + i < W && t.y < H) t.inside |= 1u << i;
+  }
+  return t;
+}
+
+// kStats: also count the (pixel, list entry) evaluations (E), the entries
 // blended, and the entries of the tile lists times the tile's pixels, into
 // stats[0..2] (for measurement; same blend otherwise).
 template <bool kStats>
@@ -87,50 +117,57 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const float *__res
                                                               float *__restrict__ T_out,
                                                               uint32_t *__restrict__ nc_out,
                                                               unsigned long long *__restrict__ stats) {
-  __shared__ float4 s_a[kThreads];
-  __shared__ float4 s_b[kThreads];
-  __shared__ float2 s_c[kThreads];
+  __shared__ float4 s_a[kBatch];
+  __shared__ float4 s_b[kBatch];
+  __shared__ float2 s_c[kBatch];
   uint32_t n_eval = 0, n_blend = 0;
   const int tile = blockIdx.x;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const int x = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int y = ty * kTile + threadIdx.x / kTile;
-  const bool inside = x < W && y < H;
-  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const TilePixels tp = tile_pixels(tile, tiles_x, W, H);
   const uint2 r = ranges[tile];
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  uint32_t last = 0;
-  bool done = !inside;
-  for (uint32_t base = r.x; base < r.y; base += kThreads) {
-    if (__syncthreads_count(done) == kThreads) break;
+  float T[kPix], c0[kPix], c1[kPix], c2[kPix];
+  uint32_t last[kPix];
+#pragma unroll
+  for (int i = 0; i < kPix; ++i) {
+    T[i] = 1.f;
+    c0[i] = c1[i] = c2[i] = 0.f;
+    last[i] = 0;
+  }
+  unsigned alive = tp.inside;
+  for (uint32_t base = r.x; base < r.y; base += kBatch) {
+    if (__syncthreads_count(alive != 0) == 0) break;
     const uint32_t i = base + threadIdx.x;
     if (i < r.y) {
       const Staged s = stage(gauss, keys[i] & gmask, n_gauss);
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
-      s_c[threadIdx.x] = make_float2(s.c.x, s.c.y);
+      s_c[threadIdx.x] = s.c;
     }
     __syncthreads();
-    if (!done) {
-      const int n = (int)min((uint32_t)kThreads, r.y - base);
-      for (int j = 0; j < n; ++j) {
-        const float4 a = s_a[j], b = s_b[j];
-        float dx, dy, t1, t2;
-        const float al = fminf(kAlphaMax, ex2_approx(log2_alpha(a, b, px, py, dx, dy, t1, t2)));
+    const int n = (int)min((uint32_t)kBatch, r.y - base);
+    for (int j = 0; j < n && alive; ++j) {
+      const float4 a = s_a[j], b = s_b[j];
+      const float dy = __fsub_rn(tp.py, a.y);
+      const float b1dy = __fmul_rn(a.w, dy), b2dy = __fmul_rn(b.y, dy);
+#pragma unroll
+      for (int q = 0; q < kPix; ++q) {
+        if (!(alive & (1u << q))) continue;
+        float t1, t2;
+        const float dx = __fsub_rn(tp.px[q], a.x);
+        const float al = fminf(kAlphaMax, ex2_approx(pixel_log2_alpha(a, b, dx, b1dy, b2dy, t1, t2)));
         if (kStats) ++n_eval;
         if (al < kAlphaMin) continue;
-        const float Tn = T * (1.f - al);
+        const float Tn = T[q] * (1.f - al);
         if (Tn < kTMin) {
-          done = true;
-          break;
+          alive &= ~(1u << q);
+          continue;
         }
-        const float w = al * T;
+        const float w = al * T[q];
         const float2 gb = s_c[j];
-        c0 = __fmaf_rn(w, b.w, c0);
-        c1 = __fmaf_rn(w, gb.x, c1);
-        c2 = __fmaf_rn(w, gb.y, c2);
-        T = Tn;
-        last = base - r.x + (uint32_t)j + 1;
+        c0[q] = __fmaf_rn(w, b.w, c0[q]);
+        c1[q] = __fmaf_rn(w, gb.x, c1[q]);
+        c2[q] = __fmaf_rn(w, gb.y, c2[q]);
+        T[q] = Tn;
+        last[q] = base - r.x + (uint32_t)j + 1;
         if (kStats) ++n_blend;
       }
     }
@@ -145,35 +182,52 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const float *__res
     if (threadIdx.x == 0) {
       atomicAdd(&stats[0], s_st[0]);
       atomicAdd(&stats[1], s_st[1]);
-      atomicAdd(&stats[2], (unsigned long long)(r.y - r.x) * kThreads);
+      atomicAdd(&stats[2], (unsigned long long)(r.y - r.x) * (kTile * kTile));
     }
   }
-  if (inside) {
-    const size_t p = (size_t)y * W + x, plane = (size_t)W * H;
-    img[p] = __fmaf_rn(T, bg.x, c0);
-    img[plane + p] = __fmaf_rn(T, bg.y, c1);
-    img[2 * plane + p] = __fmaf_rn(T, bg.z, c2);
-    T_out[p] = T;
-    nc_out[p] = last;
+  const size_t plane = (size_t)W * H;
+#pragma unroll
+  for (int q = 0; q < kPix; ++q) {
+    if (!(tp.inside & (1u << q))) continue;
+    const size_t p = (size_t)tp.y * W + tp.x0 + q;
+    img[p] = __fmaf_rn(T[q], bg.x, c0[q]);
+    img[plane + p] = __fmaf_rn(T[q], bg.y, c1[q]);
+    img[2 * plane + p] = __fmaf_rn(T[q], bg.z, c2[q]);
+    T_out[p] = T[q];
+    nc_out[p] = last[q];
   }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum 16 values over the warp, scattered: lane L returns the total of value
+// L >> 1 (lanes 2i and 2i+1 both hold total i).  16 shuffles instead of the
+// 80 of 16 butterfly all-reduces.
+__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int stage = 0, half = 8, off = 16; stage < 4; ++stage, half >>= 1, off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const float send = hi ? v[k] : v[k + half];
+      const float keep = hi ? v[k + half] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
+
+// Number of per-Gaussian sums the backward accumulates (see render_bwd_kernel).
+constexpr int kSums = 10;
 
 // Reverse walk.  With S the colour behind Gaussian j as seen through it,
 // S <- alpha_j c_j + (1 - alpha_j) S (starting from bg behind the last
 // blended Gaussian), the colour derivative is
 //     dC/dalpha_j = T_j (c_j - S),
 // which keeps the (1 - alpha_j)^-1 of the recovered transmittance out of the
-// gradient.  Per Gaussian and pixel the walk accumulates
-//   q1 = dp t1, q2 = dp t2 (dp = dL/dlog2(alpha)), q1 dx, q1 dy, q2 dx,
-//   q2 dy, dp and w g (w = alpha T),
-// and the chain rule through the staging turns their tile sums into
-// d/d(mx, my, ux, uy, isx, isy, o, r, g, b).
+// gradient.  Per Gaussian the walk accumulates, over its tile's pixels,
+//   [0] sum q1  [1] sum q2  [2] sum q1 dx  [3] sum q1 dy  [4] sum q2 dx
+//   [5] sum q2 dy  [6] sum dp  [7..9] sum w g
+// with dp = dL/dlog2(alpha), q1 = dp t1, q2 = dp t2, w = alpha T, g = dL/dC;
+// grads_from_sums turns them into d/d(record) afterwards.
 __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__restrict__ gauss,
                                                               const uint32_t *__restrict__ keys,
                                                               const uint2 *__restrict__ ranges, int W, int H,
@@ -181,39 +235,43 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__res
                                                               float3 bg, const float *__restrict__ T_final,
                                                               const uint32_t *__restrict__ n_contrib,
                                                               const float *__restrict__ dimg,
-                                                              float *__restrict__ dgauss) {
-  __shared__ float4 s_a[kThreads];
-  __shared__ float4 s_b[kThreads];
-  __shared__ float4 s_c[kThreads];
-  __shared__ float4 s_raw[kThreads];
-  __shared__ uint32_t s_g[kThreads];
+                                                              float *__restrict__ sums) {
+  __shared__ float4 s_a[kBatch];
+  __shared__ float4 s_b[kBatch];
+  __shared__ float2 s_c[kBatch];
+  __shared__ uint32_t s_g[kBatch];
   __shared__ uint32_t s_max_last;
   const int tile = blockIdx.x;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const int x = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int y = ty * kTile + threadIdx.x / kTile;
-  const bool inside = x < W && y < H;
-  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const TilePixels tp = tile_pixels(tile, tiles_x, W, H);
   const uint2 r = ranges[tile];
   const int lane = threadIdx.x & 31;
-  float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  uint32_t last = 0;
+  float T[kPix], g0[kPix], g1[kPix], g2[kPix], gS[kPix];
+  uint32_t last[kPix];
   if (threadIdx.x == 0) s_max_last = 0;
   __syncthreads();
-  if (inside) {
-    const size_t p = (size_t)y * W + x, plane = (size_t)W * H;
-    T = T_final[p];
-    last = n_contrib[p];
-    g0 = dimg[p];
-    g1 = dimg[plane + p];
-    g2 = dimg[2 * plane + p];
-    atomicMax(&s_max_last, last);
+  uint32_t my_max = 0;
+  const size_t plane = (size_t)W * H;
+#pragma unroll
+  for (int q = 0; q < kPix; ++q) {
+    T[q] = 1.f;
+    g0[q] = g1[q] = g2[q] = 0.f;
+    last[q] = 0;
+    if (tp.inside & (1u << q)) {
+      const size_t p = (size_t)tp.y * W + tp.x0 + q;
+      T[q] = T_final[p];
+      last[q] = n_contrib[p];
+      g0[q] = dimg[p];
+      g1[q] = dimg[plane + p];
+      g2[q] = dimg[2 * plane + p];
+      my_max = max(my_max, last[q]);
+    }
+    gS[q] = g0[q] * bg.x + g1[q] * bg.y + g2[q] * bg.z;  // g . S, S = bg behind the last blended Gaussian
   }
-  float gS = g0 * bg.x + g1 * bg.y + g2 * bg.z;  // g . S, S = bg behind the last blended Gaussian
+  atomicMax(&s_max_last, my_max);
   __syncthreads();
   const uint32_t max_last = min(s_max_last, r.y - r.x);
   for (uint32_t end = max_last; end > 0;) {
-    const uint32_t start = end > (uint32_t)kThreads ? end - kThreads : 0u;
+    const uint32_t start = end > (uint32_t)kBatch ? end - kBatch : 0u;
     __syncthreads();
     const uint32_t i = start + threadIdx.x;
     if (i < end) {
@@ -222,73 +280,82 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__res
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
-      s_raw[threadIdx.x] = s.raw;
       s_g[threadIdx.x] = g;
     }
     __syncthreads();
     for (int j = (int)(end - start) - 1; j >= 0; --j) {
       const uint32_t pos = start + (uint32_t)j;
-      float v[10];
+      const float4 a = s_a[j], b = s_b[j];
+      const float2 gb = s_c[j];
+      const float dy = __fsub_rn(tp.py, a.y);
+      const float b1dy = __fmul_rn(a.w, dy), b2dy = __fmul_rn(b.y, dy);
+      float v[16];
 #pragma unroll
-      for (int q = 0; q < 10; ++q) v[q] = 0.f;
+      for (int q = 0; q < 16; ++q) v[q] = 0.f;
       bool contrib = false;
-      if (pos < last) {
-        const float4 a = s_a[j], b = s_b[j];
-        float dx, dy, t1, t2;
-        const float raw = ex2_approx(log2_alpha(a, b, px, py, dx, dy, t1, t2));
+#pragma unroll
+      for (int q = 0; q < kPix; ++q) {
+        if (pos >= last[q]) continue;
+        float t1, t2;
+        const float dx = __fsub_rn(tp.px[q], a.x);
+        const float raw = ex2_approx(pixel_log2_alpha(a, b, dx, b1dy, b2dy, t1, t2));
         const float al = fminf(kAlphaMax, raw);
-        if (al >= kAlphaMin) {
-          contrib = true;
-          const float4 c = s_c[j];
-          const float one_m = 1.f - al;
-          T = __fdividef(T, one_m);             // T before this Gaussian
-          const float w = al * T;
-          const float gc = g0 * b.w + g1 * c.x + g2 * c.y;
-          const float dal = T * (gc - gS);      // dL/dalpha
-          gS = __fmaf_rn(al, gc, one_m * gS);
-          v[7] = w * g0;
-          v[8] = w * g1;
-          v[9] = w * g2;
-          if (raw <= kAlphaMax) {
-            const float dp = dal * al * kLn2;   // dL/dlog2(alpha)
-            const float q1 = dp * t1, q2 = dp * t2;
-            v[0] = q1;
-            v[1] = q2;
-            v[2] = q1 * dx;
-            v[3] = q1 * dy;
-            v[4] = q2 * dx;
-            v[5] = q2 * dy;
-            v[6] = dp;
-          }
+        if (al < kAlphaMin) continue;
+        contrib = true;
+        const float one_m = 1.f - al;
+        T[q] = __fdividef(T[q], one_m);          // T before this Gaussian
+        const float w = al * T[q];
+        const float gc = g0[q] * b.w + g1[q] * gb.x + g2[q] * gb.y;
+        const float dal = T[q] * (gc - gS[q]);   // dL/dalpha
+        gS[q] = __fmaf_rn(al, gc, one_m * gS[q]);
+        v[7] = __fmaf_rn(w, g0[q], v[7]);
+        v[8] = __fmaf_rn(w, g1[q], v[8]);
+        v[9] = __fmaf_rn(w, g2[q], v[9]);
+        if (raw <= kAlphaMax) {
+          const float dp = dal * al * kLn2;      // dL/dlog2(alpha)
+          const float q1 = dp * t1, q2 = dp * t2;
+          v[0] += q1;
+          v[1] += q2;
+          v[2] = __fmaf_rn(q1, dx, v[2]);
+          v[3] = __fmaf_rn(q1, dy, v[3]);
+          v[4] = __fmaf_rn(q2, dx, v[4]);
+          v[5] = __fmaf_rn(q2, dy, v[5]);
+          v[6] += dp;
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int q = 0; q < 10; ++q) v[q] = warp_sum(v[q]);
-        if (lane < 10) {
-          const float4 a = s_a[j], b = s_b[j], u = s_raw[j];
-          const float o = s_c[j].z;
-          // dL/dA1 = -2 sum q1 dx, dL/dB1 = -2 sum q1 dy, dL/dA2 = -2 sum q2 dx, dL/dB2 = -2 sum q2 dy
-          const float dA1 = -2.f * v[2], dB1 = -2.f * v[3], dA2 = -2.f * v[4], dB2 = -2.f * v[5];
-          float val;
-          switch (lane) {
-            case 0: val = 2.f * (a.z * v[0] + b.x * v[1]); break;                // mx
-            case 1: val = 2.f * (a.w * v[0] + b.y * v[1]); break;                // my
-            case 2: val = kKappa * (u.z * dA1 + u.w * dB2); break;               // ux
-            case 3: val = kKappa * (u.z * dB1 - u.w * dA2); break;               // uy
-            case 4: val = kKappa * (u.x * dA1 + u.y * dB1); break;               // isx
-            case 5: val = kKappa * (u.x * dB2 - u.y * dA2); break;               // isy
-            case 6: val = o > 0.f ? v[6] / (o * kLn2) : 0.f; break;              // o
-            case 7: val = v[7]; break;
-            case 8: val = v[8]; break;
-            default: val = v[9]; break;
-          }
-          if (val != 0.f && s_g[j] < n_gauss) atomicAdd(dgauss + (size_t)s_g[j] * BS_DGAUSS_FLOATS + lane, val);
-        }
+        const float tot = warp_reduce_scatter16(v, lane);
+        const int k = lane >> 1;
+        const uint32_t g = s_g[j];
+        if ((lane & 1) == 0 && k < kSums && tot != 0.f && g < n_gauss)
+          atomicAdd(sums + (size_t)g * BS_DGAUSS_FLOATS + k, tot);
       }
     }
     end = start;
   }
+}
+
+// The chain rule from the tile sums of render_bwd_kernel to the record:
+//   d/dmx = 2 (A1 s0 + A2 s1),  d/dmy = 2 (B1 s0 + B2 s1),
+//   d/dA1 = -2 s2, d/dB1 = -2 s3, d/dA2 = -2 s4, d/dB2 = -2 s5,
+//   A1 = k isx ux, B1 = k isx uy, A2 = -k isy uy, B2 = k isy ux,
+//   d/do = s6 / (o ln 2),  d/dcolour = s7..s9.   In place, one thread per Gaussian.
+__global__ void grads_from_sums_kernel(const float *__restrict__ gauss, float *__restrict__ dgauss, int64_t n) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const float4 *rec = reinterpret_cast<const float4 *>(gauss + g * BS_GAUSS_FLOATS);
+  const float4 r0 = rec[0], r1 = rec[1];
+  float4 *d = reinterpret_cast<float4 *>(dgauss + g * BS_DGAUSS_FLOATS);
+  const float4 s0 = d[0], s1 = d[1], s2 = d[2];
+  const float ux = r0.z, uy = r0.w, isx = r1.x, isy = r1.y, o = r1.z;
+  float A1, B1, A2, B2;
+  scaled_axes(ux, uy, isx, isy, A1, B1, A2, B2);
+  const float dA1 = -2.f * s0.z, dB1 = -2.f * s0.w, dA2 = -2.f * s1.x, dB2 = -2.f * s1.y;
+  d[0] = make_float4(2.f * (A1 * s0.x + A2 * s0.y), 2.f * (B1 * s0.x + B2 * s0.y),
+                     kKappa * (isx * dA1 + isy * dB2), kKappa * (isx * dB1 - isy * dA2));
+  d[1] = make_float4(kKappa * (ux * dA1 + uy * dB1), kKappa * (ux * dB2 - uy * dA2),
+                     o > 0.f ? s1.z / (o * kLn2) : 0.f, s1.w);
+  d[2] = make_float4(s2.x, s2.y, 0.f, 0.f);
 }
 
 __global__ void l2_kernel(const float *__restrict__ img, const float *__restrict__ target, int64_t n,
@@ -348,6 +415,8 @@ bs_status launch_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas
       gauss, keys, reinterpret_cast<const uint2 *>(ranges), cv.width, cv.height, tiles_x, gmask,
       (uint32_t)n_gauss, make_float3(cv.bg[0], cv.bg[1], cv.bg[2]), T_final, n_contrib, dL_dimg, dgauss);
   BS_LAUNCHED("render_bwd_kernel");
+  grads_from_sums_kernel<<<(unsigned)div_up64(n_gauss, 256), 256, 0, s>>>(gauss, dgauss, n_gauss);
+  BS_LAUNCHED("grads_from_sums_kernel");
   return BS_OK;
 }
 

@@ -136,8 +136,8 @@ def test_render_fwd_matches_oracle(bs, name):
     tab, _, _ = oracle_table(case)
     rec = table_to_f32(tab)
     gauss, b, img, T, nc = _render(bs, case, rec)
-    # flag decisions within 4e-6 (alpha) / 1e-4 (transmittance) of a threshold
-    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg, margin=4e-6, margin_T=1e-4)
+    # flag decisions within 4e-6 (alpha) / 2e-5 (transmittance) of a threshold
+    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg, margin=4e-6, margin_T=2e-5)
     ok = ~ref["flag"].numpy()
     err = np.abs(img.cpu().numpy().astype(np.float64) - ref["img"].numpy()).max(0)
     terr = np.abs(T.cpu().numpy() - ref["T"].numpy())
