@@ -79,15 +79,24 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
   return v;
 }
 
+// Per Gaussian: its pair count, its block-local exclusive offset, and its
+// rectangle packed as {tx0 | ty0 << 16, width | height << 16}.
 __global__ void __launch_bounds__(kCountThreads) count_kernel(const float *gauss, int64_t n_gauss, int W, int H,
                                                               int tile, uint32_t *local,
-                                                              unsigned long long *partial) {
+                                                              unsigned long long *partial, uint2 *rects) {
   __shared__ uint32_t s_warp[kCountThreads / 32];
   const int64_t g = (int64_t)blockIdx.x * kCountThreads + threadIdx.x;
   uint32_t cnt = 0;
   Rect r;
-  if (g < n_gauss && tile_rect(gauss, g, W, H, tile, &r))
-    cnt = (uint32_t)(r.tx1 - r.tx0 + 1) * (uint32_t)(r.ty1 - r.ty0 + 1);
+  if (g < n_gauss) {
+    uint2 packed = make_uint2(0u, 0u);
+    if (tile_rect(gauss, g, W, H, tile, &r)) {
+      const uint32_t w = (uint32_t)(r.tx1 - r.tx0 + 1), h = (uint32_t)(r.ty1 - r.ty0 + 1);
+      cnt = w * h;
+      packed = make_uint2((uint32_t)r.tx0 | ((uint32_t)r.ty0 << 16), w | (h << 16));
+    }
+    rects[g] = packed;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t incl = warp_incl_scan(cnt, lane);
   if (lane == 31) s_warp[warp] = incl;
@@ -125,7 +134,10 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(unsigned long long 
     if (threadIdx.x == 0) carry += s[1023];
     __syncthreads();
   }
-  if (threadIdx.x == 0) hdr->n_pairs = carry;
+  if (threadIdx.x == 0) {
+    hdr->n_pairs = carry;
+    partial[n] = carry;  // sentinel for the owner search
+  }
 }
 
 // ---- zero the per-call sort state and the tile ranges ----
@@ -137,52 +149,65 @@ __global__ void zero_kernel(uint32_t *a, size_t na, uint32_t *b, size_t nb) {
   }
 }
 
-// ---- emit keys (one warp writes one Gaussian's run at a time) + digit histograms ----
-__global__ void __launch_bounds__(kCountThreads) emit_kernel(const float *gauss, int64_t n_gauss, int W, int H,
-                                                             int tile, int tiles_x, int gbits,
-                                                             const uint32_t *local,
-                                                             const unsigned long long *partial, uint32_t *keys,
-                                                             int passes, int digit_bits, uint32_t *hist) {
+// ---- emit keys, one per thread, + digit histograms ----
+// The owner of pair i is found by two binary searches (CTA offsets, then
+// offsets inside the CTA), so every thread writes one key whatever the size
+// of the rectangles: a Gaussian covering thousands of tiles is spread over
+// many warps instead of serialising one.
+__device__ __forceinline__ uint32_t pair_owner(const unsigned long long *__restrict__ partial, int64_t nb,
+                                               const uint32_t *__restrict__ local, int64_t n_gauss, uint32_t i,
+                                               uint32_t *l_out) {
+  int64_t lo = 0, hi = nb;  // first block whose offset exceeds i
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (partial[mid] <= i) lo = mid + 1;
+    else hi = mid;
+  }
+  const int64_t b = lo - 1;
+  const uint32_t i2 = i - (uint32_t)partial[b];
+  lo = b * kCountThreads;
+  hi = min(lo + kCountThreads, n_gauss);
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (local[mid] <= i2) lo = mid + 1;
+    else hi = mid;
+  }
+  const int64_t g = lo - 1;
+  *l_out = i2 - local[g];
+  return (uint32_t)g;
+}
+
+__global__ void __launch_bounds__(kCountThreads) emit_kernel(const uint32_t *__restrict__ local,
+                                                             const unsigned long long *__restrict__ partial,
+                                                             int64_t nb, const uint2 *__restrict__ rects,
+                                                             int64_t n_gauss, const Hdr *hdr, int tiles_x, int gbits,
+                                                             uint32_t *__restrict__ keys, int passes,
+                                                             int digit_bits, uint32_t *hist) {
   __shared__ uint32_t s_hist[kMaxPasses * 256];
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) s_hist[i] = 0u;
   __syncthreads();
-  const int64_t g = (int64_t)blockIdx.x * kCountThreads + threadIdx.x;
+  const uint32_t n = (uint32_t)hdr->n_pairs;
   const int lane = threadIdx.x & 31;
-  Rect r = {0, -1, 0, -1};
-  bool ok = false;
-  unsigned long long off = 0;
-  if (g < n_gauss) {
-    ok = tile_rect(gauss, g, W, H, tile, &r);
-    off = partial[blockIdx.x] + local[g];
-  }
   const uint32_t dmask = (1u << digit_bits) - 1;
-  const int64_t g_warp = g - lane;
-  for (int j = 0; j < 32; ++j) {
-    const int tx0 = __shfl_sync(0xffffffffu, r.tx0, j);
-    const int tx1 = __shfl_sync(0xffffffffu, r.tx1, j);
-    const int ty0 = __shfl_sync(0xffffffffu, r.ty0, j);
-    const int ty1 = __shfl_sync(0xffffffffu, r.ty1, j);
-    const bool okj = __shfl_sync(0xffffffffu, ok, j);
-    const unsigned long long offj = __shfl_sync(0xffffffffu, off, j);
-    if (!okj) continue;
-    const uint32_t w = (uint32_t)(tx1 - tx0 + 1);
-    const uint32_t cnt = w * (uint32_t)(ty1 - ty0 + 1);
-    const uint32_t gid = (uint32_t)(g_warp + j);
-    for (uint32_t base = 0; base < cnt; base += 32) {
-      const uint32_t i = base + lane;
-      const bool valid = i < cnt;
-      uint32_t tid = 0;
-      if (valid) {
-        const uint32_t ry = i / w, rx = i - ry * w;
-        tid = (uint32_t)(ty0 + (int)ry) * (uint32_t)tiles_x + (uint32_t)(tx0 + (int)rx);
-        keys[offj + i] = (tid << gbits) | gid;
-      }
-      const unsigned active = __ballot_sync(0xffffffffu, valid);
-      for (int p = 0; p < passes; ++p) {
-        const uint32_t d = (tid >> (p * digit_bits)) & dmask;
-        const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu) & active;
-        if (valid && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&s_hist[p * 256 + d], __popc(peers));
-      }
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const uint32_t i = base + threadIdx.x;
+    const bool valid = i < n;
+    uint32_t tid = 0;
+    if (valid) {
+      uint32_t l;
+      const uint32_t g = pair_owner(partial, nb, local, n_gauss, i, &l);
+      const uint2 rc = rects[g];
+      const uint32_t w = rc.y & 0xffffu;
+      const uint32_t ry = l / w, rx = l - ry * w;
+      tid = ((rc.x >> 16) + ry) * (uint32_t)tiles_x + (rc.x & 0xffffu) + rx;
+      keys[i] = (tid << gbits) | g;
+    }
+    const unsigned active = __ballot_sync(0xffffffffu, valid);
+    for (int p = 0; p < passes; ++p) {
+      const uint32_t d = (tid >> (p * digit_bits)) & dmask;
+      const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu) & active;
+      if (valid && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&s_hist[p * 256 + d], __popc(peers));
     }
   }
   __syncthreads();
@@ -371,6 +396,7 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
   p->off_hdr = o;        o = align256(o + sizeof(Hdr));
   p->off_local = o;      o = align256(o + sizeof(uint32_t) * (size_t)(n_gauss > 0 ? n_gauss : 1));
   p->off_partial = o;    o = align256(o + sizeof(unsigned long long) * (size_t)(p->count_blocks + 1));
+  p->off_rects = o;      o = align256(o + sizeof(uint2) * (size_t)(n_gauss > 0 ? n_gauss : 1));
   p->off_keys_tmp = o;   o = align256(o + sizeof(uint32_t) * (size_t)(capacity > 0 ? capacity : 1));
   p->off_hist = o;       o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
   p->off_counter = o;    o = align256(o + sizeof(uint32_t) * kMaxPasses);
@@ -385,6 +411,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   Hdr *hdr = reinterpret_cast<Hdr *>(base + p.off_hdr);
   uint32_t *local = reinterpret_cast<uint32_t *>(base + p.off_local);
   auto *partial = reinterpret_cast<unsigned long long *>(base + p.off_partial);
+  uint2 *rects = reinterpret_cast<uint2 *>(base + p.off_rects);
   uint32_t *keys_tmp = reinterpret_cast<uint32_t *>(base + p.off_keys_tmp);
   uint32_t *hist = reinterpret_cast<uint32_t *>(base + p.off_hist);
   uint32_t *counter = reinterpret_cast<uint32_t *>(base + p.off_counter);
@@ -393,7 +420,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   BS_CUDA(cudaMemsetAsync(hdr, 0, sizeof(Hdr), s));
   if (p.n_gauss > 0) {
     count_kernel<<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(gauss, p.n_gauss, cv.width, cv.height,
-                                                                    cv.tile, local, partial);
+                                                                    cv.tile, local, partial, rects);
     BS_LAUNCHED("count_kernel");
     scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, hdr);
     BS_LAUNCHED("scan_partials_kernel");
@@ -421,9 +448,11 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   // emit into the buffer that makes the last pass land in tile_keys
   uint32_t *bufs[2] = {tile_keys, keys_tmp};
   uint32_t *src = (p.passes % 2 == 0) ? tile_keys : keys_tmp;
-  emit_kernel<<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(gauss, p.n_gauss, cv.width, cv.height, cv.tile,
-                                                                 p.tiles_x, p.gbits, local, partial, src,
-                                                                 p.passes, p.digit_bits, hist);
+  {
+    const int blocks = (int)std::min<int64_t>(div_up64(P, kCountThreads), 152 * 16);
+    emit_kernel<<<blocks, kCountThreads, 0, s>>>(local, partial, p.count_blocks, rects, p.n_gauss, hdr, p.tiles_x,
+                                                 p.gbits, src, p.passes, p.digit_bits, hist);
+  }
   BS_LAUNCHED("emit_kernel");
   for (int pass = 0; pass < p.passes; ++pass) {
     uint32_t *dst = (src == bufs[0]) ? bufs[1] : bufs[0];

@@ -21,7 +21,7 @@
 namespace bs {
 namespace {
 
-constexpr int kCurveThreads = 128;
+constexpr int kCurveThreads = 64;
 
 struct Cfg {
   int g_open, rows, kc;
@@ -33,14 +33,6 @@ __device__ __forceinline__ void bern3(double t, double w[4]) {
   w[0] = u * u * u;
   w[1] = 3.0 * u * u * t;
   w[2] = 3.0 * u * t * t;
-  w[3] = t * t * t;
-}
-
-__device__ __forceinline__ void bern3f(float t, float w[4]) {
-  const float u = 1.0f - t;
-  w[0] = u * u * u;
-  w[1] = 3.0f * u * u * t;
-  w[2] = 3.0f * u * t * t;
   w[3] = t * t * t;
 }
 
@@ -68,17 +60,29 @@ __device__ __forceinline__ const float *curve_ctrl(const bs_curves &c, int curve
   return curve < c.n_open ? c.open_ctrl + (size_t)curve * 20 : c.closed_ctrl + (size_t)(curve - c.n_open) * 24;
 }
 
+// Per-CTA tables shared by every sample of the curve: the Bernstein weights
+// of each sample index k (double [K][4]) and, for closed curves, the row
+// weights tau_r (double [rows]).  A closed curve's rows reuse the same K
+// weights, and the divisions and cosines run once per index, not per sample.
+__device__ void build_tables(const Cfg &cfg, bool closed, double *Wt, double *taut) {
+  const int K = closed ? cfg.kc : cfg.g_open, S = closed ? 2 : 3;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) bern3(chain_t(k, K, S, chain_seg(k, K, S)), Wt + 4 * k);
+  if (closed)
+    for (int r = threadIdx.x; r < cfg.rows; r += blockDim.x) taut[r] = closed_tau(r, cfg.rows);
+}
+
 // Sample points X of a curve relative to its first control point, into
-// shared memory; returns the number of samples.
-__device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, double2 *X) {
+// shared memory (after build_tables and a barrier); returns the number of
+// samples.
+__device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, const double *Wt, const double *taut,
+                            double2 *X) {
   const float *P = curve_ctrl(c, curve);
   const double ox = P[0], oy = P[1];
   if (curve < c.n_open) {
     const int K = cfg.g_open;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
       const int s = chain_seg(k, K, 3);
-      double w[4];
-      bern3(chain_t(k, K, 3, s), w);
+      const double *w = Wt + 4 * k;
       double ax = 0.0, ay = 0.0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -93,10 +97,9 @@ __device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, doubl
   const int K = cfg.kc, R2 = cfg.rows, n = R2 * K;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int r = idx / K, k = idx - r * K;
-    const double tau = closed_tau(r, R2);
+    const double tau = taut[r];
     const int s = chain_seg(k, K, 2);
-    double w[4];
-    bern3(chain_t(k, K, 2, s), w);
+    const double *w = Wt + 4 * k;
     double ax = 0.0, ay = 0.0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -180,11 +183,37 @@ __device__ __forceinline__ CurveAttr curve_attr(const bs_curves &c, int curve, i
   return a;
 }
 
-__global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss) {
-  extern __shared__ double2 X[];  // [max samples per curve]
+// Dynamic shared memory of the sampling kernels: n_max double2 sample points,
+// [bwd: n_max float2 gradients,] k_max x 4 double weights, rows double tau.
+struct CurveSmem {
+  double2 *X;
+  float2 *dX;
+  double *Wt, *taut;
+};
+
+__device__ __forceinline__ CurveSmem carve(void *base, int n_max, int k_max, bool with_grad) {
+  CurveSmem m;
+  char *p = static_cast<char *>(base);
+  m.X = reinterpret_cast<double2 *>(p);
+  p += sizeof(double2) * n_max;
+  m.Wt = reinterpret_cast<double *>(p);
+  p += sizeof(double) * 4 * k_max;
+  m.taut = reinterpret_cast<double *>(p);
+  p += sizeof(double) * 64 * ((n_max + 63) / 64);  // rows <= n_max
+  m.dX = with_grad ? reinterpret_cast<float2 *>(p) : nullptr;
+  return m;
+}
+
+__global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss, int n_max,
+                                                                   int k_max) {
+  extern __shared__ double2 smem_fwd[];
+  const CurveSmem m = carve(smem_fwd, n_max, k_max, false);
+  double2 *X = m.X;
   const int curve = blockIdx.x;
   const bool closed = curve >= c.n_open;
-  const int n = eval_samples(c, cfg, curve, X);
+  build_tables(cfg, closed, m.Wt, m.taut);
+  __syncthreads();
+  const int n = eval_samples(c, cfg, curve, m.Wt, m.taut, X);
   __syncthreads();
   const int K = closed ? cfg.kc : cfg.g_open;
   const uint32_t first = c.draw_first[curve];
@@ -223,16 +252,20 @@ __device__ __forceinline__ void sadd2(float2 *p, float x, float y) {
 }
 
 __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
-                                                                   bs_curves_grad g, int n_max) {
-  extern __shared__ double2 X[];                       // [n_max] sample points
-  float2 *dX = reinterpret_cast<float2 *>(X + n_max);  // [n_max] their gradients
+                                                                   bs_curves_grad g, int n_max, int k_max) {
+  extern __shared__ double2 smem_bwd[];
+  const CurveSmem m = carve(smem_bwd, n_max, k_max, true);
+  double2 *X = m.X;
+  float2 *dX = m.dX;
   __shared__ float2 dP[12];
   __shared__ float sAttr[8];  // opac[3] (open) or opac (closed), colour[3], width
   const int curve = blockIdx.x;
   const bool closed = curve >= c.n_open;
   for (int i = threadIdx.x; i < 12; i += blockDim.x) dP[i] = make_float2(0.f, 0.f);
   if (threadIdx.x < 8) sAttr[threadIdx.x] = 0.f;
-  const int n = eval_samples(c, cfg, curve, X);
+  build_tables(cfg, closed, m.Wt, m.taut);
+  __syncthreads();
+  const int n = eval_samples(c, cfg, curve, m.Wt, m.taut, X);
   for (int i = threadIdx.x; i < n; i += blockDim.x) dX[i] = make_float2(0.f, 0.f);
   __syncthreads();
   const int K = closed ? cfg.kc : cfg.g_open;
@@ -303,16 +336,19 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
     const float2 d = dX[idx];
     if (!closed) {
       const int s = chain_seg(idx, K, 3);
-      float w[4];
-      bern3f((float)chain_t(idx, K, 3, s), w);
+      const double *wd = m.Wt + 4 * idx;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) sadd2(&dP[3 * s + i], w[i] * d.x, w[i] * d.y);
+      for (int i = 0; i < 4; ++i) {
+        const float w = (float)wd[i];
+        sadd2(&dP[3 * s + i], w * d.x, w * d.y);
+      }
     } else {
       const int r = idx / K, k = idx - r * K;
-      const float tau = (float)closed_tau(r, cfg.rows);
+      const float tau = (float)m.taut[r];
       const int s = chain_seg(k, K, 2);
       float w[4];
-      bern3f((float)chain_t(k, K, 2, s), w);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) w[i] = (float)m.Wt[4 * k + i];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int j = 3 * s + i;
@@ -377,32 +413,40 @@ __device__ __forceinline__ uint32_t key_order(float k) {
 }
 
 constexpr int kOrderThreads = 256;
+constexpr int kOrderChunk = 1024;  // keys compared per CTA
 
-__global__ void __launch_bounds__(kOrderThreads) curve_order_kernel(bs_curves c, int g_open, int g_closed,
-                                                                   uint32_t *rank, uint32_t *first) {
-  __shared__ uint32_t sk[kOrderThreads];
+// Rank by counting: rank_i = #{j : key_j < key_i or (key_j == key_i, j < i)}.
+// CTA (x, y) compares its 256 curves against the keys of chunk y and adds its
+// counts (rank, and how many of the preceding curves are open) atomically.
+__global__ void __launch_bounds__(kOrderThreads) curve_order_count_kernel(bs_curves c, uint32_t *rank,
+                                                                         uint32_t *open_before) {
+  __shared__ uint32_t sk[kOrderChunk];
   const int n = c.n_open + c.n_closed;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int base = blockIdx.y * kOrderChunk;
+  const int m = min(kOrderChunk, n - base);
+  for (int q = threadIdx.x; q < m; q += blockDim.x) sk[q] = key_order(area_key(c, base + q));
   const uint32_t mine = i < n ? key_order(area_key(c, i)) : 0u;
-  uint32_t before = 0, open_before = 0;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int j = base + threadIdx.x;
-    sk[threadIdx.x] = j < n ? key_order(area_key(c, j)) : 0u;
-    __syncthreads();
-    const int m = min((int)blockDim.x, n - base);
-    for (int q = 0; q < m; ++q) {
-      const uint32_t kq = sk[q];
-      const int jq = base + q;
-      const bool prec = kq < mine || (kq == mine && jq < i);
-      before += prec;
-      open_before += prec && jq < c.n_open;
-    }
-    __syncthreads();
+  __syncthreads();
+  if (i >= n) return;
+  uint32_t before = 0, ob = 0;
+  const int open_end = c.n_open - base;  // chunk entries q < open_end are open curves
+  for (int q = 0; q < m; ++q) {
+    const uint32_t kq = sk[q];
+    const bool prec = kq < mine || (kq == mine && base + q < i);
+    before += prec;
+    ob += prec && q < open_end;
   }
-  if (i < n) {
-    rank[i] = before;
-    first[i] = open_before * (uint32_t)g_open + (before - open_before) * (uint32_t)g_closed;
-  }
+  if (before) atomicAdd(&rank[i], before);
+  if (ob) atomicAdd(&open_before[i], ob);
+}
+
+// first_i = g_open * (open curves before i) + g_closed * (closed curves before i)
+__global__ void curve_order_first_kernel(int n, int g_open, int g_closed, const uint32_t *rank, uint32_t *first) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t ob = first[i];
+  first[i] = ob * (uint32_t)g_open + (rank[i] - ob) * (uint32_t)g_closed;
 }
 
 Cfg to_cfg(const bs_sample_cfg &s) { return Cfg{s.g_open, s.rows_closed, s.k_closed, s.rho, s.cov_eps}; }
@@ -414,24 +458,41 @@ int max_samples(const bs_curves &c, const bs_sample_cfg &cfg) {
   return m;
 }
 
+int max_k(const bs_curves &c, const bs_sample_cfg &cfg) {
+  int m = 0;
+  if (c.n_open > 0) m = cfg.g_open;
+  if (c.n_closed > 0) m = max(m, cfg.k_closed);
+  return m;
+}
+
+size_t curve_smem(int n_max, int k_max, bool with_grad) {
+  return sizeof(double2) * n_max + sizeof(double) * 4 * k_max + sizeof(double) * 64 * ((n_max + 63) / 64) +
+         (with_grad ? sizeof(float2) * n_max : 0);
+}
+
 }  // namespace
 
 bs_status launch_curve_order(const bs_curves &c, const bs_sample_cfg &cfg, uint32_t *rank, uint32_t *first,
                              cudaStream_t s) {
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
-  curve_order_kernel<<<div_up(n, kOrderThreads), kOrderThreads, 0, s>>>(c, cfg.g_open,
-                                                                        cfg.rows_closed * cfg.k_closed, rank, first);
-  BS_LAUNCHED("curve_order_kernel");
+  BS_CUDA(cudaMemsetAsync(rank, 0, sizeof(uint32_t) * n, s));
+  BS_CUDA(cudaMemsetAsync(first, 0, sizeof(uint32_t) * n, s));
+  const dim3 grid(div_up(n, kOrderThreads), div_up(n, kOrderChunk));
+  curve_order_count_kernel<<<grid, kOrderThreads, 0, s>>>(c, rank, first);
+  BS_LAUNCHED("curve_order_count_kernel");
+  curve_order_first_kernel<<<div_up(n, 256), 256, 0, s>>>(n, cfg.g_open, cfg.rows_closed * cfg.k_closed, rank, first);
+  BS_LAUNCHED("curve_order_first_kernel");
   return BS_OK;
 }
 
 bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float *gauss, cudaStream_t s) {
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
-  const size_t smem = (size_t)max_samples(c, cfg) * sizeof(double2);
+  const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
+  const size_t smem = curve_smem(n_max, k_max, false);
   BS_CUDA(cudaFuncSetAttribute(sample_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), gauss);
+  sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), gauss, n_max, k_max);
   BS_LAUNCHED("sample_fwd_kernel");
   return BS_OK;
 }
@@ -440,10 +501,10 @@ bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const 
                             const bs_curves_grad &g, cudaStream_t s) {
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
-  const int n_max = max_samples(c, cfg);
-  const size_t smem = (size_t)n_max * (sizeof(double2) + sizeof(float2));
+  const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
+  const size_t smem = curve_smem(n_max, k_max, true);
   BS_CUDA(cudaFuncSetAttribute(sample_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), dgauss, g, n_max);
+  sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), dgauss, g, n_max, k_max);
   BS_LAUNCHED("sample_bwd_kernel");
   return BS_OK;
 }

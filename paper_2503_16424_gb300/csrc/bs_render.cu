@@ -358,27 +358,40 @@ __global__ void grads_from_sums_kernel(const float *__restrict__ gauss, float *_
   d[2] = make_float4(s2.x, s2.y, 0.f, 0.f);
 }
 
+// L2 loss and its gradient, float4 at a time; per-thread float partial sums
+// (a few dozen terms each), combined in double.
 __global__ void l2_kernel(const float *__restrict__ img, const float *__restrict__ target, int64_t n,
                           float *__restrict__ dimg, double *loss) {
   __shared__ double s_sum[32];
-  double acc = 0.0;
+  float acc = 0.f;
   const float scale = (float)(2.0 / (double)n);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const double d = (double)img[i] - (double)target[i];   // exact
-    dimg[i] = scale * (float)d;
+  const int64_t n4 = n / 4;
+  const float4 *a4 = reinterpret_cast<const float4 *>(img);
+  const float4 *t4 = reinterpret_cast<const float4 *>(target);
+  float4 *d4 = reinterpret_cast<float4 *>(dimg);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const float4 a = a4[i], t = t4[i];
+    const float4 d = make_float4(a.x - t.x, a.y - t.y, a.z - t.z, a.w - t.w);
+    d4[i] = make_float4(scale * d.x, scale * d.y, scale * d.z, scale * d.w);
+    acc += d.x * d.x + d.y * d.y + d.z * d.z + d.w * d.w;
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float d = img[i] - target[i];
+    dimg[i] = scale * d;
     acc += d * d;
   }
+  double dacc = acc;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) s_sum[warp] = acc;
+  if (lane == 0) s_sum[warp] = dacc;
   __syncthreads();
   if (warp == 0) {
-    acc = lane < (int)(blockDim.x / 32) ? s_sum[lane] : 0.0;
+    dacc = lane < (int)(blockDim.x / 32) ? s_sum[lane] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) atomicAdd(loss, acc / (double)n);
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if (lane == 0) atomicAdd(loss, dacc / (double)n);
   }
 }
 
@@ -423,7 +436,11 @@ bs_status launch_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas
 bs_status launch_l2(const float *img, const float *target, int64_t n, float *dimg, double *loss, cudaStream_t s) {
   BS_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s));
   if (n == 0) return BS_OK;
-  const int blocks = (int)std::min<int64_t>(div_up64(n, 256 * 4), 152 * 8);
+  if (((uintptr_t)img | (uintptr_t)target | (uintptr_t)dimg) & 15) {
+    set_error("img, target and dL_dimg must be 16-byte aligned");
+    return BS_ERR_INVALID_ARG;
+  }
+  const int blocks = (int)std::min<int64_t>(div_up64(n, 256 * 4 * 4), 152 * 8);
   l2_kernel<<<blocks, 256, 0, s>>>(img, target, n, dimg, loss);
   BS_LAUNCHED("l2_kernel");
   return BS_OK;
