@@ -7,6 +7,12 @@
 // order).  A stable sort on the tile bits alone therefore orders the keys by
 // (tile, depth): ceil(tile_bits / 8) passes instead of one per key byte.
 //
+// Per-tile pair counts come from a 2D difference array: each Gaussian adds
+// +1/-1 at the four corners of its rectangle, and a row scan then a column
+// scan turn the array into the number of rectangles covering each tile.
+// Their exclusive scan over tile ids is the tile ranges, and their sums by
+// digit are the histograms the sort passes need.
+//
 // Sort pass (one launch per digit): every CTA takes the next partition of
 // 4096 keys from an atomic counter (so a partition's predecessors are always
 // resident), ranks its keys stably with warp match_any, publishes its digit
@@ -24,7 +30,10 @@
 namespace bs {
 namespace {
 
-constexpr int kCountThreads = 256;   // Gaussians per count/emit CTA
+constexpr int kCountThreads = 256;   // Gaussians per count CTA
+constexpr int kEmitThreads = 256;
+constexpr int kEmitItems = 8;        // keys per emit thread
+constexpr int kEmitTile = kEmitThreads * kEmitItems;
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
@@ -69,7 +78,6 @@ __device__ __forceinline__ bool tile_rect(const float *gauss, int64_t g, int W, 
   return true;
 }
 
-// ---- count + block-local exclusive scan ----
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -79,11 +87,18 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
   return v;
 }
 
-// Per Gaussian: its pair count, its block-local exclusive offset, and its
-// rectangle packed as {tx0 | ty0 << 16, width | height << 16}.
+__global__ void zero_kernel(uint32_t *a, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = 0u;
+}
+
+// Per Gaussian: its pair count, its block-local exclusive offset, its
+// rectangle packed as {tx0 | ty0 << 16, width | height << 16}, and the four
+// corner updates of the tile difference array (row stride tiles_x + 1).
 __global__ void __launch_bounds__(kCountThreads) count_kernel(const float *gauss, int64_t n_gauss, int W, int H,
-                                                              int tile, uint32_t *local,
-                                                              unsigned long long *partial, uint2 *rects) {
+                                                              int tile, int tiles_x, uint32_t *local,
+                                                              unsigned long long *partial, uint2 *rects,
+                                                              int *diff) {
   __shared__ uint32_t s_warp[kCountThreads / 32];
   const int64_t g = (int64_t)blockIdx.x * kCountThreads + threadIdx.x;
   uint32_t cnt = 0;
@@ -94,6 +109,11 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(const float *gauss
       const uint32_t w = (uint32_t)(r.tx1 - r.tx0 + 1), h = (uint32_t)(r.ty1 - r.ty0 + 1);
       cnt = w * h;
       packed = make_uint2((uint32_t)r.tx0 | ((uint32_t)r.ty0 << 16), w | (h << 16));
+      const int stride = tiles_x + 1;
+      atomicAdd(diff + r.ty0 * stride + r.tx0, 1);
+      atomicAdd(diff + r.ty0 * stride + r.tx1 + 1, -1);
+      atomicAdd(diff + (r.ty1 + 1) * stride + r.tx0, -1);
+      atomicAdd(diff + (r.ty1 + 1) * stride + r.tx1 + 1, 1);
     }
     rects[g] = packed;
   }
@@ -112,7 +132,8 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(const float *gauss
   if (threadIdx.x == kCountThreads - 1) partial[blockIdx.x] = warp_excl + incl;
 }
 
-// Exclusive scan of the per-CTA totals (one CTA); writes the pair count.
+// Exclusive scan of the per-CTA totals (one CTA); writes the pair count and
+// the sentinel partial[n] = P.
 __global__ void __launch_bounds__(1024) scan_partials_kernel(unsigned long long *partial, int64_t n, Hdr *hdr) {
   __shared__ unsigned long long s[1024];
   __shared__ unsigned long long carry;
@@ -136,28 +157,106 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(unsigned long long 
   }
   if (threadIdx.x == 0) {
     hdr->n_pairs = carry;
-    partial[n] = carry;  // sentinel for the owner search
+    partial[n] = carry;
   }
 }
 
-// ---- zero the per-call sort state and the tile ranges ----
-__global__ void zero_kernel(uint32_t *a, size_t na, uint32_t *b, size_t nb) {
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += stride) {
-    if (i < na) a[i] = 0u;
-    else b[i - na] = 0u;
+// ---- per-tile counts from the difference array ----
+// Row scan: one warp per row, 32 columns at a time, in place.
+__global__ void diff_rows_kernel(int *diff, int rows, int cols) {
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  int *d = diff + (size_t)row * cols;
+  int carry = 0;
+  for (int c0 = 0; c0 < cols; c0 += 32) {
+    const int c = c0 + lane;
+    int v = c < cols ? d[c] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    if (c < cols) d[c] = carry + v;
+    carry += __shfl_sync(0xffffffffu, v, 31);
   }
 }
 
-// ---- emit keys, one per thread, + digit histograms ----
-// The owner of pair i is found by two binary searches (CTA offsets, then
-// offsets inside the CTA), so every thread writes one key whatever the size
-// of the rectangles: a Gaussian covering thousands of tiles is spread over
-// many warps instead of serialising one.
-__device__ __forceinline__ uint32_t pair_owner(const unsigned long long *__restrict__ partial, int64_t nb,
-                                               const uint32_t *__restrict__ local, int64_t n_gauss, uint32_t i,
-                                               uint32_t *l_out) {
-  int64_t lo = 0, hi = nb;  // first block whose offset exceeds i
+// Column scan: one warp per column, 32 rows at a time, in place.
+__global__ void diff_cols_kernel(int *diff, int rows, int cols) {
+  const int col = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= cols) return;
+  int carry = 0;
+  for (int r0 = 0; r0 < rows; r0 += 32) {
+    const int r = r0 + lane;
+    int v = r < rows ? diff[(size_t)r * cols + col] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    if (r < rows) diff[(size_t)r * cols + col] = carry + v;
+    carry += __shfl_sync(0xffffffffu, v, 31);
+  }
+}
+
+// Exclusive scan of the per-tile counts in tile-id order (one CTA): writes
+// the tile ranges ((0, 0) for an empty tile) and the digit histograms of the
+// sort passes.
+__global__ void __launch_bounds__(1024) tile_scan_kernel(const int *counts, int tiles_x, int tiles_y, int passes,
+                                                         int digit_bits, uint2 *ranges, uint32_t *hist) {
+  __shared__ uint32_t s[1024];
+  __shared__ uint32_t s_hist[kMaxPasses * 256];
+  __shared__ uint32_t carry;
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) s_hist[i] = 0u;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int n = tiles_x * tiles_y;
+  const int stride = tiles_x + 1;
+  const uint32_t dmask = (1u << digit_bits) - 1;
+  for (int base = 0; base < n; base += 1024) {
+    const int t = base + threadIdx.x;
+    uint32_t v = 0;
+    if (t < n) {
+      const int ty = t / tiles_x, tx = t - ty * tiles_x;
+      v = (uint32_t)counts[ty * stride + tx];
+      if (v)
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + (((uint32_t)t >> (p * digit_bits)) & dmask)], v);
+    }
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const uint32_t u = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
+      __syncthreads();
+      s[threadIdx.x] += u;
+      __syncthreads();
+    }
+    if (t < n) {
+      const uint32_t start = carry + s[threadIdx.x] - v;
+      ranges[t] = v ? make_uint2(start, start + v) : make_uint2(0u, 0u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += s[1023];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) hist[i] = s_hist[i];
+}
+
+// ---- emit keys ----
+// CTA b writes keys [b T, (b+1) T), T = 2048.  One binary search over the
+// CTA offsets and the offsets inside a count CTA finds the owner of the
+// first key; the offsets of the following Gaussians are then staged in
+// shared memory, where every thread finds the owners of its keys.  Keys are
+// written coalesced whatever the sizes of the rectangles.
+__device__ __forceinline__ uint32_t global_offset(const unsigned long long *partial, const uint32_t *local,
+                                                  int64_t g) {
+  return (uint32_t)partial[g / kCountThreads] + local[g];
+}
+
+__device__ __forceinline__ int64_t pair_owner(const unsigned long long *__restrict__ partial, int64_t nb,
+                                              const uint32_t *__restrict__ local, int64_t n_gauss, uint32_t i) {
+  int64_t lo = 0, hi = nb;  // first count CTA whose offset exceeds i
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
     if (partial[mid] <= i) lo = mid + 1;
@@ -172,47 +271,52 @@ __device__ __forceinline__ uint32_t pair_owner(const unsigned long long *__restr
     if (local[mid] <= i2) lo = mid + 1;
     else hi = mid;
   }
-  const int64_t g = lo - 1;
-  *l_out = i2 - local[g];
-  return (uint32_t)g;
+  return lo - 1;
 }
 
-__global__ void __launch_bounds__(kCountThreads) emit_kernel(const uint32_t *__restrict__ local,
-                                                             const unsigned long long *__restrict__ partial,
-                                                             int64_t nb, const uint2 *__restrict__ rects,
-                                                             int64_t n_gauss, const Hdr *hdr, int tiles_x, int gbits,
-                                                             uint32_t *__restrict__ keys, int passes,
-                                                             int digit_bits, uint32_t *hist) {
-  __shared__ uint32_t s_hist[kMaxPasses * 256];
-  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) s_hist[i] = 0u;
-  __syncthreads();
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__restrict__ local,
+                                                            const unsigned long long *__restrict__ partial,
+                                                            int64_t nb, const uint2 *__restrict__ rects,
+                                                            int64_t n_gauss, const Hdr *hdr, int tiles_x, int gbits,
+                                                            uint32_t *__restrict__ keys) {
+  constexpr int kWin = kEmitTile + 1;
+  __shared__ uint32_t s_off[kWin];
+  __shared__ int64_t s_g0;
   const uint32_t n = (uint32_t)hdr->n_pairs;
-  const int lane = threadIdx.x & 31;
-  const uint32_t dmask = (1u << digit_bits) - 1;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
-    const uint32_t i = base + threadIdx.x;
-    const bool valid = i < n;
-    uint32_t tid = 0;
-    if (valid) {
-      uint32_t l;
-      const uint32_t g = pair_owner(partial, nb, local, n_gauss, i, &l);
-      const uint2 rc = rects[g];
-      const uint32_t w = rc.y & 0xffffu;
-      const uint32_t ry = l / w, rx = l - ry * w;
-      tid = ((rc.x >> 16) + ry) * (uint32_t)tiles_x + (rc.x & 0xffffu) + rx;
-      keys[i] = (tid << gbits) | g;
-    }
-    const unsigned active = __ballot_sync(0xffffffffu, valid);
-    for (int p = 0; p < passes; ++p) {
-      const uint32_t d = (tid >> (p * digit_bits)) & dmask;
-      const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu) & active;
-      if (valid && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&s_hist[p * 256 + d], __popc(peers));
-    }
+  const uint32_t k0 = blockIdx.x * (uint32_t)kEmitTile;
+  if (k0 >= n) return;
+  if (threadIdx.x == 0) s_g0 = pair_owner(partial, nb, local, n_gauss, k0);
+  __syncthreads();
+  const int64_t g0 = s_g0;
+  // offsets of Gaussians g0, g0+1, ...; beyond the table: +infinity
+  for (int k = threadIdx.x; k < kWin; k += kEmitThreads) {
+    const int64_t g = g0 + k;
+    s_off[k] = g < n_gauss ? global_offset(partial, local, g) : 0xffffffffu;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
-    if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
+#pragma unroll 2
+  for (int it = 0; it < kEmitItems; ++it) {
+    const uint32_t i = k0 + (uint32_t)(it * kEmitThreads + threadIdx.x);
+    if (i >= n) break;
+    int64_t g;
+    if (s_off[kWin - 1] <= i) {
+      g = pair_owner(partial, nb, local, n_gauss, i);  // many empty Gaussians: window too short
+    } else {
+      int lo = 0, hi = kWin;  // first window entry whose offset exceeds i
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= i) lo = mid + 1;
+        else hi = mid;
+      }
+      g = g0 + lo - 1;
+    }
+    const uint32_t l = i - global_offset(partial, local, g);
+    const uint2 rc = rects[g];
+    const uint32_t w = rc.y & 0xffffu;
+    const uint32_t ry = l / w, rx = l - ry * w;
+    const uint32_t tid = ((rc.x >> 16) + ry) * (uint32_t)tiles_x + (rc.x & 0xffffu) + rx;
+    keys[i] = (tid << gbits) | (uint32_t)g;
+  }
 }
 
 // ---- one onesweep pass ----
@@ -344,17 +448,6 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
   }
 }
 
-__global__ void ranges_kernel(const uint32_t *keys, const Hdr *hdr, int gbits, uint32_t n_tiles, uint2 *ranges) {
-  const uint32_t n = (uint32_t)hdr->n_pairs;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint32_t t = keys[i] >> gbits;
-    if (t >= n_tiles) continue;  // only after a sort that gave up waiting
-    if (i == 0 || (keys[i - 1] >> gbits) != t) ranges[t].x = i;
-    if (i + 1 == n || (keys[i + 1] >> gbits) != t) ranges[t].y = i + 1;
-  }
-}
-
 int g_debug_never_publish = -1;     // test hook: a partition that never publishes
 uint32_t g_spin_limit = kSpinLimit;
 
@@ -392,15 +485,18 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
   p->capacity = capacity;
   p->count_blocks = div_up64(n_gauss > 0 ? n_gauss : 1, kCountThreads);
   p->parts = div_up64(capacity > 0 ? capacity : 1, kSortTile);
+  // zeroed at the start of every call: [hdr, hist, counter, diff, lookback]
   size_t o = 0;
   p->off_hdr = o;        o = align256(o + sizeof(Hdr));
+  p->off_hist = o;       o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
+  p->off_counter = o;    o = align256(o + sizeof(uint32_t) * kMaxPasses);
+  p->off_diff = o;       o = align256(o + sizeof(int) * (size_t)(p->tiles_x + 1) * (size_t)(p->tiles_y + 1));
+  p->off_lookback = o;   o = align256(o + sizeof(uint32_t) * (size_t)p->passes * (size_t)p->parts * 256);
+  p->zero_bytes = o;
   p->off_local = o;      o = align256(o + sizeof(uint32_t) * (size_t)(n_gauss > 0 ? n_gauss : 1));
   p->off_partial = o;    o = align256(o + sizeof(unsigned long long) * (size_t)(p->count_blocks + 1));
   p->off_rects = o;      o = align256(o + sizeof(uint2) * (size_t)(n_gauss > 0 ? n_gauss : 1));
   p->off_keys_tmp = o;   o = align256(o + sizeof(uint32_t) * (size_t)(capacity > 0 ? capacity : 1));
-  p->off_hist = o;       o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
-  p->off_counter = o;    o = align256(o + sizeof(uint32_t) * kMaxPasses);
-  p->off_lookback = o;   o = align256(o + sizeof(uint32_t) * (size_t)p->passes * (size_t)p->parts * 256);
   p->bytes = o;
   return BS_OK;
 }
@@ -412,19 +508,33 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   uint32_t *local = reinterpret_cast<uint32_t *>(base + p.off_local);
   auto *partial = reinterpret_cast<unsigned long long *>(base + p.off_partial);
   uint2 *rects = reinterpret_cast<uint2 *>(base + p.off_rects);
+  int *diff = reinterpret_cast<int *>(base + p.off_diff);
   uint32_t *keys_tmp = reinterpret_cast<uint32_t *>(base + p.off_keys_tmp);
   uint32_t *hist = reinterpret_cast<uint32_t *>(base + p.off_hist);
   uint32_t *counter = reinterpret_cast<uint32_t *>(base + p.off_counter);
   uint32_t *lookback = reinterpret_cast<uint32_t *>(base + p.off_lookback);
+  uint2 *ranges = reinterpret_cast<uint2 *>(tile_ranges);
+  const int rows = p.tiles_y + 1, cols = p.tiles_x + 1;
 
-  BS_CUDA(cudaMemsetAsync(hdr, 0, sizeof(Hdr), s));
+  {
+    const size_t nz = p.zero_bytes / sizeof(uint32_t);
+    const int blocks = (int)std::min<int64_t>(div_up64((int64_t)nz, 256), 152 * 8);
+    zero_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<uint32_t *>(base), nz);
+    BS_LAUNCHED("zero_kernel");
+  }
   if (p.n_gauss > 0) {
     count_kernel<<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(gauss, p.n_gauss, cv.width, cv.height,
-                                                                    cv.tile, local, partial, rects);
+                                                                    cv.tile, p.tiles_x, local, partial, rects, diff);
     BS_LAUNCHED("count_kernel");
     scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, hdr);
     BS_LAUNCHED("scan_partials_kernel");
   }
+  diff_rows_kernel<<<div_up(rows, 8), 256, 0, s>>>(diff, rows, cols);
+  BS_LAUNCHED("diff_rows_kernel");
+  diff_cols_kernel<<<div_up(cols, 8), 256, 0, s>>>(diff, rows, cols);
+  BS_LAUNCHED("diff_cols_kernel");
+  tile_scan_kernel<<<1, 1024, 0, s>>>(diff, p.tiles_x, p.tiles_y, p.passes, p.digit_bits, ranges, hist);
+  BS_LAUNCHED("tile_scan_kernel");
   Hdr h;
   BS_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(Hdr), cudaMemcpyDeviceToHost, s));
   BS_CUDA(cudaStreamSynchronize(s));
@@ -434,25 +544,13 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     return BS_ERR_CAPACITY;
   }
   const int64_t P = (int64_t)h.n_pairs;
-  const int64_t parts = div_up64(P, kSortTile);
-  // zero the sort state for the partitions in use, and the tile ranges
-  {
-    const size_t na = (size_t)(p.off_lookback - p.off_hist) / sizeof(uint32_t) +
-                      (size_t)p.passes * (size_t)parts * 256;  // hist, counter, (pad), lookback
-    const size_t nb = (size_t)p.n_tiles * 2;
-    const int blocks = (int)std::min<size_t>(div_up64((int64_t)(na + nb), 256), 152 * 8);
-    zero_kernel<<<blocks, 256, 0, s>>>(hist, na, tile_ranges, nb);
-    BS_LAUNCHED("zero_kernel");
-  }
   if (P == 0) return BS_OK;
+  const int64_t parts = div_up64(P, kSortTile);
   // emit into the buffer that makes the last pass land in tile_keys
   uint32_t *bufs[2] = {tile_keys, keys_tmp};
   uint32_t *src = (p.passes % 2 == 0) ? tile_keys : keys_tmp;
-  {
-    const int blocks = (int)std::min<int64_t>(div_up64(P, kCountThreads), 152 * 16);
-    emit_kernel<<<blocks, kCountThreads, 0, s>>>(local, partial, p.count_blocks, rects, p.n_gauss, hdr, p.tiles_x,
-                                                 p.gbits, src, p.passes, p.digit_bits, hist);
-  }
+  emit_kernel<<<(unsigned)div_up64(P, kEmitTile), kEmitThreads, 0, s>>>(local, partial, p.count_blocks, rects,
+                                                                       p.n_gauss, hdr, p.tiles_x, p.gbits, src);
   BS_LAUNCHED("emit_kernel");
   for (int pass = 0; pass < p.passes; ++pass) {
     uint32_t *dst = (src == bufs[0]) ? bufs[1] : bufs[0];
@@ -463,12 +561,6 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
         counter + pass, g_spin_limit, g_debug_never_publish);
     BS_LAUNCHED("onesweep_kernel");
     src = dst;
-  }
-  {
-    const int blocks = (int)std::min<int64_t>(div_up64(P, 256), 152 * 16);
-    ranges_kernel<<<blocks, 256, 0, s>>>(tile_keys, hdr, p.gbits, (uint32_t)p.n_tiles,
-                                         reinterpret_cast<uint2 *>(tile_ranges));
-    BS_LAUNCHED("ranges_kernel");
   }
   return BS_OK;
 }

@@ -45,6 +45,49 @@ struct Staged {
   float2 c;  // g, b
 };
 
+constexpr float kLog2_255 = 7.99435343685885793f;  // alpha >= 1/255 <=> t1^2 + t2^2 <= log2(o) + log2(255)
+
+// Smallest t1^2 + t2^2 over the rectangle [dx0, dx1] x [dy0, dy1] of offsets
+// from the mean: 0 if the mean is inside, else the least value on the four
+// edges (a convex quadratic restricted to a segment, minimised in closed
+// form and clamped).
+__device__ __forceinline__ float min_q_rect(float A1, float B1, float A2, float B2, float dx0, float dx1, float dy0,
+                                            float dy1) {
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
+  const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
+  float best = INFINITY;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float X = e ? dx1 : dx0;
+    const float y = fminf(fmaxf(-axy * X / byy, dy0), dy1);
+    const float t1 = A1 * X + B1 * y, t2 = A2 * X + B2 * y;
+    best = fminf(best, t1 * t1 + t2 * t2);
+    const float Y = e ? dy1 : dy0;
+    const float x = fminf(fmaxf(-axy * Y / axx, dx0), dx1);
+    const float u1 = A1 * x + B1 * Y, u2 = A2 * x + B2 * Y;
+    best = fminf(best, u1 * u1 + u2 * u2);
+  }
+  return best;
+}
+
+// Bit w set: the Gaussian can reach alpha >= 1/255 at some pixel centre of
+// the half tile w (rows 8w..8w+7) of the tile whose first pixel is (x0, y0).
+// Conservative by a margin far above the float32 error of either side, so a
+// cleared bit only skips pixels that the blend would skip anyway.
+__device__ __forceinline__ uint32_t half_tile_bits(const Staged &s, int x0, int y0) {
+  const float thr = s.b.z + kLog2_255;
+  if (!(thr >= 0.f)) return 0u;  // o < 1/255 (or not finite): never visible
+  const float margin = 1e-2f + 1e-4f * thr;
+  const float dx0 = ((float)x0 + 0.5f) - s.a.x, dx1 = ((float)x0 + 15.5f) - s.a.x;
+  uint32_t bits = 0u;
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    const float dy0 = ((float)(y0 + 8 * w) + 0.5f) - s.a.y, dy1 = ((float)(y0 + 8 * w) + 7.5f) - s.a.y;
+    if (min_q_rect(s.a.z, s.a.w, s.b.x, s.b.y, dx0, dx1, dy0, dy1) <= thr + margin) bits |= 1u << w;
+  }
+  return bits;
+}
+
 __device__ __forceinline__ void scaled_axes(float ux, float uy, float isx, float isy, float &A1, float &B1,
                                             float &A2, float &B2) {
   const float kx = __fmul_rn(kKappa, isx), ky = __fmul_rn(kKappa, isy);
@@ -109,7 +152,7 @@ __device__ __forceinline__ TilePixels tile_pixels(int tile, int tiles_x, int W, 
 // blended, and the entries of the tile lists times the tile's pixels, into
 // stats[0..2] (for measurement; same blend otherwise).
 template <bool kStats>
-__global__ void __launch_bounds__(kThreads) render_fwd_kernel(const float *__restrict__ gauss,
+__global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *__restrict__ gauss,
                                                               const uint32_t *__restrict__ keys,
                                                               const uint2 *__restrict__ ranges, int W, int H,
                                                               int tiles_x, uint32_t gmask, uint32_t n_gauss,
@@ -120,9 +163,12 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const float *__res
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
+  __shared__ uint32_t s_bits[kBatch];
   uint32_t n_eval = 0, n_blend = 0;
   const int tile = blockIdx.x;
   const TilePixels tp = tile_pixels(tile, tiles_x, W, H);
+  const int tile_x0 = (tile % tiles_x) * kTile, tile_y0 = (tile / tiles_x) * kTile;
+  const uint32_t my_half = 1u << (threadIdx.x >> 5);
   const uint2 r = ranges[tile];
   float T[kPix], c0[kPix], c1[kPix], c2[kPix];
   uint32_t last[kPix];
@@ -141,10 +187,12 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const float *__res
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
+      s_bits[threadIdx.x] = half_tile_bits(s, tile_x0, tile_y0);
     }
     __syncthreads();
     const int n = (int)min((uint32_t)kBatch, r.y - base);
     for (int j = 0; j < n && alive; ++j) {
+      if (!(s_bits[j] & my_half)) continue;  // warp-uniform: no pixel of this half tile is reached
       const float4 a = s_a[j], b = s_b[j];
       const float dy = __fsub_rn(tp.py, a.y);
       const float b1dy = __fmul_rn(a.w, dy), b2dy = __fmul_rn(b.y, dy);
@@ -228,7 +276,7 @@ constexpr int kSums = 10;
 //   [5] sum q2 dy  [6] sum dp  [7..9] sum w g
 // with dp = dL/dlog2(alpha), q1 = dp t1, q2 = dp t2, w = alpha T, g = dL/dC;
 // grads_from_sums turns them into d/d(record) afterwards.
-__global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__restrict__ gauss,
+__global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *__restrict__ gauss,
                                                               const uint32_t *__restrict__ keys,
                                                               const uint2 *__restrict__ ranges, int W, int H,
                                                               int tiles_x, uint32_t gmask, uint32_t n_gauss,
@@ -240,9 +288,12 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__res
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
   __shared__ uint32_t s_g[kBatch];
+  __shared__ uint32_t s_bits[kBatch];
   __shared__ uint32_t s_max_last;
   const int tile = blockIdx.x;
   const TilePixels tp = tile_pixels(tile, tiles_x, W, H);
+  const int tile_x0 = (tile % tiles_x) * kTile, tile_y0 = (tile / tiles_x) * kTile;
+  const uint32_t my_half = 1u << (threadIdx.x >> 5);
   const uint2 r = ranges[tile];
   const int lane = threadIdx.x & 31;
   float T[kPix], g0[kPix], g1[kPix], g2[kPix], gS[kPix];
@@ -281,9 +332,11 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float *__res
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
       s_g[threadIdx.x] = g;
+      s_bits[threadIdx.x] = half_tile_bits(s, tile_x0, tile_y0);
     }
     __syncthreads();
     for (int j = (int)(end - start) - 1; j >= 0; --j) {
+      if (!(s_bits[j] & my_half)) continue;  // warp-uniform: no pixel of this half tile is reached
       const uint32_t pos = start + (uint32_t)j;
       const float4 a = s_a[j], b = s_b[j];
       const float2 gb = s_c[j];
