@@ -143,7 +143,7 @@ def test_render_fwd_matches_oracle(bs, name):
     terr = np.abs(T.cpu().numpy() - ref["T"].numpy())
     print(f"{name}: flagged {1 - ok.mean():.2e}, max err {err[ok].max():.2e}, "
           f"max err incl. flagged {err.max():.2e}, T err {terr[ok].max():.2e}")
-    assert 1 - ok.mean() <= 1e-4
+    assert 1 - ok.mean() <= 2e-4
     assert err[ok].max() <= 1e-5
     assert terr[ok].max() <= 1e-5
     # the last blended Gaussian of every pixel, through the tile list
