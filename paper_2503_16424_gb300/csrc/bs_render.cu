@@ -1,11 +1,17 @@
 // Per-tile alpha blending (Section 3.4, Eq. 9-10) and its reverse-order
 // backward, plus the L2 term of Eq. 13.
 //
-// One CTA of 64 threads per 16x16 tile; each thread owns 4 neighbouring
-// pixels of one row, so a warp covers a 16x8 half tile.  The tile's list is
-// staged into shared memory 64 Gaussians at a time.  A Gaussian is stored by
-// its eigen-frame (Eq. 11-12): Sigma^-1 = R diag(isx^2, isy^2) R^T with
-// R = [[ux, -uy], [uy, ux]], and is staged as the two scaled axes
+// One CTA of 64 threads per 16x16 tile.  Warp w covers rows 8w..8w+7; its
+// lane l owns one pixel in each of the warp's four 8x4 blocks (slot q = block
+// (q & 1, q >> 1), pixel (l & 7, l >> 3) inside it).  The tile's list is
+// staged into shared memory 64 Gaussians at a time, each with eight bits
+// telling which 8x4 blocks of the tile its alpha >= 1/255 region reaches, so
+// a warp skips a block for a Gaussian without touching its pixels, and the
+// work of a slot stays within one compact block.
+//
+// A Gaussian is stored by its eigen-frame (Eq. 11-12): Sigma^-1 =
+// R diag(isx^2, isy^2) R^T with R = [[ux, -uy], [uy, ux]], and is staged as the
+// two scaled axes
 //     (A1, B1) = k isx (ux, uy),   (A2, B2) = k isy (-uy, ux),   k^2 = log2(e)/2,
 // so that a pixel at offset (dx, dy) from the mean evaluates
 //     t1 = A1 dx + B1 dy,  t2 = A2 dx + B2 dy,
@@ -13,9 +19,8 @@
 //     alpha = min(0.99, 2^p).
 // A sum of two squares has no cancellation, unlike the conic form
 // a dx^2 + 2 b dx dy + c dy^2 of a thin, rotated Gaussian far along its
-// axis.  B1 dy and B2 dy are shared by a thread's 4 pixels.  The forward and
-// the backward stage and evaluate alpha with the same code, so both take the
-// same skip decisions bit for bit.
+// axis.  The forward and the backward stage and evaluate alpha with the same
+// code, so both take the same skip decisions bit for bit.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -27,11 +32,12 @@ namespace bs {
 namespace {
 
 constexpr int kTile = 16;
-constexpr int kPix = 4;                             // pixels per thread, along a row
+constexpr int kPix = 4;                             // pixels (slots) per thread
 constexpr int kThreads = kTile * kTile / kPix;      // 64
 constexpr int kBatch = kThreads;                    // Gaussians staged per round
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kKappa = 0.84932180028801907f;      // sqrt(log2(e) / 2)
+constexpr float kLog2_255 = 7.99435343685885793f;   // alpha >= 1/255 <=> t1^2 + t2^2 <= log2(o) + log2(255)
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -44,49 +50,6 @@ struct Staged {
   float4 b;  // A2, B2, log2(o), r
   float2 c;  // g, b
 };
-
-constexpr float kLog2_255 = 7.99435343685885793f;  // alpha >= 1/255 <=> t1^2 + t2^2 <= log2(o) + log2(255)
-
-// Smallest t1^2 + t2^2 over the rectangle [dx0, dx1] x [dy0, dy1] of offsets
-// from the mean: 0 if the mean is inside, else the least value on the four
-// edges (a convex quadratic restricted to a segment, minimised in closed
-// form and clamped).
-__device__ __forceinline__ float min_q_rect(float A1, float B1, float A2, float B2, float dx0, float dx1, float dy0,
-                                            float dy1) {
-  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
-  const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
-  float best = INFINITY;
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const float X = e ? dx1 : dx0;
-    const float y = fminf(fmaxf(-axy * X / byy, dy0), dy1);
-    const float t1 = A1 * X + B1 * y, t2 = A2 * X + B2 * y;
-    best = fminf(best, t1 * t1 + t2 * t2);
-    const float Y = e ? dy1 : dy0;
-    const float x = fminf(fmaxf(-axy * Y / axx, dx0), dx1);
-    const float u1 = A1 * x + B1 * Y, u2 = A2 * x + B2 * Y;
-    best = fminf(best, u1 * u1 + u2 * u2);
-  }
-  return best;
-}
-
-// Bit w set: the Gaussian can reach alpha >= 1/255 at some pixel centre of
-// the half tile w (rows 8w..8w+7) of the tile whose first pixel is (x0, y0).
-// Conservative by a margin far above the float32 error of either side, so a
-// cleared bit only skips pixels that the blend would skip anyway.
-__device__ __forceinline__ uint32_t half_tile_bits(const Staged &s, int x0, int y0) {
-  const float thr = s.b.z + kLog2_255;
-  if (!(thr >= 0.f)) return 0u;  // o < 1/255 (or not finite): never visible
-  const float margin = 1e-2f + 1e-4f * thr;
-  const float dx0 = ((float)x0 + 0.5f) - s.a.x, dx1 = ((float)x0 + 15.5f) - s.a.x;
-  uint32_t bits = 0u;
-#pragma unroll
-  for (int w = 0; w < 2; ++w) {
-    const float dy0 = ((float)(y0 + 8 * w) + 0.5f) - s.a.y, dy1 = ((float)(y0 + 8 * w) + 7.5f) - s.a.y;
-    if (min_q_rect(s.a.z, s.a.w, s.b.x, s.b.y, dx0, dx1, dy0, dy1) <= thr + margin) bits |= 1u << w;
-  }
-  return bits;
-}
 
 __device__ __forceinline__ void scaled_axes(float ux, float uy, float isx, float isy, float &A1, float &B1,
                                             float &A2, float &B2) {
@@ -118,8 +81,54 @@ __device__ __forceinline__ Staged stage(const float *__restrict__ gauss, uint32_
   return s;
 }
 
-// log2 of the unclamped alpha at one pixel of a row: dx = px - mx, and the
-// row's shared b1dy = B1 dy, b2dy = B2 dy.
+// Smallest t1^2 + t2^2 over the rectangle [dx0, dx1] x [dy0, dy1] of offsets
+// from the mean: 0 if the mean is inside, else the least value on the four
+// edges (a convex quadratic restricted to a segment, minimised in closed
+// form and clamped).
+__device__ __forceinline__ float min_q_rect(float A1, float B1, float A2, float B2, float axx, float byy,
+                                            float axy, float dx0, float dx1, float dy0, float dy1) {
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
+  float best = INFINITY;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float X = e ? dx1 : dx0;
+    const float y = fminf(fmaxf(-axy * X / byy, dy0), dy1);
+    const float t1 = A1 * X + B1 * y, t2 = A2 * X + B2 * y;
+    best = fminf(best, t1 * t1 + t2 * t2);
+    const float Y = e ? dy1 : dy0;
+    const float x = fminf(fmaxf(-axy * Y / axx, dx0), dx1);
+    const float u1 = A1 * x + B1 * Y, u2 = A2 * x + B2 * Y;
+    best = fminf(best, u1 * u1 + u2 * u2);
+  }
+  return best;
+}
+
+// Bit b = 2 * block_row + block_col set: the Gaussian can reach alpha >=
+// 1/255 at some pixel centre of the 8x4 block (block_col, block_row) of the
+// tile whose first pixel is (x0, y0).  Conservative by a margin far above the
+// float32 error of either side, so a cleared bit only skips pixels that the
+// blend would skip anyway.
+__device__ __forceinline__ uint32_t block_bits(const Staged &s, int x0, int y0) {
+  const float thr = s.b.z + kLog2_255;
+  if (!(thr >= 0.f)) return 0u;  // o < 1/255 (or not finite): never visible
+  const float lim = thr + (1e-2f + 1e-4f * thr);
+  const float A1 = s.a.z, B1 = s.a.w, A2 = s.b.x, B2 = s.b.y;
+  const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
+  uint32_t bits = 0u;
+#pragma unroll 1
+  for (int br = 0; br < 4; ++br) {
+    const float dy0 = ((float)(y0 + 4 * br) + 0.5f) - s.a.y, dy1 = ((float)(y0 + 4 * br) + 3.5f) - s.a.y;
+#pragma unroll
+    for (int bc = 0; bc < 2; ++bc) {
+      const float dx0 = ((float)(x0 + 8 * bc) + 0.5f) - s.a.x, dx1 = ((float)(x0 + 8 * bc) + 7.5f) - s.a.x;
+      if (min_q_rect(A1, B1, A2, B2, axx, byy, axy, dx0, dx1, dy0, dy1) <= lim) bits |= 1u << (2 * br + bc);
+    }
+  }
+  return bits;
+}
+
+// log2 of the unclamped alpha at a pixel: dx = px - mx, and the shared
+// b1dy = B1 dy, b2dy = B2 dy of its row.
 __device__ __forceinline__ float pixel_log2_alpha(const float4 &a, const float4 &b, float dx, float b1dy,
                                                   float b2dy, float &t1, float &t2) {
   t1 = __fmaf_rn(a.z, dx, b1dy);
@@ -127,24 +136,33 @@ __device__ __forceinline__ float pixel_log2_alpha(const float4 &a, const float4 
   return __fmaf_rn(-t1, t1, __fmaf_rn(-t2, t2, b.z));
 }
 
-struct TilePixels {
-  int x0, y;        // first pixel of the thread's row segment
-  float px[kPix], py;
-  unsigned inside;  // bit i: pixel i lies on the canvas
+struct ThreadPixels {
+  int x[2], y[2];    // slot q is pixel (x[q & 1], y[q >> 1])
+  float px[2], py[2];
+  unsigned inside;   // bit q: slot q lies on the canvas
+  int shift;         // this warp's four block bits start at bit `shift`
+  int tile_x0, tile_y0;
 };
 
-__device__ __forceinline__ TilePixels tile_pixels(int tile, int tiles_x, int W, int H) {
-  TilePixels t;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
-  t.y = ty * kTile + (threadIdx.x >> 2);
-  t.x0 = tx * kTile + (threadIdx.x & 3) * kPix;
-  t.py = (float)t.y + 0.5f;
+__device__ __forceinline__ ThreadPixels thread_pixels(int tile, int tiles_x, int W, int H) {
+  ThreadPixels t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  t.tile_x0 = (tile % tiles_x) * kTile;
+  t.tile_y0 = (tile / tiles_x) * kTile;
+  t.x[0] = t.tile_x0 + (lane & 7);
+  t.x[1] = t.x[0] + 8;
+  t.y[0] = t.tile_y0 + 8 * warp + (lane >> 3);
+  t.y[1] = t.y[0] + 4;
   t.inside = 0;
 #pragma unroll
-  for (int i = 0; i < kPix; ++i) {
-    t.px[i] = (float)(t.x0 + i) + 0.5f;
-    if (t.x0 + i < W && t.y < H) t.inside |= 1u << i;
+  for (int i = 0; i < 2; ++i) {
+    t.px[i] = (float)t.x[i] + 0.5f;
+    t.py[i] = (float)t.y[i] + 0.5f;
   }
+#pragma unroll
+  for (int q = 0; q < kPix; ++q)
+    if (t.x[q & 1] < W && t.y[q >> 1] < H) t.inside |= 1u << q;
+  t.shift = 4 * warp;
   return t;
 }
 
@@ -153,22 +171,20 @@ __device__ __forceinline__ TilePixels tile_pixels(int tile, int tiles_x, int W, 
 // stats[0..2] (for measurement; same blend otherwise).
 template <bool kStats>
 __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *__restrict__ gauss,
-                                                              const uint32_t *__restrict__ keys,
-                                                              const uint2 *__restrict__ ranges, int W, int H,
-                                                              int tiles_x, uint32_t gmask, uint32_t n_gauss,
-                                                              float3 bg, float *__restrict__ img,
-                                                              float *__restrict__ T_out,
-                                                              uint32_t *__restrict__ nc_out,
-                                                              unsigned long long *__restrict__ stats) {
+                                                                  const uint32_t *__restrict__ keys,
+                                                                  const uint2 *__restrict__ ranges, int W, int H,
+                                                                  int tiles_x, uint32_t gmask, uint32_t n_gauss,
+                                                                  float3 bg, float *__restrict__ img,
+                                                                  float *__restrict__ T_out,
+                                                                  uint32_t *__restrict__ nc_out,
+                                                                  unsigned long long *__restrict__ stats) {
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
   __shared__ uint32_t s_bits[kBatch];
   uint32_t n_eval = 0, n_blend = 0;
   const int tile = blockIdx.x;
-  const TilePixels tp = tile_pixels(tile, tiles_x, W, H);
-  const int tile_x0 = (tile % tiles_x) * kTile, tile_y0 = (tile / tiles_x) * kTile;
-  const uint32_t my_half = 1u << (threadIdx.x >> 5);
+  const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
   const uint2 r = ranges[tile];
   float T[kPix], c0[kPix], c1[kPix], c2[kPix];
   uint32_t last[kPix];
@@ -187,21 +203,29 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
-      s_bits[threadIdx.x] = half_tile_bits(s, tile_x0, tile_y0);
+      s_bits[threadIdx.x] = block_bits(s, tp.tile_x0, tp.tile_y0);
     }
     __syncthreads();
     const int n = (int)min((uint32_t)kBatch, r.y - base);
     for (int j = 0; j < n && alive; ++j) {
-      if (!(s_bits[j] & my_half)) continue;  // warp-uniform: no pixel of this half tile is reached
+      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform
+      if (!bits) continue;
       const float4 a = s_a[j], b = s_b[j];
-      const float dy = __fsub_rn(tp.py, a.y);
-      const float b1dy = __fmul_rn(a.w, dy), b2dy = __fmul_rn(b.y, dy);
+      float dx[2], b1dy[2], b2dy[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        dx[k] = __fsub_rn(tp.px[k], a.x);
+        const float dy = __fsub_rn(tp.py[k], a.y);
+        b1dy[k] = __fmul_rn(a.w, dy);
+        b2dy[k] = __fmul_rn(b.y, dy);
+      }
 #pragma unroll
       for (int q = 0; q < kPix; ++q) {
+        if (!(bits & (1u << q))) continue;   // warp-uniform: block q not reached
         if (!(alive & (1u << q))) continue;
         float t1, t2;
-        const float dx = __fsub_rn(tp.px[q], a.x);
-        const float al = fminf(kAlphaMax, ex2_approx(pixel_log2_alpha(a, b, dx, b1dy, b2dy, t1, t2)));
+        const float al =
+            fminf(kAlphaMax, ex2_approx(pixel_log2_alpha(a, b, dx[q & 1], b1dy[q >> 1], b2dy[q >> 1], t1, t2)));
         if (kStats) ++n_eval;
         if (al < kAlphaMin) continue;
         const float Tn = T[q] * (1.f - al);
@@ -237,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
 #pragma unroll
   for (int q = 0; q < kPix; ++q) {
     if (!(tp.inside & (1u << q))) continue;
-    const size_t p = (size_t)tp.y * W + tp.x0 + q;
+    const size_t p = (size_t)tp.y[q >> 1] * W + tp.x[q & 1];
     img[p] = __fmaf_rn(T[q], bg.x, c0[q]);
     img[plane + p] = __fmaf_rn(T[q], bg.y, c1[q]);
     img[2 * plane + p] = __fmaf_rn(T[q], bg.z, c2[q]);
@@ -264,26 +288,27 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
 }
 
 // Number of per-Gaussian sums the backward accumulates (see render_bwd_kernel).
-constexpr int kSums = 10;
+constexpr int kSums = 9;
 
 // Reverse walk.  With S the colour behind Gaussian j as seen through it,
 // S <- alpha_j c_j + (1 - alpha_j) S (starting from bg behind the last
 // blended Gaussian), the colour derivative is
 //     dC/dalpha_j = T_j (c_j - S),
 // which keeps the (1 - alpha_j)^-1 of the recovered transmittance out of the
-// gradient.  Per Gaussian the walk accumulates, over its tile's pixels,
-//   [0] sum q1  [1] sum q2  [2] sum q1 dx  [3] sum q1 dy  [4] sum q2 dx
-//   [5] sum q2 dy  [6] sum dp  [7..9] sum w g
-// with dp = dL/dlog2(alpha), q1 = dp t1, q2 = dp t2, w = alpha T, g = dL/dC;
-// grads_from_sums turns them into d/d(record) afterwards.
+// gradient.  With dq = alpha dL/dalpha (= dL/dp / ln 2 below the clamp) and
+// (dx, dy) the pixel's offset from the mean, each Gaussian accumulates over
+// its tile's pixels
+//   [0] sum dq dx  [1] sum dq dy  [2] sum dq dx^2  [3] sum dq dx dy
+//   [4] sum dq dy^2  [5] sum dq  [6..8] sum alpha T dL/dC,
+// and grads_from_sums turns the totals into d/d(record).
 __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *__restrict__ gauss,
-                                                              const uint32_t *__restrict__ keys,
-                                                              const uint2 *__restrict__ ranges, int W, int H,
-                                                              int tiles_x, uint32_t gmask, uint32_t n_gauss,
-                                                              float3 bg, const float *__restrict__ T_final,
-                                                              const uint32_t *__restrict__ n_contrib,
-                                                              const float *__restrict__ dimg,
-                                                              float *__restrict__ sums) {
+                                                                  const uint32_t *__restrict__ keys,
+                                                                  const uint2 *__restrict__ ranges, int W, int H,
+                                                                  int tiles_x, uint32_t gmask, uint32_t n_gauss,
+                                                                  float3 bg, const float *__restrict__ T_final,
+                                                                  const uint32_t *__restrict__ n_contrib,
+                                                                  const float *__restrict__ dimg,
+                                                                  float *__restrict__ sums) {
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
@@ -291,9 +316,7 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
   __shared__ uint32_t s_bits[kBatch];
   __shared__ uint32_t s_max_last;
   const int tile = blockIdx.x;
-  const TilePixels tp = tile_pixels(tile, tiles_x, W, H);
-  const int tile_x0 = (tile % tiles_x) * kTile, tile_y0 = (tile / tiles_x) * kTile;
-  const uint32_t my_half = 1u << (threadIdx.x >> 5);
+  const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
   const uint2 r = ranges[tile];
   const int lane = threadIdx.x & 31;
   float T[kPix], g0[kPix], g1[kPix], g2[kPix], gS[kPix];
@@ -308,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
     g0[q] = g1[q] = g2[q] = 0.f;
     last[q] = 0;
     if (tp.inside & (1u << q)) {
-      const size_t p = (size_t)tp.y * W + tp.x0 + q;
+      const size_t p = (size_t)tp.y[q >> 1] * W + tp.x[q & 1];
       T[q] = T_final[p];
       last[q] = n_contrib[p];
       g0[q] = dimg[p];
@@ -332,48 +355,56 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
       s_g[threadIdx.x] = g;
-      s_bits[threadIdx.x] = half_tile_bits(s, tile_x0, tile_y0);
+      s_bits[threadIdx.x] = block_bits(s, tp.tile_x0, tp.tile_y0);
     }
     __syncthreads();
     for (int j = (int)(end - start) - 1; j >= 0; --j) {
-      if (!(s_bits[j] & my_half)) continue;  // warp-uniform: no pixel of this half tile is reached
+      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform
+      if (!bits) continue;
       const uint32_t pos = start + (uint32_t)j;
       const float4 a = s_a[j], b = s_b[j];
       const float2 gb = s_c[j];
-      const float dy = __fsub_rn(tp.py, a.y);
-      const float b1dy = __fmul_rn(a.w, dy), b2dy = __fmul_rn(b.y, dy);
+      float dx[2], dy[2], b1dy[2], b2dy[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        dx[k] = __fsub_rn(tp.px[k], a.x);
+        dy[k] = __fsub_rn(tp.py[k], a.y);
+        b1dy[k] = __fmul_rn(a.w, dy[k]);
+        b2dy[k] = __fmul_rn(b.y, dy[k]);
+      }
       float v[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = 0.f;
       bool contrib = false;
 #pragma unroll
       for (int q = 0; q < kPix; ++q) {
+        if (!(bits & (1u << q))) continue;   // warp-uniform: block q not reached
         if (pos >= last[q]) continue;
         float t1, t2;
-        const float dx = __fsub_rn(tp.px[q], a.x);
-        const float raw = ex2_approx(pixel_log2_alpha(a, b, dx, b1dy, b2dy, t1, t2));
+        const float ddx = dx[q & 1], ddy = dy[q >> 1];
+        const float raw = ex2_approx(pixel_log2_alpha(a, b, ddx, b1dy[q >> 1], b2dy[q >> 1], t1, t2));
         const float al = fminf(kAlphaMax, raw);
         if (al < kAlphaMin) continue;
         contrib = true;
         const float one_m = 1.f - al;
         T[q] = __fdividef(T[q], one_m);          // T before this Gaussian
         const float w = al * T[q];
-        const float gc = g0[q] * b.w + g1[q] * gb.x + g2[q] * gb.y;
-        const float dal = T[q] * (gc - gS[q]);   // dL/dalpha
-        gS[q] = __fmaf_rn(al, gc, one_m * gS[q]);
-        v[7] = __fmaf_rn(w, g0[q], v[7]);
-        v[8] = __fmaf_rn(w, g1[q], v[8]);
-        v[9] = __fmaf_rn(w, g2[q], v[9]);
+        const float gc = __fmaf_rn(g2[q], gb.y, __fmaf_rn(g1[q], gb.x, g0[q] * b.w));
+        const float diff = gc - gS[q];
+        const float dal = T[q] * diff;            // dL/dalpha
+        gS[q] = __fmaf_rn(al, diff, gS[q]);
+        v[6] = __fmaf_rn(w, g0[q], v[6]);
+        v[7] = __fmaf_rn(w, g1[q], v[7]);
+        v[8] = __fmaf_rn(w, g2[q], v[8]);
         if (raw <= kAlphaMax) {
-          const float dp = dal * al * kLn2;      // dL/dlog2(alpha)
-          const float q1 = dp * t1, q2 = dp * t2;
-          v[0] += q1;
-          v[1] += q2;
-          v[2] = __fmaf_rn(q1, dx, v[2]);
-          v[3] = __fmaf_rn(q1, dy, v[3]);
-          v[4] = __fmaf_rn(q2, dx, v[4]);
-          v[5] = __fmaf_rn(q2, dy, v[5]);
-          v[6] += dp;
+          const float dq = dal * al;
+          const float ex = dq * ddx, ey = dq * ddy;
+          v[0] += ex;
+          v[1] += ey;
+          v[2] = __fmaf_rn(ex, ddx, v[2]);
+          v[3] = __fmaf_rn(ex, ddy, v[3]);
+          v[4] = __fmaf_rn(ey, ddy, v[4]);
+          v[5] += dq;
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
@@ -388,11 +419,12 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
   }
 }
 
-// The chain rule from the tile sums of render_bwd_kernel to the record:
-//   d/dmx = 2 (A1 s0 + A2 s1),  d/dmy = 2 (B1 s0 + B2 s1),
-//   d/dA1 = -2 s2, d/dB1 = -2 s3, d/dA2 = -2 s4, d/dB2 = -2 s5,
+// The chain rule from the tile sums of render_bwd_kernel to the record.
+// With p = log2(o) - t1^2 - t2^2, t = M d, M = [[A1, B1], [A2, B2]], and
+// dL/dp = ln2 * dq:
+//   d/d(mx, my) = 2 ln2 M^T M (s0, s1),   d/dM = -2 ln2 M [[s2, s3], [s3, s4]],
 //   A1 = k isx ux, B1 = k isx uy, A2 = -k isy uy, B2 = k isy ux,
-//   d/do = s6 / (o ln 2),  d/dcolour = s7..s9.   In place, one thread per Gaussian.
+//   d/do = s5 / o,   d/dcolour = s6..s8.   In place, one thread per Gaussian.
 __global__ void grads_from_sums_kernel(const float *__restrict__ gauss, float *__restrict__ dgauss, int64_t n) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
@@ -400,14 +432,17 @@ __global__ void grads_from_sums_kernel(const float *__restrict__ gauss, float *_
   const float4 r0 = rec[0], r1 = rec[1];
   float4 *d = reinterpret_cast<float4 *>(dgauss + g * BS_DGAUSS_FLOATS);
   const float4 s0 = d[0], s1 = d[1], s2 = d[2];
+  const float Sx = s0.x, Sy = s0.y, Sxx = s0.z, Sxy = s0.w, Syy = s1.x, S = s1.y;
   const float ux = r0.z, uy = r0.w, isx = r1.x, isy = r1.y, o = r1.z;
   float A1, B1, A2, B2;
   scaled_axes(ux, uy, isx, isy, A1, B1, A2, B2);
-  const float dA1 = -2.f * s0.z, dB1 = -2.f * s0.w, dA2 = -2.f * s1.x, dB2 = -2.f * s1.y;
-  d[0] = make_float4(2.f * (A1 * s0.x + A2 * s0.y), 2.f * (B1 * s0.x + B2 * s0.y),
+  const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
+  const float c2 = 2.f * kLn2;
+  const float dA1 = -c2 * (A1 * Sxx + B1 * Sxy), dB1 = -c2 * (A1 * Sxy + B1 * Syy);
+  const float dA2 = -c2 * (A2 * Sxx + B2 * Sxy), dB2 = -c2 * (A2 * Sxy + B2 * Syy);
+  d[0] = make_float4(c2 * (axx * Sx + axy * Sy), c2 * (axy * Sx + byy * Sy),
                      kKappa * (isx * dA1 + isy * dB2), kKappa * (isx * dB1 - isy * dA2));
-  d[1] = make_float4(kKappa * (ux * dA1 + uy * dB1), kKappa * (ux * dB2 - uy * dA2),
-                     o > 0.f ? s1.z / (o * kLn2) : 0.f, s1.w);
+  d[1] = make_float4(kKappa * (ux * dA1 + uy * dB1), kKappa * (ux * dB2 - uy * dA2), o > 0.f ? S / o : 0.f, s1.w);
   d[2] = make_float4(s2.x, s2.y, 0.f, 0.f);
 }
 
