@@ -49,6 +49,7 @@ struct Staged {
   float4 a;  // mx, my, A1, B1
   float4 b;  // A2, B2, log2(o), r
   float2 c;  // g, b
+  float2 ext;
 };
 
 __device__ __forceinline__ void scaled_axes(float ux, float uy, float isx, float isy, float &A1, float &B1,
@@ -68,6 +69,7 @@ __device__ __forceinline__ Staged stage(const float *__restrict__ gauss, uint32_
     s.a = make_float4(0.f, 0.f, 0.f, 0.f);
     s.b = make_float4(0.f, 0.f, -INFINITY, 0.f);
     s.c = make_float2(0.f, 0.f);
+    s.ext = make_float2(-1.f, -1.f);
     return s;
   }
   const float4 *rec = reinterpret_cast<const float4 *>(gauss + (size_t)g * BS_GAUSS_FLOATS);
@@ -78,6 +80,7 @@ __device__ __forceinline__ Staged stage(const float *__restrict__ gauss, uint32_
   s.a = make_float4(r0.x, r0.y, A1, B1);
   s.b = make_float4(A2, B2, o > 0.f ? log2f(o) : -INFINITY, r1.w);
   s.c = make_float2(r2.x, r2.y);
+  s.ext = make_float2(r2.z, r2.w);
   return s;
 }
 
@@ -105,24 +108,38 @@ __device__ __forceinline__ float min_q_rect(float A1, float B1, float A2, float 
 
 // Bit b = 2 * block_row + block_col set: the Gaussian can reach alpha >=
 // 1/255 at some pixel centre of the 8x4 block (block_col, block_row) of the
-// tile whose first pixel is (x0, y0).  Conservative by a margin far above the
-// float32 error of either side, so a cleared bit only skips pixels that the
-// blend would skip anyway.
-__device__ __forceinline__ uint32_t block_bits(const Staged &s, int x0, int y0) {
+// tile whose first pixel is (x0, y0).  Blocks outside the Gaussian's box
+// (mean +- ext) are cleared first; the others get the exact ellipse test.
+// Conservative by a margin far above the float32 error of either side, so a
+// cleared bit only skips pixels that the blend would skip anyway.
+__device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, float ext_y, int x0, int y0) {
   const float thr = s.b.z + kLog2_255;
   if (!(thr >= 0.f)) return 0u;  // o < 1/255 (or not finite): never visible
+  // box test: block columns / rows whose pixel centres overlap the box
+  const float bx0 = s.a.x - ext_x - ((float)x0 + 0.5f), bx1 = s.a.x + ext_x - ((float)x0 + 0.5f);
+  const float by0 = s.a.y - ext_y - ((float)y0 + 0.5f), by1 = s.a.y + ext_y - ((float)y0 + 0.5f);
+  uint32_t cols = 0u, rows = 0u;
+#pragma unroll
+  for (int bc = 0; bc < 2; ++bc)
+    if (bx1 >= 8.f * bc - 0.5f && bx0 <= 8.f * bc + 7.5f) cols |= 1u << bc;
+#pragma unroll
+  for (int br = 0; br < 4; ++br)
+    if (by1 >= 4.f * br - 0.5f && by0 <= 4.f * br + 3.5f) rows |= 1u << br;
+  uint32_t cand = 0u;
+#pragma unroll
+  for (int br = 0; br < 4; ++br)
+    if (rows & (1u << br)) cand |= cols << (2 * br);
   const float lim = thr + (1e-2f + 1e-4f * thr);
   const float A1 = s.a.z, B1 = s.a.w, A2 = s.b.x, B2 = s.b.y;
   const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
   uint32_t bits = 0u;
-#pragma unroll 1
-  for (int br = 0; br < 4; ++br) {
+  while (cand) {
+    const int b = __ffs(cand) - 1;
+    cand &= cand - 1;
+    const int br = b >> 1, bc = b & 1;
     const float dy0 = ((float)(y0 + 4 * br) + 0.5f) - s.a.y, dy1 = ((float)(y0 + 4 * br) + 3.5f) - s.a.y;
-#pragma unroll
-    for (int bc = 0; bc < 2; ++bc) {
-      const float dx0 = ((float)(x0 + 8 * bc) + 0.5f) - s.a.x, dx1 = ((float)(x0 + 8 * bc) + 7.5f) - s.a.x;
-      if (min_q_rect(A1, B1, A2, B2, axx, byy, axy, dx0, dx1, dy0, dy1) <= lim) bits |= 1u << (2 * br + bc);
-    }
+    const float dx0 = ((float)(x0 + 8 * bc) + 0.5f) - s.a.x, dx1 = ((float)(x0 + 8 * bc) + 7.5f) - s.a.x;
+    if (min_q_rect(A1, B1, A2, B2, axx, byy, axy, dx0, dx1, dy0, dy1) <= lim) bits |= 1u << b;
   }
   return bits;
 }
@@ -203,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
-      s_bits[threadIdx.x] = block_bits(s, tp.tile_x0, tp.tile_y0);
+      s_bits[threadIdx.x] = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
     }
     __syncthreads();
     const int n = (int)min((uint32_t)kBatch, r.y - base);
@@ -296,11 +313,13 @@ constexpr int kSums = 9;
 //     dC/dalpha_j = T_j (c_j - S),
 // which keeps the (1 - alpha_j)^-1 of the recovered transmittance out of the
 // gradient.  With dq = alpha dL/dalpha (= dL/dp / ln 2 below the clamp) and
-// (dx, dy) the pixel's offset from the mean, each Gaussian accumulates over
-// its tile's pixels
-//   [0] sum dq dx  [1] sum dq dy  [2] sum dq dx^2  [3] sum dq dx dy
-//   [4] sum dq dy^2  [5] sum dq  [6..8] sum alpha T dL/dC,
-// and grads_from_sums turns the totals into d/d(record).
+// (t1, t2) the pixel's offset in the Gaussian's scaled frame, each Gaussian
+// accumulates over its tile's pixels
+//   [0] sum dq t1  [1] sum dq t2  [2] sum dq t1^2  [3] sum dq t1 t2
+//   [4] sum dq t2^2  [5] sum dq  [6..8] sum alpha T dL/dC.
+// The frame keeps every term O(1) inside the Gaussian's support (the same
+// sums in pixel offsets cancel badly for a thin Gaussian far along its
+// axis); grads_from_sums turns the totals into d/d(record).
 __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *__restrict__ gauss,
                                                                   const uint32_t *__restrict__ keys,
                                                                   const uint2 *__restrict__ ranges, int W, int H,
@@ -355,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
       s_g[threadIdx.x] = g;
-      s_bits[threadIdx.x] = block_bits(s, tp.tile_x0, tp.tile_y0);
+      s_bits[threadIdx.x] = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
     }
     __syncthreads();
     for (int j = (int)(end - start) - 1; j >= 0; --j) {
@@ -364,13 +383,13 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
       const uint32_t pos = start + (uint32_t)j;
       const float4 a = s_a[j], b = s_b[j];
       const float2 gb = s_c[j];
-      float dx[2], dy[2], b1dy[2], b2dy[2];
+      float dx[2], b1dy[2], b2dy[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         dx[k] = __fsub_rn(tp.px[k], a.x);
-        dy[k] = __fsub_rn(tp.py[k], a.y);
-        b1dy[k] = __fmul_rn(a.w, dy[k]);
-        b2dy[k] = __fmul_rn(b.y, dy[k]);
+        const float dy = __fsub_rn(tp.py[k], a.y);
+        b1dy[k] = __fmul_rn(a.w, dy);
+        b2dy[k] = __fmul_rn(b.y, dy);
       }
       float v[16];
 #pragma unroll
@@ -381,8 +400,7 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
         if (!(bits & (1u << q))) continue;   // warp-uniform: block q not reached
         if (pos >= last[q]) continue;
         float t1, t2;
-        const float ddx = dx[q & 1], ddy = dy[q >> 1];
-        const float raw = ex2_approx(pixel_log2_alpha(a, b, ddx, b1dy[q >> 1], b2dy[q >> 1], t1, t2));
+        const float raw = ex2_approx(pixel_log2_alpha(a, b, dx[q & 1], b1dy[q >> 1], b2dy[q >> 1], t1, t2));
         const float al = fminf(kAlphaMax, raw);
         if (al < kAlphaMin) continue;
         contrib = true;
@@ -398,12 +416,12 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
         v[8] = __fmaf_rn(w, g2[q], v[8]);
         if (raw <= kAlphaMax) {
           const float dq = dal * al;
-          const float ex = dq * ddx, ey = dq * ddy;
-          v[0] += ex;
-          v[1] += ey;
-          v[2] = __fmaf_rn(ex, ddx, v[2]);
-          v[3] = __fmaf_rn(ex, ddy, v[3]);
-          v[4] = __fmaf_rn(ey, ddy, v[4]);
+          const float e1 = dq * t1, e2 = dq * t2;
+          v[0] += e1;
+          v[1] += e2;
+          v[2] = __fmaf_rn(e1, t1, v[2]);
+          v[3] = __fmaf_rn(e1, t2, v[3]);
+          v[4] = __fmaf_rn(e2, t2, v[4]);
           v[5] += dq;
         }
       }
@@ -420,9 +438,10 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
 }
 
 // The chain rule from the tile sums of render_bwd_kernel to the record.
-// With p = log2(o) - t1^2 - t2^2, t = M d, M = [[A1, B1], [A2, B2]], and
-// dL/dp = ln2 * dq:
-//   d/d(mx, my) = 2 ln2 M^T M (s0, s1),   d/dM = -2 ln2 M [[s2, s3], [s3, s4]],
+// With p = log2(o) - |t|^2, t = M d, M = [[A1, B1], [A2, B2]] = k D R^T,
+// D = diag(isx, isy), dL/dp = ln2 dq and Tm = [[s2, s3], [s3, s4]]:
+//   d/d(mx, my) = 2 ln2 M^T (s0, s1),
+//   d/dM = -2 ln2 sum dq t d^T = -2 ln2 Tm M^-T = -(2 ln2 / k) Tm D^-1 R^T,
 //   A1 = k isx ux, B1 = k isx uy, A2 = -k isy uy, B2 = k isy ux,
 //   d/do = s5 / o,   d/dcolour = s6..s8.   In place, one thread per Gaussian.
 __global__ void grads_from_sums_kernel(const float *__restrict__ gauss, float *__restrict__ dgauss, int64_t n) {
@@ -432,18 +451,22 @@ __global__ void grads_from_sums_kernel(const float *__restrict__ gauss, float *_
   const float4 r0 = rec[0], r1 = rec[1];
   float4 *d = reinterpret_cast<float4 *>(dgauss + g * BS_DGAUSS_FLOATS);
   const float4 s0 = d[0], s1 = d[1], s2 = d[2];
-  const float Sx = s0.x, Sy = s0.y, Sxx = s0.z, Sxy = s0.w, Syy = s1.x, S = s1.y;
+  const float T1 = s0.x, T2 = s0.y, T11 = s0.z, T12 = s0.w, T22 = s1.x, S = s1.y;
   const float ux = r0.z, uy = r0.w, isx = r1.x, isy = r1.y, o = r1.z;
   float A1, B1, A2, B2;
   scaled_axes(ux, uy, isx, isy, A1, B1, A2, B2);
-  const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
-  const float c2 = 2.f * kLn2;
-  const float dA1 = -c2 * (A1 * Sxx + B1 * Sxy), dB1 = -c2 * (A1 * Sxy + B1 * Syy);
-  const float dA2 = -c2 * (A2 * Sxx + B2 * Sxy), dB2 = -c2 * (A2 * Sxy + B2 * Syy);
-  d[0] = make_float4(c2 * (axx * Sx + axy * Sy), c2 * (axy * Sx + byy * Sy),
+  const float c = 2.f * kLn2;
+  // X = Tm D^-1 R^T, R^T = [[ux, uy], [-uy, ux]]
+  const float sx = isx > 0.f ? 1.f / isx : 0.f, sy = isy > 0.f ? 1.f / isy : 0.f;
+  const float p00 = T11 * sx, p01 = T12 * sy, p10 = T12 * sx, p11 = T22 * sy;
+  const float X00 = p00 * ux - p01 * uy, X01 = p00 * uy + p01 * ux;
+  const float X10 = p10 * ux - p11 * uy, X11 = p10 * uy + p11 * ux;
+  const float f = -c / kKappa;
+  const float dA1 = f * X00, dB1 = f * X01, dA2 = f * X10, dB2 = f * X11;
+  d[0] = make_float4(c * (A1 * T1 + A2 * T2), c * (B1 * T1 + B2 * T2),
                      kKappa * (isx * dA1 + isy * dB2), kKappa * (isx * dB1 - isy * dA2));
-  d[1] = make_float4(kKappa * (ux * dA1 + uy * dB1), kKappa * (ux * dB2 - uy * dA2), o > 0.f ? S / o : 0.f, s1.w);
-  d[2] = make_float4(s2.x, s2.y, 0.f, 0.f);
+  d[1] = make_float4(kKappa * (ux * dA1 + uy * dB1), kKappa * (ux * dB2 - uy * dA2), o > 0.f ? S / o : 0.f, s1.z);
+  d[2] = make_float4(s1.w, s2.x, 0.f, 0.f);
 }
 
 // L2 loss and its gradient, float4 at a time; per-thread float partial sums
