@@ -32,6 +32,9 @@ namespace bs {
 namespace {
 
 constexpr int kTile = 16;
+constexpr int kPix = 4;                             // pixels (slots) per thread
+constexpr int kThreads = kTile * kTile / kPix;      // 64
+constexpr int kBatch = kThreads;                    // Gaussians staged per round
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kKappa = 0.84932180028801907f;      // sqrt(log2(e) / 2)
 constexpr float kLog2_255 = 7.99435343685885793f;   // alpha >= 1/255 <=> t1^2 + t2^2 <= log2(o) + log2(255)
@@ -150,103 +153,93 @@ __device__ __forceinline__ float pixel_log2_alpha(const float4 &a, const float4 
   return __fmaf_rn(-t1, t1, __fmaf_rn(-t2, t2, b.z));
 }
 
-// One warp per 16x16 tile; lane l owns the pixel (l & 7, l >> 3) of each of
-// the tile's eight 8x4 blocks, block q = (q & 1, q >> 1) being its slot q.
-constexpr int kSlots = 8;
-constexpr int kWarpTiles = 2;                 // tiles (warps) per CTA
-constexpr int kCtaThreads = 32 * kWarpTiles;
-
-struct WarpPixels {
-  int x[2], y[4];     // slot q is pixel (x[q & 1], y[q >> 1])
-  float px[2], py[4];
-  unsigned inside;    // bit q: slot q lies on the canvas
+struct ThreadPixels {
+  int x[2], y[2];    // slot q is pixel (x[q & 1], y[q >> 1])
+  float px[2], py[2];
+  unsigned inside;   // bit q: slot q lies on the canvas
+  int shift;         // this warp's four block bits start at bit `shift`
   int tile_x0, tile_y0;
 };
 
-__device__ __forceinline__ WarpPixels warp_pixels(int tile, int tiles_x, int W, int H, int lane) {
-  WarpPixels t;
+__device__ __forceinline__ ThreadPixels thread_pixels(int tile, int tiles_x, int W, int H) {
+  ThreadPixels t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   t.tile_x0 = (tile % tiles_x) * kTile;
   t.tile_y0 = (tile / tiles_x) * kTile;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    t.x[i] = t.tile_x0 + (lane & 7) + 8 * i;
-    t.px[i] = (float)t.x[i] + 0.5f;
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    t.y[i] = t.tile_y0 + (lane >> 3) + 4 * i;
-    t.py[i] = (float)t.y[i] + 0.5f;
-  }
+  t.x[0] = t.tile_x0 + (lane & 7);
+  t.x[1] = t.x[0] + 8;
+  t.y[0] = t.tile_y0 + 8 * warp + (lane >> 3);
+  t.y[1] = t.y[0] + 4;
   t.inside = 0;
 #pragma unroll
-  for (int q = 0; q < kSlots; ++q)
+  for (int i = 0; i < 2; ++i) {
+    t.px[i] = (float)t.x[i] + 0.5f;
+    t.py[i] = (float)t.y[i] + 0.5f;
+  }
+#pragma unroll
+  for (int q = 0; q < kPix; ++q)
     if (t.x[q & 1] < W && t.y[q >> 1] < H) t.inside |= 1u << q;
+  t.shift = 4 * warp;
   return t;
 }
 
-// kStats: also count the (pixel, list entry) evaluations performed, the
-// entries blended, the sum over tiles of list length x 256 pixels, and the
-// (pixel, list entry) pairs up to each pixel's stop (or its whole list), into
-// stats[0..3] (for measurement; same blend otherwise).
+// kStats: also count the (pixel, list entry) evaluations (E), the entries
+// blended, and the entries of the tile lists times the tile's pixels, into
+// stats[0..2] (for measurement; same blend otherwise).
 template <bool kStats>
-__global__ void __launch_bounds__(kCtaThreads) render_fwd_kernel(const float *__restrict__ gauss,
-                                                                 const uint32_t *__restrict__ keys,
-                                                                 const uint2 *__restrict__ ranges, int n_tiles,
-                                                                 int W, int H, int tiles_x, uint32_t gmask,
-                                                                 uint32_t n_gauss, float3 bg,
-                                                                 float *__restrict__ img, float *__restrict__ T_out,
-                                                                 uint32_t *__restrict__ nc_out,
-                                                                 unsigned long long *__restrict__ stats) {
-  __shared__ float4 s_a[kWarpTiles][32];
-  __shared__ float4 s_b[kWarpTiles][32];
-  __shared__ float2 s_c[kWarpTiles][32];
-  __shared__ uint32_t s_bits[kWarpTiles][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int tile = blockIdx.x * kWarpTiles + wid;
-  if (tile >= n_tiles) return;
-  const WarpPixels tp = warp_pixels(tile, tiles_x, W, H, lane);
-  const uint2 r = ranges[tile];
-  float T[kSlots], c0[kSlots], c1[kSlots], c2[kSlots];
-  uint32_t last[kSlots], stop[kSlots];
-#pragma unroll
-  for (int q = 0; q < kSlots; ++q) {
-    T[q] = 1.f;
-    c0[q] = c1[q] = c2[q] = 0.f;
-    last[q] = 0;
-    stop[q] = 0;
-  }
+__global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *__restrict__ gauss,
+                                                                  const uint32_t *__restrict__ keys,
+                                                                  const uint2 *__restrict__ ranges, int W, int H,
+                                                                  int tiles_x, uint32_t gmask, uint32_t n_gauss,
+                                                                  float3 bg, float *__restrict__ img,
+                                                                  float *__restrict__ T_out,
+                                                                  uint32_t *__restrict__ nc_out,
+                                                                  unsigned long long *__restrict__ stats) {
+  __shared__ float4 s_a[kBatch];
+  __shared__ float4 s_b[kBatch];
+  __shared__ float2 s_c[kBatch];
+  __shared__ uint32_t s_bits[kBatch];
   uint32_t n_eval = 0, n_blend = 0;
+  const int tile = blockIdx.x;
+  const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
+  const uint2 r = ranges[tile];
+  float T[kPix], c0[kPix], c1[kPix], c2[kPix];
+  uint32_t last[kPix];
+#pragma unroll
+  for (int i = 0; i < kPix; ++i) {
+    T[i] = 1.f;
+    c0[i] = c1[i] = c2[i] = 0.f;
+    last[i] = 0;
+  }
   unsigned alive = tp.inside;
-  for (uint32_t base = r.x; base < r.y; base += 32) {
-    if (!__any_sync(0xffffffffu, alive != 0)) break;
-    const uint32_t i = base + lane;
-    __syncwarp();
+  for (uint32_t base = r.x; base < r.y; base += kBatch) {
+    if (__syncthreads_count(alive != 0) == 0) break;
+    const uint32_t i = base + threadIdx.x;
     if (i < r.y) {
       const Staged s = stage(gauss, keys[i] & gmask, n_gauss);
-      s_a[wid][lane] = s.a;
-      s_b[wid][lane] = s.b;
-      s_c[wid][lane] = s.c;
-      s_bits[wid][lane] = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
+      s_a[threadIdx.x] = s.a;
+      s_b[threadIdx.x] = s.b;
+      s_c[threadIdx.x] = s.c;
+      s_bits[threadIdx.x] = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
     }
-    __syncwarp();
-    const int n = (int)min(32u, r.y - base);
-    for (int j = 0; j < n; ++j) {
-      const uint32_t bits = s_bits[wid][j] & alive;
-      if (!__any_sync(0xffffffffu, bits != 0)) continue;
-      const float4 a = s_a[wid][j], b = s_b[wid][j];
-      const uint32_t pos1 = base - r.x + (uint32_t)j + 1;
-      float dx[2], b1dy[4], b2dy[4];
+    __syncthreads();
+    const int n = (int)min((uint32_t)kBatch, r.y - base);
+    for (int j = 0; j < n && alive; ++j) {
+      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform
+      if (!bits) continue;
+      const float4 a = s_a[j], b = s_b[j];
+      float dx[2], b1dy[2], b2dy[2];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) dx[k] = __fsub_rn(tp.px[k], a.x);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 2; ++k) {
+        dx[k] = __fsub_rn(tp.px[k], a.x);
         const float dy = __fsub_rn(tp.py[k], a.y);
         b1dy[k] = __fmul_rn(a.w, dy);
         b2dy[k] = __fmul_rn(b.y, dy);
       }
 #pragma unroll
-      for (int q = 0; q < kSlots; ++q) {
-        if (!(bits & (1u << q))) continue;
+      for (int q = 0; q < kPix; ++q) {
+        if (!(bits & (1u << q))) continue;   // warp-uniform: block q not reached
+        if (!(alive & (1u << q))) continue;
         float t1, t2;
         const float al =
             fminf(kAlphaMax, ex2_approx(pixel_log2_alpha(a, b, dx[q & 1], b1dy[q >> 1], b2dy[q >> 1], t1, t2)));
@@ -255,42 +248,35 @@ __global__ void __launch_bounds__(kCtaThreads) render_fwd_kernel(const float *__
         const float Tn = T[q] * (1.f - al);
         if (Tn < kTMin) {
           alive &= ~(1u << q);
-          if (kStats) stop[q] = pos1;
           continue;
         }
         const float w = al * T[q];
-        const float2 gb = s_c[wid][j];
+        const float2 gb = s_c[j];
         c0[q] = __fmaf_rn(w, b.w, c0[q]);
         c1[q] = __fmaf_rn(w, gb.x, c1[q]);
         c2[q] = __fmaf_rn(w, gb.y, c2[q]);
         T[q] = Tn;
-        last[q] = pos1;
+        last[q] = base - r.x + (uint32_t)j + 1;
         if (kStats) ++n_blend;
       }
     }
   }
   if (kStats) {
-    unsigned long long visit = 0;
-#pragma unroll
-    for (int q = 0; q < kSlots; ++q)
-      if (tp.inside & (1u << q)) visit += stop[q] ? stop[q] : (r.y - r.x);
-    unsigned long long e = n_eval, bl = n_blend;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      e += __shfl_xor_sync(0xffffffffu, e, o);
-      bl += __shfl_xor_sync(0xffffffffu, bl, o);
-      visit += __shfl_xor_sync(0xffffffffu, visit, o);
-    }
-    if (lane == 0) {
-      atomicAdd(&stats[0], e);
-      atomicAdd(&stats[1], bl);
+    __shared__ unsigned long long s_st[2];
+    if (threadIdx.x == 0) s_st[0] = s_st[1] = 0ull;
+    __syncthreads();
+    atomicAdd(&s_st[0], (unsigned long long)n_eval);
+    atomicAdd(&s_st[1], (unsigned long long)n_blend);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicAdd(&stats[0], s_st[0]);
+      atomicAdd(&stats[1], s_st[1]);
       atomicAdd(&stats[2], (unsigned long long)(r.y - r.x) * (kTile * kTile));
-      atomicAdd(&stats[3], visit);
     }
   }
   const size_t plane = (size_t)W * H;
 #pragma unroll
-  for (int q = 0; q < kSlots; ++q) {
+  for (int q = 0; q < kPix; ++q) {
     if (!(tp.inside & (1u << q))) continue;
     const size_t p = (size_t)tp.y[q >> 1] * W + tp.x[q & 1];
     img[p] = __fmaf_rn(T[q], bg.x, c0[q]);
@@ -334,31 +320,32 @@ constexpr int kSums = 9;
 // The frame keeps every term O(1) inside the Gaussian's support (the same
 // sums in pixel offsets cancel badly for a thin Gaussian far along its
 // axis); grads_from_sums turns the totals into d/d(record).
-__global__ void __launch_bounds__(kCtaThreads) render_bwd_kernel(const float *__restrict__ gauss,
-                                                                 const uint32_t *__restrict__ keys,
-                                                                 const uint2 *__restrict__ ranges, int n_tiles,
-                                                                 int W, int H, int tiles_x, uint32_t gmask,
-                                                                 uint32_t n_gauss, float3 bg,
-                                                                 const float *__restrict__ T_final,
-                                                                 const uint32_t *__restrict__ n_contrib,
-                                                                 const float *__restrict__ dimg,
-                                                                 float *__restrict__ sums) {
-  __shared__ float4 s_a[kWarpTiles][32];
-  __shared__ float4 s_b[kWarpTiles][32];
-  __shared__ float2 s_c[kWarpTiles][32];
-  __shared__ uint32_t s_g[kWarpTiles][32];
-  __shared__ uint32_t s_bits[kWarpTiles][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int tile = blockIdx.x * kWarpTiles + wid;
-  if (tile >= n_tiles) return;
-  const WarpPixels tp = warp_pixels(tile, tiles_x, W, H, lane);
+__global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *__restrict__ gauss,
+                                                                  const uint32_t *__restrict__ keys,
+                                                                  const uint2 *__restrict__ ranges, int W, int H,
+                                                                  int tiles_x, uint32_t gmask, uint32_t n_gauss,
+                                                                  float3 bg, const float *__restrict__ T_final,
+                                                                  const uint32_t *__restrict__ n_contrib,
+                                                                  const float *__restrict__ dimg,
+                                                                  float *__restrict__ sums) {
+  __shared__ float4 s_a[kBatch];
+  __shared__ float4 s_b[kBatch];
+  __shared__ float2 s_c[kBatch];
+  __shared__ uint32_t s_g[kBatch];
+  __shared__ uint32_t s_bits[kBatch];
+  __shared__ uint32_t s_max_last;
+  const int tile = blockIdx.x;
+  const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
   const uint2 r = ranges[tile];
-  float T[kSlots], g0[kSlots], g1[kSlots], g2[kSlots], gS[kSlots];
-  uint32_t last[kSlots];
+  const int lane = threadIdx.x & 31;
+  float T[kPix], g0[kPix], g1[kPix], g2[kPix], gS[kPix];
+  uint32_t last[kPix];
+  if (threadIdx.x == 0) s_max_last = 0;
+  __syncthreads();
   uint32_t my_max = 0;
   const size_t plane = (size_t)W * H;
 #pragma unroll
-  for (int q = 0; q < kSlots; ++q) {
+  for (int q = 0; q < kPix; ++q) {
     T[q] = 1.f;
     g0[q] = g1[q] = g2[q] = 0.f;
     last[q] = 0;
@@ -373,35 +360,33 @@ __global__ void __launch_bounds__(kCtaThreads) render_bwd_kernel(const float *__
     }
     gS[q] = g0[q] * bg.x + g1[q] * bg.y + g2[q] * bg.z;  // g . S, S = bg behind the last blended Gaussian
   }
-  const uint32_t max_last = min(__reduce_max_sync(0xffffffffu, my_max), r.y - r.x);
+  atomicMax(&s_max_last, my_max);
+  __syncthreads();
+  const uint32_t max_last = min(s_max_last, r.y - r.x);
   for (uint32_t end = max_last; end > 0;) {
-    const uint32_t start = end > 32u ? end - 32u : 0u;
-    const uint32_t i = start + lane;
-    __syncwarp();
+    const uint32_t start = end > (uint32_t)kBatch ? end - kBatch : 0u;
+    __syncthreads();
+    const uint32_t i = start + threadIdx.x;
     if (i < end) {
       const uint32_t g = keys[r.x + i] & gmask;
       const Staged s = stage(gauss, g, n_gauss);
-      s_a[wid][lane] = s.a;
-      s_b[wid][lane] = s.b;
-      s_c[wid][lane] = s.c;
-      s_g[wid][lane] = g;
-      s_bits[wid][lane] = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
+      s_a[threadIdx.x] = s.a;
+      s_b[threadIdx.x] = s.b;
+      s_c[threadIdx.x] = s.c;
+      s_g[threadIdx.x] = g;
+      s_bits[threadIdx.x] = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
     }
-    __syncwarp();
+    __syncthreads();
     for (int j = (int)(end - start) - 1; j >= 0; --j) {
+      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform
+      if (!bits) continue;
       const uint32_t pos = start + (uint32_t)j;
-      uint32_t bits = s_bits[wid][j];
+      const float4 a = s_a[j], b = s_b[j];
+      const float2 gb = s_c[j];
+      float dx[2], b1dy[2], b2dy[2];
 #pragma unroll
-      for (int q = 0; q < kSlots; ++q)
-        if (pos >= last[q]) bits &= ~(1u << q);
-      if (!__any_sync(0xffffffffu, bits != 0)) continue;
-      const float4 a = s_a[wid][j], b = s_b[wid][j];
-      const float2 gb = s_c[wid][j];
-      float dx[2], b1dy[4], b2dy[4];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) dx[k] = __fsub_rn(tp.px[k], a.x);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 2; ++k) {
+        dx[k] = __fsub_rn(tp.px[k], a.x);
         const float dy = __fsub_rn(tp.py[k], a.y);
         b1dy[k] = __fmul_rn(a.w, dy);
         b2dy[k] = __fmul_rn(b.y, dy);
@@ -411,8 +396,9 @@ __global__ void __launch_bounds__(kCtaThreads) render_bwd_kernel(const float *__
       for (int q = 0; q < 16; ++q) v[q] = 0.f;
       bool contrib = false;
 #pragma unroll
-      for (int q = 0; q < kSlots; ++q) {
-        if (!(bits & (1u << q))) continue;
+      for (int q = 0; q < kPix; ++q) {
+        if (!(bits & (1u << q))) continue;   // warp-uniform: block q not reached
+        if (pos >= last[q]) continue;
         float t1, t2;
         const float raw = ex2_approx(pixel_log2_alpha(a, b, dx[q & 1], b1dy[q >> 1], b2dy[q >> 1], t1, t2));
         const float al = fminf(kAlphaMax, raw);
@@ -442,7 +428,7 @@ __global__ void __launch_bounds__(kCtaThreads) render_bwd_kernel(const float *__
       if (__any_sync(0xffffffffu, contrib)) {
         const float tot = warp_reduce_scatter16(v, lane);
         const int k = lane >> 1;
-        const uint32_t g = s_g[wid][j];
+        const uint32_t g = s_g[j];
         if ((lane & 1) == 0 && k < kSums && tot != 0.f && g < n_gauss)
           atomicAdd(sums + (size_t)g * BS_DGAUSS_FLOATS + k, tot);
       }
@@ -527,20 +513,17 @@ bs_status launch_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas
                             const uint32_t *ranges, float *img, float *T_final, uint32_t *n_contrib,
                             cudaStream_t s, unsigned long long *stats) {
   const int tiles_x = div_up(cv.width, kTile), tiles_y = div_up(cv.height, kTile);
-  const int n_tiles = tiles_x * tiles_y;
   const uint32_t gmask = gbits >= 32 ? 0xffffffffu : ((1u << gbits) - 1u);
   const auto bg = make_float3(cv.bg[0], cv.bg[1], cv.bg[2]);
   const auto *rg = reinterpret_cast<const uint2 *>(ranges);
-  const int blocks = div_up(n_tiles, kWarpTiles);
   if (stats) {
     BS_CUDA(cudaMemsetAsync(stats, 0, 4 * sizeof(unsigned long long), s));
-    render_fwd_kernel<true><<<blocks, kCtaThreads, 0, s>>>(gauss, keys, rg, n_tiles, cv.width, cv.height, tiles_x,
-                                                           gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib,
-                                                           stats);
+    render_fwd_kernel<true><<<tiles_x * tiles_y, kThreads, 0, s>>>(
+        gauss, keys, rg, cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib, stats);
   } else {
-    render_fwd_kernel<false><<<blocks, kCtaThreads, 0, s>>>(gauss, keys, rg, n_tiles, cv.width, cv.height, tiles_x,
-                                                            gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib,
-                                                            nullptr);
+    render_fwd_kernel<false><<<tiles_x * tiles_y, kThreads, 0, s>>>(
+        gauss, keys, rg, cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib,
+        nullptr);
   }
   BS_LAUNCHED("render_fwd_kernel");
   return BS_OK;
@@ -550,11 +533,10 @@ bs_status launch_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas
                             const uint32_t *keys, const uint32_t *ranges, const float *T_final,
                             const uint32_t *n_contrib, const float *dL_dimg, float *dgauss, cudaStream_t s) {
   const int tiles_x = div_up(cv.width, kTile), tiles_y = div_up(cv.height, kTile);
-  const int n_tiles = tiles_x * tiles_y;
   const uint32_t gmask = gbits >= 32 ? 0xffffffffu : ((1u << gbits) - 1u);
   BS_CUDA(cudaMemsetAsync(dgauss, 0, sizeof(float) * BS_DGAUSS_FLOATS * (size_t)n_gauss, s));
-  render_bwd_kernel<<<div_up(n_tiles, kWarpTiles), kCtaThreads, 0, s>>>(
-      gauss, keys, reinterpret_cast<const uint2 *>(ranges), n_tiles, cv.width, cv.height, tiles_x, gmask,
+  render_bwd_kernel<<<tiles_x * tiles_y, kThreads, 0, s>>>(
+      gauss, keys, reinterpret_cast<const uint2 *>(ranges), cv.width, cv.height, tiles_x, gmask,
       (uint32_t)n_gauss, make_float3(cv.bg[0], cv.bg[1], cv.bg[2]), T_final, n_contrib, dL_dimg, dgauss);
   BS_LAUNCHED("render_bwd_kernel");
   grads_from_sums_kernel<<<(unsigned)div_up64(n_gauss, 256), 256, 0, s>>>(gauss, dgauss, n_gauss);
