@@ -44,6 +44,7 @@ constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr int64_t kMaxPairs = (1ll << 30) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kLookWindow = 8;
 
 struct Hdr {
   uint32_t status;
@@ -203,43 +204,50 @@ __global__ void diff_cols_kernel(int *diff, int rows, int cols) {
 
 // Exclusive scan of the per-tile counts in tile-id order (one CTA): writes
 // the tile ranges ((0, 0) for an empty tile) and the digit histograms of the
-// sort passes.
+// sort passes.  Each thread owns a run of consecutive tiles: a local running
+// sum, one block scan of the run totals, then the ranges.
+__device__ __forceinline__ uint32_t block_excl_scan1024(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t incl = warp_incl_scan(v, lane);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = warp_incl_scan(s_warp[lane], lane);
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  *total = s_warp[31];
+  return (warp ? s_warp[warp - 1] : 0u) + incl - v;
+}
+
 __global__ void __launch_bounds__(1024) tile_scan_kernel(const int *counts, int tiles_x, int tiles_y, int passes,
                                                          int digit_bits, uint2 *ranges, uint32_t *hist) {
-  __shared__ uint32_t s[1024];
   __shared__ uint32_t s_hist[kMaxPasses * 256];
-  __shared__ uint32_t carry;
+  __shared__ uint32_t s_warp[32];
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) s_hist[i] = 0u;
-  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int n = tiles_x * tiles_y;
   const int stride = tiles_x + 1;
   const uint32_t dmask = (1u << digit_bits) - 1;
-  for (int base = 0; base < n; base += 1024) {
-    const int t = base + threadIdx.x;
-    uint32_t v = 0;
-    if (t < n) {
-      const int ty = t / tiles_x, tx = t - ty * tiles_x;
-      v = (uint32_t)counts[ty * stride + tx];
-      if (v)
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + (((uint32_t)t >> (p * digit_bits)) & dmask)], v);
-    }
-    s[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      const uint32_t u = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
-      __syncthreads();
-      s[threadIdx.x] += u;
-      __syncthreads();
-    }
-    if (t < n) {
-      const uint32_t start = carry + s[threadIdx.x] - v;
-      ranges[t] = v ? make_uint2(start, start + v) : make_uint2(0u, 0u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) carry += s[1023];
-    __syncthreads();
+  const int run = (n + 1023) / 1024;
+  const int t0 = threadIdx.x * run, t1 = min(n, t0 + run);
+  uint32_t sum = 0;
+  for (int t = t0; t < t1; ++t) {
+    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+    const uint32_t v = (uint32_t)counts[ty * stride + tx];
+    sum += v;
+    if (v)
+      for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + (((uint32_t)t >> (p * digit_bits)) & dmask)], v);
   }
+  uint32_t total;
+  uint32_t start = block_excl_scan1024(sum, s_warp, &total);
+  for (int t = t0; t < t1; ++t) {
+    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+    const uint32_t v = (uint32_t)counts[ty * stride + tx];
+    ranges[t] = v ? make_uint2(start, start + v) : make_uint2(0u, 0u);
+    start += v;
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) hist[i] = s_hist[i];
 }
 
@@ -274,20 +282,34 @@ __device__ __forceinline__ int64_t pair_owner(const unsigned long long *__restri
   return lo - 1;
 }
 
+// owner[c] = the Gaussian whose pairs contain key c * kEmitTile, for every
+// emit CTA c below the capacity.  One thread per Gaussian; a range covers
+// floor((off + cnt - 1) / T) - ceil(off / T) + 1 chunk starts (usually 0 or 1).
+__global__ void chunk_owner_kernel(const uint32_t *__restrict__ local, const unsigned long long *__restrict__ partial,
+                                   const uint2 *__restrict__ rects, int64_t n_gauss, uint32_t n_chunks,
+                                   uint32_t *__restrict__ owner) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_gauss) return;
+  const uint2 rc = rects[g];
+  const uint32_t cnt = (rc.y & 0xffffu) * (rc.y >> 16);
+  if (!cnt) return;
+  const unsigned long long off = partial[g / kCountThreads] + local[g];
+  const unsigned long long c0 = (off + kEmitTile - 1) / kEmitTile, c1 = (off + cnt - 1) / kEmitTile;
+  for (unsigned long long c = c0; c <= c1 && c < n_chunks; ++c) owner[c] = (uint32_t)g;
+}
+
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__restrict__ local,
                                                             const unsigned long long *__restrict__ partial,
                                                             int64_t nb, const uint2 *__restrict__ rects,
                                                             int64_t n_gauss, const Hdr *hdr, int tiles_x, int gbits,
+                                                            const uint32_t *__restrict__ owner,
                                                             uint32_t *__restrict__ keys) {
   constexpr int kWin = kEmitTile + 1;
   __shared__ uint32_t s_off[kWin];
-  __shared__ int64_t s_g0;
   const uint32_t n = (uint32_t)hdr->n_pairs;
   const uint32_t k0 = blockIdx.x * (uint32_t)kEmitTile;
   if (k0 >= n) return;
-  if (threadIdx.x == 0) s_g0 = pair_owner(partial, nb, local, n_gauss, k0);
-  __syncthreads();
-  const int64_t g0 = s_g0;
+  const int64_t g0 = owner[blockIdx.x];
   // offsets of Gaussians g0, g0+1, ...; beyond the table: +infinity
   for (int k = threadIdx.x; k < kWin; k += kEmitThreads) {
     const int64_t g = g0 + k;
@@ -396,23 +418,34 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
       s_gstart[tid] = gexcl;
     } else {
       if (publish) st_relaxed(mine, kFlagAgg | bcount);
+      // Look back in windows of kLookWindow predecessors: their words are
+      // loaded together, then consumed nearest first until an inclusive
+      // prefix; a word not yet published is re-read (boundedly).
       uint32_t excl = 0;
       int64_t j = (int64_t)part - 1;
       uint32_t spins = 0;
-      while (j >= 0) {
-        const uint32_t v = ld_relaxed(lookback + (size_t)j * 256 + tid);
-        const uint32_t flag = v & ~kCountMask;
-        if (flag == 0u) {
-          if (++spins > spin_limit) {
-            atomicOr(&hdr->status, kDevErrTimeout);
-            break;
+      bool done = false;
+      while (!done && j >= 0) {
+        uint32_t win[kLookWindow];
+#pragma unroll
+        for (int k = 0; k < kLookWindow; ++k)
+          win[k] = j - k >= 0 ? ld_relaxed(lookback + (size_t)(j - k) * 256 + tid) : kFlagIncl;
+#pragma unroll 1
+        for (int k = 0; k < kLookWindow && !done; ++k) {
+          uint32_t v = win[k];
+          while ((v & ~kCountMask) == 0u) {
+            if (++spins > spin_limit) {
+              atomicOr(&hdr->status, kDevErrTimeout);
+              v = kFlagIncl;  // give up: treat as an empty inclusive prefix
+              break;
+            }
+            __nanosleep(32);
+            v = ld_relaxed(lookback + (size_t)(j - k) * 256 + tid);
           }
-          __nanosleep(32);
-          continue;
+          excl += v & kCountMask;
+          done = (v & ~kCountMask) == kFlagIncl;
         }
-        excl += v & kCountMask;
-        if (flag == kFlagIncl) break;
-        --j;
+        j -= kLookWindow;
       }
       if (publish) st_relaxed(mine, kFlagIncl | ((excl + bcount) & kCountMask));
       s_gstart[tid] = gexcl + excl;
@@ -496,6 +529,7 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
   p->off_local = o;      o = align256(o + sizeof(uint32_t) * (size_t)(n_gauss > 0 ? n_gauss : 1));
   p->off_partial = o;    o = align256(o + sizeof(unsigned long long) * (size_t)(p->count_blocks + 1));
   p->off_rects = o;      o = align256(o + sizeof(uint2) * (size_t)(n_gauss > 0 ? n_gauss : 1));
+  p->off_owner = o;      o = align256(o + sizeof(uint32_t) * (size_t)(div_up64(capacity, kEmitTile) + 1));
   p->off_keys_tmp = o;   o = align256(o + sizeof(uint32_t) * (size_t)(capacity > 0 ? capacity : 1));
   p->bytes = o;
   return BS_OK;
@@ -508,6 +542,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   uint32_t *local = reinterpret_cast<uint32_t *>(base + p.off_local);
   auto *partial = reinterpret_cast<unsigned long long *>(base + p.off_partial);
   uint2 *rects = reinterpret_cast<uint2 *>(base + p.off_rects);
+  uint32_t *owner = reinterpret_cast<uint32_t *>(base + p.off_owner);
   int *diff = reinterpret_cast<int *>(base + p.off_diff);
   uint32_t *keys_tmp = reinterpret_cast<uint32_t *>(base + p.off_keys_tmp);
   uint32_t *hist = reinterpret_cast<uint32_t *>(base + p.off_hist);
@@ -528,6 +563,9 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     BS_LAUNCHED("count_kernel");
     scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, hdr);
     BS_LAUNCHED("scan_partials_kernel");
+    chunk_owner_kernel<<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(
+        local, partial, rects, p.n_gauss, (uint32_t)div_up64(p.capacity, kEmitTile), owner);
+    BS_LAUNCHED("chunk_owner_kernel");
   }
   diff_rows_kernel<<<div_up(rows, 8), 256, 0, s>>>(diff, rows, cols);
   BS_LAUNCHED("diff_rows_kernel");
@@ -550,7 +588,8 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   uint32_t *bufs[2] = {tile_keys, keys_tmp};
   uint32_t *src = (p.passes % 2 == 0) ? tile_keys : keys_tmp;
   emit_kernel<<<(unsigned)div_up64(P, kEmitTile), kEmitThreads, 0, s>>>(local, partial, p.count_blocks, rects,
-                                                                       p.n_gauss, hdr, p.tiles_x, p.gbits, src);
+                                                                       p.n_gauss, hdr, p.tiles_x, p.gbits, owner,
+                                                                       src);
   BS_LAUNCHED("emit_kernel");
   for (int pass = 0; pass < p.passes; ++pass) {
     uint32_t *dst = (src == bufs[0]) ? bufs[1] : bufs[0];

@@ -37,13 +37,14 @@ __device__ __forceinline__ void bern3(double t, double w[4]) {
 }
 
 // Segment of sample k of K on a chain of S segments, u = k/(K-1):
-// s = min(floor(S u), S-1) decided in integers; local parameter t = S u - s.
+// s = min(floor(S u), S-1), decided in integers.
 __device__ __forceinline__ int chain_seg(int k, int K, int S) {
   const int s = (S * k) / (K - 1);
   return s > S - 1 ? S - 1 : s;
 }
-__device__ __forceinline__ double chain_t(int k, int K, int S, int s) {
-  return (double)(S * k - s * (K - 1)) / (double)(K - 1);
+// Local parameter t = S u - s, u = k / (K - 1), with inv = 1 / (K - 1).
+__device__ __forceinline__ double chain_t_inv(int k, int K, int S, int s, double inv) {
+  return (double)(S * k - s * (K - 1)) * inv;
 }
 
 // Boundary groups of a closed curve: A = P0..P6, B = P0, P11, ..., P7, P6.
@@ -65,8 +66,12 @@ __device__ __forceinline__ const float *curve_ctrl(const bs_curves &c, int curve
 // weights tau_r (double [rows]).  A closed curve's rows reuse the same K
 // weights, and the divisions and cosines run once per index, not per sample.
 __device__ void build_tables(const Cfg &cfg, bool closed, double *Wt, double *taut) {
+  __shared__ double s_inv;
   const int K = closed ? cfg.kc : cfg.g_open, S = closed ? 2 : 3;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) bern3(chain_t(k, K, S, chain_seg(k, K, S)), Wt + 4 * k);
+  if (threadIdx.x == 0) s_inv = 1.0 / (double)(K - 1);  // one double division per curve
+  __syncthreads();
+  const double inv = s_inv;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) bern3(chain_t_inv(k, K, S, chain_seg(k, K, S), inv), Wt + 4 * k);
   if (closed)
     for (int r = threadIdx.x; r < cfg.rows; r += blockDim.x) taut[r] = closed_tau(r, cfg.rows);
 }

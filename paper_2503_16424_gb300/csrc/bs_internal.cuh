@@ -67,7 +67,7 @@ struct BinPlan {
   int64_t parts;           // onesweep partitions for `capacity` keys
   // byte offsets inside the workspace
   size_t off_hdr, off_hist, off_counter, off_diff, off_lookback, zero_bytes;
-  size_t off_local, off_partial, off_rects, off_keys_tmp;
+  size_t off_local, off_partial, off_rects, off_owner, off_keys_tmp;
   size_t bytes;
 };
 bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, BinPlan *p);

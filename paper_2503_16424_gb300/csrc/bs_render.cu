@@ -153,6 +153,22 @@ __device__ __forceinline__ float pixel_log2_alpha(const float4 &a, const float4 
   return __fmaf_rn(-t1, t1, __fmaf_rn(-t2, t2, b.z));
 }
 
+// Per consumer warp, the staged entries whose block bits reach it, in order:
+// each staging warp writes the indices of its qualifying lanes (ballot +
+// prefix count) into its own half of the consumer's list.  The caller
+// synchronises before the lists are read.
+__device__ __forceinline__ void compact_lists(uint32_t bits, uint8_t (*list)[2][32], uint32_t (*cnt)[2]) {
+  const int sw = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int cw = 0; cw < 2; ++cw) {
+    const bool rel = ((bits >> (4 * cw)) & 15u) != 0u;
+    const unsigned m = __ballot_sync(0xffffffffu, rel);
+    if (rel) list[cw][sw][__popc(m & lt)] = (uint8_t)threadIdx.x;
+    if (lane == 0) cnt[cw][sw] = (uint32_t)__popc(m);
+  }
+}
+
 struct ThreadPixels {
   int x[2], y[2];    // slot q is pixel (x[q & 1], y[q >> 1])
   float px[2], py[2];
@@ -199,6 +215,8 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
   __shared__ uint32_t s_bits[kBatch];
+  __shared__ uint8_t s_list[2][2][32];  // [consumer warp][staging warp][k]: entries reaching the warp
+  __shared__ uint32_t s_cnt[2][2];
   uint32_t n_eval = 0, n_blend = 0;
   const int tile = blockIdx.x;
   const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
@@ -215,18 +233,23 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
   for (uint32_t base = r.x; base < r.y; base += kBatch) {
     if (__syncthreads_count(alive != 0) == 0) break;
     const uint32_t i = base + threadIdx.x;
+    uint32_t my_bits = 0u;
     if (i < r.y) {
       const Staged s = stage(gauss, keys[i] & gmask, n_gauss);
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
-      s_bits[threadIdx.x] = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
+      my_bits = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
+      s_bits[threadIdx.x] = my_bits;
     }
+    compact_lists(my_bits, s_list, s_cnt);
     __syncthreads();
-    const int n = (int)min((uint32_t)kBatch, r.y - base);
-    for (int j = 0; j < n && alive; ++j) {
-      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform
-      if (!bits) continue;
+    const int cw = threadIdx.x >> 5;
+    for (int sw = 0; sw < 2 && alive; ++sw) {
+    const int cnt = (int)s_cnt[cw][sw];
+    for (int k = 0; k < cnt && alive; ++k) {
+      const int j = s_list[cw][sw][k];
+      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform, not 0
       const float4 a = s_a[j], b = s_b[j];
       float dx[2], b1dy[2], b2dy[2];
 #pragma unroll
@@ -259,6 +282,7 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
         last[q] = base - r.x + (uint32_t)j + 1;
         if (kStats) ++n_blend;
       }
+    }
     }
   }
   if (kStats) {
@@ -333,6 +357,8 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
   __shared__ float2 s_c[kBatch];
   __shared__ uint32_t s_g[kBatch];
   __shared__ uint32_t s_bits[kBatch];
+  __shared__ uint8_t s_list[2][2][32];  // [consumer warp][staging warp][k]: entries reaching the warp
+  __shared__ uint32_t s_cnt[2][2];
   __shared__ uint32_t s_max_last;
   const int tile = blockIdx.x;
   const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
@@ -367,6 +393,7 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
     const uint32_t start = end > (uint32_t)kBatch ? end - kBatch : 0u;
     __syncthreads();
     const uint32_t i = start + threadIdx.x;
+    uint32_t my_bits = 0u;
     if (i < end) {
       const uint32_t g = keys[r.x + i] & gmask;
       const Staged s = stage(gauss, g, n_gauss);
@@ -374,12 +401,16 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
       s_g[threadIdx.x] = g;
-      s_bits[threadIdx.x] = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
+      my_bits = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
+      s_bits[threadIdx.x] = my_bits;
     }
+    compact_lists(my_bits, s_list, s_cnt);
     __syncthreads();
-    for (int j = (int)(end - start) - 1; j >= 0; --j) {
-      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform
-      if (!bits) continue;
+    const int cw = threadIdx.x >> 5;
+    for (int sw = 1; sw >= 0; --sw)
+    for (int k = (int)s_cnt[cw][sw] - 1; k >= 0; --k) {
+      const int j = s_list[cw][sw][k];
+      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform, not 0
       const uint32_t pos = start + (uint32_t)j;
       const float4 a = s_a[j], b = s_b[j];
       const float2 gb = s_c[j];
