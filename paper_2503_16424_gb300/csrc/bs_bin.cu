@@ -203,8 +203,8 @@ __global__ void diff_cols_kernel(int *diff, int rows, int cols) {
 }
 
 // Exclusive scan of the per-tile counts in tile-id order (one CTA): writes
-// the tile ranges ((0, 0) for an empty tile) and the digit histograms of the
-// sort passes.  Each thread owns a run of consecutive tiles: a local running
+// the tile ranges ((0, 0) for an empty tile) and, per sort pass, where the
+// keys of each digit start (the exclusive scan of the digit histogram).  Each thread owns a run of consecutive tiles: a local running
 // sum, one block scan of the run totals, then the ranges.
 __device__ __forceinline__ uint32_t block_excl_scan1024(uint32_t v, uint32_t *s_warp, uint32_t *total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -248,7 +248,17 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const int *counts, int 
     start += v;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) hist[i] = s_hist[i];
+  // per pass, the exclusive prefix over digits: where each digit's keys start
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < passes) {
+    uint32_t carry = 0;
+    for (int d0 = 0; d0 < 256; d0 += 32) {
+      const uint32_t v = s_hist[warp * 256 + d0 + lane];
+      const uint32_t incl = warp_incl_scan(v, lane);
+      hist[warp * 256 + d0 + lane] = carry + incl - v;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
 }
 
 // ---- emit keys ----
@@ -298,6 +308,26 @@ __global__ void chunk_owner_kernel(const uint32_t *__restrict__ local, const uns
   for (unsigned long long c = c0; c <= c1 && c < n_chunks; ++c) owner[c] = (uint32_t)g;
 }
 
+// Owner of key i: a binary search over the CTA's window of offsets in
+// shared memory, or over the global offsets when the window is too short
+// (runs of Gaussians without pairs).
+__device__ __forceinline__ int64_t window_owner(const uint32_t *s_off, int win, int64_t g0,
+                                                const unsigned long long *partial, int64_t nb,
+                                                const uint32_t *local, int64_t n_gauss, uint32_t i) {
+  if (s_off[win - 1] <= i) return pair_owner(partial, nb, local, n_gauss, i);
+  int lo = 0, hi = win;  // first window entry whose offset exceeds i
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (s_off[mid] <= i) lo = mid + 1;
+    else hi = mid;
+  }
+  return g0 + lo - 1;
+}
+
+// CTA b writes keys [b T, (b+1) T), T = 2048; thread t makes the keys
+// 8t .. 8t+7 of that range: one owner search, then a walk along the owner's
+// rectangle row by row (a new search only when the walk leaves the owner's
+// pairs).  The keys are staged in shared memory and written coalesced.
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__restrict__ local,
                                                             const unsigned long long *__restrict__ partial,
                                                             int64_t nb, const uint2 *__restrict__ rects,
@@ -306,6 +336,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__re
                                                             uint32_t *__restrict__ keys) {
   constexpr int kWin = kEmitTile + 1;
   __shared__ uint32_t s_off[kWin];
+  __shared__ uint32_t s_keys[kEmitTile];
   const uint32_t n = (uint32_t)hdr->n_pairs;
   const uint32_t k0 = blockIdx.x * (uint32_t)kEmitTile;
   if (k0 >= n) return;
@@ -316,29 +347,39 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__re
     s_off[k] = g < n_gauss ? global_offset(partial, local, g) : 0xffffffffu;
   }
   __syncthreads();
-#pragma unroll 2
-  for (int it = 0; it < kEmitItems; ++it) {
-    const uint32_t i = k0 + (uint32_t)(it * kEmitThreads + threadIdx.x);
-    if (i >= n) break;
-    int64_t g;
-    if (s_off[kWin - 1] <= i) {
-      g = pair_owner(partial, nb, local, n_gauss, i);  // many empty Gaussians: window too short
-    } else {
-      int lo = 0, hi = kWin;  // first window entry whose offset exceeds i
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (s_off[mid] <= i) lo = mid + 1;
-        else hi = mid;
+  const uint32_t i0 = k0 + (uint32_t)threadIdx.x * kEmitItems;
+  if (i0 < n) {
+    int64_t g = window_owner(s_off, kWin, g0, partial, nb, local, n_gauss, i0);
+    uint32_t off = global_offset(partial, local, g);
+    uint2 rc = rects[g];
+    uint32_t w = rc.y & 0xffffu, cnt = w * (rc.y >> 16);
+    uint32_t l = i0 - off;
+    uint32_t ry = l / w, rx = l - ry * w;
+#pragma unroll
+    for (int it = 0; it < kEmitItems; ++it) {
+      const uint32_t i = i0 + (uint32_t)it;
+      if (i >= n) break;
+      if (i - off >= cnt) {  // left the owner's pairs
+        g = window_owner(s_off, kWin, g0, partial, nb, local, n_gauss, i);
+        off = global_offset(partial, local, g);
+        rc = rects[g];
+        w = rc.y & 0xffffu;
+        cnt = w * (rc.y >> 16);
+        l = i - off;
+        ry = l / w;
+        rx = l - ry * w;
       }
-      g = g0 + lo - 1;
+      const uint32_t tid = ((rc.x >> 16) + ry) * (uint32_t)tiles_x + (rc.x & 0xffffu) + rx;
+      s_keys[threadIdx.x * kEmitItems + it] = (tid << gbits) | (uint32_t)g;
+      if (++rx == w) {
+        rx = 0;
+        ++ry;
+      }
     }
-    const uint32_t l = i - global_offset(partial, local, g);
-    const uint2 rc = rects[g];
-    const uint32_t w = rc.y & 0xffffu;
-    const uint32_t ry = l / w, rx = l - ry * w;
-    const uint32_t tid = ((rc.x >> 16) + ry) * (uint32_t)tiles_x + (rc.x & 0xffffu) + rx;
-    keys[i] = (tid << gbits) | (uint32_t)g;
   }
+  __syncthreads();
+  const uint32_t m = min((uint32_t)kEmitTile, n - k0);
+  for (uint32_t j = threadIdx.x; j < m; j += kEmitThreads) keys[k0 + j] = s_keys[j];
 }
 
 // ---- one onesweep pass ----
@@ -354,34 +395,26 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
 __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *__restrict__ in,
                                                                 uint32_t *__restrict__ out, const Hdr *hdr_in,
                                                                 Hdr *hdr, int shift, int bits,
-                                                                const uint32_t *ghist, uint32_t *lookback,
+                                                                const uint32_t *digit_start, uint32_t *lookback,
                                                                 uint32_t *counter, uint32_t spin_limit,
                                                                 int never_publish_part) {
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_whist[kSortWarps][256];
   __shared__ uint32_t s_bexcl[256];
   __shared__ uint32_t s_gstart[256];
-  __shared__ uint32_t s_scan[256];
+  __shared__ uint32_t s_wtot[kSortWarps];
   __shared__ uint32_t s_part;
   const uint32_t n = (uint32_t)hdr_in->n_pairs;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t nbins = 1u << bits, dmask = nbins - 1;
   if (tid == 0) s_part = atomicAdd(counter, 1u);
   for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
-  // global exclusive prefix of this pass's digit histogram
-  s_scan[tid] = tid < (int)nbins ? ghist[tid] : 0u;
   __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    const uint32_t t = tid >= o ? s_scan[tid - o] : 0u;
-    __syncthreads();
-    s_scan[tid] += t;
-    __syncthreads();
-  }
-  const uint32_t gexcl = s_scan[tid] - (tid < (int)nbins ? ghist[tid] : 0u);
   const uint32_t part = s_part;
   const uint32_t base = part * (uint32_t)kSortTile + (uint32_t)warp * (32u * kSortItems);
   const unsigned lt_mask = (1u << lane) - 1;
 
+  // stable rank of each key among the keys of its warp with the same digit
   uint32_t keys[kSortItems], rank[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
@@ -402,7 +435,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
   }
   __syncthreads();
 
-  // per digit: exclusive offsets across warps, publish, look back
+  // per digit (one thread each): offsets across warps, publish, look back
   uint32_t bcount = 0;
   if (tid < (int)nbins) {
 #pragma unroll
@@ -413,6 +446,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
     }
     uint32_t *mine = lookback + (size_t)part * 256 + tid;
     const bool publish = (int)part != never_publish_part;
+    const uint32_t gexcl = digit_start[tid];
     if (part == 0) {
       if (publish) st_relaxed(mine, kFlagIncl | bcount);
       s_gstart[tid] = gexcl;
@@ -451,16 +485,14 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
       s_gstart[tid] = gexcl + excl;
     }
   }
-  // block exclusive prefix over digits
-  s_scan[tid] = bcount;
+  // exclusive prefix of bcount over digits (warp scans, then the warp totals)
+  const uint32_t incl = warp_incl_scan(bcount, lane);
+  if (lane == 31) s_wtot[warp] = incl;
   __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    const uint32_t t = tid >= o ? s_scan[tid - o] : 0u;
-    __syncthreads();
-    s_scan[tid] += t;
-    __syncthreads();
-  }
-  s_bexcl[tid] = s_scan[tid] - bcount;
+  uint32_t wbase = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) wbase += w < warp ? s_wtot[w] : 0u;
+  s_bexcl[tid] = wbase + incl - bcount;
   __syncthreads();
   // scatter into shared memory in (digit, input order) order
 #pragma unroll

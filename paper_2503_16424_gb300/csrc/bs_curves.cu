@@ -61,62 +61,87 @@ __device__ __forceinline__ const float *curve_ctrl(const bs_curves &c, int curve
   return curve < c.n_open ? c.open_ctrl + (size_t)curve * 20 : c.closed_ctrl + (size_t)(curve - c.n_open) * 24;
 }
 
-// Per-CTA tables shared by every sample of the curve: the Bernstein weights
-// of each sample index k (double [K][4]) and, for closed curves, the row
-// weights tau_r (double [rows]).  A closed curve's rows reuse the same K
-// weights, and the divisions and cosines run once per index, not per sample.
-__device__ void build_tables(const Cfg &cfg, bool closed, double *Wt, double *taut) {
-  __shared__ double s_inv;
-  const int K = closed ? cfg.kc : cfg.g_open, S = closed ? 2 : 3;
-  if (threadIdx.x == 0) s_inv = 1.0 / (double)(K - 1);  // one double division per curve
-  __syncthreads();
-  const double inv = s_inv;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) bern3(chain_t_inv(k, K, S, chain_seg(k, K, S), inv), Wt + 4 * k);
-  if (closed)
-    for (int r = threadIdx.x; r < cfg.rows; r += blockDim.x) taut[r] = closed_tau(r, cfg.rows);
+// Shared memory of the sampling kernels, per CTA (one curve):
+//   Wt   [k_max][4] double   Bernstein weights of each sample index k
+//   taut [rows]     double   row weights tau_r (closed curves)
+//   Pd   [12]       double2  control points relative to the first one
+//   Qd   [rows][7]  double2  control points of each row (closed curves)
+//   X    [n_max]    double2  sample points relative to the first control point
+//   backward only: G [4][n_max] float2  per-sample gradient pieces, whose
+//   first plane is overwritten with dL/dX by the gather.
+struct CurveSmem {
+  double *Wt, *taut;
+  double2 *Pd, *Qd, *X;
+  float2 *G;
+};
+
+__host__ __device__ inline size_t curve_smem_bytes(int n_max, int k_max, int rows, bool with_grad) {
+  return sizeof(double) * (4 * (size_t)k_max + (size_t)rows) + sizeof(double2) * (12 + 7 * (size_t)rows + n_max) +
+         (with_grad ? sizeof(float2) * 4 * (size_t)n_max : 0);
 }
 
-// Sample points X of a curve relative to its first control point, into
-// shared memory (after build_tables and a barrier); returns the number of
-// samples.
-__device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, const double *Wt, const double *taut,
-                            double2 *X) {
+__device__ __forceinline__ CurveSmem carve(void *base, int n_max, int k_max, int rows, bool with_grad) {
+  CurveSmem m;
+  char *p = static_cast<char *>(base);
+  m.X = reinterpret_cast<double2 *>(p);
+  p += sizeof(double2) * n_max;
+  m.Pd = reinterpret_cast<double2 *>(p);
+  p += sizeof(double2) * 12;
+  m.Qd = reinterpret_cast<double2 *>(p);
+  p += sizeof(double2) * 7 * rows;
+  m.Wt = reinterpret_cast<double *>(p);
+  p += sizeof(double) * 4 * k_max;
+  m.taut = reinterpret_cast<double *>(p);
+  p += sizeof(double) * rows;
+  m.G = with_grad ? reinterpret_cast<float2 *>(p) : nullptr;
+  return m;
+}
+
+// Fill the per-CTA tables and the sample points X of one curve (ends with a
+// barrier).  The control points are taken relative to the first one in
+// float32 (a perturbation of at most half an ulp of the curve's own extent,
+// shared by all samples) and everything after that is in double: the
+// Bernstein weights, the row interpolation (Eq. 4), the sums of Eq. 1 and, in
+// local_geometry, the differences of neighbouring samples.
+__device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, const CurveSmem &m) {
+  __shared__ double s_inv;
+  const bool closed = curve >= c.n_open;
   const float *P = curve_ctrl(c, curve);
-  const double ox = P[0], oy = P[1];
-  if (curve < c.n_open) {
-    const int K = cfg.g_open;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      const int s = chain_seg(k, K, 3);
-      const double *w = Wt + 4 * k;
-      double ax = 0.0, ay = 0.0;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float2 p = ld2(P, 3 * s + i);
-        ax += w[i] * ((double)p.x - ox);
-        ay += w[i] * ((double)p.y - oy);
-      }
-      X[k] = make_double2(ax, ay);
+  const int K = closed ? cfg.kc : cfg.g_open, S = closed ? 2 : 3, R2 = closed ? cfg.rows : 1;
+  const int npts = closed ? 12 : 10;
+  if (threadIdx.x == 0) s_inv = 1.0 / (double)(K - 1);
+  for (int j = threadIdx.x; j < npts; j += blockDim.x)
+    m.Pd[j] = make_double2((double)(P[2 * j] - P[0]), (double)(P[2 * j + 1] - P[1]));
+  if (closed)
+    for (int r = threadIdx.x; r < R2; r += blockDim.x) m.taut[r] = closed_tau(r, R2);
+  __syncthreads();
+  const double inv = s_inv;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) bern3(chain_t_inv(k, K, S, chain_seg(k, K, S), inv), m.Wt + 4 * k);
+  if (closed) {
+    for (int q = threadIdx.x; q < 7 * R2; q += blockDim.x) {
+      const int r = q / 7, j = q - 7 * r;
+      const double2 a = m.Pd[j], b = m.Pd[closed_b_index(j)];
+      const double tau = m.taut[r];
+      m.Qd[q] = make_double2(a.x + tau * (b.x - a.x), a.y + tau * (b.y - a.y));  // Eq. 4
     }
-    return K;
   }
-  const int K = cfg.kc, R2 = cfg.rows, n = R2 * K;
+  __syncthreads();
+  const int n = R2 * K;
+  const double2 *ctrl = closed ? m.Qd : m.Pd;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int r = idx / K, k = idx - r * K;
-    const double tau = taut[r];
-    const int s = chain_seg(k, K, 2);
-    const double *w = Wt + 4 * k;
+    const int s = chain_seg(k, K, S);
+    const double *w = m.Wt + 4 * k;
+    const double2 *q = ctrl + 7 * r + 3 * s;  // open curves: r = 0
     double ax = 0.0, ay = 0.0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int j = 3 * s + i;
-      const float2 a = ld2(P, j), b = ld2(P, closed_b_index(j));
-      const double qx = (1.0 - tau) * ((double)a.x - ox) + tau * ((double)b.x - ox);  // Eq. 4
-      const double qy = (1.0 - tau) * ((double)a.y - oy) + tau * ((double)b.y - oy);
-      ax += w[i] * qx;
-      ay += w[i] * qy;
+      ax += w[i] * q[i].x;
+      ay += w[i] * q[i].y;
     }
-    X[idx] = make_double2(ax, ay);
+    m.X[idx] = make_double2(ax, ay);
   }
+  __syncthreads();
   return n;
 }
 
@@ -129,8 +154,7 @@ __device__ __forceinline__ float2 diff(const double2 *X, int hi, int lo) {
 // difference f (closed curves, for sigma_y); the scales; the unit tangent u.
 struct Local {
   float2 e, t, f;
-  int e_hi, e_lo, t_hi, t_lo, f_hi, f_lo;  // sample indices the differences use
-  float le, lt, lf;                         // their lengths
+  float le, lt, lf;  // their lengths
   float sx, sy, ux, uy;
 };
 
@@ -139,26 +163,17 @@ __device__ __forceinline__ Local local_geometry(const double2 *X, int idx, int K
   Local L;
   const int r = closed ? idx / K : 0;
   const int k = idx - r * K;
-  const int row = r * K;
-  if (k + 1 < K) { L.e_hi = row + k + 1; L.e_lo = row + k; }
-  else { L.e_hi = row + k; L.e_lo = row + k - 1; }
-  if (k == 0) { L.t_hi = row + 1; L.t_lo = row; }
-  else if (k == K - 1) { L.t_hi = row + k; L.t_lo = row + k - 1; }
-  else { L.t_hi = row + k + 1; L.t_lo = row + k - 1; }
-  L.e = diff(X, L.e_hi, L.e_lo);
-  L.t = diff(X, L.t_hi, L.t_lo);
+  L.e = k + 1 < K ? diff(X, idx + 1, idx) : diff(X, idx, idx - 1);
+  L.t = k == 0 ? diff(X, idx + 1, idx) : (k == K - 1 ? diff(X, idx, idx - 1) : diff(X, idx + 1, idx - 1));
   L.le = sqrtf(L.e.x * L.e.x + L.e.y * L.e.y);
   L.lt = sqrtf(L.t.x * L.t.x + L.t.y * L.t.y);
   L.sx = L.le / rho;
   if (closed) {
-    if (r + 1 < R2) { L.f_hi = idx + K; L.f_lo = idx; }
-    else { L.f_hi = idx; L.f_lo = idx - K; }
-    L.f = diff(X, L.f_hi, L.f_lo);
+    L.f = r + 1 < R2 ? diff(X, idx + K, idx) : diff(X, idx, idx - K);
     L.lf = sqrtf(L.f.x * L.f.x + L.f.y * L.f.y);
     L.sy = L.lf / rho;
   } else {
     L.f = make_float2(0.f, 0.f);
-    L.f_hi = L.f_lo = idx;
     L.lf = 0.f;
     L.sy = width;
   }
@@ -188,38 +203,13 @@ __device__ __forceinline__ CurveAttr curve_attr(const bs_curves &c, int curve, i
   return a;
 }
 
-// Dynamic shared memory of the sampling kernels: n_max double2 sample points,
-// [bwd: n_max float2 gradients,] k_max x 4 double weights, rows double tau.
-struct CurveSmem {
-  double2 *X;
-  float2 *dX;
-  double *Wt, *taut;
-};
-
-__device__ __forceinline__ CurveSmem carve(void *base, int n_max, int k_max, bool with_grad) {
-  CurveSmem m;
-  char *p = static_cast<char *>(base);
-  m.X = reinterpret_cast<double2 *>(p);
-  p += sizeof(double2) * n_max;
-  m.Wt = reinterpret_cast<double *>(p);
-  p += sizeof(double) * 4 * k_max;
-  m.taut = reinterpret_cast<double *>(p);
-  p += sizeof(double) * 64 * ((n_max + 63) / 64);  // rows <= n_max
-  m.dX = with_grad ? reinterpret_cast<float2 *>(p) : nullptr;
-  return m;
-}
-
 __global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss, int n_max,
                                                                    int k_max) {
   extern __shared__ double2 smem_fwd[];
-  const CurveSmem m = carve(smem_fwd, n_max, k_max, false);
-  double2 *X = m.X;
+  const CurveSmem m = carve(smem_fwd, n_max, k_max, cfg.rows, false);
   const int curve = blockIdx.x;
   const bool closed = curve >= c.n_open;
-  build_tables(cfg, closed, m.Wt, m.taut);
-  __syncthreads();
-  const int n = eval_samples(c, cfg, curve, m.Wt, m.taut, X);
-  __syncthreads();
+  const int n = eval_samples(c, cfg, curve, m);
   const int K = closed ? cfg.kc : cfg.g_open;
   const uint32_t first = c.draw_first[curve];
   const float *P = curve_ctrl(c, curve);
@@ -227,7 +217,7 @@ __global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, 
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int seg = closed ? 0 : chain_seg(idx, K, 3);
     const CurveAttr at = curve_attr(c, curve, seg);
-    const Local L = local_geometry(X, idx, K, cfg.rows, closed, at.width, cfg.rho);
+    const Local L = local_geometry(m.X, idx, K, cfg.rows, closed, at.width, cfg.rho);
     // Sigma = R diag(lx, ly) R^T (Eq. 11-12 with the eps floor)
     const float lx = L.sx * L.sx + cfg.eps, ly = L.sy * L.sy + cfg.eps;
     float ex = -1.f, ey = -1.f;
@@ -239,7 +229,7 @@ __global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, 
       ey = sqrtf(2.0f * lth * syy) + kExtPad;
     }
     float4 *rec = reinterpret_cast<float4 *>(gauss + (size_t)(first + idx) * BS_GAUSS_FLOATS);
-    rec[0] = make_float4((float)(ox + X[idx].x), (float)(oy + X[idx].y), L.ux, L.uy);
+    rec[0] = make_float4((float)(ox + m.X[idx].x), (float)(oy + m.X[idx].y), L.ux, L.uy);
     rec[1] = make_float4(rsqrtf(lx), rsqrtf(ly), at.opac, at.col.x);
     rec[2] = make_float4(at.col.y, at.col.z, ex, ey);
   }
@@ -251,29 +241,24 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__device__ __forceinline__ void sadd2(float2 *p, float x, float y) {
-  atomicAdd(&p->x, x);
-  atomicAdd(&p->y, y);
-}
-
+// Backward of the sampling, without atomics on the geometry.  Phase 1: each
+// sample turns its Gaussian's gradient into the gradients of its mean and
+// of its three difference vectors (e: sigma_x, t: the rotation, f: sigma_y of
+// a closed row), kept per sample.  Phase 2: each sample point gathers the
+// pieces of every difference that uses it.  Phase 3: each control point
+// coordinate gathers the Bernstein-weighted (and, for closed rows,
+// tau-weighted, Eq. 4) gradients of the sample points it moves.
 __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
                                                                    bs_curves_grad g, int n_max, int k_max) {
   extern __shared__ double2 smem_bwd[];
-  const CurveSmem m = carve(smem_bwd, n_max, k_max, true);
-  double2 *X = m.X;
-  float2 *dX = m.dX;
-  __shared__ float2 dP[12];
+  const CurveSmem m = carve(smem_bwd, n_max, k_max, cfg.rows, true);
+  float2 *GM = m.G, *GE = m.G + n_max, *GT = m.G + 2 * n_max, *GF = m.G + 3 * n_max;
   __shared__ float sAttr[8];  // opac[3] (open) or opac (closed), colour[3], width
   const int curve = blockIdx.x;
   const bool closed = curve >= c.n_open;
-  for (int i = threadIdx.x; i < 12; i += blockDim.x) dP[i] = make_float2(0.f, 0.f);
   if (threadIdx.x < 8) sAttr[threadIdx.x] = 0.f;
-  build_tables(cfg, closed, m.Wt, m.taut);
-  __syncthreads();
-  const int n = eval_samples(c, cfg, curve, m.Wt, m.taut, X);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dX[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  const int K = closed ? cfg.kc : cfg.g_open;
+  const int n = eval_samples(c, cfg, curve, m);
+  const int K = closed ? cfg.kc : cfg.g_open, R2 = closed ? cfg.rows : 1;
   const uint32_t first = c.draw_first[curve];
   const int lane = threadIdx.x & 31;
   const int n_rounds = div_up(n, blockDim.x);
@@ -283,7 +268,7 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
     if (idx < n) {
       const int seg = closed ? 0 : chain_seg(idx, K, 3);
       const CurveAttr at = curve_attr(c, curve, seg);
-      const Local L = local_geometry(X, idx, K, cfg.rows, closed, at.width, cfg.rho);
+      const Local L = local_geometry(m.X, idx, K, cfg.rows, closed, at.width, cfg.rho);
       const float *dg = dgauss + (size_t)(first + idx) * BS_DGAUSS_FLOATS;
       const float4 d0 = *reinterpret_cast<const float4 *>(dg);      // mx, my, ux, uy
       const float4 d1 = *reinterpret_cast<const float4 *>(dg + 4);  // isx, isy, o, r
@@ -292,29 +277,23 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
       const float isx = rsqrtf(L.sx * L.sx + cfg.eps), isy = rsqrtf(L.sy * L.sy + cfg.eps);
       const float dsx = -d1.x * L.sx * isx * isx * isx;
       const float dsy = -d1.y * L.sy * isy * isy * isy;
-      // mean
-      sadd2(&dX[idx], d0.x, d0.y);
+      GM[idx] = make_float2(d0.x, d0.y);
       // sigma_x = |e| / rho
-      if (L.le > 0.f) {
-        const float k = dsx / (L.le * cfg.rho);
-        sadd2(&dX[L.e_hi], k * L.e.x, k * L.e.y);
-        sadd2(&dX[L.e_lo], -k * L.e.x, -k * L.e.y);
-      }
+      const float ke = L.le > 0.f ? dsx / (L.le * cfg.rho) : 0.f;
+      GE[idx] = make_float2(ke * L.e.x, ke * L.e.y);
       // u = t / |t|  ->  dL/dt = (du - u (u . du)) / |t|
       if (L.lt > 0.f) {
         const float proj = L.ux * d0.z + L.uy * d0.w;
-        const float gx = (d0.z - L.ux * proj) / L.lt, gy = (d0.w - L.uy * proj) / L.lt;
-        sadd2(&dX[L.t_hi], gx, gy);
-        sadd2(&dX[L.t_lo], -gx, -gy);
+        GT[idx] = make_float2((d0.z - L.ux * proj) / L.lt, (d0.w - L.uy * proj) / L.lt);
+      } else {
+        GT[idx] = make_float2(0.f, 0.f);
       }
       if (closed) {
-        if (L.lf > 0.f) {
-          const float k = dsy / (L.lf * cfg.rho);
-          sadd2(&dX[L.f_hi], k * L.f.x, k * L.f.y);
-          sadd2(&dX[L.f_lo], -k * L.f.x, -k * L.f.y);
-        }
+        const float kf = L.lf > 0.f ? dsy / (L.lf * cfg.rho) : 0.f;
+        GF[idx] = make_float2(kf * L.f.x, kf * L.f.y);
         d_op[0] = d1.z;
       } else {
+        GF[idx] = make_float2(0.f, 0.f);
         d_w = dsy;
         d_op[seg] = d1.z;
       }
@@ -336,40 +315,63 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
     if (lane == 0) atomicAdd(&sAttr[6], w);
   }
   __syncthreads();
-  // sample points -> control points (Eq. 1-2; closed rows also Eq. 4)
-  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const float2 d = dX[idx];
-    if (!closed) {
-      const int s = chain_seg(idx, K, 3);
-      const double *wd = m.Wt + 4 * idx;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float w = (float)wd[i];
-        sadd2(&dP[3 * s + i], w * d.x, w * d.y);
-      }
-    } else {
-      const int r = idx / K, k = idx - r * K;
-      const float tau = (float)m.taut[r];
-      const int s = chain_seg(k, K, 2);
-      float w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) w[i] = (float)m.Wt[4 * k + i];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int j = 3 * s + i;
-        const float wa = w[i] * (1.0f - tau), wb = w[i] * tau;
-        sadd2(&dP[j], wa * d.x, wa * d.y);
-        sadd2(&dP[closed_b_index(j)], wb * d.x, wb * d.y);
-      }
+  // phase 2: dL/dX_m from the differences that use sample m (see local_geometry)
+  for (int mi = threadIdx.x; mi < n; mi += blockDim.x) {
+    const int r = mi / K, k = mi - r * K;
+    float2 d = GM[mi];
+    // e_k = X_{k+1} - X_k (k < K-1), X_k - X_{k-1} (k = K-1)
+    if (k >= 1) { d.x += GE[mi - 1].x; d.y += GE[mi - 1].y; }
+    if (k == K - 1) { d.x += GE[mi].x; d.y += GE[mi].y; }
+    if (k < K - 1) { d.x -= GE[mi].x; d.y -= GE[mi].y; }
+    if (k == K - 2) { d.x -= GE[mi + 1].x; d.y -= GE[mi + 1].y; }
+    // t_k = X_{k+1} - X_{k-1}, one-sided at both ends
+    if (k >= 1) { d.x += GT[mi - 1].x; d.y += GT[mi - 1].y; }
+    if (k == K - 1) { d.x += GT[mi].x; d.y += GT[mi].y; }
+    if (k <= K - 2) { d.x -= GT[mi + 1].x; d.y -= GT[mi + 1].y; }
+    if (k == 0) { d.x -= GT[mi].x; d.y -= GT[mi].y; }
+    if (closed) {
+      // f_k = X_{r+1,k} - X_{r,k} (r < R2-1), X_{r,k} - X_{r-1,k} (last row)
+      if (r >= 1) { d.x += GF[mi - K].x; d.y += GF[mi - K].y; }
+      if (r == R2 - 1) { d.x += GF[mi].x; d.y += GF[mi].y; }
+      if (r < R2 - 1) { d.x -= GF[mi].x; d.y -= GF[mi].y; }
+      if (r == R2 - 2) { d.x -= GF[mi + K].x; d.y -= GF[mi + K].y; }
     }
+    GM[mi] = d;  // only this thread reads GM[mi]
   }
   __syncthreads();
-  if (!closed) {
-    float *gp = g.open_ctrl + (size_t)curve * 20;
-    for (int i = threadIdx.x; i < 10; i += blockDim.x) {
-      gp[2 * i] = dP[i].x;
-      gp[2 * i + 1] = dP[i].y;
+  // phase 3: control points (Eq. 1-2; closed rows through Eq. 4)
+  const float2 *dX = GM;
+  const int npts = closed ? 12 : 10;
+  const int S = closed ? 2 : 3;
+  for (int q = threadIdx.x; q < 2 * npts; q += blockDim.x) {
+    const int p = q >> 1, comp = q & 1;
+    float acc = 0.f;
+    if (!closed) {
+      for (int k = 0; k < K; ++k) {
+        const int i = p - 3 * chain_seg(k, K, S);
+        if (i >= 0 && i <= 3) acc += (float)m.Wt[4 * k + i] * (comp ? dX[k].y : dX[k].x);
+      }
+    } else {
+      // A_j = P_j (j = 0..6), B_j = P_{12-j} (j = 1..5), B_0 = P_0, B_6 = P_6
+      const int ja = p <= 6 ? p : -1;
+      const int jb = (p == 0 || p == 6) ? p : (p >= 7 ? 12 - p : -1);
+      for (int k = 0; k < K; ++k) {
+        const int s = chain_seg(k, K, S);
+        const int ia = ja - 3 * s, ib = jb - 3 * s;
+        const bool use_a = ja >= 0 && ia >= 0 && ia <= 3, use_b = jb >= 0 && ib >= 0 && ib <= 3;
+        if (!use_a && !use_b) continue;
+        const float wa = use_a ? (float)m.Wt[4 * k + ia] : 0.f, wb = use_b ? (float)m.Wt[4 * k + ib] : 0.f;
+        for (int r = 0; r < R2; ++r) {
+          const float tau = (float)m.taut[r];
+          const float2 dx = dX[r * K + k];
+          acc += (wa * (1.f - tau) + wb * tau) * (comp ? dx.y : dx.x);
+        }
+      }
     }
+    if (!closed) g.open_ctrl[(size_t)curve * 20 + q] = acc;
+    else g.closed_ctrl[(size_t)(curve - c.n_open) * 24 + q] = acc;
+  }
+  if (!closed) {
     if (threadIdx.x < 3) {
       g.open_opac[curve * 3 + threadIdx.x] = sAttr[threadIdx.x];
       g.open_color[curve * 3 + threadIdx.x] = sAttr[3 + threadIdx.x];
@@ -377,11 +379,6 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
     if (threadIdx.x == 0) g.open_width[curve] = sAttr[6];
   } else {
     const int j = curve - c.n_open;
-    float *gp = g.closed_ctrl + (size_t)j * 24;
-    for (int i = threadIdx.x; i < 12; i += blockDim.x) {
-      gp[2 * i] = dP[i].x;
-      gp[2 * i + 1] = dP[i].y;
-    }
     if (threadIdx.x < 3) g.closed_color[j * 3 + threadIdx.x] = sAttr[3 + threadIdx.x];
     if (threadIdx.x == 0) g.closed_opac[j] = sAttr[0];
   }
@@ -418,7 +415,7 @@ __device__ __forceinline__ uint32_t key_order(float k) {
 }
 
 constexpr int kOrderThreads = 256;
-constexpr int kOrderChunk = 1024;  // keys compared per CTA
+constexpr int kOrderChunk = 256;  // keys compared per CTA
 
 // Rank by counting: rank_i = #{j : key_j < key_i or (key_j == key_i, j < i)}.
 // CTA (x, y) compares its 256 curves against the keys of chunk y and adds its
@@ -470,11 +467,6 @@ int max_k(const bs_curves &c, const bs_sample_cfg &cfg) {
   return m;
 }
 
-size_t curve_smem(int n_max, int k_max, bool with_grad) {
-  return sizeof(double2) * n_max + sizeof(double) * 4 * k_max + sizeof(double) * 64 * ((n_max + 63) / 64) +
-         (with_grad ? sizeof(float2) * n_max : 0);
-}
-
 }  // namespace
 
 bs_status launch_curve_order(const bs_curves &c, const bs_sample_cfg &cfg, uint32_t *rank, uint32_t *first,
@@ -495,7 +487,7 @@ bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float 
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
   const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
-  const size_t smem = curve_smem(n_max, k_max, false);
+  const size_t smem = curve_smem_bytes(n_max, k_max, cfg.rows_closed, false);
   BS_CUDA(cudaFuncSetAttribute(sample_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), gauss, n_max, k_max);
   BS_LAUNCHED("sample_fwd_kernel");
@@ -507,7 +499,7 @@ bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const 
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
   const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
-  const size_t smem = curve_smem(n_max, k_max, true);
+  const size_t smem = curve_smem_bytes(n_max, k_max, cfg.rows_closed, true);
   BS_CUDA(cudaFuncSetAttribute(sample_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), dgauss, g, n_max, k_max);
   BS_LAUNCHED("sample_bwd_kernel");
