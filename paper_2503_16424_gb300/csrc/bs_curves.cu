@@ -98,11 +98,10 @@ __device__ __forceinline__ CurveSmem carve(void *base, int n_max, int k_max, int
 }
 
 // Fill the per-CTA tables and the sample points X of one curve (ends with a
-// barrier).  The control points are taken relative to the first one in
-// float32 (a perturbation of at most half an ulp of the curve's own extent,
-// shared by all samples) and everything after that is in double: the
-// Bernstein weights, the row interpolation (Eq. 4), the sums of Eq. 1 and, in
-// local_geometry, the differences of neighbouring samples.
+// barrier).  Everything up to the differences of neighbouring samples is in
+// double: the control points relative to the first one (exact), the
+// Bernstein weights, the row interpolation (Eq. 4), the sums of Eq. 1 and,
+// in local_geometry, the differences themselves.
 __device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, const CurveSmem &m) {
   __shared__ double s_inv;
   const bool closed = curve >= c.n_open;
@@ -111,7 +110,7 @@ __device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, const
   const int npts = closed ? 12 : 10;
   if (threadIdx.x == 0) s_inv = 1.0 / (double)(K - 1);
   for (int j = threadIdx.x; j < npts; j += blockDim.x)
-    m.Pd[j] = make_double2((double)(P[2 * j] - P[0]), (double)(P[2 * j + 1] - P[1]));
+    m.Pd[j] = make_double2((double)P[2 * j] - (double)P[0], (double)P[2 * j + 1] - (double)P[1]);
   if (closed)
     for (int r = threadIdx.x; r < R2; r += blockDim.x) m.taut[r] = closed_tau(r, R2);
   __syncthreads();
