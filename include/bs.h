@@ -190,6 +190,30 @@ bs_status bs_bin_tiles(const float *gauss, int64_t n_gauss, const bs_canvas *can
                        bs_stream stream);
 
 /*
+ * bs_bin_tiles for callers that cannot allocate device memory: the same
+ * binning, with its scratch in one fixed array of 32 MiB that the library
+ * keeps in device memory (every GPU that loads the library holds it until the
+ * process exits).  Meant for code that may not call cudaMalloc or a caching
+ * allocator, for instance a host that hands this library a fixed memory
+ * budget, or a callback that must not allocate.  The caller still provides
+ * gauss, tile_keys and tile_ranges.  The paper has no counterpart of this call.
+ *   - A request whose scratch would exceed 32 MiB (a pair_capacity above
+ *     about 6.7 M for 262,144 Gaussians on a 2048 x 2048 canvas; see
+ *     bs_bin_tiles_workspace for the size of a request) returns
+ *     BS_ERR_INVALID_ARG with the size it needs; nothing is launched.
+ *   - No allocation is made: no cudaMalloc, cudaFree or allocating library
+ *     routine.  The first call on a device looks up the array's device
+ *     address, so make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (each call clears what it needs cleared): calls that overlap on the GPU,
+ *     on any streams, race with each other.  bs_device_status does not read it.
+ * Arguments, results and the one synchronisation are those of bs_bin_tiles.
+ */
+bs_status bs_bin_tiles_static(const float *gauss, int64_t n_gauss, const bs_canvas *canvas,
+                              int64_t pair_capacity, int64_t *n_pairs_out,
+                              uint32_t *tile_keys, uint32_t *tile_ranges, bs_stream stream);
+
+/*
  * Forward blend (Eq. 9-10).  Per pixel, over its tile's list in order:
  * alpha = min(0.99, o exp(-0.5 d^T Sigma^-1 d)); skipped if alpha < 1/255;
  * the pixel stops at the first Gaussian that would bring its transmittance

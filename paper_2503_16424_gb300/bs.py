@@ -70,6 +70,7 @@ _sig("bs_sample_curves_bwd", POINTER(bs_curves), POINTER(bs_sample_cfg), _P, POI
 _sig("bs_bin_tiles_workspace", c_int64, POINTER(bs_canvas), c_int64, POINTER(c_size_t))
 _sig("bs_bin_tiles", _P, c_int64, POINTER(bs_canvas), _P, c_size_t, c_int64, POINTER(c_int64), _P, _P, _P)
 _sig("bs_render_fwd", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P)
+_sig("bs_bin_tiles_static", _P, c_int64, POINTER(bs_canvas), c_int64, POINTER(c_int64), _P, _P, _P)
 _sig("bs_l2_loss_grad", _P, _P, c_int64, _P, _P, _P)
 _sig("bs_render_stats", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P, _P)
 _sig("bs_render_bwd", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P,
@@ -281,6 +282,22 @@ class Binning:
         _check("bs_device_status", lib.bs_device_status(_ptr(self.ws), self.ws.numel(), ctypes.byref(out),
                                                          _stream()))
         return int(out.value)
+
+
+def bin_tiles_static(gauss: torch.Tensor, canvas: Canvas, tile_keys: torch.Tensor, tile_ranges: torch.Tensor):
+    """bs_bin_tiles_static: binning with the library's fixed scratch (no
+    workspace argument).  tile_keys [pair_capacity] and tile_ranges
+    [n_tiles, 2] int32 are the caller's; returns the pair count."""
+    n_gauss = int(gauss.shape[0])
+    _want(gauss, torch.float32, (n_gauss, GAUSS_FLOATS), "gauss")
+    _want(tile_keys, torch.int32, None, "tile_keys")
+    _want(tile_ranges, torch.int32, (canvas.n_tiles, 2), "tile_ranges")
+    cv = canvas.c()
+    n_pairs = c_int64(0)
+    _check("bs_bin_tiles_static", lib.bs_bin_tiles_static(_ptr(gauss), n_gauss, ctypes.byref(cv),
+                                                           tile_keys.numel(), ctypes.byref(n_pairs),
+                                                           _ptr(tile_keys), _ptr(tile_ranges), _stream()))
+    return int(n_pairs.value)
 
 
 def render_fwd(gauss: torch.Tensor, canvas: Canvas, binning: Binning, out=None):

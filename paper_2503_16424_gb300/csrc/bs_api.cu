@@ -176,6 +176,26 @@ bs_status bs_bin_tiles(const float *gauss, int64_t n_gauss, const bs_canvas *can
   return run_binning(p, gauss, *canvas, ws, n_pairs_out, tile_keys, tile_ranges, (cudaStream_t)stream);
 }
 
+bs_status bs_bin_tiles_static(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, int64_t pair_capacity,
+                              int64_t *n_pairs_out, uint32_t *tile_keys, uint32_t *tile_ranges, bs_stream stream) {
+  BS_TRY(check_canvas(canvas));
+  if (!n_pairs_out) return invalid("n_pairs_out is NULL");
+  *n_pairs_out = 0;
+  BinPlan p;
+  BS_TRY(plan_binning(n_gauss, *canvas, pair_capacity, &p));
+  if (p.bytes > kStaticScratchBytes)
+    return invalid("this binning needs %zu bytes of scratch; the fixed scratch of bs_bin_tiles_static holds %zu "
+                   "(lower pair_capacity or n_gauss, or use bs_bin_tiles with a workspace)",
+                   p.bytes, kStaticScratchBytes);
+  if (n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  if (!tile_ranges || !aligned16(tile_ranges)) return invalid("tile_ranges must be an 8-byte aligned device pointer");
+  if (pair_capacity > 0 && !tile_keys) return invalid("tile_keys is NULL");
+  BS_TRY(check_device());
+  void *ws = nullptr;
+  BS_TRY(static_scratch(&ws));
+  return run_binning(p, gauss, *canvas, ws, n_pairs_out, tile_keys, tile_ranges, (cudaStream_t)stream);
+}
+
 bs_status bs_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, const uint32_t *tile_keys,
                         const uint32_t *tile_ranges, float *img, float *T_final, uint32_t *n_contrib,
                         bs_stream stream) {

@@ -636,6 +636,35 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   return BS_OK;
 }
 
+// ---- binning without caller-provided scratch ----
+// The scratch lives in one file-scope device array of kStaticScratchBytes,
+// which every GPU that loads the library holds until the process exits.
+// Host code may not pass the array's name to a kernel (on the host it only
+// names a stand-in); its device address is looked up once per device, with
+// that device current, and cached.
+namespace {
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_static_scratch_ptr[kMaxDevices] = {};
+}  // namespace
+
+bs_status static_scratch(void **ptr) {
+  int dev = 0;
+  BS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device %d: at most %d devices supported", dev, kMaxDevices);
+    return BS_ERR_UNSUPPORTED;
+  }
+  if (!g_static_scratch_ptr[dev]) {
+    void *p = nullptr;
+    BS_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_scratch_ptr[dev] = p;
+  }
+  *ptr = g_static_scratch_ptr[dev];
+  return BS_OK;
+}
+
 bs_status read_device_status(const void *ws, size_t ws_bytes, int32_t *out, cudaStream_t s) {
   if (ws_bytes < sizeof(Hdr)) {
     set_error("workspace too small");

@@ -75,6 +75,9 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
                       int64_t *n_pairs, uint32_t *tile_keys, uint32_t *tile_ranges,
                       cudaStream_t s);
 bs_status read_device_status(const void *ws, size_t ws_bytes, int32_t *out, cudaStream_t s);
+// Fixed scratch of bs_bin_tiles_static: 32 MiB of device memory per GPU.
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;
+bs_status static_scratch(void **ptr);
 
 // render (bs_render.cu)
 bs_status launch_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas &cv, int gbits,
