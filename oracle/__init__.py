@@ -16,6 +16,8 @@ Modules
   raster   Section 3.4: alpha blending (Eq. 9-10), per-pixel brute force
   binning  Section 3.4: tile rectangles and (tile, depth) keys
   loss     Section 3.5: the L2 term of Eq. 13
+  prune_densify  Section 3.5, Algorithm 1, Appendix B: pruning, splitting,
+           error regions and circular initialisation of new curves
 
 Parity pins: every function is pinned by a test in tests/test_oracle_*.py
 against closed forms, invariants, brute force or finite differences; none is
@@ -30,3 +32,4 @@ from .curves import (  # noqa: F401
 from .raster import render_pixels, render_image, render_grads  # noqa: F401
 from .binning import tile_rects_f32, tile_keys, key_bits  # noqa: F401
 from .loss import l2_loss  # noqa: F401
+from .prune_densify import PDCfg, prune_densify  # noqa: F401
