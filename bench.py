@@ -212,6 +212,21 @@ def run_ours(args, rank, world):
         e_ms = float(t.item())
     e2e_value = world * args.steps / (e_ms / 1e3)
 
+    # the periodic pass (every few hundred steps, outside the step): prune and
+    # densify a copy of the curves against the last rendered image
+    pd_curves = bs.CurveSet(**{k: getattr(curves, k).clone() for k in bs.CURVE_FIELDS})
+    pd_cfg = bs.PDCfg(step=200, t_end=1000)
+    pd_ms = []
+    for i in range(3):
+        pd_work = bs.CurveSet(**{k: getattr(pd_curves, k).clone() for k in bs.CURVE_FIELDS})
+        a, b = mk(), mk()
+        a.record(stream)
+        _, pd_stats = r.prune_densify(pd_work, target, pd_cfg)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            pd_ms.append(a.elapsed_time(b))
+
     peaks, src = load_peaks()
     clocks = clk.summary()
     fwd_avg, bwd_avg = float(np.mean(fwd_ms)), float(np.mean(bwd_ms))
@@ -244,6 +259,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": None,
         "clocks": clocks,
+        "periodic": {"prune_densify_ms": round(float(np.mean(pd_ms)), 4), "not_in_step": True, **pd_stats},
     }
     # kernels launched per step: curve_order 1, sample 1, bin (count, scan,
     # zero, emit, passes x onesweep, ranges), render_fwd 1, l2 1, render_bwd 1,

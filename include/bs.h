@@ -264,6 +264,97 @@ bs_status bs_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas *ca
                         const bs_curves *curves, const bs_sample_cfg *cfg,
                         const bs_curves_grad *grad, bs_stream stream);
 
+/* Curves that bs_prune_densify edits in place: the arrays of bs_curves,
+ * writable (device, same layouts). */
+typedef struct {
+  int32_t n_open;
+  int32_t n_closed;
+  float *open_ctrl;     /* [n_open][10][2] px  */
+  float *open_width;    /* [n_open]            */
+  float *open_color;    /* [n_open][3]         */
+  float *open_opac;     /* [n_open][3]         */
+  float *closed_ctrl;   /* [n_closed][12][2] px */
+  float *closed_color;  /* [n_closed][3]       */
+  float *closed_opac;   /* [n_closed]          */
+} bs_curves_mut;
+
+/* Parameters of one pruning and densification pass (Section 3.5,
+ * Algorithm 1, Appendix B).  Thresholds compare float32 values. */
+typedef struct {
+  float op_start;     /* opacity threshold at step 0, e.g. 0.2                */
+  float op_end;       /* opacity threshold from step t_end on, e.g. 0.02      */
+  int32_t step;       /* optimisation step of this pass, >= 0                 */
+  int32_t t_end;      /* step where the threshold reaches op_end, >= 1        */
+  float area_min;     /* px^2: a curve whose area key is below is pruned      */
+  float color_eps;    /* RGB distance below which two curves are similar      */
+  float iou_min;      /* box IoU above which a similar curve is redundant     */
+  float err_thresh;   /* a pixel is in error when its channel-mean |img - target| exceeds it */
+  float split_drop;   /* an open curve whose middle opacity is this far below
+                         both end opacities is split                          */
+  float new_opacity;  /* opacity of a new curve (every segment), in [0, 1]    */
+  float new_width;    /* width of a new open curve, px, > 0                   */
+} bs_pd_cfg;
+
+/* What one pass did (host struct, written). */
+typedef struct {
+  int32_t pruned;        /* curves removed (any criterion)                      */
+  int32_t low_opacity;   /* curves below the opacity threshold                  */
+  int32_t small_area;    /* curves below the area threshold                     */
+  int32_t overlap;       /* curves redundant with a similar curve in front      */
+  int32_t split;         /* open curves split                                   */
+  int32_t split_placed;  /* second halves written into a freed open slot        */
+  int32_t regions;       /* connected error regions found                       */
+  int32_t inserted;      /* new curves placed on error regions                  */
+  int32_t transparent;   /* freed slots left with opacity 0 (no region left)    */
+} bs_pd_stats;
+
+/* Workspace bytes bs_prune_densify needs.  Host arithmetic only. */
+bs_status bs_prune_densify_workspace(int32_t n_open, int32_t n_closed, const bs_canvas *canvas,
+                                     size_t *bytes);
+
+/*
+ * One pass of adaptive pruning and densification (Section 3.5, Algorithm 1;
+ * the split rule of Appendix B), in place on `curves`; the number of curves
+ * stays the same (the budget is constant).
+ * Pruning.  Curve i is removed when
+ *   - its opacity (closed: its opacity; open: ((o0 + o1) + o2) / 3) is below
+ *     tau = op_start (1 - f) + op_end f, f = min(1, step / t_end);
+ *   - its area key (the draw-order key of bs_curve_order) is below area_min;
+ *   - a curve j drawn in front of it (lower draw rank) has RGB distance
+ *     < color_eps and bounding-box IoU > iou_min.  Boxes are the control
+ *     points' box, widened by width / 2 on every side for an open curve.
+ * Splitting.  A kept open curve whose middle opacity is more than
+ * split_drop below both end opacities keeps its first segment, re-cut into
+ * three segments (de Casteljau at 1/3 and 2/3) with opacity o0; its last
+ * segment, cut the same way with opacity o2 and the curve's colour and
+ * width, goes into the lowest-index freed open slot not yet taken (split
+ * curves in index order); without a free open slot it is dropped.
+ * Densification.  Error map e = ((|d_r| + |d_g|) + |d_b|) / 3, d = img -
+ * target; regions are the 4-connected components of e > err_thresh, ranked
+ * by pixel count (descending), equal counts by their first pixel in
+ * row-major order.  The freed slots still empty, open ones first then closed
+ * ones, each in index order, receive the regions in rank order: control
+ * points on the circle around the region's centroid (pixel centres) of
+ * radius sqrt(count / pi) at angles 2 pi j / 12 (closed, j = 0..11) or
+ * 2 pi j / 11 (open, j = 0..9), colour = the region's mean target colour,
+ * opacity new_opacity, width new_width.  Freed slots left over keep their
+ * geometry with opacity 0.
+ *   img, target  [3][H][W] (device, read); canvas: width and height are used
+ *   ws, ws_bytes scratch of bs_prune_densify_workspace bytes (device)
+ *   changed_out  [n_open + n_closed] 1 where a curve was pruned, split,
+ *                replaced or made transparent, else 0 (device, written;
+ *                may be NULL)
+ *   stats_out    (HOST, may be NULL) counts of the pass
+ * n_open + n_closed <= 65536 (the pair test is quadratic).  The draw order
+ * (bs_curve_order) must be recomputed afterwards.  Synchronises the stream
+ * once, at the end.  BS_ERR_TIMEOUT if a bounded retry loop of the region
+ * labelling ran out (the curves are then unchanged only up to that point).
+ */
+bs_status bs_prune_densify(const bs_curves_mut *curves, const bs_pd_cfg *cfg,
+                           const bs_canvas *canvas, const float *img, const float *target,
+                           void *ws, size_t ws_bytes, uint8_t *changed_out,
+                           bs_pd_stats *stats_out, bs_stream stream);
+
 /* Synchronise the stream and read the device status word of a binning
  * workspace: BS_OK or the first kernel-side error recorded since the
  * workspace's last bs_bin_tiles call. */

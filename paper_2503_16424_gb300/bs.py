@@ -51,6 +51,25 @@ class bs_canvas(ctypes.Structure):
     _fields_ = [("width", c_int32), ("height", c_int32), ("tile", c_int32), ("bg", c_float * 3)]
 
 
+class bs_curves_mut(ctypes.Structure):
+    _fields_ = [("n_open", c_int32), ("n_closed", c_int32),
+                ("open_ctrl", c_void_p), ("open_width", c_void_p), ("open_color", c_void_p),
+                ("open_opac", c_void_p), ("closed_ctrl", c_void_p), ("closed_color", c_void_p),
+                ("closed_opac", c_void_p)]
+
+
+class bs_pd_cfg(ctypes.Structure):
+    _fields_ = [("op_start", c_float), ("op_end", c_float), ("step", c_int32), ("t_end", c_int32),
+                ("area_min", c_float), ("color_eps", c_float), ("iou_min", c_float),
+                ("err_thresh", c_float), ("split_drop", c_float), ("new_opacity", c_float),
+                ("new_width", c_float)]
+
+
+class bs_pd_stats(ctypes.Structure):
+    _fields_ = [(k, c_int32) for k in ("pruned", "low_opacity", "small_area", "overlap", "split",
+                                      "split_placed", "regions", "inserted", "transparent")]
+
+
 def _sig(name, *args):
     f = getattr(lib, name)
     f.argtypes = list(args)
@@ -75,6 +94,9 @@ _sig("bs_l2_loss_grad", _P, _P, c_int64, _P, _P, _P)
 _sig("bs_render_stats", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P, _P)
 _sig("bs_render_bwd", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P,
      POINTER(bs_curves), POINTER(bs_sample_cfg), POINTER(bs_curves_grad), _P)
+_sig("bs_prune_densify_workspace", c_int32, c_int32, POINTER(bs_canvas), POINTER(c_size_t))
+_sig("bs_prune_densify", POINTER(bs_curves_mut), POINTER(bs_pd_cfg), POINTER(bs_canvas), _P, _P, _P, c_size_t, _P,
+     POINTER(bs_pd_stats), _P)
 _sig("bs_device_status", _P, c_size_t, POINTER(c_int32), _P)
 _sig("bs_debug_sort_fault", c_int32, c_uint32)
 
@@ -185,6 +207,9 @@ class CurveSet:
 
     def grad_c(self):
         return bs_curves_grad(*(_ptr(getattr(self, k)) for k in CURVE_FIELDS))
+
+    def mut_c(self):
+        return bs_curves_mut(self.n_open, self.n_closed, *(_ptr(getattr(self, k)) for k in CURVE_FIELDS))
 
 
 def num_gaussians(n_open, n_closed, cfg: SampleCfg) -> int:
@@ -358,6 +383,56 @@ def render_bwd(gauss, canvas: Canvas, binning: Binning, T_final, n_contrib, dimg
                                                _ptr(binning.ranges), _ptr(T_final), _ptr(n_contrib),
                                                _ptr(dimg), _ptr(dgauss), cp, kp, gp, _stream()))
     return dgauss, grad
+
+
+@dataclass
+class PDCfg:
+    """Parameters of one pruning/densification pass (bs_pd_cfg)."""
+    op_start: float = 0.2
+    op_end: float = 0.02
+    step: int = 0
+    t_end: int = 1
+    area_min: float = 4.0
+    color_eps: float = 0.03
+    iou_min: float = 0.9
+    err_thresh: float = 0.1
+    split_drop: float = 0.5
+    new_opacity: float = 0.5
+    new_width: float = 2.0
+
+    def c(self):
+        return bs_pd_cfg(self.op_start, self.op_end, self.step, self.t_end, self.area_min, self.color_eps,
+                         self.iou_min, self.err_thresh, self.split_drop, self.new_opacity, self.new_width)
+
+
+def prune_densify_workspace(n_open: int, n_closed: int, canvas: Canvas) -> int:
+    cv = canvas.c()
+    nb = c_size_t(0)
+    _check("bs_prune_densify_workspace", lib.bs_prune_densify_workspace(n_open, n_closed, ctypes.byref(cv),
+                                                                         ctypes.byref(nb)))
+    return int(nb.value)
+
+
+def prune_densify(curves: CurveSet, img: torch.Tensor, target: torch.Tensor, cfg: PDCfg, canvas: Canvas,
+                  ws: torch.Tensor = None, changed: torch.Tensor = None):
+    """One pruning/densification pass, in place on `curves`.  Returns the
+    per-curve changed mask (uint8) and the pass's counts.  Synchronises."""
+    curves.check()
+    n = curves.n_open + curves.n_closed
+    shape = (3, canvas.height, canvas.width)
+    _want(img, torch.float32, shape, "img")
+    _want(target, torch.float32, shape, "target")
+    dev = img.device
+    nbytes = prune_densify_workspace(curves.n_open, curves.n_closed, canvas)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    changed = changed if changed is not None else torch.empty(max(1, n), dtype=torch.uint8, device=dev)
+    c, k, cv = curves.mut_c(), cfg.c(), canvas.c()
+    st = bs_pd_stats()
+    _check("bs_prune_densify", lib.bs_prune_densify(ctypes.byref(c), ctypes.byref(k), ctypes.byref(cv), _ptr(img),
+                                                     _ptr(target), _ptr(ws), ws.numel(), _ptr(changed),
+                                                     ctypes.byref(st), _stream()))
+    return changed[:n], {f: int(getattr(st, f)) for f, _ in bs_pd_stats._fields_}
 
 
 def debug_sort_fault(never_publish_partition: int = -1, spin_limit: int = 0):

@@ -1,5 +1,6 @@
 // The C ABI of libbs.so: argument validation on the host, then the launchers.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 
@@ -103,6 +104,24 @@ bs_status check_canvas(const bs_canvas *cv) {
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+bs_status check_pd_counts(int32_t n_open, int32_t n_closed) {
+  if (n_open < 0 || n_closed < 0) return invalid("negative curve count");
+  if ((int64_t)n_open + n_closed > kMaxPdCurves) return invalid("more than %d curves", kMaxPdCurves);
+  return BS_OK;
+}
+
+bs_status check_pd_cfg(const bs_pd_cfg *cfg) {
+  if (!cfg) return invalid("cfg is NULL");
+  if (cfg->step < 0 || cfg->t_end < 1) return invalid("step must be >= 0 and t_end >= 1");
+  const float v[] = {cfg->op_start, cfg->op_end, cfg->area_min, cfg->color_eps, cfg->iou_min,
+                     cfg->err_thresh, cfg->split_drop, cfg->new_opacity, cfg->new_width};
+  for (float x : v)
+    if (!isfinite(x)) return invalid("prune/densify thresholds must be finite");
+  if (!(cfg->new_opacity >= 0.f && cfg->new_opacity <= 1.f)) return invalid("new_opacity not in [0, 1]");
+  if (!(cfg->new_width > 0.f)) return invalid("new_width must be > 0");
+  return BS_OK;
+}
 
 }  // namespace
 
@@ -250,6 +269,34 @@ bs_status bs_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas *ca
                              n_contrib, dL_dimg, dgauss, s));
   if (grad) return bs_sample_curves_bwd(curves, cfg, dgauss, grad, stream);
   return BS_OK;
+}
+
+bs_status bs_prune_densify_workspace(int32_t n_open, int32_t n_closed, const bs_canvas *canvas, size_t *bytes) {
+  BS_TRY(check_canvas(canvas));
+  BS_TRY(check_pd_counts(n_open, n_closed));
+  if (!bytes) return invalid("bytes is NULL");
+  *bytes = prune_densify_bytes(n_open, n_closed, canvas->width, canvas->height);
+  return BS_OK;
+}
+
+bs_status bs_prune_densify(const bs_curves_mut *curves, const bs_pd_cfg *cfg, const bs_canvas *canvas,
+                           const float *img, const float *target, void *ws, size_t ws_bytes, uint8_t *changed_out,
+                           bs_pd_stats *stats_out, bs_stream stream) {
+  BS_TRY(check_canvas(canvas));
+  if (!curves) return invalid("curves is NULL");
+  BS_TRY(check_pd_counts(curves->n_open, curves->n_closed));
+  if (curves->n_open > 0 && (!curves->open_ctrl || !curves->open_width || !curves->open_color || !curves->open_opac))
+    return invalid("open curve arrays must be non-NULL when n_open > 0");
+  if (curves->n_closed > 0 && (!curves->closed_ctrl || !curves->closed_color || !curves->closed_opac))
+    return invalid("closed curve arrays must be non-NULL when n_closed > 0");
+  BS_TRY(check_pd_cfg(cfg));
+  if (!img || !target) return invalid("img and target must be non-NULL");
+  const size_t need = prune_densify_bytes(curves->n_open, curves->n_closed, canvas->width, canvas->height);
+  if (!ws || ws_bytes < need || !aligned16(ws))
+    return invalid("workspace of %zu bytes (16-byte aligned) needed, got %zu", need, ws_bytes);
+  BS_TRY(check_device());
+  return run_prune_densify(*curves, *cfg, canvas->width, canvas->height, img, target, ws, changed_out, stats_out,
+                           (cudaStream_t)stream);
 }
 
 bs_status bs_device_status(const void *ws, size_t ws_bytes, int32_t *status_out, bs_stream stream) {

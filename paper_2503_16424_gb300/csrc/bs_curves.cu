@@ -55,8 +55,6 @@ __device__ __forceinline__ double closed_tau(int r, int rows) {
   return 0.5 * (1.0 - cospi((double)r / (double)(rows - 1)));
 }
 
-__device__ __forceinline__ float2 ld2(const float *p, int i) { return make_float2(p[2 * i], p[2 * i + 1]); }
-
 __device__ __forceinline__ const float *curve_ctrl(const bs_curves &c, int curve) {
   return curve < c.n_open ? c.open_ctrl + (size_t)curve * 20 : c.closed_ctrl + (size_t)(curve - c.n_open) * 24;
 }
@@ -385,32 +383,7 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
 
 // ---- draw order ----
 __device__ __forceinline__ float area_key(const bs_curves &c, int i) {
-  if (i < c.n_open) {
-    const float *P = c.open_ctrl + (size_t)i * 20;
-    float acc = 0.f;
-    for (int j = 0; j < 9; ++j) {
-      const float dx = __fsub_rn(P[2 * j + 2], P[2 * j]);
-      const float dy = __fsub_rn(P[2 * j + 3], P[2 * j + 1]);
-      acc = __fadd_rn(acc, __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy))));
-    }
-    return __fmul_rn(acc, c.open_width[i]);
-  }
-  const float *P = c.closed_ctrl + (size_t)(i - c.n_open) * 24;
-  float acc = 0.f;
-  for (int j = 0; j < 12; ++j) {
-    const int jn = j == 11 ? 0 : j + 1;
-    const float cross = __fsub_rn(__fmul_rn(P[2 * j], P[2 * jn + 1]), __fmul_rn(P[2 * jn], P[2 * j + 1]));
-    acc = __fadd_rn(acc, cross);
-  }
-  return __fmul_rn(fabsf(acc), 0.5f);
-}
-
-// Order-preserving integer image of a float key (NaN last, -0 == +0).
-__device__ __forceinline__ uint32_t key_order(float k) {
-  if (k != k) return 0xffffffffu;
-  k = __fadd_rn(k, 0.0f);
-  const uint32_t b = __float_as_uint(k);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+  return curve_area_key(c.n_open, c.open_ctrl, c.open_width, c.closed_ctrl, i);
 }
 
 constexpr int kOrderThreads = 256;

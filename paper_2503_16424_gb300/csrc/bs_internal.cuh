@@ -47,6 +47,43 @@ inline int bit_length(uint64_t v) {
 }
 inline int gauss_bits(int64_t n_gauss) { return n_gauss > 1 ? bit_length((uint64_t)(n_gauss - 1)) : 1; }
 
+// ---- draw-order key (Section 3.3), shared by the draw order and pruning ----
+#ifdef __CUDACC__
+// Area key of curve i in float32, each operation rounded in order: a closed
+// curve's key is half the absolute shoelace sum of its 12-point control
+// polygon, an open curve's the length of its 10-point control polygon times
+// its width.  Curves i < n_open are open.
+__device__ __forceinline__ float curve_area_key(int n_open, const float *open_ctrl, const float *open_width,
+                                                const float *closed_ctrl, int i) {
+  if (i < n_open) {
+    const float *P = open_ctrl + (size_t)i * 20;
+    float acc = 0.f;
+    for (int j = 0; j < 9; ++j) {
+      const float dx = __fsub_rn(P[2 * j + 2], P[2 * j]);
+      const float dy = __fsub_rn(P[2 * j + 3], P[2 * j + 1]);
+      acc = __fadd_rn(acc, __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy))));
+    }
+    return __fmul_rn(acc, open_width[i]);
+  }
+  const float *P = closed_ctrl + (size_t)(i - n_open) * 24;
+  float acc = 0.f;
+  for (int j = 0; j < 12; ++j) {
+    const int jn = j == 11 ? 0 : j + 1;
+    const float cross = __fsub_rn(__fmul_rn(P[2 * j], P[2 * jn + 1]), __fmul_rn(P[2 * jn], P[2 * j + 1]));
+    acc = __fadd_rn(acc, cross);
+  }
+  return __fmul_rn(fabsf(acc), 0.5f);
+}
+
+// Order-preserving integer image of a float key (NaN last, -0 == +0).
+__device__ __forceinline__ uint32_t key_order(float k) {
+  if (k != k) return 0xffffffffu;
+  k = __fadd_rn(k, 0.0f);
+  const uint32_t b = __float_as_uint(k);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+#endif
+
 // ---- launchers (one per translation unit) ----
 // curves (bs_curves.cu)
 bs_status launch_curve_order(const bs_curves &c, const bs_sample_cfg &cfg, uint32_t *rank,
@@ -90,5 +127,12 @@ bs_status launch_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas
                             cudaStream_t s);
 bs_status launch_l2(const float *img, const float *target, int64_t n, float *dimg, double *loss,
                     cudaStream_t s);
+
+// pruning and densification (bs_prune.cu)
+constexpr int kMaxPdCurves = 65536;
+size_t prune_densify_bytes(int n_open, int n_closed, int width, int height);
+bs_status run_prune_densify(const bs_curves_mut &c, const bs_pd_cfg &cfg, int width, int height,
+                            const float *img, const float *target, void *ws, uint8_t *changed,
+                            bs_pd_stats *stats, cudaStream_t s);
 
 }  // namespace bs

@@ -5,7 +5,10 @@ counts, sampling) and runs the hot path call by call:
   bs_curve_order -> bs_sample_curves -> bs_bin_tiles -> bs_render_fwd
   -> bs_l2_loss_grad -> bs_render_bwd (render backward + sampling backward).
 Only the blend state T_final/n_contrib (8 bytes per pixel) is kept between
-forward and backward; everything per Gaussian is recomputed.
+forward and backward; everything per Gaussian is recomputed.  Every few
+hundred steps ``prune_densify`` edits the curve set in place against the
+last rendered image (bs_prune_densify); the next forward recomputes the
+draw order.
 """
 
 from __future__ import annotations
@@ -34,6 +37,7 @@ class Rasterizer:
         self.loss = torch.empty((), dtype=torch.float64, device=device)
         self.binning = Binning(canvas, device, pair_capacity)
         self.rank = self.first = None
+        self.pd_ws = None
 
     def forward(self, curves: CurveSet):
         self.rank, self.first = bs.curve_order(curves, self.cfg)
@@ -54,6 +58,16 @@ class Rasterizer:
         bs.l2_loss_grad(self.img, target, dimg=self.dimg, loss=self.loss)
         grad = self.backward(curves, self.dimg, grad)
         return self.loss, grad
+
+
+    def prune_densify(self, curves: CurveSet, target: torch.Tensor, cfg: bs.PDCfg, img: torch.Tensor = None):
+        """One pruning/densification pass against `img` (default: the last
+        forward's image).  Returns (changed mask, counts)."""
+        img = self.img if img is None else img
+        if self.pd_ws is None:
+            n = bs.prune_densify_workspace(self.n_open, self.n_closed, self.canvas)
+            self.pd_ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return bs.prune_densify(curves, img, target, cfg, self.canvas, ws=self.pd_ws)
 
 
 class BezierRasterize(torch.autograd.Function):

@@ -163,6 +163,62 @@ def lowfreq_noise(seed: int, W: int, H: int, amp: float = 0.1, grid: int = 8):
     return out.astype(np.float32)
 
 
+def prune_inputs(seed: int, W: int, H: int, n_open: int, n_closed: int, n_blobs: int = 40,
+                 frac: float = 0.06, n_shapes: int = 40):
+    """Inputs of a pruning/densification pass: a "local" curve set in which
+    about `frac` of the curves each get low opacities, a shrunken outline
+    (closed curves), a near-copy of another curve (geometry jittered by
+    N(0, 0.2) px, colour by N(0, 0.004)), or a faint middle segment (open
+    curves); a procedural target; and an image equal to the target plus
+    U[-0.02, 0.02] noise and `n_blobs` filled ellipses offset by U[0.3, 0.6]
+    per channel (the error regions).  Returns (curve dict, img, target)."""
+    c = make_curves(seed, W, H, n_open, n_closed, style="local").as_dict()
+    c = {k: v.copy() for k, v in c.items()}
+    r_pick, r_val, r_img = _rngs(seed + 7919, 3)
+    oo, co = c["open_opac"], c["closed_opac"]
+    low_o = r_pick.random(n_open) < frac
+    oo[low_o] = r_val.uniform(0.0, 0.15, (int(low_o.sum()), 3))
+    low_c = r_pick.random(n_closed) < frac
+    co[low_c] = r_val.uniform(0.0, 0.18, int(low_c.sum()))
+    small = r_pick.random(n_closed) < frac
+    cc = c["closed_ctrl"]
+    ctr = cc[small].mean(1, keepdims=True)
+    cc[small] = ctr + (cc[small] - ctr) * np.float32(0.02)
+    dip = r_pick.random(n_open) < frac
+    k = int(dip.sum())
+    oo[dip] = np.stack([r_val.uniform(0.8, 1.0, k), r_val.uniform(0.0, 0.25, k), r_val.uniform(0.8, 1.0, k)], 1)
+    for kind, ctrl_key, extra in (("open", "open_ctrl", ("open_width", "open_opac")),
+                                  ("closed", "closed_ctrl", ("closed_opac",))):
+        n = n_open if kind == "open" else n_closed
+        col_key = kind + "_color"
+        if n < 2:
+            continue
+        dst = np.nonzero(r_pick.random(n) < frac)[0]
+        src = r_pick.integers(0, n, dst.shape[0])
+        keep = src != dst
+        dst, src = dst[keep], src[keep]
+        c[ctrl_key][dst] = c[ctrl_key][src] + r_val.normal(0, 0.2, c[ctrl_key][src].shape).astype(np.float32)
+        c[col_key][dst] = c[col_key][src] + r_val.normal(0, 0.004, (dst.shape[0], 3)).astype(np.float32)
+        for e in extra:
+            c[e][dst] = c[e][src]
+    target = procedural_target(seed, W, H, n_shapes)
+    img = target + r_img.uniform(-0.02, 0.02, target.shape).astype(np.float32)
+    side = min(W, H)
+    for _ in range(n_blobs):
+        cx, cy = r_img.uniform(0, W), r_img.uniform(0, H)
+        ax, ay = np.exp(r_img.uniform(np.log(0.005 * side + 0.5), np.log(0.06 * side + 1), 2))
+        x0, x1 = int(max(0, np.floor(cx - ax))), int(min(W, np.ceil(cx + ax) + 1))
+        y0, y1 = int(max(0, np.floor(cy - ay))), int(min(H, np.ceil(cy + ay) + 1))
+        off = r_img.uniform(0.3, 0.6, 3) * r_img.choice([-1.0, 1.0], 3)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        ys, xs = np.mgrid[y0:y1, x0:x1].astype(np.float64)
+        m = ((xs + 0.5 - cx) / ax) ** 2 + ((ys + 0.5 - cy) / ay) ** 2 <= 1.0
+        for ch in range(3):
+            img[ch, y0:y1, x0:x1][m] += np.float32(off[ch])
+    return c, np.ascontiguousarray(img, dtype=np.float32), target
+
+
 # The workloads, by what they are.
 WORKLOADS = {
     # 256x256, 64 open curves, 16 Gaussians per curve, 16x16 tiles

@@ -76,3 +76,33 @@ def test_binding_refuses_cpu_tensors(bs):
     import torch
     with pytest.raises(TypeError):
         bs.CurveSet(*(torch.zeros(0, 10, 2),) * 7).check()
+
+
+def test_prune_densify_host_validation(bs):
+    cv = bs.Canvas(64, 48).c()
+    nb = ctypes.c_size_t(0)
+    assert bs.lib.bs_prune_densify_workspace(10, 5, ctypes.byref(cv), ctypes.byref(nb)) == bs.BS_OK
+    small = nb.value
+    assert small >= 64 * 48 * (4 + 4 + 4)           # labels, counts, region keys
+    bs.lib.bs_prune_densify_workspace(10, 5000, ctypes.byref(cv), ctypes.byref(nb))
+    assert nb.value > small
+    assert bs.lib.bs_prune_densify_workspace(40000, 30000, ctypes.byref(cv), ctypes.byref(nb)) == \
+        bs.BS_ERR_INVALID_ARG
+    cfg = bs.PDCfg().c()
+    curves = bs.bs_curves_mut(3, 0, None, None, None, None, None, None, None)
+    st = bs.lib.bs_prune_densify(ctypes.byref(curves), ctypes.byref(cfg), ctypes.byref(cv), None, None, None, 0,
+                                 None, None, None)
+    assert st == bs.BS_ERR_INVALID_ARG and b"open curve arrays" in bs.lib.bs_last_error()
+    empty = bs.bs_curves_mut(0, 0, None, None, None, None, None, None, None)
+    for bad in (bs.PDCfg(t_end=0), bs.PDCfg(step=-1), bs.PDCfg(new_width=0.0), bs.PDCfg(new_opacity=1.5),
+                bs.PDCfg(err_thresh=float("nan"))):
+        c = bad.c()
+        assert bs.lib.bs_prune_densify(ctypes.byref(empty), ctypes.byref(c), ctypes.byref(cv), None, None, None,
+                                       0, None, None, None) == bs.BS_ERR_INVALID_ARG
+    # no image, then too small a workspace
+    assert bs.lib.bs_prune_densify(ctypes.byref(empty), ctypes.byref(cfg), ctypes.byref(cv), None, None, None, 0,
+                                   None, None, None) == bs.BS_ERR_INVALID_ARG
+    fake = ctypes.c_void_p(1 << 20)
+    assert bs.lib.bs_prune_densify(ctypes.byref(empty), ctypes.byref(cfg), ctypes.byref(cv), fake, fake, fake, 16,
+                                   None, None, None) == bs.BS_ERR_INVALID_ARG
+    assert b"workspace" in bs.lib.bs_last_error()
