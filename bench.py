@@ -34,6 +34,11 @@ FP32_FLOP_PER_FWD_EVAL = 22     # per (pixel, list entry) evaluation, forward
 FP32_FLOP_PER_BWD_EVAL = 55     # per (pixel, list entry) evaluation, backward
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one launch of each render kernel on this
+# workload, from one ncu capture of the current kernel
+# (profiles/render_bwd_kernel_hires_2048_4096.md); None where no capture of
+# the current kernel exists.
+DRAM_BYTES_PER_LAUNCH = {"render_bwd_kernel": 131342336, "render_fwd_kernel": None}
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
@@ -249,7 +254,7 @@ def run_ours(args, rank, world):
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": round(ach, 3),
                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-                     "traffic": None,
+                     "traffic": DRAM_BYTES_PER_LAUNCH.get(dom),
                      "peak_source": f"FP32 {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                     f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)"},
         "kernels_ms": {"render_fwd": round(fwd_avg, 4), "render_bwd": round(bwd_avg, 4)},
@@ -261,11 +266,13 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "periodic": {"prune_densify_ms": round(float(np.mean(pd_ms)), 4), "not_in_step": True, **pd_stats},
     }
-    # kernels launched per step: curve_order 1, sample 1, bin (count, scan,
-    # zero, emit, passes x onesweep, ranges), render_fwd 1, l2 1, render_bwd 1,
-    # sample_bwd 1 (memsets are not kernels)
+    # kernels launched per step: curve_order 2 (count, first), sample 1,
+    # binning 8 + sort passes (zero, count, scan_partials, chunk_owner,
+    # diff_rows, diff_cols, tile_scan, emit, onesweep x passes), render_fwd 1,
+    # l2 1, render_bwd 2 (blend backward, grads_from_sums), sample_bwd 1;
+    # memsets are not kernels
     passes = -(-max(1, (canvas.n_tiles - 1).bit_length()) // 8)
-    per_step = 1 + 1 + (5 + passes) + 1 + 1 + 1 + 1
+    per_step = 2 + 1 + (8 + passes) + 1 + 1 + 2 + 1
     out["gpu_launches"] = per_step * args.steps
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(side=8)

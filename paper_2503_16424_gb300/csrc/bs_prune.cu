@@ -13,7 +13,8 @@
 //   union_kernel     vertical links between runs: lock-free union-find
 //                    whose roots are the smallest pixel index (atomicMin)
 //   heads_kernel     run heads point to their root
-//   flatten_kernel   every pixel to its root; pixel count per root
+//   flatten_kernel   every pixel to its root; pixel count per root (warp-
+//                    aggregated atomics)
 //   roots_kernel     one 64-bit key per region: (count descending, root)
 //   select_*         radix select (8 x 8 bits) of the n-th smallest key
 //   gather/rank      the selected keys, ranked by counting (keys are unique)
@@ -299,6 +300,7 @@ __global__ void runs_kernel(const float *img, const float *tgt, int W, int H, fl
   const size_t P = (size_t)W * H;
   const int row = y * W;
   int carry = -1;  // run start of the pixel left of this chunk, -1 if not in the mask
+#pragma unroll 4
   for (int x0 = 0; x0 < W; x0 += 32) {
     const int x = x0 + lane;
     const bool in = x < W && in_error(img, tgt, P, (size_t)row + x, thr);
@@ -370,31 +372,55 @@ __global__ void heads_kernel(int W, int64_t P, int32_t *L) {
   L[p] = find_root(L, (int)p);
 }
 
-// Every pixel to its root (head -> root); pixel counts per root, one atomic
-// per run piece.
+// A warp covers kWarpPx consecutive pixels of one row, lane l the pixels
+// x0 + l + 32 k (coalesced).  Each lane accumulates while its root stays the
+// same; at the end the lanes holding the same root add up their partial
+// sums and one lane issues the atomics, so a large region costs one atomic
+// per warp instead of one per pixel run.
+constexpr int kWarpPx = 32 * kSegPx;
+
+__device__ __forceinline__ int64_t warp_chunk(int W, int H, int *y, int *x0) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int cpr = (W + kWarpPx - 1) / kWarpPx;
+  if (w >= (int64_t)cpr * H) return -1;
+  *y = (int)(w / cpr);
+  *x0 = (int)(w % cpr) * kWarpPx;
+  return w;
+}
+
+// Every pixel to its root (head -> root); pixel counts per root.
 __global__ void flatten_kernel(int W, int H, int32_t *L, uint32_t *area) {
-  const int segs = (W + kSegPx - 1) / kSegPx;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)segs * H) return;
-  const int y = (int)(t / segs), xs = (int)(t % segs) * kSegPx;
-  const int xe = min(W, xs + kSegPx);
+  int y, x0;
+  if (warp_chunk(W, H, &y, &x0) < 0) return;  // whole warps leave together
+  const int lane = threadIdx.x & 31;
   int cur = -1;
   uint32_t cnt = 0;
-  for (int x = xs; x < xe; ++x) {
-    const size_t p = (size_t)y * W + x;
-    const int l = L[p];
-    const int root = l < 0 ? -1 : L[l];
+  for (int k = 0; k < kSegPx; ++k) {
+    const int x = x0 + lane + 32 * k;
+    int root = -1;
+    if (x < W) {
+      const size_t p = (size_t)y * W + x;
+      const int l = L[p];
+      if (l >= 0) {
+        root = L[l];
+        L[p] = root;
+      }
+    }
     if (root != cur) {
       if (cur >= 0) atomicAdd(area + cur, cnt);
       cur = root;
       cnt = 0;
     }
-    if (root >= 0) {
-      L[p] = root;
-      ++cnt;
-    }
+    if (root >= 0) ++cnt;
   }
-  if (cur >= 0) atomicAdd(area + cur, cnt);
+  for (uint32_t pending = __ballot_sync(0xffffffffu, cur >= 0); pending;) {
+    const int leader = __ffs(pending) - 1;
+    const int r = __shfl_sync(0xffffffffu, cur, leader);
+    const bool mine = cur == r;
+    const uint32_t sum = __reduce_add_sync(0xffffffffu, mine ? cnt : 0u);
+    if (lane == leader) atomicAdd(area + r, sum);
+    pending &= ~__ballot_sync(0xffffffffu, mine);
+  }
 }
 
 // key = (0xffffffff - count) << 32 | root: ascending keys = count
@@ -501,42 +527,53 @@ __global__ void __launch_bounds__(kThreads) rank_sel_kernel(const unsigned long 
   }
 }
 
-// Sums over the pixels of each selected region, one atomic set per run piece.
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sums over the pixels of each selected region (same warp layout and
+// aggregation as flatten_kernel).
 __global__ void sums_kernel(const float *tgt, int W, int H, const int32_t *L, const uint32_t *area,
                             RegionAcc *acc) {
-  const int segs = (W + kSegPx - 1) / kSegPx;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)segs * H) return;
+  int y, x0;
+  if (warp_chunk(W, H, &y, &x0) < 0) return;
+  const int lane = threadIdx.x & 31;
   const size_t P = (size_t)W * H;
-  const int y = (int)(t / segs), xs = (int)(t % segs) * kSegPx;
-  const int xe = min(W, xs + kSegPx);
   int cur = -1;
   unsigned long long sx = 0, sy = 0;
   double r = 0, g = 0, b = 0;
-  auto flush = [&]() {
-    if (cur < 0) return;
-    RegionAcc *a = acc + cur;
-    atomicAdd(&a->sx, sx);
-    atomicAdd(&a->sy, sy);
-    atomicAdd(&a->r, r);
-    atomicAdd(&a->g, g);
-    atomicAdd(&a->b, b);
-  };
-  for (int x = xs; x < xe; ++x) {
-    const size_t p = (size_t)y * W + x;
-    const int l = L[p];
-    int k = -1;
-    if (l >= 0) {
-      const uint32_t v = area[l];
-      if (v & kSelected) k = (int)(v & ~kSelected);
+  for (int k = 0; k < kSegPx; ++k) {
+    const int x = x0 + lane + 32 * k;
+    int sel = -1;
+    size_t p = 0;
+    if (x < W) {
+      p = (size_t)y * W + x;
+      const int l = L[p];
+      if (l >= 0) {
+        const uint32_t v = area[l];
+        if (v & kSelected) sel = (int)(v & ~kSelected);
+      }
     }
-    if (k != cur) {
-      flush();
-      cur = k;
+    if (sel != cur) {
+      if (cur >= 0) {
+        RegionAcc *a = acc + cur;
+        atomicAdd(&a->sx, sx);
+        atomicAdd(&a->sy, sy);
+        atomicAdd(&a->r, r);
+        atomicAdd(&a->g, g);
+        atomicAdd(&a->b, b);
+      }
+      cur = sel;
       sx = sy = 0;
       r = g = b = 0;
     }
-    if (k >= 0) {
+    if (sel >= 0) {
       sx += (unsigned long long)x;
       sy += (unsigned long long)y;
       r += (double)tgt[p];
@@ -544,7 +581,22 @@ __global__ void sums_kernel(const float *tgt, int W, int H, const int32_t *L, co
       b += (double)tgt[2 * P + p];
     }
   }
-  flush();
+  for (uint32_t pending = __ballot_sync(0xffffffffu, cur >= 0); pending;) {
+    const int leader = __ffs(pending) - 1;
+    const int k = __shfl_sync(0xffffffffu, cur, leader);
+    const bool mine = cur == k;
+    const unsigned long long tx = warp_sum_u64(mine ? sx : 0ull), ty = warp_sum_u64(mine ? sy : 0ull);
+    const double tr = warp_sum_d(mine ? r : 0.0), tg = warp_sum_d(mine ? g : 0.0), tb = warp_sum_d(mine ? b : 0.0);
+    if (lane == leader) {
+      RegionAcc *a = acc + k;
+      atomicAdd(&a->sx, tx);
+      atomicAdd(&a->sy, ty);
+      atomicAdd(&a->r, tr);
+      atomicAdd(&a->g, tg);
+      atomicAdd(&a->b, tb);
+    }
+    pending &= ~__ballot_sync(0xffffffffu, mine);
+  }
 }
 
 // ---- edits ----
@@ -691,7 +743,7 @@ bs_status run_prune_densify(const bs_curves_mut &cm, const bs_pd_cfg &cfg, int W
   BS_LAUNCHED("prune union_kernel");
   heads_kernel<<<pb, kThreads, 0, s>>>(W, P, label);
   BS_LAUNCHED("prune heads_kernel");
-  const int64_t seg_threads = (int64_t)div_up(W, kSegPx) * H;
+  const int64_t seg_threads = (int64_t)div_up(W, kWarpPx) * H * 32;
   const unsigned sb = (unsigned)div_up64(seg_threads, kThreads);
   flatten_kernel<<<sb, kThreads, 0, s>>>(W, H, label, area);
   BS_LAUNCHED("prune flatten_kernel");
