@@ -106,6 +106,21 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's x (a collective only when world > 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, ms: float) -> float:
+    """Steps of all replicas per second of the slowest rank's clock."""
+    return world * steps / (ms / 1e3)
+
+
 def make_problem(device):
     import torch
     from paper_2503_16424_gb300 import bs, synth
@@ -174,14 +189,11 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
     fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
     bwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = job_throughput(world, args.steps, ms)
 
     # end to end through the public API with host buffers: H2D of the step's
     # inputs (curves + target) from pinned memory, D2H of loss and gradients
@@ -210,12 +222,8 @@ def run_ours(args, rank, world):
     e0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
-    e_ms = (time.perf_counter() - e0) * 1e3
-    if world > 1:
-        t = torch.tensor([e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e_ms = float(t.item())
-    e2e_value = world * args.steps / (e_ms / 1e3)
+    e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3, world, dev)
+    e2e_value = job_throughput(world, args.steps, e_ms)
 
     # the periodic pass (every few hundred steps, outside the step): prune and
     # densify a copy of the curves against the last rendered image
