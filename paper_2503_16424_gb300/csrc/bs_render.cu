@@ -229,8 +229,11 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
     c0[i] = c1[i] = c2[i] = 0.f;
     last[i] = 0;
   }
+  __shared__ uint32_t s_alive[2];  // per warp: slots (8x4 blocks) with a pixel still blending
   unsigned alive = tp.inside;
   for (uint32_t base = r.x; base < r.y; base += kBatch) {
+    const uint32_t walive = __reduce_or_sync(0xffffffffu, alive);
+    if ((threadIdx.x & 31) == 0) s_alive[threadIdx.x >> 5] = walive;
     if (__syncthreads_count(alive != 0) == 0) break;
     const uint32_t i = base + threadIdx.x;
     uint32_t my_bits = 0u;
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
-      my_bits = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
+      my_bits = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0) & (s_alive[0] | (s_alive[1] << 4));
       s_bits[threadIdx.x] = my_bits;
     }
     compact_lists(my_bits, s_list, s_cnt);
@@ -311,21 +314,41 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
   }
 }
 
-// Sum 16 values over the warp, scattered: lane L returns the total of value
-// L >> 1 (lanes 2i and 2i+1 both hold total i).  16 shuffles instead of the
-// 80 of 16 butterfly all-reduces.
-__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
+// Sum 9 values over the warp, scattered: each lane gets the total of value
+// scatter9_index(lane) (< 0: a padding slot; lanes 2i and 2i+1 hold the
+// same total).  Recursive halving on lane bits 16, 8, 4, 2 keeps the lower
+// half of the values on lanes with the bit clear and the upper half on the
+// others (9 -> 5 -> 3 -> 2 -> 1 values, padded with zeros), then the pair
+// exchange: 5 + 3 + 2 + 1 + 1 = 12 shuffles.
+template <int N, int OFF>
+__device__ __forceinline__ void halve(const float *in, float *out, int lane) {
+  constexpr int H = (N + 1) / 2;
+  const bool hi = (lane & OFF) != 0;
 #pragma unroll
-  for (int stage = 0, half = 8, off = 16; stage < 4; ++stage, half >>= 1, off >>= 1) {
-    const bool hi = (lane & off) != 0;
-#pragma unroll
-    for (int k = 0; k < half; ++k) {
-      const float send = hi ? v[k] : v[k + half];
-      const float keep = hi ? v[k + half] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
+  for (int k = 0; k < H; ++k) {
+    const float lo_v = in[k], hi_v = k + H < N ? in[k + H] : 0.f;
+    const float send = hi ? lo_v : hi_v, keep = hi ? hi_v : lo_v;
+    out[k] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
   }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ float warp_reduce_scatter9(const float v[9], int lane) {
+  float a[5], b[3], c[2], d[1];
+  halve<9, 16>(v, a, lane);
+  halve<5, 8>(a, b, lane);
+  halve<3, 4>(b, c, lane);
+  halve<2, 2>(c, d, lane);
+  return d[0] + __shfl_xor_sync(0xffffffffu, d[0], 1);
+}
+
+// The value whose total warp_reduce_scatter9 leaves on `lane`, -1 for none.
+__device__ __forceinline__ int scatter9_index(int lane) {
+  const int x = (((lane >> 2) & 1) ? 2 : 0) + ((lane >> 1) & 1);
+  if (x > 2) return -1;
+  const int w = (((lane >> 3) & 1) ? 3 : 0) + x;
+  if (w > 4) return -1;
+  const int v = (((lane >> 4) & 1) ? 5 : 0) + w;
+  return v > 8 ? -1 : v;
 }
 
 // Number of per-Gaussian sums the backward accumulates (see render_bwd_kernel).
@@ -360,6 +383,7 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
   __shared__ uint8_t s_list[2][2][32];  // [consumer warp][staging warp][k]: entries reaching the warp
   __shared__ uint32_t s_cnt[2][2];
   __shared__ uint32_t s_max_last;
+  __shared__ uint32_t s_wlast[2][kPix];
   const int tile = blockIdx.x;
   const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
   const uint2 r = ranges[tile];
@@ -387,6 +411,14 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
     gS[q] = g0[q] * bg.x + g1[q] * bg.y + g2[q] * bg.z;  // g . S, S = bg behind the last blended Gaussian
   }
   atomicMax(&s_max_last, my_max);
+  // per warp and slot (8x4 block), the deepest last entry of its pixels: an
+  // entry at or past it is left out of that block when it is staged
+#pragma unroll
+  for (int q = 0; q < kPix; ++q) {
+    const uint32_t wl = __reduce_max_sync(0xffffffffu, last[q]);
+    if (lane == 0) s_wlast[threadIdx.x >> 5][q] = wl;
+  }
+  const int sum_idx = (lane & 1) ? -1 : scatter9_index(lane);
   __syncthreads();
   const uint32_t max_last = min(s_max_last, r.y - r.x);
   for (uint32_t end = max_last; end > 0;) {
@@ -402,6 +434,9 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
       s_c[threadIdx.x] = s.c;
       s_g[threadIdx.x] = g;
       my_bits = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
+#pragma unroll
+      for (int b = 0; b < 2 * kPix; ++b)
+        if (i >= s_wlast[b >> 2][b & 3]) my_bits &= ~(1u << b);
       s_bits[threadIdx.x] = my_bits;
     }
     compact_lists(my_bits, s_list, s_cnt);
@@ -410,8 +445,8 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
     for (int sw = 1; sw >= 0; --sw)
     for (int k = (int)s_cnt[cw][sw] - 1; k >= 0; --k) {
       const int j = s_list[cw][sw][k];
-      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform, not 0
       const uint32_t pos = start + (uint32_t)j;
+      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform, not 0
       const float4 a = s_a[j], b = s_b[j];
       const float2 gb = s_c[j];
       float dx[2], b1dy[2], b2dy[2];
@@ -422,9 +457,9 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
         b1dy[k] = __fmul_rn(a.w, dy);
         b2dy[k] = __fmul_rn(b.y, dy);
       }
-      float v[16];
+      float v[kSums];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = 0.f;
+      for (int q = 0; q < kSums; ++q) v[q] = 0.f;
       bool contrib = false;
 #pragma unroll
       for (int q = 0; q < kPix; ++q) {
@@ -457,11 +492,10 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-        const float tot = warp_reduce_scatter16(v, lane);
-        const int k = lane >> 1;
+        const float tot = warp_reduce_scatter9(v, lane);
         const uint32_t g = s_g[j];
-        if ((lane & 1) == 0 && k < kSums && tot != 0.f && g < n_gauss)
-          atomicAdd(sums + (size_t)g * BS_DGAUSS_FLOATS + k, tot);
+        if (sum_idx >= 0 && tot != 0.f && g < n_gauss)
+          atomicAdd(sums + (size_t)g * BS_DGAUSS_FLOATS + sum_idx, tot);
       }
     }
     end = start;
