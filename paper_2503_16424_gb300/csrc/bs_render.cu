@@ -87,19 +87,21 @@ __device__ __forceinline__ Staged stage(const float *__restrict__ gauss, uint32_
 // Smallest t1^2 + t2^2 over the rectangle [dx0, dx1] x [dy0, dy1] of offsets
 // from the mean: 0 if the mean is inside, else the least value on the four
 // edges (a convex quadratic restricted to a segment, minimised in closed
-// form and clamped).
-__device__ __forceinline__ float min_q_rect(float A1, float B1, float A2, float B2, float axx, float byy,
-                                            float axy, float dx0, float dx1, float dy0, float dy1) {
+// form and clamped).  r_axx = -axy / axx and r_byy = -axy / byy give the
+// minimising coordinate on an edge; any point of the edge bounds the minimum
+// from above, so rounding in them only makes the test more conservative.
+__device__ __forceinline__ float min_q_rect(float A1, float B1, float A2, float B2, float r_axx, float r_byy,
+                                            float dx0, float dx1, float dy0, float dy1) {
   if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
   float best = INFINITY;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     const float X = e ? dx1 : dx0;
-    const float y = fminf(fmaxf(-axy * X / byy, dy0), dy1);
+    const float y = fminf(fmaxf(r_byy * X, dy0), dy1);
     const float t1 = A1 * X + B1 * y, t2 = A2 * X + B2 * y;
     best = fminf(best, t1 * t1 + t2 * t2);
     const float Y = e ? dy1 : dy0;
-    const float x = fminf(fmaxf(-axy * Y / axx, dx0), dx1);
+    const float x = fminf(fmaxf(r_axx * Y, dx0), dx1);
     const float u1 = A1 * x + B1 * Y, u2 = A2 * x + B2 * Y;
     best = fminf(best, u1 * u1 + u2 * u2);
   }
@@ -132,6 +134,8 @@ __device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, flo
   const float lim = thr + (1e-2f + 1e-4f * thr);
   const float A1 = s.a.z, B1 = s.a.w, A2 = s.b.x, B2 = s.b.y;
   const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
+  // axx, byy > 0 for a staged Gaussian (isx, isy > 0 and (ux, uy) a unit vector)
+  const float r_axx = axx > 0.f ? -axy * __frcp_rn(axx) : 0.f, r_byy = byy > 0.f ? -axy * __frcp_rn(byy) : 0.f;
   uint32_t bits = 0u;
   while (cand) {
     const int b = __ffs(cand) - 1;
@@ -139,7 +143,7 @@ __device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, flo
     const int br = b >> 1, bc = b & 1;
     const float dy0 = ((float)(y0 + 4 * br) + 0.5f) - s.a.y, dy1 = ((float)(y0 + 4 * br) + 3.5f) - s.a.y;
     const float dx0 = ((float)(x0 + 8 * bc) + 0.5f) - s.a.x, dx1 = ((float)(x0 + 8 * bc) + 7.5f) - s.a.x;
-    if (min_q_rect(A1, B1, A2, B2, axx, byy, axy, dx0, dx1, dy0, dy1) <= lim) bits |= 1u << b;
+    if (min_q_rect(A1, B1, A2, B2, r_axx, r_byy, dx0, dx1, dy0, dy1) <= lim) bits |= 1u << b;
   }
   return bits;
 }
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
       const int j = s_list[cw][sw][k];
       const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform, not 0
       const float4 a = s_a[j], b = s_b[j];
+      const float2 gb = s_c[j];
       float dx[2], b1dy[2], b2dy[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
@@ -277,7 +282,6 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
           continue;
         }
         const float w = al * T[q];
-        const float2 gb = s_c[j];
         c0[q] = __fmaf_rn(w, b.w, c0[q]);
         c1[q] = __fmaf_rn(w, gb.x, c1[q]);
         c2[q] = __fmaf_rn(w, gb.y, c2[q]);
@@ -464,32 +468,30 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
 #pragma unroll
       for (int q = 0; q < kPix; ++q) {
         if (!(bits & (1u << q))) continue;   // warp-uniform: block q not reached
-        if (pos >= last[q]) continue;
+        // branch-free per pixel: a pixel past its last blended Gaussian, or
+        // below the alpha threshold, gets alpha = 0, an exact no-op below
         float t1, t2;
         const float raw = ex2_approx(pixel_log2_alpha(a, b, dx[q & 1], b1dy[q >> 1], b2dy[q >> 1], t1, t2));
-        const float al = fminf(kAlphaMax, raw);
-        if (al < kAlphaMin) continue;
-        contrib = true;
-        const float one_m = 1.f - al;
-        T[q] = __fdividef(T[q], one_m);          // T before this Gaussian
+        const float al0 = fminf(kAlphaMax, raw);
+        const bool on = pos < last[q] && al0 >= kAlphaMin;
+        const float al = on ? al0 : 0.f;
+        contrib |= on;
+        T[q] = on ? __fdividef(T[q], 1.f - al) : T[q];  // T before this Gaussian
         const float w = al * T[q];
         const float gc = __fmaf_rn(g2[q], gb.y, __fmaf_rn(g1[q], gb.x, g0[q] * b.w));
         const float diff = gc - gS[q];
-        const float dal = T[q] * diff;            // dL/dalpha
         gS[q] = __fmaf_rn(al, diff, gS[q]);
         v[6] = __fmaf_rn(w, g0[q], v[6]);
         v[7] = __fmaf_rn(w, g1[q], v[7]);
         v[8] = __fmaf_rn(w, g2[q], v[8]);
-        if (raw <= kAlphaMax) {
-          const float dq = dal * al;
-          const float e1 = dq * t1, e2 = dq * t2;
-          v[0] += e1;
-          v[1] += e2;
-          v[2] = __fmaf_rn(e1, t1, v[2]);
-          v[3] = __fmaf_rn(e1, t2, v[3]);
-          v[4] = __fmaf_rn(e2, t2, v[4]);
-          v[5] += dq;
-        }
+        const float dq = raw <= kAlphaMax ? (T[q] * diff) * al : 0.f;  // alpha dL/dalpha; 0 past the clamp
+        const float e1 = dq * t1, e2 = dq * t2;
+        v[0] += e1;
+        v[1] += e2;
+        v[2] = __fmaf_rn(e1, t1, v[2]);
+        v[3] = __fmaf_rn(e1, t2, v[3]);
+        v[4] = __fmaf_rn(e2, t2, v[4]);
+        v[5] += dq;
       }
       if (__any_sync(0xffffffffu, contrib)) {
         const float tot = warp_reduce_scatter9(v, lane);
