@@ -318,45 +318,56 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
   }
 }
 
-// Sum 9 values over the warp, scattered: each lane gets the total of value
-// scatter9_index(lane) (< 0: a padding slot; lanes 2i and 2i+1 hold the
-// same total).  Recursive halving on lane bits 16, 8, 4, 2 keeps the lower
-// half of the values on lanes with the bit clear and the upper half on the
-// others (9 -> 5 -> 3 -> 2 -> 1 values, padded with zeros), then the pair
-// exchange: 5 + 3 + 2 + 1 + 1 = 12 shuffles.
-template <int N, int OFF>
-__device__ __forceinline__ void halve(const float *in, float *out, int lane) {
-  constexpr int H = (N + 1) / 2;
-  const bool hi = (lane & OFF) != 0;
-#pragma unroll
-  for (int k = 0; k < H; ++k) {
-    const float lo_v = in[k], hi_v = k + H < N ? in[k + H] : 0.f;
-    const float send = hi ? lo_v : hi_v, keep = hi ? hi_v : lo_v;
-    out[k] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
-  }
-}
-
-__device__ __forceinline__ float warp_reduce_scatter9(const float v[9], int lane) {
-  float a[5], b[3], c[2], d[1];
-  halve<9, 16>(v, a, lane);
-  halve<5, 8>(a, b, lane);
-  halve<3, 4>(b, c, lane);
-  halve<2, 2>(c, d, lane);
-  return d[0] + __shfl_xor_sync(0xffffffffu, d[0], 1);
-}
-
-// The value whose total warp_reduce_scatter9 leaves on `lane`, -1 for none.
-__device__ __forceinline__ int scatter9_index(int lane) {
-  const int x = (((lane >> 2) & 1) ? 2 : 0) + ((lane >> 1) & 1);
-  if (x > 2) return -1;
-  const int w = (((lane >> 3) & 1) ? 3 : 0) + x;
-  if (w > 4) return -1;
-  const int v = (((lane >> 4) & 1) ? 5 : 0) + w;
-  return v > 8 ? -1 : v;
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Number of per-Gaussian sums the backward accumulates (see render_bwd_kernel).
 constexpr int kSums = 9;
+// The backward parks the per-lane partial sums of up to kPend entries of a
+// warp in shared memory, then reduces them transposed: lane l adds up row l
+// (entry l / 8, sum l % 8) and eight lanes per entry finish sum 8.  A row
+// holds the 32 lanes' partials padded to 36 floats, so the 128-bit reads of
+// a quarter-warp hit distinct banks.
+constexpr int kPend = 4;
+constexpr int kRow = 36;
+
+// Reduce the parked partials of n_pend (<= kPend) entries of this warp and
+// add the totals to the per-Gaussian sums.  part is the warp's
+// [kPend * kSums][kRow] block, pend_g the entries' Gaussian indices.
+__device__ __forceinline__ void flush_pending(const float *part, const uint32_t *pend_g, int n_pend, int lane,
+                                              float *__restrict__ sums, uint32_t n_gauss) {
+  __syncwarp();
+  {  // sums 0..7 of entries 0..3: one row per lane
+    const int e = lane >> 3, k = lane & 7;
+    const float4 *row = reinterpret_cast<const float4 *>(part + (e * kSums + k) * kRow);
+    float4 acc = row[0];
+#pragma unroll
+    for (int c = 1; c < 8; ++c) {
+      const float4 x = row[c];
+      acc.x += x.x;
+      acc.y += x.y;
+      acc.z += x.z;
+      acc.w += x.w;
+    }
+    const float tot = (acc.x + acc.y) + (acc.z + acc.w);
+    const uint32_t g = pend_g[e];
+    if (e < n_pend && tot != 0.f && g < n_gauss) atomicAdd(sums + (size_t)g * BS_DGAUSS_FLOATS + k, tot);
+  }
+  {  // sum 8 of entry lane / 8: eight lanes, four partials each
+    const int e = lane >> 3, c = lane & 7;
+    const float4 x = reinterpret_cast<const float4 *>(part + (e * kSums + 8) * kRow)[c];
+    float tot = (x.x + x.y) + (x.z + x.w);
+    tot += __shfl_xor_sync(0xffffffffu, tot, 4);
+    tot += __shfl_xor_sync(0xffffffffu, tot, 2);
+    tot += __shfl_xor_sync(0xffffffffu, tot, 1);
+    const uint32_t g = pend_g[e];
+    if (c == 0 && e < n_pend && tot != 0.f && g < n_gauss) atomicAdd(sums + (size_t)g * BS_DGAUSS_FLOATS + 8, tot);
+  }
+  __syncwarp();
+}
 
 // Reverse walk.  With S the colour behind Gaussian j as seen through it,
 // S <- alpha_j c_j + (1 - alpha_j) S (starting from bg behind the last
@@ -388,6 +399,8 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
   __shared__ uint32_t s_cnt[2][2];
   __shared__ uint32_t s_max_last;
   __shared__ uint32_t s_wlast[2][kPix];
+  __shared__ __align__(16) float s_part[2][kPend * kSums * kRow];
+  __shared__ uint32_t s_pend_g[2][kPend];
   const int tile = blockIdx.x;
   const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
   const uint2 r = ranges[tile];
@@ -422,7 +435,9 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
     const uint32_t wl = __reduce_max_sync(0xffffffffu, last[q]);
     if (lane == 0) s_wlast[threadIdx.x >> 5][q] = wl;
   }
-  const int sum_idx = (lane & 1) ? -1 : scatter9_index(lane);
+  float *const part = s_part[threadIdx.x >> 5];
+  uint32_t *const pend_g = s_pend_g[threadIdx.x >> 5];
+  int n_pend = 0;  // warp-uniform
   __syncthreads();
   const uint32_t max_last = min(s_max_last, r.y - r.x);
   for (uint32_t end = max_last; end > 0;) {
@@ -476,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
         const bool on = pos < last[q] && al0 >= kAlphaMin;
         const float al = on ? al0 : 0.f;
         contrib |= on;
-        T[q] = on ? __fdividef(T[q], 1.f - al) : T[q];  // T before this Gaussian
+        T[q] = on ? T[q] * rcp_approx(1.f - al) : T[q];  // T before this Gaussian
         const float w = al * T[q];
         const float gc = __fmaf_rn(g2[q], gb.y, __fmaf_rn(g1[q], gb.x, g0[q] * b.w));
         const float diff = gc - gS[q];
@@ -494,14 +509,19 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
         v[5] += dq;
       }
       if (__any_sync(0xffffffffu, contrib)) {
-        const float tot = warp_reduce_scatter9(v, lane);
-        const uint32_t g = s_g[j];
-        if (sum_idx >= 0 && tot != 0.f && g < n_gauss)
-          atomicAdd(sums + (size_t)g * BS_DGAUSS_FLOATS + sum_idx, tot);
+        float *dst = part + n_pend * kSums * kRow + lane;
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) dst[q * kRow] = v[q];
+        if (lane == 0) pend_g[n_pend] = s_g[j];
+        if (++n_pend == kPend) {
+          flush_pending(part, pend_g, n_pend, lane, sums, n_gauss);
+          n_pend = 0;
+        }
       }
     }
     end = start;
   }
+  if (n_pend) flush_pending(part, pend_g, n_pend, lane, sums, n_gauss);
 }
 
 // The chain rule from the tile sums of render_bwd_kernel to the record.
