@@ -1,7 +1,7 @@
 """Throughput of the Bezier Splatting rasterizer: fwd+bwd raster steps/s.
 
 One step = the whole hot path over one synthetic problem:
-  curve order -> sample Gaussians -> bin (count, emit, onesweep sort, ranges)
+  curve order -> sample Gaussians -> bin (count, emit, radix sort, ranges)
   -> blend forward -> L2 loss gradient -> blend backward -> sampling backward.
 Workload (default): 2048x2048 RGB target, 2048 open + 2048 closed cubic
 curves, 64 Gaussians per curve (262,144 Gaussians), 16x16 tiles.
@@ -275,12 +275,12 @@ def run_ours(args, rank, world):
         "periodic": {"prune_densify_ms": round(float(np.mean(pd_ms)), 4), "not_in_step": True, **pd_stats},
     }
     # kernels launched per step: curve_order 2 (count, first), sample 1,
-    # binning 8 + sort passes (zero, count, scan_partials, chunk_owner,
-    # diff_rows, diff_cols, tile_scan, emit, onesweep x passes), render_fwd 1,
-    # l2 1, render_bwd 2 (blend backward, grads_from_sums), sample_bwd 1;
-    # memsets are not kernels
+    # binning 8 + 3 per sort pass (zero, count, scan_partials, chunk_owner,
+    # diff_rows, diff_cols, tile_scan, emit; upsweep, scan_parts, downsweep
+    # per pass), render_fwd 1, l2 1, render_bwd 2 (blend backward,
+    # grads_from_sums), sample_bwd 1; memsets are not kernels
     passes = -(-max(1, (canvas.n_tiles - 1).bit_length()) // 8)
-    per_step = 2 + 1 + (8 + passes) + 1 + 1 + 2 + 1
+    per_step = 2 + 1 + (8 + 3 * passes) + 1 + 1 + 2 + 1
     out["gpu_launches"] = per_step * args.steps
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(side=8)

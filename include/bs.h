@@ -19,9 +19,8 @@
  *     before anything is launched; an invalid argument returns
  *     BS_ERR_INVALID_ARG and launches nothing.  bs_last_error() gives a
  *     thread-local message for the last non-OK status.
- *   - Errors found by a kernel (a bounded wait that ran out, a count that
- *     overflowed) are recorded in a status word inside the binning
- *     workspace; bs_device_status reads it.
+ *   - Errors found by a kernel (a count that overflowed) are recorded in a
+ *     status word inside the binning workspace; bs_device_status reads it.
  *   - Coordinates are pixels: pixel (x, y) covers [x, x+1) x [y, y+1) and
  *     its centre is (x + 0.5, y + 0.5).  Colours and opacities are the
  *     activated values in [0, 1].
@@ -46,7 +45,7 @@ typedef enum {
   BS_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported parameter value */
   BS_ERR_CUDA = 2,          /* a CUDA runtime call failed (message in bs_last_error) */
   BS_ERR_CAPACITY = 3,      /* pair_capacity too small; *n_pairs_out holds the need  */
-  BS_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out (device status)    */
+  BS_ERR_TIMEOUT = 4,       /* a bounded device-side retry loop ran out              */
   BS_ERR_NOT_FINITE = 5,    /* reserved: non-finite values detected                 */
   BS_ERR_UNSUPPORTED = 6    /* device or configuration the library does not support */
 } bs_status;
@@ -173,7 +172,8 @@ bs_status bs_bin_tiles_workspace(int64_t n_gauss, const bs_canvas *canvas,
  *     key = tile_id << gbits | g,  tile_id = ty * tiles_x + tx,
  *     gbits = max(1, bit length of n_gauss - 1),
  * and are sorted ascending by a hand-written stable LSD radix sort of the
- * tile bits (decoupled look-back), so each tile's list is front to back.
+ * tile bits (per pass: digit counts per partition, their scan, a stable
+ * scatter), so each tile's list is front to back.
  * tile bits + gbits must be <= 32 (else BS_ERR_UNSUPPORTED).
  *   ws, ws_bytes    scratch of bs_bin_tiles_workspace bytes (device)
  *   pair_capacity   room in tile_keys and ws
@@ -198,7 +198,7 @@ bs_status bs_bin_tiles(const float *gauss, int64_t n_gauss, const bs_canvas *can
  * budget, or a callback that must not allocate.  The caller still provides
  * gauss, tile_keys and tile_ranges.  The paper has no counterpart of this call.
  *   - A request whose scratch would exceed 32 MiB (a pair_capacity above
- *     about 6.7 M for 262,144 Gaussians on a 2048 x 2048 canvas; see
+ *     about 7.1 M for 262,144 Gaussians on a 2048 x 2048 canvas; see
  *     bs_bin_tiles_workspace for the size of a request) returns
  *     BS_ERR_INVALID_ARG with the size it needs; nothing is launched.
  *   - No allocation is made: no cudaMalloc, cudaFree or allocating library
@@ -361,13 +361,15 @@ bs_status bs_prune_densify(const bs_curves_mut *curves, const bs_pd_cfg *cfg,
 bs_status bs_device_status(const void *ws, size_t ws_bytes, int32_t *status_out,
                            bs_stream stream);
 
-/* Test hook for the bounded waits of the sort.  Partition
- * never_publish_partition (-1: none) never publishes its digit counts, and
- * every look-back wait gives up after spin_limit polls (0: the default
- * bound).  Applies to later bs_bin_tiles calls in this process; while a
- * partition is held back the sorted keys are invalid and bs_device_status
- * reports BS_ERR_TIMEOUT.  No wait is unbounded either way. */
-bs_status bs_debug_sort_fault(int32_t never_publish_partition, uint32_t spin_limit);
+/* Test hook for the bounded device-side retry loops.  The only one is the
+ * union step of bs_prune_densify's region labelling, which tries again when
+ * another thread moved a root under it.  Each union makes at most
+ * max_attempts linking attempts (< 0: the default bound, 2^20; 0: a union
+ * with anything to link gives up at once); a union that gives up makes that
+ * bs_prune_densify call return BS_ERR_TIMEOUT.  Applies to later calls in
+ * this process.  No device loop is unbounded either way, and no kernel of
+ * the library waits on another thread. */
+bs_status bs_debug_retry_limit(int64_t max_attempts);
 
 /* Message of the last non-OK status on this thread ("" if none). */
 const char *bs_last_error(void);

@@ -98,7 +98,7 @@ _sig("bs_prune_densify_workspace", c_int32, c_int32, POINTER(bs_canvas), POINTER
 _sig("bs_prune_densify", POINTER(bs_curves_mut), POINTER(bs_pd_cfg), POINTER(bs_canvas), _P, _P, _P, c_size_t, _P,
      POINTER(bs_pd_stats), _P)
 _sig("bs_device_status", _P, c_size_t, POINTER(c_int32), _P)
-_sig("bs_debug_sort_fault", c_int32, c_uint32)
+_sig("bs_debug_retry_limit", c_int64)
 
 
 class BSError(RuntimeError):
@@ -435,7 +435,8 @@ def prune_densify(curves: CurveSet, img: torch.Tensor, target: torch.Tensor, cfg
     return changed[:n], {f: int(getattr(st, f)) for f, _ in bs_pd_stats._fields_}
 
 
-def debug_sort_fault(never_publish_partition: int = -1, spin_limit: int = 0):
-    """Test hook: make one sort partition never publish its counts, with a
-    short bound on the look-back wait (-1 restores normal operation)."""
-    _check("bs_debug_sort_fault", lib.bs_debug_sort_fault(never_publish_partition, spin_limit))
+def debug_retry_limit(max_attempts: int = -1):
+    """Test hook: bound the device-side retry loops (the union step of the
+    region labelling) to max_attempts linking attempts (< 0 restores the
+    default bound; 0 makes every union with anything to link give up)."""
+    _check("bs_debug_retry_limit", lib.bs_debug_retry_limit(max_attempts))

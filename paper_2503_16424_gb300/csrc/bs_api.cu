@@ -50,7 +50,7 @@ bs_status check_device() {
   return BS_OK;
 }
 
-void debug_set_sort_fault(int never_publish_part, uint32_t spin_limit);
+void debug_set_retry_limit(int64_t max_attempts);
 const char *last_error_cstr();
 
 }  // namespace bs
@@ -304,8 +304,8 @@ bs_status bs_device_status(const void *ws, size_t ws_bytes, int32_t *status_out,
   return read_device_status(ws, ws_bytes, status_out, (cudaStream_t)stream);
 }
 
-bs_status bs_debug_sort_fault(int32_t never_publish_partition, uint32_t spin_limit) {
-  debug_set_sort_fault(never_publish_partition, spin_limit);
+bs_status bs_debug_retry_limit(int64_t max_attempts) {
+  debug_set_retry_limit(max_attempts);
   return BS_OK;
 }
 

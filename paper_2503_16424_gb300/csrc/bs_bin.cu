@@ -1,5 +1,5 @@
 // Tile binning (Section 3.4): per-Gaussian tile rectangles, (tile, depth)
-// keys, a hand-written stable onesweep LSD radix sort of the tile bits, and
+// keys, a hand-written stable LSD radix sort of the tile bits, and
 // per-tile ranges.
 //
 // The keys are emitted Gaussian by Gaussian, so the emitted array is already
@@ -13,12 +13,13 @@
 // Their exclusive scan over tile ids is the tile ranges, and their sums by
 // digit are the histograms the sort passes need.
 //
-// Sort pass (one launch per digit): every CTA takes the next partition of
-// 4096 keys from an atomic counter (so a partition's predecessors are always
-// resident), ranks its keys stably with warp match_any, publishes its digit
-// counts, and resolves its global offsets by decoupled look-back over the
-// partitions before it.  Every look-back wait is bounded; when a bound runs
-// out the CTA records kDevErrTimeout in the workspace status word and goes on.
+// Sort pass (per digit, reduce then scan then scatter): the keys are cut into
+// partitions of 4096; upsweep_kernel counts each partition's digits,
+// scan_parts_kernel turns the counts into each partition's first output index
+// per digit (the digit's global start, from the tile counts, plus the counts
+// of the partitions before it), and downsweep_kernel ranks each partition's
+// keys stably with warp match_any and writes them there.  Nothing waits on
+// another CTA.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -39,12 +40,8 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per partition
 constexpr int kMaxPasses = 4;
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagIncl = 2u << 30;
-constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr int64_t kMaxPairs = (1ll << 30) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
-constexpr int kLookWindow = 8;
+constexpr int kScanThreads = 1024;
 
 struct Hdr {
   uint32_t status;
@@ -382,40 +379,94 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__re
   for (uint32_t j = threadIdx.x; j < m; j += kEmitThreads) keys[k0 + j] = s_keys[j];
 }
 
-// ---- one onesweep pass ----
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// ---- sort passes ----
+
+// Digit counts of partition blockIdx.x, stored digit-major:
+// hist[d * parts + partition].
+__global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const uint32_t *__restrict__ in, const Hdr *hdr,
+                                                               int shift, int bits, uint32_t *__restrict__ hist,
+                                                               uint32_t parts) {
+  __shared__ uint32_t s_h[kSortWarps][256];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&s_h[0][0])[i] = 0u;
+  __syncthreads();
+  const uint32_t n = (uint32_t)hdr->n_pairs, nbins = 1u << bits, dmask = nbins - 1;
+  const uint32_t base = blockIdx.x * (uint32_t)kSortTile;
+#pragma unroll 4
+  for (int i = tid; i < kSortTile; i += kSortThreads) {
+    const uint32_t idx = base + (uint32_t)i;
+    if (idx < n) atomicAdd(&s_h[warp][(in[idx] >> shift) & dmask], 1u);
+  }
+  __syncthreads();
+  for (uint32_t d = tid; d < nbins; d += kSortThreads) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) c += s_h[w][d];
+    hist[(size_t)d * parts + blockIdx.x] = c;
+  }
 }
 
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *__restrict__ in,
-                                                                uint32_t *__restrict__ out, const Hdr *hdr_in,
-                                                                Hdr *hdr, int shift, int bits,
-                                                                const uint32_t *digit_start, uint32_t *lookback,
-                                                                uint32_t *counter, uint32_t spin_limit,
-                                                                int never_publish_part) {
+// Digit blockIdx.x: in place, the exclusive prefix over partitions of its
+// counts plus the digit's global start = each partition's first output index
+// for its keys of this digit.
+__global__ void __launch_bounds__(kScanThreads) scan_parts_kernel(uint32_t *__restrict__ hist, uint32_t parts,
+                                                                  const uint32_t *__restrict__ digit_start) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *row = hist + (size_t)blockIdx.x * parts;
+  if (threadIdx.x == 0) s_carry = digit_start[blockIdx.x];
+  constexpr int kPer = 4;
+  for (uint32_t base = 0; base < parts; base += kScanThreads * kPer) {
+    uint32_t v[kPer], sum = 0;
+    const uint32_t i0 = base + threadIdx.x * kPer;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      v[k] = i0 + k < parts ? row[i0 + k] : 0u;
+      sum += v[k];
+    }
+    const uint32_t incl = warp_incl_scan(sum, lane);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) s_warp[lane] = warp_incl_scan(s_warp[lane], lane);
+    __syncthreads();
+    uint32_t run = s_carry + (warp ? s_warp[warp - 1] : 0u) + incl - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (i0 + k < parts) row[i0 + k] = run;
+      run += v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += s_warp[31];
+    __syncthreads();
+  }
+}
+
+// Partition blockIdx.x: stable rank of each key among the partition's keys
+// with the same digit (warp match_any, then per-warp running counts), keys
+// gathered by digit in shared memory, then written at the partition's first
+// output index for the digit (from scan_parts_kernel) plus their rank.
+__global__ void __launch_bounds__(kSortThreads, 4) downsweep_kernel(const uint32_t *__restrict__ in,
+                                                                 uint32_t *__restrict__ out, const Hdr *hdr,
+                                                                 int shift, int bits,
+                                                                 const uint32_t *__restrict__ offs, uint32_t parts) {
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_whist[kSortWarps][256];
   __shared__ uint32_t s_bexcl[256];
-  __shared__ uint32_t s_gstart[256];
+  __shared__ uint32_t s_dst[256];
   __shared__ uint32_t s_wtot[kSortWarps];
-  __shared__ uint32_t s_part;
-  const uint32_t n = (uint32_t)hdr_in->n_pairs;
+  const uint32_t n = (uint32_t)hdr->n_pairs;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t nbins = 1u << bits, dmask = nbins - 1;
-  if (tid == 0) s_part = atomicAdd(counter, 1u);
+  const uint32_t part = blockIdx.x;
   for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
   __syncthreads();
-  const uint32_t part = s_part;
   const uint32_t base = part * (uint32_t)kSortTile + (uint32_t)warp * (32u * kSortItems);
   const unsigned lt_mask = (1u << lane) - 1;
 
-  // stable rank of each key among the keys of its warp with the same digit
-  uint32_t keys[kSortItems], rank[kSortItems];
+  // a key's rank among its warp's keys of the same digit is < 512: two
+  // ranks share a register
+  uint32_t keys[kSortItems], rank2[kSortItems / 2];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t idx = base + (uint32_t)i * 32u + (uint32_t)lane;
@@ -428,14 +479,15 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
     const uint32_t d = (keys[i] >> shift) & dmask;
     const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu);
     const uint32_t cnt = valid ? s_whist[warp][d] : 0u;
-    rank[i] = cnt + __popc(peers & lt_mask);
+    const uint32_t rk = cnt + __popc(peers & lt_mask);
+    rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (rk << 16)) : rk;
     __syncwarp();
     if (valid && (peers & lt_mask) == 0) s_whist[warp][d] = cnt + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
 
-  // per digit (one thread each): offsets across warps, publish, look back
+  // per digit (one thread each): warp offsets within the partition
   uint32_t bcount = 0;
   if (tid < (int)nbins) {
 #pragma unroll
@@ -444,63 +496,25 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
       s_whist[w][tid] = bcount;
       bcount += c;
     }
-    uint32_t *mine = lookback + (size_t)part * 256 + tid;
-    const bool publish = (int)part != never_publish_part;
-    const uint32_t gexcl = digit_start[tid];
-    if (part == 0) {
-      if (publish) st_relaxed(mine, kFlagIncl | bcount);
-      s_gstart[tid] = gexcl;
-    } else {
-      if (publish) st_relaxed(mine, kFlagAgg | bcount);
-      // Look back in windows of kLookWindow predecessors: their words are
-      // loaded together, then consumed nearest first until an inclusive
-      // prefix; a word not yet published is re-read (boundedly).
-      uint32_t excl = 0;
-      int64_t j = (int64_t)part - 1;
-      uint32_t spins = 0;
-      bool done = false;
-      while (!done && j >= 0) {
-        uint32_t win[kLookWindow];
-#pragma unroll
-        for (int k = 0; k < kLookWindow; ++k)
-          win[k] = j - k >= 0 ? ld_relaxed(lookback + (size_t)(j - k) * 256 + tid) : kFlagIncl;
-#pragma unroll 1
-        for (int k = 0; k < kLookWindow && !done; ++k) {
-          uint32_t v = win[k];
-          while ((v & ~kCountMask) == 0u) {
-            if (++spins > spin_limit) {
-              atomicOr(&hdr->status, kDevErrTimeout);
-              v = kFlagIncl;  // give up: treat as an empty inclusive prefix
-              break;
-            }
-            __nanosleep(32);
-            v = ld_relaxed(lookback + (size_t)(j - k) * 256 + tid);
-          }
-          excl += v & kCountMask;
-          done = (v & ~kCountMask) == kFlagIncl;
-        }
-        j -= kLookWindow;
-      }
-      if (publish) st_relaxed(mine, kFlagIncl | ((excl + bcount) & kCountMask));
-      s_gstart[tid] = gexcl + excl;
-    }
   }
-  // exclusive prefix of bcount over digits (warp scans, then the warp totals)
+  // exclusive prefix of the partition's digit counts (warp scans, then totals)
   const uint32_t incl = warp_incl_scan(bcount, lane);
   if (lane == 31) s_wtot[warp] = incl;
   __syncthreads();
   uint32_t wbase = 0;
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) wbase += w < warp ? s_wtot[w] : 0u;
-  s_bexcl[tid] = wbase + incl - bcount;
+  const uint32_t bexcl = wbase + incl - bcount;
+  s_bexcl[tid] = bexcl;
+  if (tid < (int)nbins) s_dst[tid] = offs[(size_t)tid * parts + part] - bexcl;
   __syncthreads();
-  // scatter into shared memory in (digit, input order) order
+  // gather in shared memory by (digit, input order)
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t idx = base + (uint32_t)i * 32u + (uint32_t)lane;
     if (idx < n) {
       const uint32_t d = (keys[i] >> shift) & dmask;
-      s_keys[s_bexcl[d] + s_whist[warp][d] + rank[i]] = keys[i];
+      s_keys[s_bexcl[d] + s_whist[warp][d] + ((rank2[i >> 1] >> (16 * (i & 1))) & 0xffffu)] = keys[i];
     }
   }
   __syncthreads();
@@ -508,13 +522,10 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
   const uint32_t n_here = n > pstart ? min((uint32_t)kSortTile, n - pstart) : 0u;
   for (uint32_t j = tid; j < n_here; j += kSortThreads) {
     const uint32_t k = s_keys[j];
-    const uint32_t d = (k >> shift) & dmask;
-    out[s_gstart[d] + (j - s_bexcl[d])] = k;
+    out[s_dst[(k >> shift) & dmask] + j] = k;
   }
 }
 
-int g_debug_never_publish = -1;     // test hook: a partition that never publishes
-uint32_t g_spin_limit = kSpinLimit;
 
 }  // namespace
 
@@ -550,14 +561,14 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
   p->capacity = capacity;
   p->count_blocks = div_up64(n_gauss > 0 ? n_gauss : 1, kCountThreads);
   p->parts = div_up64(capacity > 0 ? capacity : 1, kSortTile);
-  // zeroed at the start of every call: [hdr, hist, counter, diff, lookback]
+  // zeroed at the start of every call: [hdr, hist, diff]
   size_t o = 0;
   p->off_hdr = o;        o = align256(o + sizeof(Hdr));
   p->off_hist = o;       o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
-  p->off_counter = o;    o = align256(o + sizeof(uint32_t) * kMaxPasses);
   p->off_diff = o;       o = align256(o + sizeof(int) * (size_t)(p->tiles_x + 1) * (size_t)(p->tiles_y + 1));
-  p->off_lookback = o;   o = align256(o + sizeof(uint32_t) * (size_t)p->passes * (size_t)p->parts * 256);
   p->zero_bytes = o;
+  // per-partition digit counts of one pass, then its output offsets (in place)
+  p->off_parts = o;      o = align256(o + sizeof(uint32_t) * (size_t)p->parts * 256);
   p->off_local = o;      o = align256(o + sizeof(uint32_t) * (size_t)(n_gauss > 0 ? n_gauss : 1));
   p->off_partial = o;    o = align256(o + sizeof(unsigned long long) * (size_t)(p->count_blocks + 1));
   p->off_rects = o;      o = align256(o + sizeof(uint2) * (size_t)(n_gauss > 0 ? n_gauss : 1));
@@ -578,8 +589,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   int *diff = reinterpret_cast<int *>(base + p.off_diff);
   uint32_t *keys_tmp = reinterpret_cast<uint32_t *>(base + p.off_keys_tmp);
   uint32_t *hist = reinterpret_cast<uint32_t *>(base + p.off_hist);
-  uint32_t *counter = reinterpret_cast<uint32_t *>(base + p.off_counter);
-  uint32_t *lookback = reinterpret_cast<uint32_t *>(base + p.off_lookback);
+  uint32_t *part_offs = reinterpret_cast<uint32_t *>(base + p.off_parts);
   uint2 *ranges = reinterpret_cast<uint2 *>(tile_ranges);
   const int rows = p.tiles_y + 1, cols = p.tiles_x + 1;
 
@@ -627,10 +637,13 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     uint32_t *dst = (src == bufs[0]) ? bufs[1] : bufs[0];
     const int shift = p.gbits + pass * p.digit_bits;
     const int bits = std::min(p.digit_bits, p.tbits - pass * p.digit_bits);
-    onesweep_kernel<<<(unsigned)parts, kSortThreads, 0, s>>>(
-        src, dst, hdr, hdr, shift, bits, hist + pass * 256, lookback + (size_t)pass * (size_t)parts * 256,
-        counter + pass, g_spin_limit, g_debug_never_publish);
-    BS_LAUNCHED("onesweep_kernel");
+    upsweep_kernel<<<(unsigned)parts, kSortThreads, 0, s>>>(src, hdr, shift, bits, part_offs, (uint32_t)parts);
+    BS_LAUNCHED("upsweep_kernel");
+    scan_parts_kernel<<<1u << bits, kScanThreads, 0, s>>>(part_offs, (uint32_t)parts, hist + pass * 256);
+    BS_LAUNCHED("scan_parts_kernel");
+    downsweep_kernel<<<(unsigned)parts, kSortThreads, 0, s>>>(src, dst, hdr, shift, bits, part_offs,
+                                                               (uint32_t)parts);
+    BS_LAUNCHED("downsweep_kernel");
     src = dst;
   }
   return BS_OK;
@@ -675,11 +688,6 @@ bs_status read_device_status(const void *ws, size_t ws_bytes, int32_t *out, cuda
   BS_CUDA(cudaStreamSynchronize(s));
   *out = (h.status & kDevErrTimeout) ? BS_ERR_TIMEOUT : (h.status ? BS_ERR_CAPACITY : BS_OK);
   return BS_OK;
-}
-
-void debug_set_sort_fault(int never_publish_part, uint32_t spin_limit) {
-  g_debug_never_publish = never_publish_part;
-  g_spin_limit = spin_limit ? spin_limit : kSpinLimit;
 }
 
 }  // namespace bs

@@ -101,9 +101,9 @@ struct BinPlan {
   int passes, digit_bits;
   int64_t capacity;
   int64_t count_blocks;    // blocks of the count/emit kernels
-  int64_t parts;           // onesweep partitions for `capacity` keys
+  int64_t parts;           // sort partitions for `capacity` keys
   // byte offsets inside the workspace
-  size_t off_hdr, off_hist, off_counter, off_diff, off_lookback, zero_bytes;
+  size_t off_hdr, off_hist, off_diff, zero_bytes, off_parts;
   size_t off_local, off_partial, off_rects, off_owner, off_keys_tmp;
   size_t bytes;
 };

@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kSegPx = 16;                   // pixels per thread in the run-aggregated passes
-constexpr uint32_t kUnionRetries = 1u << 20;
+constexpr uint32_t kUnionAttempts = 1u << 20;  // default bound of the union step's linking attempts
 constexpr uint32_t kSelected = 0x80000000u;  // area[root] holds the region's rank when set
 constexpr int kSelectBlocks = 608;           // 152 SMs x 4
 
@@ -329,13 +329,15 @@ __device__ __forceinline__ int find_root(const int32_t *L, int x) {
 }
 
 // Link the trees of a and b; the larger root is hooked under the smaller one,
-// so every root stays the smallest pixel index of its component.
-__device__ void unite(int32_t *L, int a, int b, uint32_t *status) {
+// so every root stays the smallest pixel index of its component.  A new
+// attempt follows a root that another thread moved meanwhile; after
+// max_attempts the step gives up and records kDevErrTimeout.
+__device__ void unite(int32_t *L, int a, int b, uint32_t *status, uint32_t max_attempts) {
   for (uint32_t it = 0;; ++it) {
     a = find_root(L, a);
     b = find_root(L, b);
     if (a == b) return;
-    if (it >= kUnionRetries) {
+    if (it >= max_attempts) {
       atomicOr(status, kDevErrTimeout);
       return;
     }
@@ -353,14 +355,14 @@ __device__ void unite(int32_t *L, int a, int b, uint32_t *status) {
 
 // Vertical neighbours in the mask: unite their runs, once per overlap of two
 // runs (at its leftmost column).
-__global__ void union_kernel(int W, int64_t P, int32_t *L, uint32_t *status) {
+__global__ void union_kernel(int W, int64_t P, int32_t *L, uint32_t *status, uint32_t max_attempts) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P || p < W) return;
   const int x = (int)(p % W);
   const int a = __ldcg(L + p), b = __ldcg(L + p - W);
   if (a < 0 || b < 0) return;
   if (x > 0 && __ldcg(L + p - 1) >= 0 && __ldcg(L + p - W - 1) >= 0) return;
-  unite(L, a, b, status);
+  unite(L, a, b, status, max_attempts);
 }
 
 // Run heads (first pixel of a run) point straight to their root.
@@ -695,7 +697,13 @@ __global__ void apply_kernel(Curves c, float new_opacity, float new_width, const
   }
 }
 
+uint32_t g_union_attempts = kUnionAttempts;
+
 }  // namespace
+
+void debug_set_retry_limit(int64_t max_attempts) {
+  g_union_attempts = max_attempts < 0 ? kUnionAttempts : (uint32_t)std::min<int64_t>(max_attempts, 0xffffffffll);
+}
 
 size_t prune_densify_bytes(int n_open, int n_closed, int width, int height) {
   return layout(n_open + n_closed, (int64_t)width * height).bytes;
@@ -739,7 +747,7 @@ bs_status run_prune_densify(const bs_curves_mut &cm, const bs_pd_cfg &cfg, int W
   const unsigned pb = (unsigned)div_up64(P, kThreads);
   runs_kernel<<<div_up(H, kThreads / 32), kThreads, 0, s>>>(img, target, W, H, cfg.err_thresh, label, area);
   BS_LAUNCHED("prune runs_kernel");
-  union_kernel<<<pb, kThreads, 0, s>>>(W, P, label, &hdr->status);
+  union_kernel<<<pb, kThreads, 0, s>>>(W, P, label, &hdr->status, g_union_attempts);
   BS_LAUNCHED("prune union_kernel");
   heads_kernel<<<pb, kThreads, 0, s>>>(W, P, label);
   BS_LAUNCHED("prune heads_kernel");
@@ -783,7 +791,7 @@ bs_status run_prune_densify(const bs_curves_mut &cm, const bs_pd_cfg &cfg, int W
     stats->transparent = (int32_t)(h.n_slots - h.n_sel);
   }
   if (h.status & kDevErrTimeout) {
-    set_error("bs_prune_densify: a bounded union-find retry loop ran out");
+    set_error("bs_prune_densify: a union step of the region labelling gave up after its bounded attempts");
     return BS_ERR_TIMEOUT;
   }
   return BS_OK;

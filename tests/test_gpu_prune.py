@@ -156,3 +156,21 @@ def test_pruned_curves_render_through_the_pipeline(bs):
     assert st["pruned"] > 0 and changed.any()
     loss1, grad = r.step(curves, t_d)
     assert torch.isfinite(loss1) and all(torch.isfinite(getattr(grad, k)).all() for k in FIELDS)
+
+
+def test_bounded_retry_gives_up_and_recovers(bs):
+    """With no linking attempt allowed, the union step gives up: the call
+    reports BS_ERR_TIMEOUT and returns (nothing waits).  With the default
+    bound restored the next call matches the oracle."""
+    W, H = 120, 90
+    arr, img, tgt = synth.prune_inputs(17, W, H, 60, 40, n_blobs=12)
+    curves = bs.CurveSet.from_arrays(arr)
+    i_d, t_d = torch.as_tensor(img).cuda(), torch.as_tensor(tgt).cuda()
+    try:
+        bs.debug_retry_limit(0)
+        with pytest.raises(bs.BSError) as e:
+            bs.prune_densify(curves, i_d, t_d, bs.PDCfg(), bs.Canvas(W, H))
+        assert e.value.status == bs.BS_ERR_TIMEOUT
+    finally:
+        bs.debug_retry_limit(-1)
+    compare(arr, *run_both(bs, arr, img, tgt, W, H))

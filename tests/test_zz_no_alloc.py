@@ -64,7 +64,7 @@ def test_static_scratch_refuses_oversized_requests(bs):
     ranges = torch.empty(canvas.n_tiles, 2, dtype=torch.int32, device="cuda")
     cv = canvas.c()
     n_pairs = ctypes.c_int64(0)
-    st = bs.lib.bs_bin_tiles_static(ctypes.c_void_p(gauss.data_ptr()), 262144, ctypes.byref(cv), 7_000_000,
+    st = bs.lib.bs_bin_tiles_static(ctypes.c_void_p(gauss.data_ptr()), 262144, ctypes.byref(cv), 7_200_000,
                                     ctypes.byref(n_pairs), ctypes.c_void_p(keys.data_ptr()),
                                     ctypes.c_void_p(ranges.data_ptr()), None)
     assert st == bs.BS_ERR_INVALID_ARG
