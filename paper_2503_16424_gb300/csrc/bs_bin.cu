@@ -18,7 +18,8 @@
 // scan_parts_kernel turns the counts into each partition's first output index
 // per digit (the digit's global start, from the tile counts, plus the counts
 // of the partitions before it), and downsweep_kernel ranks each partition's
-// keys stably with warp match_any and writes them there.  Nothing waits on
+// keys stably (peer lanes of a digit from one ballot per digit bit) and
+// writes them there.  Nothing waits on
 // another CTA.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_parts_kernel(uint32_t *__re
 }
 
 // Partition blockIdx.x: stable rank of each key among the partition's keys
-// with the same digit (warp match_any, then per-warp running counts), keys
+// with the same digit (peer lanes from ballots, then per-warp running counts), keys
 // gathered by digit in shared memory, then written at the partition's first
 // output index for the digit (from scan_parts_kernel) plus their rank.
 __global__ void __launch_bounds__(kSortThreads, 4) downsweep_kernel(const uint32_t *__restrict__ in,
@@ -477,7 +478,12 @@ __global__ void __launch_bounds__(kSortThreads, 4) downsweep_kernel(const uint32
     const uint32_t idx = base + (uint32_t)i * 32u + (uint32_t)lane;
     const bool valid = idx < n;
     const uint32_t d = (keys[i] >> shift) & dmask;
-    const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu);
+    // lanes with the same digit: the AND of one ballot per digit bit
+    unsigned peers = __ballot_sync(0xffffffffu, valid);
+    for (int b = 0; b < bits; ++b) {
+      const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+      peers &= ((d >> b) & 1u) ? bb : ~bb;
+    }
     const uint32_t cnt = valid ? s_whist[warp][d] : 0u;
     const uint32_t rk = cnt + __popc(peers & lt_mask);
     rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (rk << 16)) : rk;
