@@ -326,28 +326,41 @@ __device__ __forceinline__ int64_t window_owner(const uint32_t *s_off, int win, 
 // 8t .. 8t+7 of that range: one owner search, then a walk along the owner's
 // rectangle row by row (a new search only when the walk leaves the owner's
 // pairs).  The keys are staged in shared memory and written coalesced.
+// The CTA's keys belong to Gaussians owner[b] .. owner[b+1], so only their
+// offsets are staged.  It also adds the digit counts of its keys for the
+// sort's first pass to hist1 (digit-major, partition b / 2).
+static_assert(2 * kEmitTile == kSortTile, "a sort partition is two emit chunks");
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__restrict__ local,
                                                             const unsigned long long *__restrict__ partial,
                                                             int64_t nb, const uint2 *__restrict__ rects,
                                                             int64_t n_gauss, const Hdr *hdr, int tiles_x, int gbits,
                                                             const uint32_t *__restrict__ owner,
-                                                            uint32_t *__restrict__ keys) {
+                                                            uint32_t *__restrict__ keys, int bits1,
+                                                            uint32_t *__restrict__ hist1, uint32_t parts) {
   constexpr int kWin = kEmitTile + 1;
   __shared__ uint32_t s_off[kWin];
   __shared__ uint32_t s_keys[kEmitTile];
+  __shared__ uint32_t s_h[256];
   const uint32_t n = (uint32_t)hdr->n_pairs;
   const uint32_t k0 = blockIdx.x * (uint32_t)kEmitTile;
   if (k0 >= n) return;
   const int64_t g0 = owner[blockIdx.x];
+  // the window ends one past the owner of the next chunk's first key (the
+  // last chunk: capped; an owner outside the window is found globally)
+  const bool last_chunk = k0 + (uint32_t)kEmitTile >= n;
+  const int64_t win_need = last_chunk ? n_gauss - g0 + 1 : (int64_t)owner[blockIdx.x + 1] - g0 + 2;
+  const int win = (int)(win_need < kWin ? win_need : kWin);
+  for (int k = threadIdx.x; k < 256; k += kEmitThreads) s_h[k] = 0u;
   // offsets of Gaussians g0, g0+1, ...; beyond the table: +infinity
-  for (int k = threadIdx.x; k < kWin; k += kEmitThreads) {
+  for (int k = threadIdx.x; k < win; k += kEmitThreads) {
     const int64_t g = g0 + k;
     s_off[k] = g < n_gauss ? global_offset(partial, local, g) : 0xffffffffu;
   }
   __syncthreads();
   const uint32_t i0 = k0 + (uint32_t)threadIdx.x * kEmitItems;
+  const uint32_t dmask = (1u << bits1) - 1;
   if (i0 < n) {
-    int64_t g = window_owner(s_off, kWin, g0, partial, nb, local, n_gauss, i0);
+    int64_t g = window_owner(s_off, win, g0, partial, nb, local, n_gauss, i0);
     uint32_t off = global_offset(partial, local, g);
     uint2 rc = rects[g];
     uint32_t w = rc.y & 0xffffu, cnt = w * (rc.y >> 16);
@@ -358,7 +371,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__re
       const uint32_t i = i0 + (uint32_t)it;
       if (i >= n) break;
       if (i - off >= cnt) {  // left the owner's pairs
-        g = window_owner(s_off, kWin, g0, partial, nb, local, n_gauss, i);
+        g = window_owner(s_off, win, g0, partial, nb, local, n_gauss, i);
         off = global_offset(partial, local, g);
         rc = rects[g];
         w = rc.y & 0xffffu;
@@ -369,6 +382,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__re
       }
       const uint32_t tid = ((rc.x >> 16) + ry) * (uint32_t)tiles_x + (rc.x & 0xffffu) + rx;
       s_keys[threadIdx.x * kEmitItems + it] = (tid << gbits) | (uint32_t)g;
+      atomicAdd(&s_h[tid & dmask], 1u);
       if (++rx == w) {
         rx = 0;
         ++ry;
@@ -378,6 +392,8 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__re
   __syncthreads();
   const uint32_t m = min((uint32_t)kEmitTile, n - k0);
   for (uint32_t j = threadIdx.x; j < m; j += kEmitThreads) keys[k0 + j] = s_keys[j];
+  for (uint32_t d = threadIdx.x; d <= dmask; d += kEmitThreads)
+    if (s_h[d]) atomicAdd(&hist1[(size_t)d * parts + (blockIdx.x >> 1)], s_h[d]);
 }
 
 // ---- sort passes ----
@@ -635,16 +651,20 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   // emit into the buffer that makes the last pass land in tile_keys
   uint32_t *bufs[2] = {tile_keys, keys_tmp};
   uint32_t *src = (p.passes % 2 == 0) ? tile_keys : keys_tmp;
+  const int bits0 = std::min(p.digit_bits, p.tbits);
+  BS_CUDA(cudaMemsetAsync(part_offs, 0, sizeof(uint32_t) * ((size_t)1 << bits0) * (size_t)parts, s));
   emit_kernel<<<(unsigned)div_up64(P, kEmitTile), kEmitThreads, 0, s>>>(local, partial, p.count_blocks, rects,
                                                                        p.n_gauss, hdr, p.tiles_x, p.gbits, owner,
-                                                                       src);
+                                                                       src, bits0, part_offs, (uint32_t)parts);
   BS_LAUNCHED("emit_kernel");
   for (int pass = 0; pass < p.passes; ++pass) {
     uint32_t *dst = (src == bufs[0]) ? bufs[1] : bufs[0];
     const int shift = p.gbits + pass * p.digit_bits;
     const int bits = std::min(p.digit_bits, p.tbits - pass * p.digit_bits);
-    upsweep_kernel<<<(unsigned)parts, kSortThreads, 0, s>>>(src, hdr, shift, bits, part_offs, (uint32_t)parts);
-    BS_LAUNCHED("upsweep_kernel");
+    if (pass > 0) {  // the first pass's counts come from emit_kernel
+      upsweep_kernel<<<(unsigned)parts, kSortThreads, 0, s>>>(src, hdr, shift, bits, part_offs, (uint32_t)parts);
+      BS_LAUNCHED("upsweep_kernel");
+    }
     scan_parts_kernel<<<1u << bits, kScanThreads, 0, s>>>(part_offs, (uint32_t)parts, hist + pass * 256);
     BS_LAUNCHED("scan_parts_kernel");
     downsweep_kernel<<<(unsigned)parts, kSortThreads, 0, s>>>(src, dst, hdr, shift, bits, part_offs,
