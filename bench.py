@@ -275,13 +275,15 @@ def run_ours(args, rank, world):
         "periodic": {"prune_densify_ms": round(float(np.mean(pd_ms)), 4), "not_in_step": True, **pd_stats},
     }
     # kernels launched per step: curve_order 2 (count, first), sample 1,
-    # binning 8 + 3 per sort pass - 1 (zero, count, scan_partials,
-    # chunk_owner, diff_rows, diff_cols, tile_scan, emit; upsweep, scan_parts,
-    # downsweep per pass, the first pass's counts coming from emit),
-    # render_fwd 1, l2 1, render_bwd 2 (blend backward, grads_from_sums),
-    # sample_bwd 1; memsets are not kernels
+    # binning 6 + 3 per sort pass - 1 (zero, count, scan_partials,
+    # chunk_owner, fused_tile_scan, emit; upsweep, scan_parts, downsweep per
+    # pass, the first pass's counts coming from emit; a tile grid too large
+    # for one CTA's shared memory takes 2 more), render_fwd 1, l2 1,
+    # render_bwd 2 (blend backward, grads_from_sums), sample_bwd 1; memsets
+    # are not kernels
     passes = -(-max(1, (canvas.n_tiles - 1).bit_length()) // 8)
-    per_step = 2 + 1 + (8 + 3 * passes - 1) + 1 + 1 + 2 + 1
+    fused = (canvas.width // canvas.tile + 2) * (canvas.height // canvas.tile + 2) + canvas.n_tiles <= 48 * 1024
+    per_step = 2 + 1 + (6 + 3 * passes - 1 + (0 if fused and passes <= 2 else 2)) + 1 + 1 + 2 + 1
     out["gpu_launches"] = per_step * args.steps
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(side=8)

@@ -259,6 +259,115 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const int *counts, int 
   }
 }
 
+// The difference array's row and column scans, the tile scan and the digit
+// starts in one CTA, with the whole (tiles_y + 1) x (tiles_x + 1) array and
+// the per-tile prefixes in shared memory (used when they fit; at most two
+// sort passes).  Digit counts: pass 0 (digit t mod 2^digit_bits) by
+// shared-memory adds from consecutive tiles, which hit distinct digits; the
+// last pass's digit d covers the tile range [d 2^shift, (d + 1) 2^shift),
+// whose count is a difference of two prefixes.
+constexpr int kFusedMaxWords = 48 * 1024;   // ints of array + prefixes in shared memory
+__global__ void __launch_bounds__(1024) fused_tile_scan_kernel(const int *__restrict__ diff, int tiles_x,
+                                                               int tiles_y, int passes, int digit_bits,
+                                                               uint2 *__restrict__ ranges, uint32_t *__restrict__ hist) {
+  extern __shared__ int s_dyn[];
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_dig[kMaxPasses * 256];
+  const int rows = tiles_y + 1, cols = tiles_x + 1;
+  const int n = tiles_x * tiles_y;
+  int *s_cnt = s_dyn;                                        // [rows][cols]
+  uint32_t *s_pre = reinterpret_cast<uint32_t *>(s_dyn + rows * cols);  // [n + 1]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) s_dig[i] = 0u;
+  {
+    const int m = rows * cols;
+    constexpr int kU = 8;
+    for (int i0 = 0; i0 < m; i0 += kU * 1024) {
+      int v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * 1024 + threadIdx.x;
+        v[u] = i < m ? diff[i] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * 1024 + threadIdx.x;
+        if (i < m) s_cnt[i] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  for (int r = warp; r < rows; r += 32) {      // row scans
+    int carry = 0;
+    for (int c0 = 0; c0 < cols; c0 += 32) {
+      const int c = c0 + lane;
+      int v = c < cols ? s_cnt[r * cols + c] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (c < cols) s_cnt[r * cols + c] = carry + v;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+  __syncthreads();
+  for (int c = warp; c < cols; c += 32) {      // column scans
+    int carry = 0;
+    for (int r0 = 0; r0 < rows; r0 += 32) {
+      const int r = r0 + lane;
+      int v = r < rows ? s_cnt[r * cols + c] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (r < rows) s_cnt[r * cols + c] = carry + v;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+  __syncthreads();
+  // exclusive prefix over tiles: thread i sums tiles [i run, (i + 1) run)
+  const int run = (n + 1023) / 1024;
+  const int t0 = min(n, (int)threadIdx.x * run), t1 = min(n, t0 + run);
+  const int ty0 = t0 / tiles_x, tx0 = t0 - ty0 * tiles_x;
+  uint32_t sum = 0;
+  for (int t = t0, ty = ty0, tx = tx0; t < t1; ++t) {
+    sum += (uint32_t)s_cnt[ty * cols + tx];
+    if (++tx == tiles_x) tx = 0, ++ty;
+  }
+  uint32_t total;
+  uint32_t start = block_excl_scan1024(sum, s_warp, &total);
+  for (int t = t0, ty = ty0, tx = tx0; t < t1; ++t) {
+    s_pre[t] = start;
+    start += (uint32_t)s_cnt[ty * cols + tx];
+    if (++tx == tiles_x) tx = 0, ++ty;
+  }
+  if (threadIdx.x == 0) s_pre[n] = total;
+  __syncthreads();
+  // ranges, coalesced; pass-0 digit counts
+  const uint32_t dmask = (1u << digit_bits) - 1;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const uint32_t pre = s_pre[t], v = s_pre[t + 1] - pre;
+    ranges[t] = v ? make_uint2(pre, pre + v) : make_uint2(0u, 0u);
+    if (passes > 1 && v) atomicAdd(&s_dig[t & dmask], v);
+  }
+  const int hshift = digit_bits * (passes - 1);
+  const int nmark = (n + (1 << hshift) - 1) >> hshift;
+  for (int d = threadIdx.x; d < nmark; d += blockDim.x)   // last pass: prefix differences
+    s_dig[(passes - 1) * 256 + d] = s_pre[min(n, (d + 1) << hshift)] - s_pre[d << hshift];
+  __syncthreads();
+  if (warp < passes) {  // per pass, the exclusive prefix over digits
+    uint32_t carry = 0;
+    for (int d0 = 0; d0 < 256; d0 += 32) {
+      const uint32_t v = s_dig[warp * 256 + d0 + lane];
+      const uint32_t incl = warp_incl_scan(v, lane);
+      hist[warp * 256 + d0 + lane] = carry + incl - v;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
 // ---- emit keys ----
 // CTA b writes keys [b T, (b+1) T), T = 2048.  One binary search over the
 // CTA offsets and the offsets inside a count CTA finds the owner of the
@@ -631,12 +740,26 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
         local, partial, rects, p.n_gauss, (uint32_t)div_up64(p.capacity, kEmitTile), owner);
     BS_LAUNCHED("chunk_owner_kernel");
   }
-  diff_rows_kernel<<<div_up(rows, 8), 256, 0, s>>>(diff, rows, cols);
-  BS_LAUNCHED("diff_rows_kernel");
-  diff_cols_kernel<<<div_up(cols, 8), 256, 0, s>>>(diff, rows, cols);
-  BS_LAUNCHED("diff_cols_kernel");
-  tile_scan_kernel<<<1, 1024, 0, s>>>(diff, p.tiles_x, p.tiles_y, p.passes, p.digit_bits, ranges, hist);
-  BS_LAUNCHED("tile_scan_kernel");
+  if ((int64_t)rows * cols + p.n_tiles + 1 <= kFusedMaxWords && p.passes <= 2) {
+    const size_t smem = sizeof(int) * ((size_t)rows * cols + (size_t)p.n_tiles + 1);
+    static bool attr_set[64] = {};
+    int dev = 0;
+    BS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+      BS_CUDA(cudaFuncSetAttribute(fused_tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(int) * kFusedMaxWords)));
+      if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    fused_tile_scan_kernel<<<1, 1024, smem, s>>>(diff, p.tiles_x, p.tiles_y, p.passes, p.digit_bits, ranges, hist);
+    BS_LAUNCHED("fused_tile_scan_kernel");
+  } else {
+    diff_rows_kernel<<<div_up(rows, 8), 256, 0, s>>>(diff, rows, cols);
+    BS_LAUNCHED("diff_rows_kernel");
+    diff_cols_kernel<<<div_up(cols, 8), 256, 0, s>>>(diff, rows, cols);
+    BS_LAUNCHED("diff_cols_kernel");
+    tile_scan_kernel<<<1, 1024, 0, s>>>(diff, p.tiles_x, p.tiles_y, p.passes, p.digit_bits, ranges, hist);
+    BS_LAUNCHED("tile_scan_kernel");
+  }
   Hdr h;
   BS_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(Hdr), cudaMemcpyDeviceToHost, s));
   BS_CUDA(cudaStreamSynchronize(s));
