@@ -282,7 +282,8 @@ def run_ours(args, rank, world):
     # render_bwd 2 (blend backward, grads_from_sums), sample_bwd 1; memsets
     # are not kernels
     passes = -(-max(1, (canvas.n_tiles - 1).bit_length()) // 8)
-    fused = (canvas.width // canvas.tile + 2) * (canvas.height // canvas.tile + 2) + canvas.n_tiles <= 48 * 1024
+    tiles_x, tiles_y = -(-canvas.width // canvas.tile), -(-canvas.height // canvas.tile)
+    fused = (tiles_x + 1) * (tiles_y + 1) + canvas.n_tiles + 1 <= 48 * 1024
     per_step = 2 + 1 + (6 + 3 * passes - 1 + (0 if fused and passes <= 2 else 2)) + 1 + 1 + 2 + 1
     out["gpu_launches"] = per_step * args.steps
     if rank == 0 and not args.no_cpu_baseline:
