@@ -38,7 +38,7 @@ FP32_LANES_PER_SM = 128
 # workload, from one ncu capture of the current kernel
 # (profiles/render_bwd_kernel_hires_2048_4096.md); None where no capture of
 # the current kernel exists.
-DRAM_BYTES_PER_LAUNCH = {"render_bwd_kernel": None, "render_fwd_kernel": None}
+DRAM_BYTES_PER_LAUNCH = {"render_bwd_kernel": 131236096, "render_fwd_kernel": None}
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
