@@ -2,7 +2,8 @@
 
 One step = the whole hot path over one synthetic problem:
   curve order -> sample Gaussians -> bin (count, emit, radix sort, ranges)
-  -> blend forward -> L2 loss gradient -> blend backward -> sampling backward.
+  -> blend forward with the L2 loss gradient (one kernel) -> blend backward
+  -> sampling backward.
 Workload (default): 2048x2048 RGB target, 2048 open + 2048 closed cubic
 curves, 64 Gaussians per curve (262,144 Gaussians), 16x16 tiles.
 
@@ -158,11 +159,10 @@ def run_ours(args, rank, world):
         r.binning.run(r.gauss)
         if e:
             e[0].record(stream)
-        bs.render_fwd(r.gauss, canvas, r.binning, out=(r.img, r.T, r.nc))
+        # blend forward with the L2 loss and its gradient in the same pass
+        bs.render_fwd_l2(r.gauss, canvas, r.binning, target, out=(r.img, r.T, r.nc), dimg=r.dimg, loss=r.loss)
         if e:
             e[1].record(stream)
-        bs.l2_loss_grad(r.img, target, dimg=r.dimg, loss=r.loss)
-        if e:
             e[2].record(stream)
         bs.render_bwd(r.gauss, canvas, r.binning, r.T, r.nc, r.dimg, r.dgauss)
         if e:
@@ -278,13 +278,13 @@ def run_ours(args, rank, world):
     # binning 6 + 3 per sort pass - 1 (zero, count, scan_partials,
     # chunk_owner, fused_tile_scan, emit; upsweep, scan_parts, downsweep per
     # pass, the first pass's counts coming from emit; a tile grid too large
-    # for one CTA's shared memory takes 2 more), render_fwd 1, l2 1,
-    # render_bwd 2 (blend backward, grads_from_sums), sample_bwd 1; memsets
-    # are not kernels
+    # for one CTA's shared memory takes 2 more), render_fwd with the L2 term
+    # 1, render_bwd 2 (blend backward, grads_from_sums), sample_bwd 1;
+    # memsets are not kernels
     passes = -(-max(1, (canvas.n_tiles - 1).bit_length()) // 8)
     tiles_x, tiles_y = -(-canvas.width // canvas.tile), -(-canvas.height // canvas.tile)
     fused = (tiles_x + 1) * (tiles_y + 1) + canvas.n_tiles + 1 <= 48 * 1024
-    per_step = 2 + 1 + (6 + 3 * passes - 1 + (0 if fused and passes <= 2 else 2)) + 1 + 1 + 2 + 1
+    per_step = 2 + 1 + (6 + 3 * passes - 1 + (0 if fused and passes <= 2 else 2)) + 1 + 2 + 1
     out["gpu_launches"] = per_step * args.steps
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(side=8)

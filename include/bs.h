@@ -229,6 +229,22 @@ bs_status bs_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas *ca
                         float *img, float *T_final, uint32_t *n_contrib, bs_stream stream);
 
 /*
+ * bs_render_fwd followed by bs_l2_loss_grad on its image (Eq. 9-10, then the
+ * L2 term of Eq. 13 with lambda_1 = 1 over the 3 H W entries), in one pass
+ * over the pixels: img, T_final and n_contrib as bs_render_fwd writes them,
+ * dL_dimg = 2 (img - target) / (3 H W) bit-identical to bs_l2_loss_grad's,
+ * and loss_out = mean((img - target)^2) equal to it up to the order of the
+ * summation.
+ *   target   [3][H][W]  (device, read)
+ *   dL_dimg  [3][H][W]  (device, written)
+ *   loss_out            (device double, written)
+ */
+bs_status bs_render_fwd_l2(const float *gauss, int64_t n_gauss, const bs_canvas *canvas,
+                           const uint32_t *tile_keys, const uint32_t *tile_ranges,
+                           const float *target, float *img, float *T_final, uint32_t *n_contrib,
+                           float *dL_dimg, double *loss_out, bs_stream stream);
+
+/*
  * bs_render_fwd plus work counters, for measurement: stats_out (device,
  * 4 x uint64, zeroed and written) receives [0] the (pixel, list entry)
  * evaluations performed, [1] the entries blended, [2] the sum over tiles of

@@ -90,6 +90,7 @@ _sig("bs_bin_tiles_workspace", c_int64, POINTER(bs_canvas), c_int64, POINTER(c_s
 _sig("bs_bin_tiles", _P, c_int64, POINTER(bs_canvas), _P, c_size_t, c_int64, POINTER(c_int64), _P, _P, _P)
 _sig("bs_render_fwd", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P)
 _sig("bs_bin_tiles_static", _P, c_int64, POINTER(bs_canvas), c_int64, POINTER(c_int64), _P, _P, _P)
+_sig("bs_render_fwd_l2", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P, _P, _P, _P)
 _sig("bs_l2_loss_grad", _P, _P, c_int64, _P, _P, _P)
 _sig("bs_render_stats", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P, _P)
 _sig("bs_render_bwd", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P,
@@ -338,6 +339,28 @@ def render_fwd(gauss: torch.Tensor, canvas: Canvas, binning: Binning, out=None):
                                                _ptr(binning.keys), _ptr(binning.ranges), _ptr(img), _ptr(T),
                                                _ptr(nc), _stream()))
     return img, T, nc
+
+
+def render_fwd_l2(gauss: torch.Tensor, canvas: Canvas, binning: Binning, target: torch.Tensor, out=None,
+                  dimg=None, loss=None):
+    """Forward blend and the L2 loss gradient in one pass: (img, T_final,
+    n_contrib), dL/dimg, loss (device double)."""
+    W, H = canvas.width, canvas.height
+    dev = gauss.device
+    _want(target, torch.float32, (3, H, W), "target")
+    if out is None:
+        out = (torch.empty(3, H, W, dtype=torch.float32, device=dev),
+               torch.empty(H, W, dtype=torch.float32, device=dev),
+               torch.empty(H, W, dtype=torch.int32, device=dev))
+    img, T, nc = out
+    dimg = dimg if dimg is not None else torch.empty_like(img)
+    loss = loss if loss is not None else torch.empty((), dtype=torch.float64, device=dev)
+    cv = canvas.c()
+    _check("bs_render_fwd_l2", lib.bs_render_fwd_l2(_ptr(gauss), int(gauss.shape[0]), ctypes.byref(cv),
+                                                     _ptr(binning.keys), _ptr(binning.ranges), _ptr(target),
+                                                     _ptr(img), _ptr(T), _ptr(nc), _ptr(dimg),
+                                                     c_void_p(loss.data_ptr()), _stream()))
+    return (img, T, nc), dimg, loss
 
 
 def render_stats(gauss: torch.Tensor, canvas: Canvas, binning: Binning):

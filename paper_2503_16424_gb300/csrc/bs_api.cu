@@ -227,6 +227,19 @@ bs_status bs_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas *ca
                            (cudaStream_t)stream);
 }
 
+bs_status bs_render_fwd_l2(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, const uint32_t *tile_keys,
+                           const uint32_t *tile_ranges, const float *target, float *img, float *T_final,
+                           uint32_t *n_contrib, float *dL_dimg, double *loss_out, bs_stream stream) {
+  BS_TRY(check_canvas(canvas));
+  if (n_gauss < 0 || n_gauss > (1ll << 31) - 1) return invalid("n_gauss out of range");
+  if (n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  if (!tile_ranges || !img || !T_final || !n_contrib) return invalid("NULL output or tile_ranges");
+  if (!target || !dL_dimg || !loss_out) return invalid("target, dL_dimg and loss_out must be non-NULL");
+  BS_TRY(check_device());
+  return launch_render_fwd_l2(gauss, n_gauss, *canvas, gauss_bits(n_gauss), tile_keys, tile_ranges, target, img,
+                              T_final, n_contrib, dL_dimg, loss_out, (cudaStream_t)stream);
+}
+
 bs_status bs_render_stats(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, const uint32_t *tile_keys,
                           const uint32_t *tile_ranges, float *img, float *T_final, uint32_t *n_contrib,
                           unsigned long long *stats_out, bs_stream stream) {

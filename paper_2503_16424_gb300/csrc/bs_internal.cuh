@@ -121,6 +121,9 @@ bs_status launch_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas
                             const uint32_t *keys, const uint32_t *ranges, float *img,
                             float *T_final, uint32_t *n_contrib, cudaStream_t s,
                             unsigned long long *stats = nullptr);
+bs_status launch_render_fwd_l2(const float *gauss, int64_t n_gauss, const bs_canvas &cv, int gbits,
+                               const uint32_t *keys, const uint32_t *ranges, const float *target, float *img,
+                               float *T_final, uint32_t *n_contrib, float *dimg, double *loss, cudaStream_t s);
 bs_status launch_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas &cv, int gbits,
                             const uint32_t *keys, const uint32_t *ranges, const float *T_final,
                             const uint32_t *n_contrib, const float *dL_dimg, float *dgauss,

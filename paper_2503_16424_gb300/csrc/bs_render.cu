@@ -206,7 +206,10 @@ __device__ __forceinline__ ThreadPixels thread_pixels(int tile, int tiles_x, int
 // kStats: also count the (pixel, list entry) evaluations (E), the entries
 // blended, and the entries of the tile lists times the tile's pixels, into
 // stats[0..2] (for measurement; same blend otherwise).
-template <bool kStats>
+// kL2: also the L2 term of Eq. 13 on the finished pixels: dL/dimg =
+// (2 / n) (img - target), and mean((img - target)^2) added to *loss (one
+// double atomic per CTA; *loss zeroed by the launcher).
+template <bool kStats, bool kL2 = false>
 __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *__restrict__ gauss,
                                                                   const uint32_t *__restrict__ keys,
                                                                   const uint2 *__restrict__ ranges, int W, int H,
@@ -214,7 +217,10 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
                                                                   float3 bg, float *__restrict__ img,
                                                                   float *__restrict__ T_out,
                                                                   uint32_t *__restrict__ nc_out,
-                                                                  unsigned long long *__restrict__ stats) {
+                                                                  unsigned long long *__restrict__ stats,
+                                                                  const float *__restrict__ target = nullptr,
+                                                                  float *__restrict__ dimg = nullptr,
+                                                                  double *__restrict__ loss = nullptr) {
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
@@ -306,15 +312,41 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
     }
   }
   const size_t plane = (size_t)W * H;
+  float l2 = 0.f;
+  const float scale = kL2 ? (float)(2.0 / (double)(3 * plane)) : 0.f;
 #pragma unroll
   for (int q = 0; q < kPix; ++q) {
     if (!(tp.inside & (1u << q))) continue;
     const size_t p = (size_t)tp.y[q >> 1] * W + tp.x[q & 1];
-    img[p] = __fmaf_rn(T[q], bg.x, c0[q]);
-    img[plane + p] = __fmaf_rn(T[q], bg.y, c1[q]);
-    img[2 * plane + p] = __fmaf_rn(T[q], bg.z, c2[q]);
+    const float v0 = __fmaf_rn(T[q], bg.x, c0[q]);
+    const float v1 = __fmaf_rn(T[q], bg.y, c1[q]);
+    const float v2 = __fmaf_rn(T[q], bg.z, c2[q]);
+    img[p] = v0;
+    img[plane + p] = v1;
+    img[2 * plane + p] = v2;
     T_out[p] = T[q];
     nc_out[p] = last[q];
+    if (kL2) {
+      const float d0 = v0 - target[p], d1 = v1 - target[plane + p], d2 = v2 - target[2 * plane + p];
+      dimg[p] = scale * d0;
+      dimg[plane + p] = scale * d1;
+      dimg[2 * plane + p] = scale * d2;
+      l2 += d0 * d0 + d1 * d1 + d2 * d2;
+    }
+  }
+  if (kL2) {
+    __shared__ double s_l2[kThreads / 32];
+    double v = l2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_l2[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) t += s_l2[w];
+      atomicAdd(loss, t / (double)(3 * plane));
+    }
   }
 }
 
@@ -612,6 +644,20 @@ bs_status launch_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas
         gauss, keys, rg, cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib,
         nullptr);
   }
+  BS_LAUNCHED("render_fwd_kernel");
+  return BS_OK;
+}
+
+bs_status launch_render_fwd_l2(const float *gauss, int64_t n_gauss, const bs_canvas &cv, int gbits,
+                               const uint32_t *keys, const uint32_t *ranges, const float *target, float *img,
+                               float *T_final, uint32_t *n_contrib, float *dimg, double *loss, cudaStream_t s) {
+  const int tiles_x = div_up(cv.width, kTile), tiles_y = div_up(cv.height, kTile);
+  const uint32_t gmask = gbits >= 32 ? 0xffffffffu : ((1u << gbits) - 1u);
+  const auto bg = make_float3(cv.bg[0], cv.bg[1], cv.bg[2]);
+  BS_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s));
+  render_fwd_kernel<false, true><<<tiles_x * tiles_y, kThreads, 0, s>>>(
+      gauss, keys, reinterpret_cast<const uint2 *>(ranges), cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss,
+      bg, img, T_final, n_contrib, nullptr, target, dimg, loss);
   BS_LAUNCHED("render_fwd_kernel");
   return BS_OK;
 }

@@ -53,9 +53,13 @@ class Rasterizer:
         return grad
 
     def step(self, curves: CurveSet, target: torch.Tensor, grad: CurveSet = None):
-        """sample -> bin -> render -> L2 loss/grad -> render bwd -> sample bwd."""
-        self.forward(curves)
-        bs.l2_loss_grad(self.img, target, dimg=self.dimg, loss=self.loss)
+        """sample -> bin -> render with the L2 loss/grad fused -> render bwd
+        -> sample bwd."""
+        self.rank, self.first = bs.curve_order(curves, self.cfg)
+        bs.sample_curves(curves, self.cfg, self.first, out=self.gauss)
+        self.binning.run(self.gauss)
+        bs.render_fwd_l2(self.gauss, self.canvas, self.binning, target, out=(self.img, self.T, self.nc),
+                         dimg=self.dimg, loss=self.loss)
         grad = self.backward(curves, self.dimg, grad)
         return self.loss, grad
 

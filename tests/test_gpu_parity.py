@@ -218,3 +218,24 @@ def test_l2_matches_oracle(bs):
     # float differences and per-thread float partial sums (a few terms here)
     assert abs(loss.item() - float(L)) <= 4e-6 * float(L)
     assert np.abs(dimg.cpu().numpy() - g.numpy()).max() <= 3e-7 * np.abs(g.numpy()).max()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fused_forward_l2_matches_the_separate_calls(bs, name):
+    """bs_render_fwd_l2 = bs_render_fwd then bs_l2_loss_grad: image, blend
+    state and dL/dimg bit-identical, loss equal up to summation order."""
+    case = CASES[name]
+    arr = arrays(case)
+    curves = _gpu_curves(bs, arr)
+    cfg, canvas = _cfg(bs, case), _canvas(bs, case)
+    _, first = bs.curve_order(curves, cfg)
+    gauss = bs.sample_curves(curves, cfg, first)
+    b = bs.Binning(canvas, "cuda").run(gauss)
+    tgt = torch.as_tensor(target(case), device="cuda")
+    img, T, nc = bs.render_fwd(gauss, canvas, b)
+    loss, dimg = bs.l2_loss_grad(img, tgt)
+    (img2, T2, nc2), dimg2, loss2 = bs.render_fwd_l2(gauss, canvas, b, tgt)
+    torch.cuda.synchronize()
+    for x, y in ((img, img2), (T, T2), (nc, nc2), (dimg, dimg2)):
+        assert torch.equal(x, y)
+    assert abs(float(loss2) - float(loss)) <= 1e-7 * abs(float(loss))
