@@ -371,6 +371,165 @@ bs_status bs_prune_densify(const bs_curves_mut *curves, const bs_pd_cfg *cfg,
                            void *ws, size_t ws_bytes, uint8_t *changed_out,
                            bs_pd_stats *stats_out, bs_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many images of different sizes and curve counts optimised
+ * together (the method of Section 3 applied to each image independently).
+ * Each image b has its own canvas, curves and sampling; its arrays are
+ * concatenated image after image:
+ *   curves      bs_curves whose n_open / n_closed are the batch totals; image
+ *               b's open curves are rows [open0_b, open0_b + n_open_b) of the
+ *               open arrays (open0_b = sum of the earlier images' n_open), its
+ *               closed curves likewise in the closed arrays.  Control points
+ *               are in the image's own pixel coordinates.
+ *   Gaussians   image b's records are rows [gauss0_b, gauss0_b + n_gauss_b)
+ *               of the table, in the image's draw order (gauss0_b = sum of
+ *               the earlier images' bs_num_gaussians).
+ *   pixels      image b's planar image [3][H_b][W_b] starts at float 3 pix0_b
+ *               of an image buffer, its per-pixel maps [H_b][W_b] at pix0_b
+ *               (pix0_b = sum of the earlier images' W H).
+ *   tiles       image b's tiles are numbered tile0_b + ty tiles_x_b + tx
+ *               (tile0_b = sum of the earlier images' tile counts).
+ * Every batched call takes the same bs_batch descriptor.  Its workspace
+ * holds the device table of the layout (written by bs_batch_setup) and the
+ * binning scratch.  No batched call synchronises the stream, allocates, or
+ * depends on a value read back to the host, so a whole optimisation step
+ * (draw order, sampling, binning, blend with loss, backward, bs_adam_step)
+ * can be captured in a CUDA graph; bs_batch_status reports a capacity
+ * overflow afterwards.
+ * ---------------------------------------------------------------------- */
+
+/* One image of a batch (host struct). */
+typedef struct {
+  int32_t width, height;   /* canvas px, 1..32768                        */
+  int32_t n_open, n_closed;/* its curves                                 */
+  bs_sample_cfg sample;    /* its sampling (Section 3.3)                 */
+  float bg[3];             /* its background colour                      */
+} bs_batch_image;
+
+/* A batch: the layout, the tiling, and the workspace. */
+typedef struct {
+  const bs_batch_image *images;  /* HOST [n_images]                                  */
+  int32_t n_images;              /* >= 1                                             */
+  int32_t tile;                  /* tile side in px: 16                              */
+  int64_t pair_capacity;         /* room for (tile, Gaussian) pairs, >= 1            */
+  void *ws;                      /* device workspace of bs_batch_plan's ws_bytes     */
+  size_t ws_bytes;
+} bs_batch;
+
+/* Totals of a batch (host struct, written by bs_batch_plan). */
+typedef struct {
+  int64_t n_open, n_closed;  /* curves of all images                          */
+  int64_t n_gauss;           /* rows of the Gaussian table                    */
+  int64_t n_pixels;          /* sum of W H; image buffers hold 3 n_pixels floats */
+  int64_t n_tiles;           /* rows of tile_ranges                           */
+  size_t ws_bytes;           /* workspace bytes                               */
+} bs_batch_sizes;
+
+/* Host arithmetic only: the totals of a batch and its workspace size
+ * (batch->ws is not read).  Batch keys are 64-bit (tile << 32 | Gaussian),
+ * so any batch whose tiles and Gaussians each fit in 32 bits is accepted. */
+bs_status bs_batch_plan(const bs_batch *batch, bs_batch_sizes *out);
+
+/* Write the layout's device table into the workspace (one host-to-device
+ * copy, synchronous).  Call once before the other batched calls, and again
+ * whenever images, tile or pair_capacity change; every later call must pass
+ * the same images, tile and pair_capacity. */
+bs_status bs_batch_setup(const bs_batch *batch, bs_stream stream);
+
+/* Draw order of every image (bs_curve_order per image): ranks are within an
+ * image, first_out indexes the batch's Gaussian table (gauss0_b + the
+ * image's own first index).  rank_out, first_out [n_open + n_closed]
+ * (device, written), in the batch's curve numbering (open curves, then
+ * closed).  curves->draw_first is not read. */
+bs_status bs_batch_curve_order(const bs_batch *batch, const bs_curves *curves, uint32_t *rank_out,
+                               uint32_t *first_out, bs_stream stream);
+
+/* bs_sample_curves for every image with its own bs_sample_cfg (Section 3.3,
+ * Eq. 3-8, 11-12).  gauss [n_gauss][12] (device, written). */
+bs_status bs_batch_sample_curves(const bs_batch *batch, const bs_curves *curves, float *gauss,
+                                 bs_stream stream);
+
+/*
+ * Tile binning of every image (Section 3.4; the same tile rule as
+ * bs_bin_tiles, with each image's own canvas).  Keys (global tile << 32 | g)
+ * are emitted in Gaussian order and sorted stably by the tile bits with the
+ * library's LSD radix sort; the last pass writes only the Gaussian indices.
+ *   tile_vals    [pair_capacity] Gaussian indices, each tile's list front to
+ *                back (device, written [0, P))
+ *   tile_ranges  [n_tiles][2] (start, end) into tile_vals, (0, 0) when empty
+ *                (device, written)
+ * Grids are sized by pair_capacity and nothing is read back.  When P exceeds
+ * pair_capacity the status word records BS_ERR_CAPACITY, every range is
+ * (0, 0) (nothing is blended), and bs_batch_status reports P.
+ */
+bs_status bs_batch_bin_tiles(const bs_batch *batch, const float *gauss, uint32_t *tile_vals,
+                             uint32_t *tile_ranges, bs_stream stream);
+
+/*
+ * Forward blend of every image (Eq. 9-10, the rules of bs_render_fwd), by a
+ * persistent kernel whose CTAs take (image, tile) work items from an atomic
+ * queue.  If target is non-NULL, also the L2 term of Eq. 13 per image:
+ * dL_dimg = 2 (img - target) / (3 W_b H_b) and loss_out[b] =
+ * mean((img_b - target_b)^2) (otherwise dL_dimg and loss_out are not
+ * touched and may be NULL).
+ *   target, img, dL_dimg  [3 n_pixels] in the batch's image layout (device)
+ *   T_final, n_contrib    [n_pixels]  (device, written)
+ *   loss_out              [n_images] double (device, written)
+ */
+bs_status bs_batch_render_fwd(const bs_batch *batch, const float *gauss, const uint32_t *tile_vals,
+                              const uint32_t *tile_ranges, const float *target, float *img, float *T_final,
+                              uint32_t *n_contrib, float *dL_dimg, double *loss_out, bs_stream stream);
+
+/*
+ * Backward of bs_batch_render_fwd (the reverse walk of bs_render_bwd on
+ * every image, persistent, atomic work queue), then of the sampling of every
+ * image: dgauss [n_gauss][12] (device, zeroed and written); if grad is
+ * non-NULL, the curve gradients in the batch's curve layout.
+ */
+bs_status bs_batch_render_bwd(const bs_batch *batch, const float *gauss, const uint32_t *tile_vals,
+                              const uint32_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
+                              const float *dL_dimg, float *dgauss, const bs_curves *curves,
+                              const bs_curves_grad *grad, bs_stream stream);
+
+/* Synchronise the stream and read the batch workspace's status word:
+ * *status_out = BS_OK, BS_ERR_CAPACITY (the last bs_batch_bin_tiles found
+ * more pairs than pair_capacity) or BS_ERR_UNSUPPORTED (its pair totals over
+ * Gaussians and over tiles disagreed, so nothing was sorted; not expected,
+ * bs_last_error has both totals); *n_pairs_out (HOST, may be NULL) = the
+ * pairs that call found. */
+bs_status bs_batch_status(const bs_batch *batch, int32_t *status_out, int64_t *n_pairs_out, bs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Adam (Kingma and Ba; the optimiser of Section 4.1) over parameter groups,
+ * in one launch:  t = *step + 1,
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p = clamp(p - lr_i (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), lo, hi),
+ * lr_i = lr * row_scale[i / row_len] (row_scale NULL: lr); then *step = t.
+ * The step counter lives in device memory, so a replayed CUDA graph
+ * advances it.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  float *param;            /* [n] device, updated in place                     */
+  const float *grad;       /* [n] device                                        */
+  float *m, *v;            /* [n] device moments (zero before the first step)   */
+  int64_t n;
+  float lr;                /* >= 0                                              */
+  float lo, hi;            /* the updated value is clamped to [lo, hi]          */
+  const float *row_scale;  /* [n / row_len] device lr multipliers, or NULL      */
+  int32_t row_len;         /* >= 1                                              */
+} bs_adam_group;
+
+typedef struct {
+  float beta1, beta2, eps;
+} bs_adam_cfg;
+
+#define BS_ADAM_MAX_GROUPS 16
+
+/* groups: HOST [n_groups], 1 <= n_groups <= BS_ADAM_MAX_GROUPS;
+ * step: device int32, t before this step (0 before the first). */
+bs_status bs_adam_step(const bs_adam_group *groups, int32_t n_groups, const bs_adam_cfg *cfg, int32_t *step,
+                       bs_stream stream);
+
 /* Synchronise the stream and read the device status word of a binning
  * workspace: BS_OK or the first kernel-side error recorded since the
  * workspace's last bs_bin_tiles call. */

@@ -18,6 +18,7 @@ Modules
   loss     Section 3.5: the L2 term of Eq. 13
   prune_densify  Section 3.5, Algorithm 1, Appendix B: pruning, splitting,
            error regions and circular initialisation of new curves
+  adam     Section 4.1: the Adam update (Kingma and Ba), box-projected
 
 Parity pins: every function is pinned by a test in tests/test_oracle_*.py
 against closed forms, invariants, brute force or finite differences; none is
@@ -33,3 +34,4 @@ from .raster import render_pixels, render_image, render_grads  # noqa: F401
 from .binning import tile_rects_f32, tile_keys, key_bits  # noqa: F401
 from .loss import l2_loss  # noqa: F401
 from .prune_densify import PDCfg, prune_densify  # noqa: F401
+from .adam import adam_step  # noqa: F401

@@ -70,6 +70,33 @@ class bs_pd_stats(ctypes.Structure):
                                       "split_placed", "regions", "inserted", "transparent")]
 
 
+class bs_batch_image(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("n_open", c_int32), ("n_closed", c_int32),
+                ("sample", bs_sample_cfg), ("bg", c_float * 3)]
+
+
+class bs_batch(ctypes.Structure):
+    _fields_ = [("images", c_void_p), ("n_images", c_int32), ("tile", c_int32), ("pair_capacity", c_int64),
+                ("ws", c_void_p), ("ws_bytes", c_size_t)]
+
+
+class bs_batch_sizes(ctypes.Structure):
+    _fields_ = [("n_open", c_int64), ("n_closed", c_int64), ("n_gauss", c_int64), ("n_pixels", c_int64),
+                ("n_tiles", c_int64), ("ws_bytes", c_size_t)]
+
+
+class bs_adam_group(ctypes.Structure):
+    _fields_ = [("param", c_void_p), ("grad", c_void_p), ("m", c_void_p), ("v", c_void_p), ("n", c_int64),
+                ("lr", c_float), ("lo", c_float), ("hi", c_float), ("row_scale", c_void_p), ("row_len", c_int32)]
+
+
+class bs_adam_cfg(ctypes.Structure):
+    _fields_ = [("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
+
+
+ADAM_MAX_GROUPS = 16
+
+
 def _sig(name, *args):
     f = getattr(lib, name)
     f.argtypes = list(args)
@@ -99,6 +126,16 @@ _sig("bs_prune_densify_workspace", c_int32, c_int32, POINTER(bs_canvas), POINTER
 _sig("bs_prune_densify", POINTER(bs_curves_mut), POINTER(bs_pd_cfg), POINTER(bs_canvas), _P, _P, _P, c_size_t, _P,
      POINTER(bs_pd_stats), _P)
 _sig("bs_device_status", _P, c_size_t, POINTER(c_int32), _P)
+_B = POINTER(bs_batch)
+_sig("bs_batch_plan", _B, POINTER(bs_batch_sizes))
+_sig("bs_batch_setup", _B, _P)
+_sig("bs_batch_curve_order", _B, POINTER(bs_curves), _P, _P, _P)
+_sig("bs_batch_sample_curves", _B, POINTER(bs_curves), _P, _P)
+_sig("bs_batch_bin_tiles", _B, _P, _P, _P, _P)
+_sig("bs_batch_render_fwd", _B, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P)
+_sig("bs_batch_render_bwd", _B, _P, _P, _P, _P, _P, _P, _P, POINTER(bs_curves), POINTER(bs_curves_grad), _P)
+_sig("bs_batch_status", _B, POINTER(c_int32), POINTER(c_int64), _P)
+_sig("bs_adam_step", POINTER(bs_adam_group), c_int32, POINTER(bs_adam_cfg), _P, _P)
 _sig("bs_debug_retry_limit", c_int64)
 
 
@@ -463,3 +500,168 @@ def debug_retry_limit(max_attempts: int = -1):
     region labelling) to max_attempts linking attempts (< 0 restores the
     default bound; 0 makes every union with anything to link give up)."""
     _check("bs_debug_retry_limit", lib.bs_debug_retry_limit(max_attempts))
+
+
+# ---------------------------------------------------------------------------
+# Batches of images (bs_batch_*) and the Adam step (bs_adam_step)
+
+@dataclass
+class BatchImage:
+    """One image of a batch: canvas, curve counts, sampling, background."""
+    width: int
+    height: int
+    n_open: int
+    n_closed: int
+    sample: SampleCfg
+    bg: tuple = (0.0, 0.0, 0.0)
+
+    def c(self):
+        return bs_batch_image(self.width, self.height, self.n_open, self.n_closed, self.sample.c(),
+                              (c_float * 3)(*self.bg))
+
+
+class Batch:
+    """The layout of a batch and its device workspace (bs_batch_plan,
+    bs_batch_setup).  Host-side offsets of every image's curves, Gaussians,
+    pixels and tiles in the concatenated arrays are kept for slicing."""
+
+    def __init__(self, images, tile: int = 16, pair_capacity: int = 1 << 22, device="cuda"):
+        self.images = list(images)
+        self.tile = int(tile)
+        self.device = device
+        self._arr = (bs_batch_image * len(self.images))(*(im.c() for im in self.images))
+        self._plan(pair_capacity)
+        no = [im.n_open for im in self.images]
+        nc = [im.n_closed for im in self.images]
+        ng = [im.n_open * im.sample.g_open + im.n_closed * im.sample.rows_closed * im.sample.k_closed
+              for im in self.images]
+        npx = [im.width * im.height for im in self.images]
+        nt = [(-(-im.width // self.tile)) * (-(-im.height // self.tile)) for im in self.images]
+
+        def prefix(v):
+            out, acc = [], 0
+            for x in v:
+                out.append(acc)
+                acc += x
+            return out
+        self.open0, self.closed0, self.gauss0 = prefix(no), prefix(nc), prefix(ng)
+        self.pix0, self.tile0 = prefix(npx), prefix(nt)
+        self.n_gauss_of = ng
+
+    def _plan(self, pair_capacity):
+        self.pair_capacity = int(pair_capacity)
+        sz = bs_batch_sizes()
+        b = bs_batch(ctypes.cast(self._arr, c_void_p), len(self.images), self.tile, self.pair_capacity, None, 0)
+        _check("bs_batch_plan", lib.bs_batch_plan(ctypes.byref(b), ctypes.byref(sz)))
+        self.sizes = sz
+        self.n_open, self.n_closed = int(sz.n_open), int(sz.n_closed)
+        self.n_gauss, self.n_pixels, self.n_tiles = int(sz.n_gauss), int(sz.n_pixels), int(sz.n_tiles)
+        self.ws = torch.empty(int(sz.ws_bytes), dtype=torch.uint8, device=self.device)
+        _check("bs_batch_setup", lib.bs_batch_setup(ctypes.byref(self.c()), _stream()))
+
+    def grow(self, pair_capacity: int):
+        """Re-plan with a larger pair capacity (new workspace, new table)."""
+        self._plan(pair_capacity)
+
+    def c(self):
+        return bs_batch(ctypes.cast(self._arr, c_void_p), len(self.images), self.tile, self.pair_capacity,
+                        _ptr(self.ws), self.ws.numel())
+
+    def image(self, t: torch.Tensor, b: int):
+        """Image b's [3, H, W] view of a batch image buffer [3 n_pixels]."""
+        im = self.images[b]
+        n = im.width * im.height
+        return t[3 * self.pix0[b]:3 * (self.pix0[b] + n)].view(3, im.height, im.width)
+
+    def pixel_map(self, t: torch.Tensor, b: int):
+        """Image b's [H, W] view of a per-pixel buffer [n_pixels]."""
+        im = self.images[b]
+        return t[self.pix0[b]:self.pix0[b] + im.width * im.height].view(im.height, im.width)
+
+    def curve_order(self, curves: CurveSet, rank=None, first=None):
+        n = curves.n_open + curves.n_closed
+        rank = rank if rank is not None else torch.empty(n, dtype=torch.int32, device=self.device)
+        first = first if first is not None else torch.empty(n, dtype=torch.int32, device=self.device)
+        c, b = curves.c(), self.c()
+        _check("bs_batch_curve_order", lib.bs_batch_curve_order(ctypes.byref(b), ctypes.byref(c), _ptr(rank),
+                                                                 _ptr(first), _stream()))
+        return rank, first
+
+    def sample_curves(self, curves: CurveSet, first, out=None):
+        gauss = out if out is not None else torch.empty(self.n_gauss, GAUSS_FLOATS, dtype=torch.float32,
+                                                        device=self.device)
+        _want(gauss, torch.float32, (self.n_gauss, GAUSS_FLOATS), "gauss")
+        c, b = curves.c(first), self.c()
+        _check("bs_batch_sample_curves", lib.bs_batch_sample_curves(ctypes.byref(b), ctypes.byref(c), _ptr(gauss),
+                                                                     _stream()))
+        return gauss
+
+    def bin_tiles(self, gauss, vals, ranges):
+        _want(vals, torch.int32, None, "tile_vals")
+        _want(ranges, torch.int32, (self.n_tiles, 2), "tile_ranges")
+        if vals.numel() < self.pair_capacity:
+            raise ValueError("tile_vals must hold pair_capacity entries")
+        b = self.c()
+        _check("bs_batch_bin_tiles", lib.bs_batch_bin_tiles(ctypes.byref(b), _ptr(gauss), _ptr(vals), _ptr(ranges),
+                                                             _stream()))
+
+    def render_fwd(self, gauss, vals, ranges, img, T, nc, target=None, dimg=None, loss=None):
+        b = self.c()
+        _check("bs_batch_render_fwd", lib.bs_batch_render_fwd(
+            ctypes.byref(b), _ptr(gauss), _ptr(vals), _ptr(ranges), _ptr(target), _ptr(img), _ptr(T), _ptr(nc),
+            _ptr(dimg), c_void_p(loss.data_ptr()) if loss is not None else c_void_p(0), _stream()))
+
+    def render_bwd(self, gauss, vals, ranges, T, nc, dimg, dgauss, curves: CurveSet = None, first=None,
+                   grad: CurveSet = None):
+        b = self.c()
+        if grad is not None:
+            c, g = curves.c(first), grad.grad_c()
+            cp, gp = ctypes.byref(c), ctypes.byref(g)
+        else:
+            cp = gp = None
+        _check("bs_batch_render_bwd", lib.bs_batch_render_bwd(
+            ctypes.byref(b), _ptr(gauss), _ptr(vals), _ptr(ranges), _ptr(T), _ptr(nc), _ptr(dimg), _ptr(dgauss),
+            cp, gp, _stream()))
+
+    def status(self):
+        """(status, pairs found by the last binning); synchronises."""
+        st, n = c_int32(0), c_int64(0)
+        b = self.c()
+        _check("bs_batch_status", lib.bs_batch_status(ctypes.byref(b), ctypes.byref(st), ctypes.byref(n), _stream()))
+        return int(st.value), int(n.value)
+
+
+@dataclass
+class AdamGroup:
+    """One parameter group of bs_adam_step: param, grad, and its moments (all
+    float32 device tensors of the same size), lr, box [lo, hi], optional
+    per-row lr multipliers."""
+    param: torch.Tensor
+    grad: torch.Tensor
+    m: torch.Tensor
+    v: torch.Tensor
+    lr: float
+    lo: float = -3.0e38
+    hi: float = 3.0e38
+    row_scale: torch.Tensor = None
+    row_len: int = 1
+
+    def c(self):
+        for k in ("param", "grad", "m", "v"):
+            _want(getattr(self, k), torch.float32, None, k)
+        n = self.param.numel()
+        if any(getattr(self, k).numel() != n for k in ("grad", "m", "v")):
+            raise ValueError("param, grad, m and v must have the same size")
+        return bs_adam_group(_ptr(self.param), _ptr(self.grad), _ptr(self.m), _ptr(self.v), n, self.lr, self.lo,
+                             self.hi, _ptr(self.row_scale), int(self.row_len))
+
+
+def adam_step(groups, step: torch.Tensor, beta1=0.9, beta2=0.999, eps=1e-8):
+    """bs_adam_step over up to 16 groups; step is a device int32 scalar
+    (advanced by one on the device)."""
+    if not 1 <= len(groups) <= ADAM_MAX_GROUPS:
+        raise ValueError("1 to 16 groups")
+    _want(step, torch.int32, None, "step")
+    arr = (bs_adam_group * len(groups))(*(g.c() for g in groups))
+    cfg = bs_adam_cfg(beta1, beta2, eps)
+    _check("bs_adam_step", lib.bs_adam_step(arr, len(groups), ctypes.byref(cfg), _ptr(step), _stream()))

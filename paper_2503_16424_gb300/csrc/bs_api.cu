@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "bs_internal.cuh"
 
@@ -121,6 +122,40 @@ bs_status check_pd_cfg(const bs_pd_cfg *cfg) {
   if (!(cfg->new_opacity >= 0.f && cfg->new_opacity <= 1.f)) return invalid("new_opacity not in [0, 1]");
   if (!(cfg->new_width > 0.f)) return invalid("new_width must be > 0");
   return BS_OK;
+}
+
+// The plan of a batch, with every image's sampling validated.
+bs_status batch_plan(const bs_batch *b, BatchPlan *p) {
+  if (!b) return invalid("batch is NULL");
+  if (!b->images || b->n_images < 1) return invalid("a batch needs a host array of at least one image");
+  for (int i = 0; i < b->n_images; ++i) {
+    const bs_status st = check_cfg(&b->images[i].sample);
+    if (st != BS_OK) {
+      const std::string msg = last_error_cstr();
+      return invalid("image %d: %s", i, msg.c_str());
+    }
+  }
+  return plan_batch(b->images, b->n_images, b->tile, b->pair_capacity, p);
+}
+
+// The plan, and a workspace large enough for it.
+bs_status batch_plan_ws(const bs_batch *b, BatchPlan *p) {
+  BS_TRY(batch_plan(b, p));
+  if (!b->ws || b->ws_bytes < p->bytes || ((uintptr_t)b->ws & 255u))
+    return invalid("batch workspace needs %zu bytes (256-byte aligned), got %zu", p->bytes, b->ws_bytes);
+  return BS_OK;
+}
+
+bs_status check_batch_curves(const bs_curves *c, const BatchPlan &p, bool need_first) {
+  BS_TRY(check_curves(c, need_first));
+  if (c->n_open != p.n_open || c->n_closed != p.n_closed)
+    return invalid("curves hold %d open + %d closed curves, the batch %lld + %lld", c->n_open, c->n_closed,
+                   (long long)p.n_open, (long long)p.n_closed);
+  return BS_OK;
+}
+
+const BatchImage *batch_table_of(const bs_batch *b, const BatchPlan &p) {
+  return reinterpret_cast<const BatchImage *>(static_cast<const char *>(b->ws) + p.off_images);
 }
 
 }  // namespace
@@ -282,6 +317,124 @@ bs_status bs_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas *ca
                              n_contrib, dL_dimg, dgauss, s));
   if (grad) return bs_sample_curves_bwd(curves, cfg, dgauss, grad, stream);
   return BS_OK;
+}
+
+bs_status bs_batch_plan(const bs_batch *batch, bs_batch_sizes *out) {
+  if (!out) return invalid("out is NULL");
+  BatchPlan p;
+  BS_TRY(batch_plan(batch, &p));
+  out->n_open = p.n_open;
+  out->n_closed = p.n_closed;
+  out->n_gauss = p.n_gauss;
+  out->n_pixels = p.n_pix;
+  out->n_tiles = p.n_tiles;
+  out->ws_bytes = p.bytes;
+  return BS_OK;
+}
+
+bs_status bs_batch_setup(const bs_batch *batch, bs_stream stream) {
+  BatchPlan p;
+  BS_TRY(batch_plan_ws(batch, &p));
+  BS_TRY(check_device());
+  std::vector<BatchImage> tab((size_t)p.n_images);
+  fill_batch_table(batch->images, p, tab.data());
+  const cudaStream_t s = (cudaStream_t)stream;
+  BS_CUDA(cudaMemcpyAsync(static_cast<char *>(batch->ws) + p.off_images, tab.data(), sizeof(BatchImage) * tab.size(),
+                          cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaStreamSynchronize(s));
+  return BS_OK;
+}
+
+bs_status bs_batch_curve_order(const bs_batch *batch, const bs_curves *curves, uint32_t *rank_out,
+                               uint32_t *first_out, bs_stream stream) {
+  BatchPlan p;
+  BS_TRY(batch_plan_ws(batch, &p));
+  BS_TRY(check_batch_curves(curves, p, false));
+  if (p.n_curves > 0 && (!rank_out || !first_out)) return invalid("rank_out/first_out is NULL");
+  BS_TRY(check_device());
+  return launch_batch_curve_order(p, batch_table_of(batch, p), *curves, rank_out, first_out, (cudaStream_t)stream);
+}
+
+bs_status bs_batch_sample_curves(const bs_batch *batch, const bs_curves *curves, float *gauss, bs_stream stream) {
+  BatchPlan p;
+  BS_TRY(batch_plan_ws(batch, &p));
+  BS_TRY(check_batch_curves(curves, p, true));
+  if (p.n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  BS_TRY(check_device());
+  return launch_batch_sample_fwd(p, batch_table_of(batch, p), *curves, gauss, (cudaStream_t)stream);
+}
+
+bs_status bs_batch_bin_tiles(const bs_batch *batch, const float *gauss, uint32_t *tile_vals, uint32_t *tile_ranges,
+                             bs_stream stream) {
+  BatchPlan p;
+  BS_TRY(batch_plan_ws(batch, &p));
+  if (p.n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  if (!tile_vals || !tile_ranges || !aligned16(tile_ranges))
+    return invalid("tile_vals and tile_ranges (8-byte aligned) must be device pointers");
+  BS_TRY(check_device());
+  return run_batch_binning(p, batch->ws, gauss, tile_vals, tile_ranges, (cudaStream_t)stream);
+}
+
+bs_status bs_batch_render_fwd(const bs_batch *batch, const float *gauss, const uint32_t *tile_vals,
+                              const uint32_t *tile_ranges, const float *target, float *img, float *T_final,
+                              uint32_t *n_contrib, float *dL_dimg, double *loss_out, bs_stream stream) {
+  BatchPlan p;
+  BS_TRY(batch_plan_ws(batch, &p));
+  if (p.n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  if (!tile_vals || !tile_ranges || !img || !T_final || !n_contrib) return invalid("NULL input or output");
+  if (target && (!dL_dimg || !loss_out)) return invalid("with a target, dL_dimg and loss_out must be non-NULL");
+  BS_TRY(check_device());
+  return launch_batch_render_fwd(p, batch->ws, gauss, tile_vals, tile_ranges, target, img, T_final, n_contrib,
+                                 dL_dimg, loss_out, (cudaStream_t)stream);
+}
+
+bs_status bs_batch_render_bwd(const bs_batch *batch, const float *gauss, const uint32_t *tile_vals,
+                              const uint32_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
+                              const float *dL_dimg, float *dgauss, const bs_curves *curves,
+                              const bs_curves_grad *grad, bs_stream stream) {
+  BatchPlan p;
+  BS_TRY(batch_plan_ws(batch, &p));
+  if (p.n_gauss > 0 && (!gauss || !aligned16(gauss) || !dgauss || !aligned16(dgauss)))
+    return invalid("gauss/dgauss must be 16-byte aligned device pointers");
+  if (!tile_vals || !tile_ranges || !T_final || !n_contrib || !dL_dimg) return invalid("NULL input");
+  if (grad) {
+    BS_TRY(check_batch_curves(curves, p, true));
+    if (p.n_open > 0 && (!grad->open_ctrl || !grad->open_width || !grad->open_color || !grad->open_opac))
+      return invalid("open gradient arrays must be non-NULL");
+    if (p.n_closed > 0 && (!grad->closed_ctrl || !grad->closed_color || !grad->closed_opac))
+      return invalid("closed gradient arrays must be non-NULL");
+  }
+  BS_TRY(check_device());
+  const cudaStream_t s = (cudaStream_t)stream;
+  BS_TRY(launch_batch_render_bwd(p, batch->ws, gauss, tile_vals, tile_ranges, T_final, n_contrib, dL_dimg, dgauss,
+                                 s));
+  if (grad) return launch_batch_sample_bwd(p, batch_table_of(batch, p), *curves, dgauss, *grad, s);
+  return BS_OK;
+}
+
+bs_status bs_batch_status(const bs_batch *batch, int32_t *status_out, int64_t *n_pairs_out, bs_stream stream) {
+  BatchPlan p;
+  BS_TRY(batch_plan_ws(batch, &p));
+  if (!status_out) return invalid("status_out is NULL");
+  return read_batch_status(p, batch->ws, status_out, n_pairs_out, (cudaStream_t)stream);
+}
+
+bs_status bs_adam_step(const bs_adam_group *groups, int32_t n_groups, const bs_adam_cfg *cfg, int32_t *step,
+                       bs_stream stream) {
+  if (!groups || n_groups < 1 || n_groups > BS_ADAM_MAX_GROUPS)
+    return invalid("1 <= n_groups <= %d host groups needed", BS_ADAM_MAX_GROUPS);
+  if (!cfg || !step) return invalid("cfg and step must be non-NULL");
+  if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f))
+    return invalid("betas must be in [0, 1) and eps > 0");
+  for (int k = 0; k < n_groups; ++k) {
+    const bs_adam_group &g = groups[k];
+    if (g.n < 0) return invalid("group %d: n < 0", k);
+    if (g.n > 0 && (!g.param || !g.grad || !g.m || !g.v)) return invalid("group %d: NULL array", k);
+    if (!(g.lr >= 0.f) || !(g.lo <= g.hi)) return invalid("group %d: lr must be >= 0 and lo <= hi", k);
+    if (g.row_scale && g.row_len < 1) return invalid("group %d: row_len must be >= 1", k);
+  }
+  BS_TRY(check_device());
+  return launch_adam(groups, n_groups, *cfg, step, (cudaStream_t)stream);
 }
 
 bs_status bs_prune_densify_workspace(int32_t n_open, int32_t n_closed, const bs_canvas *canvas, size_t *bytes) {

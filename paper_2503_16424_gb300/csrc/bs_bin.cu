@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(const float *gauss
 
 // Exclusive scan of the per-CTA totals (one CTA); writes the pair count and
 // the sentinel partial[n] = P.
-__global__ void __launch_bounds__(1024) scan_partials_kernel(unsigned long long *partial, int64_t n, Hdr *hdr) {
+__global__ void __launch_bounds__(1024) scan_partials_kernel(unsigned long long *partial, int64_t n,
+                                                             unsigned long long *total_out) {
   __shared__ unsigned long long s[1024];
   __shared__ unsigned long long carry;
   if (threadIdx.x == 0) carry = 0;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(unsigned long long 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    hdr->n_pairs = carry;
+    *total_out = carry;
     partial[n] = carry;
   }
 }
@@ -402,13 +403,18 @@ __device__ __forceinline__ int64_t pair_owner(const unsigned long long *__restri
 // owner[c] = the Gaussian whose pairs contain key c * kEmitTile, for every
 // emit CTA c below the capacity.  One thread per Gaussian; a range covers
 // floor((off + cnt - 1) / T) - ceil(off / T) + 1 chunk starts (usually 0 or 1).
+// Pairs of a packed rectangle: {tx0 | ty0 << 16, w | h << 16} (one canvas)
+// or {first tile, tiles_x, w, h} (a batch).
+__device__ __forceinline__ uint32_t rect_pairs(const uint2 &rc) { return (rc.y & 0xffffu) * (rc.y >> 16); }
+__device__ __forceinline__ uint32_t rect_pairs(const uint4 &rc) { return rc.z * rc.w; }
+
+template <typename Rect>
 __global__ void chunk_owner_kernel(const uint32_t *__restrict__ local, const unsigned long long *__restrict__ partial,
-                                   const uint2 *__restrict__ rects, int64_t n_gauss, uint32_t n_chunks,
+                                   const Rect *__restrict__ rects, int64_t n_gauss, uint32_t n_chunks,
                                    uint32_t *__restrict__ owner) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_gauss) return;
-  const uint2 rc = rects[g];
-  const uint32_t cnt = (rc.y & 0xffffu) * (rc.y >> 16);
+  const uint32_t cnt = rect_pairs(rects[g]);
   if (!cnt) return;
   const unsigned long long off = partial[g / kCountThreads] + local[g];
   const unsigned long long c0 = (off + kEmitTile - 1) / kEmitTile, c1 = (off + cnt - 1) / kEmitTile;
@@ -442,7 +448,8 @@ static_assert(2 * kEmitTile == kSortTile, "a sort partition is two emit chunks")
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__restrict__ local,
                                                             const unsigned long long *__restrict__ partial,
                                                             int64_t nb, const uint2 *__restrict__ rects,
-                                                            int64_t n_gauss, const Hdr *hdr, int tiles_x, int gbits,
+                                                            int64_t n_gauss, const unsigned long long *count,
+                                                            int tiles_x, int gbits,
                                                             const uint32_t *__restrict__ owner,
                                                             uint32_t *__restrict__ keys, int bits1,
                                                             uint32_t *__restrict__ hist1, uint32_t parts) {
@@ -450,7 +457,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__re
   __shared__ uint32_t s_off[kWin];
   __shared__ uint32_t s_keys[kEmitTile];
   __shared__ uint32_t s_h[256];
-  const uint32_t n = (uint32_t)hdr->n_pairs;
+  const uint32_t n = (uint32_t)*count;
   const uint32_t k0 = blockIdx.x * (uint32_t)kEmitTile;
   if (k0 >= n) return;
   const int64_t g0 = owner[blockIdx.x];
@@ -509,19 +516,20 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__re
 
 // Digit counts of partition blockIdx.x, stored digit-major:
 // hist[d * parts + partition].
-__global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const uint32_t *__restrict__ in, const Hdr *hdr,
-                                                               int shift, int bits, uint32_t *__restrict__ hist,
-                                                               uint32_t parts) {
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const K *__restrict__ in,
+                                                               const unsigned long long *count, int shift, int bits,
+                                                               uint32_t *__restrict__ hist, uint32_t parts) {
   __shared__ uint32_t s_h[kSortWarps][256];
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&s_h[0][0])[i] = 0u;
   __syncthreads();
-  const uint32_t n = (uint32_t)hdr->n_pairs, nbins = 1u << bits, dmask = nbins - 1;
+  const uint32_t n = (uint32_t)*count, nbins = 1u << bits, dmask = nbins - 1;
   const uint32_t base = blockIdx.x * (uint32_t)kSortTile;
 #pragma unroll 4
   for (int i = tid; i < kSortTile; i += kSortThreads) {
     const uint32_t idx = base + (uint32_t)i;
-    if (idx < n) atomicAdd(&s_h[warp][(in[idx] >> shift) & dmask], 1u);
+    if (idx < n) atomicAdd(&s_h[warp][(uint32_t)(in[idx] >> shift) & dmask], 1u);
   }
   __syncthreads();
   for (uint32_t d = tid; d < nbins; d += kSortThreads) {
@@ -572,19 +580,25 @@ __global__ void __launch_bounds__(kScanThreads) scan_parts_kernel(uint32_t *__re
 // with the same digit (peer lanes from ballots, then per-warp running counts), keys
 // gathered by digit in shared memory, then written at the partition's first
 // output index for the digit (from scan_parts_kernel) plus their rank.
-__global__ void __launch_bounds__(kSortThreads, 4) downsweep_kernel(const uint32_t *__restrict__ in,
-                                                                 uint32_t *__restrict__ out, const Hdr *hdr,
+// K: the key type; O: the output type (the last pass of a batch writes the
+// key's low 32 bits, the Gaussian index, only).  A partition past the count
+// has nothing to write.
+template <typename K, typename O>
+__global__ void __launch_bounds__(kSortThreads, 4) downsweep_kernel(const K *__restrict__ in,
+                                                                 O *__restrict__ out,
+                                                                 const unsigned long long *count,
                                                                  int shift, int bits,
                                                                  const uint32_t *__restrict__ offs, uint32_t parts) {
-  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ K s_keys[kSortTile];
   __shared__ uint32_t s_whist[kSortWarps][256];
   __shared__ uint32_t s_bexcl[256];
   __shared__ uint32_t s_dst[256];
   __shared__ uint32_t s_wtot[kSortWarps];
-  const uint32_t n = (uint32_t)hdr->n_pairs;
+  const uint32_t n = (uint32_t)*count;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t nbins = 1u << bits, dmask = nbins - 1;
   const uint32_t part = blockIdx.x;
+  if (part * (uint32_t)kSortTile >= n) return;
   for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
   __syncthreads();
   const uint32_t base = part * (uint32_t)kSortTile + (uint32_t)warp * (32u * kSortItems);
@@ -592,17 +606,18 @@ __global__ void __launch_bounds__(kSortThreads, 4) downsweep_kernel(const uint32
 
   // a key's rank among its warp's keys of the same digit is < 512: two
   // ranks share a register
-  uint32_t keys[kSortItems], rank2[kSortItems / 2];
+  K keys[kSortItems];
+  uint32_t rank2[kSortItems / 2];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t idx = base + (uint32_t)i * 32u + (uint32_t)lane;
-    keys[i] = idx < n ? in[idx] : 0u;
+    keys[i] = idx < n ? in[idx] : K(0);
   }
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t idx = base + (uint32_t)i * 32u + (uint32_t)lane;
     const bool valid = idx < n;
-    const uint32_t d = (keys[i] >> shift) & dmask;
+    const uint32_t d = (uint32_t)(keys[i] >> shift) & dmask;
     // lanes with the same digit: the AND of one ballot per digit bit
     unsigned peers = __ballot_sync(0xffffffffu, valid);
     for (int b = 0; b < bits; ++b) {
@@ -644,7 +659,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) downsweep_kernel(const uint32
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t idx = base + (uint32_t)i * 32u + (uint32_t)lane;
     if (idx < n) {
-      const uint32_t d = (keys[i] >> shift) & dmask;
+      const uint32_t d = (uint32_t)(keys[i] >> shift) & dmask;
       s_keys[s_bexcl[d] + s_whist[warp][d] + ((rank2[i >> 1] >> (16 * (i & 1))) & 0xffffu)] = keys[i];
     }
   }
@@ -652,11 +667,321 @@ __global__ void __launch_bounds__(kSortThreads, 4) downsweep_kernel(const uint32
   const uint32_t pstart = part * (uint32_t)kSortTile;
   const uint32_t n_here = n > pstart ? min((uint32_t)kSortTile, n - pstart) : 0u;
   for (uint32_t j = tid; j < n_here; j += kSortThreads) {
-    const uint32_t k = s_keys[j];
-    out[s_dst[(k >> shift) & dmask] + j] = k;
+    const K k = s_keys[j];
+    out[s_dst[(uint32_t)(k >> shift) & dmask] + j] = (O)k;
   }
 }
 
+
+// ---- batches of images ----
+
+// Per Gaussian of a batch: its image's tile rectangle (the rule of
+// tile_rect on the image's canvas), packed as {first tile (global), tiles_x,
+// w, h}; its pair count and block-local offset; the four corner updates of
+// its image's difference array.
+__global__ void __launch_bounds__(kCountThreads) batch_count_kernel(const float *gauss, int64_t n_gauss,
+                                                                    const BatchImage *__restrict__ tab, int n_images,
+                                                                    int tile, uint32_t *local,
+                                                                    unsigned long long *partial, uint4 *rects,
+                                                                    int *diff) {
+  __shared__ uint32_t s_warp[kCountThreads / 32];
+  const int64_t g = (int64_t)blockIdx.x * kCountThreads + threadIdx.x;
+  uint32_t cnt = 0;
+  if (g < n_gauss) {
+    const BatchImage &im = tab[last_image_le<&BatchImage::gauss0>(tab, n_images, g)];
+    uint4 packed = make_uint4(0u, 0u, 0u, 0u);
+    Rect r;
+    if (tile_rect(gauss, g, im.W, im.H, tile, &r)) {
+      const uint32_t w = (uint32_t)(r.tx1 - r.tx0 + 1), h = (uint32_t)(r.ty1 - r.ty0 + 1);
+      cnt = w * h;
+      packed = make_uint4((uint32_t)(im.tile0 + (int64_t)r.ty0 * im.tiles_x + r.tx0), (uint32_t)im.tiles_x, w, h);
+      const int stride = im.tiles_x + 1;
+      int *d = diff + im.diff0;
+      atomicAdd(d + r.ty0 * stride + r.tx0, 1);
+      atomicAdd(d + r.ty0 * stride + r.tx1 + 1, -1);
+      atomicAdd(d + (r.ty1 + 1) * stride + r.tx0, -1);
+      atomicAdd(d + (r.ty1 + 1) * stride + r.tx1 + 1, 1);
+    }
+    rects[g] = packed;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t incl = warp_incl_scan(cnt, lane);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < kCountThreads / 32 ? s_warp[lane] : 0u;
+    v = warp_incl_scan(v, lane);
+    if (lane < kCountThreads / 32) s_warp[lane] = v;
+  }
+  __syncthreads();
+  const uint32_t warp_excl = warp == 0 ? 0u : s_warp[warp - 1];
+  if (g < n_gauss) local[g] = warp_excl + incl - cnt;
+  if (threadIdx.x == kCountThreads - 1) partial[blockIdx.x] = warp_excl + incl;
+}
+
+// Row scans of every image's difference array: one warp per row.
+__global__ void batch_diff_rows_kernel(int *diff, const BatchImage *__restrict__ tab, int n_images, int64_t n_rows) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  const BatchImage &im = tab[last_image_le<&BatchImage::row0>(tab, n_images, row)];
+  const int cols = im.tiles_x + 1;
+  int *d = diff + im.diff0 + (row - im.row0) * cols;
+  int carry = 0;
+  for (int c0 = 0; c0 < cols; c0 += 32) {
+    const int c = c0 + lane;
+    int v = c < cols ? d[c] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    if (c < cols) d[c] = carry + v;
+    carry += __shfl_sync(0xffffffffu, v, 31);
+  }
+}
+
+// Column scans of every image's difference array: one warp per column.
+__global__ void batch_diff_cols_kernel(int *diff, const BatchImage *__restrict__ tab, int n_images, int64_t n_cols) {
+  const int64_t col = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= n_cols) return;
+  const BatchImage &im = tab[last_image_le<&BatchImage::col0>(tab, n_images, col)];
+  const int cols = im.tiles_x + 1, rows = im.tiles_y + 1;
+  int *d = diff + im.diff0 + (col - im.col0);
+  int carry = 0;
+  for (int r0 = 0; r0 < rows; r0 += 32) {
+    const int r = r0 + lane;
+    int v = r < rows ? d[(size_t)r * cols] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    if (r < rows) d[(size_t)r * cols] = carry + v;
+    carry += __shfl_sync(0xffffffffu, v, 31);
+  }
+}
+
+// Per-tile counts of a batch in tile order: thread i of CTA c walks tiles
+// [(c 256 + i) 8, +8), which may cross into the next image.
+constexpr int kTileThreads = 256;
+constexpr int kTileItems = 8;
+constexpr int kTilesPerCta = kTileThreads * kTileItems;
+
+struct TileWalk {
+  int b, tiles_x, tx, ty;
+  int64_t next0, diff0;
+};
+
+__device__ __forceinline__ TileWalk tile_walk_start(const BatchImage *__restrict__ tab, int n_images, int64_t t) {
+  TileWalk w;
+  w.b = last_image_le<&BatchImage::tile0>(tab, n_images, t);
+  const BatchImage &im = tab[w.b];
+  const int local = (int)(t - im.tile0);
+  w.tiles_x = im.tiles_x;
+  w.ty = local / im.tiles_x;
+  w.tx = local - w.ty * im.tiles_x;
+  w.diff0 = im.diff0;
+  w.next0 = w.b + 1 < n_images ? tab[w.b + 1].tile0 : INT64_MAX;
+  return w;
+}
+
+// The count of tile t (the walk's current tile), then the walk moves on.
+__device__ __forceinline__ uint32_t tile_walk_next(TileWalk &w, const BatchImage *__restrict__ tab, int n_images,
+                                                   const int *__restrict__ diff, int64_t t) {
+  if (t == w.next0) {  // the next image starts at its tile (0, 0)
+    ++w.b;
+    w.tiles_x = tab[w.b].tiles_x;
+    w.diff0 = tab[w.b].diff0;
+    w.next0 = w.b + 1 < n_images ? tab[w.b + 1].tile0 : INT64_MAX;
+    w.tx = w.ty = 0;
+  }
+  const uint32_t v = (uint32_t)diff[w.diff0 + (int64_t)w.ty * (w.tiles_x + 1) + w.tx];
+  if (++w.tx == w.tiles_x) {
+    w.tx = 0;
+    ++w.ty;
+  }
+  return v;
+}
+
+// Sum of each CTA's tiles (tsum) and, per sort pass, the digit totals of the
+// tile ids weighted by their counts (hist, added atomically).
+__global__ void __launch_bounds__(kTileThreads) batch_tile_reduce_kernel(const int *__restrict__ diff,
+                                                                         const BatchImage *__restrict__ tab,
+                                                                         int n_images, int64_t n_tiles, int passes,
+                                                                         int digit_bits,
+                                                                         unsigned long long *__restrict__ tsum,
+                                                                         uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_h[kMaxPasses * 256];
+  __shared__ unsigned long long s_w[kTileThreads / 32];
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += kTileThreads) s_h[i] = 0u;
+  __syncthreads();
+  const uint32_t dmask = (1u << digit_bits) - 1;
+  const int64_t t0 = ((int64_t)blockIdx.x * kTileThreads + threadIdx.x) * kTileItems;
+  unsigned long long sum = 0;
+  if (t0 < n_tiles) {
+    TileWalk w = tile_walk_start(tab, n_images, t0);
+    for (int k = 0; k < kTileItems; ++k) {
+      const int64_t t = t0 + k;
+      if (t >= n_tiles) break;
+      const uint32_t v = tile_walk_next(w, tab, n_images, diff, t);
+      sum += v;
+      if (v)
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (((uint32_t)t >> (p * digit_bits)) & dmask)], v);
+    }
+  }
+  unsigned long long x = sum;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+#pragma unroll
+    for (int w = 0; w < kTileThreads / 32; ++w) t += s_w[w];
+    tsum[blockIdx.x] = t;
+  }
+  for (int i = threadIdx.x; i < passes * 256; i += kTileThreads)
+    if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
+}
+
+// The pair count against the capacity (status and the count to sort), and
+// per pass the exclusive prefix of the digit totals: where each digit's
+// keys start.  One warp per pass.
+// The sort trusts that the digit starts (from the tile counts) and the keys
+// (from the Gaussians' rectangles) agree; both totals are compared and
+// nothing is sorted if they differ.
+__global__ void batch_digits_kernel(BatchHdr *hdr, int64_t capacity, int passes, uint32_t *hist) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long P = hdr->n_pairs;
+  const bool over = P > (unsigned long long)capacity;
+  const bool mismatch = hdr->tile_total != P;
+  if (threadIdx.x == 0) {
+    hdr->n_sorted = (over || mismatch) ? 0ull : P;
+    if (over) hdr->status |= kDevErrCapacity;
+    if (mismatch) hdr->status |= kDevErrCounts;
+  }
+  if (warp < passes) {
+    uint32_t carry = 0;
+    for (int d0 = 0; d0 < 256; d0 += 32) {
+      const uint32_t v = hist[warp * 256 + d0 + lane];
+      const uint32_t incl = warp_incl_scan(v, lane);
+      hist[warp * 256 + d0 + lane] = carry + incl - v;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
+// Tile ranges of a batch: tsum holds each CTA's first output index (the
+// exclusive scan of the CTA sums).  Every range is (0, 0) after an overflow.
+__global__ void __launch_bounds__(kTileThreads) batch_tile_ranges_kernel(const int *__restrict__ diff,
+                                                                         const BatchImage *__restrict__ tab,
+                                                                         int n_images, int64_t n_tiles,
+                                                                         const unsigned long long *__restrict__ tsum,
+                                                                         const BatchHdr *hdr, uint2 *__restrict__ ranges) {
+  __shared__ unsigned long long s_w[kTileThreads / 32];
+  const int64_t t0 = ((int64_t)blockIdx.x * kTileThreads + threadIdx.x) * kTileItems;
+  uint32_t cnt[kTileItems];
+  unsigned long long sum = 0;
+  TileWalk w;
+  if (t0 < n_tiles) {
+    w = tile_walk_start(tab, n_images, t0);
+#pragma unroll
+    for (int k = 0; k < kTileItems; ++k) {
+      const int64_t t = t0 + k;
+      cnt[k] = t < n_tiles ? tile_walk_next(w, tab, n_images, diff, t) : 0u;
+      sum += cnt[k];
+    }
+  }
+  // block-exclusive prefix of the thread sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  unsigned long long base = tsum[blockIdx.x];
+  for (int k = 0; k < warp; ++k) base += s_w[k];
+  if (t0 >= n_tiles) return;
+  const bool over = (hdr->status & (kDevErrCapacity | kDevErrCounts)) != 0u;
+  unsigned long long start = base + incl - sum;
+#pragma unroll
+  for (int k = 0; k < kTileItems; ++k) {
+    const int64_t t = t0 + k;
+    if (t >= n_tiles) break;
+    ranges[t] = (!over && cnt[k]) ? make_uint2((uint32_t)start, (uint32_t)(start + cnt[k])) : make_uint2(0u, 0u);
+    start += cnt[k];
+  }
+}
+
+// emit_kernel for a batch: 64-bit keys (global tile << 32 | g) from the
+// packed rectangles {first tile, tiles_x, w, h}; the first sort pass's digit
+// counts go to hist1 as in emit_kernel.
+__global__ void __launch_bounds__(kEmitThreads) batch_emit_kernel(const uint32_t *__restrict__ local,
+                                                                  const unsigned long long *__restrict__ partial,
+                                                                  int64_t nb, const uint4 *__restrict__ rects,
+                                                                  int64_t n_gauss, const unsigned long long *count,
+                                                                  const uint32_t *__restrict__ owner,
+                                                                  unsigned long long *__restrict__ keys, int bits1,
+                                                                  uint32_t *__restrict__ hist1, uint32_t parts) {
+  constexpr int kWin = kEmitTile + 1;
+  __shared__ uint32_t s_off[kWin];
+  __shared__ unsigned long long s_keys[kEmitTile];
+  __shared__ uint32_t s_h[256];
+  const uint32_t n = (uint32_t)*count;
+  const uint32_t k0 = blockIdx.x * (uint32_t)kEmitTile;
+  if (k0 >= n) return;
+  const int64_t g0 = owner[blockIdx.x];
+  const bool last_chunk = k0 + (uint32_t)kEmitTile >= n;
+  const int64_t win_need = last_chunk ? n_gauss - g0 + 1 : (int64_t)owner[blockIdx.x + 1] - g0 + 2;
+  const int win = (int)(win_need < kWin ? win_need : kWin);
+  for (int k = threadIdx.x; k < 256; k += kEmitThreads) s_h[k] = 0u;
+  for (int k = threadIdx.x; k < win; k += kEmitThreads) {
+    const int64_t g = g0 + k;
+    s_off[k] = g < n_gauss ? global_offset(partial, local, g) : 0xffffffffu;
+  }
+  __syncthreads();
+  const uint32_t i0 = k0 + (uint32_t)threadIdx.x * kEmitItems;
+  const uint32_t dmask = (1u << bits1) - 1;
+  if (i0 < n) {
+    int64_t g = window_owner(s_off, win, g0, partial, nb, local, n_gauss, i0);
+    uint32_t off = global_offset(partial, local, g);
+    uint4 rc = rects[g];
+    uint32_t cnt = rc.z * rc.w;
+    uint32_t l = i0 - off;
+    uint32_t ry = l / rc.z, rx = l - ry * rc.z;
+#pragma unroll
+    for (int it = 0; it < kEmitItems; ++it) {
+      const uint32_t i = i0 + (uint32_t)it;
+      if (i >= n) break;
+      if (i - off >= cnt) {  // left the owner's pairs
+        g = window_owner(s_off, win, g0, partial, nb, local, n_gauss, i);
+        off = global_offset(partial, local, g);
+        rc = rects[g];
+        cnt = rc.z * rc.w;
+        l = i - off;
+        ry = l / rc.z;
+        rx = l - ry * rc.z;
+      }
+      const uint32_t tid = rc.x + ry * rc.y + rx;
+      s_keys[threadIdx.x * kEmitItems + it] = ((unsigned long long)tid << 32) | (unsigned long long)g;
+      atomicAdd(&s_h[tid & dmask], 1u);
+      if (++rx == rc.z) {
+        rx = 0;
+        ++ry;
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t m = min((uint32_t)kEmitTile, n - k0);
+  for (uint32_t j = threadIdx.x; j < m; j += kEmitThreads) keys[k0 + j] = s_keys[j];
+  for (uint32_t d = threadIdx.x; d <= dmask; d += kEmitThreads)
+    if (s_h[d]) atomicAdd(&hist1[(size_t)d * parts + (blockIdx.x >> 1)], s_h[d]);
+}
 
 }  // namespace
 
@@ -734,9 +1059,9 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     count_kernel<<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(gauss, p.n_gauss, cv.width, cv.height,
                                                                     cv.tile, p.tiles_x, local, partial, rects, diff);
     BS_LAUNCHED("count_kernel");
-    scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, hdr);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, &hdr->n_pairs);
     BS_LAUNCHED("scan_partials_kernel");
-    chunk_owner_kernel<<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(
+    chunk_owner_kernel<uint2><<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(
         local, partial, rects, p.n_gauss, (uint32_t)div_up64(p.capacity, kEmitTile), owner);
     BS_LAUNCHED("chunk_owner_kernel");
   }
@@ -777,7 +1102,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   const int bits0 = std::min(p.digit_bits, p.tbits);
   BS_CUDA(cudaMemsetAsync(part_offs, 0, sizeof(uint32_t) * ((size_t)1 << bits0) * (size_t)parts, s));
   emit_kernel<<<(unsigned)div_up64(P, kEmitTile), kEmitThreads, 0, s>>>(local, partial, p.count_blocks, rects,
-                                                                       p.n_gauss, hdr, p.tiles_x, p.gbits, owner,
+                                                                       p.n_gauss, &hdr->n_pairs, p.tiles_x, p.gbits, owner,
                                                                        src, bits0, part_offs, (uint32_t)parts);
   BS_LAUNCHED("emit_kernel");
   for (int pass = 0; pass < p.passes; ++pass) {
@@ -785,16 +1110,109 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     const int shift = p.gbits + pass * p.digit_bits;
     const int bits = std::min(p.digit_bits, p.tbits - pass * p.digit_bits);
     if (pass > 0) {  // the first pass's counts come from emit_kernel
-      upsweep_kernel<<<(unsigned)parts, kSortThreads, 0, s>>>(src, hdr, shift, bits, part_offs, (uint32_t)parts);
+      upsweep_kernel<uint32_t><<<(unsigned)parts, kSortThreads, 0, s>>>(src, &hdr->n_pairs, shift, bits, part_offs,
+                                                                        (uint32_t)parts);
       BS_LAUNCHED("upsweep_kernel");
     }
     scan_parts_kernel<<<1u << bits, kScanThreads, 0, s>>>(part_offs, (uint32_t)parts, hist + pass * 256);
     BS_LAUNCHED("scan_parts_kernel");
-    downsweep_kernel<<<(unsigned)parts, kSortThreads, 0, s>>>(src, dst, hdr, shift, bits, part_offs,
-                                                               (uint32_t)parts);
+    downsweep_kernel<uint32_t, uint32_t><<<(unsigned)parts, kSortThreads, 0, s>>>(src, dst, &hdr->n_pairs, shift,
+                                                                                   bits, part_offs, (uint32_t)parts);
     BS_LAUNCHED("downsweep_kernel");
     src = dst;
   }
+  return BS_OK;
+}
+
+bs_status run_batch_binning(const BatchPlan &p, void *ws, const float *gauss, uint32_t *tile_vals,
+                            uint32_t *tile_ranges, cudaStream_t s) {
+  char *base = static_cast<char *>(ws);
+  BatchHdr *hdr = reinterpret_cast<BatchHdr *>(base + p.off_hdr);
+  uint32_t *hist = reinterpret_cast<uint32_t *>(base + p.off_hist);
+  int *diff = reinterpret_cast<int *>(base + p.off_diff);
+  const BatchImage *tab = reinterpret_cast<const BatchImage *>(base + p.off_images);
+  uint32_t *part_offs = reinterpret_cast<uint32_t *>(base + p.off_parts);
+  uint32_t *local = reinterpret_cast<uint32_t *>(base + p.off_local);
+  auto *partial = reinterpret_cast<unsigned long long *>(base + p.off_partial);
+  uint4 *rects = reinterpret_cast<uint4 *>(base + p.off_rects);
+  uint32_t *owner = reinterpret_cast<uint32_t *>(base + p.off_owner);
+  auto *tsum = reinterpret_cast<unsigned long long *>(base + p.off_tsum);
+  auto *keys0 = reinterpret_cast<unsigned long long *>(base + p.off_keys0);
+  auto *keys1 = reinterpret_cast<unsigned long long *>(base + p.off_keys1);
+  uint2 *ranges = reinterpret_cast<uint2 *>(tile_ranges);
+  {
+    const size_t nz = p.zero_bytes / sizeof(uint32_t);
+    const int blocks = (int)std::min<int64_t>(div_up64((int64_t)nz, 256), 152 * 8);
+    zero_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<uint32_t *>(base), nz);
+    BS_LAUNCHED("zero_kernel");
+  }
+  if (p.n_gauss > 0) {
+    batch_count_kernel<<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(gauss, p.n_gauss, tab, p.n_images,
+                                                                          p.tile, local, partial, rects, diff);
+    BS_LAUNCHED("batch_count_kernel");
+    scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, &hdr->n_pairs);
+    BS_LAUNCHED("scan_partials_kernel");
+    chunk_owner_kernel<uint4><<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(
+        local, partial, rects, p.n_gauss, (uint32_t)div_up64(p.capacity, kEmitTile), owner);
+    BS_LAUNCHED("chunk_owner_kernel");
+  }
+  batch_diff_rows_kernel<<<(unsigned)div_up64(p.diff_rows, 8), 256, 0, s>>>(diff, tab, p.n_images, p.diff_rows);
+  BS_LAUNCHED("batch_diff_rows_kernel");
+  batch_diff_cols_kernel<<<(unsigned)div_up64(p.diff_cols, 8), 256, 0, s>>>(diff, tab, p.n_images, p.diff_cols);
+  BS_LAUNCHED("batch_diff_cols_kernel");
+  batch_tile_reduce_kernel<<<(unsigned)p.tile_blocks, kTileThreads, 0, s>>>(diff, tab, p.n_images, p.n_tiles,
+                                                                            p.passes, p.digit_bits, tsum, hist);
+  BS_LAUNCHED("batch_tile_reduce_kernel");
+  scan_partials_kernel<<<1, 1024, 0, s>>>(tsum, p.tile_blocks, &hdr->tile_total);
+  BS_LAUNCHED("scan_partials_kernel");
+  batch_digits_kernel<<<1, 32 * kMaxPasses, 0, s>>>(hdr, p.capacity, p.passes, hist);
+  BS_LAUNCHED("batch_digits_kernel");
+  batch_tile_ranges_kernel<<<(unsigned)p.tile_blocks, kTileThreads, 0, s>>>(diff, tab, p.n_images, p.n_tiles, tsum,
+                                                                            hdr, ranges);
+  BS_LAUNCHED("batch_tile_ranges_kernel");
+  // emit and sort, sized by the capacity: kernels past the pair count return
+  const int bits0 = std::min(p.digit_bits, p.tbits);
+  BS_CUDA(cudaMemsetAsync(part_offs, 0, sizeof(uint32_t) * ((size_t)1 << bits0) * (size_t)p.parts, s));
+  batch_emit_kernel<<<(unsigned)div_up64(p.capacity, kEmitTile), kEmitThreads, 0, s>>>(
+      local, partial, p.count_blocks, rects, p.n_gauss, &hdr->n_sorted, owner, keys0, bits0, part_offs,
+      (uint32_t)p.parts);
+  BS_LAUNCHED("batch_emit_kernel");
+  unsigned long long *src = keys0;
+  for (int pass = 0; pass < p.passes; ++pass) {
+    const int shift = 32 + pass * p.digit_bits;
+    const int bits = std::min(p.digit_bits, p.tbits - pass * p.digit_bits);
+    if (pass > 0) {
+      upsweep_kernel<unsigned long long><<<(unsigned)p.parts, kSortThreads, 0, s>>>(src, &hdr->n_sorted, shift, bits,
+                                                                                   part_offs, (uint32_t)p.parts);
+      BS_LAUNCHED("upsweep_kernel");
+    }
+    scan_parts_kernel<<<1u << bits, kScanThreads, 0, s>>>(part_offs, (uint32_t)p.parts, hist + pass * 256);
+    BS_LAUNCHED("scan_parts_kernel");
+    if (pass + 1 < p.passes) {
+      unsigned long long *dst = src == keys0 ? keys1 : keys0;
+      downsweep_kernel<unsigned long long, unsigned long long><<<(unsigned)p.parts, kSortThreads, 0, s>>>(
+          src, dst, &hdr->n_sorted, shift, bits, part_offs, (uint32_t)p.parts);
+      src = dst;
+    } else {
+      downsweep_kernel<unsigned long long, uint32_t><<<(unsigned)p.parts, kSortThreads, 0, s>>>(
+          src, tile_vals, &hdr->n_sorted, shift, bits, part_offs, (uint32_t)p.parts);
+    }
+    BS_LAUNCHED("downsweep_kernel");
+  }
+  return BS_OK;
+}
+
+bs_status read_batch_status(const BatchPlan &p, const void *ws, int32_t *status, int64_t *n_pairs, cudaStream_t s) {
+  BatchHdr h;
+  BS_CUDA(cudaMemcpyAsync(&h, static_cast<const char *>(ws) + p.off_hdr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  BS_CUDA(cudaStreamSynchronize(s));
+  *status = (h.status & kDevErrCapacity) ? BS_ERR_CAPACITY : BS_OK;
+  if (h.status & kDevErrCounts) {
+    set_error("batch binning: %llu pairs from the Gaussians but %llu from the tiles; nothing was sorted",
+              h.n_pairs, h.tile_total);
+    *status = BS_ERR_UNSUPPORTED;
+  }
+  if (n_pairs) *n_pairs = (int64_t)h.n_pairs;
   return BS_OK;
 }
 

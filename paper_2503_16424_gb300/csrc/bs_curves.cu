@@ -200,11 +200,24 @@ __device__ __forceinline__ CurveAttr curve_attr(const bs_curves &c, int curve, i
   return a;
 }
 
+// The sampling of curve `curve` of a batch: its image's.
+__device__ __forceinline__ Cfg batch_cfg(const BatchImage *__restrict__ tab, int n_images, const bs_curves &c,
+                                         int curve) {
+  const int b = curve < c.n_open ? last_image_le<&BatchImage::open0>(tab, n_images, curve)
+                                 : last_image_le<&BatchImage::closed0>(tab, n_images, curve - c.n_open);
+  const BatchImage &im = tab[b];
+  return Cfg{im.g_open, im.rows, im.kc, im.rho, im.eps};
+}
+
+// tab == nullptr: one canvas, sampling cfg; else a batch, each curve with
+// its image's sampling (dynamic shared memory sized for the largest).
 __global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss, int n_max,
-                                                                   int k_max) {
+                                                                   int k_max, const BatchImage *tab = nullptr,
+                                                                   int n_images = 0) {
   extern __shared__ double2 smem_fwd[];
-  const CurveSmem m = carve(smem_fwd, n_max, k_max, cfg.rows, false);
   const int curve = blockIdx.x;
+  if (tab) cfg = batch_cfg(tab, n_images, c, curve);
+  const CurveSmem m = carve(smem_fwd, n_max, k_max, cfg.rows, false);
   const bool closed = curve >= c.n_open;
   const int n = eval_samples(c, cfg, curve, m);
   const int K = closed ? cfg.kc : cfg.g_open;
@@ -246,8 +259,11 @@ __device__ __forceinline__ float warp_sum(float v) {
 // coordinate gathers the Bernstein-weighted (and, for closed rows,
 // tau-weighted, Eq. 4) gradients of the sample points it moves.
 __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
-                                                                   bs_curves_grad g, int n_max, int k_max) {
+                                                                   bs_curves_grad g, int n_max, int k_max,
+                                                                   const BatchImage *tab = nullptr,
+                                                                   int n_images = 0) {
   extern __shared__ double2 smem_bwd[];
+  if (tab) cfg = batch_cfg(tab, n_images, c, blockIdx.x);
   const CurveSmem m = carve(smem_bwd, n_max, k_max, cfg.rows, true);
   float2 *GM = m.G, *GE = m.G + n_max, *GT = m.G + 2 * n_max, *GF = m.G + 3 * n_max;
   __shared__ float sAttr[8];  // opac[3] (open) or opac (closed), colour[3], width
@@ -423,6 +439,57 @@ __global__ void curve_order_first_kernel(int n, int g_open, int g_closed, const 
   first[i] = ob * (uint32_t)g_open + (rank[i] - ob) * (uint32_t)g_closed;
 }
 
+// Draw order of a batch: ranks within each image.  CTA k of the grid is
+// (image b, chunk ci of its curves, chunk cj of the keys it compares with),
+// k - order0_b = ci order_chunks_b + cj.  Image-local curve l is open curve
+// open0_b + l for l < n_open_b, else closed curve closed0_b + l - n_open_b,
+// and equal keys rank by l, as bs_curve_order does on the image alone.
+__device__ __forceinline__ int batch_curve(const BatchImage &im, int total_open, int l) {
+  return l < im.n_open ? (int)im.open0 + l : total_open + (int)im.closed0 + (l - im.n_open);
+}
+
+__global__ void __launch_bounds__(kOrderThreads) batch_curve_order_count_kernel(bs_curves c,
+                                                                               const BatchImage *__restrict__ tab,
+                                                                               int n_images, uint32_t *rank,
+                                                                               uint32_t *open_before) {
+  __shared__ uint32_t sk[kOrderChunk];
+  const int b = last_image_le<&BatchImage::order0>(tab, n_images, blockIdx.x);
+  const BatchImage &im = tab[b];
+  const int local = blockIdx.x - (int)im.order0;
+  const int ci = local / im.order_chunks, cj = local - ci * im.order_chunks;
+  const int n = im.n_open + im.n_closed;
+  const int i = ci * kOrderThreads + threadIdx.x;  // image-local
+  const int base = cj * kOrderChunk;
+  const int m = min(kOrderChunk, n - base);
+  for (int q = threadIdx.x; q < m; q += blockDim.x) sk[q] = key_order(area_key(c, batch_curve(im, c.n_open, base + q)));
+  const int gi = i < n ? batch_curve(im, c.n_open, i) : 0;
+  const uint32_t mine = i < n ? key_order(area_key(c, gi)) : 0u;
+  __syncthreads();
+  if (i >= n) return;
+  uint32_t before = 0, ob = 0;
+  const int open_end = im.n_open - base;  // chunk entries q < open_end are open curves
+  for (int q = 0; q < m; ++q) {
+    const uint32_t kq = sk[q];
+    const bool prec = kq < mine || (kq == mine && base + q < i);
+    before += prec;
+    ob += prec && q < open_end;
+  }
+  if (before) atomicAdd(&rank[gi], before);
+  if (ob) atomicAdd(&open_before[gi], ob);
+}
+
+// first_i = gauss0_b + g_open_b (open curves before i) + G_closed_b (closed curves before i)
+__global__ void batch_curve_order_first_kernel(bs_curves c, const BatchImage *__restrict__ tab, int n_images,
+                                               const uint32_t *rank, uint32_t *first) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.n_open + c.n_closed) return;
+  const int b = i < c.n_open ? last_image_le<&BatchImage::open0>(tab, n_images, i)
+                             : last_image_le<&BatchImage::closed0>(tab, n_images, i - c.n_open);
+  const BatchImage &im = tab[b];
+  const uint32_t ob = first[i];
+  first[i] = (uint32_t)im.gauss0 + ob * (uint32_t)im.g_open + (rank[i] - ob) * (uint32_t)(im.rows * im.kc);
+}
+
 Cfg to_cfg(const bs_sample_cfg &s) { return Cfg{s.g_open, s.rows_closed, s.k_closed, s.rho, s.cov_eps}; }
 
 int max_samples(const bs_curves &c, const bs_sample_cfg &cfg) {
@@ -440,6 +507,26 @@ int max_k(const bs_curves &c, const bs_sample_cfg &cfg) {
 }
 
 }  // namespace
+
+// Dynamic shared memory of the sampling kernels: the attribute is raised
+// per device and kernel to the largest size asked so far, never lowered (a
+// batch sizes it for its largest image).
+template <typename Kernel>
+bs_status raise_smem(Kernel k, size_t smem, int slot) {
+  constexpr int kMaxDev = 64;
+  static size_t done[kMaxDev][2] = {};
+  int dev = 0;
+  BS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) {
+    set_error("device %d: at most %d devices supported", dev, kMaxDev);
+    return BS_ERR_UNSUPPORTED;
+  }
+  if (smem > done[dev][slot]) {
+    BS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    done[dev][slot] = smem;
+  }
+  return BS_OK;
+}
 
 bs_status launch_curve_order(const bs_curves &c, const bs_sample_cfg &cfg, uint32_t *rank, uint32_t *first,
                              cudaStream_t s) {
@@ -460,7 +547,7 @@ bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float 
   if (n == 0) return BS_OK;
   const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
   const size_t smem = curve_smem_bytes(n_max, k_max, cfg.rows_closed, false);
-  BS_CUDA(cudaFuncSetAttribute(sample_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
   sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), gauss, n_max, k_max);
   BS_LAUNCHED("sample_fwd_kernel");
   return BS_OK;
@@ -472,8 +559,43 @@ bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const 
   if (n == 0) return BS_OK;
   const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
   const size_t smem = curve_smem_bytes(n_max, k_max, cfg.rows_closed, true);
-  BS_CUDA(cudaFuncSetAttribute(sample_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
   sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), dgauss, g, n_max, k_max);
+  BS_LAUNCHED("sample_bwd_kernel");
+  return BS_OK;
+}
+
+bs_status launch_batch_curve_order(const BatchPlan &p, const BatchImage *table, const bs_curves &c,
+                                   uint32_t *rank, uint32_t *first, cudaStream_t s) {
+  const int n = c.n_open + c.n_closed;
+  if (n == 0) return BS_OK;
+  BS_CUDA(cudaMemsetAsync(rank, 0, sizeof(uint32_t) * n, s));
+  BS_CUDA(cudaMemsetAsync(first, 0, sizeof(uint32_t) * n, s));
+  batch_curve_order_count_kernel<<<(unsigned)p.order_ctas, kOrderThreads, 0, s>>>(c, table, p.n_images, rank, first);
+  BS_LAUNCHED("batch_curve_order_count_kernel");
+  batch_curve_order_first_kernel<<<div_up(n, 256), 256, 0, s>>>(c, table, p.n_images, rank, first);
+  BS_LAUNCHED("batch_curve_order_first_kernel");
+  return BS_OK;
+}
+
+bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, const bs_curves &c, float *gauss,
+                                  cudaStream_t s) {
+  const int n = c.n_open + c.n_closed;
+  if (n == 0) return BS_OK;
+  const size_t smem = curve_smem_bytes(p.n_max, p.k_max, p.rows_max, false);
+  BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
+  sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, Cfg{}, gauss, p.n_max, p.k_max, table, p.n_images);
+  BS_LAUNCHED("sample_fwd_kernel");
+  return BS_OK;
+}
+
+bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, const bs_curves &c,
+                                  const float *dgauss, const bs_curves_grad &g, cudaStream_t s) {
+  const int n = c.n_open + c.n_closed;
+  if (n == 0) return BS_OK;
+  const size_t smem = curve_smem_bytes(p.n_max, p.k_max, p.rows_max, true);
+  BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
+  sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, Cfg{}, dgauss, g, p.n_max, p.k_max, table, p.n_images);
   BS_LAUNCHED("sample_bwd_kernel");
   return BS_OK;
 }

@@ -36,6 +36,7 @@ bs_status check_device();
 // ---- device status word (inside the binning workspace) ----
 constexpr uint32_t kDevErrTimeout = 1u;
 constexpr uint32_t kDevErrCapacity = 2u;
+constexpr uint32_t kDevErrCounts = 4u;   // batch binning: pair totals disagree (never expected)
 
 // ---- small math helpers usable on host and device ----
 __host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
@@ -130,6 +131,98 @@ bs_status launch_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas
                             cudaStream_t s);
 bs_status launch_l2(const float *img, const float *target, int64_t n, float *dimg, double *loss,
                     cudaStream_t s);
+
+// ---- batches of images (bs_batch.cu and the batched kernels) ----
+// One entry of the device table of a batch: where image b's curves,
+// Gaussians, pixels, tiles and difference array start in the batch's
+// concatenated arrays, and its canvas and sampling.
+struct BatchImage {
+  int W, H, tiles_x, tiles_y;
+  int n_open, n_closed;
+  int g_open, rows, kc;
+  float rho, eps;
+  float bg[3];
+  float l2_scale;       // 2 / (3 W H)
+  int order_chunks;     // ceil((n_open + n_closed) / 256)
+  int pad;
+  int64_t open0, closed0;  // first open / closed curve
+  int64_t gauss0, n_gauss; // first Gaussian and count
+  int64_t pix0;            // first pixel
+  int64_t tile0;           // first tile of the batch's tile numbering
+  int64_t diff0;           // first word of its (tiles_y + 1) x (tiles_x + 1) difference array
+  int64_t row0, col0;      // first row / column of the stacked difference arrays
+  int64_t order0;          // first CTA of the draw-order grid
+};
+
+struct BatchPlan {
+  int n_images, tile;
+  int64_t n_open, n_closed, n_curves, n_gauss, n_pix, n_tiles;
+  int64_t diff_words, diff_rows, diff_cols, order_ctas;
+  int tbits, passes, digit_bits;
+  int64_t capacity, parts, count_blocks, tile_blocks;
+  int n_max, k_max, rows_max;  // sampling: largest samples per curve / per row, rows
+  // byte offsets inside the batch workspace
+  size_t off_hdr, off_hist, off_diff, off_queue, zero_bytes;
+  size_t off_images, off_parts, off_local, off_partial, off_rects, off_owner, off_tsum, off_keys0, off_keys1;
+  size_t bytes;
+};
+
+// Header of the batch workspace.  status bits: kDevErrCapacity when the
+// pairs exceed the capacity (the ranges are then empty and nothing is
+// sorted).  n_pairs is the number of pairs the binning found (the sum of
+// the Gaussians' counts), n_sorted the number it sorted (0 on overflow),
+// tile_total the same pairs summed over the tiles.
+struct BatchHdr {
+  uint32_t status;
+  uint32_t pad;
+  unsigned long long n_pairs;
+  unsigned long long n_sorted;
+  unsigned long long tile_total;
+};
+
+#ifdef __CUDACC__
+// The batch's tables: image b owns Gaussians [gauss0, gauss0 + n_gauss),
+// tiles [tile0, tile0 + tiles_x tiles_y), difference-array rows [row0,
+// row0 + tiles_y + 1), columns [col0, col0 + tiles_x + 1), open curves
+// [open0, open0 + n_open) and so on.  An index belongs to the last image
+// whose first index is <= it (an image owning none of a kind shares its first
+// index with the next image and is passed over).
+template <int64_t BatchImage::*F>
+__device__ __forceinline__ int last_image_le(const BatchImage *__restrict__ tab, int n_images, int64_t v) {
+  int lo = 0, hi = n_images;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (tab[mid].*F <= v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo - 1;
+}
+#endif
+
+bs_status plan_batch(const bs_batch_image *images, int32_t n_images, int32_t tile, int64_t capacity,
+                     BatchPlan *p);
+void fill_batch_table(const bs_batch_image *images, const BatchPlan &p, BatchImage *out);
+
+// launchers of the batched kernels; `table` is the device table in the workspace
+bs_status launch_batch_curve_order(const BatchPlan &p, const BatchImage *table, const bs_curves &c,
+                                   uint32_t *rank, uint32_t *first, cudaStream_t s);
+bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, const bs_curves &c, float *gauss,
+                                  cudaStream_t s);
+bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, const bs_curves &c,
+                                  const float *dgauss, const bs_curves_grad &g, cudaStream_t s);
+bs_status run_batch_binning(const BatchPlan &p, void *ws, const float *gauss, uint32_t *tile_vals,
+                            uint32_t *tile_ranges, cudaStream_t s);
+bs_status read_batch_status(const BatchPlan &p, const void *ws, int32_t *status, int64_t *n_pairs, cudaStream_t s);
+bs_status launch_batch_render_fwd(const BatchPlan &p, void *ws, const float *gauss, const uint32_t *vals,
+                                  const uint32_t *ranges, const float *target, float *img, float *T_final,
+                                  uint32_t *n_contrib, float *dimg, double *loss, cudaStream_t s);
+bs_status launch_batch_render_bwd(const BatchPlan &p, void *ws, const float *gauss, const uint32_t *vals,
+                                  const uint32_t *ranges, const float *T_final, const uint32_t *n_contrib,
+                                  const float *dimg, float *dgauss, cudaStream_t s);
+
+// Adam (bs_adam.cu)
+bs_status launch_adam(const bs_adam_group *groups, int n_groups, const bs_adam_cfg &cfg, int32_t *step,
+                      cudaStream_t s);
 
 // pruning and densification (bs_prune.cu)
 constexpr int kMaxPdCurves = 65536;

@@ -181,11 +181,11 @@ struct ThreadPixels {
   int tile_x0, tile_y0;
 };
 
-__device__ __forceinline__ ThreadPixels thread_pixels(int tile, int tiles_x, int W, int H) {
+__device__ __forceinline__ ThreadPixels thread_pixels(int tile_x0, int tile_y0, int W, int H) {
   ThreadPixels t;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  t.tile_x0 = (tile % tiles_x) * kTile;
-  t.tile_y0 = (tile / tiles_x) * kTile;
+  t.tile_x0 = tile_x0;
+  t.tile_y0 = tile_y0;
   t.x[0] = t.tile_x0 + (lane & 7);
   t.x[1] = t.x[0] + 8;
   t.y[0] = t.tile_y0 + 8 * warp + (lane >> 3);
@@ -203,24 +203,33 @@ __device__ __forceinline__ ThreadPixels thread_pixels(int tile, int tiles_x, int
   return t;
 }
 
-// kStats: also count the (pixel, list entry) evaluations (E), the entries
-// blended, and the entries of the tile lists times the tile's pixels, into
-// stats[0..2] (for measurement; same blend otherwise).
-// kL2: also the L2 term of Eq. 13 on the finished pixels: dL/dimg =
-// (2 / n) (img - target), and mean((img - target)^2) added to *loss (one
-// double atomic per CTA; *loss zeroed by the launcher).
-template <bool kStats, bool kL2 = false>
-__global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *__restrict__ gauss,
-                                                                  const uint32_t *__restrict__ keys,
-                                                                  const uint2 *__restrict__ ranges, int W, int H,
-                                                                  int tiles_x, uint32_t gmask, uint32_t n_gauss,
-                                                                  float3 bg, float *__restrict__ img,
-                                                                  float *__restrict__ T_out,
-                                                                  uint32_t *__restrict__ nc_out,
-                                                                  unsigned long long *__restrict__ stats,
-                                                                  const float *__restrict__ target = nullptr,
-                                                                  float *__restrict__ dimg = nullptr,
-                                                                  double *__restrict__ loss = nullptr) {
+// One tile of one image as the blend kernels see it: its first pixel, the
+// canvas, its list range, and the image's planes (plane = W H floats).
+struct TileView {
+  int x0, y0, W, H;
+  uint2 r;
+  float3 bg;
+};
+
+struct FwdOut {
+  float *img, *T_out;
+  uint32_t *nc_out;
+  const float *target;  // kL2 only
+  float *dimg;          // kL2 only
+  float scale;          // kL2 only: 2 / (3 W H)
+};
+
+// The forward blend of one tile.  kStats: also count the (pixel, list
+// entry) evaluations (E), the entries blended, and the entries of the tile
+// list times the tile's pixels, into stats[0..2] (for measurement; same
+// blend otherwise).  kL2: also the L2 term of Eq. 13 on the finished
+// pixels: dL/dimg = scale (img - target); returns this thread's sum of
+// (img - target)^2 (0 without kL2).  Starts and ends with every thread of
+// the CTA past a barrier.
+template <bool kStats, bool kL2>
+__device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, const float *__restrict__ gauss,
+                                          const uint32_t *__restrict__ keys, uint32_t gmask, uint32_t n_gauss,
+                                          unsigned long long *__restrict__ stats) {
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
@@ -228,9 +237,8 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
   __shared__ uint8_t s_list[2][2][32];  // [consumer warp][staging warp][k]: entries reaching the warp
   __shared__ uint32_t s_cnt[2][2];
   uint32_t n_eval = 0, n_blend = 0;
-  const int tile = blockIdx.x;
-  const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
-  const uint2 r = ranges[tile];
+  const ThreadPixels tp = thread_pixels(v.x0, v.y0, v.W, v.H);
+  const uint2 r = v.r;
   float T[kPix], c0[kPix], c1[kPix], c2[kPix];
   uint32_t last[kPix];
 #pragma unroll
@@ -311,43 +319,129 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
       atomicAdd(&stats[2], (unsigned long long)(r.y - r.x) * (kTile * kTile));
     }
   }
-  const size_t plane = (size_t)W * H;
+  const size_t plane = (size_t)v.W * v.H;
   float l2 = 0.f;
-  const float scale = kL2 ? (float)(2.0 / (double)(3 * plane)) : 0.f;
 #pragma unroll
   for (int q = 0; q < kPix; ++q) {
     if (!(tp.inside & (1u << q))) continue;
-    const size_t p = (size_t)tp.y[q >> 1] * W + tp.x[q & 1];
-    const float v0 = __fmaf_rn(T[q], bg.x, c0[q]);
-    const float v1 = __fmaf_rn(T[q], bg.y, c1[q]);
-    const float v2 = __fmaf_rn(T[q], bg.z, c2[q]);
-    img[p] = v0;
-    img[plane + p] = v1;
-    img[2 * plane + p] = v2;
-    T_out[p] = T[q];
-    nc_out[p] = last[q];
+    const size_t p = (size_t)tp.y[q >> 1] * v.W + tp.x[q & 1];
+    const float v0 = __fmaf_rn(T[q], v.bg.x, c0[q]);
+    const float v1 = __fmaf_rn(T[q], v.bg.y, c1[q]);
+    const float v2 = __fmaf_rn(T[q], v.bg.z, c2[q]);
+    o.img[p] = v0;
+    o.img[plane + p] = v1;
+    o.img[2 * plane + p] = v2;
+    o.T_out[p] = T[q];
+    o.nc_out[p] = last[q];
     if (kL2) {
-      const float d0 = v0 - target[p], d1 = v1 - target[plane + p], d2 = v2 - target[2 * plane + p];
-      dimg[p] = scale * d0;
-      dimg[plane + p] = scale * d1;
-      dimg[2 * plane + p] = scale * d2;
+      const float d0 = v0 - o.target[p], d1 = v1 - o.target[plane + p], d2 = v2 - o.target[2 * plane + p];
+      o.dimg[p] = o.scale * d0;
+      o.dimg[plane + p] = o.scale * d1;
+      o.dimg[2 * plane + p] = o.scale * d2;
       l2 += d0 * d0 + d1 * d1 + d2 * d2;
     }
   }
-  if (kL2) {
-    __shared__ double s_l2[kThreads / 32];
-    double v = l2;
+  return l2;
+}
+
+// CTA sum of one float per thread, in double (valid in thread 0).
+__device__ __forceinline__ double cta_sum(float x) {
+  __shared__ double s_l2[kThreads / 32];
+  double v = x;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_l2[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_l2[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
 #pragma unroll
-      for (int w = 0; w < kThreads / 32; ++w) t += s_l2[w];
-      atomicAdd(loss, t / (double)(3 * plane));
-    }
+    for (int w = 0; w < kThreads / 32; ++w) t += s_l2[w];
   }
+  return t;
+}
+
+// One CTA per tile of one canvas.  kL2: mean((img - target)^2) added to
+// *loss (one double atomic per CTA; *loss zeroed by the launcher).
+template <bool kStats, bool kL2 = false>
+__global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *__restrict__ gauss,
+                                                                  const uint32_t *__restrict__ keys,
+                                                                  const uint2 *__restrict__ ranges, int W, int H,
+                                                                  int tiles_x, uint32_t gmask, uint32_t n_gauss,
+                                                                  float3 bg, float *__restrict__ img,
+                                                                  float *__restrict__ T_out,
+                                                                  uint32_t *__restrict__ nc_out,
+                                                                  unsigned long long *__restrict__ stats,
+                                                                  const float *__restrict__ target = nullptr,
+                                                                  float *__restrict__ dimg = nullptr,
+                                                                  double *__restrict__ loss = nullptr) {
+  const int tile = blockIdx.x;
+  const TileView v{(tile % tiles_x) * kTile, (tile / tiles_x) * kTile, W, H, ranges[tile], bg};
+  const size_t plane = (size_t)W * H;
+  const FwdOut o{img, T_out, nc_out, target, dimg, kL2 ? (float)(2.0 / (double)(3 * plane)) : 0.f};
+  const float l2 = fwd_tile<kStats, kL2>(v, o, gauss, keys, gmask, n_gauss, stats);
+  if (kL2) {
+    const double t = cta_sum(l2);
+    if (threadIdx.x == 0) atomicAdd(loss, t / (double)(3 * plane));
+  }
+}
+
+// Image of global tile t.
+__device__ __forceinline__ int batch_image_of_tile(const BatchImage *__restrict__ tab, int n_images, uint32_t t) {
+  return last_image_le<&BatchImage::tile0>(tab, n_images, (int64_t)t);
+}
+
+// The tile view of global tile t of a batch (image b).
+__device__ __forceinline__ TileView batch_view(const BatchImage &im, uint32_t t, const uint2 *__restrict__ ranges) {
+  const int local = (int)((int64_t)t - im.tile0);
+  const int ty = local / im.tiles_x, tx = local - ty * im.tiles_x;
+  return TileView{tx * kTile, ty * kTile, im.W, im.H, ranges[t], make_float3(im.bg[0], im.bg[1], im.bg[2])};
+}
+
+// Persistent forward over a batch: each CTA takes tiles from the atomic
+// queue *queue (zeroed by the launcher) until all n_tiles are done.  kL2:
+// loss[b] += mean over image b of (img - target)^2; a CTA keeps a running
+// sum while its tiles stay in one image and adds it once per change.
+template <bool kL2>
+__global__ void __launch_bounds__(kThreads, 16) batch_render_fwd_kernel(
+    const float *__restrict__ gauss, const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges,
+    const BatchImage *__restrict__ tab, int n_images, uint32_t n_tiles, uint32_t n_gauss,
+    unsigned int *__restrict__ queue, const float *__restrict__ target, float *__restrict__ img,
+    float *__restrict__ T_out, uint32_t *__restrict__ nc_out, float *__restrict__ dimg,
+    double *__restrict__ loss) {
+  __shared__ uint32_t s_t;
+  __shared__ int s_b;
+  double acc = 0.0;  // thread 0: pending sum of image acc_b
+  int acc_b = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(queue, 1u);
+      s_t = t;
+      s_b = t < n_tiles ? batch_image_of_tile(tab, n_images, t) : -1;
+    }
+    __syncthreads();
+    const uint32_t t = s_t;
+    const int b = s_b;
+    if (t >= n_tiles) break;
+    const BatchImage &im = tab[b];
+    const TileView v = batch_view(im, t, ranges);
+    const FwdOut o{img + 3 * im.pix0, T_out + im.pix0, nc_out + im.pix0, kL2 ? target + 3 * im.pix0 : nullptr,
+                   kL2 ? dimg + 3 * im.pix0 : nullptr, im.l2_scale};
+    const float l2 = fwd_tile<false, kL2>(v, o, gauss, vals, 0xffffffffu, n_gauss, nullptr);
+    if (kL2) {
+      const double s = cta_sum(l2);
+      if (threadIdx.x == 0) {
+        if (b != acc_b) {
+          if (acc_b >= 0) atomicAdd(loss + acc_b, acc / (3.0 * (double)tab[acc_b].W * (double)tab[acc_b].H));
+          acc = 0.0;
+          acc_b = b;
+        }
+        acc += s;
+      }
+    }
+    __syncthreads();
+  }
+  if (kL2 && threadIdx.x == 0 && acc_b >= 0)
+    atomicAdd(loss + acc_b, acc / (3.0 * (double)tab[acc_b].W * (double)tab[acc_b].H));
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -414,14 +508,17 @@ __device__ __forceinline__ void flush_pending(const float *part, const uint32_t 
 // The frame keeps every term O(1) inside the Gaussian's support (the same
 // sums in pixel offsets cancel badly for a thin Gaussian far along its
 // axis); grads_from_sums turns the totals into d/d(record).
-__global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *__restrict__ gauss,
-                                                                  const uint32_t *__restrict__ keys,
-                                                                  const uint2 *__restrict__ ranges, int W, int H,
-                                                                  int tiles_x, uint32_t gmask, uint32_t n_gauss,
-                                                                  float3 bg, const float *__restrict__ T_final,
-                                                                  const uint32_t *__restrict__ n_contrib,
-                                                                  const float *__restrict__ dimg,
-                                                                  float *__restrict__ sums) {
+struct BwdIn {
+  const float *T_final;
+  const uint32_t *n_contrib;
+  const float *dimg;
+};
+
+// The reverse walk of one tile (see above).  Starts and ends with every
+// thread of the CTA past a barrier.
+__device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, const float *__restrict__ gauss,
+                                         const uint32_t *__restrict__ keys, uint32_t gmask, uint32_t n_gauss,
+                                         float *__restrict__ sums) {
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
@@ -433,28 +530,28 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
   __shared__ uint32_t s_wlast[2][kPix];
   __shared__ __align__(16) float s_part[2][kPend * kSums * kRow];
   __shared__ uint32_t s_pend_g[2][kPend];
-  const int tile = blockIdx.x;
-  const ThreadPixels tp = thread_pixels(tile, tiles_x, W, H);
-  const uint2 r = ranges[tile];
+  const ThreadPixels tp = thread_pixels(v.x0, v.y0, v.W, v.H);
+  const uint2 r = v.r;
+  const float3 bg = v.bg;
   const int lane = threadIdx.x & 31;
   float T[kPix], g0[kPix], g1[kPix], g2[kPix], gS[kPix];
   uint32_t last[kPix];
   if (threadIdx.x == 0) s_max_last = 0;
   __syncthreads();
   uint32_t my_max = 0;
-  const size_t plane = (size_t)W * H;
+  const size_t plane = (size_t)v.W * v.H;
 #pragma unroll
   for (int q = 0; q < kPix; ++q) {
     T[q] = 1.f;
     g0[q] = g1[q] = g2[q] = 0.f;
     last[q] = 0;
     if (tp.inside & (1u << q)) {
-      const size_t p = (size_t)tp.y[q >> 1] * W + tp.x[q & 1];
-      T[q] = T_final[p];
-      last[q] = n_contrib[p];
-      g0[q] = dimg[p];
-      g1[q] = dimg[plane + p];
-      g2[q] = dimg[2 * plane + p];
+      const size_t p = (size_t)tp.y[q >> 1] * v.W + tp.x[q & 1];
+      T[q] = in.T_final[p];
+      last[q] = in.n_contrib[p];
+      g0[q] = in.dimg[p];
+      g1[q] = in.dimg[plane + p];
+      g2[q] = in.dimg[2 * plane + p];
       my_max = max(my_max, last[q]);
     }
     gS[q] = g0[q] * bg.x + g1[q] * bg.y + g2[q] * bg.z;  // g . S, S = bg behind the last blended Gaussian
@@ -554,6 +651,46 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
     end = start;
   }
   if (n_pend) flush_pending(part, pend_g, n_pend, lane, sums, n_gauss);
+  __syncthreads();
+}
+
+// One CTA per tile of one canvas.
+__global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *__restrict__ gauss,
+                                                                  const uint32_t *__restrict__ keys,
+                                                                  const uint2 *__restrict__ ranges, int W, int H,
+                                                                  int tiles_x, uint32_t gmask, uint32_t n_gauss,
+                                                                  float3 bg, const float *__restrict__ T_final,
+                                                                  const uint32_t *__restrict__ n_contrib,
+                                                                  const float *__restrict__ dimg,
+                                                                  float *__restrict__ sums) {
+  const int tile = blockIdx.x;
+  const TileView v{(tile % tiles_x) * kTile, (tile / tiles_x) * kTile, W, H, ranges[tile], bg};
+  bwd_tile(v, BwdIn{T_final, n_contrib, dimg}, gauss, keys, gmask, n_gauss, sums);
+}
+
+// Persistent backward over a batch (the queue of batch_render_fwd_kernel).
+__global__ void __launch_bounds__(kThreads, 12) batch_render_bwd_kernel(
+    const float *__restrict__ gauss, const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges,
+    const BatchImage *__restrict__ tab, int n_images, uint32_t n_tiles, uint32_t n_gauss,
+    unsigned int *__restrict__ queue, const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
+    const float *__restrict__ dimg, float *__restrict__ sums) {
+  __shared__ uint32_t s_t;
+  __shared__ int s_b;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(queue, 1u);
+      s_t = t;
+      s_b = t < n_tiles ? batch_image_of_tile(tab, n_images, t) : -1;
+    }
+    __syncthreads();
+    const uint32_t t = s_t;
+    const int b = s_b;
+    if (t >= n_tiles) break;
+    const BatchImage &im = tab[b];
+    const TileView v = batch_view(im, t, ranges);
+    bwd_tile(v, BwdIn{T_final + im.pix0, n_contrib + im.pix0, dimg + 3 * im.pix0}, gauss, vals, 0xffffffffu,
+             n_gauss, sums);
+  }
 }
 
 // The chain rule from the tile sums of render_bwd_kernel to the record.
@@ -687,6 +824,82 @@ bs_status launch_l2(const float *img, const float *target, int64_t n, float *dim
   const int blocks = (int)std::min<int64_t>(div_up64(n, 256 * 4 * 4), 152 * 8);
   l2_kernel<<<blocks, 256, 0, s>>>(img, target, n, dimg, loss);
   BS_LAUNCHED("l2_kernel");
+  return BS_OK;
+}
+
+// Persistent grids: as many CTAs as fit on the device at once (queried once
+// per device and kernel).
+template <typename Kernel>
+bs_status persistent_grid(Kernel k, int threads, int slot, int *grid) {
+  constexpr int kMaxDev = 64;
+  static int cache[kMaxDev][4] = {};
+  int dev = 0;
+  BS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) {
+    set_error("device %d: at most %d devices supported", dev, kMaxDev);
+    return BS_ERR_UNSUPPORTED;
+  }
+  if (!cache[dev][slot]) {
+    int per_sm = 0, sms = 0;
+    BS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0));
+    BS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cache[dev][slot] = std::max(1, per_sm) * std::max(1, sms);
+  }
+  *grid = cache[dev][slot];
+  return BS_OK;
+}
+
+// The workspace's two queue counters: [0] forward, [1] backward.
+unsigned int *batch_queue(const BatchPlan &p, void *ws) {
+  return reinterpret_cast<unsigned int *>(static_cast<char *>(ws) + p.off_queue);
+}
+
+const BatchImage *batch_table(const BatchPlan &p, const void *ws) {
+  return reinterpret_cast<const BatchImage *>(static_cast<const char *>(ws) + p.off_images);
+}
+
+bs_status launch_batch_render_fwd(const BatchPlan &p, void *ws, const float *gauss, const uint32_t *vals,
+                                  const uint32_t *ranges, const float *target, float *img, float *T_final,
+                                  uint32_t *n_contrib, float *dimg, double *loss, cudaStream_t s) {
+  unsigned int *queue = batch_queue(p, ws);
+  BS_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned int), s));
+  const auto *rg = reinterpret_cast<const uint2 *>(ranges);
+  int grid = 0;
+  if (target) {
+    BS_CUDA(cudaMemsetAsync(loss, 0, sizeof(double) * (size_t)p.n_images, s));
+    BS_TRY(persistent_grid(batch_render_fwd_kernel<true>, kThreads, 0, &grid));
+    grid = (int)std::min<int64_t>(grid, p.n_tiles);
+    batch_render_fwd_kernel<true><<<grid, kThreads, 0, s>>>(gauss, vals, rg, batch_table(p, ws), p.n_images,
+                                                           (uint32_t)p.n_tiles, (uint32_t)p.n_gauss, queue, target,
+                                                           img, T_final, n_contrib, dimg, loss);
+  } else {
+    BS_TRY(persistent_grid(batch_render_fwd_kernel<false>, kThreads, 1, &grid));
+    grid = (int)std::min<int64_t>(grid, p.n_tiles);
+    batch_render_fwd_kernel<false><<<grid, kThreads, 0, s>>>(gauss, vals, rg, batch_table(p, ws), p.n_images,
+                                                            (uint32_t)p.n_tiles, (uint32_t)p.n_gauss, queue,
+                                                            nullptr, img, T_final, n_contrib, nullptr, nullptr);
+  }
+  BS_LAUNCHED("batch_render_fwd_kernel");
+  return BS_OK;
+}
+
+bs_status launch_batch_render_bwd(const BatchPlan &p, void *ws, const float *gauss, const uint32_t *vals,
+                                  const uint32_t *ranges, const float *T_final, const uint32_t *n_contrib,
+                                  const float *dimg, float *dgauss, cudaStream_t s) {
+  unsigned int *queue = batch_queue(p, ws) + 1;
+  BS_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned int), s));
+  BS_CUDA(cudaMemsetAsync(dgauss, 0, sizeof(float) * BS_DGAUSS_FLOATS * (size_t)p.n_gauss, s));
+  int grid = 0;
+  BS_TRY(persistent_grid(batch_render_bwd_kernel, kThreads, 2, &grid));
+  grid = (int)std::min<int64_t>(grid, p.n_tiles);
+  batch_render_bwd_kernel<<<grid, kThreads, 0, s>>>(gauss, vals, reinterpret_cast<const uint2 *>(ranges),
+                                                    batch_table(p, ws), p.n_images, (uint32_t)p.n_tiles,
+                                                    (uint32_t)p.n_gauss, queue, T_final, n_contrib, dimg, dgauss);
+  BS_LAUNCHED("batch_render_bwd_kernel");
+  if (p.n_gauss > 0) {
+    grads_from_sums_kernel<<<(unsigned)div_up64(p.n_gauss, 256), 256, 0, s>>>(gauss, dgauss, p.n_gauss);
+    BS_LAUNCHED("grads_from_sums_kernel");
+  }
   return BS_OK;
 }
 

@@ -220,6 +220,33 @@ def prune_inputs(seed: int, W: int, H: int, n_open: int, n_closed: int, n_blobs:
 
 
 # The workloads, by what they are.
+def batch_layout(seed: int, n_images: int = 64, side=(256, 2048), aspect=(0.5, 2.0), curves=(128, 4096)):
+    """A ragged batch: per image W, H, n_open, n_closed and a seed.  The
+    side s is log-uniform in `side`, the aspect a = W / H uniform in `aspect`
+    (W = s sqrt(a), H = s / sqrt(a), at least 16 px), the curve count
+    log-uniform in `curves`, half open (rounded down) and half closed."""
+    (rng,) = _rngs(seed, 1)
+    out = []
+    for i in range(n_images):
+        s = float(np.exp(rng.uniform(np.log(side[0]), np.log(side[1]))))
+        a = float(rng.uniform(aspect[0], aspect[1]))
+        W = max(16, int(round(s * np.sqrt(a))))
+        H = max(16, int(round(s / np.sqrt(a))))
+        n = int(round(np.exp(rng.uniform(np.log(curves[0]), np.log(curves[1])))))
+        out.append(dict(W=W, H=H, n_open=n // 2, n_closed=n - n // 2, seed=seed * 1000 + i))
+    return out
+
+
+def batch_inputs(layout, n_shapes: int = 16, style: str = "local"):
+    """Curves (concatenated image after image, the batch layout) and the
+    targets (flattened planar images, concatenated) of a batch_layout."""
+    arrs = [make_curves(e["seed"], e["W"], e["H"], e["n_open"], e["n_closed"], style=style).as_dict()
+            for e in layout]
+    cat = {k: np.concatenate([a[k] for a in arrs], 0) for k in arrs[0]} if arrs else {}
+    targets = [procedural_target(e["seed"] + 1, e["W"], e["H"], n_shapes) for e in layout]
+    return arrs, cat, targets
+
+
 WORKLOADS = {
     # 256x256, 64 open curves, 16 Gaussians per curve, 16x16 tiles
     "tiny_256_64open": dict(W=256, H=256, n_open=64, n_closed=0, style="uniform",
@@ -233,3 +260,8 @@ WORKLOADS = {
                             g_open=64, rows_closed=8, k_closed=8, tile=16, seed=20,
                             n_shapes=200),
 }
+
+# 64 ragged images (sides log-uniform in [256, 2048], aspect in [0.5, 2],
+# 128..4096 curves each, half open and half closed), optimised together
+BATCH_WORKLOAD = dict(name="batch64_ragged", n_images=64, seed=30, side=(256, 2048), aspect=(0.5, 2.0),
+                      curves=(128, 4096), n_shapes=16)

@@ -106,3 +106,55 @@ def test_prune_densify_host_validation(bs):
     assert bs.lib.bs_prune_densify(ctypes.byref(empty), ctypes.byref(cfg), ctypes.byref(cv), fake, fake, fake, 16,
                                    None, None, None) == bs.BS_ERR_INVALID_ARG
     assert b"workspace" in bs.lib.bs_last_error()
+
+
+def _batch(bs, images, tile=16, capacity=100000):
+    arr = (bs.bs_batch_image * len(images))(*(im.c() for im in images))
+    return arr, bs.bs_batch(ctypes.cast(arr, ctypes.c_void_p), len(images), tile, capacity, None, 0)
+
+
+def test_batch_plan_host_arithmetic(bs):
+    images = [bs.BatchImage(300, 200, 5, 3, bs.SampleCfg(g_open=16, rows_closed=4, k_closed=8)),
+              bs.BatchImage(64, 64, 0, 2, bs.SampleCfg(g_open=8, rows_closed=6, k_closed=4)),
+              bs.BatchImage(1, 1, 1, 0, bs.SampleCfg(g_open=4))]
+    arr, b = _batch(bs, images)
+    sz = bs.bs_batch_sizes()
+    assert bs.lib.bs_batch_plan(ctypes.byref(b), ctypes.byref(sz)) == bs.BS_OK
+    assert (sz.n_open, sz.n_closed) == (6, 5)
+    assert sz.n_gauss == 5 * 16 + 3 * 32 + 2 * 24 + 4
+    assert sz.n_pixels == 300 * 200 + 64 * 64 + 1
+    assert sz.n_tiles == 19 * 13 + 4 * 4 + 1
+    assert sz.ws_bytes > 2 * 8 * 100000      # two 64-bit key buffers of the capacity
+    arr2, b2 = _batch(bs, images, capacity=200000)
+    sz2 = bs.bs_batch_sizes()
+    assert bs.lib.bs_batch_plan(ctypes.byref(b2), ctypes.byref(sz2)) == bs.BS_OK
+    assert sz2.ws_bytes > sz.ws_bytes
+
+
+def test_batch_plan_rejects_bad_batches(bs):
+    good = bs.BatchImage(32, 32, 1, 1, bs.SampleCfg())
+    sz = bs.bs_batch_sizes()
+    _, b = _batch(bs, [good], capacity=0)
+    assert bs.lib.bs_batch_plan(ctypes.byref(b), ctypes.byref(sz)) == bs.BS_ERR_INVALID_ARG
+    _, b = _batch(bs, [good, bs.BatchImage(32, 32, 1, 0, bs.SampleCfg(g_open=1))])
+    assert bs.lib.bs_batch_plan(ctypes.byref(b), ctypes.byref(sz)) == bs.BS_ERR_INVALID_ARG
+    assert b"image 1" in bs.lib.bs_last_error()
+    _, b = _batch(bs, [bs.BatchImage(0, 32, 1, 0, bs.SampleCfg())])
+    assert bs.lib.bs_batch_plan(ctypes.byref(b), ctypes.byref(sz)) == bs.BS_ERR_INVALID_ARG
+    _, b = _batch(bs, [good], tile=12)
+    assert bs.lib.bs_batch_plan(ctypes.byref(b), ctypes.byref(sz)) == bs.BS_ERR_UNSUPPORTED
+    # a workspace smaller than the plan is refused before anything runs
+    arr, b = _batch(bs, [good])
+    b.ws, b.ws_bytes = ctypes.c_void_p(256), 16
+    assert bs.lib.bs_batch_setup(ctypes.byref(b), None) == bs.BS_ERR_INVALID_ARG
+
+
+def test_adam_rejects_bad_groups(bs):
+    cfg = bs.bs_adam_cfg(0.9, 0.999, 1e-8)
+    g = bs.bs_adam_group(None, None, None, None, 10, 0.1, 0.0, 1.0, None, 1)
+    arr = (bs.bs_adam_group * 1)(g)
+    assert bs.lib.bs_adam_step(arr, 1, ctypes.byref(cfg), ctypes.c_void_p(256), None) == bs.BS_ERR_INVALID_ARG
+    assert bs.lib.bs_adam_step(arr, 0, ctypes.byref(cfg), ctypes.c_void_p(256), None) == bs.BS_ERR_INVALID_ARG
+    bad = bs.bs_adam_cfg(1.0, 0.999, 1e-8)
+    ok = (bs.bs_adam_group * 1)(bs.bs_adam_group(None, None, None, None, 0, 0.1, 0.0, 1.0, None, 1))
+    assert bs.lib.bs_adam_step(ok, 1, ctypes.byref(bad), ctypes.c_void_p(256), None) == bs.BS_ERR_INVALID_ARG
