@@ -12,9 +12,11 @@
  *   - All array pointers are DEVICE pointers owned by the caller, unless a
  *     parameter says "host".  The library never allocates device memory.
  *   - Calls are asynchronous on the given stream (a cudaStream_t; NULL is
- *     the legacy default stream).  The only call that synchronises is
- *     bs_bin_tiles (one 8-byte read-back of the pair count) and
- *     bs_device_status.
+ *     the legacy default stream).  The calls that synchronise are
+ *     bs_bin_tiles and bs_bin_tiles_static (one 8-byte read-back of the pair
+ *     count), bs_prune_densify (its counts), bs_batch_setup (the copy of the
+ *     layout table), and the status reads bs_device_status and
+ *     bs_batch_status.
  *   - Every call returns a bs_status.  Arguments are validated on the host
  *     before anything is launched; an invalid argument returns
  *     BS_ERR_INVALID_ARG and launches nothing.  bs_last_error() gives a
@@ -97,7 +99,7 @@ typedef struct {
 typedef struct {
   int32_t width;   /* W px, 1..32768 */
   int32_t height;  /* H px, 1..32768 */
-  int32_t tile;    /* tile side in px; 16 */
+  int32_t tile;    /* tile side in px: 8, 16 or 32 */
   float bg[3];     /* background colour blended with the final transmittance */
 } bs_canvas;
 
@@ -174,12 +176,16 @@ bs_status bs_bin_tiles_workspace(int64_t n_gauss, const bs_canvas *canvas,
  * and are sorted ascending by a hand-written stable LSD radix sort of the
  * tile bits (per pass: digit counts per partition, their scan, a stable
  * scatter), so each tile's list is front to back.
- * tile bits + gbits must be <= 32 (else BS_ERR_UNSUPPORTED).
+ * When tile bits + gbits exceed 32 ("wide" keys), the keys are 64-bit
+ * (tile << 32 | g) inside the workspace and tile_keys receives only g for
+ * each pair, in the same order; the blend calls tell the two apart from
+ * n_gauss and the canvas.
  *   ws, ws_bytes    scratch of bs_bin_tiles_workspace bytes (device)
  *   pair_capacity   room in tile_keys and ws
  *   n_pairs_out     (HOST) the number of pairs P; on BS_ERR_CAPACITY the
  *                   number needed (nothing else is valid then)
- *   tile_keys       [pair_capacity] sorted keys (device, written [0, P))
+ *   tile_keys       [pair_capacity] sorted keys, or their g (wide keys)
+ *                   (device, written [0, P))
  *   tile_ranges     [n_tiles][2] (start, end) into tile_keys; an empty tile
  *                   has (0, 0) (device, written)
  * Synchronises the stream once to read P.
@@ -410,7 +416,7 @@ typedef struct {
 typedef struct {
   const bs_batch_image *images;  /* HOST [n_images]                                  */
   int32_t n_images;              /* >= 1                                             */
-  int32_t tile;                  /* tile side in px: 16                              */
+  int32_t tile;                  /* tile side in px: 8, 16 or 32                     */
   int64_t pair_capacity;         /* room for (tile, Gaussian) pairs, >= 1            */
   void *ws;                      /* device workspace of bs_batch_plan's ws_bytes     */
   size_t ws_bytes;

@@ -63,14 +63,14 @@ def tile_rects_f32(rec: np.ndarray, W: int, H: int, tile: int):
 def tile_keys(rec: np.ndarray, W: int, H: int, tile: int):
     """All (tile, Gaussian) keys sorted ascending, the tile ranges [n_tiles, 2]
     (start, end) into them (an empty tile has (0, 0)), and the per-Gaussian
-    pair counts."""
+    pair counts.  Keys are uint32, or uint64 when tile bits + Gaussian bits
+    exceed 32."""
     ng = rec.shape[0]
     tiles_x = -(-W // tile)
     tiles_y = -(-H // tile)
     n_tiles = tiles_x * tiles_y
     gbits, tbits = key_bits(ng, n_tiles)
-    if gbits + tbits > 32:
-        raise ValueError("keys wider than 32 bits")
+    wide = gbits + tbits > 32          # then the keys are uint64
     tx0, tx1, ty0, ty1, ok = tile_rects_f32(rec, W, H, tile)
     counts = np.where(ok, (tx1 - tx0 + 1) * (ty1 - ty0 + 1), 0).astype(np.int64)
     # every tile of every rectangle, row by row
@@ -81,9 +81,11 @@ def tile_keys(rec: np.ndarray, W: int, H: int, tile: int):
     tx = tx0[g] + local % width
     ty = ty0[g] + local // width
     tid = (ty * tiles_x + tx).astype(np.uint64)
-    keys = np.sort((tid << np.uint64(gbits)) | g.astype(np.uint64)).astype(np.uint32)
-    tile_of = keys >> np.uint32(gbits)
-    t = np.arange(n_tiles, dtype=np.uint32)
+    keys = np.sort((tid << np.uint64(gbits)) | g.astype(np.uint64))
+    if not wide:
+        keys = keys.astype(np.uint32)
+    tile_of = keys >> keys.dtype.type(gbits)
+    t = np.arange(n_tiles, dtype=keys.dtype)
     ranges = np.stack([np.searchsorted(tile_of, t, side="left"),
                        np.searchsorted(tile_of, t, side="right")], axis=1).astype(np.uint32)
     ranges[ranges[:, 0] == ranges[:, 1]] = 0       # an empty tile is (0, 0)

@@ -222,12 +222,12 @@ class PlainOptimizer:
     (bs_curve_order ... bs_render_bwd, then bs_adam_step per image)."""
 
     def __init__(self, images, curves_per_image, targets, cfg: AdamCfg = None, device="cuda",
-                 pair_capacity: int = 1 << 20):
+                 pair_capacity: int = 1 << 20, tile: int = 16):
         from .raster import Rasterizer
         self.cfg = cfg or AdamCfg()
         self.items = []
         for im, cv, tg in zip(images, curves_per_image, targets):
-            r = Rasterizer(bs.Canvas(im.width, im.height, 16, im.bg), im.sample, im.n_open, im.n_closed,
+            r = Rasterizer(bs.Canvas(im.width, im.height, tile, im.bg), im.sample, im.n_open, im.n_closed,
                            device=device, pair_capacity=pair_capacity)
             grad = cv.zeros_like()
             adam = CurveAdam(cv, grad, [im], self.cfg, device)

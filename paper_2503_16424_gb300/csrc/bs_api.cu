@@ -97,8 +97,8 @@ bs_status check_canvas(const bs_canvas *cv) {
   if (!cv) return invalid("canvas is NULL");
   if (cv->width < 1 || cv->height < 1 || cv->width > 32768 || cv->height > 32768)
     return invalid("canvas %dx%d out of range", cv->width, cv->height);
-  if (cv->tile != 16) {
-    set_error("tile side %d not supported (16)", cv->tile);
+  if (cv->tile != 8 && cv->tile != 16 && cv->tile != 32) {
+    set_error("tile side %d not supported (8, 16, 32)", cv->tile);
     return BS_ERR_UNSUPPORTED;
   }
   return BS_OK;
@@ -258,7 +258,7 @@ bs_status bs_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas *ca
   if (n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
   if (!tile_ranges || !img || !T_final || !n_contrib) return invalid("NULL output or tile_ranges");
   BS_TRY(check_device());
-  return launch_render_fwd(gauss, n_gauss, *canvas, gauss_bits(n_gauss), tile_keys, tile_ranges, img, T_final, n_contrib,
+  return launch_render_fwd(gauss, n_gauss, *canvas, key_gbits(n_gauss, *canvas), tile_keys, tile_ranges, img, T_final, n_contrib,
                            (cudaStream_t)stream);
 }
 
@@ -271,7 +271,7 @@ bs_status bs_render_fwd_l2(const float *gauss, int64_t n_gauss, const bs_canvas 
   if (!tile_ranges || !img || !T_final || !n_contrib) return invalid("NULL output or tile_ranges");
   if (!target || !dL_dimg || !loss_out) return invalid("target, dL_dimg and loss_out must be non-NULL");
   BS_TRY(check_device());
-  return launch_render_fwd_l2(gauss, n_gauss, *canvas, gauss_bits(n_gauss), tile_keys, tile_ranges, target, img,
+  return launch_render_fwd_l2(gauss, n_gauss, *canvas, key_gbits(n_gauss, *canvas), tile_keys, tile_ranges, target, img,
                               T_final, n_contrib, dL_dimg, loss_out, (cudaStream_t)stream);
 }
 
@@ -283,7 +283,7 @@ bs_status bs_render_stats(const float *gauss, int64_t n_gauss, const bs_canvas *
   if (n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
   if (!tile_ranges || !img || !T_final || !n_contrib || !stats_out) return invalid("NULL output or tile_ranges");
   BS_TRY(check_device());
-  return launch_render_fwd(gauss, n_gauss, *canvas, gauss_bits(n_gauss), tile_keys, tile_ranges, img, T_final,
+  return launch_render_fwd(gauss, n_gauss, *canvas, key_gbits(n_gauss, *canvas), tile_keys, tile_ranges, img, T_final,
                            n_contrib, (cudaStream_t)stream, stats_out);
 }
 
@@ -313,7 +313,7 @@ bs_status bs_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas *ca
   BS_TRY(check_device());
   const cudaStream_t s = (cudaStream_t)stream;
   if (n_gauss > 0)
-    BS_TRY(launch_render_bwd(gauss, n_gauss, *canvas, gauss_bits(n_gauss), tile_keys, tile_ranges, T_final,
+    BS_TRY(launch_render_bwd(gauss, n_gauss, *canvas, key_gbits(n_gauss, *canvas), tile_keys, tile_ranges, T_final,
                              n_contrib, dL_dimg, dgauss, s));
   if (grad) return bs_sample_curves_bwd(curves, cfg, dgauss, grad, stream);
   return BS_OK;

@@ -35,8 +35,8 @@ bs_status plan_batch(const bs_batch_image *images, int32_t n_images, int32_t til
     set_error("a batch needs at least one image");
     return BS_ERR_INVALID_ARG;
   }
-  if (tile != 16) {
-    set_error("tile side %d not supported (16)", tile);
+  if (tile != 8 && tile != 16 && tile != 32) {
+    set_error("tile side %d not supported (8, 16, 32)", tile);
     return BS_ERR_UNSUPPORTED;
   }
   if (capacity < 1 || capacity > kMaxBatchPairs) {

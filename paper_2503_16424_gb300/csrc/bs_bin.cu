@@ -444,18 +444,21 @@ __device__ __forceinline__ int64_t window_owner(const uint32_t *s_off, int win, 
 // The CTA's keys belong to Gaussians owner[b] .. owner[b+1], so only their
 // offsets are staged.  It also adds the digit counts of its keys for the
 // sort's first pass to hist1 (digit-major, partition b / 2).
+// K = uint32_t: key = tile << gbits | g; K = unsigned long long (wide keys,
+// tile bits + gbits > 32): key = tile << 32 | g.
 static_assert(2 * kEmitTile == kSortTile, "a sort partition is two emit chunks");
+template <typename K>
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__restrict__ local,
                                                             const unsigned long long *__restrict__ partial,
                                                             int64_t nb, const uint2 *__restrict__ rects,
                                                             int64_t n_gauss, const unsigned long long *count,
                                                             int tiles_x, int gbits,
                                                             const uint32_t *__restrict__ owner,
-                                                            uint32_t *__restrict__ keys, int bits1,
+                                                            K *__restrict__ keys, int bits1,
                                                             uint32_t *__restrict__ hist1, uint32_t parts) {
   constexpr int kWin = kEmitTile + 1;
   __shared__ uint32_t s_off[kWin];
-  __shared__ uint32_t s_keys[kEmitTile];
+  __shared__ K s_keys[kEmitTile];
   __shared__ uint32_t s_h[256];
   const uint32_t n = (uint32_t)*count;
   const uint32_t k0 = blockIdx.x * (uint32_t)kEmitTile;
@@ -497,7 +500,10 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const uint32_t *__re
         rx = l - ry * w;
       }
       const uint32_t tid = ((rc.x >> 16) + ry) * (uint32_t)tiles_x + (rc.x & 0xffffu) + rx;
-      s_keys[threadIdx.x * kEmitItems + it] = (tid << gbits) | (uint32_t)g;
+      if constexpr (sizeof(K) == 8)
+        s_keys[threadIdx.x * kEmitItems + it] = ((K)tid << 32) | (K)g;
+      else
+        s_keys[threadIdx.x * kEmitItems + it] = (tid << gbits) | (uint32_t)g;
       atomicAdd(&s_h[tid & dmask], 1u);
       if (++rx == w) {
         rx = 0;
@@ -994,8 +1000,8 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
     set_error("canvas %dx%d out of range", cv.width, cv.height);
     return BS_ERR_INVALID_ARG;
   }
-  if (cv.tile != 16) {
-    set_error("tile side %d not supported (16)", cv.tile);
+  if (cv.tile != 8 && cv.tile != 16 && cv.tile != 32) {
+    set_error("tile side %d not supported (8, 16, 32)", cv.tile);
     return BS_ERR_UNSUPPORTED;
   }
   if (capacity < 0 || capacity > kMaxPairs) {
@@ -1008,10 +1014,7 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
   p->n_tiles = p->tiles_x * p->tiles_y;
   p->gbits = gauss_bits(n_gauss);
   p->tbits = p->n_tiles > 1 ? bit_length((uint64_t)(p->n_tiles - 1)) : 1;
-  if (p->gbits + p->tbits > 32) {
-    set_error("keys need %d tile + %d Gaussian bits > 32", p->tbits, p->gbits);
-    return BS_ERR_UNSUPPORTED;
-  }
+  p->wide = p->gbits + p->tbits > 32;
   p->passes = div_up(p->tbits, 8);
   p->digit_bits = div_up(p->tbits, p->passes);
   p->capacity = capacity;
@@ -1029,7 +1032,8 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
   p->off_partial = o;    o = align256(o + sizeof(unsigned long long) * (size_t)(p->count_blocks + 1));
   p->off_rects = o;      o = align256(o + sizeof(uint2) * (size_t)(n_gauss > 0 ? n_gauss : 1));
   p->off_owner = o;      o = align256(o + sizeof(uint32_t) * (size_t)(div_up64(capacity, kEmitTile) + 1));
-  p->off_keys_tmp = o;   o = align256(o + sizeof(uint32_t) * (size_t)(capacity > 0 ? capacity : 1));
+  p->off_keys_tmp = o;
+  o = align256(o + (p->wide ? 2 * sizeof(unsigned long long) : sizeof(uint32_t)) * (size_t)(capacity > 0 ? capacity : 1));
   p->bytes = o;
   return BS_OK;
 }
@@ -1096,14 +1100,46 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   const int64_t P = (int64_t)h.n_pairs;
   if (P == 0) return BS_OK;
   const int64_t parts = div_up64(P, kSortTile);
+  const int bits0 = std::min(p.digit_bits, p.tbits);
+  BS_CUDA(cudaMemsetAsync(part_offs, 0, sizeof(uint32_t) * ((size_t)1 << bits0) * (size_t)parts, s));
+  if (p.wide) {
+    // 64-bit keys in the workspace; the last pass writes g alone to tile_keys
+    auto *k64 = reinterpret_cast<unsigned long long *>(base + p.off_keys_tmp);
+    unsigned long long *kb[2] = {k64, k64 + p.capacity};
+    emit_kernel<unsigned long long><<<(unsigned)div_up64(P, kEmitTile), kEmitThreads, 0, s>>>(
+        local, partial, p.count_blocks, rects, p.n_gauss, &hdr->n_pairs, p.tiles_x, p.gbits, owner, kb[0], bits0,
+        part_offs, (uint32_t)parts);
+    BS_LAUNCHED("emit_kernel");
+    int cur = 0;
+    for (int pass = 0; pass < p.passes; ++pass) {
+      const int shift = 32 + pass * p.digit_bits;
+      const int bits = std::min(p.digit_bits, p.tbits - pass * p.digit_bits);
+      if (pass > 0) {
+        upsweep_kernel<unsigned long long><<<(unsigned)parts, kSortThreads, 0, s>>>(kb[cur], &hdr->n_pairs, shift,
+                                                                                   bits, part_offs, (uint32_t)parts);
+        BS_LAUNCHED("upsweep_kernel");
+      }
+      scan_parts_kernel<<<1u << bits, kScanThreads, 0, s>>>(part_offs, (uint32_t)parts, hist + pass * 256);
+      BS_LAUNCHED("scan_parts_kernel");
+      if (pass + 1 < p.passes) {
+        downsweep_kernel<unsigned long long, unsigned long long><<<(unsigned)parts, kSortThreads, 0, s>>>(
+            kb[cur], kb[1 - cur], &hdr->n_pairs, shift, bits, part_offs, (uint32_t)parts);
+        cur = 1 - cur;
+      } else {
+        downsweep_kernel<unsigned long long, uint32_t><<<(unsigned)parts, kSortThreads, 0, s>>>(
+            kb[cur], tile_keys, &hdr->n_pairs, shift, bits, part_offs, (uint32_t)parts);
+      }
+      BS_LAUNCHED("downsweep_kernel");
+    }
+    return BS_OK;
+  }
   // emit into the buffer that makes the last pass land in tile_keys
   uint32_t *bufs[2] = {tile_keys, keys_tmp};
   uint32_t *src = (p.passes % 2 == 0) ? tile_keys : keys_tmp;
-  const int bits0 = std::min(p.digit_bits, p.tbits);
-  BS_CUDA(cudaMemsetAsync(part_offs, 0, sizeof(uint32_t) * ((size_t)1 << bits0) * (size_t)parts, s));
-  emit_kernel<<<(unsigned)div_up64(P, kEmitTile), kEmitThreads, 0, s>>>(local, partial, p.count_blocks, rects,
-                                                                       p.n_gauss, &hdr->n_pairs, p.tiles_x, p.gbits, owner,
-                                                                       src, bits0, part_offs, (uint32_t)parts);
+  emit_kernel<uint32_t><<<(unsigned)div_up64(P, kEmitTile), kEmitThreads, 0, s>>>(local, partial, p.count_blocks, rects,
+                                                                                 p.n_gauss, &hdr->n_pairs, p.tiles_x,
+                                                                                 p.gbits, owner, src, bits0, part_offs,
+                                                                                 (uint32_t)parts);
   BS_LAUNCHED("emit_kernel");
   for (int pass = 0; pass < p.passes; ++pass) {
     uint32_t *dst = (src == bufs[0]) ? bufs[1] : bufs[0];

@@ -47,6 +47,18 @@ inline int bit_length(uint64_t v) {
   return n;
 }
 inline int gauss_bits(int64_t n_gauss) { return n_gauss > 1 ? bit_length((uint64_t)(n_gauss - 1)) : 1; }
+// Tile-id bits of a canvas.
+inline int tile_bits(const bs_canvas &cv) {
+  const int64_t n = (int64_t)div_up(cv.width, cv.tile) * div_up(cv.height, cv.tile);
+  return n > 1 ? bit_length((uint64_t)(n - 1)) : 1;
+}
+// Bits of the Gaussian index inside a sorted key of one canvas: gauss_bits
+// for 32-bit keys (tile << gbits | g); 32 when tile bits + gbits exceed 32
+// and the binning sorts 64-bit keys, whose sorted output is g alone.
+inline int key_gbits(int64_t n_gauss, const bs_canvas &cv) {
+  const int g = gauss_bits(n_gauss);
+  return g + tile_bits(cv) > 32 ? 32 : g;
+}
 
 // ---- draw-order key (Section 3.3), shared by the draw order and pruning ----
 #ifdef __CUDACC__
@@ -99,13 +111,14 @@ struct BinPlan {
   int64_t n_gauss;
   int tiles_x, tiles_y, n_tiles;
   int gbits, tbits;
+  bool wide;               // tbits + gbits > 32: 64-bit keys (tile << 32 | g), g alone written out
   int passes, digit_bits;
   int64_t capacity;
   int64_t count_blocks;    // blocks of the count/emit kernels
   int64_t parts;           // sort partitions for `capacity` keys
   // byte offsets inside the workspace
   size_t off_hdr, off_hist, off_diff, zero_bytes, off_parts;
-  size_t off_local, off_partial, off_rects, off_owner, off_keys_tmp;
+  size_t off_local, off_partial, off_rects, off_owner, off_keys_tmp;  // keys_tmp: u32 [capacity], or u64 [2][capacity] when wide
   size_t bytes;
 };
 bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, BinPlan *p);

@@ -1,13 +1,15 @@
 // Per-tile alpha blending (Section 3.4, Eq. 9-10) and its reverse-order
 // backward, plus the L2 term of Eq. 13.
 //
-// One CTA of 64 threads per 16x16 tile.  Warp w covers rows 8w..8w+7; its
-// lane l owns one pixel in each of the warp's four 8x4 blocks (slot q = block
-// (q & 1, q >> 1), pixel (l & 7, l >> 3) inside it).  The tile's list is
-// staged into shared memory 64 Gaussians at a time, each with eight bits
-// telling which 8x4 blocks of the tile its alpha >= 1/255 region reaches, so
-// a warp skips a block for a Gaussian without touching its pixels, and the
-// work of a slot stays within one compact block.
+// One CTA per T x T tile, T = 8, 16 or 32 (Geo<T>).  A warp covers a region
+// of 8x4-pixel blocks: 8 x 8 pixels (two blocks) for T = 8, 16 x 8 pixels
+// (four blocks) for T = 16 and 32, so a tile has 1, 2 or 8 warps.  Lane l
+// owns pixel (l & 7, l >> 3) of each of its warp's blocks (its slots).  The
+// tile's list is staged into shared memory one Gaussian per thread at a
+// time, each with one bit per block of the tile telling whether its
+// alpha >= 1/255 region reaches the block, so a warp skips a block for a
+// Gaussian without touching its pixels, and the work of a slot stays within
+// one compact block.
 //
 // A Gaussian is stored by its eigen-frame (Eq. 11-12): Sigma^-1 =
 // R diag(isx^2, isy^2) R^T with R = [[ux, -uy], [uy, ux]], and is staged as the
@@ -31,10 +33,39 @@
 namespace bs {
 namespace {
 
-constexpr int kTile = 16;
-constexpr int kPix = 4;                             // pixels (slots) per thread
-constexpr int kThreads = kTile * kTile / kPix;      // 64
-constexpr int kBatch = kThreads;                    // Gaussians staged per round
+// Geometry of a T x T tile.
+template <int kT>
+struct Geo {
+  static_assert(kT == 8 || kT == 16 || kT == 32, "tile side 8, 16 or 32");
+  static constexpr int kBC = kT == 8 ? 1 : 2;        // 8x4 block columns per warp
+  static constexpr int kWX = kT / (8 * kBC);         // warps across the tile
+  static constexpr int kWY = kT / 8;                 // warps down the tile (two block rows each)
+  static constexpr int kWarps = kWX * kWY;
+  static constexpr int kThreads = 32 * kWarps;
+  static constexpr int kPix = 2 * kBC;               // pixels (slots) per thread
+  static constexpr int kBatch = kThreads;            // Gaussians staged per round
+  static constexpr int kBits = kWarps * kPix;        // block bits of a tile
+  static constexpr uint32_t kSlotMask = (1u << kPix) - 1u;
+  // bit of block (bc, br) of the tile: warp-major, then slot
+  __host__ __device__ static constexpr int bit(int bc, int br) {
+    return kPix * ((br >> 1) * kWX + bc / kBC) + (bc % kBC) + kBC * (br & 1);
+  }
+  __host__ __device__ static constexpr unsigned bcol(unsigned b) { return ((b / kPix) % kWX) * kBC + (b % kPix) % kBC; }
+  __host__ __device__ static constexpr unsigned brow(unsigned b) { return 2 * ((b / kPix) / kWX) + (b % kPix) / kBC; }
+  // the bits of block row br for the block columns in `cols`
+  __host__ __device__ static constexpr uint32_t row_bits(uint32_t cols, int br) {
+    return kT == 8 ? cols << br
+         : kT == 16 ? cols << (2 * br)
+                    : ((cols & 3u) | ((cols & 12u) << 2)) << (8 * (br >> 1) + 2 * (br & 1));
+  }
+};
+static_assert(Geo<16>::bit(1, 3) == 7 && Geo<16>::bcol(7) == 1 && Geo<16>::brow(7) == 3, "T = 16 block bits");
+static_assert(Geo<32>::row_bits(15u, 5) == ((1u << Geo<32>::bit(0, 5)) | (1u << Geo<32>::bit(1, 5)) |
+                                            (1u << Geo<32>::bit(2, 5)) | (1u << Geo<32>::bit(3, 5))),
+              "T = 32 row bits");
+static_assert(Geo<32>::bcol(Geo<32>::bit(3, 6)) == 3 && Geo<32>::brow(Geo<32>::bit(3, 6)) == 6, "T = 32 block bits");
+static_assert(Geo<8>::row_bits(1u, 1) == (1u << Geo<8>::bit(0, 1)), "T = 8 row bits");
+static_assert(Geo<32>::kBits == 32 && Geo<8>::kBits == 2, "block bits fit a word");
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kKappa = 0.84932180028801907f;      // sqrt(log2(e) / 2)
 constexpr float kLog2_255 = 7.99435343685885793f;   // alpha >= 1/255 <=> t1^2 + t2^2 <= log2(o) + log2(255)
@@ -108,13 +139,15 @@ __device__ __forceinline__ float min_q_rect(float A1, float B1, float A2, float 
   return best;
 }
 
-// Bit b = 2 * block_row + block_col set: the Gaussian can reach alpha >=
-// 1/255 at some pixel centre of the 8x4 block (block_col, block_row) of the
-// tile whose first pixel is (x0, y0).  Blocks outside the Gaussian's box
+// Bit Geo<T>::bit(block_col, block_row) set: the Gaussian can reach alpha
+// >= 1/255 at some pixel centre of the 8x4 block (block_col, block_row) of
+// the tile whose first pixel is (x0, y0).  Blocks outside the Gaussian's box
 // (mean +- ext) are cleared first; the others get the exact ellipse test.
 // Conservative by a margin far above the float32 error of either side, so a
 // cleared bit only skips pixels that the blend would skip anyway.
+template <int kT>
 __device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, float ext_y, int x0, int y0) {
+  using G = Geo<kT>;
   const float thr = s.b.z + kLog2_255;
   if (!(thr >= 0.f)) return 0u;  // o < 1/255 (or not finite): never visible
   // box test: block columns / rows whose pixel centres overlap the box
@@ -122,15 +155,15 @@ __device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, flo
   const float by0 = s.a.y - ext_y - ((float)y0 + 0.5f), by1 = s.a.y + ext_y - ((float)y0 + 0.5f);
   uint32_t cols = 0u, rows = 0u;
 #pragma unroll
-  for (int bc = 0; bc < 2; ++bc)
+  for (int bc = 0; bc < kT / 8; ++bc)
     if (bx1 >= 8.f * bc - 0.5f && bx0 <= 8.f * bc + 7.5f) cols |= 1u << bc;
 #pragma unroll
-  for (int br = 0; br < 4; ++br)
+  for (int br = 0; br < kT / 4; ++br)
     if (by1 >= 4.f * br - 0.5f && by0 <= 4.f * br + 3.5f) rows |= 1u << br;
   uint32_t cand = 0u;
 #pragma unroll
-  for (int br = 0; br < 4; ++br)
-    if (rows & (1u << br)) cand |= cols << (2 * br);
+  for (int br = 0; br < kT / 4; ++br)
+    if (rows & (1u << br)) cand |= G::row_bits(cols, br);
   const float lim = thr + (1e-2f + 1e-4f * thr);
   const float A1 = s.a.z, B1 = s.a.w, A2 = s.b.x, B2 = s.b.y;
   const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
@@ -138,9 +171,9 @@ __device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, flo
   const float r_axx = axx > 0.f ? -axy * __frcp_rn(axx) : 0.f, r_byy = byy > 0.f ? -axy * __frcp_rn(byy) : 0.f;
   uint32_t bits = 0u;
   while (cand) {
-    const int b = __ffs(cand) - 1;
+    const unsigned b = (unsigned)(__ffs(cand) - 1);
     cand &= cand - 1;
-    const int br = b >> 1, bc = b & 1;
+    const int br = (int)G::brow(b), bc = (int)G::bcol(b);
     const float dy0 = ((float)(y0 + 4 * br) + 0.5f) - s.a.y, dy1 = ((float)(y0 + 4 * br) + 3.5f) - s.a.y;
     const float dx0 = ((float)(x0 + 8 * bc) + 0.5f) - s.a.x, dx1 = ((float)(x0 + 8 * bc) + 7.5f) - s.a.x;
     if (min_q_rect(A1, B1, A2, B2, r_axx, r_byy, dx0, dx1, dy0, dy1) <= lim) bits |= 1u << b;
@@ -159,47 +192,55 @@ __device__ __forceinline__ float pixel_log2_alpha(const float4 &a, const float4 
 
 // Per consumer warp, the staged entries whose block bits reach it, in order:
 // each staging warp writes the indices of its qualifying lanes (ballot +
-// prefix count) into its own half of the consumer's list.  The caller
+// prefix count) into its own part of the consumer's list.  The caller
 // synchronises before the lists are read.
-__device__ __forceinline__ void compact_lists(uint32_t bits, uint8_t (*list)[2][32], uint32_t (*cnt)[2]) {
+template <int kT>
+__device__ __forceinline__ void compact_lists(uint32_t bits, uint8_t (*list)[Geo<kT>::kWarps][32],
+                                              uint32_t (*cnt)[Geo<kT>::kWarps]) {
+  using G = Geo<kT>;
   const int sw = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-  for (int cw = 0; cw < 2; ++cw) {
-    const bool rel = ((bits >> (4 * cw)) & 15u) != 0u;
+  for (int cw = 0; cw < G::kWarps; ++cw) {
+    const bool rel = ((bits >> (G::kPix * cw)) & G::kSlotMask) != 0u;
     const unsigned m = __ballot_sync(0xffffffffu, rel);
     if (rel) list[cw][sw][__popc(m & lt)] = (uint8_t)threadIdx.x;
     if (lane == 0) cnt[cw][sw] = (uint32_t)__popc(m);
   }
 }
 
+template <int kT>
 struct ThreadPixels {
-  int x[2], y[2];    // slot q is pixel (x[q & 1], y[q >> 1])
-  float px[2], py[2];
-  unsigned inside;   // bit q: slot q lies on the canvas
-  int shift;         // this warp's four block bits start at bit `shift`
+  int x[Geo<kT>::kBC], y[2];  // slot q is pixel (x[q % kBC], y[q / kBC])
+  float px[Geo<kT>::kBC], py[2];
+  unsigned inside;            // bit q: slot q lies on the canvas
+  int shift;                  // this warp's block bits start at bit `shift`
   int tile_x0, tile_y0;
 };
 
-__device__ __forceinline__ ThreadPixels thread_pixels(int tile_x0, int tile_y0, int W, int H) {
-  ThreadPixels t;
+template <int kT>
+__device__ __forceinline__ ThreadPixels<kT> thread_pixels(int tile_x0, int tile_y0, int W, int H) {
+  using G = Geo<kT>;
+  ThreadPixels<kT> t;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wx = warp % G::kWX, wy = warp / G::kWX;
   t.tile_x0 = tile_x0;
   t.tile_y0 = tile_y0;
-  t.x[0] = t.tile_x0 + (lane & 7);
-  t.x[1] = t.x[0] + 8;
-  t.y[0] = t.tile_y0 + 8 * warp + (lane >> 3);
-  t.y[1] = t.y[0] + 4;
-  t.inside = 0;
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    t.px[i] = (float)t.x[i] + 0.5f;
-    t.py[i] = (float)t.y[i] + 0.5f;
+  for (int c = 0; c < G::kBC; ++c) {
+    t.x[c] = tile_x0 + 8 * G::kBC * wx + 8 * c + (lane & 7);
+    t.px[c] = (float)t.x[c] + 0.5f;
   }
 #pragma unroll
-  for (int q = 0; q < kPix; ++q)
-    if (t.x[q & 1] < W && t.y[q >> 1] < H) t.inside |= 1u << q;
-  t.shift = 4 * warp;
+  for (int r = 0; r < 2; ++r) {
+    t.y[r] = tile_y0 + 8 * wy + 4 * r + (lane >> 3);
+    t.py[r] = (float)t.y[r] + 0.5f;
+  }
+  t.inside = 0;
+#pragma unroll
+  for (int q = 0; q < G::kPix; ++q)
+    if (t.x[q % G::kBC] < W && t.y[q / G::kBC] < H) t.inside |= 1u << q;
+  t.shift = G::kPix * warp;
   return t;
 }
 
@@ -226,18 +267,20 @@ struct FwdOut {
 // pixels: dL/dimg = scale (img - target); returns this thread's sum of
 // (img - target)^2 (0 without kL2).  Starts and ends with every thread of
 // the CTA past a barrier.
-template <bool kStats, bool kL2>
+template <int kT, bool kStats, bool kL2>
 __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, const float *__restrict__ gauss,
                                           const uint32_t *__restrict__ keys, uint32_t gmask, uint32_t n_gauss,
                                           unsigned long long *__restrict__ stats) {
+  using G = Geo<kT>;
+  constexpr int kPix = G::kPix, kBatch = G::kBatch, kW = G::kWarps, kBC = G::kBC;
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
   __shared__ uint32_t s_bits[kBatch];
-  __shared__ uint8_t s_list[2][2][32];  // [consumer warp][staging warp][k]: entries reaching the warp
-  __shared__ uint32_t s_cnt[2][2];
+  __shared__ uint8_t s_list[kW][kW][32];  // [consumer warp][staging warp][k]: entries reaching the warp
+  __shared__ uint32_t s_cnt[kW][kW];
   uint32_t n_eval = 0, n_blend = 0;
-  const ThreadPixels tp = thread_pixels(v.x0, v.y0, v.W, v.H);
+  const ThreadPixels<kT> tp = thread_pixels<kT>(v.x0, v.y0, v.W, v.H);
   const uint2 r = v.r;
   float T[kPix], c0[kPix], c1[kPix], c2[kPix];
   uint32_t last[kPix];
@@ -247,7 +290,7 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
     c0[i] = c1[i] = c2[i] = 0.f;
     last[i] = 0;
   }
-  __shared__ uint32_t s_alive[2];  // per warp: slots (8x4 blocks) with a pixel still blending
+  __shared__ uint32_t s_alive[kW];  // per warp: slots (8x4 blocks) with a pixel still blending
   unsigned alive = tp.inside;
   for (uint32_t base = r.x; base < r.y; base += kBatch) {
     const uint32_t walive = __reduce_or_sync(0xffffffffu, alive);
@@ -260,23 +303,27 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
-      my_bits = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0) & (s_alive[0] | (s_alive[1] << 4));
+      uint32_t alive_all = 0u;
+#pragma unroll
+      for (int w = 0; w < kW; ++w) alive_all |= s_alive[w] << (kPix * w);
+      my_bits = block_bits<kT>(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0) & alive_all;
       s_bits[threadIdx.x] = my_bits;
     }
-    compact_lists(my_bits, s_list, s_cnt);
+    compact_lists<kT>(my_bits, s_list, s_cnt);
     __syncthreads();
     const int cw = threadIdx.x >> 5;
-    for (int sw = 0; sw < 2 && alive; ++sw) {
+    for (int sw = 0; sw < kW && alive; ++sw) {
     const int cnt = (int)s_cnt[cw][sw];
     for (int k = 0; k < cnt && alive; ++k) {
       const int j = s_list[cw][sw][k];
-      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform, not 0
+      const uint32_t bits = (s_bits[j] >> tp.shift) & G::kSlotMask;  // warp-uniform, not 0
       const float4 a = s_a[j], b = s_b[j];
       const float2 gb = s_c[j];
-      float dx[2], b1dy[2], b2dy[2];
+      float dx[kBC], b1dy[2], b2dy[2];
+#pragma unroll
+      for (int k = 0; k < kBC; ++k) dx[k] = __fsub_rn(tp.px[k], a.x);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        dx[k] = __fsub_rn(tp.px[k], a.x);
         const float dy = __fsub_rn(tp.py[k], a.y);
         b1dy[k] = __fmul_rn(a.w, dy);
         b2dy[k] = __fmul_rn(b.y, dy);
@@ -286,8 +333,8 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
         if (!(bits & (1u << q))) continue;   // warp-uniform: block q not reached
         if (!(alive & (1u << q))) continue;
         float t1, t2;
-        const float al =
-            fminf(kAlphaMax, ex2_approx(pixel_log2_alpha(a, b, dx[q & 1], b1dy[q >> 1], b2dy[q >> 1], t1, t2)));
+        const float al = fminf(
+            kAlphaMax, ex2_approx(pixel_log2_alpha(a, b, dx[q % kBC], b1dy[q / kBC], b2dy[q / kBC], t1, t2)));
         if (kStats) ++n_eval;
         if (al < kAlphaMin) continue;
         const float Tn = T[q] * (1.f - al);
@@ -316,7 +363,7 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
     if (threadIdx.x == 0) {
       atomicAdd(&stats[0], s_st[0]);
       atomicAdd(&stats[1], s_st[1]);
-      atomicAdd(&stats[2], (unsigned long long)(r.y - r.x) * (kTile * kTile));
+      atomicAdd(&stats[2], (unsigned long long)(r.y - r.x) * (kT * kT));
     }
   }
   const size_t plane = (size_t)v.W * v.H;
@@ -324,7 +371,7 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
 #pragma unroll
   for (int q = 0; q < kPix; ++q) {
     if (!(tp.inside & (1u << q))) continue;
-    const size_t p = (size_t)tp.y[q >> 1] * v.W + tp.x[q & 1];
+    const size_t p = (size_t)tp.y[q / kBC] * v.W + tp.x[q % kBC];
     const float v0 = __fmaf_rn(T[q], v.bg.x, c0[q]);
     const float v1 = __fmaf_rn(T[q], v.bg.y, c1[q]);
     const float v2 = __fmaf_rn(T[q], v.bg.z, c2[q]);
@@ -345,7 +392,9 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
 }
 
 // CTA sum of one float per thread, in double (valid in thread 0).
+template <int kT>
 __device__ __forceinline__ double cta_sum(float x) {
+  constexpr int kThreads = Geo<kT>::kThreads;
   __shared__ double s_l2[kThreads / 32];
   double v = x;
 #pragma unroll
@@ -360,10 +409,15 @@ __device__ __forceinline__ double cta_sum(float x) {
   return t;
 }
 
+// Resident CTAs per SM the blend kernels are compiled for: the forward
+// fits 64 registers a thread, the backward 80.
+template <int kT> constexpr int fwd_min_blocks() { return kT == 8 ? 32 : (kT == 16 ? 16 : 4); }
+template <int kT> constexpr int bwd_min_blocks() { return kT == 8 ? 24 : (kT == 16 ? 12 : 3); }
+
 // One CTA per tile of one canvas.  kL2: mean((img - target)^2) added to
 // *loss (one double atomic per CTA; *loss zeroed by the launcher).
-template <bool kStats, bool kL2 = false>
-__global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *__restrict__ gauss,
+template <int kT, bool kStats, bool kL2 = false>
+__global__ void __launch_bounds__(Geo<kT>::kThreads, fwd_min_blocks<kT>()) render_fwd_kernel(const float *__restrict__ gauss,
                                                                   const uint32_t *__restrict__ keys,
                                                                   const uint2 *__restrict__ ranges, int W, int H,
                                                                   int tiles_x, uint32_t gmask, uint32_t n_gauss,
@@ -375,12 +429,12 @@ __global__ void __launch_bounds__(kThreads, 16) render_fwd_kernel(const float *_
                                                                   float *__restrict__ dimg = nullptr,
                                                                   double *__restrict__ loss = nullptr) {
   const int tile = blockIdx.x;
-  const TileView v{(tile % tiles_x) * kTile, (tile / tiles_x) * kTile, W, H, ranges[tile], bg};
+  const TileView v{(tile % tiles_x) * kT, (tile / tiles_x) * kT, W, H, ranges[tile], bg};
   const size_t plane = (size_t)W * H;
   const FwdOut o{img, T_out, nc_out, target, dimg, kL2 ? (float)(2.0 / (double)(3 * plane)) : 0.f};
-  const float l2 = fwd_tile<kStats, kL2>(v, o, gauss, keys, gmask, n_gauss, stats);
+  const float l2 = fwd_tile<kT, kStats, kL2>(v, o, gauss, keys, gmask, n_gauss, stats);
   if (kL2) {
-    const double t = cta_sum(l2);
+    const double t = cta_sum<kT>(l2);
     if (threadIdx.x == 0) atomicAdd(loss, t / (double)(3 * plane));
   }
 }
@@ -391,18 +445,19 @@ __device__ __forceinline__ int batch_image_of_tile(const BatchImage *__restrict_
 }
 
 // The tile view of global tile t of a batch (image b).
+template <int kT>
 __device__ __forceinline__ TileView batch_view(const BatchImage &im, uint32_t t, const uint2 *__restrict__ ranges) {
   const int local = (int)((int64_t)t - im.tile0);
   const int ty = local / im.tiles_x, tx = local - ty * im.tiles_x;
-  return TileView{tx * kTile, ty * kTile, im.W, im.H, ranges[t], make_float3(im.bg[0], im.bg[1], im.bg[2])};
+  return TileView{tx * kT, ty * kT, im.W, im.H, ranges[t], make_float3(im.bg[0], im.bg[1], im.bg[2])};
 }
 
 // Persistent forward over a batch: each CTA takes tiles from the atomic
 // queue *queue (zeroed by the launcher) until all n_tiles are done.  kL2:
 // loss[b] += mean over image b of (img - target)^2; a CTA keeps a running
 // sum while its tiles stay in one image and adds it once per change.
-template <bool kL2>
-__global__ void __launch_bounds__(kThreads, 16) batch_render_fwd_kernel(
+template <int kT, bool kL2>
+__global__ void __launch_bounds__(Geo<kT>::kThreads, fwd_min_blocks<kT>()) batch_render_fwd_kernel(
     const float *__restrict__ gauss, const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges,
     const BatchImage *__restrict__ tab, int n_images, uint32_t n_tiles, uint32_t n_gauss,
     unsigned int *__restrict__ queue, const float *__restrict__ target, float *__restrict__ img,
@@ -423,12 +478,12 @@ __global__ void __launch_bounds__(kThreads, 16) batch_render_fwd_kernel(
     const int b = s_b;
     if (t >= n_tiles) break;
     const BatchImage &im = tab[b];
-    const TileView v = batch_view(im, t, ranges);
+    const TileView v = batch_view<kT>(im, t, ranges);
     const FwdOut o{img + 3 * im.pix0, T_out + im.pix0, nc_out + im.pix0, kL2 ? target + 3 * im.pix0 : nullptr,
                    kL2 ? dimg + 3 * im.pix0 : nullptr, im.l2_scale};
-    const float l2 = fwd_tile<false, kL2>(v, o, gauss, vals, 0xffffffffu, n_gauss, nullptr);
+    const float l2 = fwd_tile<kT, false, kL2>(v, o, gauss, vals, 0xffffffffu, n_gauss, nullptr);
     if (kL2) {
-      const double s = cta_sum(l2);
+      const double s = cta_sum<kT>(l2);
       if (threadIdx.x == 0) {
         if (b != acc_b) {
           if (acc_b >= 0) atomicAdd(loss + acc_b, acc / (3.0 * (double)tab[acc_b].W * (double)tab[acc_b].H));
@@ -453,43 +508,53 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Number of per-Gaussian sums the backward accumulates (see render_bwd_kernel).
 constexpr int kSums = 9;
 // The backward parks the per-lane partial sums of up to kPend entries of a
-// warp in shared memory, then reduces them transposed: lane l adds up row l
-// (entry l / 8, sum l % 8) and eight lanes per entry finish sum 8.  A row
-// holds the 32 lanes' partials padded to 36 floats, so the 128-bit reads of
-// a quarter-warp hit distinct banks.
-constexpr int kPend = 4;
+// warp in shared memory (4; 2 for 32 x 32 tiles, whose eight warps would
+// otherwise need more shared memory than a CTA's static 48 KB), then reduces
+// them transposed: lane l adds up row l (entry l / 8, sum l % 8) and eight
+// lanes per entry finish sum 8.  A row holds the 32 lanes' partials padded
+// to 36 floats, so the 128-bit reads of a quarter-warp hit distinct banks.
+template <int kT> constexpr int pend_of() { return kT == 32 ? 2 : 4; }
 constexpr int kRow = 36;
 
 // Reduce the parked partials of n_pend (<= kPend) entries of this warp and
 // add the totals to the per-Gaussian sums.  part is the warp's
 // [kPend * kSums][kRow] block, pend_g the entries' Gaussian indices.
+template <int kPend>
 __device__ __forceinline__ void flush_pending(const float *part, const uint32_t *pend_g, int n_pend, int lane,
                                               float *__restrict__ sums, uint32_t n_gauss) {
   __syncwarp();
-  {  // sums 0..7 of entries 0..3: one row per lane
-    const int e = lane >> 3, k = lane & 7;
-    const float4 *row = reinterpret_cast<const float4 *>(part + (e * kSums + k) * kRow);
-    float4 acc = row[0];
+  const int e = lane >> 3;                   // this lane's entry
+  const bool mine = kPend == 4 || e < kPend;  // lanes past the parked entries add nothing
+  {  // sums 0..7 of each entry: one row per lane
+    const int k = lane & 7;
+    float tot = 0.f;
+    if (mine) {
+      const float4 *row = reinterpret_cast<const float4 *>(part + (e * kSums + k) * kRow);
+      float4 acc = row[0];
 #pragma unroll
-    for (int c = 1; c < 8; ++c) {
-      const float4 x = row[c];
-      acc.x += x.x;
-      acc.y += x.y;
-      acc.z += x.z;
-      acc.w += x.w;
+      for (int c = 1; c < 8; ++c) {
+        const float4 x = row[c];
+        acc.x += x.x;
+        acc.y += x.y;
+        acc.z += x.z;
+        acc.w += x.w;
+      }
+      tot = (acc.x + acc.y) + (acc.z + acc.w);
     }
-    const float tot = (acc.x + acc.y) + (acc.z + acc.w);
-    const uint32_t g = pend_g[e];
+    const uint32_t g = mine ? pend_g[e] : 0xffffffffu;
     if (e < n_pend && tot != 0.f && g < n_gauss) atomicAdd(sums + (size_t)g * BS_DGAUSS_FLOATS + k, tot);
   }
-  {  // sum 8 of entry lane / 8: eight lanes, four partials each
-    const int e = lane >> 3, c = lane & 7;
-    const float4 x = reinterpret_cast<const float4 *>(part + (e * kSums + 8) * kRow)[c];
-    float tot = (x.x + x.y) + (x.z + x.w);
+  {  // sum 8 of each entry: eight lanes, four partials each
+    const int c = lane & 7;
+    float tot = 0.f;
+    if (mine) {
+      const float4 x = reinterpret_cast<const float4 *>(part + (e * kSums + 8) * kRow)[c];
+      tot = (x.x + x.y) + (x.z + x.w);
+    }
     tot += __shfl_xor_sync(0xffffffffu, tot, 4);
     tot += __shfl_xor_sync(0xffffffffu, tot, 2);
     tot += __shfl_xor_sync(0xffffffffu, tot, 1);
-    const uint32_t g = pend_g[e];
+    const uint32_t g = mine ? pend_g[e] : 0xffffffffu;
     if (c == 0 && e < n_pend && tot != 0.f && g < n_gauss) atomicAdd(sums + (size_t)g * BS_DGAUSS_FLOATS + 8, tot);
   }
   __syncwarp();
@@ -516,21 +581,24 @@ struct BwdIn {
 
 // The reverse walk of one tile (see above).  Starts and ends with every
 // thread of the CTA past a barrier.
+template <int kT>
 __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, const float *__restrict__ gauss,
                                          const uint32_t *__restrict__ keys, uint32_t gmask, uint32_t n_gauss,
                                          float *__restrict__ sums) {
+  using G = Geo<kT>;
+  constexpr int kPix = G::kPix, kBatch = G::kBatch, kW = G::kWarps, kBC = G::kBC, kPend = pend_of<kT>();
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
   __shared__ uint32_t s_g[kBatch];
   __shared__ uint32_t s_bits[kBatch];
-  __shared__ uint8_t s_list[2][2][32];  // [consumer warp][staging warp][k]: entries reaching the warp
-  __shared__ uint32_t s_cnt[2][2];
+  __shared__ uint8_t s_list[kW][kW][32];  // [consumer warp][staging warp][k]: entries reaching the warp
+  __shared__ uint32_t s_cnt[kW][kW];
   __shared__ uint32_t s_max_last;
-  __shared__ uint32_t s_wlast[2][kPix];
-  __shared__ __align__(16) float s_part[2][kPend * kSums * kRow];
-  __shared__ uint32_t s_pend_g[2][kPend];
-  const ThreadPixels tp = thread_pixels(v.x0, v.y0, v.W, v.H);
+  __shared__ uint32_t s_wlast[kW][kPix];
+  __shared__ __align__(16) float s_part[kW][kPend * kSums * kRow];
+  __shared__ uint32_t s_pend_g[kW][kPend];
+  const ThreadPixels<kT> tp = thread_pixels<kT>(v.x0, v.y0, v.W, v.H);
   const uint2 r = v.r;
   const float3 bg = v.bg;
   const int lane = threadIdx.x & 31;
@@ -546,7 +614,7 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
     g0[q] = g1[q] = g2[q] = 0.f;
     last[q] = 0;
     if (tp.inside & (1u << q)) {
-      const size_t p = (size_t)tp.y[q >> 1] * v.W + tp.x[q & 1];
+      const size_t p = (size_t)tp.y[q / kBC] * v.W + tp.x[q % kBC];
       T[q] = in.T_final[p];
       last[q] = in.n_contrib[p];
       g0[q] = in.dimg[p];
@@ -581,26 +649,27 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
       s_g[threadIdx.x] = g;
-      my_bits = block_bits(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
+      my_bits = block_bits<kT>(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0);
 #pragma unroll
-      for (int b = 0; b < 2 * kPix; ++b)
-        if (i >= s_wlast[b >> 2][b & 3]) my_bits &= ~(1u << b);
+      for (int b = 0; b < G::kBits; ++b)
+        if (i >= s_wlast[b / kPix][b % kPix]) my_bits &= ~(1u << b);
       s_bits[threadIdx.x] = my_bits;
     }
-    compact_lists(my_bits, s_list, s_cnt);
+    compact_lists<kT>(my_bits, s_list, s_cnt);
     __syncthreads();
     const int cw = threadIdx.x >> 5;
-    for (int sw = 1; sw >= 0; --sw)
+    for (int sw = kW - 1; sw >= 0; --sw)
     for (int k = (int)s_cnt[cw][sw] - 1; k >= 0; --k) {
       const int j = s_list[cw][sw][k];
       const uint32_t pos = start + (uint32_t)j;
-      const uint32_t bits = (s_bits[j] >> tp.shift) & 15u;  // warp-uniform, not 0
+      const uint32_t bits = (s_bits[j] >> tp.shift) & G::kSlotMask;  // warp-uniform, not 0
       const float4 a = s_a[j], b = s_b[j];
       const float2 gb = s_c[j];
-      float dx[2], b1dy[2], b2dy[2];
+      float dx[kBC], b1dy[2], b2dy[2];
+#pragma unroll
+      for (int k = 0; k < kBC; ++k) dx[k] = __fsub_rn(tp.px[k], a.x);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        dx[k] = __fsub_rn(tp.px[k], a.x);
         const float dy = __fsub_rn(tp.py[k], a.y);
         b1dy[k] = __fmul_rn(a.w, dy);
         b2dy[k] = __fmul_rn(b.y, dy);
@@ -615,7 +684,7 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
         // branch-free per pixel: a pixel past its last blended Gaussian, or
         // below the alpha threshold, gets alpha = 0, an exact no-op below
         float t1, t2;
-        const float raw = ex2_approx(pixel_log2_alpha(a, b, dx[q & 1], b1dy[q >> 1], b2dy[q >> 1], t1, t2));
+        const float raw = ex2_approx(pixel_log2_alpha(a, b, dx[q % kBC], b1dy[q / kBC], b2dy[q / kBC], t1, t2));
         const float al0 = fminf(kAlphaMax, raw);
         const bool on = pos < last[q] && al0 >= kAlphaMin;
         const float al = on ? al0 : 0.f;
@@ -643,19 +712,20 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
         for (int q = 0; q < kSums; ++q) dst[q * kRow] = v[q];
         if (lane == 0) pend_g[n_pend] = s_g[j];
         if (++n_pend == kPend) {
-          flush_pending(part, pend_g, n_pend, lane, sums, n_gauss);
+          flush_pending<kPend>(part, pend_g, n_pend, lane, sums, n_gauss);
           n_pend = 0;
         }
       }
     }
     end = start;
   }
-  if (n_pend) flush_pending(part, pend_g, n_pend, lane, sums, n_gauss);
+  if (n_pend) flush_pending<kPend>(part, pend_g, n_pend, lane, sums, n_gauss);
   __syncthreads();
 }
 
 // One CTA per tile of one canvas.
-__global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *__restrict__ gauss,
+template <int kT>
+__global__ void __launch_bounds__(Geo<kT>::kThreads, bwd_min_blocks<kT>()) render_bwd_kernel(const float *__restrict__ gauss,
                                                                   const uint32_t *__restrict__ keys,
                                                                   const uint2 *__restrict__ ranges, int W, int H,
                                                                   int tiles_x, uint32_t gmask, uint32_t n_gauss,
@@ -664,12 +734,13 @@ __global__ void __launch_bounds__(kThreads, 12) render_bwd_kernel(const float *_
                                                                   const float *__restrict__ dimg,
                                                                   float *__restrict__ sums) {
   const int tile = blockIdx.x;
-  const TileView v{(tile % tiles_x) * kTile, (tile / tiles_x) * kTile, W, H, ranges[tile], bg};
-  bwd_tile(v, BwdIn{T_final, n_contrib, dimg}, gauss, keys, gmask, n_gauss, sums);
+  const TileView v{(tile % tiles_x) * kT, (tile / tiles_x) * kT, W, H, ranges[tile], bg};
+  bwd_tile<kT>(v, BwdIn{T_final, n_contrib, dimg}, gauss, keys, gmask, n_gauss, sums);
 }
 
 // Persistent backward over a batch (the queue of batch_render_fwd_kernel).
-__global__ void __launch_bounds__(kThreads, 12) batch_render_bwd_kernel(
+template <int kT>
+__global__ void __launch_bounds__(Geo<kT>::kThreads, bwd_min_blocks<kT>()) batch_render_bwd_kernel(
     const float *__restrict__ gauss, const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges,
     const BatchImage *__restrict__ tab, int n_images, uint32_t n_tiles, uint32_t n_gauss,
     unsigned int *__restrict__ queue, const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
@@ -687,9 +758,9 @@ __global__ void __launch_bounds__(kThreads, 12) batch_render_bwd_kernel(
     const int b = s_b;
     if (t >= n_tiles) break;
     const BatchImage &im = tab[b];
-    const TileView v = batch_view(im, t, ranges);
-    bwd_tile(v, BwdIn{T_final + im.pix0, n_contrib + im.pix0, dimg + 3 * im.pix0}, gauss, vals, 0xffffffffu,
-             n_gauss, sums);
+    const TileView v = batch_view<kT>(im, t, ranges);
+    bwd_tile<kT>(v, BwdIn{T_final + im.pix0, n_contrib + im.pix0, dimg + 3 * im.pix0}, gauss, vals, 0xffffffffu,
+                 n_gauss, sums);
   }
 }
 
@@ -764,23 +835,56 @@ __global__ void l2_kernel(const float *__restrict__ img, const float *__restrict
 
 }  // namespace
 
+// Tile side -> one instantiation of a launcher template.
+#define BS_BY_TILE(tile, call)                                                  \
+  switch (tile) {                                                              \
+    case 8: { constexpr int kT = 8; call; } break;                             \
+    case 16: { constexpr int kT = 16; call; } break;                           \
+    case 32: { constexpr int kT = 32; call; } break;                           \
+    default: set_error("tile side %d not supported (8, 16, 32)", (int)(tile)); \
+      return BS_ERR_UNSUPPORTED;                                               \
+  }
+
+template <int kT>
+void fwd_plain(const float *gauss, int64_t n_gauss, const bs_canvas &cv, uint32_t gmask, const uint32_t *keys,
+               const uint2 *rg, float *img, float *T_final, uint32_t *n_contrib, cudaStream_t s,
+               unsigned long long *stats, const float *target, float *dimg, double *loss) {
+  const int tiles_x = div_up(cv.width, kT), tiles_y = div_up(cv.height, kT);
+  const auto bg = make_float3(cv.bg[0], cv.bg[1], cv.bg[2]);
+  constexpr int kThreads = Geo<kT>::kThreads;
+  if (stats)
+    render_fwd_kernel<kT, true><<<tiles_x * tiles_y, kThreads, 0, s>>>(
+        gauss, keys, rg, cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib, stats);
+  else if (target)
+    render_fwd_kernel<kT, false, true><<<tiles_x * tiles_y, kThreads, 0, s>>>(
+        gauss, keys, rg, cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib,
+        nullptr, target, dimg, loss);
+  else
+    render_fwd_kernel<kT, false><<<tiles_x * tiles_y, kThreads, 0, s>>>(
+        gauss, keys, rg, cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib,
+        nullptr);
+}
+
+template <int kT>
+void bwd_plain(const float *gauss, int64_t n_gauss, const bs_canvas &cv, uint32_t gmask, const uint32_t *keys,
+               const uint2 *rg, const float *T_final, const uint32_t *n_contrib, const float *dL_dimg, float *dgauss,
+               cudaStream_t s) {
+  const int tiles_x = div_up(cv.width, kT), tiles_y = div_up(cv.height, kT);
+  render_bwd_kernel<kT><<<tiles_x * tiles_y, Geo<kT>::kThreads, 0, s>>>(
+      gauss, keys, rg, cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss,
+      make_float3(cv.bg[0], cv.bg[1], cv.bg[2]), T_final, n_contrib, dL_dimg, dgauss);
+}
+
+uint32_t gauss_mask(int gbits) { return gbits >= 32 ? 0xffffffffu : ((1u << gbits) - 1u); }
+
 bs_status launch_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas &cv, int gbits,
                             const uint32_t *keys,
                             const uint32_t *ranges, float *img, float *T_final, uint32_t *n_contrib,
                             cudaStream_t s, unsigned long long *stats) {
-  const int tiles_x = div_up(cv.width, kTile), tiles_y = div_up(cv.height, kTile);
-  const uint32_t gmask = gbits >= 32 ? 0xffffffffu : ((1u << gbits) - 1u);
-  const auto bg = make_float3(cv.bg[0], cv.bg[1], cv.bg[2]);
   const auto *rg = reinterpret_cast<const uint2 *>(ranges);
-  if (stats) {
-    BS_CUDA(cudaMemsetAsync(stats, 0, 4 * sizeof(unsigned long long), s));
-    render_fwd_kernel<true><<<tiles_x * tiles_y, kThreads, 0, s>>>(
-        gauss, keys, rg, cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib, stats);
-  } else {
-    render_fwd_kernel<false><<<tiles_x * tiles_y, kThreads, 0, s>>>(
-        gauss, keys, rg, cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss, bg, img, T_final, n_contrib,
-        nullptr);
-  }
+  if (stats) BS_CUDA(cudaMemsetAsync(stats, 0, 4 * sizeof(unsigned long long), s));
+  BS_BY_TILE(cv.tile, (fwd_plain<kT>(gauss, n_gauss, cv, gauss_mask(gbits), keys, rg, img, T_final, n_contrib, s,
+                                     stats, nullptr, nullptr, nullptr)));
   BS_LAUNCHED("render_fwd_kernel");
   return BS_OK;
 }
@@ -788,13 +892,10 @@ bs_status launch_render_fwd(const float *gauss, int64_t n_gauss, const bs_canvas
 bs_status launch_render_fwd_l2(const float *gauss, int64_t n_gauss, const bs_canvas &cv, int gbits,
                                const uint32_t *keys, const uint32_t *ranges, const float *target, float *img,
                                float *T_final, uint32_t *n_contrib, float *dimg, double *loss, cudaStream_t s) {
-  const int tiles_x = div_up(cv.width, kTile), tiles_y = div_up(cv.height, kTile);
-  const uint32_t gmask = gbits >= 32 ? 0xffffffffu : ((1u << gbits) - 1u);
-  const auto bg = make_float3(cv.bg[0], cv.bg[1], cv.bg[2]);
   BS_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s));
-  render_fwd_kernel<false, true><<<tiles_x * tiles_y, kThreads, 0, s>>>(
-      gauss, keys, reinterpret_cast<const uint2 *>(ranges), cv.width, cv.height, tiles_x, gmask, (uint32_t)n_gauss,
-      bg, img, T_final, n_contrib, nullptr, target, dimg, loss);
+  const auto *rg = reinterpret_cast<const uint2 *>(ranges);
+  BS_BY_TILE(cv.tile, (fwd_plain<kT>(gauss, n_gauss, cv, gauss_mask(gbits), keys, rg, img, T_final, n_contrib, s,
+                                     nullptr, target, dimg, loss)));
   BS_LAUNCHED("render_fwd_kernel");
   return BS_OK;
 }
@@ -802,12 +903,10 @@ bs_status launch_render_fwd_l2(const float *gauss, int64_t n_gauss, const bs_can
 bs_status launch_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas &cv, int gbits,
                             const uint32_t *keys, const uint32_t *ranges, const float *T_final,
                             const uint32_t *n_contrib, const float *dL_dimg, float *dgauss, cudaStream_t s) {
-  const int tiles_x = div_up(cv.width, kTile), tiles_y = div_up(cv.height, kTile);
-  const uint32_t gmask = gbits >= 32 ? 0xffffffffu : ((1u << gbits) - 1u);
   BS_CUDA(cudaMemsetAsync(dgauss, 0, sizeof(float) * BS_DGAUSS_FLOATS * (size_t)n_gauss, s));
-  render_bwd_kernel<<<tiles_x * tiles_y, kThreads, 0, s>>>(
-      gauss, keys, reinterpret_cast<const uint2 *>(ranges), cv.width, cv.height, tiles_x, gmask,
-      (uint32_t)n_gauss, make_float3(cv.bg[0], cv.bg[1], cv.bg[2]), T_final, n_contrib, dL_dimg, dgauss);
+  const auto *rg = reinterpret_cast<const uint2 *>(ranges);
+  BS_BY_TILE(cv.tile, (bwd_plain<kT>(gauss, n_gauss, cv, gauss_mask(gbits), keys, rg, T_final, n_contrib, dL_dimg,
+                                     dgauss, s)));
   BS_LAUNCHED("render_bwd_kernel");
   grads_from_sums_kernel<<<(unsigned)div_up64(n_gauss, 256), 256, 0, s>>>(gauss, dgauss, n_gauss);
   BS_LAUNCHED("grads_from_sums_kernel");
@@ -828,14 +927,14 @@ bs_status launch_l2(const float *img, const float *target, int64_t n, float *dim
 }
 
 // Persistent grids: as many CTAs as fit on the device at once (queried once
-// per device and kernel).
+// per device and kernel; slot names the kernel).
 template <typename Kernel>
 bs_status persistent_grid(Kernel k, int threads, int slot, int *grid) {
-  constexpr int kMaxDev = 64;
-  static int cache[kMaxDev][4] = {};
+  constexpr int kMaxDev = 64, kSlots = 16;
+  static int cache[kMaxDev][kSlots] = {};
   int dev = 0;
   BS_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDev) {
+  if (dev < 0 || dev >= kMaxDev || slot < 0 || slot >= kSlots) {
     set_error("device %d: at most %d devices supported", dev, kMaxDev);
     return BS_ERR_UNSUPPORTED;
   }
@@ -849,6 +948,8 @@ bs_status persistent_grid(Kernel k, int threads, int slot, int *grid) {
   return BS_OK;
 }
 
+template <int kT> constexpr int tile_slot() { return kT == 8 ? 0 : (kT == 16 ? 1 : 2); }
+
 // The workspace's two queue counters: [0] forward, [1] backward.
 unsigned int *batch_queue(const BatchPlan &p, void *ws) {
   return reinterpret_cast<unsigned int *>(static_cast<char *>(ws) + p.off_queue);
@@ -858,27 +959,50 @@ const BatchImage *batch_table(const BatchPlan &p, const void *ws) {
   return reinterpret_cast<const BatchImage *>(static_cast<const char *>(ws) + p.off_images);
 }
 
+template <int kT>
+bs_status fwd_batch(const BatchPlan &p, void *ws, const float *gauss, const uint32_t *vals, const uint2 *rg,
+                    const float *target, float *img, float *T_final, uint32_t *n_contrib, float *dimg, double *loss,
+                    cudaStream_t s) {
+  constexpr int kThreads = Geo<kT>::kThreads;
+  unsigned int *queue = batch_queue(p, ws);
+  int grid = 0;
+  if (target) {
+    BS_TRY(persistent_grid(batch_render_fwd_kernel<kT, true>, kThreads, tile_slot<kT>(), &grid));
+    grid = (int)std::min<int64_t>(grid, p.n_tiles);
+    batch_render_fwd_kernel<kT, true><<<grid, kThreads, 0, s>>>(gauss, vals, rg, batch_table(p, ws), p.n_images,
+                                                               (uint32_t)p.n_tiles, (uint32_t)p.n_gauss, queue,
+                                                               target, img, T_final, n_contrib, dimg, loss);
+  } else {
+    BS_TRY(persistent_grid(batch_render_fwd_kernel<kT, false>, kThreads, 3 + tile_slot<kT>(), &grid));
+    grid = (int)std::min<int64_t>(grid, p.n_tiles);
+    batch_render_fwd_kernel<kT, false><<<grid, kThreads, 0, s>>>(gauss, vals, rg, batch_table(p, ws), p.n_images,
+                                                                (uint32_t)p.n_tiles, (uint32_t)p.n_gauss, queue,
+                                                                nullptr, img, T_final, n_contrib, nullptr, nullptr);
+  }
+  return BS_OK;
+}
+
+template <int kT>
+bs_status bwd_batch(const BatchPlan &p, void *ws, const float *gauss, const uint32_t *vals, const uint2 *rg,
+                    const float *T_final, const uint32_t *n_contrib, const float *dimg, float *dgauss,
+                    cudaStream_t s) {
+  constexpr int kThreads = Geo<kT>::kThreads;
+  int grid = 0;
+  BS_TRY(persistent_grid(batch_render_bwd_kernel<kT>, kThreads, 6 + tile_slot<kT>(), &grid));
+  grid = (int)std::min<int64_t>(grid, p.n_tiles);
+  batch_render_bwd_kernel<kT><<<grid, kThreads, 0, s>>>(gauss, vals, rg, batch_table(p, ws), p.n_images,
+                                                        (uint32_t)p.n_tiles, (uint32_t)p.n_gauss,
+                                                        batch_queue(p, ws) + 1, T_final, n_contrib, dimg, dgauss);
+  return BS_OK;
+}
+
 bs_status launch_batch_render_fwd(const BatchPlan &p, void *ws, const float *gauss, const uint32_t *vals,
                                   const uint32_t *ranges, const float *target, float *img, float *T_final,
                                   uint32_t *n_contrib, float *dimg, double *loss, cudaStream_t s) {
-  unsigned int *queue = batch_queue(p, ws);
-  BS_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned int), s));
+  BS_CUDA(cudaMemsetAsync(batch_queue(p, ws), 0, sizeof(unsigned int), s));
+  if (target) BS_CUDA(cudaMemsetAsync(loss, 0, sizeof(double) * (size_t)p.n_images, s));
   const auto *rg = reinterpret_cast<const uint2 *>(ranges);
-  int grid = 0;
-  if (target) {
-    BS_CUDA(cudaMemsetAsync(loss, 0, sizeof(double) * (size_t)p.n_images, s));
-    BS_TRY(persistent_grid(batch_render_fwd_kernel<true>, kThreads, 0, &grid));
-    grid = (int)std::min<int64_t>(grid, p.n_tiles);
-    batch_render_fwd_kernel<true><<<grid, kThreads, 0, s>>>(gauss, vals, rg, batch_table(p, ws), p.n_images,
-                                                           (uint32_t)p.n_tiles, (uint32_t)p.n_gauss, queue, target,
-                                                           img, T_final, n_contrib, dimg, loss);
-  } else {
-    BS_TRY(persistent_grid(batch_render_fwd_kernel<false>, kThreads, 1, &grid));
-    grid = (int)std::min<int64_t>(grid, p.n_tiles);
-    batch_render_fwd_kernel<false><<<grid, kThreads, 0, s>>>(gauss, vals, rg, batch_table(p, ws), p.n_images,
-                                                            (uint32_t)p.n_tiles, (uint32_t)p.n_gauss, queue,
-                                                            nullptr, img, T_final, n_contrib, nullptr, nullptr);
-  }
+  BS_BY_TILE(p.tile, BS_TRY((fwd_batch<kT>(p, ws, gauss, vals, rg, target, img, T_final, n_contrib, dimg, loss, s))));
   BS_LAUNCHED("batch_render_fwd_kernel");
   return BS_OK;
 }
@@ -886,15 +1010,10 @@ bs_status launch_batch_render_fwd(const BatchPlan &p, void *ws, const float *gau
 bs_status launch_batch_render_bwd(const BatchPlan &p, void *ws, const float *gauss, const uint32_t *vals,
                                   const uint32_t *ranges, const float *T_final, const uint32_t *n_contrib,
                                   const float *dimg, float *dgauss, cudaStream_t s) {
-  unsigned int *queue = batch_queue(p, ws) + 1;
-  BS_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned int), s));
+  BS_CUDA(cudaMemsetAsync(batch_queue(p, ws) + 1, 0, sizeof(unsigned int), s));
   BS_CUDA(cudaMemsetAsync(dgauss, 0, sizeof(float) * BS_DGAUSS_FLOATS * (size_t)p.n_gauss, s));
-  int grid = 0;
-  BS_TRY(persistent_grid(batch_render_bwd_kernel, kThreads, 2, &grid));
-  grid = (int)std::min<int64_t>(grid, p.n_tiles);
-  batch_render_bwd_kernel<<<grid, kThreads, 0, s>>>(gauss, vals, reinterpret_cast<const uint2 *>(ranges),
-                                                    batch_table(p, ws), p.n_images, (uint32_t)p.n_tiles,
-                                                    (uint32_t)p.n_gauss, queue, T_final, n_contrib, dimg, dgauss);
+  const auto *rg = reinterpret_cast<const uint2 *>(ranges);
+  BS_BY_TILE(p.tile, BS_TRY((bwd_batch<kT>(p, ws, gauss, vals, rg, T_final, n_contrib, dimg, dgauss, s))));
   BS_LAUNCHED("batch_render_bwd_kernel");
   if (p.n_gauss > 0) {
     grads_from_sums_kernel<<<(unsigned)div_up64(p.n_gauss, 256), 256, 0, s>>>(gauss, dgauss, p.n_gauss);

@@ -64,9 +64,14 @@ def test_invalid_arguments_are_rejected_on_the_host(bs):
     assert bs.lib.bs_bin_tiles_workspace(10, ctypes.byref(cv), 100, ctypes.byref(nb)) == bs.BS_ERR_INVALID_ARG
     cv = bs.Canvas(64, 64, tile=12).c()
     assert bs.lib.bs_bin_tiles_workspace(10, ctypes.byref(cv), 100, ctypes.byref(nb)) == bs.BS_ERR_UNSUPPORTED
-    # keys wider than 32 bits
+    # keys wider than 32 bits (22 tile + 20 Gaussian bits): two 64-bit key
+    # buffers of the capacity in the workspace instead of one 32-bit buffer
     cv = bs.Canvas(32768, 32768).c()
-    assert bs.lib.bs_bin_tiles_workspace(1 << 20, ctypes.byref(cv), 100, ctypes.byref(nb)) == bs.BS_ERR_UNSUPPORTED
+    assert bs.lib.bs_bin_tiles_workspace(1 << 20, ctypes.byref(cv), 100000, ctypes.byref(nb)) == bs.BS_OK
+    wide = nb.value
+    cv = bs.Canvas(2048, 2048).c()
+    assert bs.lib.bs_bin_tiles_workspace(1 << 18, ctypes.byref(cv), 100000, ctypes.byref(nb)) == bs.BS_OK
+    assert wide - nb.value >= 100000 * (16 - 4)
     assert bs.lib.bs_status_string(bs.BS_ERR_TIMEOUT) == b"BS_ERR_TIMEOUT"
     bad = bs.SampleCfg(g_open=16, rho=0.0).c()
     assert bs.lib.bs_sample_curves(ctypes.byref(curves), ctypes.byref(bad), None, None) == bs.BS_ERR_INVALID_ARG
