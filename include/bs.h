@@ -536,6 +536,68 @@ typedef struct {
 bs_status bs_adam_step(const bs_adam_group *groups, int32_t n_groups, const bs_adam_cfg *cfg, int32_t *step,
                        bs_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Learned initialisation (not in the paper: a proposal network for initial
+ * curves).  A 5-layer convolutional encoder maps a side x side RGB patch
+ * (side a multiple of 32) to one closed curve per 32 x 32 cell: five 4 x 4
+ * convolutions of stride 2 and padding 1 with ReLU (channels 8 -> 32 -> 64
+ * -> 128 -> 256 -> 256, the RGB input padded to 8), then a 1 x 1 head
+ * (256 -> 32).  The head's first 28 outputs o of a cell with centre c give
+ * the curve: control points P_j = c + BS_NET_REACH tanh(o_{2j}, o_{2j+1})
+ * (j = 0..11, patch pixels), colour sigmoid(o_24..26), opacity
+ * sigmoid(o_27).  Convolutions run as implicit GEMMs on the bf16 tensor
+ * cores with float32 accumulation; activations are bf16.
+ * ---------------------------------------------------------------------- */
+#define BS_NET_LAYERS 6
+#define BS_NET_REACH 24.0f
+
+/* Weights of the network (device, caller-owned).  w[l]: float32 master
+ * weights of layer l, [Cout][ky][kx][Cin] then the bias [Cout]
+ * (bs_net_param_count(l) floats; layer 5 is the head, [32][256] + [32]).
+ * w_bf16[l]: bfloat16 copy of the weights (without the bias), written by
+ * bs_net_sync_weights. */
+typedef struct {
+  const float *w[BS_NET_LAYERS];
+  uint16_t *w_bf16[BS_NET_LAYERS];
+} bs_net;
+
+/* Gradients of the master weights (device, float32, same layouts). */
+typedef struct {
+  float *g[BS_NET_LAYERS];
+} bs_net_grad;
+
+/* Floats of layer `layer`'s master array (weights + bias); -1 if out of range. */
+int64_t bs_net_param_count(int32_t layer);
+
+/* Workspace bytes for n patches of side `side` (activations and their
+ * gradients, bf16).  Host arithmetic only. */
+bs_status bs_net_workspace(int32_t n, int32_t side, size_t *bytes);
+
+/* w_bf16[l] = bf16(w[l]) for every layer (after an update of the master
+ * weights). */
+bs_status bs_net_sync_weights(const bs_net *net, bs_stream stream);
+
+/*
+ * Forward of n patches (planar float32 [n][3][side][side], values in [0,1]).
+ * Writes (device, each may be NULL) the head outputs head_out [n][cells][32],
+ * and the proposed curves: ctrl [n][cells][12][2] patch pixels, color
+ * [n][cells][3], opac [n][cells]; cells = (side / 32)^2, row-major.
+ */
+bs_status bs_net_forward(const bs_net *net, const float *patches, int32_t n, int32_t side, void *ws,
+                         size_t ws_bytes, float *head_out, float *ctrl, float *color, float *opac,
+                         bs_stream stream);
+
+/*
+ * One training step's forward and backward against target curves t_ctrl
+ * [n][cells][12][2], t_color [n][cells][3], t_opac [n][cells] (device): the
+ * loss L = mean over cells of sum_j |P_j - P*_j|^2 / BS_NET_REACH^2 +
+ * |colour - colour*|^2 + (opacity - opacity*)^2 to loss_out (device double),
+ * and dL/d(master weights) to grad (zeroed and written).
+ */
+bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, int32_t side,
+                            const float *t_ctrl, const float *t_color, const float *t_opac, void *ws,
+                            size_t ws_bytes, const bs_net_grad *grad, double *loss_out, bs_stream stream);
+
 /* Synchronise the stream and read the device status word of a binning
  * workspace: BS_OK or the first kernel-side error recorded since the
  * workspace's last bs_bin_tiles call. */

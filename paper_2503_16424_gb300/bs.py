@@ -95,6 +95,16 @@ class bs_adam_cfg(ctypes.Structure):
 
 
 ADAM_MAX_GROUPS = 16
+NET_LAYERS = 6
+NET_REACH = 24.0
+
+
+class bs_net(ctypes.Structure):
+    _fields_ = [("w", c_void_p * NET_LAYERS), ("w_bf16", c_void_p * NET_LAYERS)]
+
+
+class bs_net_grad(ctypes.Structure):
+    _fields_ = [("g", c_void_p * NET_LAYERS)]
 
 
 def _sig(name, *args):
@@ -136,6 +146,13 @@ _sig("bs_batch_render_fwd", _B, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P)
 _sig("bs_batch_render_bwd", _B, _P, _P, _P, _P, _P, _P, _P, POINTER(bs_curves), POINTER(bs_curves_grad), _P)
 _sig("bs_batch_status", _B, POINTER(c_int32), POINTER(c_int64), _P)
 _sig("bs_adam_step", POINTER(bs_adam_group), c_int32, POINTER(bs_adam_cfg), _P, _P)
+lib.bs_net_param_count.argtypes = [c_int32]
+lib.bs_net_param_count.restype = c_int64
+_sig("bs_net_workspace", c_int32, c_int32, POINTER(c_size_t))
+_sig("bs_net_sync_weights", POINTER(bs_net), _P)
+_sig("bs_net_forward", POINTER(bs_net), _P, c_int32, c_int32, _P, c_size_t, _P, _P, _P, _P, _P)
+_sig("bs_net_train_step", POINTER(bs_net), _P, c_int32, c_int32, _P, _P, _P, _P, c_size_t, POINTER(bs_net_grad),
+     _P, _P)
 _sig("bs_debug_retry_limit", c_int64)
 
 
@@ -665,3 +682,48 @@ def adam_step(groups, step: torch.Tensor, beta1=0.9, beta2=0.999, eps=1e-8):
     arr = (bs_adam_group * len(groups))(*(g.c() for g in groups))
     cfg = bs_adam_cfg(beta1, beta2, eps)
     _check("bs_adam_step", lib.bs_adam_step(arr, len(groups), ctypes.byref(cfg), _ptr(step), _stream()))
+
+
+# ---------------------------------------------------------------------------
+# The learned initialiser's network (bs_net_*)
+
+def net_param_count(layer: int) -> int:
+    n = lib.bs_net_param_count(layer)
+    if n < 0:
+        raise ValueError("layer out of range")
+    return int(n)
+
+
+def net_workspace(n: int, side: int) -> int:
+    nb = c_size_t(0)
+    _check("bs_net_workspace", lib.bs_net_workspace(n, side, ctypes.byref(nb)))
+    return int(nb.value)
+
+
+def _net_c(w, w_bf16):
+    return bs_net((c_void_p * NET_LAYERS)(*(t.data_ptr() for t in w)),
+                  (c_void_p * NET_LAYERS)(*(t.data_ptr() for t in w_bf16)))
+
+
+def net_sync_weights(w, w_bf16):
+    """w: 6 float32 master tensors, w_bf16: 6 int16 tensors (bf16 bits)."""
+    net = _net_c(w, w_bf16)
+    _check("bs_net_sync_weights", lib.bs_net_sync_weights(ctypes.byref(net), _stream()))
+
+
+def net_forward(w, w_bf16, patches, ws, head=None, ctrl=None, color=None, opac=None):
+    _want(patches, torch.float32, None, "patches")
+    n, side = int(patches.shape[0]), int(patches.shape[-1])
+    net = _net_c(w, w_bf16)
+    _check("bs_net_forward", lib.bs_net_forward(ctypes.byref(net), _ptr(patches), n, side, _ptr(ws), ws.numel(),
+                                                 _ptr(head), _ptr(ctrl), _ptr(color), _ptr(opac), _stream()))
+
+
+def net_train_step(w, w_bf16, grads, patches, t_ctrl, t_color, t_opac, ws, loss):
+    _want(patches, torch.float32, None, "patches")
+    n, side = int(patches.shape[0]), int(patches.shape[-1])
+    net = _net_c(w, w_bf16)
+    g = bs_net_grad((c_void_p * NET_LAYERS)(*(t.data_ptr() for t in grads)))
+    _check("bs_net_train_step", lib.bs_net_train_step(ctypes.byref(net), _ptr(patches), n, side, _ptr(t_ctrl),
+                                                       _ptr(t_color), _ptr(t_opac), _ptr(ws), ws.numel(),
+                                                       ctypes.byref(g), c_void_p(loss.data_ptr()), _stream()))

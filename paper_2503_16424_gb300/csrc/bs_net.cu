@@ -1,0 +1,602 @@
+// The learned initialiser: a 5-layer convolutional encoder that maps a
+// 256 x 256 RGB patch to 64 closed-curve proposals (one per cell of an 8 x 8
+// grid), trained on curve sets the method itself optimised.
+//
+// Layers: five 4 x 4 convolutions of stride 2 and padding 1 (channels 8 -> 32
+// -> 64 -> 128 -> 256 -> 256; the RGB input is padded to 8 channels), each
+// followed by ReLU, then a 1 x 1 head (256 -> 32, the first 28 used).
+// Activations are NHWC bfloat16, weights bfloat16 copies of float32 master
+// weights, accumulation float32.
+//
+// Every convolution and its two backward products is one implicit GEMM on
+// the tensor cores (mma.sync m16n8k16, bf16 inputs, f32 accumulators):
+//   forward   out[m][co] = sum_k patch[m][k] w[co][k]        (k = tap, ci)
+//   input     din[m][ci] = sum_k dout[m'][co] w[co][tap][ci] (one GEMM per
+//             parity class of the input pixel: a stride-2 4 x 4 kernel reaches
+//             each input pixel through 2 x 2 taps of fixed parity)
+//   weights   dw[co][k]  = sum_m dout[m][co] patch[m][k]      (split over m,
+//             float32 atomics)
+// Operands are gathered into shared memory 8 bf16 (16 bytes) at a time by
+// the op's load functions; a 64 x 64 tile per CTA, four warps of 32 x 32.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "bs_internal.cuh"
+
+namespace bs {
+namespace {
+
+constexpr int kBM = 64, kBN = 64, kBK = 32, kSK = kBK + 8;  // smem row stride (bf16): conflict-free fragments
+constexpr int kGemmThreads = 128;
+
+__device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C[m][n] = sum_k A[m][k] B[n][k] over k in the op's range for blockIdx.z.
+// Op: M, N; k_begin(z), k_end(z) (multiples of 8); load_a(m, k) / load_b(n, k):
+// the 8 bf16 at k..k+7 of row m / n (zero outside); store(m, n, v0, v1):
+// the results at (m, n) and (m, n + 1) (n even).
+template <class Op>
+__global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const Op op) {
+  __shared__ __align__(16) __nv_bfloat16 sA[kBM][kSK];
+  __shared__ __align__(16) __nv_bfloat16 sB[kBN][kSK];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const int kb = op.k_begin(blockIdx.z), ke = op.k_end(blockIdx.z);
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+  // each thread stages two 16-byte vectors of A and two of B per chunk:
+  // vector v = tid + 128 i covers row v / 4, columns 8 (v % 4) .. + 7
+  uint4 ra[2], rb[2];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int v = tid + kGemmThreads * i, row = v >> 2, kk = k0 + 8 * (v & 3);
+      ra[i] = kk < ke ? op.load_a(m0 + row, kk) : zero4();
+      rb[i] = kk < ke ? op.load_b(n0 + row, kk) : zero4();
+    }
+  };
+  if (kb < ke) fetch(kb);
+  for (int k0 = kb; k0 < ke; k0 += kBK) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int v = tid + kGemmThreads * i, row = v >> 2, col = 8 * (v & 3);
+      *reinterpret_cast<uint4 *>(&sA[row][col]) = ra[i];
+      *reinterpret_cast<uint4 *>(&sB[row][col]) = rb[i];
+    }
+    __syncthreads();
+    if (k0 + kBK < ke) fetch(k0 + kBK);  // the next chunk's loads overlap these MMAs
+#pragma unroll
+    for (int ks = 0; ks < kBK; ks += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + g;
+        a[i][0] = *reinterpret_cast<const uint32_t *>(&sA[r][ks + 2 * t]);
+        a[i][1] = *reinterpret_cast<const uint32_t *>(&sA[r + 8][ks + 2 * t]);
+        a[i][2] = *reinterpret_cast<const uint32_t *>(&sA[r][ks + 2 * t + 8]);
+        a[i][3] = *reinterpret_cast<const uint32_t *>(&sA[r + 8][ks + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = wn + 8 * j + g;
+        b[j][0] = *reinterpret_cast<const uint32_t *>(&sB[n][ks + 2 * t]);
+        b[j][1] = *reinterpret_cast<const uint32_t *>(&sB[n][ks + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = m0 + wm + 16 * i + g, n = n0 + wn + 8 * j + 2 * t;
+      op.store(m, n, acc[i][j][0], acc[i][j][1]);
+      op.store(m + 8, n, acc[i][j][2], acc[i][j][3]);
+    }
+}
+
+// ---- the operations ----
+struct Geom {
+  int N, Hi, Wi, Cin, Ho, Wo, Cout, KS, S, P;
+  __host__ __device__ int M() const { return N * Ho * Wo; }
+  __host__ __device__ int K() const { return KS * KS * Cin; }
+};
+
+// The 8 input channels ci..ci+7 of tap (ky, kx) of output pixel m (zero in
+// the padding).  Cin is a multiple of 8.
+__device__ __forceinline__ uint4 patch8(const Geom &g, const __nv_bfloat16 *__restrict__ in, int m, int k) {
+  if (m >= g.M()) return zero4();
+  const int hw = g.Ho * g.Wo, n = m / hw, r = m - n * hw, oy = r / g.Wo, ox = r - oy * g.Wo;
+  const int tap = k / g.Cin, ci = k - tap * g.Cin, ky = tap / g.KS, kx = tap - ky * g.KS;
+  const int iy = g.S * oy + ky - g.P, ix = g.S * ox + kx - g.P;
+  if (iy < 0 || iy >= g.Hi || ix < 0 || ix >= g.Wi) return zero4();
+  return *reinterpret_cast<const uint4 *>(in + (((size_t)n * g.Hi + iy) * g.Wi + ix) * g.Cin + ci);
+}
+
+// Forward: out = act(patch . w^T + b).  Relu: bf16 NHWC output with ReLU;
+// else float32 [M][Cout] (the head).
+template <bool kRelu>
+struct FwdOp {
+  Geom g;
+  const __nv_bfloat16 *in, *w;
+  const float *bias;
+  __nv_bfloat16 *out_bf;
+  float *out_f;
+  __device__ int k_begin(int) const { return 0; }
+  __device__ int k_end(int) const { return g.K(); }
+  __device__ uint4 load_a(int m, int k) const { return patch8(g, in, m, k); }
+  __device__ uint4 load_b(int n, int k) const {
+    return n < g.Cout ? *reinterpret_cast<const uint4 *>(w + (size_t)n * g.K() + k) : zero4();
+  }
+  __device__ void store(int m, int n, float v0, float v1) const {
+    if (m >= g.M() || n >= g.Cout) return;
+    v0 += bias[n];
+    v1 += bias[n + 1];
+    if (kRelu) {
+      *reinterpret_cast<__nv_bfloat162 *>(out_bf + (size_t)m * g.Cout + n) =
+          __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+    } else {
+      out_f[(size_t)m * g.Cout + n] = v0;
+      out_f[(size_t)m * g.Cout + n + 1] = v1;
+    }
+  }
+};
+
+// Input gradient of a 4 x 4, stride-2, padding-1 convolution for the input
+// pixels of parity (qy, qx): iy = 2 hy + qy.  Such a pixel is reached by the
+// taps ky = (1 - qy) + 2a, a = 0, 1, from output row oy = hy + qy - a (and
+// likewise in x), so din = sum over k = (a, b, co) of dout[oy, ox, co] wq[ci][k]
+// with wq the class's weights gathered by net_dgrad_weights_kernel.  The
+// result is multiplied by the ReLU mask of the input activation (the gradient
+// of the previous layer's pre-activation).
+struct DgradOp {
+  Geom g;
+  int qy, qx;
+  const __nv_bfloat16 *dout, *wq, *act_in;
+  __nv_bfloat16 *din;
+  __device__ int Mh() const { return g.N * (g.Hi / 2) * (g.Wi / 2); }
+  __device__ int k_begin(int) const { return 0; }
+  __device__ int k_end(int) const { return 4 * g.Cout; }
+  __device__ void pixel(int m, int &n, int &iy, int &ix) const {
+    const int hh = g.Hi / 2, wh = g.Wi / 2, hw = hh * wh;
+    n = m / hw;
+    const int r = m - n * hw, hy = r / wh, hx = r - hy * wh;
+    iy = 2 * hy + qy;
+    ix = 2 * hx + qx;
+  }
+  __device__ uint4 load_a(int m, int k) const {
+    if (m >= Mh()) return zero4();
+    int n, iy, ix;
+    pixel(m, n, iy, ix);
+    const int tp = k / g.Cout, co = k - tp * g.Cout, a = tp >> 1, b = tp & 1;
+    const int oy = (iy >> 1) + qy - a, ox = (ix >> 1) + qx - b;
+    if (oy < 0 || oy >= g.Ho || ox < 0 || ox >= g.Wo) return zero4();
+    return *reinterpret_cast<const uint4 *>(dout + (((size_t)n * g.Ho + oy) * g.Wo + ox) * g.Cout + co);
+  }
+  __device__ uint4 load_b(int n, int k) const {
+    return n < g.Cin ? *reinterpret_cast<const uint4 *>(wq + (size_t)n * 4 * g.Cout + k) : zero4();
+  }
+  __device__ void store(int m, int ci, float v0, float v1) const {
+    if (m >= Mh() || ci >= g.Cin) return;
+    int n, iy, ix;
+    pixel(m, n, iy, ix);
+    const size_t o = (((size_t)n * g.Hi + iy) * g.Wi + ix) * g.Cin + ci;
+    const __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(act_in + o);
+    const float m0 = __bfloat162float(x.x) > 0.f ? 1.f : 0.f, m1 = __bfloat162float(x.y) > 0.f ? 1.f : 0.f;
+    *reinterpret_cast<__nv_bfloat162 *>(din + o) = __floats2bfloat162_rn(v0 * m0, v1 * m1);
+  }
+};
+
+// Input gradient of the 1 x 1 head: din[m][ci] = sum_co dout[m][co] w[co][ci],
+// times the ReLU mask of the head's input.  wt = w transposed, [Cin][Cout].
+struct HeadDgradOp {
+  int M, Cin, Cout;
+  const __nv_bfloat16 *dout, *wt, *act_in;
+  __nv_bfloat16 *din;
+  __device__ int k_begin(int) const { return 0; }
+  __device__ int k_end(int) const { return Cout; }
+  __device__ uint4 load_a(int m, int k) const {
+    return m < M ? *reinterpret_cast<const uint4 *>(dout + (size_t)m * Cout + k) : zero4();
+  }
+  __device__ uint4 load_b(int n, int k) const {
+    return n < Cin ? *reinterpret_cast<const uint4 *>(wt + (size_t)n * Cout + k) : zero4();
+  }
+  __device__ void store(int m, int ci, float v0, float v1) const {
+    if (m >= M || ci >= Cin) return;
+    const size_t o = (size_t)m * Cin + ci;
+    const __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(act_in + o);
+    const float m0 = __bfloat162float(x.x) > 0.f ? 1.f : 0.f, m1 = __bfloat162float(x.y) > 0.f ? 1.f : 0.f;
+    *reinterpret_cast<__nv_bfloat162 *>(din + o) = __floats2bfloat162_rn(v0 * m0, v1 * m1);
+  }
+};
+
+// Weight gradient: dw[co][k] += sum over output pixels m of this split of
+// dout[m][co] patch[m][k]; K of the GEMM = the pixels, 8 at a time.
+struct WgradOp {
+  Geom g;
+  int chunk;  // pixels per split, a multiple of kBK
+  const __nv_bfloat16 *dout, *in;
+  float *dw;
+  __device__ int k_begin(int z) const { return z * chunk; }
+  __device__ int k_end(int z) const { return min(g.M(), (z + 1) * chunk); }
+  __device__ uint4 load_a(int co, int m) const {  // dout[m..m+7][co]
+    if (co >= g.Cout) return zero4();
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      v[i] = m + i < g.M() ? dout[(size_t)(m + i) * g.Cout + co] : __float2bfloat16(0.f);
+    return *reinterpret_cast<const uint4 *>(v);
+  }
+  __device__ uint4 load_b(int kk, int m) const {  // patch[m..m+7][kk]
+    if (kk >= g.K()) return zero4();
+    const int tap = kk / g.Cin, ci = kk - tap * g.Cin, ky = tap / g.KS, kx = tap - ky * g.KS;
+    const int hw = g.Ho * g.Wo;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      v[i] = __float2bfloat16(0.f);
+      const int mm = m + i;
+      if (mm < g.M()) {
+        const int n = mm / hw, r = mm - n * hw, oy = r / g.Wo, ox = r - oy * g.Wo;
+        const int iy = g.S * oy + ky - g.P, ix = g.S * ox + kx - g.P;
+        if (iy >= 0 && iy < g.Hi && ix >= 0 && ix < g.Wi)
+          v[i] = in[(((size_t)n * g.Hi + iy) * g.Wi + ix) * g.Cin + ci];
+      }
+    }
+    return *reinterpret_cast<const uint4 *>(v);
+  }
+  __device__ void store(int co, int kk, float v0, float v1) const {
+    if (co >= g.Cout || kk >= g.K()) return;
+    if (v0 != 0.f) atomicAdd(dw + (size_t)co * g.K() + kk, v0);
+    if (v1 != 0.f) atomicAdd(dw + (size_t)co * g.K() + kk + 1, v1);
+  }
+};
+
+template <class Op>
+bs_status run_gemm(const Op &op, int M, int N, int splits, cudaStream_t s) {
+  const dim3 grid((unsigned)div_up(M, kBM), (unsigned)div_up(N, kBN), (unsigned)splits);
+  gemm_kernel<Op><<<grid, kGemmThreads, 0, s>>>(op);
+  BS_LAUNCHED("gemm_kernel");
+  return BS_OK;
+}
+
+// ---- element-wise pieces ----
+// Planar float32 patches [N][3][H][W] -> NHWC bf16 [N][H][W][8] (channels
+// 3..7 zero).
+__global__ void net_input_kernel(const float *__restrict__ x, int N, int H, int W, __nv_bfloat16 *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t plane = (int64_t)H * W;
+  if (i >= N * plane) return;
+  const int64_t n = i / plane, p = i - n * plane;
+  const float *src = x + n * 3 * plane + p;
+  __align__(16) __nv_bfloat16 v[8];
+  v[0] = __float2bfloat16(src[0]);
+  v[1] = __float2bfloat16(src[plane]);
+  v[2] = __float2bfloat16(src[2 * plane]);
+#pragma unroll
+  for (int c = 3; c < 8; ++c) v[c] = __float2bfloat16(0.f);
+  *reinterpret_cast<uint4 *>(out + i * 8) = *reinterpret_cast<const uint4 *>(v);
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ x, int64_t n, __nv_bfloat16 *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __float2bfloat16(x[i]);
+}
+
+// wq[q][ci][(a, b, co)] = w[co][ky][kx][ci], ky = (1 - qy) + 2a, kx = (1 - qx) + 2b
+// for the four parity classes q = 2 qy + qx of a 4 x 4 kernel.
+__global__ void net_dgrad_weights_kernel(const float *__restrict__ w, int Cin, int Cout,
+                                         __nv_bfloat16 *__restrict__ wq) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)Cin * 4 * Cout;
+  if (i >= 4 * per) return;
+  const int q = (int)(i / per);
+  const int64_t r = i - q * per;
+  const int ci = (int)(r / (4 * Cout)), k = (int)(r - (int64_t)ci * 4 * Cout);
+  const int tp = k / Cout, co = k - tp * Cout, a = tp >> 1, b = tp & 1;
+  const int qy = q >> 1, qx = q & 1;
+  const int ky = (1 - qy) + 2 * a, kx = (1 - qx) + 2 * b;
+  wq[i] = __float2bfloat16(w[((size_t)co * 16 + ky * 4 + kx) * Cin + ci]);
+}
+
+// wt[ci][co] = w[co][ci] (the head), bf16.
+__global__ void net_transpose_kernel(const float *__restrict__ w, int Cin, int Cout, __nv_bfloat16 *__restrict__ wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Cin * Cout) return;
+  const int ci = i / Cout, co = i - ci * Cout;
+  wt[i] = __float2bfloat16(w[(size_t)co * Cin + ci]);
+}
+
+// db[co] += sum over m of dout[m][co] (bf16 dout).
+__global__ void net_bias_grad_kernel(const __nv_bfloat16 *__restrict__ dout, int M, int C, float *__restrict__ db) {
+  const int co = blockIdx.y * blockDim.x + threadIdx.x;
+  if (co >= C) return;
+  float acc = 0.f;
+  for (int m = blockIdx.x; m < M; m += gridDim.x) acc += __bfloat162float(dout[(size_t)m * C + co]);
+  atomicAdd(db + co, acc);
+}
+
+// The head's 28 outputs per cell o -> one closed curve (Section 3.2: 12
+// control points, colour, opacity) in the patch's pixel coordinates:
+// P_j = cell centre + reach tanh(o_{2j..2j+1}), colour = sigmoid(o_24..26),
+// opacity = sigmoid(o_27).  Cells are row-major on the grid x grid lattice
+// of cell side `cell`.  With targets: the loss
+//   L = mean over cells of [ sum_j |P_j - P*_j|^2 / reach^2 + |c - c*|^2 + (a - a*)^2 ]
+// (added to *loss, one double atomic per thread with cells) and dL/do (float
+// [cells][32], zero in 28..31) as bf16 for the head's backward and float.
+constexpr int kHeadOut = 32, kCurveOut = 28;
+__global__ void net_head_kernel(const float *__restrict__ o, int n_cells, int grid, float cell, float reach,
+                                float *__restrict__ ctrl, float *__restrict__ color, float *__restrict__ opac,
+                                const float *__restrict__ t_ctrl, const float *__restrict__ t_color,
+                                const float *__restrict__ t_opac, double *__restrict__ loss,
+                                __nv_bfloat16 *__restrict__ dout) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const float *oc = o + (size_t)c * kHeadOut;
+  const int cc = c % (grid * grid), gy = cc / grid, gx = cc - gy * grid;
+  const float cx = (gx + 0.5f) * cell, cy = (gy + 0.5f) * cell;
+  float d[kHeadOut];
+  double l = 0.0;
+  const float inv = 1.f / (reach * reach), scale = 1.f / (float)n_cells;
+  for (int j = 0; j < 12; ++j) {
+    const float tx = tanhf(oc[2 * j]), ty = tanhf(oc[2 * j + 1]);
+    const float px = cx + reach * tx, py = cy + reach * ty;
+    if (ctrl) {
+      ctrl[(size_t)c * 24 + 2 * j] = px;
+      ctrl[(size_t)c * 24 + 2 * j + 1] = py;
+    }
+    if (t_ctrl) {
+      const float ex = px - t_ctrl[(size_t)c * 24 + 2 * j], ey = py - t_ctrl[(size_t)c * 24 + 2 * j + 1];
+      l += (double)(ex * ex + ey * ey) * inv;
+      d[2 * j] = scale * 2.f * ex * inv * reach * (1.f - tx * tx);
+      d[2 * j + 1] = scale * 2.f * ey * inv * reach * (1.f - ty * ty);
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    const float s = 1.f / (1.f + __expf(-oc[24 + k]));
+    if (k < 3 && color) color[(size_t)c * 3 + k] = s;
+    if (k == 3 && opac) opac[c] = s;
+    if (t_ctrl) {
+      const float e = s - (k < 3 ? t_color[(size_t)c * 3 + k] : t_opac[c]);
+      l += (double)(e * e);
+      d[24 + k] = scale * 2.f * e * s * (1.f - s);
+    }
+  }
+  if (t_ctrl) {
+    for (int k = kCurveOut; k < kHeadOut; ++k) d[k] = 0.f;
+    for (int k = 0; k < kHeadOut; ++k) dout[(size_t)c * kHeadOut + k] = __float2bfloat16(d[k]);
+    atomicAdd(loss, l / (double)n_cells);
+  }
+}
+
+}  // namespace
+
+// ---- host side ----
+// The layer geometry of a batch of n patches of side `side` (a multiple of
+// 32): layer l in 0..4 the 4 x 4 stride-2 convolutions, 5 the head.
+static const int kNetCh[6] = {8, 32, 64, 128, 256, 256};
+
+Geom net_layer(int l, int n, int side) {
+  Geom g{};
+  g.N = n;
+  if (l < 5) {
+    g.Hi = g.Wi = side >> l;
+    g.Ho = g.Wo = side >> (l + 1);
+    g.Cin = kNetCh[l];
+    g.Cout = kNetCh[l + 1];
+    g.KS = 4;
+    g.S = 2;
+    g.P = 1;
+  } else {
+    g.Hi = g.Wi = g.Ho = g.Wo = side >> 5;
+    g.Cin = 256;
+    g.Cout = kHeadOut;
+    g.KS = 1;
+    g.S = 1;
+    g.P = 0;
+  }
+  return g;
+}
+
+size_t net_param_count(int l) {
+  const Geom g = net_layer(l, 1, 256);
+  return (size_t)g.Cout * g.K() + g.Cout;  // weights then bias
+}
+
+}  // namespace bs
+
+using namespace bs;
+
+namespace {
+
+bs_status net_invalid(const char *msg) {
+  set_error("%s", msg);
+  return BS_ERR_INVALID_ARG;
+}
+
+bs_status check_net(const bs_net *net, int32_t n, int32_t side) {
+  if (!net) return net_invalid("net is NULL");
+  if (n < 1 || side < 32 || side % 32 || side > 1024) return net_invalid("n >= 1 patches of side 32..1024, a multiple of 32");
+  for (int l = 0; l < BS_NET_LAYERS; ++l)
+    if (!net->w[l] || !net->w_bf16[l]) return net_invalid("net weights must be non-NULL");
+  return BS_OK;
+}
+
+// Activation buffers inside the workspace: x0 (input, 8 channels) and the
+// outputs of layers 0..4, NHWC bf16; the head output (float [cells][32]).
+struct NetWs {
+  __nv_bfloat16 *act[6];
+  float *head;
+  __nv_bfloat16 *dact[6];  // gradients of the activations (same shapes)
+  __nv_bfloat16 *dhead;
+  __nv_bfloat16 *wq;       // dgrad weights of the largest layer (4 classes)
+  size_t bytes;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+NetWs carve_net(void *base, int n, int side) {
+  NetWs w{};
+  char *p = static_cast<char *>(base);
+  size_t o = 0;
+  for (int l = 0; l <= 5; ++l) {
+    const int s = side >> l;
+    const size_t e = (size_t)n * s * s * kNetCh[l];
+    w.act[l] = base ? reinterpret_cast<__nv_bfloat16 *>(p + o) : nullptr;
+    o = align256(o + 2 * e);
+    w.dact[l] = base ? reinterpret_cast<__nv_bfloat16 *>(p + o) : nullptr;
+    o = align256(o + 2 * e);
+  }
+  const size_t cells = (size_t)n * (side >> 5) * (side >> 5);
+  w.head = base ? reinterpret_cast<float *>(p + o) : nullptr;
+  o = align256(o + 4 * cells * kHeadOut);
+  w.dhead = base ? reinterpret_cast<__nv_bfloat16 *>(p + o) : nullptr;
+  o = align256(o + 2 * cells * kHeadOut);
+  w.wq = base ? reinterpret_cast<__nv_bfloat16 *>(p + o) : nullptr;
+  o = align256(o + 2 * (size_t)4 * 256 * 4 * 256);
+  w.bytes = o;
+  return w;
+}
+
+const __nv_bfloat16 *wbf(const bs_net *net, int l) { return reinterpret_cast<const __nv_bfloat16 *>(net->w_bf16[l]); }
+
+bs_status net_forward(const bs_net *net, const float *patches, int n, int side, const NetWs &ws, cudaStream_t s) {
+  const int64_t px = (int64_t)n * side * side;
+  net_input_kernel<<<(unsigned)div_up64(px, 256), 256, 0, s>>>(patches, n, side, side, ws.act[0]);
+  BS_LAUNCHED("net_input_kernel");
+  for (int l = 0; l < 5; ++l) {
+    const Geom g = net_layer(l, n, side);
+    const FwdOp<true> op{g, ws.act[l], wbf(net, l), net->w[l] + (size_t)g.Cout * g.K(), ws.act[l + 1], nullptr};
+    BS_TRY(run_gemm(op, g.M(), g.Cout, 1, s));
+  }
+  const Geom g = net_layer(5, n, side);
+  const FwdOp<false> op{g, ws.act[5], wbf(net, 5), net->w[5] + (size_t)g.Cout * g.K(), nullptr, ws.head};
+  return run_gemm(op, g.M(), g.Cout, 1, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+bs_status bs_net_workspace(int32_t n, int32_t side, size_t *bytes) {
+  if (!bytes) return net_invalid("bytes is NULL");
+  if (n < 1 || side < 32 || side % 32 || side > 1024) return net_invalid("n >= 1 patches of side 32..1024, a multiple of 32");
+  *bytes = carve_net(nullptr, n, side).bytes;
+  return BS_OK;
+}
+
+int64_t bs_net_param_count(int32_t layer) {
+  if (layer < 0 || layer >= BS_NET_LAYERS) return -1;
+  return (int64_t)net_param_count(layer);
+}
+
+bs_status bs_net_sync_weights(const bs_net *net, bs_stream stream) {
+  if (!net) return net_invalid("net is NULL");
+  for (int l = 0; l < BS_NET_LAYERS; ++l)
+    if (!net->w[l] || !net->w_bf16[l]) return net_invalid("net weights must be non-NULL");
+  BS_TRY(check_device());
+  const cudaStream_t s = (cudaStream_t)stream;
+  for (int l = 0; l < BS_NET_LAYERS; ++l) {
+    const Geom g = net_layer(l, 1, 256);
+    const int64_t nw = (int64_t)g.Cout * g.K();
+    to_bf16_kernel<<<(unsigned)div_up64(nw, 256), 256, 0, s>>>(net->w[l], nw,
+                                                              reinterpret_cast<__nv_bfloat16 *>(net->w_bf16[l]));
+    BS_LAUNCHED("to_bf16_kernel");
+  }
+  return BS_OK;
+}
+
+bs_status bs_net_forward(const bs_net *net, const float *patches, int32_t n, int32_t side, void *ws, size_t ws_bytes,
+                         float *head_out, float *ctrl, float *color, float *opac, bs_stream stream) {
+  BS_TRY(check_net(net, n, side));
+  const NetWs w = carve_net(ws, n, side);
+  if (!ws || ws_bytes < w.bytes || ((uintptr_t)ws & 255u)) return net_invalid("workspace too small or not 256-byte aligned");
+  if (!patches) return net_invalid("patches is NULL");
+  BS_TRY(check_device());
+  const cudaStream_t s = (cudaStream_t)stream;
+  BS_TRY(net_forward(net, patches, n, side, w, s));
+  const int grid = side >> 5, cells = n * grid * grid;
+  net_head_kernel<<<div_up(cells, 128), 128, 0, s>>>(w.head, cells, grid, 32.f, BS_NET_REACH, ctrl, color, opac,
+                                                     nullptr, nullptr, nullptr, nullptr, nullptr);
+  BS_LAUNCHED("net_head_kernel");
+  if (head_out) BS_CUDA(cudaMemcpyAsync(head_out, w.head, sizeof(float) * cells * kHeadOut, cudaMemcpyDeviceToDevice, s));
+  return BS_OK;
+}
+
+bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, int32_t side, const float *t_ctrl,
+                            const float *t_color, const float *t_opac, void *ws, size_t ws_bytes, const bs_net_grad *grad,
+                            double *loss_out, bs_stream stream) {
+  BS_TRY(check_net(net, n, side));
+  if (!grad || !t_ctrl || !t_color || !t_opac || !loss_out) return net_invalid("NULL target, gradient or loss");
+  for (int l = 0; l < BS_NET_LAYERS; ++l)
+    if (!grad->g[l]) return net_invalid("gradient buffers must be non-NULL");
+  const NetWs w = carve_net(ws, n, side);
+  if (!ws || ws_bytes < w.bytes || ((uintptr_t)ws & 255u)) return net_invalid("workspace too small or not 256-byte aligned");
+  if (!patches) return net_invalid("patches is NULL");
+  BS_TRY(check_device());
+  const cudaStream_t s = (cudaStream_t)stream;
+  BS_TRY(net_forward(net, patches, n, side, w, s));
+  const int grid = side >> 5, cells = n * grid * grid;
+  BS_CUDA(cudaMemsetAsync(loss_out, 0, sizeof(double), s));
+  net_head_kernel<<<div_up(cells, 128), 128, 0, s>>>(w.head, cells, grid, 32.f, BS_NET_REACH, nullptr, nullptr,
+                                                     nullptr, t_ctrl, t_color, t_opac, loss_out, w.dhead);
+  BS_LAUNCHED("net_head_kernel");
+  for (int l = 0; l < BS_NET_LAYERS; ++l)
+    BS_CUDA(cudaMemsetAsync(grad->g[l], 0, sizeof(float) * net_param_count(l), s));
+  // head: weights, bias, input gradient
+  {
+    const Geom g = net_layer(5, n, side);
+    const int chunk = std::max(kBK, (int)div_up64(div_up64(g.M(), 152), kBK) * kBK);
+    const WgradOp op{g, chunk, w.dhead, w.act[5], grad->g[5]};
+    BS_TRY(run_gemm(op, g.Cout, g.K(), div_up(g.M(), chunk), s));
+    net_bias_grad_kernel<<<dim3(128, div_up(g.Cout, 128)), 128, 0, s>>>(w.dhead, g.M(), g.Cout,
+                                                                        grad->g[5] + (size_t)g.Cout * g.K());
+    BS_LAUNCHED("net_bias_grad_kernel");
+    net_transpose_kernel<<<div_up(g.Cin * g.Cout, 256), 256, 0, s>>>(net->w[5], g.Cin, g.Cout, w.wq);
+    BS_LAUNCHED("net_transpose_kernel");
+    const HeadDgradOp dop{g.M(), g.Cin, g.Cout, w.dhead, w.wq, w.act[5], w.dact[5]};
+    BS_TRY(run_gemm(dop, g.M(), g.Cin, 1, s));
+  }
+  for (int l = 4; l >= 0; --l) {
+    const Geom g = net_layer(l, n, side);
+    const __nv_bfloat16 *dout = w.dact[l + 1];
+    const int chunk = std::max(kBK, (int)div_up64(div_up64(g.M(), 304), kBK) * kBK);
+    const WgradOp op{g, chunk, dout, w.act[l], grad->g[l]};
+    BS_TRY(run_gemm(op, g.Cout, g.K(), div_up(g.M(), chunk), s));
+    net_bias_grad_kernel<<<dim3(256, div_up(g.Cout, 128)), 128, 0, s>>>(dout, g.M(), g.Cout,
+                                                                        grad->g[l] + (size_t)g.Cout * g.K());
+    BS_LAUNCHED("net_bias_grad_kernel");
+    if (l == 0) break;  // the input image needs no gradient
+    const int64_t nq = 4ll * g.Cin * 4 * g.Cout;
+    net_dgrad_weights_kernel<<<(unsigned)div_up64(nq, 256), 256, 0, s>>>(net->w[l], g.Cin, g.Cout, w.wq);
+    BS_LAUNCHED("net_dgrad_weights_kernel");
+    for (int q = 0; q < 4; ++q) {
+      const DgradOp dop{g, q >> 1, q & 1, dout, w.wq + (size_t)q * g.Cin * 4 * g.Cout, w.act[l], w.dact[l]};
+      BS_TRY(run_gemm(dop, g.N * (g.Hi / 2) * (g.Wi / 2), g.Cin, 1, s));
+    }
+  }
+  return BS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,250 @@
+"""Learned initialisation of curves: a convolutional proposal network
+(bs_net_* calls) trained on curve sets the method itself optimised.
+
+Pairs.  A pair is a procedural 256 x 256 patch and the 64 closed curves the
+method reaches on it from the circular initialisation of Section 4.1 (one
+circle of radius 10 px per 32 x 32 cell, the cell's mean target colour,
+opacity 0.8), after `steps` Adam steps of the batched path (64 patches per
+batch, one CUDA-graph replay per step).  Curve i stays the curve of cell i,
+which gives the network a fixed slot per cell.
+
+Network.  bs.h describes it: five stride-2 4 x 4 convolutions and a 1 x 1
+head, bf16 tensor-core GEMMs with float32 accumulation; the head's bias
+starts at the circular initialisation, so an untrained network proposes
+exactly the baseline circles (with colour 0.5).  Training minimises the
+mean squared distance to the optimised curves (control points in units of
+the 24 px reach) with Adam (bs_adam_step) on float32 master weights.
+
+Use.  A large target is cut into 256 x 256 patches; each patch's 64
+proposals, shifted to the patch's place, initialise the method on the whole
+image.  Without the network the same image starts from the circles.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import bs, synth
+from .batch import AdamCfg, BatchOptimizer, BatchRasterizer, CurveAdam
+
+SIDE = 256
+CELL = 32
+GRID = SIDE // CELL
+CELLS = GRID * GRID
+RADIUS = 10.0
+OPACITY = 0.8
+# pair generation: a faster control-point step than the paper's 15k-step
+# schedule, so that a few hundred steps move the curves (same for both arms
+# of the evaluation)
+PAIR_ADAM = AdamCfg(lr_ctrl=2e-3, lr_color=0.01, lr_opac=0.025)
+KERNEL_CH = (8, 32, 64, 128, 256, 256)
+
+
+def circle_points(cx, cy, r):
+    """12 control points on the circle of radius r around (cx, cy) at angles
+    2 pi j / 12: a closed curve of four cubic segments (P12 = P0)."""
+    a = 2.0 * np.pi * np.arange(12) / 12.0
+    return np.stack([cx[..., None] + r * np.cos(a), cy[..., None] + r * np.sin(a)], -1)
+
+
+def circle_init(n_patches: int, side: int = SIDE, target: np.ndarray = None):
+    """Closed-curve arrays of the circular initialisation for n patches of
+    side `side` (curves patch by patch, cells row-major), in patch pixels;
+    colours the cells' mean target colours (0.5 without a target)."""
+    g = side // CELL
+    gy, gx = np.meshgrid(np.arange(g), np.arange(g), indexing="ij")
+    cx = np.broadcast_to((gx.reshape(-1) + 0.5) * CELL, (n_patches, g * g))
+    cy = np.broadcast_to((gy.reshape(-1) + 0.5) * CELL, (n_patches, g * g))
+    ctrl = circle_points(cx, cy, RADIUS).reshape(n_patches * g * g, 12, 2).astype(np.float32)
+    if target is None:
+        color = np.full((n_patches * g * g, 3), 0.5, np.float32)
+    else:
+        t = np.asarray(target, dtype=np.float64).reshape(n_patches, 3, g, CELL, g, CELL)
+        color = np.clip(t.mean(axis=(3, 5)), 0.0, 1.0).transpose(0, 2, 3, 1).reshape(-1, 3).astype(np.float32)
+    opac = np.full(n_patches * g * g, OPACITY, np.float32)
+    return ctrl, color, opac
+
+
+def _closed_set(ctrl, color, opac, device):
+    z2, z1 = np.zeros((0, 10, 2), np.float32), np.zeros((0,), np.float32)
+    return bs.CurveSet.from_arrays(dict(open_ctrl=z2, open_width=z1, open_color=np.zeros((0, 3), np.float32),
+                                        open_opac=np.zeros((0, 3), np.float32), closed_ctrl=ctrl,
+                                        closed_color=color, closed_opac=opac), device=device)
+
+
+def make_pairs(n: int, seed: int, steps: int = 200, n_shapes: int = 6, device="cuda", batch: int = 64,
+               sample=(4, 8)):
+    """n (patch, optimised curves) pairs.  Returns device tensors patches
+    [n, 3, 256, 256], ctrl [n, 64, 12, 2], color [n, 64, 3], opac [n, 64];
+    control points clamped to the network's reach around their cell."""
+    rows, kc = sample
+    out = {"patches": [], "ctrl": [], "color": [], "opac": []}
+    for b0 in range(0, n, batch):
+        m = min(batch, n - b0)
+        tg = np.stack([synth.procedural_target(seed * 100003 + b0 + i, SIDE, SIDE, n_shapes) for i in range(m)])
+        ctrl, color, opac = circle_init(m, SIDE, tg)
+        curves = _closed_set(ctrl, color, opac, device)
+        images = [bs.BatchImage(SIDE, SIDE, 0, CELLS, bs.SampleCfg(g_open=2, rows_closed=rows, k_closed=kc))
+                  for _ in range(m)]
+        target = torch.as_tensor(tg.reshape(-1), device=device)
+        r = BatchRasterizer(images, pair_capacity=1 << 22, device=device)
+        opt = BatchOptimizer(r, curves, target, cfg=PAIR_ADAM, graph=True, check_every=0)
+        for _ in range(steps):
+            opt.step()
+        out["patches"].append(torch.as_tensor(tg, device=device))
+        out["ctrl"].append(curves.closed_ctrl.view(m, CELLS, 12, 2).clone())
+        out["color"].append(curves.closed_color.view(m, CELLS, 3).clone())
+        out["opac"].append(curves.closed_opac.view(m, CELLS).clone())
+    res = {k: torch.cat(v, 0) for k, v in out.items()}
+    g = torch.arange(GRID, device=device, dtype=torch.float32)
+    cy, cx = torch.meshgrid((g + 0.5) * CELL, (g + 0.5) * CELL, indexing="ij")
+    centre = torch.stack([cx.reshape(-1), cy.reshape(-1)], -1)[None, :, None, :]
+    lim = 0.98 * bs.NET_REACH
+    res["ctrl"] = (centre + (res["ctrl"] - centre).clamp(-lim, lim)).contiguous()
+    return res
+
+
+class InitNet:
+    """The proposal network: float32 master weights, their bf16 copies,
+    gradients and Adam state, on the device."""
+
+    def __init__(self, device="cuda", seed: int = 0, lr: float = 1e-3):
+        self.device = device
+        rng = np.random.default_rng(seed)
+        self.w, self.w_bf16, self.g = [], [], []
+        for l in range(bs.NET_LAYERS):
+            n = bs.net_param_count(l)
+            if l < 5:
+                cin, cout, ks = KERNEL_CH[l], KERNEL_CH[l + 1], 4
+                fan_in = ks * ks * (3 if l == 0 else cin)
+            else:
+                cin, cout, ks, fan_in = 256, 32, 1, 256
+            nw = cout * ks * ks * cin
+            bound = math.sqrt(6.0 / fan_in) * (0.1 if l == 5 else 1.0)
+            w = np.zeros(n, np.float32)
+            w[:nw] = rng.uniform(-bound, bound, nw)
+            if l == 0:   # the padding channels 3..7 of the input carry nothing
+                w[:nw].reshape(cout, ks, ks, cin)[..., 3:] = 0.0
+            if l == 5:   # head bias: the circular initialisation (colour 0.5)
+                a = 2.0 * np.pi * np.arange(12) / 12.0
+                off = RADIUS / bs.NET_REACH
+                b = w[nw:]
+                b[0:24:2] = np.arctanh(off * np.cos(a))
+                b[1:24:2] = np.arctanh(off * np.sin(a))
+                b[27] = math.log(OPACITY / (1.0 - OPACITY))
+            self.w.append(torch.as_tensor(w, device=device))
+            self.w_bf16.append(torch.empty(nw, dtype=torch.int16, device=device))
+            self.g.append(torch.zeros(n, dtype=torch.float32, device=device))
+        self.m = [torch.zeros_like(x) for x in self.w]
+        self.v = [torch.zeros_like(x) for x in self.w]
+        self.t = torch.zeros(1, dtype=torch.int32, device=device)
+        self.groups = [bs.AdamGroup(p, g, m, v, lr) for p, g, m, v in zip(self.w, self.g, self.m, self.v)]
+        self.loss = torch.zeros((), dtype=torch.float64, device=device)
+        self._ws = {}
+        bs.net_sync_weights(self.w, self.w_bf16)
+
+    def ws(self, n: int, side: int = SIDE):
+        key = (n, side)
+        if key not in self._ws:
+            self._ws[key] = torch.empty(bs.net_workspace(n, side), dtype=torch.uint8, device=self.device)
+        return self._ws[key]
+
+    def propose(self, patches: torch.Tensor):
+        """ctrl [n, cells, 12, 2] (patch pixels), color [n, cells, 3], opac [n, cells]."""
+        n, side = int(patches.shape[0]), int(patches.shape[-1])
+        cells = (side // CELL) ** 2
+        ctrl = torch.empty(n, cells, 12, 2, device=self.device)
+        color = torch.empty(n, cells, 3, device=self.device)
+        opac = torch.empty(n, cells, device=self.device)
+        bs.net_forward(self.w, self.w_bf16, patches.contiguous(), self.ws(n, side), ctrl=ctrl, color=color, opac=opac)
+        return ctrl, color, opac
+
+    def train_step(self, patches, t_ctrl, t_color, t_opac):
+        """Forward, backward, Adam, bf16 copies; the loss (device double)."""
+        n, side = int(patches.shape[0]), int(patches.shape[-1])
+        bs.net_train_step(self.w, self.w_bf16, self.g, patches, t_ctrl, t_color, t_opac, self.ws(n, side), self.loss)
+        bs.adam_step(self.groups, self.t)
+        bs.net_sync_weights(self.w, self.w_bf16)
+        return self.loss
+
+
+def train(net: InitNet, data: dict, steps: int, batch: int = 64, seed: int = 0):
+    """steps minibatch steps over the pairs (sampled with replacement);
+    returns the loss of every step (synchronises once at the end)."""
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    n = int(data["patches"].shape[0])
+    losses = torch.empty(steps, dtype=torch.float64, device=net.device)
+    for i in range(steps):
+        idx = torch.randint(0, n, (min(batch, n),), generator=gen).to(net.device)
+        p = data["patches"].index_select(0, idx).contiguous()
+        c = data["ctrl"].index_select(0, idx).contiguous()
+        col = data["color"].index_select(0, idx).contiguous()
+        o = data["opac"].index_select(0, idx).contiguous()
+        losses[i] = net.train_step(p, c, col, o)
+    return losses.cpu().numpy()
+
+
+def image_patches(target: torch.Tensor):
+    """[3, H, W] (H, W multiples of 256) -> patches [n, 3, 256, 256] in
+    row-major patch order."""
+    _, H, W = target.shape
+    p = target.view(3, H // SIDE, SIDE, W // SIDE, SIDE).permute(1, 3, 0, 2, 4)
+    return p.reshape(-1, 3, SIDE, SIDE).contiguous()
+
+
+def to_image(ctrl, color, opac, H: int, W: int):
+    """Patch proposals [n, cells, ...] -> closed curves of the whole image
+    (patch origins added)."""
+    py, px = torch.meshgrid(torch.arange(H // SIDE, device=ctrl.device), torch.arange(W // SIDE, device=ctrl.device),
+                            indexing="ij")
+    origin = torch.stack([px.reshape(-1), py.reshape(-1)], -1).float() * SIDE
+    c = ctrl + origin[:, None, None, :]
+    return c.reshape(-1, 12, 2), color.reshape(-1, 3), opac.reshape(-1)
+
+
+def initial_curves(target: torch.Tensor, net: InitNet = None):
+    """Closed curves initialising the method on target [3, H, W]: the
+    network's proposals, or (net None) the circular initialisation."""
+    _, H, W = target.shape
+    if net is None:
+        n = (H // SIDE) * (W // SIDE)
+        tg = image_patches(target).cpu().numpy()
+        ctrl, color, opac = circle_init(n, SIDE, tg)
+        c, col, o = to_image(torch.as_tensor(ctrl, device=target.device).view(n, CELLS, 12, 2),
+                             torch.as_tensor(color, device=target.device).view(n, CELLS, 3),
+                             torch.as_tensor(opac, device=target.device).view(n, CELLS), H, W)
+    else:
+        c, col, o = to_image(*net.propose(image_patches(target)), H, W)
+    return _closed_set(c.cpu().numpy(), col.cpu().numpy(), o.cpu().numpy(), target.device)
+
+
+def optimise(target: torch.Tensor, curves: bs.CurveSet, steps: int, sample=(4, 8), every: int = 10,
+             cfg: AdamCfg = PAIR_ADAM):
+    """The method on one image from `curves` (in place): PSNR every `every`
+    steps (index 0 = the initial curves) and the ms per step."""
+    from .raster import Rasterizer
+    _, H, W = target.shape
+    rows, kc = sample
+    r = Rasterizer(bs.Canvas(W, H, 16), bs.SampleCfg(g_open=2, rows_closed=rows, k_closed=kc), 0, curves.n_closed,
+                   device=target.device, pair_capacity=1 << 22)
+    grad = curves.zeros_like()
+    adam = CurveAdam(curves, grad, [bs.BatchImage(W, H, 0, curves.n_closed, r.cfg)], cfg, target.device)
+    psnr = []
+    t_ms = 0.0
+    for i in range(steps + 1):
+        if i % every == 0 or i == steps:
+            img = r.forward(curves)
+            psnr.append(float(-10.0 * torch.log10(((img - target).double() ** 2).mean())))
+        if i == steps:
+            break
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r.step(curves, target, grad)
+        adam.step()
+        b.record()
+        b.synchronize()
+        t_ms += a.elapsed_time(b)
+    return psnr, t_ms / max(1, steps)
