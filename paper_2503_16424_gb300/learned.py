@@ -248,3 +248,97 @@ def optimise(target: torch.Tensor, curves: bs.CurveSet, steps: int, sample=(4, 8
         b.synchronize()
         t_ms += a.elapsed_time(b)
     return psnr, t_ms / max(1, steps)
+
+
+def train_flops(n: int, side: int = SIDE) -> float:
+    """Multiply-adds x 2 of one training step on n patches: per convolution
+    the forward and the weight gradient each 2 M K Cout, the input gradient
+    the same except for the first layer."""
+    tot = 0.0
+    for l in range(6):
+        if l < 5:
+            ho = side >> (l + 1)
+            m, k, co = n * ho * ho, 16 * KERNEL_CH[l], KERNEL_CH[l + 1]
+        else:
+            m, k, co = n * (side // CELL) ** 2, 256, 32
+        f = 2.0 * m * k * co
+        tot += f * (2 if l == 0 else 3)
+    return tot
+
+
+def main(argv=None):
+    """Pairs -> training -> evaluation on 2048 x 2048 targets (64 patches
+    each); prints one JSON line."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--pairs", type=int, default=20000)
+    ap.add_argument("--pair-steps", type=int, default=150)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--targets", type=int, default=2)
+    ap.add_argument("--side", type=int, default=2048)
+    ap.add_argument("--eval-steps", type=int, default=300)
+    ap.add_argument("--every", type=int, default=10)
+    a = ap.parse_args(argv)
+    dev = "cuda"
+    t0 = time.perf_counter()
+    data = make_pairs(a.pairs, seed=1, steps=a.pair_steps, device=dev)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    net = InitNet(device=dev, seed=0, lr=a.lr)
+    learned_t0 = time.perf_counter()
+    losses = train(net, data, a.train_steps, batch=a.batch)
+    t_train = time.perf_counter() - learned_t0
+    # the network's tensor-core throughput on one training batch
+    idx = torch.arange(min(a.batch, a.pairs), device=dev)
+    p, c, col, o = (data[k].index_select(0, idx).contiguous() for k in ("patches", "ctrl", "color", "opac"))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        net.train_step(p, c, col, o)
+    e0.record()
+    for _ in range(10):
+        net.train_step(p, c, col, o)
+    e1.record()
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / 10
+    evals = []
+    for i in range(a.targets):
+        tg = torch.as_tensor(synth.procedural_target(7000 + i, a.side, a.side, 200), device=dev)
+        res = {}
+        for name, m in (("circles", None), ("learned", net)):
+            s0 = time.perf_counter()
+            curves = initial_curves(tg, m)
+            torch.cuda.synchronize()
+            init_ms = (time.perf_counter() - s0) * 1e3
+            psnr, ms = optimise(tg, curves, a.eval_steps, every=a.every)
+            res[name] = dict(psnr=[round(x, 3) for x in psnr], ms_per_step=round(ms, 4), init_ms=round(init_ms, 2))
+        goal = res["circles"]["psnr"][-1]
+        hit = next((j for j, x in enumerate(res["learned"]["psnr"]) if x >= goal), None)
+        steps_learned = None if hit is None else min(a.eval_steps, hit * a.every)
+        res["circles_final_db"] = goal
+        res["learned_steps_to_circles_final"] = steps_learned
+        res["circles_steps"] = a.eval_steps
+        if steps_learned is not None:
+            t_c = a.eval_steps * res["circles"]["ms_per_step"] + res["circles"]["init_ms"]
+            t_l = steps_learned * res["learned"]["ms_per_step"] + res["learned"]["init_ms"]
+            res["wall_ms_circles"] = round(t_c, 2)
+            res["wall_ms_learned"] = round(t_l, 2)
+        evals.append(res)
+    out = {
+        "what": "learned initialisation vs circular initialisation of the method",
+        "pairs": {"n": a.pairs, "optimiser_steps": a.pair_steps, "seconds": round(t_pairs, 2)},
+        "train": {"steps": a.train_steps, "batch": a.batch, "seconds": round(t_train, 2),
+                  "loss_first": round(float(losses[:10].mean()), 5), "loss_last": round(float(losses[-10:].mean()), 5),
+                  "step_ms": round(step_ms, 4), "tflops": round(train_flops(a.batch) / (step_ms * 1e-3) / 1e12, 3)},
+        "eval": {"side": a.side, "patches": (a.side // SIDE) ** 2, "curves": (a.side // SIDE) ** 2 * CELLS,
+                 "targets": evals},
+    }
+    print(json.dumps(out))
+    return out
+
+
+if __name__ == "__main__":
+    main()
