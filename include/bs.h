@@ -72,6 +72,12 @@ typedef struct {
   const float *closed_opac;   /* [n_closed]                                          */
   const uint32_t *draw_first; /* [n_open + n_closed] index of each curve's first
                                  Gaussian in the draw-ordered table (bs_curve_order) */
+  /* Linear-gradient fills of closed curves (Appendix D), each may be NULL
+   * (a uniform fill): the colour / opacity at P6.  Sample k of a row of K
+   * takes x = x0 + u (x1 - x0), u = k / (K - 1), from the value x0 at P0
+   * (closed_color / closed_opac) to x1 at P6. */
+  const float *closed_color2; /* [n_closed][3] or NULL                               */
+  const float *closed_opac2;  /* [n_closed] or NULL                                  */
 } bs_curves;
 
 /* Gradients in the layout of bs_curves (device, written by the callee). */
@@ -83,6 +89,8 @@ typedef struct {
   float *closed_ctrl;   /* [n_closed][12][2] */
   float *closed_color;  /* [n_closed][3]   */
   float *closed_opac;   /* [n_closed]      */
+  float *closed_color2; /* [n_closed][3], written when the curves have closed_color2 and this is non-NULL */
+  float *closed_opac2;  /* [n_closed], likewise                                                          */
 } bs_curves_grad;
 
 /* Sampling of Gaussians on curves (Section 3.3, Eq. 3-8). */
@@ -535,6 +543,41 @@ typedef struct {
  * step: device int32, t before this step (0 before the first). */
 bs_status bs_adam_step(const bs_adam_group *groups, int32_t n_groups, const bs_adam_cfg *cfg, int32_t *step,
                        bs_stream stream);
+
+/*
+ * The Xing loss of Eq. 13 (the convexity term, as defined by LIVE, which the
+ * paper adopts): per cubic segment (A, B, C, D) of every closed curve, with
+ * u = B - A, v = C - B, w = D - C, D1 = [u x v >= 0], D2 = (u x w) / (|u| |w|),
+ * L_seg = D1 relu(-D2) + (1 - D1) relu(D2) (0 when |u| or |w| is 0).
+ *   loss_out          lambda * mean of L_seg over the 4 n_closed segments
+ *                     (device double, written)
+ *   grad_closed_ctrl  [n_closed][12][2] (device): d(loss_out)/d(control
+ *                     points) is ADDED to it; may be NULL
+ * Only curves->n_closed and closed_ctrl are read.
+ */
+bs_status bs_xing_loss(const bs_curves *curves, float lambda, double *loss_out, float *grad_closed_ctrl,
+                       bs_stream stream);
+
+/*
+ * SVG export (Appendix C, Algorithm 2).  All arrays of `curves` and `rank`
+ * are HOST pointers here (pixel coordinates, activated colours).  Curves are
+ * written back to front: by descending draw rank when rank is non-NULL
+ * (rank 0 is front-most, so it comes last), else in index order.  A closed
+ * curve is the path M P0, C P1 P2 P3, C P4 P5 P6, C P7 P8 P9, C P10 P11 P0, Z,
+ * filled with rgb(round(255 colour)) at fill-opacity 1 (Algorithm 2), or at
+ * its own opacity with flags bit 0; a closed curve with a gradient fill is
+ * filled by a linearGradient from P0 to P6 whose stops are its two colours
+ * (and, with bit 0, opacities).  An open curve is the unfilled path M P0,
+ * C P1 P2 P3, C P4 P5 P6, C P7 P8 P9 stroked with its colour at width
+ * 2 width and the mean of its segment opacities.  Numbers carry 9
+ * significant digits, so float32 values read back exactly.
+ *   buf, buf_bytes  (HOST) receives the NUL-terminated document; may be NULL
+ *                   to ask for the size
+ *   needed_out      (HOST) bytes the document needs, NUL included
+ * Host-only: needs no GPU.
+ */
+bs_status bs_svg_export(const bs_curves *curves, const uint32_t *rank, int32_t width, int32_t height,
+                        int32_t flags, char *buf, size_t buf_bytes, size_t *needed_out);
 
 /* ------------------------------------------------------------------------
  * Learned initialisation (not in the paper: a proposal network for initial

@@ -173,8 +173,12 @@ def closed_tau(rows: int) -> torch.Tensor:
     return (1.0 - torch.cos(math.pi * r / (rows - 1))) / 2.0
 
 
-def sample_closed(ctrl, color, opac, cfg: SampleCfg):
-    """Gaussians filling closed curves, [Nc, R+2, K] per field (Eq. 4-8)."""
+def sample_closed(ctrl, color, opac, cfg: SampleCfg, color2=None, opac2=None):
+    """Gaussians filling closed curves, [Nc, R+2, K] per field (Eq. 4-8).
+
+    Linear-gradient fills (Appendix D; reading): with color2 / opac2 given,
+    sample k of every row takes x0 + u (x1 - x0), u = k / (K - 1), from the
+    value x0 at P0 to x1 at P6, the two ends of both boundaries."""
     rows, K = cfg.rows_closed, cfg.k_closed
     A, B = closed_boundaries(ctrl)
     tau = closed_tau(rows)[None, :, None, None]
@@ -184,8 +188,15 @@ def sample_closed(ctrl, color, opac, cfg: SampleCfg):
     nxt = X[:, 1:] - X[:, :-1]                                 # X_{r+1,k} - X_{r,k}
     sy_vec = torch.cat([nxt, nxt[:, -1:]], dim=1)              # last row uses (R, R+1)
     sigma_y = _norm(sy_vec) / cfg.rho                          # Eq. 7, second line
-    o = opac[:, None, None].expand(-1, rows, K)
-    col = color[:, None, None, :].expand(-1, rows, K, -1)
+    u = torch.arange(K, dtype=F64) / (K - 1)
+    if opac2 is None:
+        o = opac[:, None, None].expand(-1, rows, K)
+    else:
+        o = (opac[:, None] + u[None, :] * (opac2 - opac)[:, None])[:, None, :].expand(-1, rows, K)
+    if color2 is None:
+        col = color[:, None, None, :].expand(-1, rows, K, -1)
+    else:
+        col = (color[:, None, :] + u[None, :, None] * (color2 - color)[:, None, :])[:, None].expand(-1, rows, K, -1)
     return dict(mu=X, sigma_x=sigma_x, sigma_y=sigma_y, theta=theta, o=o, col=col)
 
 
@@ -269,7 +280,8 @@ def gaussian_table(curves: dict, cfg: SampleCfg, first=None):
         so = sample_open(oc, ow, curves["open_color"], curves["open_opac"], cfg)
         parts.append((so, cfg.g_open, 0))
     if cc.shape[0]:
-        sc = sample_closed(cc, curves["closed_color"], curves["closed_opac"], cfg)
+        sc = sample_closed(cc, curves["closed_color"], curves["closed_opac"], cfg,
+                           curves.get("closed_color2"), curves.get("closed_opac2"))
         sc = {k: v.reshape((v.shape[0], -1) + tuple(v.shape[3:])) for k, v in sc.items()}
         parts.append((sc, cfg.per_closed, n_open))
     n_g = n_open * cfg.g_open + cc.shape[0] * cfg.per_closed

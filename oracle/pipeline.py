@@ -23,11 +23,15 @@ CURVE_KEYS = ("open_ctrl", "open_width", "open_color", "open_opac",
               "closed_ctrl", "closed_color", "closed_opac")
 
 
+FILL_KEYS = ("closed_color2", "closed_opac2")
+
+
 def as_curves(d: dict, requires_grad=False):
     out = {}
-    for k in CURVE_KEYS:
-        v = torch.as_tensor(np.asarray(d[k]), dtype=torch.float64).clone()
-        out[k] = v.requires_grad_(requires_grad)
+    for k in CURVE_KEYS + FILL_KEYS:
+        if k in d and d[k] is not None:
+            v = torch.as_tensor(np.asarray(d[k]), dtype=torch.float64).clone()
+            out[k] = v.requires_grad_(requires_grad)
     return out
 
 
@@ -38,9 +42,9 @@ def sample_vjp(curves: dict, cfg: SampleCfg, dtab: dict, first=None):
     tab = gaussian_table(cv, cfg, first)
     outs = [tab[k] for k in GRAD_KEYS]
     grads = [torch.as_tensor(dtab[k], dtype=torch.float64) for k in GRAD_KEYS]
-    gs = torch.autograd.grad(outs, [cv[k] for k in CURVE_KEYS], grad_outputs=grads,
-                             allow_unused=True)
-    return {k: (g if g is not None else torch.zeros_like(cv[k])) for k, g in zip(CURVE_KEYS, gs)}
+    keys = [k for k in CURVE_KEYS + FILL_KEYS if k in cv]
+    gs = torch.autograd.grad(outs, [cv[k] for k in keys], grad_outputs=grads, allow_unused=True)
+    return {k: (g if g is not None else torch.zeros_like(cv[k])) for k, g in zip(keys, gs)}
 
 
 def step(curves: dict, cfg: SampleCfg, W: int, H: int, target, bg=(0.0, 0.0, 0.0),

@@ -147,11 +147,13 @@ class CurveAdam:
             "open_opac": (cfg.lr_opac, 0.0, 1.0, None, 1),
             "closed_color": (cfg.lr_color, 0.0, 1.0, None, 1),
             "closed_opac": (cfg.lr_opac, 0.0, 1.0, None, 1),
+            "closed_color2": (cfg.lr_color, 0.0, 1.0, None, 1),
+            "closed_opac2": (cfg.lr_opac, 0.0, 1.0, None, 1),
         }
         self.groups = []
         for k, (lr, lo, hi, rs, rl) in spec.items():
             p = getattr(curves, k)
-            if p.numel() == 0:
+            if p is None or p.numel() == 0:
                 continue
             self.groups.append(bs.AdamGroup(p, getattr(grad, k), getattr(self.m, k), getattr(self.v, k), lr, lo, hi,
                                             rs, rl))

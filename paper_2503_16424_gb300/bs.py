@@ -33,13 +33,14 @@ class bs_curves(ctypes.Structure):
     _fields_ = [("n_open", c_int32), ("n_closed", c_int32),
                 ("open_ctrl", c_void_p), ("open_width", c_void_p), ("open_color", c_void_p),
                 ("open_opac", c_void_p), ("closed_ctrl", c_void_p), ("closed_color", c_void_p),
-                ("closed_opac", c_void_p), ("draw_first", c_void_p)]
+                ("closed_opac", c_void_p), ("draw_first", c_void_p), ("closed_color2", c_void_p),
+                ("closed_opac2", c_void_p)]
 
 
 class bs_curves_grad(ctypes.Structure):
     _fields_ = [("open_ctrl", c_void_p), ("open_width", c_void_p), ("open_color", c_void_p),
                 ("open_opac", c_void_p), ("closed_ctrl", c_void_p), ("closed_color", c_void_p),
-                ("closed_opac", c_void_p)]
+                ("closed_opac", c_void_p), ("closed_color2", c_void_p), ("closed_opac2", c_void_p)]
 
 
 class bs_sample_cfg(ctypes.Structure):
@@ -146,6 +147,8 @@ _sig("bs_batch_render_fwd", _B, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P)
 _sig("bs_batch_render_bwd", _B, _P, _P, _P, _P, _P, _P, _P, POINTER(bs_curves), POINTER(bs_curves_grad), _P)
 _sig("bs_batch_status", _B, POINTER(c_int32), POINTER(c_int64), _P)
 _sig("bs_adam_step", POINTER(bs_adam_group), c_int32, POINTER(bs_adam_cfg), _P, _P)
+_sig("bs_xing_loss", POINTER(bs_curves), c_float, _P, _P, _P)
+_sig("bs_svg_export", POINTER(bs_curves), _P, c_int32, c_int32, c_int32, _P, c_size_t, POINTER(c_size_t))
 lib.bs_net_param_count.argtypes = [c_int32]
 lib.bs_net_param_count.restype = c_int64
 _sig("bs_net_workspace", c_int32, c_int32, POINTER(c_size_t))
@@ -218,6 +221,7 @@ class Canvas:
 
 CURVE_FIELDS = ("open_ctrl", "open_width", "open_color", "open_opac",
                 "closed_ctrl", "closed_color", "closed_opac")
+FILL_FIELDS = ("closed_color2", "closed_opac2")
 
 
 @dataclass
@@ -231,6 +235,8 @@ class CurveSet:
     closed_ctrl: torch.Tensor   # [Nc,12,2]
     closed_color: torch.Tensor  # [Nc,3]
     closed_opac: torch.Tensor   # [Nc]
+    closed_color2: torch.Tensor = None  # [Nc,3] linear-gradient fill: colour at P6 (None: uniform)
+    closed_opac2: torch.Tensor = None   # [Nc] opacity at P6 (None: uniform)
 
     @property
     def n_open(self):
@@ -244,24 +250,30 @@ class CurveSet:
         no, nc = self.n_open, self.n_closed
         shapes = dict(open_ctrl=(no, 10, 2), open_width=(no,), open_color=(no, 3), open_opac=(no, 3),
                       closed_ctrl=(nc, 12, 2), closed_color=(nc, 3), closed_opac=(nc,))
+        shapes.update(closed_color2=(nc, 3), closed_opac2=(nc,))
         for k, s in shapes.items():
-            _want(getattr(self, k), torch.float32, s, k)
+            if getattr(self, k) is not None:
+                _want(getattr(self, k), torch.float32, s, k)
         return self
+
+    def fields(self):
+        """The names of the tensors this set holds (the fill fields when given)."""
+        return CURVE_FIELDS + tuple(k for k in FILL_FIELDS if getattr(self, k) is not None)
 
     def c(self, draw_first=None):
         return bs_curves(self.n_open, self.n_closed, *(_ptr(getattr(self, k)) for k in CURVE_FIELDS),
-                         _ptr(draw_first))
+                         _ptr(draw_first), *(_ptr(getattr(self, k)) for k in FILL_FIELDS))
 
     @staticmethod
     def from_arrays(arrays: dict, device="cuda"):
         return CurveSet(**{k: torch.as_tensor(arrays[k], dtype=torch.float32, device=device).contiguous()
-                           for k in CURVE_FIELDS})
+                           for k in CURVE_FIELDS + FILL_FIELDS if k in arrays and arrays[k] is not None})
 
     def zeros_like(self):
-        return CurveSet(**{k: torch.zeros_like(getattr(self, k)) for k in CURVE_FIELDS})
+        return CurveSet(**{k: torch.zeros_like(getattr(self, k)) for k in self.fields()})
 
     def grad_c(self):
-        return bs_curves_grad(*(_ptr(getattr(self, k)) for k in CURVE_FIELDS))
+        return bs_curves_grad(*(_ptr(getattr(self, k)) for k in CURVE_FIELDS + FILL_FIELDS))
 
     def mut_c(self):
         return bs_curves_mut(self.n_open, self.n_closed, *(_ptr(getattr(self, k)) for k in CURVE_FIELDS))
@@ -727,3 +739,48 @@ def net_train_step(w, w_bf16, grads, patches, t_ctrl, t_color, t_opac, ws, loss)
     _check("bs_net_train_step", lib.bs_net_train_step(ctypes.byref(net), _ptr(patches), n, side, _ptr(t_ctrl),
                                                        _ptr(t_color), _ptr(t_opac), _ptr(ws), ws.numel(),
                                                        ctypes.byref(g), c_void_p(loss.data_ptr()), _stream()))
+
+
+# ---------------------------------------------------------------------------
+# Xing loss (bs_xing_loss) and SVG export (bs_svg_export)
+
+def xing_loss(curves: CurveSet, lam: float, grad_closed_ctrl: torch.Tensor = None, loss=None):
+    """lambda * mean Xing loss of the closed curves (device double); adds its
+    gradient to grad_closed_ctrl when given."""
+    loss = loss if loss is not None else torch.empty((), dtype=torch.float64, device=curves.closed_ctrl.device)
+    c = curves.c()
+    if grad_closed_ctrl is not None:
+        _want(grad_closed_ctrl, torch.float32, tuple(curves.closed_ctrl.shape), "grad_closed_ctrl")
+    _check("bs_xing_loss", lib.bs_xing_loss(ctypes.byref(c), lam, c_void_p(loss.data_ptr()), _ptr(grad_closed_ctrl),
+                                             _stream()))
+    return loss
+
+
+def svg_export(arrays: dict, width: int, height: int, rank=None, own_opacity: bool = False) -> str:
+    """The SVG document of host curve arrays (numpy, the CurveSet fields,
+    optionally closed_color2 / closed_opac2), back to front by draw rank."""
+    import numpy as np
+    keep = []
+
+    def hp(k, dtype=np.float32):
+        v = arrays.get(k)
+        if v is None:
+            return c_void_p(0)
+        a = np.ascontiguousarray(np.asarray(v, dtype=dtype))
+        keep.append(a)
+        return c_void_p(a.ctypes.data) if a.size else c_void_p(0)
+    no = int(np.asarray(arrays["open_ctrl"]).shape[0])
+    nc = int(np.asarray(arrays["closed_ctrl"]).shape[0])
+    c = bs_curves(no, nc, *(hp(k) for k in CURVE_FIELDS), c_void_p(0), *(hp(k) for k in FILL_FIELDS))
+    r = c_void_p(0)
+    if rank is not None:
+        ra = np.ascontiguousarray(np.asarray(rank, dtype=np.uint32))
+        keep.append(ra)
+        r = c_void_p(ra.ctypes.data)
+    need = c_size_t(0)
+    flags = 1 if own_opacity else 0
+    _check("bs_svg_export", lib.bs_svg_export(ctypes.byref(c), r, width, height, flags, None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check("bs_svg_export", lib.bs_svg_export(ctypes.byref(c), r, width, height, flags, buf, need.value,
+                                               ctypes.byref(need)))
+    return buf.value.decode()

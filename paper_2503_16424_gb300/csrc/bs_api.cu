@@ -5,6 +5,8 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <string.h>
+
 #include <string>
 #include <vector>
 
@@ -105,6 +107,132 @@ bs_status check_canvas(const bs_canvas *cv) {
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ---- SVG export (Appendix C, Algorithm 2) ----
+// Numbers with 9 significant digits (a float32 reads back exactly); colours
+// rgb(round(255 c)) of the colour clamped to [0, 1].
+void svg_num(std::string &s, float v) {
+  char b[32];
+  snprintf(b, sizeof(b), "%.9g", (double)v);
+  s += b;
+}
+
+void svg_pt(std::string &s, const float *p) {
+  svg_num(s, p[0]);
+  s += ' ';
+  svg_num(s, p[1]);
+}
+
+void svg_rgb(std::string &s, const float *c) {
+  char b[48];
+  int v[3];
+  for (int i = 0; i < 3; ++i) {
+    const float x = c[i] < 0.f ? 0.f : (c[i] > 1.f ? 1.f : c[i]);
+    v[i] = (int)lrintf(255.f * x);
+  }
+  snprintf(b, sizeof(b), "rgb(%d,%d,%d)", v[0], v[1], v[2]);
+  s += b;
+}
+
+// The document: curves back to front (descending draw rank when rank is
+// given, else in index order, open curves first).  Closed curve: "M P0 C P1
+// P2 P3 C P4 P5 P6 C P7 P8 P9 C P10 P11 P0 Z" filled with its colour, at
+// opacity 1 as in Algorithm 2 (flag 1: its own opacity); with a gradient
+// fill a linearGradient from P0 to P6 (user space) with the two colours and
+// opacities as stops.  Open curve: "M P0 C P1 P2 P3 C P4 P5 P6 C P7 P8 P9",
+// unfilled, stroked with its colour, width 2 w and the mean of its three
+// segment opacities.
+bs_status svg_document(const bs_curves &c, const uint32_t *rank, int width, int height, int flags,
+                       std::string *out) {
+  const int n = c.n_open + c.n_closed;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  if (rank) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rank[a] > rank[b]; });
+  std::string &s = *out;
+  char b[256];
+  snprintf(b, sizeof(b),
+           "<svg xmlns=\"http://www.w3.org/2000/svg\" width=\"%d\" height=\"%d\" viewBox=\"0 0 %d %d\">\n", width,
+           height, width, height);
+  s += b;
+  const bool grad = c.closed_color2 || c.closed_opac2;
+  if (grad && c.n_closed > 0) {
+    s += "<defs>\n";
+    for (int j = 0; j < c.n_closed; ++j) {
+      const float *P = c.closed_ctrl + (size_t)j * 24;
+      const float *c0 = c.closed_color + (size_t)j * 3;
+      const float *c1 = c.closed_color2 ? c.closed_color2 + (size_t)j * 3 : c0;
+      const float o0 = c.closed_opac[j], o1 = c.closed_opac2 ? c.closed_opac2[j] : o0;
+      snprintf(b, sizeof(b), "<linearGradient id=\"f%d\" gradientUnits=\"userSpaceOnUse\" x1=\"", j);
+      s += b;
+      svg_num(s, P[0]);
+      s += "\" y1=\"";
+      svg_num(s, P[1]);
+      s += "\" x2=\"";
+      svg_num(s, P[12]);
+      s += "\" y2=\"";
+      svg_num(s, P[13]);
+      s += "\"><stop offset=\"0\" stop-color=\"";
+      svg_rgb(s, c0);
+      s += "\" stop-opacity=\"";
+      svg_num(s, (flags & 1) ? o0 : 1.f);
+      s += "\"/><stop offset=\"1\" stop-color=\"";
+      svg_rgb(s, c1);
+      s += "\" stop-opacity=\"";
+      svg_num(s, (flags & 1) ? o1 : 1.f);
+      s += "\"/></linearGradient>\n";
+    }
+    s += "</defs>\n";
+  }
+  for (int idx : order) {
+    if (idx < c.n_open) {
+      const float *P = c.open_ctrl + (size_t)idx * 20;
+      s += "<path d=\"M ";
+      svg_pt(s, P);
+      for (int seg = 0; seg < 3; ++seg) {
+        s += " C ";
+        svg_pt(s, P + 2 * (3 * seg + 1));
+        s += ' ';
+        svg_pt(s, P + 2 * (3 * seg + 2));
+        s += ' ';
+        svg_pt(s, P + 2 * (3 * seg + 3));
+      }
+      s += "\" fill=\"none\" stroke=\"";
+      svg_rgb(s, c.open_color + (size_t)idx * 3);
+      s += "\" stroke-width=\"";
+      svg_num(s, 2.f * c.open_width[idx]);
+      const float *o = c.open_opac + (size_t)idx * 3;
+      s += "\" stroke-opacity=\"";
+      svg_num(s, ((o[0] + o[1]) + o[2]) / 3.f);
+      s += "\" stroke-linecap=\"round\"/>\n";
+    } else {
+      const int j = idx - c.n_open;
+      const float *P = c.closed_ctrl + (size_t)j * 24;
+      s += "<path d=\"M ";
+      svg_pt(s, P);
+      for (int seg = 0; seg < 4; ++seg) {
+        s += " C ";
+        svg_pt(s, P + 2 * (3 * seg + 1));
+        s += ' ';
+        svg_pt(s, P + 2 * (3 * seg + 2));
+        s += ' ';
+        svg_pt(s, P + 2 * ((3 * seg + 3) % 12));
+      }
+      s += " Z\" fill=\"";
+      if (grad) {
+        snprintf(b, sizeof(b), "url(#f%d)", j);
+        s += b;
+        s += "\"/>\n";
+      } else {
+        svg_rgb(s, c.closed_color + (size_t)j * 3);
+        s += "\" fill-opacity=\"";
+        svg_num(s, (flags & 1) ? c.closed_opac[j] : 1.f);
+        s += "\"/>\n";
+      }
+    }
+  }
+  s += "</svg>\n";
+  return BS_OK;
+}
 
 bs_status check_pd_counts(int32_t n_open, int32_t n_closed) {
   if (n_open < 0 || n_closed < 0) return invalid("negative curve count");
@@ -435,6 +563,30 @@ bs_status bs_adam_step(const bs_adam_group *groups, int32_t n_groups, const bs_a
   }
   BS_TRY(check_device());
   return launch_adam(groups, n_groups, *cfg, step, (cudaStream_t)stream);
+}
+
+bs_status bs_xing_loss(const bs_curves *curves, float lambda, double *loss_out, float *grad_closed_ctrl,
+                       bs_stream stream) {
+  BS_TRY(check_curves(curves, false));
+  if (!loss_out) return invalid("loss_out is NULL");
+  if (!(lambda >= 0.f) || !isfinite(lambda)) return invalid("lambda must be finite and >= 0");
+  BS_TRY(check_device());
+  return launch_xing(*curves, lambda, loss_out, grad_closed_ctrl, (cudaStream_t)stream);
+}
+
+bs_status bs_svg_export(const bs_curves *curves, const uint32_t *rank, int32_t width, int32_t height, int32_t flags,
+                        char *buf, size_t buf_bytes, size_t *needed_out) {
+  BS_TRY(check_curves(curves, false));
+  if (width < 1 || height < 1) return invalid("canvas %dx%d out of range", width, height);
+  if (!needed_out) return invalid("needed_out is NULL");
+  std::string out;
+  BS_TRY(svg_document(*curves, rank, width, height, flags, &out));
+  *needed_out = out.size() + 1;
+  if (buf) {
+    if (buf_bytes < out.size() + 1) return invalid("buffer of %zu bytes, %zu needed", buf_bytes, out.size() + 1);
+    memcpy(buf, out.c_str(), out.size() + 1);
+  }
+  return BS_OK;
 }
 
 bs_status bs_prune_densify_workspace(int32_t n_open, int32_t n_closed, const bs_canvas *canvas, size_t *bytes) {

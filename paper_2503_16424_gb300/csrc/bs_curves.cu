@@ -185,7 +185,13 @@ struct CurveAttr {
   float3 col;
 };
 
-__device__ __forceinline__ CurveAttr curve_attr(const bs_curves &c, int curve, int seg) {
+// Width, opacity and colour of a sample.  Closed curves with a
+// linear-gradient fill (Appendix D; closed_color2 / closed_opac2 non-NULL)
+// interpolate from the values at P0 to those at P6 by the sample's position
+// u = k / (K - 1) along its row: x = x0 + u (x1 - x0).
+__device__ __forceinline__ float lerp_f(float a, float b, float u) { return a + u * (b - a); }
+
+__device__ __forceinline__ CurveAttr curve_attr(const bs_curves &c, int curve, int seg, float u) {
   CurveAttr a;
   if (curve < c.n_open) {
     a.width = c.open_width[curve];
@@ -194,10 +200,19 @@ __device__ __forceinline__ CurveAttr curve_attr(const bs_curves &c, int curve, i
   } else {
     const int j = curve - c.n_open;
     a.width = 0.f;
-    a.opac = c.closed_opac[j];
+    a.opac = c.closed_opac2 ? lerp_f(c.closed_opac[j], c.closed_opac2[j], u) : c.closed_opac[j];
     a.col = make_float3(c.closed_color[j * 3], c.closed_color[j * 3 + 1], c.closed_color[j * 3 + 2]);
+    if (c.closed_color2)
+      a.col = make_float3(lerp_f(a.col.x, c.closed_color2[j * 3], u), lerp_f(a.col.y, c.closed_color2[j * 3 + 1], u),
+                          lerp_f(a.col.z, c.closed_color2[j * 3 + 2], u));
   }
   return a;
+}
+
+// u of sample idx of a closed curve with K samples per row
+__device__ __forceinline__ float row_u(int idx, int K) {
+  const int k = idx % K;
+  return (float)k / (float)(K - 1);
 }
 
 // The sampling of curve `curve` of a batch: its image's.
@@ -226,7 +241,7 @@ __global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, 
   const double ox = P[0], oy = P[1];
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int seg = closed ? 0 : chain_seg(idx, K, 3);
-    const CurveAttr at = curve_attr(c, curve, seg);
+    const CurveAttr at = curve_attr(c, curve, seg, closed ? row_u(idx, K) : 0.f);
     const Local L = local_geometry(m.X, idx, K, cfg.rows, closed, at.width, cfg.rho);
     // Sigma = R diag(lx, ly) R^T (Eq. 11-12 with the eps floor)
     const float lx = L.sx * L.sx + cfg.eps, ly = L.sy * L.sy + cfg.eps;
@@ -266,10 +281,12 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
   if (tab) cfg = batch_cfg(tab, n_images, c, blockIdx.x);
   const CurveSmem m = carve(smem_bwd, n_max, k_max, cfg.rows, true);
   float2 *GM = m.G, *GE = m.G + n_max, *GT = m.G + 2 * n_max, *GF = m.G + 3 * n_max;
-  __shared__ float sAttr[8];  // opac[3] (open) or opac (closed), colour[3], width
+  // opac[3] (open) or opac (closed), colour[3], width, then (gradient
+  // fills) the far-end opacity [7] and colour [8..10]
+  __shared__ float sAttr[12];
   const int curve = blockIdx.x;
   const bool closed = curve >= c.n_open;
-  if (threadIdx.x < 8) sAttr[threadIdx.x] = 0.f;
+  if (threadIdx.x < 12) sAttr[threadIdx.x] = 0.f;
   const int n = eval_samples(c, cfg, curve, m);
   const int K = closed ? cfg.kc : cfg.g_open, R2 = closed ? cfg.rows : 1;
   const uint32_t first = c.draw_first[curve];
@@ -278,9 +295,11 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
   for (int round = 0; round < n_rounds; ++round) {
     const int idx = round * blockDim.x + threadIdx.x;
     float d_op[3] = {0.f, 0.f, 0.f}, d_col[3] = {0.f, 0.f, 0.f}, d_w = 0.f;
+    float d_op2 = 0.f, d_col2[3] = {0.f, 0.f, 0.f};
     if (idx < n) {
       const int seg = closed ? 0 : chain_seg(idx, K, 3);
-      const CurveAttr at = curve_attr(c, curve, seg);
+      const float u = closed ? row_u(idx, K) : 0.f;
+      const CurveAttr at = curve_attr(c, curve, seg, u);
       const Local L = local_geometry(m.X, idx, K, cfg.rows, closed, at.width, cfg.rho);
       const float *dg = dgauss + (size_t)(first + idx) * BS_DGAUSS_FLOATS;
       const float4 d0 = *reinterpret_cast<const float4 *>(dg);      // mx, my, ux, uy
@@ -304,7 +323,12 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
       if (closed) {
         const float kf = L.lf > 0.f ? dsy / (L.lf * cfg.rho) : 0.f;
         GF[idx] = make_float2(kf * L.f.x, kf * L.f.y);
-        d_op[0] = d1.z;
+        if (c.closed_opac2) {
+          d_op[0] = (1.f - u) * d1.z;
+          d_op2 = u * d1.z;
+        } else {
+          d_op[0] = d1.z;
+        }
       } else {
         GF[idx] = make_float2(0.f, 0.f);
         d_w = dsy;
@@ -313,6 +337,13 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
       d_col[0] = d1.w;
       d_col[1] = d2.x;
       d_col[2] = d2.y;
+      if (closed && c.closed_color2) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          d_col2[i] = u * d_col[i];
+          d_col[i] -= d_col2[i];
+        }
+      }
     }
     // per-curve scalars: warp sums, then one shared atomic per warp
 #pragma unroll
@@ -326,6 +357,15 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
     }
     const float w = warp_sum(d_w);
     if (lane == 0) atomicAdd(&sAttr[6], w);
+    if (closed && (c.closed_opac2 || c.closed_color2)) {
+      const float o2 = warp_sum(d_op2);
+      if (lane == 0) atomicAdd(&sAttr[7], o2);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float b2 = warp_sum(d_col2[i]);
+        if (lane == 0) atomicAdd(&sAttr[8 + i], b2);
+      }
+    }
   }
   __syncthreads();
   // phase 2: dL/dX_m from the differences that use sample m (see local_geometry)
@@ -394,6 +434,8 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
     const int j = curve - c.n_open;
     if (threadIdx.x < 3) g.closed_color[j * 3 + threadIdx.x] = sAttr[3 + threadIdx.x];
     if (threadIdx.x == 0) g.closed_opac[j] = sAttr[0];
+    if (c.closed_color2 && g.closed_color2 && threadIdx.x < 3) g.closed_color2[j * 3 + threadIdx.x] = sAttr[8 + threadIdx.x];
+    if (c.closed_opac2 && g.closed_opac2 && threadIdx.x == 0) g.closed_opac2[j] = sAttr[7];
   }
 }
 
@@ -488,6 +530,69 @@ __global__ void batch_curve_order_first_kernel(bs_curves c, const BatchImage *__
   const BatchImage &im = tab[b];
   const uint32_t ob = first[i];
   first[i] = (uint32_t)im.gauss0 + ob * (uint32_t)im.g_open + (rank[i] - ob) * (uint32_t)(im.rows * im.kc);
+}
+
+// ---- Xing loss (the convexity term of Eq. 13) ----
+// Per cubic segment (A, B, C, D) of a closed curve, with u = B - A,
+// v = C - B, w = D - C:
+//   D1 = 1 if u x v >= 0 else 0,  D2 = (u x w) / (|u| |w|),
+//   L  = D1 relu(-D2) + (1 - D1) relu(D2)
+// (zero, with zero gradient, when |u| or |w| is 0).  One thread per closed
+// curve walks its four segments (segment s: P_3s .. P_3s+3, P_12 = P_0), so
+// its control-point gradient needs no atomics; the loss is lambda times the
+// mean over all segments, added to *loss with one double atomic per CTA.
+__global__ void xing_kernel(const float *__restrict__ ctrl, int n_closed, float lambda, double *__restrict__ loss,
+                            float *__restrict__ grad) {
+  __shared__ double s_sum[8];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (c < n_closed) {
+    const float *P = ctrl + (size_t)c * 24;
+    float g[24];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) g[i] = 0.f;
+    const float scale = lambda / (4.f * (float)n_closed);
+#pragma unroll
+    for (int sgm = 0; sgm < 4; ++sgm) {
+      const int ia = 3 * sgm, ib = ia + 1, ic = ia + 2, id = (ia + 3) % 12;
+      const float ux = P[2 * ib] - P[2 * ia], uy = P[2 * ib + 1] - P[2 * ia + 1];
+      const float vx = P[2 * ic] - P[2 * ib], vy = P[2 * ic + 1] - P[2 * ib + 1];
+      const float wx = P[2 * id] - P[2 * ic], wy = P[2 * id + 1] - P[2 * ic + 1];
+      const float nu = sqrtf(ux * ux + uy * uy), nw = sqrtf(wx * wx + wy * wy);
+      if (!(nu > 0.f) || !(nw > 0.f)) continue;
+      const float d1 = (ux * vy - uy * vx) >= 0.f ? 1.f : 0.f;
+      const float cr = ux * wy - uy * wx, inv = 1.f / (nu * nw), d2 = cr * inv;
+      l += d1 * fmaxf(-d2, 0.f) + (1.f - d1) * fmaxf(d2, 0.f);
+      const float sgn = (d1 > 0.f && d2 < 0.f) ? -1.f : ((d1 == 0.f && d2 > 0.f) ? 1.f : 0.f);  // dL/dD2
+      if (sgn == 0.f) continue;
+      // dD2/du = (w_y, -w_x) inv - D2 u / |u|^2,  dD2/dw = (-u_y, u_x) inv - D2 w / |w|^2
+      const float k = sgn * scale;
+      const float dux = k * (wy * inv - d2 * ux / (nu * nu)), duy = k * (-wx * inv - d2 * uy / (nu * nu));
+      const float dwx = k * (-uy * inv - d2 * wx / (nw * nw)), dwy = k * (ux * inv - d2 * wy / (nw * nw));
+      g[2 * ia] -= dux;
+      g[2 * ia + 1] -= duy;
+      g[2 * ib] += dux;
+      g[2 * ib + 1] += duy;
+      g[2 * ic] -= dwx;
+      g[2 * ic + 1] -= dwy;
+      g[2 * id] += dwx;
+      g[2 * id + 1] += dwy;
+    }
+    if (grad) {
+      float *G = grad + (size_t)c * 24;
+#pragma unroll
+      for (int i = 0; i < 24; ++i) G[i] += g[i];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_sum[w];
+    if (t != 0.0) atomicAdd(loss, t * (double)lambda / (4.0 * (double)n_closed));
+  }
 }
 
 Cfg to_cfg(const bs_sample_cfg &s) { return Cfg{s.g_open, s.rows_closed, s.k_closed, s.rho, s.cov_eps}; }
@@ -597,6 +702,14 @@ bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, c
   BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
   sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, Cfg{}, dgauss, g, p.n_max, p.k_max, table, p.n_images);
   BS_LAUNCHED("sample_bwd_kernel");
+  return BS_OK;
+}
+
+bs_status launch_xing(const bs_curves &c, float lambda, double *loss, float *grad_closed_ctrl, cudaStream_t s) {
+  BS_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s));
+  if (c.n_closed == 0) return BS_OK;
+  xing_kernel<<<div_up(c.n_closed, 256), 256, 0, s>>>(c.closed_ctrl, c.n_closed, lambda, loss, grad_closed_ctrl);
+  BS_LAUNCHED("xing_kernel");
   return BS_OK;
 }
 

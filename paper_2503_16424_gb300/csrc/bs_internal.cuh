@@ -105,6 +105,7 @@ bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float 
                             cudaStream_t s);
 bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const float *dgauss,
                             const bs_curves_grad &g, cudaStream_t s);
+bs_status launch_xing(const bs_curves &c, float lambda, double *loss, float *grad_closed_ctrl, cudaStream_t s);
 
 // binning (bs_bin.cu)
 struct BinPlan {

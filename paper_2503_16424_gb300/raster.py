@@ -52,15 +52,19 @@ class Rasterizer:
                                 curves=curves, cfg=self.cfg, first=self.first, grad=grad)
         return grad
 
-    def step(self, curves: CurveSet, target: torch.Tensor, grad: CurveSet = None):
+    def step(self, curves: CurveSet, target: torch.Tensor, grad: CurveSet = None, xing: float = 0.0):
         """sample -> bin -> render with the L2 loss/grad fused -> render bwd
-        -> sample bwd."""
+        -> sample bwd; with xing > 0 also the Xing term of Eq. 13 (lambda_2 =
+        xing; its value in self.xing_loss, its gradient added to the closed
+        curves' control points)."""
         self.rank, self.first = bs.curve_order(curves, self.cfg)
         bs.sample_curves(curves, self.cfg, self.first, out=self.gauss)
         self.binning.run(self.gauss)
         bs.render_fwd_l2(self.gauss, self.canvas, self.binning, target, out=(self.img, self.T, self.nc),
                          dimg=self.dimg, loss=self.loss)
         grad = self.backward(curves, self.dimg, grad)
+        if xing > 0.0:
+            self.xing_loss = bs.xing_loss(curves, xing, grad.closed_ctrl)
         return self.loss, grad
 
 
