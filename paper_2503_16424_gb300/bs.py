@@ -148,6 +148,7 @@ _sig("bs_batch_render_bwd", _B, _P, _P, _P, _P, _P, _P, _P, POINTER(bs_curves), 
 _sig("bs_batch_status", _B, POINTER(c_int32), POINTER(c_int64), _P)
 _sig("bs_adam_step", POINTER(bs_adam_group), c_int32, POINTER(bs_adam_cfg), _P, _P)
 _sig("bs_xing_loss", POINTER(bs_curves), c_float, _P, _P, _P)
+_sig("bs_debug_gemm_engine", c_int32, POINTER(c_int64))
 _sig("bs_svg_export", POINTER(bs_curves), _P, c_int32, c_int32, c_int32, _P, c_size_t, POINTER(c_size_t))
 lib.bs_net_param_count.argtypes = [c_int32]
 lib.bs_net_param_count.restype = c_int64
@@ -784,3 +785,11 @@ def svg_export(arrays: dict, width: int, height: int, rank=None, own_opacity: bo
     _check("bs_svg_export", lib.bs_svg_export(ctypes.byref(c), r, width, height, flags, buf, need.value,
                                                ctypes.byref(need)))
     return buf.value.decode()
+
+
+def debug_gemm_engine(engine: int):
+    """Test hook: the network GEMM engine for later calls (1 tcgen05, 0
+    mma.sync); returns the tcgen05 tiles that gave up a bounded wait so far."""
+    t = c_int64(0)
+    _check("bs_debug_gemm_engine", lib.bs_debug_gemm_engine(engine, ctypes.byref(t)))
+    return int(t.value)

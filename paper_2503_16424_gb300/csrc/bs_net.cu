@@ -116,6 +116,190 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const Op op) {
     }
 }
 
+// ---- the same GEMM on the 5th-generation tensor cores (tcgen05) ----
+// A CTA of four warps computes a 128 x 64 tile.  Per 32-wide K chunk every
+// thread gathers its share of A (128 x 32) and B (64 x 32) with the op's
+// load functions into shared memory in the canonical K-major layout without
+// swizzle: 8 x 16-byte core matrices, the core matrix of rows 8i..8i+7 and
+// columns 8j..8j+7 at byte (i * 512 + j * 128), one row per 16 bytes inside.
+// One thread then issues two tcgen05.mma (M 128, N 64, K 16, bf16 inputs,
+// float32 accumulator in tensor memory) per chunk and commits them to the
+// chunk's mbarrier; two stages, so the gather of a chunk overlaps the MMAs
+// of the previous one.  The epilogue reads the accumulator back with
+// tcgen05.ld (warp w owns tensor-memory lanes 32w..32w+31, the tile's rows)
+// and hands it to the op's store.  Every wait on an mbarrier is bounded; a
+// wait that gives up counts in *err and the tile is not stored.
+constexpr int kUM = 128, kUN = 64, kUK = 32;
+constexpr uint32_t kUmmaLbo = 128, kUmmaSbo = 512;          // bytes: next 8 K columns / next 8 rows
+constexpr uint32_t kUmmaCols = 64;                          // tensor-memory columns (float32 accumulators)
+constexpr uint32_t kWaitLimit = 1u << 24;
+// instruction descriptor, kind::f16: D float32 (bit 4), A and B bf16 (bits
+// 7 and 10), both K-major, N / 8 at bit 17, M / 16 at bit 24
+constexpr uint32_t kUmmaIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUN >> 3) << 17) |
+                                ((uint32_t)(kUM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets in 16-byte units, version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(const void *p, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Wait until the phase of `parity` of the barrier completed; false when the
+// bounded wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kUmmaIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// byte offset of the 16-byte vector (row r, columns 8j..8j+7) in a stage
+__device__ __forceinline__ uint32_t core_off(int r, int j) { return (uint32_t)((r >> 3) * kUmmaSbo + j * kUmmaLbo + (r & 7) * 16); }
+
+template <class Op>
+__global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, unsigned int *err) {
+  __shared__ __align__(128) uint8_t sA[2][kUM * kUK * 2];
+  __shared__ __align__(128) uint8_t sB[2][kUN * kUK * 2];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kUM, n0 = blockIdx.y * kUN;
+  const int kb = op.k_begin(blockIdx.z), ke = op.k_end(blockIdx.z);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kUmmaCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  // A: 512 vectors (row v / 4, columns 8 (v % 4)..), four per thread; B: 256, two
+  uint4 ra[4], rb[2];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int v = tid + kGemmThreads * i, row = v >> 2, kk = k0 + 8 * (v & 3);
+      ra[i] = kk < ke ? op.load_a(m0 + row, kk) : zero4();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int v = tid + kGemmThreads * i, row = v >> 2, kk = k0 + 8 * (v & 3);
+      rb[i] = kk < ke ? op.load_b(n0 + row, kk) : zero4();
+    }
+  };
+  const int n_chunks = ke > kb ? (ke - kb + kUK - 1) / kUK : 0;
+  bool ok = true;
+  if (n_chunks > 0) fetch(kb);
+  for (int c = 0; c < n_chunks; ++c) {
+    const int st = c & 1;
+    if (c >= 2) {  // the MMAs that read this stage: thread 0 waits, the CTA follows its verdict
+      const bool w = tid == 0 ? mbar_wait(&bar[st], (uint32_t)(((c - 2) >> 1) & 1)) : true;
+      if (!__syncthreads_and(w)) {
+        ok = false;
+        break;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int v = tid + kGemmThreads * i;
+      *reinterpret_cast<uint4 *>(sA[st] + core_off(v >> 2, v & 3)) = ra[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int v = tid + kGemmThreads * i;
+      *reinterpret_cast<uint4 *>(sB[st] + core_off(v >> 2, v & 3)) = rb[i];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the stores, visible to the tensor cores
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < kUK / 16; ++ks) {
+        const uint64_t da = umma_desc(sA[st] + ks * 2 * kUmmaLbo, kUmmaLbo, kUmmaSbo);
+        const uint64_t db = umma_desc(sB[st] + ks * 2 * kUmmaLbo, kUmmaLbo, kUmmaSbo);
+        umma_bf16(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
+      }
+      umma_commit(&bar[st]);
+    }
+    if (c + 1 < n_chunks) fetch(kb + (c + 1) * kUK);
+  }
+  if (n_chunks > 0) {
+    // thread 0 waits for the last commit, which covers every MMA it issued;
+    // after a wait that gave up, a second bounded wait before the tensor
+    // memory is released, and the tile is not stored
+    const int last = n_chunks - 1;
+    bool w = true;
+    if (tid == 0) {
+      w = ok && mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1));
+      if (!w) {
+        mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1));
+        atomicAdd(err, 1u);
+      }
+    }
+    ok = __syncthreads_and(w) && ok;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool store = __syncthreads_and(ok);
+  if (store) {
+    const int m = m0 + warp * 32 + lane;
+#pragma unroll
+    for (int col = 0; col < kUN; col += 8) {
+      uint32_t v[8];
+      if (n_chunks > 0) {
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+            "tcgen05.wait::ld.sync.aligned;\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+            : "r"(ta)
+            : "memory");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) op.store(m, n0 + col + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kUmmaCols) : "memory");
+}
+
 // ---- the operations ----
 struct Geom {
   int N, Hi, Wi, Cin, Ho, Wo, Cout, KS, S, P;
@@ -273,8 +457,21 @@ struct WgradOp {
   }
 };
 
+// The GEMM engine: 1 = tcgen05 (default), 0 = mma.sync (kept as a cross-check
+// for the tests, selected with bs_debug_gemm_engine).
+int g_gemm_engine = 1;
+__device__ unsigned int g_umma_timeouts;
+
 template <class Op>
 bs_status run_gemm(const Op &op, int M, int N, int splits, cudaStream_t s) {
+  if (g_gemm_engine == 1) {
+    unsigned int *err = nullptr;
+    BS_CUDA(cudaGetSymbolAddress((void **)&err, g_umma_timeouts));
+    const dim3 grid((unsigned)div_up(M, kUM), (unsigned)div_up(N, kUN), (unsigned)splits);
+    umma_gemm_kernel<Op><<<grid, kGemmThreads, 0, s>>>(op, err);
+    BS_LAUNCHED("umma_gemm_kernel");
+    return BS_OK;
+  }
   const dim3 grid((unsigned)div_up(M, kBM), (unsigned)div_up(N, kBN), (unsigned)splits);
   gemm_kernel<Op><<<grid, kGemmThreads, 0, s>>>(op);
   BS_LAUNCHED("gemm_kernel");
@@ -498,6 +695,17 @@ bs_status net_forward(const bs_net *net, const float *patches, int n, int side, 
 }  // namespace
 
 extern "C" {
+
+bs_status bs_debug_gemm_engine(int32_t engine, int64_t *timeouts_out) {
+  if (engine != 0 && engine != 1) return net_invalid("engine must be 0 (mma.sync) or 1 (tcgen05)");
+  g_gemm_engine = engine;
+  if (timeouts_out) {
+    unsigned int t = 0;
+    BS_CUDA(cudaMemcpyFromSymbol(&t, g_umma_timeouts, sizeof(t)));
+    *timeouts_out = t;
+  }
+  return BS_OK;
+}
 
 bs_status bs_net_workspace(int32_t n, int32_t side, size_t *bytes) {
   if (!bytes) return net_invalid("bytes is NULL");

@@ -108,3 +108,40 @@ def test_training_fits_pairs_and_beats_the_circles(learned):
         gains0.append(res["learned"][0] - res["circles"][0])
         gains.append(res["learned"][-1] - res["circles"][-1])
     assert min(gains0) > 0.0 and min(gains) > 0.0
+
+
+def test_tcgen05_and_mma_sync_engines_agree(learned):
+    """Every GEMM of the network (forward, both input gradients, the weight
+    gradients) on the tcgen05 engine against the mma.sync engine: the same
+    bf16 products summed in float32 in another order, so the outputs agree to
+    a few float32 ulps of their sums, up to activations whose bf16 rounding
+    flips; and no tcgen05 tile gave up waiting for its MMAs."""
+    import paper_2503_16424_gb300.bs as bs
+    net = _rand_net(learned, 6)
+    rng = np.random.default_rng(11)
+    n, side = 3, 96
+    x = torch.as_tensor(rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32), device="cuda")
+    cells = (side // 32) ** 2
+    t_ctrl = torch.as_tensor(rng.uniform(0, side, (n, cells, 12, 2)).astype(np.float32), device="cuda")
+    t_color = torch.as_tensor(rng.uniform(0, 1, (n, cells, 3)).astype(np.float32), device="cuda")
+    t_opac = torch.as_tensor(rng.uniform(0, 1, (n, cells)).astype(np.float32), device="cuda")
+    out = {}
+    for engine in (0, 1):
+        bs.debug_gemm_engine(engine)
+        head = torch.empty(n, cells, 32, device="cuda")
+        bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), head)
+        loss = torch.zeros((), dtype=torch.float64, device="cuda")
+        bs.net_train_step(net.w, net.w_bf16, net.g, x, t_ctrl, t_color, t_opac, net.ws(n, side), loss)
+        torch.cuda.synchronize()
+        out[engine] = (head.cpu().double(), [g.cpu().double() for g in net.g], float(loss))
+    timeouts = bs.debug_gemm_engine(1)
+    assert timeouts == 0
+    h0, g0, l0 = out[0]
+    h1, g1, l1 = out[1]
+    assert float((h1 - h0).abs().max() / h0.abs().max()) <= 5e-3
+    assert abs(l1 - l0) <= 5e-3 * abs(l0)
+    for l in range(6):
+        err = float((g1[l] - g0[l]).abs().max() / g0[l].abs().max())
+        cos = float(g1[l] @ g0[l] / (g1[l].norm() * g0[l].norm()))
+        print(f"layer {l}: tcgen05 vs mma.sync rel {err:.2e}, cosine {cos:.7f}")
+        assert err <= 2e-2 and cos >= 0.9999, l
