@@ -642,10 +642,12 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
                             size_t ws_bytes, const bs_net_grad *grad, double *loss_out, bs_stream stream);
 
 /* Test hook: the engine of the network's GEMMs for later calls in this
- * process, 1 = tcgen05 (the default: 128 x 64 tiles, accumulators in tensor
- * memory), 0 = mma.sync (64 x 64 tiles, accumulators in registers), and
- * (timeouts_out, HOST, may be NULL) how many tcgen05 tiles so far gave up a
- * bounded wait on their MMAs (their results were not stored; 0 expected). */
+ * process: 1 (the default) tcgen05 (128 x 64 tiles, accumulators in tensor
+ * memory) for GEMMs whose reduction per CTA is at least 1024 long and
+ * mma.sync (64 x 64 tiles, accumulators in registers) for the shorter ones;
+ * 2 tcgen05 always; 0 mma.sync always.  timeouts_out (HOST, may be NULL):
+ * how many tcgen05 tiles so far gave up a bounded wait on their MMAs (their
+ * results were not stored; 0 expected). */
 bs_status bs_debug_gemm_engine(int32_t engine, int64_t *timeouts_out);
 
 /* Synchronise the stream and read the device status word of a binning

@@ -33,6 +33,11 @@ constexpr int kGemmThreads = 128;
 
 __device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
 
+// A decoded operand row (its meaning is the op's; a < 0: a row past the matrix).
+struct Row {
+  int a, b, c, d;
+};
+
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -42,9 +47,11 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 }
 
 // C[m][n] = sum_k A[m][k] B[n][k] over k in the op's range for blockIdx.z.
-// Op: M, N; k_begin(z), k_end(z) (multiples of 8); load_a(m, k) / load_b(n, k):
-// the 8 bf16 at k..k+7 of row m / n (zero outside); store(m, n, v0, v1):
-// the results at (m, n) and (m, n + 1) (n even).
+// Op: k_begin(z), k_end(z) (multiples of 8); row_a(m) / row_b(n): what a row
+// needs to be read, decoded once per thread before the K loop (a row with
+// a < 0 reads as zeros); load_a(row, k) / load_b(row, k): the 8 bf16 at
+// k..k+7 of the row; store(m, n, v0, v1): the results at (m, n) and
+// (m, n + 1) (n even).
 template <class Op>
 __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const Op op) {
   __shared__ __align__(16) __nv_bfloat16 sA[kBM][kSK];
@@ -64,12 +71,19 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const Op op) {
   // each thread stages two 16-byte vectors of A and two of B per chunk:
   // vector v = tid + 128 i covers row v / 4, columns 8 (v % 4) .. + 7
   uint4 ra[2], rb[2];
+  Row rowa[2], rowb[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int row = (tid + kGemmThreads * i) >> 2;
+    rowa[i] = op.row_a(m0 + row);
+    rowb[i] = op.row_b(n0 + row);
+  }
   auto fetch = [&](int k0) {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      const int v = tid + kGemmThreads * i, row = v >> 2, kk = k0 + 8 * (v & 3);
-      ra[i] = kk < ke ? op.load_a(m0 + row, kk) : zero4();
-      rb[i] = kk < ke ? op.load_b(n0 + row, kk) : zero4();
+      const int v = tid + kGemmThreads * i, kk = k0 + 8 * (v & 3);
+      ra[i] = kk < ke ? op.load_a(rowa[i], kk) : zero4();
+      rb[i] = kk < ke ? op.load_b(rowb[i], kk) : zero4();
     }
   };
   if (kb < ke) fetch(kb);
@@ -117,7 +131,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const Op op) {
 }
 
 // ---- the same GEMM on the 5th-generation tensor cores (tcgen05) ----
-// A CTA of four warps computes a 128 x 64 tile.  Per 32-wide K chunk every
+// A CTA of eight warps computes a 128 x 64 tile.  Per 32-wide K chunk every
 // thread gathers its share of A (128 x 32) and B (64 x 32) with the op's
 // load functions into shared memory in the canonical K-major layout without
 // swizzle: 8 x 16-byte core matrices, the core matrix of rows 8i..8i+7 and
@@ -126,10 +140,11 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const Op op) {
 // float32 accumulator in tensor memory) per chunk and commits them to the
 // chunk's mbarrier; two stages, so the gather of a chunk overlaps the MMAs
 // of the previous one.  The epilogue reads the accumulator back with
-// tcgen05.ld (warp w owns tensor-memory lanes 32w..32w+31, the tile's rows)
-// and hands it to the op's store.  Every wait on an mbarrier is bounded; a
+// tcgen05.ld (warp w reads tensor-memory lanes 32 (w % 4).., the tile's
+// rows, and columns 32 (w / 4)..+31) and hands it to the op's store.  Every wait on an mbarrier is bounded; a
 // wait that gives up counts in *err and the tile is not stored.
 constexpr int kUM = 128, kUN = 64, kUK = 32;
+constexpr int kUThreads = 256;  // eight warps gather; warps w and w + 4 share tensor-memory lanes 32 (w % 4)..
 constexpr uint32_t kUmmaLbo = 128, kUmmaSbo = 512;          // bytes: next 8 K columns / next 8 rows
 constexpr uint32_t kUmmaCols = 64;                          // tensor-memory columns (float32 accumulators)
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -184,7 +199,7 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
 __device__ __forceinline__ uint32_t core_off(int r, int j) { return (uint32_t)((r >> 3) * kUmmaSbo + j * kUmmaLbo + (r & 7) * 16); }
 
 template <class Op>
-__global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, unsigned int *err) {
+__global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsigned int *err) {
   __shared__ __align__(128) uint8_t sA[2][kUM * kUK * 2];
   __shared__ __align__(128) uint8_t sB[2][kUN * kUK * 2];
   __shared__ __align__(8) uint64_t bar[2];
@@ -207,19 +222,20 @@ __global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, un
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  // A: 512 vectors (row v / 4, columns 8 (v % 4)..), four per thread; B: 256, two
-  uint4 ra[4], rb[2];
+  // A: 512 vectors (row v / 4, columns 8 (v % 4)..), two per thread; B: 256, one
+  uint4 ra[2], rb;
+  Row rowa[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) rowa[i] = op.row_a(m0 + ((tid + kUThreads * i) >> 2));
+  const Row rowb = op.row_b(n0 + (tid >> 2));
   auto fetch = [&](int k0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int v = tid + kGemmThreads * i, row = v >> 2, kk = k0 + 8 * (v & 3);
-      ra[i] = kk < ke ? op.load_a(m0 + row, kk) : zero4();
-    }
-#pragma unroll
     for (int i = 0; i < 2; ++i) {
-      const int v = tid + kGemmThreads * i, row = v >> 2, kk = k0 + 8 * (v & 3);
-      rb[i] = kk < ke ? op.load_b(n0 + row, kk) : zero4();
+      const int v = tid + kUThreads * i, kk = k0 + 8 * (v & 3);
+      ra[i] = kk < ke ? op.load_a(rowa[i], kk) : zero4();
     }
+    const int kk = k0 + 8 * (tid & 3);
+    rb = kk < ke ? op.load_b(rowb, kk) : zero4();
   };
   const int n_chunks = ke > kb ? (ke - kb + kUK - 1) / kUK : 0;
   bool ok = true;
@@ -234,15 +250,11 @@ __global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, un
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int v = tid + kGemmThreads * i;
+    for (int i = 0; i < 2; ++i) {
+      const int v = tid + kUThreads * i;
       *reinterpret_cast<uint4 *>(sA[st] + core_off(v >> 2, v & 3)) = ra[i];
     }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int v = tid + kGemmThreads * i;
-      *reinterpret_cast<uint4 *>(sB[st] + core_off(v >> 2, v & 3)) = rb[i];
-    }
+    *reinterpret_cast<uint4 *>(sB[st] + core_off(tid >> 2, tid & 3)) = rb;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the stores, visible to the tensor cores
     __syncthreads();
     if (tid == 0) {
@@ -275,12 +287,13 @@ __global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, un
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const bool store = __syncthreads_and(ok);
   if (store) {
-    const int m = m0 + warp * 32 + lane;
+    const int q = warp & 3, half = warp >> 2;
+    const int m = m0 + q * 32 + lane;
 #pragma unroll
-    for (int col = 0; col < kUN; col += 8) {
+    for (int col = 32 * half; col < 32 * half + 32; col += 8) {
       uint32_t v[8];
       if (n_chunks > 0) {
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col;
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
             "tcgen05.wait::ld.sync.aligned;\n"
@@ -301,25 +314,18 @@ __global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, un
 }
 
 // ---- the operations ----
+// lcin, lcout, lks: log2 of Cin, Cout, KS (all powers of two here)
 struct Geom {
   int N, Hi, Wi, Cin, Ho, Wo, Cout, KS, S, P;
+  int lcin, lcout, lks;
   __host__ __device__ int M() const { return N * Ho * Wo; }
   __host__ __device__ int K() const { return KS * KS * Cin; }
 };
 
-// The 8 input channels ci..ci+7 of tap (ky, kx) of output pixel m (zero in
-// the padding).  Cin is a multiple of 8.
-__device__ __forceinline__ uint4 patch8(const Geom &g, const __nv_bfloat16 *__restrict__ in, int m, int k) {
-  if (m >= g.M()) return zero4();
-  const int hw = g.Ho * g.Wo, n = m / hw, r = m - n * hw, oy = r / g.Wo, ox = r - oy * g.Wo;
-  const int tap = k / g.Cin, ci = k - tap * g.Cin, ky = tap / g.KS, kx = tap - ky * g.KS;
-  const int iy = g.S * oy + ky - g.P, ix = g.S * ox + kx - g.P;
-  if (iy < 0 || iy >= g.Hi || ix < 0 || ix >= g.Wi) return zero4();
-  return *reinterpret_cast<const uint4 *>(in + (((size_t)n * g.Hi + iy) * g.Wi + ix) * g.Cin + ci);
-}
-
 // Forward: out = act(patch . w^T + b).  Relu: bf16 NHWC output with ReLU;
-// else float32 [M][Cout] (the head).
+// else float32 [M][Cout] (the head).  A row is an output pixel: (image,
+// first input row, first input column); k = tap * Cin + ci reads the 8
+// channels ci..ci+7 of tap (ky, kx) (zero in the padding).
 template <bool kRelu>
 struct FwdOp {
   Geom g;
@@ -329,9 +335,21 @@ struct FwdOp {
   float *out_f;
   __device__ int k_begin(int) const { return 0; }
   __device__ int k_end(int) const { return g.K(); }
-  __device__ uint4 load_a(int m, int k) const { return patch8(g, in, m, k); }
-  __device__ uint4 load_b(int n, int k) const {
-    return n < g.Cout ? *reinterpret_cast<const uint4 *>(w + (size_t)n * g.K() + k) : zero4();
+  __device__ Row row_a(int m) const {
+    if (m >= g.M()) return Row{-1, 0, 0, 0};
+    const int hw = g.Ho * g.Wo, n = m / hw, r = m - n * hw, oy = r / g.Wo, ox = r - oy * g.Wo;
+    return Row{n, g.S * oy - g.P, g.S * ox - g.P, 0};
+  }
+  __device__ uint4 load_a(const Row &r, int k) const {
+    if (r.a < 0) return zero4();
+    const int tap = k >> g.lcin, ci = k & (g.Cin - 1);
+    const int iy = r.b + (tap >> g.lks), ix = r.c + (tap & (g.KS - 1));
+    if (iy < 0 || iy >= g.Hi || ix < 0 || ix >= g.Wi) return zero4();
+    return *reinterpret_cast<const uint4 *>(in + (((size_t)r.a * g.Hi + iy) * g.Wi + ix) * g.Cin + ci);
+  }
+  __device__ Row row_b(int n) const { return Row{n < g.Cout ? n : -1, 0, 0, 0}; }
+  __device__ uint4 load_b(const Row &r, int k) const {
+    return r.a >= 0 ? *reinterpret_cast<const uint4 *>(w + (size_t)r.a * g.K() + k) : zero4();
   }
   __device__ void store(int m, int n, float v0, float v1) const {
     if (m >= g.M() || n >= g.Cout) return;
@@ -353,7 +371,8 @@ struct FwdOp {
 // likewise in x), so din = sum over k = (a, b, co) of dout[oy, ox, co] wq[ci][k]
 // with wq the class's weights gathered by net_dgrad_weights_kernel.  The
 // result is multiplied by the ReLU mask of the input activation (the gradient
-// of the previous layer's pre-activation).
+// of the previous layer's pre-activation).  A row is an input pixel of the
+// class: (image, hy + qy, hx + qx).
 struct DgradOp {
   Geom g;
   int qy, qx;
@@ -369,17 +388,22 @@ struct DgradOp {
     iy = 2 * hy + qy;
     ix = 2 * hx + qx;
   }
-  __device__ uint4 load_a(int m, int k) const {
-    if (m >= Mh()) return zero4();
+  __device__ Row row_a(int m) const {
+    if (m >= Mh()) return Row{-1, 0, 0, 0};
     int n, iy, ix;
     pixel(m, n, iy, ix);
-    const int tp = k / g.Cout, co = k - tp * g.Cout, a = tp >> 1, b = tp & 1;
-    const int oy = (iy >> 1) + qy - a, ox = (ix >> 1) + qx - b;
-    if (oy < 0 || oy >= g.Ho || ox < 0 || ox >= g.Wo) return zero4();
-    return *reinterpret_cast<const uint4 *>(dout + (((size_t)n * g.Ho + oy) * g.Wo + ox) * g.Cout + co);
+    return Row{n, (iy >> 1) + qy, (ix >> 1) + qx, 0};
   }
-  __device__ uint4 load_b(int n, int k) const {
-    return n < g.Cin ? *reinterpret_cast<const uint4 *>(wq + (size_t)n * 4 * g.Cout + k) : zero4();
+  __device__ uint4 load_a(const Row &r, int k) const {
+    if (r.a < 0) return zero4();
+    const int tp = k >> g.lcout, co = k & (g.Cout - 1);
+    const int oy = r.b - (tp >> 1), ox = r.c - (tp & 1);
+    if (oy < 0 || oy >= g.Ho || ox < 0 || ox >= g.Wo) return zero4();
+    return *reinterpret_cast<const uint4 *>(dout + (((size_t)r.a * g.Ho + oy) * g.Wo + ox) * g.Cout + co);
+  }
+  __device__ Row row_b(int n) const { return Row{n < g.Cin ? n : -1, 0, 0, 0}; }
+  __device__ uint4 load_b(const Row &r, int k) const {
+    return r.a >= 0 ? *reinterpret_cast<const uint4 *>(wq + (size_t)r.a * 4 * g.Cout + k) : zero4();
   }
   __device__ void store(int m, int ci, float v0, float v1) const {
     if (m >= Mh() || ci >= g.Cin) return;
@@ -400,11 +424,13 @@ struct HeadDgradOp {
   __nv_bfloat16 *din;
   __device__ int k_begin(int) const { return 0; }
   __device__ int k_end(int) const { return Cout; }
-  __device__ uint4 load_a(int m, int k) const {
-    return m < M ? *reinterpret_cast<const uint4 *>(dout + (size_t)m * Cout + k) : zero4();
+  __device__ Row row_a(int m) const { return Row{m < M ? m : -1, 0, 0, 0}; }
+  __device__ uint4 load_a(const Row &r, int k) const {
+    return r.a >= 0 ? *reinterpret_cast<const uint4 *>(dout + (size_t)r.a * Cout + k) : zero4();
   }
-  __device__ uint4 load_b(int n, int k) const {
-    return n < Cin ? *reinterpret_cast<const uint4 *>(wt + (size_t)n * Cout + k) : zero4();
+  __device__ Row row_b(int n) const { return Row{n < Cin ? n : -1, 0, 0, 0}; }
+  __device__ uint4 load_b(const Row &r, int k) const {
+    return r.a >= 0 ? *reinterpret_cast<const uint4 *>(wt + (size_t)r.a * Cout + k) : zero4();
   }
   __device__ void store(int m, int ci, float v0, float v1) const {
     if (m >= M || ci >= Cin) return;
@@ -424,19 +450,40 @@ struct WgradOp {
   float *dw;
   __device__ int k_begin(int z) const { return z * chunk; }
   __device__ int k_end(int z) const { return min(g.M(), (z + 1) * chunk); }
-  __device__ uint4 load_a(int co, int m) const {  // dout[m..m+7][co]
-    if (co >= g.Cout) return zero4();
+  __device__ Row row_a(int co) const { return Row{co < g.Cout ? co : -1, 0, 0, 0}; }
+  __device__ uint4 load_a(const Row &r, int m) const {  // dout[m..m+7][co]
+    if (r.a < 0) return zero4();
+    const int co = r.a;
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
       v[i] = m + i < g.M() ? dout[(size_t)(m + i) * g.Cout + co] : __float2bfloat16(0.f);
     return *reinterpret_cast<const uint4 *>(v);
   }
-  __device__ uint4 load_b(int kk, int m) const {  // patch[m..m+7][kk]
-    if (kk >= g.K()) return zero4();
-    const int tap = kk / g.Cin, ci = kk - tap * g.Cin, ky = tap / g.KS, kx = tap - ky * g.KS;
+  __device__ Row row_b(int kk) const {  // (ci, ky, kx) of weight column kk
+    if (kk >= g.K()) return Row{-1, 0, 0, 0};
+    const int tap = kk >> g.lcin;
+    return Row{kk & (g.Cin - 1), tap >> g.lks, tap & (g.KS - 1), 0};
+  }
+  __device__ uint4 load_b(const Row &rw, int m) const {  // patch[m..m+7][kk]
+    if (rw.a < 0) return zero4();
+    const int ci = rw.a, ky = rw.b, kx = rw.c;
     const int hw = g.Ho * g.Wo;
     __align__(16) __nv_bfloat16 v[8];
+    {  // the 8 pixels in one output row: one input row, x in steps of S
+      const int n = m / hw, r = m - n * hw, oy = r / g.Wo, ox = r - oy * g.Wo;
+      if (m + 7 < g.M() && ox + 7 < g.Wo) {
+        const int iy = g.S * oy + ky - g.P;
+        if (iy < 0 || iy >= g.Hi) return zero4();
+        const __nv_bfloat16 *row = in + (((size_t)n * g.Hi + iy) * g.Wi) * g.Cin + ci;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int ix = g.S * (ox + i) + kx - g.P;
+          v[i] = (ix >= 0 && ix < g.Wi) ? row[(size_t)ix * g.Cin] : __float2bfloat16(0.f);
+        }
+        return *reinterpret_cast<const uint4 *>(v);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       v[i] = __float2bfloat16(0.f);
@@ -457,18 +504,37 @@ struct WgradOp {
   }
 };
 
-// The GEMM engine: 1 = tcgen05 (default), 0 = mma.sync (kept as a cross-check
-// for the tests, selected with bs_debug_gemm_engine).
+// The GEMM engine: 1 (default) = tcgen05 for a reduction of at least
+// kUmmaMinK per CTA, mma.sync below (a tcgen05 CTA pays a fixed cost for its
+// tensor memory, barriers and read-back, which a few K chunks do not
+// amortise); 2 = tcgen05 always, 0 = mma.sync always (the test hook
+// bs_debug_gemm_engine selects them).
 int g_gemm_engine = 1;
+constexpr int kUmmaMinK = 1024;
 __device__ unsigned int g_umma_timeouts;
 
+// The device address of g_umma_timeouts, looked up once per device.
+bs_status umma_err_ptr(unsigned int **out) {
+  constexpr int kMaxDev = 64;
+  static unsigned int *cache[kMaxDev] = {};
+  int dev = 0;
+  BS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) {
+    set_error("device %d: at most %d devices supported", dev, kMaxDev);
+    return BS_ERR_UNSUPPORTED;
+  }
+  if (!cache[dev]) BS_CUDA(cudaGetSymbolAddress((void **)&cache[dev], g_umma_timeouts));
+  *out = cache[dev];
+  return BS_OK;
+}
+
 template <class Op>
-bs_status run_gemm(const Op &op, int M, int N, int splits, cudaStream_t s) {
-  if (g_gemm_engine == 1) {
+bs_status run_gemm(const Op &op, int M, int N, int K, int splits, cudaStream_t s) {
+  if (g_gemm_engine == 2 || (g_gemm_engine == 1 && K >= kUmmaMinK)) {
     unsigned int *err = nullptr;
-    BS_CUDA(cudaGetSymbolAddress((void **)&err, g_umma_timeouts));
+    BS_TRY(umma_err_ptr(&err));
     const dim3 grid((unsigned)div_up(M, kUM), (unsigned)div_up(N, kUN), (unsigned)splits);
-    umma_gemm_kernel<Op><<<grid, kGemmThreads, 0, s>>>(op, err);
+    umma_gemm_kernel<Op><<<grid, kUThreads, 0, s>>>(op, err);
     BS_LAUNCHED("umma_gemm_kernel");
     return BS_OK;
   }
@@ -613,6 +679,9 @@ Geom net_layer(int l, int n, int side) {
     g.S = 1;
     g.P = 0;
   }
+  g.lcin = bit_length((uint64_t)g.Cin) - 1;
+  g.lcout = bit_length((uint64_t)g.Cout) - 1;
+  g.lks = bit_length((uint64_t)g.KS) - 1;
   return g;
 }
 
@@ -685,11 +754,11 @@ bs_status net_forward(const bs_net *net, const float *patches, int n, int side, 
   for (int l = 0; l < 5; ++l) {
     const Geom g = net_layer(l, n, side);
     const FwdOp<true> op{g, ws.act[l], wbf(net, l), net->w[l] + (size_t)g.Cout * g.K(), ws.act[l + 1], nullptr};
-    BS_TRY(run_gemm(op, g.M(), g.Cout, 1, s));
+    BS_TRY(run_gemm(op, g.M(), g.Cout, g.K(), 1, s));
   }
   const Geom g = net_layer(5, n, side);
   const FwdOp<false> op{g, ws.act[5], wbf(net, 5), net->w[5] + (size_t)g.Cout * g.K(), nullptr, ws.head};
-  return run_gemm(op, g.M(), g.Cout, 1, s);
+  return run_gemm(op, g.M(), g.Cout, g.K(), 1, s);
 }
 
 }  // namespace
@@ -697,7 +766,7 @@ bs_status net_forward(const bs_net *net, const float *patches, int n, int side, 
 extern "C" {
 
 bs_status bs_debug_gemm_engine(int32_t engine, int64_t *timeouts_out) {
-  if (engine != 0 && engine != 1) return net_invalid("engine must be 0 (mma.sync) or 1 (tcgen05)");
+  if (engine < 0 || engine > 2) return net_invalid("engine must be 0 (mma.sync), 1 (by reduction length) or 2 (tcgen05)");
   g_gemm_engine = engine;
   if (timeouts_out) {
     unsigned int t = 0;
@@ -777,21 +846,21 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
     const Geom g = net_layer(5, n, side);
     const int chunk = std::max(kBK, (int)div_up64(div_up64(g.M(), 152), kBK) * kBK);
     const WgradOp op{g, chunk, w.dhead, w.act[5], grad->g[5]};
-    BS_TRY(run_gemm(op, g.Cout, g.K(), div_up(g.M(), chunk), s));
+    BS_TRY(run_gemm(op, g.Cout, g.K(), chunk, div_up(g.M(), chunk), s));
     net_bias_grad_kernel<<<dim3(128, div_up(g.Cout, 128)), 128, 0, s>>>(w.dhead, g.M(), g.Cout,
                                                                         grad->g[5] + (size_t)g.Cout * g.K());
     BS_LAUNCHED("net_bias_grad_kernel");
     net_transpose_kernel<<<div_up(g.Cin * g.Cout, 256), 256, 0, s>>>(net->w[5], g.Cin, g.Cout, w.wq);
     BS_LAUNCHED("net_transpose_kernel");
     const HeadDgradOp dop{g.M(), g.Cin, g.Cout, w.dhead, w.wq, w.act[5], w.dact[5]};
-    BS_TRY(run_gemm(dop, g.M(), g.Cin, 1, s));
+    BS_TRY(run_gemm(dop, g.M(), g.Cin, g.Cout, 1, s));
   }
   for (int l = 4; l >= 0; --l) {
     const Geom g = net_layer(l, n, side);
     const __nv_bfloat16 *dout = w.dact[l + 1];
     const int chunk = std::max(kBK, (int)div_up64(div_up64(g.M(), 304), kBK) * kBK);
     const WgradOp op{g, chunk, dout, w.act[l], grad->g[l]};
-    BS_TRY(run_gemm(op, g.Cout, g.K(), div_up(g.M(), chunk), s));
+    BS_TRY(run_gemm(op, g.Cout, g.K(), chunk, div_up(g.M(), chunk), s));
     net_bias_grad_kernel<<<dim3(256, div_up(g.Cout, 128)), 128, 0, s>>>(dout, g.M(), g.Cout,
                                                                         grad->g[l] + (size_t)g.Cout * g.K());
     BS_LAUNCHED("net_bias_grad_kernel");
@@ -801,7 +870,7 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
     BS_LAUNCHED("net_dgrad_weights_kernel");
     for (int q = 0; q < 4; ++q) {
       const DgradOp dop{g, q >> 1, q & 1, dout, w.wq + (size_t)q * g.Cin * 4 * g.Cout, w.act[l], w.dact[l]};
-      BS_TRY(run_gemm(dop, g.N * (g.Hi / 2) * (g.Wi / 2), g.Cin, 1, s));
+      BS_TRY(run_gemm(dop, g.N * (g.Hi / 2) * (g.Wi / 2), g.Cin, 4 * g.Cout, 1, s));
     }
   }
   return BS_OK;

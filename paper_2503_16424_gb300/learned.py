@@ -75,16 +75,39 @@ def _closed_set(ctrl, color, opac, device):
                                         closed_color=color, closed_opac=opac), device=device)
 
 
+_POOL = None
+
+
+def _target(args):
+    seed, n_shapes = args
+    return synth.procedural_target(seed, SIDE, SIDE, n_shapes)
+
+
+def _targets(seeds, n_shapes, workers):
+    """Procedural patches, drawn by a process pool when workers > 1 (spawned
+    processes: they share nothing with this process's CUDA context)."""
+    global _POOL
+    if workers <= 1 or len(seeds) < 8:
+        return np.stack([_target((s, n_shapes)) for s in seeds])
+    if _POOL is None:
+        import multiprocessing as mp
+        _POOL = mp.get_context("spawn").Pool(workers)
+    return np.stack(_POOL.map(_target, [(s, n_shapes) for s in seeds], chunksize=max(1, len(seeds) // workers)))
+
+
 def make_pairs(n: int, seed: int, steps: int = 200, n_shapes: int = 6, device="cuda", batch: int = 64,
-               sample=(4, 8)):
+               sample=(4, 8), workers: int = 0):
     """n (patch, optimised curves) pairs.  Returns device tensors patches
     [n, 3, 256, 256], ctrl [n, 64, 12, 2], color [n, 64, 3], opac [n, 64];
-    control points clamped to the network's reach around their cell."""
+    control points clamped to the network's reach around their cell.
+    workers: host processes drawing the patches (0: the host's cores)."""
+    import os
+    workers = workers or min(16, os.cpu_count() or 1)
     rows, kc = sample
     out = {"patches": [], "ctrl": [], "color": [], "opac": []}
     for b0 in range(0, n, batch):
         m = min(batch, n - b0)
-        tg = np.stack([synth.procedural_target(seed * 100003 + b0 + i, SIDE, SIDE, n_shapes) for i in range(m)])
+        tg = _targets([seed * 100003 + b0 + i for i in range(m)], n_shapes, workers)
         ctrl, color, opac = circle_init(m, SIDE, tg)
         curves = _closed_set(ctrl, color, opac, device)
         images = [bs.BatchImage(SIDE, SIDE, 0, CELLS, bs.SampleCfg(g_open=2, rows_closed=rows, k_closed=kc))
