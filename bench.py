@@ -43,9 +43,9 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of each render kernel on this
 # workload, from one ncu capture of the current kernel
-# (profiles/render_bwd_kernel_hires_2048_4096.md); None where no capture of
+# (profiles/render_bwd_kernel_hires_2048_4096.md, render_fwd_kernel_hires_2048_4096.md); None where no capture of
 # the current kernel exists.
-DRAM_BYTES_PER_LAUNCH = {"render_bwd_kernel": 131236096, "render_fwd_kernel": None}
+DRAM_BYTES_PER_LAUNCH = {"render_bwd_kernel": 131174912, "render_fwd_kernel": 171156480}
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
