@@ -294,9 +294,63 @@ def run_ours(args, rank, world):
     out["gpu_launches"] = per_step * args.steps
     if not args.no_batched:
         out["batched"] = run_batched(dev, args)
+    if not args.no_paper_shape:
+        out["paper_shape"] = run_paper_shape(dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(side=8)
     return out
+
+
+# The paper's own timings (RTX 4090 per the teaser caption; context, not a
+# target): Table 1 at 2040 x 1344 with 2048 curves, forward and backward ms;
+# Table 4, 2048 closed curves with R interior rows, forward (with gradients)
+# and backward ms, resolution not stated.
+PAPER_MS = {"open_2048": (4.5, 4.7, "Table 1"), "closed_2048_R20": (14.1, 24.58, "Table 1"),
+            "closed_2048_R40": (14.79, 25.06, "Table 4"), "closed_2048_R80": (27.01, 33.40, "Table 4")}
+
+
+def run_paper_shape(dev, steps=10, warmup=3):
+    """Forward (draw order, sampling, binning, blend with the L2 term) and
+    backward (blend backward, sampling backward) ms on the paper's shapes:
+    2040 x 1344 with 2048 open curves of 64 Gaussians, or 2048 closed curves
+    with R = 20, 40, 80 interior rows of 32 samples (Section 4, Table 1,
+    Table 4)."""
+    import torch
+    from paper_2503_16424_gb300 import bs, synth
+    from paper_2503_16424_gb300.raster import Rasterizer
+    W, H = 2040, 1344
+    target = torch.as_tensor(synth.procedural_target(21, W, H, 50), device=dev)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, (no, nc, g, rows, kc) in {"open_2048": (2048, 0, 64, 4, 8), "closed_2048_R20": (0, 2048, 16, 22, 32),
+                                        "closed_2048_R40": (0, 2048, 16, 42, 32),
+                                        "closed_2048_R80": (0, 2048, 16, 82, 32)}.items():
+        curves = bs.CurveSet.from_arrays(synth.make_curves(21, W, H, no, nc, style="local").as_dict(), device=dev)
+        cfg = bs.SampleCfg(g_open=g, rows_closed=rows, k_closed=kc)
+        r = Rasterizer(bs.Canvas(W, H, 16), cfg, no, nc, device=dev, pair_capacity=1 << 24)
+        grad = curves.zeros_like()
+        ev = []
+        for i in range(warmup + steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            r.rank, r.first = bs.curve_order(curves, cfg)
+            bs.sample_curves(curves, cfg, r.first, out=r.gauss)
+            r.binning.run(r.gauss)
+            bs.render_fwd_l2(r.gauss, r.canvas, r.binning, target, out=(r.img, r.T, r.nc), dimg=r.dimg, loss=r.loss)
+            e[1].record(stream)
+            r.backward(curves, r.dimg, grad)
+            e[2].record(stream)
+            if i >= warmup:
+                ev.append(e)
+        torch.cuda.synchronize()
+        fwd = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+        bwd = float(np.median([e[1].elapsed_time(e[2]) for e in ev]))
+        pf, pb, src = PAPER_MS[name]
+        out[name] = {"gaussians": r.n_gauss, "pairs": r.binning.n_pairs, "fwd_ms": round(fwd, 4),
+                     "bwd_ms": round(bwd, 4), "paper_fwd_ms": pf, "paper_bwd_ms": pb, "paper_source": src}
+        del r
+    return {"canvas": f"{W}x{H}", "note": "context: the paper's numbers are another GPU's (RTX 4090), "
+                                          "Table 4's resolution is not stated", "cases": out}
 
 
 def run_batched(dev, args):
@@ -453,6 +507,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-paper-shape", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=20)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -98,7 +98,7 @@ typedef struct {
   int32_t g_open;      /* K: samples per open curve, 2..1024                      */
   int32_t rows_closed; /* R + 2: rows of a closed curve incl. both boundaries, >= 2 */
   int32_t k_closed;    /* K: samples per row of a closed curve, >= 2;
-                          rows_closed * k_closed <= 2048                           */
+                          rows_closed * k_closed <= 3072                           */
   float rho;           /* the density constant of Eq. 7, > 0                      */
   float cov_eps;       /* isotropic covariance floor in px^2 (Sigma += eps I), >= 0 */
 } bs_sample_cfg;

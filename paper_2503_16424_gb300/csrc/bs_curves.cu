@@ -1,7 +1,8 @@
 // Curves -> Gaussians: draw order (Section 3.3 "depth from area"), sampling
 // (Section 3.3, Eq. 3-8, Eq. 11-12) and its backward.
 //
-// One CTA per curve.  The CTA evaluates the curve's sample points X into
+// One CTA per curve (64 threads, 256 for curves of 512 samples or more).
+// The CTA evaluates the curve's sample points X into
 // shared memory, then each thread turns one sample and its neighbours into
 // a Gaussian record (forward), or pushes one Gaussian's gradient back to the
 // sample points and from there, with the Bernstein weights of Eq. 1-2, to the
@@ -21,7 +22,10 @@
 namespace bs {
 namespace {
 
-constexpr int kCurveThreads = 64;
+constexpr int kCurveThreads = 64;       // threads per curve
+constexpr int kCurveThreadsWide = 256;  // for curves of kWideSamples samples or more
+constexpr int kWideSamples = 512;
+__host__ __device__ inline int curve_threads(int n_max) { return n_max >= kWideSamples ? kCurveThreadsWide : kCurveThreads; }
 
 struct Cfg {
   int g_open, rows, kc;
@@ -226,7 +230,7 @@ __device__ __forceinline__ Cfg batch_cfg(const BatchImage *__restrict__ tab, int
 
 // tab == nullptr: one canvas, sampling cfg; else a batch, each curve with
 // its image's sampling (dynamic shared memory sized for the largest).
-__global__ void __launch_bounds__(kCurveThreads) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss, int n_max,
+__global__ void __launch_bounds__(kCurveThreadsWide) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss, int n_max,
                                                                    int k_max, const BatchImage *tab = nullptr,
                                                                    int n_images = 0) {
   extern __shared__ double2 smem_fwd[];
@@ -273,7 +277,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // pieces of every difference that uses it.  Phase 3: each control point
 // coordinate gathers the Bernstein-weighted (and, for closed rows,
 // tau-weighted, Eq. 4) gradients of the sample points it moves.
-__global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
+__global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
                                                                    bs_curves_grad g, int n_max, int k_max,
                                                                    const BatchImage *tab = nullptr,
                                                                    int n_images = 0) {
@@ -396,6 +400,29 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
   const float2 *dX = GM;
   const int npts = closed ? 12 : 10;
   const int S = closed ? 2 : 3;
+  // Row r of a closed curve is (1 - tau_r) A + tau_r B (Eq. 4), so the
+  // gradient of a boundary point through column k is the same Bernstein
+  // weight times sum_r (1 - tau_r) dX_rk (boundary A) or sum_r tau_r dX_rk
+  // (boundary B): those column sums first (one thread per column), kept in
+  // the no longer needed GE / GT planes, then every control point runs over
+  // the K columns only.
+  float2 *colA = GE, *colB = GT;
+  if (closed) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+      for (int r = 0; r < R2; ++r) {
+        const float tau = (float)m.taut[r];
+        const float2 dx = dX[r * K + k];
+        a.x += (1.f - tau) * dx.x;
+        a.y += (1.f - tau) * dx.y;
+        b.x += tau * dx.x;
+        b.y += tau * dx.y;
+      }
+      colA[k] = a;
+      colB[k] = b;
+    }
+    __syncthreads();
+  }
   for (int q = threadIdx.x; q < 2 * npts; q += blockDim.x) {
     const int p = q >> 1, comp = q & 1;
     float acc = 0.f;
@@ -414,11 +441,7 @@ __global__ void __launch_bounds__(kCurveThreads) sample_bwd_kernel(bs_curves c, 
         const bool use_a = ja >= 0 && ia >= 0 && ia <= 3, use_b = jb >= 0 && ib >= 0 && ib <= 3;
         if (!use_a && !use_b) continue;
         const float wa = use_a ? (float)m.Wt[4 * k + ia] : 0.f, wb = use_b ? (float)m.Wt[4 * k + ib] : 0.f;
-        for (int r = 0; r < R2; ++r) {
-          const float tau = (float)m.taut[r];
-          const float2 dx = dX[r * K + k];
-          acc += (wa * (1.f - tau) + wb * tau) * (comp ? dx.y : dx.x);
-        }
+        acc += wa * (comp ? colA[k].y : colA[k].x) + wb * (comp ? colB[k].y : colB[k].x);
       }
     }
     if (!closed) g.open_ctrl[(size_t)curve * 20 + q] = acc;
@@ -653,7 +676,7 @@ bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float 
   const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
   const size_t smem = curve_smem_bytes(n_max, k_max, cfg.rows_closed, false);
   BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-  sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), gauss, n_max, k_max);
+  sample_fwd_kernel<<<n, curve_threads(n_max), smem, s>>>(c, to_cfg(cfg), gauss, n_max, k_max);
   BS_LAUNCHED("sample_fwd_kernel");
   return BS_OK;
 }
@@ -665,7 +688,7 @@ bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const 
   const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
   const size_t smem = curve_smem_bytes(n_max, k_max, cfg.rows_closed, true);
   BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-  sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, to_cfg(cfg), dgauss, g, n_max, k_max);
+  sample_bwd_kernel<<<n, curve_threads(n_max), smem, s>>>(c, to_cfg(cfg), dgauss, g, n_max, k_max);
   BS_LAUNCHED("sample_bwd_kernel");
   return BS_OK;
 }
@@ -689,7 +712,7 @@ bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, c
   if (n == 0) return BS_OK;
   const size_t smem = curve_smem_bytes(p.n_max, p.k_max, p.rows_max, false);
   BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-  sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, Cfg{}, gauss, p.n_max, p.k_max, table, p.n_images);
+  sample_fwd_kernel<<<n, curve_threads(p.n_max), smem, s>>>(c, Cfg{}, gauss, p.n_max, p.k_max, table, p.n_images);
   BS_LAUNCHED("sample_fwd_kernel");
   return BS_OK;
 }
@@ -700,7 +723,8 @@ bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, c
   if (n == 0) return BS_OK;
   const size_t smem = curve_smem_bytes(p.n_max, p.k_max, p.rows_max, true);
   BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-  sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, Cfg{}, dgauss, g, p.n_max, p.k_max, table, p.n_images);
+  sample_bwd_kernel<<<n, curve_threads(p.n_max), smem, s>>>(c, Cfg{}, dgauss, g, p.n_max, p.k_max, table,
+                                                             p.n_images);
   BS_LAUNCHED("sample_bwd_kernel");
   return BS_OK;
 }

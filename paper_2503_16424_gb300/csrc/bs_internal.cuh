@@ -16,7 +16,7 @@ constexpr float kAlphaMax = 0.99f;          // alpha clamp
 constexpr float kTMin = 1e-4f;              // stop a pixel before T drops below
 constexpr float kExtPad = 0.01f;            // px added to support half extents
 
-constexpr int kMaxSamplesPerCurve = 2048;
+constexpr int kMaxSamplesPerCurve = 3072;  // a closed curve's rows x samples per row
 
 // ---- status plumbing ----
 void set_error(const char *fmt, ...);
