@@ -249,7 +249,10 @@ def run_ours(args, rank, world):
     peaks, src = load_peaks()
     clocks = clk.summary()
     fwd_avg, bwd_avg = float(np.mean(fwd_ms)), float(np.mean(bwd_ms))
-    e_fwd, e_bwd = stats["evals"], stats["n_contrib_sum"]
+    # E per pass: (pixel, list entry) pairs up to each pixel's stop point
+    # (forward: the entry that stops it or the list's end; backward: its
+    # last blended entry), whatever the kernels skip inside a list
+    e_fwd, e_bwd = stats["visits"], stats["n_contrib_sum"]
     fwd_tf = FP32_FLOP_PER_FWD_EVAL * e_fwd / (fwd_avg * 1e-3) / 1e12
     bwd_tf = FP32_FLOP_PER_BWD_EVAL * e_bwd / (bwd_avg * 1e-3) / 1e12
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
@@ -272,7 +275,8 @@ def run_ours(args, rank, world):
                      "peak_source": f"FP32 {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                     f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)"},
         "kernels_ms": {"render_fwd": round(fwd_avg, 4), "render_bwd": round(bwd_avg, 4)},
-        "work": {"fwd_evals": e_fwd, "bwd_evals": e_bwd, "blended": stats["blended"],
+        "work": {"fwd_evals": e_fwd, "bwd_evals": e_bwd, "fwd_evals_performed": stats["evals"],
+                 "blended": stats["blended"],
                  "fwd_tflops": round(fwd_tf, 3), "bwd_tflops": round(bwd_tf, 3)},
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},

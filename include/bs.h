@@ -261,8 +261,10 @@ bs_status bs_render_fwd_l2(const float *gauss, int64_t n_gauss, const bs_canvas 
 /*
  * bs_render_fwd plus work counters, for measurement: stats_out (device,
  * 4 x uint64, zeroed and written) receives [0] the (pixel, list entry)
- * evaluations performed, [1] the entries blended, [2] the sum over tiles of
- * list length x 256 pixels, [3] 0.
+ * evaluations performed (after the block culling), [1] the entries blended,
+ * [2] the sum over tiles of list length x tile pixels, [3] the sum over
+ * pixels of the list entries up to the pixel's stop point (the entry whose
+ * blend would bring its transmittance below 1e-4, or the list's end).
  */
 bs_status bs_render_stats(const float *gauss, int64_t n_gauss, const bs_canvas *canvas,
                           const uint32_t *tile_keys, const uint32_t *tile_ranges,

@@ -44,7 +44,8 @@ def render_pixels(tab: dict, xs, ys, bg=(0.0, 0.0, 0.0), margin: float = 1e-4, m
     """Blend all Gaussians of ``tab`` at pixels (xs[i], ys[i]).
 
     Returns dict(C [n,3], T [n] final transmittance, last [n] index of the
-    last blended Gaussian or -1, n_blend [n], flag [n]).  ``flag`` marks a
+    last blended Gaussian or -1, n_blend [n], flag [n], stop [n] index of the
+    Gaussian at which the pixel stops, or the number of Gaussians).  ``flag`` marks a
     pixel where some threshold decision (the 1/255 skip, the 1e-4 stop, the
     0.99 clamp) lies within a relative ``margin`` of its threshold (``margin_T``
     for the transmittance stop, default ``margin``), so that an fp32
@@ -80,7 +81,7 @@ def render_pixels(tab: dict, xs, ys, bg=(0.0, 0.0, 0.0), margin: float = 1e-4, m
         mT = margin if margin_T is None else margin_T
         near_stop = (torch.abs(T_after - T_MIN) <= mT * T_MIN) & considered & (alpha > 0)
         flag = (near_skip | near_clamp | near_stop).any(dim=1)
-    return dict(C=C, T=T_final, last=last, n_blend=n_blend, flag=flag)
+    return dict(C=C, T=T_final, last=last, n_blend=n_blend, flag=flag, stop=first_stop)
 
 
 def _chunks(n, size):
@@ -91,20 +92,22 @@ def _chunks(n, size):
 def render_image(tab: dict, W: int, H: int, bg=(0.0, 0.0, 0.0), margin=1e-4, margin_T=None,
                  max_entries: int = 1 << 22):
     """Brute-force render of a W x H image.  Returns planar img [3,H,W],
-    T [H,W], last [H,W], flag [H,W] (no autograd)."""
+    T [H,W], last [H,W], flag [H,W], stop [H,W], n_blend [H,W] (no autograd)."""
     ng = max(1, tab["mx"].shape[0])
     chunk = max(1, max_entries // ng)
     ys, xs = torch.meshgrid(torch.arange(H, dtype=torch.float64),
                             torch.arange(W, dtype=torch.float64), indexing="ij")
     xs, ys = xs.reshape(-1), ys.reshape(-1)
-    C, T, last, flag = [], [], [], []
+    C, T, last, flag, stop, nb = [], [], [], [], [], []
     with torch.no_grad():
         for s, e in _chunks(xs.shape[0], chunk):
             r = render_pixels(tab, xs[s:e], ys[s:e], bg, margin, margin_T)
             C.append(r["C"]); T.append(r["T"]); last.append(r["last"]); flag.append(r["flag"])
+            stop.append(r["stop"]); nb.append(r["n_blend"])
     C = torch.cat(C).reshape(H, W, 3).permute(2, 0, 1).contiguous()
     return dict(img=C, T=torch.cat(T).reshape(H, W), last=torch.cat(last).reshape(H, W),
-                flag=torch.cat(flag).reshape(H, W))
+                flag=torch.cat(flag).reshape(H, W), stop=torch.cat(stop).reshape(H, W),
+                n_blend=torch.cat(nb).reshape(H, W))
 
 
 GRAD_KEYS = ("mx", "my", "ux", "uy", "isx", "isy", "o", "col")

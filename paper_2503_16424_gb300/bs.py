@@ -431,7 +431,9 @@ def render_fwd_l2(gauss: torch.Tensor, canvas: Canvas, binning: Binning, target:
 
 
 def render_stats(gauss: torch.Tensor, canvas: Canvas, binning: Binning):
-    """Work counters of a forward blend: dict(evals, blended, tile_px_entries)."""
+    """Work counters of a forward blend: dict(evals (performed), blended,
+    tile_px_entries, visits (entries up to each pixel's stop point),
+    n_contrib_sum)."""
     W, H = canvas.width, canvas.height
     dev = gauss.device
     img = torch.empty(3, H, W, dtype=torch.float32, device=dev)
@@ -443,7 +445,7 @@ def render_stats(gauss: torch.Tensor, canvas: Canvas, binning: Binning):
                                                    _ptr(binning.keys), _ptr(binning.ranges), _ptr(img), _ptr(T),
                                                    _ptr(nc), _ptr(st), _stream()))
     v = st.cpu().tolist()
-    return dict(evals=v[0], blended=v[1], tile_px_entries=v[2], n_contrib_sum=int(nc.sum().item()))
+    return dict(evals=v[0], blended=v[1], tile_px_entries=v[2], visits=v[3], n_contrib_sum=int(nc.sum().item()))
 
 
 def l2_loss_grad(img: torch.Tensor, target: torch.Tensor, dimg=None, loss=None):

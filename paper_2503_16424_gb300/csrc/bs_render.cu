@@ -261,9 +261,10 @@ struct FwdOut {
 };
 
 // The forward blend of one tile.  kStats: also count the (pixel, list
-// entry) evaluations (E), the entries blended, and the entries of the tile
-// list times the tile's pixels, into stats[0..2] (for measurement; same
-// blend otherwise).  kL2: also the L2 term of Eq. 13 on the finished
+// entry) evaluations performed, the entries blended, the entries of the tile
+// list times the tile's pixels, and the entries each pixel visits up to its
+// stop point (the entry that would bring T below 1e-4, or the list's end),
+// into stats[0..3] (for measurement; same blend otherwise).  kL2: also the L2 term of Eq. 13 on the finished
 // pixels: dL/dimg = scale (img - target); returns this thread's sum of
 // (img - target)^2 (0 without kL2).  Starts and ends with every thread of
 // the CTA past a barrier.
@@ -283,12 +284,13 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
   const ThreadPixels<kT> tp = thread_pixels<kT>(v.x0, v.y0, v.W, v.H);
   const uint2 r = v.r;
   float T[kPix], c0[kPix], c1[kPix], c2[kPix];
-  uint32_t last[kPix];
+  uint32_t last[kPix], stop[kStats ? kPix : 1];
 #pragma unroll
   for (int i = 0; i < kPix; ++i) {
     T[i] = 1.f;
     c0[i] = c1[i] = c2[i] = 0.f;
     last[i] = 0;
+    if (kStats) stop[i] = (tp.inside >> i) & 1u ? r.y - r.x : 0u;
   }
   __shared__ uint32_t s_alive[kW];  // per warp: slots (8x4 blocks) with a pixel still blending
   unsigned alive = tp.inside;
@@ -340,6 +342,7 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
         const float Tn = T[q] * (1.f - al);
         if (Tn < kTMin) {
           alive &= ~(1u << q);
+          if (kStats) stop[q] = base - r.x + (uint32_t)j + 1;
           continue;
         }
         const float w = al * T[q];
@@ -354,16 +357,21 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
     }
   }
   if (kStats) {
-    __shared__ unsigned long long s_st[2];
-    if (threadIdx.x == 0) s_st[0] = s_st[1] = 0ull;
+    __shared__ unsigned long long s_st[3];
+    if (threadIdx.x == 0) s_st[0] = s_st[1] = s_st[2] = 0ull;
     __syncthreads();
+    unsigned long long visits = 0;
+#pragma unroll
+    for (int q = 0; q < kPix; ++q) visits += kStats ? stop[q] : 0u;
     atomicAdd(&s_st[0], (unsigned long long)n_eval);
     atomicAdd(&s_st[1], (unsigned long long)n_blend);
+    atomicAdd(&s_st[2], visits);
     __syncthreads();
     if (threadIdx.x == 0) {
       atomicAdd(&stats[0], s_st[0]);
       atomicAdd(&stats[1], s_st[1]);
       atomicAdd(&stats[2], (unsigned long long)(r.y - r.x) * (kT * kT));
+      atomicAdd(&stats[3], s_st[2]);
     }
   }
   const size_t plane = (size_t)v.W * v.H;

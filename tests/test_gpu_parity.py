@@ -239,3 +239,35 @@ def test_fused_forward_l2_matches_the_separate_calls(bs, name):
     for x, y in ((img, img2), (T, T2), (nc, nc2), (dimg, dimg2)):
         assert torch.equal(x, y)
     assert abs(float(loss2) - float(loss)) <= 1e-7 * abs(float(loss))
+
+
+@pytest.mark.parametrize("name", ["tiny256", "mixed"])
+def test_work_counters_match_oracle(bs, name):
+    """bs_render_stats: blended entries and per-pixel visits (list entries up
+    to the stop point) against the oracle's blends and stop indices; pixels
+    the oracle flags may differ by up to their list length."""
+    case = CASES[name]
+    tab, _, _ = oracle_table(case)
+    rec = table_to_f32(tab)
+    gauss = torch.as_tensor(rec, device="cuda")
+    b = bs.Binning(_canvas(bs, case), "cuda", pair_capacity=1024).run(gauss)
+    st = bs.render_stats(gauss, _canvas(bs, case), b)
+    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg, margin=4e-6, margin_T=2e-5)
+    keys, ranges, _ = oracle.tile_keys(rec, case.W, case.H, 16)
+    gbits = max(1, (rec.shape[0] - 1).bit_length())
+    tiles_x = -(-case.W // 16)
+    stop = ref["stop"].numpy()
+    ng = rec.shape[0]
+    visits, slack = 0, 0
+    for y in range(case.H):
+        for x in range(case.W):
+            t = (y // 16) * tiles_x + x // 16
+            lst = (keys[ranges[t, 0]:ranges[t, 1]] & ((1 << gbits) - 1)).astype(np.int64)
+            sg = int(stop[y, x])
+            v = len(lst) if sg >= ng else int(np.searchsorted(lst, sg)) + 1
+            visits += v
+            if bool(ref["flag"][y, x]):
+                slack += len(lst)
+    assert abs(st["visits"] - visits) <= slack
+    assert st["visits"] >= st["evals"] >= st["blended"]
+    assert abs(st["blended"] - int(ref["n_blend"].sum())) <= slack
