@@ -6,7 +6,8 @@
 // (four blocks) for T = 16 and 32, so a tile has 1, 2 or 8 warps.  Lane l
 // owns pixel (l & 7, l >> 3) of each of its warp's blocks (its slots).  The
 // tile's list is staged into shared memory one Gaussian per thread at a
-// time, each with one bit per block of the tile telling whether its
+// time (in the forward by cp.async, one batch ahead of the blend), each
+// with one bit per block of the tile telling whether its
 // alpha >= 1/255 region reaches the block, so a warp skips a block for a
 // Gaussian without touching its pixels, and the work of a slot stays within
 // one compact block.
@@ -92,19 +93,19 @@ __device__ __forceinline__ void scaled_axes(float ux, float uy, float isx, float
   B2 = __fmul_rn(ky, ux);
 }
 
-// Stage Gaussian g; an index past the table (only possible after a sort that
-// gave up waiting) stages an invisible Gaussian.
-__device__ __forceinline__ Staged stage(const float *__restrict__ gauss, uint32_t g, uint32_t n_gauss) {
+// Stage one record (its three float4s); an index past the table (only
+// possible after a sort that gave up waiting) stages an invisible Gaussian.
+__device__ __forceinline__ Staged stage_none() {
   Staged s;
-  if (g >= n_gauss) {
-    s.a = make_float4(0.f, 0.f, 0.f, 0.f);
-    s.b = make_float4(0.f, 0.f, -INFINITY, 0.f);
-    s.c = make_float2(0.f, 0.f);
-    s.ext = make_float2(-1.f, -1.f);
-    return s;
-  }
-  const float4 *rec = reinterpret_cast<const float4 *>(gauss + (size_t)g * BS_GAUSS_FLOATS);
-  const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+  s.a = make_float4(0.f, 0.f, 0.f, 0.f);
+  s.b = make_float4(0.f, 0.f, -INFINITY, 0.f);
+  s.c = make_float2(0.f, 0.f);
+  s.ext = make_float2(-1.f, -1.f);
+  return s;
+}
+
+__device__ __forceinline__ Staged stage_rec(const float4 r0, const float4 r1, const float4 r2) {
+  Staged s;
   float A1, B1, A2, B2;
   scaled_axes(r0.z, r0.w, r1.x, r1.y, A1, B1, A2, B2);
   const float o = r1.z;
@@ -113,6 +114,60 @@ __device__ __forceinline__ Staged stage(const float *__restrict__ gauss, uint32_
   s.c = make_float2(r2.x, r2.y);
   s.ext = make_float2(r2.z, r2.w);
   return s;
+}
+
+// Stage Gaussian g straight from global memory (the backward's path).
+__device__ __forceinline__ Staged stage(const float *__restrict__ gauss, uint32_t g, uint32_t n_gauss) {
+  if (g >= n_gauss) return stage_none();
+  const float4 *rec = reinterpret_cast<const float4 *>(gauss + (size_t)g * BS_GAUSS_FLOATS);
+  return stage_rec(__ldg(rec), __ldg(rec + 1), __ldg(rec + 2));
+}
+
+// Asynchronous staging of a tile's list (the forward's path).  While the
+// CTA blends one batch of kBatch entries, thread t has in flight the
+// cp.async copies of its entry of the next batch (the 48-byte record, three
+// 16-byte copies into rec[.][t]) and of its key two batches ahead (into
+// key[.][t]).  A thread reads only the slots it wrote, so
+// cp.async.wait_group alone makes them visible; a slot is overwritten only
+// after the thread has consumed what it held (the copy is issued after the
+// instructions that use the loaded values).  The backward stages with plain
+// loads: the same prefetch there measured 2 % slower (5 % more warp
+// instructions at the same occupancy).
+template <int kBatch>
+struct StageBuf {
+  float4 rec[3][kBatch];
+  uint32_t key[2][kBatch];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Copy Gaussian g's record into this thread's slot (nothing for g past the
+// table; stage_slot stages it as invisible).
+template <int kBatch>
+__device__ __forceinline__ void issue_rec(StageBuf<kBatch> &buf, const float *__restrict__ gauss, uint32_t g,
+                                          uint32_t n_gauss) {
+  if (g >= n_gauss) return;
+  const float4 *rec = reinterpret_cast<const float4 *>(gauss + (size_t)g * BS_GAUSS_FLOATS);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) cp_async16(&buf.rec[k][threadIdx.x], rec + k);
+}
+
+template <int kBatch>
+__device__ __forceinline__ Staged stage_slot(const StageBuf<kBatch> &buf, uint32_t g, uint32_t n_gauss) {
+  if (g >= n_gauss) return stage_none();
+  return stage_rec(buf.rec[0][threadIdx.x], buf.rec[1][threadIdx.x], buf.rec[2][threadIdx.x]);
 }
 
 // Smallest t1^2 + t2^2 over the rectangle [dx0, dx1] x [dy0, dy1] of offsets
@@ -293,15 +348,26 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
     if (kStats) stop[i] = (tp.inside >> i) & 1u ? r.y - r.x : 0u;
   }
   __shared__ uint32_t s_alive[kW];  // per warp: slots (8x4 blocks) with a pixel still blending
+  __shared__ __align__(16) StageBuf<kBatch> s_buf;
+  // batch 0's key and record, batch 1's key
+  if (r.x + threadIdx.x < r.y) {
+    const uint32_t key = keys[r.x + threadIdx.x];
+    s_buf.key[0][threadIdx.x] = key;
+    issue_rec(s_buf, gauss, key & gmask, n_gauss);
+  }
+  if (r.x + kBatch + threadIdx.x < r.y) cp_async4(&s_buf.key[1][threadIdx.x], keys + r.x + kBatch + threadIdx.x);
+  cp_async_commit();
   unsigned alive = tp.inside;
-  for (uint32_t base = r.x; base < r.y; base += kBatch) {
+  uint32_t kb = 0;  // key slot of this batch
+  for (uint32_t base = r.x; base < r.y; base += kBatch, kb ^= 1u) {
     const uint32_t walive = __reduce_or_sync(0xffffffffu, alive);
     if ((threadIdx.x & 31) == 0) s_alive[threadIdx.x >> 5] = walive;
     if (__syncthreads_count(alive != 0) == 0) break;
+    cp_async_wait_all();
     const uint32_t i = base + threadIdx.x;
     uint32_t my_bits = 0u;
     if (i < r.y) {
-      const Staged s = stage(gauss, keys[i] & gmask, n_gauss);
+      const Staged s = stage_slot(s_buf, s_buf.key[kb][threadIdx.x] & gmask, n_gauss);
       s_a[threadIdx.x] = s.a;
       s_b[threadIdx.x] = s.b;
       s_c[threadIdx.x] = s.c;
@@ -311,6 +377,10 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
       my_bits = block_bits<kT>(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0) & alive_all;
       s_bits[threadIdx.x] = my_bits;
     }
+    // in flight while this batch blends: the next batch's record, the key after it
+    if (i + kBatch < r.y) issue_rec(s_buf, gauss, s_buf.key[kb ^ 1u][threadIdx.x] & gmask, n_gauss);
+    if (i + 2 * kBatch < r.y) cp_async4(&s_buf.key[kb][threadIdx.x], keys + i + 2 * kBatch);
+    cp_async_commit();
     compact_lists<kT>(my_bits, s_list, s_cnt);
     __syncthreads();
     const int cw = threadIdx.x >> 5;
@@ -356,6 +426,7 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
     }
     }
   }
+  cp_async_wait_all();  // nothing in flight into s_buf past the tile
   if (kStats) {
     __shared__ unsigned long long s_st[3];
     if (threadIdx.x == 0) s_st[0] = s_st[1] = s_st[2] = 0ull;
