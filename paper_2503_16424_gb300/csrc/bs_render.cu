@@ -757,18 +757,18 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
 #pragma unroll
       for (int q = 0; q < kSums; ++q) v[q] = 0.f;
       bool contrib = false;
-#pragma unroll
-      for (int q = 0; q < kPix; ++q) {
-        if (!(bits & (1u << q))) continue;   // warp-uniform: block q not reached
-        // branch-free per pixel: a pixel past its last blended Gaussian, or
-        // below the alpha threshold, gets alpha = 0, an exact no-op below
+      // One slot (8x4 block) of this thread.  Branch-free per pixel: a pixel
+      // past its last blended Gaussian, or below the alpha threshold, gets
+      // alpha = 0, an exact no-op below (rcp.approx(1) is exactly 1, so T
+      // stays as it is).
+      const auto slot = [&](const int q) {
         float t1, t2;
         const float raw = ex2_approx(pixel_log2_alpha(a, b, dx[q % kBC], b1dy[q / kBC], b2dy[q / kBC], t1, t2));
         const float al0 = fminf(kAlphaMax, raw);
         const bool on = pos < last[q] && al0 >= kAlphaMin;
         const float al = on ? al0 : 0.f;
         contrib |= on;
-        T[q] = on ? T[q] * rcp_approx(1.f - al) : T[q];  // T before this Gaussian
+        T[q] = T[q] * rcp_approx(1.f - al);  // T before this Gaussian
         const float w = al * T[q];
         const float gc = __fmaf_rn(g2[q], gb.y, __fmaf_rn(g1[q], gb.x, g0[q] * b.w));
         const float diff = gc - gS[q];
@@ -776,7 +776,7 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
         v[6] = __fmaf_rn(w, g0[q], v[6]);
         v[7] = __fmaf_rn(w, g1[q], v[7]);
         v[8] = __fmaf_rn(w, g2[q], v[8]);
-        const float dq = raw <= kAlphaMax ? (T[q] * diff) * al : 0.f;  // alpha dL/dalpha; 0 past the clamp
+        const float dq = raw <= kAlphaMax ? w * diff : 0.f;  // alpha dL/dalpha; 0 past the clamp
         const float e1 = dq * t1, e2 = dq * t2;
         v[0] += e1;
         v[1] += e2;
@@ -784,6 +784,14 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
         v[3] = __fmaf_rn(e1, t2, v[3]);
         v[4] = __fmaf_rn(e2, t2, v[4]);
         v[5] += dq;
+      };
+      if (bits == G::kSlotMask) {  // every block reached: one straight run, the slots' chains interleave
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) slot(q);
+      } else {  // each block behind its warp-uniform bit
+#pragma unroll
+        for (int q = 0; q < kPix; ++q)
+          if (bits & (1u << q)) slot(q);
       }
       if (__any_sync(0xffffffffu, contrib)) {
         float *dst = part + n_pend * kSums * kRow + lane;
