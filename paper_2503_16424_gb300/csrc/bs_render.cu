@@ -400,20 +400,14 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
         b1dy[k] = __fmul_rn(a.w, dy);
         b2dy[k] = __fmul_rn(b.y, dy);
       }
-#pragma unroll
-      for (int q = 0; q < kPix; ++q) {
-        if (!(bits & (1u << q))) continue;   // warp-uniform: block q not reached
-        if (!(alive & (1u << q))) continue;
-        float t1, t2;
-        const float al = fminf(
-            kAlphaMax, ex2_approx(pixel_log2_alpha(a, b, dx[q % kBC], b1dy[q / kBC], b2dy[q / kBC], t1, t2)));
+      const auto blend = [&](const int q, const float al) {
         if (kStats) ++n_eval;
-        if (al < kAlphaMin) continue;
+        if (al < kAlphaMin) return;
         const float Tn = T[q] * (1.f - al);
         if (Tn < kTMin) {
           alive &= ~(1u << q);
           if (kStats) stop[q] = base - r.x + (uint32_t)j + 1;
-          continue;
+          return;
         }
         const float w = al * T[q];
         c0[q] = __fmaf_rn(w, b.w, c0[q]);
@@ -422,6 +416,21 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
         T[q] = Tn;
         last[q] = base - r.x + (uint32_t)j + 1;
         if (kStats) ++n_blend;
+      };
+      const auto alpha = [&](const int q) {
+        float t1, t2;
+        return fminf(kAlphaMax,
+                     ex2_approx(pixel_log2_alpha(a, b, dx[q % kBC], b1dy[q / kBC], b2dy[q / kBC], t1, t2)));
+      };
+      {  // the alphas of all slots first, in one straight run whose chains interleave (a slot the
+         // entry does not reach costs one evaluation; its alpha is not used)
+        float al[kPix];
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) al[q] = alpha(q);
+        const uint32_t go = bits & alive;
+#pragma unroll
+        for (int q = 0; q < kPix; ++q)
+          if (go & (1u << q)) blend(q, al[q]);
       }
     }
     }
