@@ -409,6 +409,10 @@ def run_batched(dev, args):
     n_img = len(images)
     diff = [abs(a - b) for a, b in zip(p_batch, p_plain)]
     passes = -(-max(1, (r.batch.n_tiles - 1).bit_length()) // 8)
+    # curves below 512 samples and the rest are sampled by separate launches
+    sizes = [im.sample.g_open for im in images if im.n_open] + \
+            [im.sample.rows_closed * im.sample.k_closed for im in images if im.n_closed]
+    classes = len({n >= 512 for n in sizes})
     return {
         "workload": W["name"], "images": n_img, "pixels": r.batch.n_pixels,
         "curves": r.batch.n_open + r.batch.n_closed, "gaussians": r.batch.n_gauss, "pairs": n_pairs,
@@ -417,7 +421,7 @@ def run_batched(dev, args):
         "plain_ms_per_step": round(p_ms, 4), "plain_image_steps_per_s": round(n_img * 1e3 / p_ms, 2),
         "speedup_vs_plain": round(p_ms / b_ms, 3),
         "step": "draw order, sampling, binning, blend + L2, backward, Adam; batched = one CUDA graph replay",
-        "launches_per_step": 19 + 3 * passes,
+        "launches_per_step": 17 + 3 * passes + 2 * classes,
         "psnr": {"steps": k_psnr, "batched_mean_db": round(float(np.mean(p_batch)), 4),
                  "plain_mean_db": round(float(np.mean(p_plain)), 4),
                  "max_abs_diff_db": round(float(max(diff)), 5)},

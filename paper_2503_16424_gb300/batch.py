@@ -239,3 +239,49 @@ class PlainOptimizer:
         for r, cv, tg, grad, adam in self.items:
             r.step(cv, tg, grad)
             adam.step()
+
+
+def main():
+    """Optimise the 64-image ragged workload (synth.BATCH_WORKLOAD, each image
+    sampled by the autotuner's spacing rule) with BatchOptimizer: one eager
+    step, one captured step, then graph replays; prints one JSON line with
+    the ms per replayed step.  The batched step's launch list is taken on
+    this command."""
+    import argparse
+    import json
+
+    import numpy as np
+
+    from . import autotune, synth
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--steps", type=int, default=5, help="steps in all (at least 3)")
+    ap.add_argument("--tile", type=int, default=16, choices=(8, 16, 32))
+    args = ap.parse_args()
+    steps = max(3, args.steps)
+    dev = torch.device("cuda", 0)
+    W = synth.BATCH_WORKLOAD
+    layout = synth.batch_layout(W["seed"], W["n_images"], W["side"], W["aspect"], W["curves"])
+    arrs, cat, targets = synth.batch_inputs(layout, W["n_shapes"])
+    base = [BatchImage(e["W"], e["H"], e["n_open"], e["n_closed"], bs.SampleCfg()) for e in layout]
+    images = autotune._with_sampling(base, autotune.spacing_sampling(base, arrs))
+    target = torch.as_tensor(np.concatenate([t.reshape(-1) for t in targets]), device=dev)
+    curves = CurveSet.from_arrays(cat, device=dev)
+    rast = BatchRasterizer(images, tile=args.tile, pair_capacity=1 << 24, device=dev)
+    opt = BatchOptimizer(rast, curves, target, graph=True, check_every=0)
+    opt.step()
+    opt.step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps - 2):
+        opt.step()
+    e1.record()
+    torch.cuda.synchronize()
+    st, n_pairs = rast.batch.status()
+    print(json.dumps({"workload": W["name"], "images": len(images), "gaussians": rast.batch.n_gauss,
+                      "pairs": n_pairs, "binning_status": st, "tile": args.tile,
+                      "ms_per_step": round(e0.elapsed_time(e1) / (steps - 2), 4)}))
+
+
+if __name__ == "__main__":
+    main()

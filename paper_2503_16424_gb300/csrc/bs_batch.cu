@@ -70,15 +70,19 @@ bs_status plan_batch(const bs_batch_image *images, int32_t n_images, int32_t til
     p->diff_rows += ty + 1;
     p->diff_cols += tx + 1;
     p->order_ctas += chunks * chunks;
-    if (im.n_open > 0) {
-      p->n_max = std::max(p->n_max, im.sample.g_open);
-      p->k_max = std::max(p->k_max, im.sample.g_open);
-    }
-    if (im.n_closed > 0) {
-      p->n_max = std::max(p->n_max, im.sample.rows_closed * im.sample.k_closed);
-      p->k_max = std::max(p->k_max, im.sample.k_closed);
-    }
-    p->rows_max = std::max(p->rows_max, im.sample.rows_closed);
+    const auto note = [p](int n, int k, int rows) {
+      p->n_max = std::max(p->n_max, n);
+      p->k_max = std::max(p->k_max, k);
+      p->rows_max = std::max(p->rows_max, rows);
+      int *cls = n < kWideSamples ? &p->n_max_narrow : &p->n_max_wide;  // n, k, rows of the class
+      int *kc = n < kWideSamples ? &p->k_max_narrow : &p->k_max_wide;
+      int *rc = n < kWideSamples ? &p->rows_max_narrow : &p->rows_max_wide;
+      *cls = std::max(*cls, n);
+      *kc = std::max(*kc, k);
+      *rc = std::max(*rc, rows);
+    };
+    if (im.n_open > 0) note(im.sample.g_open, im.sample.g_open, 1);
+    if (im.n_closed > 0) note(im.sample.rows_closed * im.sample.k_closed, im.sample.k_closed, im.sample.rows_closed);
   }
   p->n_curves = p->n_open + p->n_closed;
   if (p->n_curves > (1ll << 30)) {

@@ -9,11 +9,20 @@
 // control points (backward).  A curve's Gaussians are contiguous in the
 // draw-ordered table, so the backward needs no global atomics.
 //
-// Precision: the sample points and the differences of neighbouring samples
-// (Eq. 7-8) are computed in double, relative to the curve's first control
-// point.  Subtracting two float32 positions loses the digits that a short
-// tangent or a thin row spacing needs; the difference vectors, once formed,
-// are well conditioned and everything after them runs in float32.
+// Precision: a short tangent or a thin row spacing is the difference of two
+// nearby sample points far from the curve's first control point, and
+// subtracting two float32 positions would lose the digits it needs.  The
+// sample points are therefore formed in float-float arithmetic (a float pair
+// hi + lo carrying about 48 bits, from the error-free two-sum of Knuth and
+// the FMA two-product, the construction of double-double arithmetic carried
+// over to floats; FP64 units are a small fraction of FP32 ones on this GPU),
+// relative to the first control point, and the difference vectors are taken
+// in that arithmetic before being rounded to float32.  A closed curve's row r
+// is (1 - tau_r) A + tau_r B (Eq. 4), so its points are X_A + tau_r (X_B - X_A)
+// and its differences are those of the two boundaries interpolated by tau_r;
+// the across-row difference is (tau_{r+1} - tau_r)(X_B - X_A), with the tau
+// step from a product of sines, accurate however thin the row.  Everything
+// after the difference vectors runs in float32.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -22,9 +31,6 @@
 namespace bs {
 namespace {
 
-constexpr int kCurveThreads = 64;       // threads per curve
-constexpr int kCurveThreadsWide = 256;  // for curves of kWideSamples samples or more
-constexpr int kWideSamples = 512;
 __host__ __device__ inline int curve_threads(int n_max) { return n_max >= kWideSamples ? kCurveThreadsWide : kCurveThreads; }
 
 struct Cfg {
@@ -32,12 +38,46 @@ struct Cfg {
   float rho, eps;
 };
 
-__device__ __forceinline__ void bern3(double t, double w[4]) {
-  const double u = 1.0 - t;
-  w[0] = u * u * u;
-  w[1] = 3.0 * u * u * t;
-  w[2] = 3.0 * u * t * t;
-  w[3] = t * t * t;
+// ---- float-float arithmetic: x = hi + lo, |lo| <= ulp(hi) / 2 ----
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {  // a + b exactly (Knuth)
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return ff{s, e};
+}
+
+__device__ __forceinline__ ff quick_sum(float a, float b) {  // a + b exactly when |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff two_prod(float a, float b) {  // a b exactly (one FMA)
+  const float p = __fmul_rn(a, b);
+  return ff{p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return quick_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const ff p = two_prod(a.hi, b.hi);
+  return quick_sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
+}
+
+__device__ __forceinline__ float ff_round(ff a) { return __fadd_rn(a.hi, a.lo); }
+
+// b - a of two float-float points (x.hi, x.lo, y.hi, y.lo), rounded to float
+__device__ __forceinline__ float2 ff2_diff(const float4 &b, const float4 &a) {
+  return make_float2(ff_round(ff_add(ff{b.x, b.y}, ff_neg(ff{a.x, a.y}))),
+                     ff_round(ff_add(ff{b.z, b.w}, ff_neg(ff{a.z, a.w}))));
 }
 
 // Segment of sample k of K on a chain of S segments, u = k/(K-1):
@@ -46,135 +86,186 @@ __device__ __forceinline__ int chain_seg(int k, int K, int S) {
   const int s = (S * k) / (K - 1);
   return s > S - 1 ? S - 1 : s;
 }
-// Local parameter t = S u - s, u = k / (K - 1), with inv = 1 / (K - 1).
-__device__ __forceinline__ double chain_t_inv(int k, int K, int S, int s, double inv) {
-  return (double)(S * k - s * (K - 1)) * inv;
+
+// Local parameter t = S u - s = (S k - s (K - 1)) / (K - 1) in float-float
+// (the remainder of a correctly rounded quotient is exact under an FMA).
+__device__ __forceinline__ ff chain_t(int k, int K, int S, int s) {
+  const float num = (float)(S * k - s * (K - 1)), den = (float)(K - 1);
+  const float q = __fdiv_rn(num, den);
+  return ff{q, __fdiv_rn(__fmaf_rn(-q, den, num), den)};
+}
+
+// The cubic Bernstein weights of Eq. 1-2 at t, in float-float.
+__device__ __forceinline__ void bern3_ff(ff t, ff w[4]) {
+  const ff u = ff_add(ff{1.f, 0.f}, ff_neg(t));
+  const ff uu = ff_mul(u, u), tt = ff_mul(t, t), three{3.f, 0.f};
+  w[0] = ff_mul(uu, u);
+  w[1] = ff_mul(three, ff_mul(uu, t));
+  w[2] = ff_mul(three, ff_mul(u, tt));
+  w[3] = ff_mul(tt, t);
 }
 
 // Boundary groups of a closed curve: A = P0..P6, B = P0, P11, ..., P7, P6.
 __device__ __forceinline__ int closed_b_index(int j) { return (j == 0 || j == 6) ? j : 12 - j; }
 
-// tau_r = (1 - cos(pi r/(R+1)))/2 with rows = R + 2.
-__device__ __forceinline__ double closed_tau(int r, int rows) {
-  return 0.5 * (1.0 - cospi((double)r / (double)(rows - 1)));
-}
-
 __device__ __forceinline__ const float *curve_ctrl(const bs_curves &c, int curve) {
   return curve < c.n_open ? c.open_ctrl + (size_t)curve * 20 : c.closed_ctrl + (size_t)(curve - c.n_open) * 24;
 }
 
-// Shared memory of the sampling kernels, per CTA (one curve):
-//   Wt   [k_max][4] double   Bernstein weights of each sample index k
-//   taut [rows]     double   row weights tau_r (closed curves)
-//   Pd   [12]       double2  control points relative to the first one
-//   Qd   [rows][7]  double2  control points of each row (closed curves)
-//   X    [n_max]    double2  sample points relative to the first control point
+// Shared memory of the sampling kernels, per CTA (one curve), by column k
+// (open curves: one column per sample; closed curves: a column of R2 rows):
+//   Q    [12]     float4  control points minus the first one, float-float (x.hi, x.lo, y.hi, y.lo)
+//   W    [k_max]  float4  Bernstein weights of column k (float, for the backward's gather)
+//   XA   [k_max]  float4  the point of boundary A (open: the curve) at k, float-float, relative to P0
+//   EA   [k_max]  float4  along-row difference e and tangent difference t of boundary A
+//   EB   [k_max]  float4  the same of boundary B (closed)
+//   D    [k_max]  float2  X_B - X_A (closed)
+//   tau  [rows]   float2  (tau_r, tau_{r+1} - tau_r) (closed)
 //   backward only: G [4][n_max] float2  per-sample gradient pieces, whose
 //   first plane is overwritten with dL/dX by the gather.
+//   XB   [k_max]  float4  boundary B while the columns are built (in G's place when there is a G)
 struct CurveSmem {
-  double *Wt, *taut;
-  double2 *Pd, *Qd, *X;
-  float2 *G;
+  float4 *Q, *W, *XA, *EA, *EB, *XB;
+  float2 *D, *tau, *G;
 };
 
 __host__ __device__ inline size_t curve_smem_bytes(int n_max, int k_max, int rows, bool with_grad) {
-  return sizeof(double) * (4 * (size_t)k_max + (size_t)rows) + sizeof(double2) * (12 + 7 * (size_t)rows + n_max) +
-         (with_grad ? sizeof(float2) * 4 * (size_t)n_max : 0);
+  return sizeof(float4) * (12 + 4 * (size_t)k_max) + sizeof(float2) * ((size_t)k_max + (size_t)rows) +
+         (with_grad ? sizeof(float2) * 4 * (size_t)(n_max > k_max ? n_max : k_max) : sizeof(float4) * (size_t)k_max);
 }
 
 __device__ __forceinline__ CurveSmem carve(void *base, int n_max, int k_max, int rows, bool with_grad) {
+  // the float4 tables first, then G (or XB), then the float2 tables: every
+  // table starts on a multiple of its element size
   CurveSmem m;
   char *p = static_cast<char *>(base);
-  m.X = reinterpret_cast<double2 *>(p);
-  p += sizeof(double2) * n_max;
-  m.Pd = reinterpret_cast<double2 *>(p);
-  p += sizeof(double2) * 12;
-  m.Qd = reinterpret_cast<double2 *>(p);
-  p += sizeof(double2) * 7 * rows;
-  m.Wt = reinterpret_cast<double *>(p);
-  p += sizeof(double) * 4 * k_max;
-  m.taut = reinterpret_cast<double *>(p);
-  p += sizeof(double) * rows;
-  m.G = with_grad ? reinterpret_cast<float2 *>(p) : nullptr;
+  m.Q = reinterpret_cast<float4 *>(p);
+  p += sizeof(float4) * 12;
+  m.W = reinterpret_cast<float4 *>(p);
+  p += sizeof(float4) * k_max;
+  m.XA = reinterpret_cast<float4 *>(p);
+  p += sizeof(float4) * k_max;
+  m.EA = reinterpret_cast<float4 *>(p);
+  p += sizeof(float4) * k_max;
+  m.EB = reinterpret_cast<float4 *>(p);
+  p += sizeof(float4) * k_max;
+  m.XB = reinterpret_cast<float4 *>(p);  // with a G: in G's place ([k_max] float4 fits in [4][n_max] float2)
+  if (with_grad) {
+    m.G = reinterpret_cast<float2 *>(p);
+    p += sizeof(float2) * 4 * (size_t)(n_max > k_max ? n_max : k_max);
+  } else {
+    m.G = nullptr;
+    p += sizeof(float4) * k_max;
+  }
+  m.D = reinterpret_cast<float2 *>(p);
+  p += sizeof(float2) * k_max;
+  m.tau = reinterpret_cast<float2 *>(p);
   return m;
 }
 
-// Fill the per-CTA tables and the sample points X of one curve (ends with a
-// barrier).  Everything up to the differences of neighbouring samples is in
-// double: the control points relative to the first one (exact), the
-// Bernstein weights, the row interpolation (Eq. 4), the sums of Eq. 1 and,
-// in local_geometry, the differences themselves.
+// Point of a boundary at column k: sum_i w_i Q[j(3s + i)], float-float.
+__device__ __forceinline__ float4 boundary_point(const float4 *Q, const ff w[4], int s, bool b_side) {
+  ff x{0.f, 0.f}, y{0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = b_side ? closed_b_index(3 * s + i) : 3 * s + i;
+    const float4 q = Q[j];
+    x = ff_add(x, ff_mul(w[i], ff{q.x, q.y}));
+    y = ff_add(y, ff_mul(w[i], ff{q.z, q.w}));
+  }
+  return make_float4(x.hi, x.lo, y.hi, y.lo);
+}
+
+// Along-row difference e_k and tangent difference t_k of a column table X
+// (one-sided at both ends), each rounded to float from float-float.
+__device__ __forceinline__ float4 column_diffs(const float4 *X, int k, int K) {
+  const float2 e = k + 1 < K ? ff2_diff(X[k + 1], X[k]) : ff2_diff(X[k], X[k - 1]);
+  const float2 t = k == 0 ? ff2_diff(X[1], X[0]) : (k == K - 1 ? ff2_diff(X[k], X[k - 1]) : ff2_diff(X[k + 1], X[k - 1]));
+  return make_float4(e.x, e.y, t.x, t.y);
+}
+
+// Fill the per-CTA column tables of one curve (ends with a barrier);
+// returns its sample count.
 __device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, const CurveSmem &m) {
-  __shared__ double s_inv;
   const bool closed = curve >= c.n_open;
   const float *P = curve_ctrl(c, curve);
   const int K = closed ? cfg.kc : cfg.g_open, S = closed ? 2 : 3, R2 = closed ? cfg.rows : 1;
   const int npts = closed ? 12 : 10;
-  if (threadIdx.x == 0) s_inv = 1.0 / (double)(K - 1);
-  for (int j = threadIdx.x; j < npts; j += blockDim.x)
-    m.Pd[j] = make_double2((double)P[2 * j] - (double)P[0], (double)P[2 * j + 1] - (double)P[1]);
-  if (closed)
-    for (int r = threadIdx.x; r < R2; r += blockDim.x) m.taut[r] = closed_tau(r, R2);
-  __syncthreads();
-  const double inv = s_inv;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) bern3(chain_t_inv(k, K, S, chain_seg(k, K, S), inv), m.Wt + 4 * k);
+  for (int j = threadIdx.x; j < npts; j += blockDim.x) {
+    const ff x = two_sum(P[2 * j], -P[0]), y = two_sum(P[2 * j + 1], -P[1]);  // exact
+    m.Q[j] = make_float4(x.hi, x.lo, y.hi, y.lo);
+  }
   if (closed) {
-    for (int q = threadIdx.x; q < 7 * R2; q += blockDim.x) {
-      const int r = q / 7, j = q - 7 * r;
-      const double2 a = m.Pd[j], b = m.Pd[closed_b_index(j)];
-      const double tau = m.taut[r];
-      m.Qd[q] = make_double2(a.x + tau * (b.x - a.x), a.y + tau * (b.y - a.y));  // Eq. 4
+    // tau_r = (1 - cos(pi r / N)) / 2 = sin^2(pi r / 2N), N = R2 - 1, and
+    // tau_{r+1} - tau_r = sin(pi (2r + 1) / 2N) sin(pi / 2N)
+    const float inv2n = 1.f / (float)(2 * (R2 - 1)), s1 = sinpif(inv2n);
+    for (int r = threadIdx.x; r < R2; r += blockDim.x) {
+      const float sr = sinpif((float)r * inv2n);
+      m.tau[r] = make_float2(sr * sr, r + 1 < R2 ? sinpif((float)(2 * r + 1) * inv2n) * s1 : 0.f);
     }
   }
   __syncthreads();
-  const int n = R2 * K;
-  const double2 *ctrl = closed ? m.Qd : m.Pd;
-  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int r = idx / K, k = idx - r * K;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
     const int s = chain_seg(k, K, S);
-    const double *w = m.Wt + 4 * k;
-    const double2 *q = ctrl + 7 * r + 3 * s;  // open curves: r = 0
-    double ax = 0.0, ay = 0.0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      ax += w[i] * q[i].x;
-      ay += w[i] * q[i].y;
-    }
-    m.X[idx] = make_double2(ax, ay);
+    ff w[4];
+    bern3_ff(chain_t(k, K, S, s), w);
+    m.W[k] = make_float4(ff_round(w[0]), ff_round(w[1]), ff_round(w[2]), ff_round(w[3]));
+    m.XA[k] = boundary_point(m.Q, w, s, false);
+    if (closed) m.XB[k] = boundary_point(m.Q, w, s, true);
   }
   __syncthreads();
-  return n;
-}
-
-__device__ __forceinline__ float2 diff(const double2 *X, int hi, int lo) {
-  return make_float2((float)(X[hi].x - X[lo].x), (float)(X[hi].y - X[lo].y));
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    m.EA[k] = column_diffs(m.XA, k, K);
+    if (closed) {
+      m.EB[k] = column_diffs(m.XB, k, K);
+      m.D[k] = ff2_diff(m.XB[k], m.XA[k]);
+    }
+  }
+  __syncthreads();
+  return R2 * K;
 }
 
 // Local geometry of one sample (Eq. 7-8): the along-row difference e (for
 // sigma_x), the tangent difference t (for the rotation), the across-row
-// difference f (closed curves, for sigma_y); the scales; the unit tangent u.
+// difference f (closed curves, for sigma_y); the scales; the unit tangent u;
+// the mean relative to the first control point.
 struct Local {
   float2 e, t, f;
   float le, lt, lf;  // their lengths
   float sx, sy, ux, uy;
+  float mx, my;
 };
 
-__device__ __forceinline__ Local local_geometry(const double2 *X, int idx, int K, int R2, bool closed,
+__device__ __forceinline__ Local local_geometry(const CurveSmem &m, int idx, int K, int R2, bool closed,
                                                 float width, float rho) {
   Local L;
   const int r = closed ? idx / K : 0;
   const int k = idx - r * K;
-  L.e = k + 1 < K ? diff(X, idx + 1, idx) : diff(X, idx, idx - 1);
-  L.t = k == 0 ? diff(X, idx + 1, idx) : (k == K - 1 ? diff(X, idx, idx - 1) : diff(X, idx + 1, idx - 1));
+  const float4 ea = m.EA[k], xa = m.XA[k];
+  if (closed) {
+    const float tau = m.tau[r].x, omt = 1.f - tau;
+    const float4 eb = m.EB[k];
+    const float2 d = m.D[k];
+    L.e = make_float2(omt * ea.x + tau * eb.x, omt * ea.y + tau * eb.y);
+    L.t = make_float2(omt * ea.z + tau * eb.z, omt * ea.w + tau * eb.w);
+    const float dt = r + 1 < R2 ? m.tau[r].y : m.tau[r - 1].y;
+    L.f = make_float2(dt * d.x, dt * d.y);
+    L.mx = xa.x + (xa.y + tau * d.x);
+    L.my = xa.z + (xa.w + tau * d.y);
+  } else {
+    L.e = make_float2(ea.x, ea.y);
+    L.t = make_float2(ea.z, ea.w);
+    L.f = make_float2(0.f, 0.f);
+    L.mx = xa.x + xa.y;
+    L.my = xa.z + xa.w;
+  }
   L.le = sqrtf(L.e.x * L.e.x + L.e.y * L.e.y);
   L.lt = sqrtf(L.t.x * L.t.x + L.t.y * L.t.y);
   L.sx = L.le / rho;
   if (closed) {
-    L.f = r + 1 < R2 ? diff(X, idx + K, idx) : diff(X, idx, idx - K);
     L.lf = sqrtf(L.f.x * L.f.x + L.f.y * L.f.y);
     L.sy = L.lf / rho;
   } else {
-    L.f = make_float2(0.f, 0.f);
     L.lf = 0.f;
     L.sy = width;
   }
@@ -232,21 +323,23 @@ __device__ __forceinline__ Cfg batch_cfg(const BatchImage *__restrict__ tab, int
 // its image's sampling (dynamic shared memory sized for the largest).
 __global__ void __launch_bounds__(kCurveThreadsWide) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss, int n_max,
                                                                    int k_max, const BatchImage *tab = nullptr,
-                                                                   int n_images = 0) {
-  extern __shared__ double2 smem_fwd[];
+                                                                   int n_images = 0, int n_lo = 0,
+                                                                   int n_hi = 0x7fffffff) {
+  extern __shared__ float4 smem_fwd[];
   const int curve = blockIdx.x;
-  if (tab) cfg = batch_cfg(tab, n_images, c, curve);
-  const CurveSmem m = carve(smem_fwd, n_max, k_max, cfg.rows, false);
   const bool closed = curve >= c.n_open;
+  if (tab) cfg = batch_cfg(tab, n_images, c, curve);
+  const int n_curve = closed ? cfg.rows * cfg.kc : cfg.g_open;
+  if (n_curve < n_lo || n_curve >= n_hi) return;  // sampled by the other launch
+  const CurveSmem m = carve(smem_fwd, n_max, k_max, cfg.rows, false);
   const int n = eval_samples(c, cfg, curve, m);
   const int K = closed ? cfg.kc : cfg.g_open;
   const uint32_t first = c.draw_first[curve];
   const float *P = curve_ctrl(c, curve);
-  const double ox = P[0], oy = P[1];
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int seg = closed ? 0 : chain_seg(idx, K, 3);
     const CurveAttr at = curve_attr(c, curve, seg, closed ? row_u(idx, K) : 0.f);
-    const Local L = local_geometry(m.X, idx, K, cfg.rows, closed, at.width, cfg.rho);
+    const Local L = local_geometry(m, idx, K, cfg.rows, closed, at.width, cfg.rho);
     // Sigma = R diag(lx, ly) R^T (Eq. 11-12 with the eps floor)
     const float lx = L.sx * L.sx + cfg.eps, ly = L.sy * L.sy + cfg.eps;
     float ex = -1.f, ey = -1.f;
@@ -258,11 +351,13 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_fwd_kernel(bs_curves
       ey = sqrtf(2.0f * lth * syy) + kExtPad;
     }
     float4 *rec = reinterpret_cast<float4 *>(gauss + (size_t)(first + idx) * BS_GAUSS_FLOATS);
-    rec[0] = make_float4((float)(ox + m.X[idx].x), (float)(oy + m.X[idx].y), L.ux, L.uy);
+    rec[0] = make_float4(P[0] + L.mx, P[1] + L.my, L.ux, L.uy);
     rec[1] = make_float4(rsqrtf(lx), rsqrtf(ly), at.opac, at.col.x);
     rec[2] = make_float4(at.col.y, at.col.z, ex, ey);
   }
 }
+
+__device__ __forceinline__ float w_at(const float4 &w, int i) { return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w)); }
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -280,9 +375,14 @@ __device__ __forceinline__ float warp_sum(float v) {
 __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
                                                                    bs_curves_grad g, int n_max, int k_max,
                                                                    const BatchImage *tab = nullptr,
-                                                                   int n_images = 0) {
-  extern __shared__ double2 smem_bwd[];
+                                                                   int n_images = 0, int n_lo = 0,
+                                                                   int n_hi = 0x7fffffff) {
+  extern __shared__ float4 smem_bwd[];
   if (tab) cfg = batch_cfg(tab, n_images, c, blockIdx.x);
+  {
+    const int n_curve = (int)blockIdx.x >= c.n_open ? cfg.rows * cfg.kc : cfg.g_open;
+    if (n_curve < n_lo || n_curve >= n_hi) return;  // sampled by the other launch
+  }
   const CurveSmem m = carve(smem_bwd, n_max, k_max, cfg.rows, true);
   float2 *GM = m.G, *GE = m.G + n_max, *GT = m.G + 2 * n_max, *GF = m.G + 3 * n_max;
   // opac[3] (open) or opac (closed), colour[3], width, then (gradient
@@ -304,7 +404,7 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
       const int seg = closed ? 0 : chain_seg(idx, K, 3);
       const float u = closed ? row_u(idx, K) : 0.f;
       const CurveAttr at = curve_attr(c, curve, seg, u);
-      const Local L = local_geometry(m.X, idx, K, cfg.rows, closed, at.width, cfg.rho);
+      const Local L = local_geometry(m, idx, K, cfg.rows, closed, at.width, cfg.rho);
       const float *dg = dgauss + (size_t)(first + idx) * BS_DGAUSS_FLOATS;
       const float4 d0 = *reinterpret_cast<const float4 *>(dg);      // mx, my, ux, uy
       const float4 d1 = *reinterpret_cast<const float4 *>(dg + 4);  // isx, isy, o, r
@@ -411,7 +511,7 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
       float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
       for (int r = 0; r < R2; ++r) {
-        const float tau = (float)m.taut[r];
+        const float tau = m.tau[r].x;
         const float2 dx = dX[r * K + k];
         a.x += (1.f - tau) * dx.x;
         a.y += (1.f - tau) * dx.y;
@@ -429,7 +529,7 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
     if (!closed) {
       for (int k = 0; k < K; ++k) {
         const int i = p - 3 * chain_seg(k, K, S);
-        if (i >= 0 && i <= 3) acc += (float)m.Wt[4 * k + i] * (comp ? dX[k].y : dX[k].x);
+        if (i >= 0 && i <= 3) acc += w_at(m.W[k], i) * (comp ? dX[k].y : dX[k].x);
       }
     } else {
       // A_j = P_j (j = 0..6), B_j = P_{12-j} (j = 1..5), B_0 = P_0, B_6 = P_6
@@ -440,7 +540,7 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
         const int ia = ja - 3 * s, ib = jb - 3 * s;
         const bool use_a = ja >= 0 && ia >= 0 && ia <= 3, use_b = jb >= 0 && ib >= 0 && ib <= 3;
         if (!use_a && !use_b) continue;
-        const float wa = use_a ? (float)m.Wt[4 * k + ia] : 0.f, wb = use_b ? (float)m.Wt[4 * k + ib] : 0.f;
+        const float wa = use_a ? w_at(m.W[k], ia) : 0.f, wb = use_b ? w_at(m.W[k], ib) : 0.f;
         acc += wa * (comp ? colA[k].y : colA[k].x) + wb * (comp ? colB[k].y : colB[k].x);
       }
     }
@@ -710,22 +810,42 @@ bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, c
                                   cudaStream_t s) {
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
-  const size_t smem = curve_smem_bytes(p.n_max, p.k_max, p.rows_max, false);
-  BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-  sample_fwd_kernel<<<n, curve_threads(p.n_max), smem, s>>>(c, Cfg{}, gauss, p.n_max, p.k_max, table, p.n_images);
-  BS_LAUNCHED("sample_fwd_kernel");
+  // curves below kWideSamples samples on narrow CTAs, the rest on wide ones,
+  // each launch with the shared memory of its own largest curve
+  if (p.n_max_narrow > 0) {
+    const size_t smem = curve_smem_bytes(p.n_max_narrow, p.k_max_narrow, p.rows_max_narrow, false);
+    BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
+    sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, Cfg{}, gauss, p.n_max_narrow, p.k_max_narrow, table,
+                                                     p.n_images, 0, kWideSamples);
+    BS_LAUNCHED("sample_fwd_kernel");
+  }
+  if (p.n_max_wide > 0) {
+    const size_t smem = curve_smem_bytes(p.n_max_wide, p.k_max_wide, p.rows_max_wide, false);
+    BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
+    sample_fwd_kernel<<<n, kCurveThreadsWide, smem, s>>>(c, Cfg{}, gauss, p.n_max_wide, p.k_max_wide, table,
+                                                         p.n_images, kWideSamples);
+    BS_LAUNCHED("sample_fwd_kernel");
+  }
   return BS_OK;
 }
-
 bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, const bs_curves &c,
                                   const float *dgauss, const bs_curves_grad &g, cudaStream_t s) {
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
-  const size_t smem = curve_smem_bytes(p.n_max, p.k_max, p.rows_max, true);
-  BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-  sample_bwd_kernel<<<n, curve_threads(p.n_max), smem, s>>>(c, Cfg{}, dgauss, g, p.n_max, p.k_max, table,
-                                                             p.n_images);
-  BS_LAUNCHED("sample_bwd_kernel");
+  if (p.n_max_narrow > 0) {
+    const size_t smem = curve_smem_bytes(p.n_max_narrow, p.k_max_narrow, p.rows_max_narrow, true);
+    BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
+    sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, Cfg{}, dgauss, g, p.n_max_narrow, p.k_max_narrow, table,
+                                                     p.n_images, 0, kWideSamples);
+    BS_LAUNCHED("sample_bwd_kernel");
+  }
+  if (p.n_max_wide > 0) {
+    const size_t smem = curve_smem_bytes(p.n_max_wide, p.k_max_wide, p.rows_max_wide, true);
+    BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
+    sample_bwd_kernel<<<n, kCurveThreadsWide, smem, s>>>(c, Cfg{}, dgauss, g, p.n_max_wide, p.k_max_wide, table,
+                                                         p.n_images, kWideSamples);
+    BS_LAUNCHED("sample_bwd_kernel");
+  }
   return BS_OK;
 }
 

@@ -17,6 +17,11 @@ constexpr float kTMin = 1e-4f;              // stop a pixel before T drops below
 constexpr float kExtPad = 0.01f;            // px added to support half extents
 
 constexpr int kMaxSamplesPerCurve = 3072;  // a closed curve's rows x samples per row
+// Curves of at least this many samples are sampled by CTAs of
+// kCurveThreadsWide threads, the others by CTAs of kCurveThreads.
+constexpr int kWideSamples = 512;
+constexpr int kCurveThreads = 64;
+constexpr int kCurveThreadsWide = 256;
 
 // ---- status plumbing ----
 void set_error(const char *fmt, ...);
@@ -175,6 +180,9 @@ struct BatchPlan {
   int tbits, passes, digit_bits;
   int64_t capacity, parts, count_blocks, tile_blocks;
   int n_max, k_max, rows_max;  // sampling: largest samples per curve / per row, rows
+  // the same over the curves of fewer than kWideSamples samples (sampled by
+  // narrow CTAs) and over the others (wide CTAs); n_max 0: no such curve
+  int n_max_narrow, k_max_narrow, rows_max_narrow, n_max_wide, k_max_wide, rows_max_wide;
   // byte offsets inside the batch workspace
   size_t off_hdr, off_hist, off_diff, off_queue, zero_bytes;
   size_t off_images, off_parts, off_local, off_partial, off_rects, off_owner, off_tsum, off_keys0, off_keys1;
