@@ -180,13 +180,19 @@ struct AdamArgs {
   int n_groups;
 };
 
-// One thread per parameter (grid-stride); t = *step + 1 is read by every
-// thread, and step_advance_kernel writes it back after this kernel.
+// One thread per parameter (grid-stride); t = *step + 1 is read once per
+// CTA, and step_advance_kernel writes it back after this kernel.
 __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a, const bs_adam_cfg cfg,
                                                    const int32_t *__restrict__ step) {
-  const int t = *step + 1;
-  const float bc1 = (float)(1.0 - pow((double)cfg.beta1, (double)t));
-  const float bc2 = (float)(1.0 - pow((double)cfg.beta2, (double)t));
+  // the bias corrections 1 - beta^t, once per CTA (FP64 is slow here)
+  __shared__ float s_bc[2];
+  if (threadIdx.x == 0) {
+    const int t = *step + 1;
+    s_bc[0] = (float)(1.0 - pow((double)cfg.beta1, (double)t));
+    s_bc[1] = (float)(1.0 - pow((double)cfg.beta2, (double)t));
+  }
+  __syncthreads();
+  const float bc1 = s_bc[0], bc2 = s_bc[1];
   const int64_t total = a.start[a.n_groups];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {

@@ -87,6 +87,10 @@ __device__ __forceinline__ int chain_seg(int k, int K, int S) {
   return s > S - 1 ? S - 1 : s;
 }
 
+// First sample of segment s (0 <= s <= S): the least k with
+// chain_seg(k, K, S) >= s, i.e. ceil(s (K - 1) / S); K for s = S.
+__device__ __forceinline__ int seg_first(int s, int K, int S) { return s >= S ? K : (s * (K - 1) + S - 1) / S; }
+
 // Local parameter t = S u - s = (S k - s (K - 1)) / (K - 1) in float-float
 // (the remainder of a correctly rounded quotient is exact under an FMA).
 __device__ __forceinline__ ff chain_t(int k, int K, int S, int s) {
@@ -523,29 +527,50 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
     }
     __syncthreads();
   }
-  for (int q = threadIdx.x; q < 2 * npts; q += blockDim.x) {
-    const int p = q >> 1, comp = q & 1;
-    float acc = 0.f;
+  // Each (control point, segment it shapes, coordinate) item sums over that
+  // segment's samples only (a contiguous k range, no division per sample);
+  // then each control point coordinate adds its items in a fixed order.
+  // Items q = 0..n_items/2-1 per coordinate: open, q < 10: P_q on segment
+  // min(q/3, 2); q = 10, 11: P3 on segment 0, P6 on segment 1 (weight 3).
+  // Closed, side A (q < 8) and B (q >= 8), boundary index j = q % 8 < 7 on
+  // segment min(j/3, 1), and j = 3 on segment 0 for q % 8 = 7.
+  __shared__ float s_item[64];
+  const int n_items = closed ? 32 : 24;
+  for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
+    const int comp = it & 1, q = it >> 1;
+    int j, sg;
+    const float2 *src = dX;
     if (!closed) {
-      for (int k = 0; k < K; ++k) {
-        const int i = p - 3 * chain_seg(k, K, S);
-        if (i >= 0 && i <= 3) acc += w_at(m.W[k], i) * (comp ? dX[k].y : dX[k].x);
-      }
+      j = q < 10 ? q : (q == 10 ? 3 : 6);
+      sg = q < 10 ? min(q / 3, 2) : (q == 10 ? 0 : 1);
     } else {
-      // A_j = P_j (j = 0..6), B_j = P_{12-j} (j = 1..5), B_0 = P_0, B_6 = P_6
-      const int ja = p <= 6 ? p : -1;
-      const int jb = (p == 0 || p == 6) ? p : (p >= 7 ? 12 - p : -1);
-      for (int k = 0; k < K; ++k) {
-        const int s = chain_seg(k, K, S);
-        const int ia = ja - 3 * s, ib = jb - 3 * s;
-        const bool use_a = ja >= 0 && ia >= 0 && ia <= 3, use_b = jb >= 0 && ib >= 0 && ib <= 3;
-        if (!use_a && !use_b) continue;
-        const float wa = use_a ? w_at(m.W[k], ia) : 0.f, wb = use_b ? w_at(m.W[k], ib) : 0.f;
-        acc += wa * (comp ? colA[k].y : colA[k].x) + wb * (comp ? colB[k].y : colB[k].x);
-      }
+      const int r = q & 7;
+      j = r < 7 ? r : 3;
+      sg = r < 7 ? min(r / 3, 1) : 0;
+      src = q < 8 ? colA : colB;
     }
-    if (!closed) g.open_ctrl[(size_t)curve * 20 + q] = acc;
-    else g.closed_ctrl[(size_t)(curve - c.n_open) * 24 + q] = acc;
+    const int i = j - 3 * sg;
+    const int k0 = seg_first(sg, K, S), k1 = seg_first(sg + 1, K, S);
+    float acc = 0.f;
+    for (int k = k0; k < k1; ++k) acc += w_at(m.W[k], i) * (comp ? src[k].y : src[k].x);
+    s_item[it] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * npts; t += blockDim.x) {
+    const int p = t >> 1, comp = t & 1;
+    float acc = 0.f;
+    for (int q = 0; q < n_items / 2; ++q) {
+      int pq;  // the control point item q shapes
+      if (!closed) {
+        pq = q < 10 ? q : (q == 10 ? 3 : 6);
+      } else {
+        const int r = q & 7, j = r < 7 ? r : 3;
+        pq = q < 8 ? j : closed_b_index(j);
+      }
+      if (pq == p) acc += s_item[2 * q + comp];
+    }
+    if (!closed) g.open_ctrl[(size_t)curve * 20 + t] = acc;
+    else g.closed_ctrl[(size_t)(curve - c.n_open) * 24 + t] = acc;
   }
   if (!closed) {
     if (threadIdx.x < 3) {
