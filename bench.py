@@ -158,22 +158,22 @@ def run_ours(args, rank, world):
         return torch.cuda.Event(enable_timing=True)
     ev = [[mk() for _ in range(4)] for _ in range(args.steps)]
 
-    def step(e=None):
+    def step(e=None, cv=curves, tg=target, gr=grad):
         # forward: order, sample, bin, blend
-        r.rank, r.first = bs.curve_order(curves, cfg)
-        bs.sample_curves(curves, cfg, r.first, out=r.gauss)
+        r.rank, r.first = bs.curve_order(cv, cfg)
+        bs.sample_curves(cv, cfg, r.first, out=r.gauss)
         r.binning.run(r.gauss)
         if e:
             e[0].record(stream)
         # blend forward with the L2 loss and its gradient in the same pass
-        bs.render_fwd_l2(r.gauss, canvas, r.binning, target, out=(r.img, r.T, r.nc), dimg=r.dimg, loss=r.loss)
+        bs.render_fwd_l2(r.gauss, canvas, r.binning, tg, out=(r.img, r.T, r.nc), dimg=r.dimg, loss=r.loss)
         if e:
             e[1].record(stream)
             e[2].record(stream)
         bs.render_bwd(r.gauss, canvas, r.binning, r.T, r.nc, r.dimg, r.dgauss)
         if e:
             e[3].record(stream)
-        bs.sample_curves_bwd(curves, cfg, r.first, r.dgauss, grad)
+        bs.sample_curves_bwd(cv, cfg, r.first, r.dgauss, gr)
 
     for _ in range(args.warmup):
         step()
@@ -201,35 +201,68 @@ def run_ours(args, rank, world):
     ms_per_step = ms / args.steps
     value = job_throughput(world, args.steps, ms)
 
-    # end to end through the public API with host buffers: H2D of the step's
-    # inputs (curves + target) from pinned memory, D2H of loss and gradients
+    # end to end through the public API with host buffers: every step copies
+    # its inputs (curves + target) from pinned memory and reads its loss and
+    # gradients back.  Two device buffer sets and a copy stream: step i+1's
+    # inputs go up while step i computes, step i's results come down after
+    # it; every copy of every step is inside the timed region.
     host_in = {k: torch.as_tensor(v).pin_memory() for k, v in arrays.items()}
     host_target = torch.as_tensor(target_np).pin_memory()
-    host_out = {k: torch.empty_like(getattr(grad, k), device="cpu").pin_memory() for k in bs.CURVE_FIELDS}
-    host_loss = torch.empty((), dtype=torch.float64).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in host_in.values()) + host_target.numel() * 4
-    d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 8
+    d2h = sum(getattr(grad, k).numel() * getattr(grad, k).element_size() for k in bs.CURVE_FIELDS) + 8
+    bufs = []
+    for _ in range(2):
+        cv = bs.CurveSet(**{k: torch.empty_like(getattr(curves, k)) for k in bs.CURVE_FIELDS})
+        bufs.append({"cv": cv, "tg": torch.empty_like(target), "gr": curves.zeros_like(),
+                     "out": {k: torch.empty_like(getattr(grad, k), device="cpu").pin_memory()
+                             for k in bs.CURVE_FIELDS},
+                     "loss": torch.empty((), dtype=torch.float64).pin_memory(),
+                     "loss_dev": torch.empty((), dtype=torch.float64, device=dev),
+                     "up": torch.cuda.Event(), "done": torch.cuda.Event(), "down": torch.cuda.Event()})
+    copy = torch.cuda.Stream(device=dev)
 
-    def e2e_step():
-        for k in bs.CURVE_FIELDS:
-            getattr(curves, k).copy_(host_in[k], non_blocking=True)
-        target.copy_(host_target, non_blocking=True)
-        step()
-        for k in bs.CURVE_FIELDS:
-            host_out[k].copy_(getattr(grad, k), non_blocking=True)
-        host_loss.copy_(r.loss, non_blocking=True)
+    def upload(b):
+        with torch.cuda.stream(copy):
+            copy.wait_event(b["done"])      # the step that last used these buffers has finished
+            for k in bs.CURVE_FIELDS:
+                getattr(b["cv"], k).copy_(host_in[k], non_blocking=True)
+            b["tg"].copy_(host_target, non_blocking=True)
+            b["up"].record(copy)
+
+    def run_e2e(n):
+        for b in bufs:
+            b["done"].record(stream)
+            b["down"].record(stream)
+        upload(bufs[0])
+        for i in range(n):
+            b = bufs[i % 2]
+            if i + 1 < n:
+                upload(bufs[(i + 1) % 2])
+            stream.wait_event(b["up"])
+            stream.wait_event(b["down"])     # its gradients of two steps ago have been read back
+            step(cv=b["cv"], tg=b["tg"], gr=b["gr"])
+            b["loss_dev"].copy_(r.loss)       # the next step rewrites r.loss
+            b["done"].record(stream)
+            with torch.cuda.stream(copy):
+                copy.wait_event(b["done"])
+                for k in bs.CURVE_FIELDS:
+                    b["out"][k].copy_(getattr(b["gr"], k), non_blocking=True)
+                b["loss"].copy_(b["loss_dev"], non_blocking=True)
+                b["down"].record(copy)
         torch.cuda.synchronize()
 
-    for _ in range(2):
-        e2e_step()
+    run_e2e(3)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    run_e2e(args.steps)
     e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3, world, dev)
     e2e_value = job_throughput(world, args.steps, e_ms)
+    # same inputs as the device-timed steps: the same gradients up to the
+    # order of the backward's atomic sums
+    g_e2e, g_dev = bufs[(args.steps - 1) % 2]["out"]["open_ctrl"], grad.open_ctrl.cpu()
+    assert float((g_e2e - g_dev).abs().max()) <= 1e-3 * float(g_dev.abs().max()), "end-to-end gradients differ"
 
     # the periodic pass (every few hundred steps, outside the step): prune and
     # densify a copy of the curves against the last rendered image
