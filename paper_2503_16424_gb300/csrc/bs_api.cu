@@ -286,6 +286,10 @@ const BatchImage *batch_table_of(const bs_batch *b, const BatchPlan &p) {
   return reinterpret_cast<const BatchImage *>(static_cast<const char *>(b->ws) + p.off_images);
 }
 
+const int32_t *batch_curve_ids_of(const bs_batch *b, const BatchPlan &p) {
+  return reinterpret_cast<const int32_t *>(static_cast<const char *>(b->ws) + p.off_curve_ids);
+}
+
 }  // namespace
 
 extern "C" {
@@ -466,9 +470,14 @@ bs_status bs_batch_setup(const bs_batch *batch, bs_stream stream) {
   BS_TRY(check_device());
   std::vector<BatchImage> tab((size_t)p.n_images);
   fill_batch_table(batch->images, p, tab.data());
+  std::vector<int32_t> ids((size_t)p.n_curves);
+  fill_curve_classes(batch->images, p, ids.data());
   const cudaStream_t s = (cudaStream_t)stream;
   BS_CUDA(cudaMemcpyAsync(static_cast<char *>(batch->ws) + p.off_images, tab.data(), sizeof(BatchImage) * tab.size(),
                           cudaMemcpyHostToDevice, s));
+  if (!ids.empty())
+    BS_CUDA(cudaMemcpyAsync(static_cast<char *>(batch->ws) + p.off_curve_ids, ids.data(), sizeof(int32_t) * ids.size(),
+                            cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaStreamSynchronize(s));
   return BS_OK;
 }
@@ -489,7 +498,8 @@ bs_status bs_batch_sample_curves(const bs_batch *batch, const bs_curves *curves,
   BS_TRY(check_batch_curves(curves, p, true));
   if (p.n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
   BS_TRY(check_device());
-  return launch_batch_sample_fwd(p, batch_table_of(batch, p), *curves, gauss, (cudaStream_t)stream);
+  return launch_batch_sample_fwd(p, batch_table_of(batch, p), batch_curve_ids_of(batch, p), *curves, gauss,
+                                 (cudaStream_t)stream);
 }
 
 bs_status bs_batch_bin_tiles(const bs_batch *batch, const float *gauss, uint32_t *tile_vals, uint32_t *tile_ranges,
@@ -536,7 +546,8 @@ bs_status bs_batch_render_bwd(const bs_batch *batch, const float *gauss, const u
   const cudaStream_t s = (cudaStream_t)stream;
   BS_TRY(launch_batch_render_bwd(p, batch->ws, gauss, tile_vals, tile_ranges, T_final, n_contrib, dL_dimg, dgauss,
                                  s));
-  if (grad) return launch_batch_sample_bwd(p, batch_table_of(batch, p), *curves, dgauss, *grad, s);
+  if (grad) return launch_batch_sample_bwd(p, batch_table_of(batch, p), batch_curve_ids_of(batch, p), *curves, dgauss,
+                                           *grad, s);
   return BS_OK;
 }
 

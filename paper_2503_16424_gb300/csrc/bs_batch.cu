@@ -83,6 +83,8 @@ bs_status plan_batch(const bs_batch_image *images, int32_t n_images, int32_t til
     };
     if (im.n_open > 0) note(im.sample.g_open, im.sample.g_open, 1);
     if (im.n_closed > 0) note(im.sample.rows_closed * im.sample.k_closed, im.sample.k_closed, im.sample.rows_closed);
+    (im.sample.g_open < kWideSamples ? p->n_curves_narrow : p->n_curves_wide) += im.n_open;
+    (im.sample.rows_closed * im.sample.k_closed < kWideSamples ? p->n_curves_narrow : p->n_curves_wide) += im.n_closed;
   }
   p->n_curves = p->n_open + p->n_closed;
   if (p->n_curves > (1ll << 30)) {
@@ -116,6 +118,7 @@ bs_status plan_batch(const bs_batch_image *images, int32_t n_images, int32_t til
   p->zero_bytes = o;
   p->off_queue = o;   o = align256(o + sizeof(uint32_t) * 2);
   p->off_images = o;  o = align256(o + sizeof(BatchImage) * (size_t)n_images);
+  p->off_curve_ids = o;  o = align256(o + sizeof(int32_t) * (size_t)(p->n_curves > 0 ? p->n_curves : 1));
   p->off_parts = o;   o = align256(o + sizeof(uint32_t) * 256 * (size_t)p->parts);
   p->off_local = o;   o = align256(o + sizeof(uint32_t) * ng);
   p->off_partial = o; o = align256(o + sizeof(unsigned long long) * (size_t)(p->count_blocks + 1));
@@ -168,6 +171,20 @@ void fill_batch_table(const bs_batch_image *images, const BatchPlan &p, BatchIma
     row0 += e.tiles_y + 1;
     col0 += e.tiles_x + 1;
     order0 += (int64_t)e.order_chunks * e.order_chunks;
+  }
+}
+
+void fill_curve_classes(const bs_batch_image *images, const BatchPlan &p, int32_t *out) {
+  // curve indices: the open curves of all images, then the closed ones
+  int64_t narrow = 0, wide = p.n_curves_narrow, open0 = 0, closed0 = p.n_open;
+  for (int b = 0; b < p.n_images; ++b) {
+    const bs_batch_image &im = images[b];
+    const bool ow = im.sample.g_open >= kWideSamples;
+    const bool cw = im.sample.rows_closed * im.sample.k_closed >= kWideSamples;
+    for (int i = 0; i < im.n_open; ++i) out[ow ? wide++ : narrow++] = (int32_t)(open0 + i);
+    for (int i = 0; i < im.n_closed; ++i) out[cw ? wide++ : narrow++] = (int32_t)(closed0 + i);
+    open0 += im.n_open;
+    closed0 += im.n_closed;
   }
 }
 

@@ -323,18 +323,17 @@ __device__ __forceinline__ Cfg batch_cfg(const BatchImage *__restrict__ tab, int
   return Cfg{im.g_open, im.rows, im.kc, im.rho, im.eps};
 }
 
-// tab == nullptr: one canvas, sampling cfg; else a batch, each curve with
-// its image's sampling (dynamic shared memory sized for the largest).
+// tab == nullptr: one canvas, sampling cfg, CTA b samples curve b; else a
+// batch, CTA b samples curve curve_ids[b] with its image's sampling
+// (dynamic shared memory sized for the largest curve of the launch).
 __global__ void __launch_bounds__(kCurveThreadsWide) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss, int n_max,
                                                                    int k_max, const BatchImage *tab = nullptr,
-                                                                   int n_images = 0, int n_lo = 0,
-                                                                   int n_hi = 0x7fffffff) {
+                                                                   int n_images = 0,
+                                                                   const int32_t *curve_ids = nullptr) {
   extern __shared__ float4 smem_fwd[];
-  const int curve = blockIdx.x;
+  const int curve = curve_ids ? curve_ids[blockIdx.x] : (int)blockIdx.x;
   const bool closed = curve >= c.n_open;
   if (tab) cfg = batch_cfg(tab, n_images, c, curve);
-  const int n_curve = closed ? cfg.rows * cfg.kc : cfg.g_open;
-  if (n_curve < n_lo || n_curve >= n_hi) return;  // sampled by the other launch
   const CurveSmem m = carve(smem_fwd, n_max, k_max, cfg.rows, false);
   const int n = eval_samples(c, cfg, curve, m);
   const int K = closed ? cfg.kc : cfg.g_open;
@@ -379,20 +378,16 @@ __device__ __forceinline__ float warp_sum(float v) {
 __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
                                                                    bs_curves_grad g, int n_max, int k_max,
                                                                    const BatchImage *tab = nullptr,
-                                                                   int n_images = 0, int n_lo = 0,
-                                                                   int n_hi = 0x7fffffff) {
+                                                                   int n_images = 0,
+                                                                   const int32_t *curve_ids = nullptr) {
   extern __shared__ float4 smem_bwd[];
-  if (tab) cfg = batch_cfg(tab, n_images, c, blockIdx.x);
-  {
-    const int n_curve = (int)blockIdx.x >= c.n_open ? cfg.rows * cfg.kc : cfg.g_open;
-    if (n_curve < n_lo || n_curve >= n_hi) return;  // sampled by the other launch
-  }
+  const int curve = curve_ids ? curve_ids[blockIdx.x] : (int)blockIdx.x;
+  if (tab) cfg = batch_cfg(tab, n_images, c, curve);
   const CurveSmem m = carve(smem_bwd, n_max, k_max, cfg.rows, true);
   float2 *GM = m.G, *GE = m.G + n_max, *GT = m.G + 2 * n_max, *GF = m.G + 3 * n_max;
   // opac[3] (open) or opac (closed), colour[3], width, then (gradient
   // fills) the far-end opacity [7] and colour [8..10]
   __shared__ float sAttr[12];
-  const int curve = blockIdx.x;
   const bool closed = curve >= c.n_open;
   if (threadIdx.x < 12) sAttr[threadIdx.x] = 0.f;
   const int n = eval_samples(c, cfg, curve, m);
@@ -831,44 +826,43 @@ bs_status launch_batch_curve_order(const BatchPlan &p, const BatchImage *table, 
   return BS_OK;
 }
 
-bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, const bs_curves &c, float *gauss,
-                                  cudaStream_t s) {
-  const int n = c.n_open + c.n_closed;
-  if (n == 0) return BS_OK;
-  // curves below kWideSamples samples on narrow CTAs, the rest on wide ones,
-  // each launch with the shared memory of its own largest curve
-  if (p.n_max_narrow > 0) {
+bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, const int32_t *curve_ids,
+                                  const bs_curves &c, float *gauss, cudaStream_t s) {
+  // curves below kWideSamples samples on narrow CTAs, the rest on wide ones
+  // (curve_ids lists the narrow curves, then the wide ones), each launch
+  // with the shared memory of its own largest curve
+  if (p.n_curves_narrow > 0) {
     const size_t smem = curve_smem_bytes(p.n_max_narrow, p.k_max_narrow, p.rows_max_narrow, false);
     BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-    sample_fwd_kernel<<<n, kCurveThreads, smem, s>>>(c, Cfg{}, gauss, p.n_max_narrow, p.k_max_narrow, table,
-                                                     p.n_images, 0, kWideSamples);
+    sample_fwd_kernel<<<(unsigned)p.n_curves_narrow, kCurveThreads, smem, s>>>(
+        c, Cfg{}, gauss, p.n_max_narrow, p.k_max_narrow, table, p.n_images, curve_ids);
     BS_LAUNCHED("sample_fwd_kernel");
   }
-  if (p.n_max_wide > 0) {
+  if (p.n_curves_wide > 0) {
     const size_t smem = curve_smem_bytes(p.n_max_wide, p.k_max_wide, p.rows_max_wide, false);
     BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-    sample_fwd_kernel<<<n, kCurveThreadsWide, smem, s>>>(c, Cfg{}, gauss, p.n_max_wide, p.k_max_wide, table,
-                                                         p.n_images, kWideSamples);
+    sample_fwd_kernel<<<(unsigned)p.n_curves_wide, kCurveThreadsWide, smem, s>>>(
+        c, Cfg{}, gauss, p.n_max_wide, p.k_max_wide, table, p.n_images, curve_ids + p.n_curves_narrow);
     BS_LAUNCHED("sample_fwd_kernel");
   }
   return BS_OK;
 }
-bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, const bs_curves &c,
-                                  const float *dgauss, const bs_curves_grad &g, cudaStream_t s) {
-  const int n = c.n_open + c.n_closed;
-  if (n == 0) return BS_OK;
-  if (p.n_max_narrow > 0) {
+
+bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, const int32_t *curve_ids,
+                                  const bs_curves &c, const float *dgauss, const bs_curves_grad &g,
+                                  cudaStream_t s) {
+  if (p.n_curves_narrow > 0) {
     const size_t smem = curve_smem_bytes(p.n_max_narrow, p.k_max_narrow, p.rows_max_narrow, true);
     BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-    sample_bwd_kernel<<<n, kCurveThreads, smem, s>>>(c, Cfg{}, dgauss, g, p.n_max_narrow, p.k_max_narrow, table,
-                                                     p.n_images, 0, kWideSamples);
+    sample_bwd_kernel<<<(unsigned)p.n_curves_narrow, kCurveThreads, smem, s>>>(
+        c, Cfg{}, dgauss, g, p.n_max_narrow, p.k_max_narrow, table, p.n_images, curve_ids);
     BS_LAUNCHED("sample_bwd_kernel");
   }
-  if (p.n_max_wide > 0) {
+  if (p.n_curves_wide > 0) {
     const size_t smem = curve_smem_bytes(p.n_max_wide, p.k_max_wide, p.rows_max_wide, true);
     BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-    sample_bwd_kernel<<<n, kCurveThreadsWide, smem, s>>>(c, Cfg{}, dgauss, g, p.n_max_wide, p.k_max_wide, table,
-                                                         p.n_images, kWideSamples);
+    sample_bwd_kernel<<<(unsigned)p.n_curves_wide, kCurveThreadsWide, smem, s>>>(
+        c, Cfg{}, dgauss, g, p.n_max_wide, p.k_max_wide, table, p.n_images, curve_ids + p.n_curves_narrow);
     BS_LAUNCHED("sample_bwd_kernel");
   }
   return BS_OK;

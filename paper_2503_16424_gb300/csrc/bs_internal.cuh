@@ -183,9 +183,10 @@ struct BatchPlan {
   // the same over the curves of fewer than kWideSamples samples (sampled by
   // narrow CTAs) and over the others (wide CTAs); n_max 0: no such curve
   int n_max_narrow, k_max_narrow, rows_max_narrow, n_max_wide, k_max_wide, rows_max_wide;
+  int64_t n_curves_narrow, n_curves_wide;  // curves of each class
   // byte offsets inside the batch workspace
   size_t off_hdr, off_hist, off_diff, off_queue, zero_bytes;
-  size_t off_images, off_parts, off_local, off_partial, off_rects, off_owner, off_tsum, off_keys0, off_keys1;
+  size_t off_images, off_curve_ids, off_parts, off_local, off_partial, off_rects, off_owner, off_tsum, off_keys0, off_keys1;
   size_t bytes;
 };
 
@@ -224,14 +225,17 @@ __device__ __forceinline__ int last_image_le(const BatchImage *__restrict__ tab,
 bs_status plan_batch(const bs_batch_image *images, int32_t n_images, int32_t tile, int64_t capacity,
                      BatchPlan *p);
 void fill_batch_table(const bs_batch_image *images, const BatchPlan &p, BatchImage *out);
+// The batch's curve indices, the narrow class first, then the wide one
+// (curves of fewer / at least kWideSamples samples); out holds n_curves.
+void fill_curve_classes(const bs_batch_image *images, const BatchPlan &p, int32_t *out);
 
 // launchers of the batched kernels; `table` is the device table in the workspace
 bs_status launch_batch_curve_order(const BatchPlan &p, const BatchImage *table, const bs_curves &c,
                                    uint32_t *rank, uint32_t *first, cudaStream_t s);
-bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, const bs_curves &c, float *gauss,
-                                  cudaStream_t s);
-bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, const bs_curves &c,
-                                  const float *dgauss, const bs_curves_grad &g, cudaStream_t s);
+bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, const int32_t *curve_ids,
+                                  const bs_curves &c, float *gauss, cudaStream_t s);
+bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, const int32_t *curve_ids,
+                                  const bs_curves &c, const float *dgauss, const bs_curves_grad &g, cudaStream_t s);
 bs_status run_batch_binning(const BatchPlan &p, void *ws, const float *gauss, uint32_t *tile_vals,
                             uint32_t *tile_ranges, cudaStream_t s);
 bs_status read_batch_status(const BatchPlan &p, const void *ws, int32_t *status, int64_t *n_pairs, cudaStream_t s);
