@@ -446,8 +446,10 @@ typedef struct {
  * so any batch whose tiles and Gaussians each fit in 32 bits is accepted. */
 bs_status bs_batch_plan(const bs_batch *batch, bs_batch_sizes *out);
 
-/* Write the layout's device table into the workspace (one host-to-device
- * copy, synchronous).  Call once before the other batched calls, and again
+/* Write the layout's device table into the workspace, and the curve
+ * indices grouped by sample count (curves of fewer than 512 samples, then
+ * the rest; the batched sampling runs each group in its own launch) (two
+ * host-to-device copies, synchronous).  Call once before the other batched calls, and again
  * whenever images, tile or pair_capacity change; every later call must pass
  * the same images, tile and pair_capacity. */
 bs_status bs_batch_setup(const bs_batch *batch, bs_stream stream);
