@@ -70,21 +70,26 @@ bs_status plan_batch(const bs_batch_image *images, int32_t n_images, int32_t til
     p->diff_rows += ty + 1;
     p->diff_cols += tx + 1;
     p->order_ctas += chunks * chunks;
-    const auto note = [p](int n, int k, int rows) {
+    const auto cls = [p](int n) -> BatchPlan::SampleClass & { return n < kWideSamples ? p->narrow : p->wide; };
+    if (im.n_open > 0) {
+      const int n = im.sample.g_open;
       p->n_max = std::max(p->n_max, n);
-      p->k_max = std::max(p->k_max, k);
-      p->rows_max = std::max(p->rows_max, rows);
-      int *cls = n < kWideSamples ? &p->n_max_narrow : &p->n_max_wide;  // n, k, rows of the class
-      int *kc = n < kWideSamples ? &p->k_max_narrow : &p->k_max_wide;
-      int *rc = n < kWideSamples ? &p->rows_max_narrow : &p->rows_max_wide;
-      *cls = std::max(*cls, n);
-      *kc = std::max(*kc, k);
-      *rc = std::max(*rc, rows);
-    };
-    if (im.n_open > 0) note(im.sample.g_open, im.sample.g_open, 1);
-    if (im.n_closed > 0) note(im.sample.rows_closed * im.sample.k_closed, im.sample.k_closed, im.sample.rows_closed);
-    (im.sample.g_open < kWideSamples ? p->n_curves_narrow : p->n_curves_wide) += im.n_open;
-    (im.sample.rows_closed * im.sample.k_closed < kWideSamples ? p->n_curves_narrow : p->n_curves_wide) += im.n_closed;
+      p->k_max = std::max(p->k_max, n);
+      BatchPlan::SampleClass &c = cls(n);
+      c.n_curves += im.n_open;
+      c.open_g = std::max(c.open_g, n);
+    }
+    if (im.n_closed > 0) {
+      const int n = im.sample.rows_closed * im.sample.k_closed;
+      p->n_max = std::max(p->n_max, n);
+      p->k_max = std::max(p->k_max, im.sample.k_closed);
+      p->rows_max = std::max(p->rows_max, im.sample.rows_closed);
+      BatchPlan::SampleClass &c = cls(n);
+      c.n_curves += im.n_closed;
+      c.closed_n = std::max(c.closed_n, n);
+      c.closed_k = std::max(c.closed_k, im.sample.k_closed);
+      c.closed_rows = std::max(c.closed_rows, im.sample.rows_closed);
+    }
   }
   p->n_curves = p->n_open + p->n_closed;
   if (p->n_curves > (1ll << 30)) {
@@ -176,7 +181,7 @@ void fill_batch_table(const bs_batch_image *images, const BatchPlan &p, BatchIma
 
 void fill_curve_classes(const bs_batch_image *images, const BatchPlan &p, int32_t *out) {
   // curve indices: the open curves of all images, then the closed ones
-  int64_t narrow = 0, wide = p.n_curves_narrow, open0 = 0, closed0 = p.n_open;
+  int64_t narrow = 0, wide = p.narrow.n_curves, open0 = 0, closed0 = p.n_open;
   for (int b = 0; b < p.n_images; ++b) {
     const bs_batch_image &im = images[b];
     const bool ow = im.sample.g_open >= kWideSamples;

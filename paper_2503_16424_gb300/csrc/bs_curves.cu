@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "bs_internal.cuh"
 
 namespace bs {
@@ -133,37 +135,49 @@ struct CurveSmem {
   float2 *D, *tau, *G;
 };
 
-__host__ __device__ inline size_t curve_smem_bytes(int n_max, int k_max, int rows, bool with_grad) {
-  return sizeof(float4) * (12 + 4 * (size_t)k_max) + sizeof(float2) * ((size_t)k_max + (size_t)rows) +
-         (with_grad ? sizeof(float2) * 4 * (size_t)(n_max > k_max ? n_max : k_max) : sizeof(float4) * (size_t)k_max);
+// Bytes of one curve's tables in carve's layout: n samples, k columns,
+// rows rows; an open curve has no EB, XB, D or tau.
+__host__ __device__ inline size_t curve_smem_bytes(bool closed, int n, int k, int rows, bool with_grad) {
+  size_t b = sizeof(float4) * (12 + (closed ? 4 : 3) * (size_t)k);
+  if (with_grad) b += sizeof(float2) * 4 * (size_t)(n > k ? n : k);  // G (XB in its place)
+  else if (closed) b += sizeof(float4) * (size_t)k;                     // XB
+  if (closed) b += sizeof(float2) * ((size_t)k + (size_t)rows);         // D, tau
+  return b;
 }
 
-__device__ __forceinline__ CurveSmem carve(void *base, int n_max, int k_max, int rows, bool with_grad) {
-  // the float4 tables first, then G (or XB), then the float2 tables: every
-  // table starts on a multiple of its element size
+// The tables of one curve from its own sizes: the float4 tables first, then
+// G (or XB), then the float2 tables, so that every table starts on a
+// multiple of its element size.
+__device__ __forceinline__ CurveSmem carve(void *base, bool closed, int n, int k, int rows, bool with_grad) {
   CurveSmem m;
   char *p = static_cast<char *>(base);
   m.Q = reinterpret_cast<float4 *>(p);
   p += sizeof(float4) * 12;
   m.W = reinterpret_cast<float4 *>(p);
-  p += sizeof(float4) * k_max;
+  p += sizeof(float4) * k;
   m.XA = reinterpret_cast<float4 *>(p);
-  p += sizeof(float4) * k_max;
+  p += sizeof(float4) * k;
   m.EA = reinterpret_cast<float4 *>(p);
-  p += sizeof(float4) * k_max;
-  m.EB = reinterpret_cast<float4 *>(p);
-  p += sizeof(float4) * k_max;
-  m.XB = reinterpret_cast<float4 *>(p);  // with a G: in G's place ([k_max] float4 fits in [4][n_max] float2)
+  p += sizeof(float4) * k;
+  m.EB = nullptr;
+  if (closed) {
+    m.EB = reinterpret_cast<float4 *>(p);
+    p += sizeof(float4) * k;
+  }
+  m.XB = reinterpret_cast<float4 *>(p);  // with a G: in G's place ([k] float4 fits in [4][n] float2)
+  m.G = nullptr;
   if (with_grad) {
     m.G = reinterpret_cast<float2 *>(p);
-    p += sizeof(float2) * 4 * (size_t)(n_max > k_max ? n_max : k_max);
-  } else {
-    m.G = nullptr;
-    p += sizeof(float4) * k_max;
+    p += sizeof(float2) * 4 * (size_t)(n > k ? n : k);
+  } else if (closed) {
+    p += sizeof(float4) * k;
   }
-  m.D = reinterpret_cast<float2 *>(p);
-  p += sizeof(float2) * k_max;
-  m.tau = reinterpret_cast<float2 *>(p);
+  m.D = m.tau = nullptr;
+  if (closed) {
+    m.D = reinterpret_cast<float2 *>(p);
+    p += sizeof(float2) * k;
+    m.tau = reinterpret_cast<float2 *>(p);
+  }
   return m;
 }
 
@@ -326,15 +340,16 @@ __device__ __forceinline__ Cfg batch_cfg(const BatchImage *__restrict__ tab, int
 // tab == nullptr: one canvas, sampling cfg, CTA b samples curve b; else a
 // batch, CTA b samples curve curve_ids[b] with its image's sampling
 // (dynamic shared memory sized for the largest curve of the launch).
-__global__ void __launch_bounds__(kCurveThreadsWide) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss, int n_max,
-                                                                   int k_max, const BatchImage *tab = nullptr,
+__global__ void __launch_bounds__(kCurveThreadsWide) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss,
+                                                                   const BatchImage *tab = nullptr,
                                                                    int n_images = 0,
                                                                    const int32_t *curve_ids = nullptr) {
   extern __shared__ float4 smem_fwd[];
   const int curve = curve_ids ? curve_ids[blockIdx.x] : (int)blockIdx.x;
   const bool closed = curve >= c.n_open;
   if (tab) cfg = batch_cfg(tab, n_images, c, curve);
-  const CurveSmem m = carve(smem_fwd, n_max, k_max, cfg.rows, false);
+  const CurveSmem m = carve(smem_fwd, closed, closed ? cfg.rows * cfg.kc : cfg.g_open, closed ? cfg.kc : cfg.g_open,
+                            closed ? cfg.rows : 1, false);
   const int n = eval_samples(c, cfg, curve, m);
   const int K = closed ? cfg.kc : cfg.g_open;
   const uint32_t first = c.draw_first[curve];
@@ -376,19 +391,20 @@ __device__ __forceinline__ float warp_sum(float v) {
 // coordinate gathers the Bernstein-weighted (and, for closed rows,
 // tau-weighted, Eq. 4) gradients of the sample points it moves.
 __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
-                                                                   bs_curves_grad g, int n_max, int k_max,
+                                                                   bs_curves_grad g,
                                                                    const BatchImage *tab = nullptr,
                                                                    int n_images = 0,
                                                                    const int32_t *curve_ids = nullptr) {
   extern __shared__ float4 smem_bwd[];
   const int curve = curve_ids ? curve_ids[blockIdx.x] : (int)blockIdx.x;
   if (tab) cfg = batch_cfg(tab, n_images, c, curve);
-  const CurveSmem m = carve(smem_bwd, n_max, k_max, cfg.rows, true);
-  float2 *GM = m.G, *GE = m.G + n_max, *GT = m.G + 2 * n_max, *GF = m.G + 3 * n_max;
+  const bool closed = curve >= c.n_open;
+  const int n_here = closed ? cfg.rows * cfg.kc : cfg.g_open;
+  const CurveSmem m = carve(smem_bwd, closed, n_here, closed ? cfg.kc : cfg.g_open, closed ? cfg.rows : 1, true);
+  float2 *GM = m.G, *GE = m.G + n_here, *GT = m.G + 2 * n_here, *GF = m.G + 3 * n_here;
   // opac[3] (open) or opac (closed), colour[3], width, then (gradient
   // fills) the far-end opacity [7] and colour [8..10]
   __shared__ float sAttr[12];
-  const bool closed = curve >= c.n_open;
   if (threadIdx.x < 12) sAttr[threadIdx.x] = 0.f;
   const int n = eval_samples(c, cfg, curve, m);
   const int K = closed ? cfg.kc : cfg.g_open, R2 = closed ? cfg.rows : 1;
@@ -747,11 +763,23 @@ int max_samples(const bs_curves &c, const bs_sample_cfg &cfg) {
   return m;
 }
 
-int max_k(const bs_curves &c, const bs_sample_cfg &cfg) {
-  int m = 0;
-  if (c.n_open > 0) m = cfg.g_open;
-  if (c.n_closed > 0) m = max(m, cfg.k_closed);
-  return m;
+// Shared memory for a launch whose largest open curve has open_g samples
+// and whose largest closed curve closed_n samples in closed_rows rows of
+// closed_k (0: no such curve).
+size_t launch_smem(int open_g, int closed_n, int closed_k, int closed_rows, bool with_grad) {
+  size_t b = 0;
+  if (open_g > 0) b = curve_smem_bytes(false, open_g, open_g, 1, with_grad);
+  if (closed_n > 0) b = std::max(b, curve_smem_bytes(true, closed_n, closed_k, closed_rows, with_grad));
+  return b;
+}
+
+size_t launch_smem(const BatchPlan::SampleClass &k, bool with_grad) {
+  return launch_smem(k.open_g, k.closed_n, k.closed_k, k.closed_rows, with_grad);
+}
+
+size_t launch_smem(const bs_curves &c, const bs_sample_cfg &cfg, bool with_grad) {
+  return launch_smem(c.n_open > 0 ? cfg.g_open : 0, c.n_closed > 0 ? cfg.rows_closed * cfg.k_closed : 0,
+                     cfg.k_closed, cfg.rows_closed, with_grad);
 }
 
 }  // namespace
@@ -793,10 +821,9 @@ bs_status launch_curve_order(const bs_curves &c, const bs_sample_cfg &cfg, uint3
 bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float *gauss, cudaStream_t s) {
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
-  const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
-  const size_t smem = curve_smem_bytes(n_max, k_max, cfg.rows_closed, false);
+  const size_t smem = launch_smem(c, cfg, false);
   BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-  sample_fwd_kernel<<<n, curve_threads(n_max), smem, s>>>(c, to_cfg(cfg), gauss, n_max, k_max);
+  sample_fwd_kernel<<<n, curve_threads(max_samples(c, cfg)), smem, s>>>(c, to_cfg(cfg), gauss);
   BS_LAUNCHED("sample_fwd_kernel");
   return BS_OK;
 }
@@ -805,10 +832,9 @@ bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const 
                             const bs_curves_grad &g, cudaStream_t s) {
   const int n = c.n_open + c.n_closed;
   if (n == 0) return BS_OK;
-  const int n_max = max_samples(c, cfg), k_max = max_k(c, cfg);
-  const size_t smem = curve_smem_bytes(n_max, k_max, cfg.rows_closed, true);
+  const size_t smem = launch_smem(c, cfg, true);
   BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-  sample_bwd_kernel<<<n, curve_threads(n_max), smem, s>>>(c, to_cfg(cfg), dgauss, g, n_max, k_max);
+  sample_bwd_kernel<<<n, curve_threads(max_samples(c, cfg)), smem, s>>>(c, to_cfg(cfg), dgauss, g);
   BS_LAUNCHED("sample_bwd_kernel");
   return BS_OK;
 }
@@ -830,19 +856,19 @@ bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, c
                                   const bs_curves &c, float *gauss, cudaStream_t s) {
   // curves below kWideSamples samples on narrow CTAs, the rest on wide ones
   // (curve_ids lists the narrow curves, then the wide ones), each launch
-  // with the shared memory of its own largest curve
-  if (p.n_curves_narrow > 0) {
-    const size_t smem = curve_smem_bytes(p.n_max_narrow, p.k_max_narrow, p.rows_max_narrow, false);
+  // with the shared memory of its own largest curves
+  if (p.narrow.n_curves > 0) {
+    const size_t smem = launch_smem(p.narrow, false);
     BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-    sample_fwd_kernel<<<(unsigned)p.n_curves_narrow, kCurveThreads, smem, s>>>(
-        c, Cfg{}, gauss, p.n_max_narrow, p.k_max_narrow, table, p.n_images, curve_ids);
+    sample_fwd_kernel<<<(unsigned)p.narrow.n_curves, kCurveThreads, smem, s>>>(c, Cfg{}, gauss, table, p.n_images,
+                                                                               curve_ids);
     BS_LAUNCHED("sample_fwd_kernel");
   }
-  if (p.n_curves_wide > 0) {
-    const size_t smem = curve_smem_bytes(p.n_max_wide, p.k_max_wide, p.rows_max_wide, false);
+  if (p.wide.n_curves > 0) {
+    const size_t smem = launch_smem(p.wide, false);
     BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-    sample_fwd_kernel<<<(unsigned)p.n_curves_wide, kCurveThreadsWide, smem, s>>>(
-        c, Cfg{}, gauss, p.n_max_wide, p.k_max_wide, table, p.n_images, curve_ids + p.n_curves_narrow);
+    sample_fwd_kernel<<<(unsigned)p.wide.n_curves, kCurveThreadsWide, smem, s>>>(c, Cfg{}, gauss, table, p.n_images,
+                                                                                 curve_ids + p.narrow.n_curves);
     BS_LAUNCHED("sample_fwd_kernel");
   }
   return BS_OK;
@@ -851,18 +877,19 @@ bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, c
 bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, const int32_t *curve_ids,
                                   const bs_curves &c, const float *dgauss, const bs_curves_grad &g,
                                   cudaStream_t s) {
-  if (p.n_curves_narrow > 0) {
-    const size_t smem = curve_smem_bytes(p.n_max_narrow, p.k_max_narrow, p.rows_max_narrow, true);
+  if (p.narrow.n_curves > 0) {
+    const size_t smem = launch_smem(p.narrow, true);
     BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-    sample_bwd_kernel<<<(unsigned)p.n_curves_narrow, kCurveThreads, smem, s>>>(
-        c, Cfg{}, dgauss, g, p.n_max_narrow, p.k_max_narrow, table, p.n_images, curve_ids);
+    sample_bwd_kernel<<<(unsigned)p.narrow.n_curves, kCurveThreads, smem, s>>>(c, Cfg{}, dgauss, g, table,
+                                                                               p.n_images, curve_ids);
     BS_LAUNCHED("sample_bwd_kernel");
   }
-  if (p.n_curves_wide > 0) {
-    const size_t smem = curve_smem_bytes(p.n_max_wide, p.k_max_wide, p.rows_max_wide, true);
+  if (p.wide.n_curves > 0) {
+    const size_t smem = launch_smem(p.wide, true);
     BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-    sample_bwd_kernel<<<(unsigned)p.n_curves_wide, kCurveThreadsWide, smem, s>>>(
-        c, Cfg{}, dgauss, g, p.n_max_wide, p.k_max_wide, table, p.n_images, curve_ids + p.n_curves_narrow);
+    sample_bwd_kernel<<<(unsigned)p.wide.n_curves, kCurveThreadsWide, smem, s>>>(c, Cfg{}, dgauss, g, table,
+                                                                                 p.n_images,
+                                                                                 curve_ids + p.narrow.n_curves);
     BS_LAUNCHED("sample_bwd_kernel");
   }
   return BS_OK;

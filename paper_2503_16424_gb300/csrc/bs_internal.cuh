@@ -180,10 +180,12 @@ struct BatchPlan {
   int tbits, passes, digit_bits;
   int64_t capacity, parts, count_blocks, tile_blocks;
   int n_max, k_max, rows_max;  // sampling: largest samples per curve / per row, rows
-  // the same over the curves of fewer than kWideSamples samples (sampled by
-  // narrow CTAs) and over the others (wide CTAs); n_max 0: no such curve
-  int n_max_narrow, k_max_narrow, rows_max_narrow, n_max_wide, k_max_wide, rows_max_wide;
-  int64_t n_curves_narrow, n_curves_wide;  // curves of each class
+  // The curves of fewer than kWideSamples samples (sampled by narrow CTAs)
+  // and the others (wide CTAs): their count and largest sizes (0: none).
+  struct SampleClass {
+    int64_t n_curves;
+    int open_g, closed_n, closed_k, closed_rows;
+  } narrow, wide;
   // byte offsets inside the batch workspace
   size_t off_hdr, off_hist, off_diff, off_queue, zero_bytes;
   size_t off_images, off_curve_ids, off_parts, off_local, off_partial, off_rects, off_owner, off_tsum, off_keys0, off_keys1;
