@@ -37,6 +37,10 @@ CASES = {
     "ragged": Case("ragged", 100, 73, 12, 6, "local", 12, 5, 7, 2, bg=(0.2, 0.5, 0.1), dup=2),
     # several sort partitions, both curve kinds
     "mixed": Case("mixed", 192, 160, 40, 24, "local", 16, 4, 8, 3, bg=(0.0, 0.3, 0.6), dup=3),
+    # curves of 512 samples or more (sampled by the wide CTAs): open curves
+    # of 600 samples, closed curves of R = 80 interior rows (82 x 8), whose
+    # rows near the boundaries are thin
+    "dense": Case("dense", 120, 90, 2, 2, "local", 600, 82, 8, 4, bg=(0.1, 0.1, 0.1)),
 }
 
 

@@ -34,8 +34,9 @@ def bs():
 
 
 # (W, H, n_open, n_closed, g_open, rows, kc, bg, seed): ragged canvases, an
-# open-only, a closed-only, a 1x1 and a curve-free image, and one with
-# enough pairs for several sort partitions
+# open-only, a closed-only, a 1x1 and a curve-free image, one with enough
+# pairs for several sort partitions, and one whose curves have 512 samples
+# or more (so the batch's sampling runs both the narrow and the wide launch)
 SPECS = [
     (100, 73, 12, 6, 12, 5, 7, (0.2, 0.5, 0.1), 11),
     (64, 48, 6, 0, 10, 4, 6, (0.0, 0.0, 0.0), 12),
@@ -43,6 +44,7 @@ SPECS = [
     (1, 1, 2, 1, 6, 3, 4, (0.1, 0.2, 0.3), 14),
     (48, 40, 0, 0, 8, 4, 4, (0.5, 0.4, 0.3), 15),
     (256, 200, 60, 30, 16, 4, 8, (0.0, 0.1, 0.2), 16),
+    (90, 70, 2, 2, 600, 82, 8, (0.2, 0.2, 0.2), 17),
 ]
 
 
