@@ -74,7 +74,9 @@ def spacing_sampling(images, arrs, max_spacing: float = 8.0):
     return out
 
 
-def _with_sampling(images, picks):
+def with_sampling(images, picks):
+    """The images with their sampling replaced: picks[b] = (g_open,
+    rows_closed, k_closed) for image b."""
     return [bs.BatchImage(im.width, im.height, im.n_open, im.n_closed,
                           bs.SampleCfg(g_open=g, rows_closed=r, k_closed=k, rho=im.sample.rho,
                                        cov_eps=im.sample.cov_eps), im.bg)
@@ -94,11 +96,11 @@ def pick_sampling(images, curves: bs.CurveSet, psnr_min: float = 35.0, schedule=
     psnr_min dB (PSNR, peak 1) of the `reference` sampling's render, else
     the last entry.  Returns (images with those samplings, per-image PSNR
     table {entry: [dB per image]})."""
-    ref = _render(_with_sampling(images, [reference] * len(images)), curves, tile, device)
+    ref = _render(with_sampling(images, [reference] * len(images)), curves, tile, device)
     table = {}
     picks = [None] * len(images)
     for entry in schedule:
-        r = _render(_with_sampling(images, [entry] * len(images)), curves, tile, device)
+        r = _render(with_sampling(images, [entry] * len(images)), curves, tile, device)
         dbs = []
         for b in range(len(images)):
             d = (r.batch.image(r.img, b) - ref.batch.image(ref.img, b)).double()
@@ -110,7 +112,7 @@ def pick_sampling(images, curves: bs.CurveSet, psnr_min: float = 35.0, schedule=
         table[entry] = dbs
         del r
     picks = [p if p is not None else schedule[-1] for p in picks]
-    return _with_sampling(images, picks), table
+    return with_sampling(images, picks), table
 
 
 def pick_tile(images, curves: bs.CurveSet, target: torch.Tensor, tiles=TILES, steps: int = 4, device="cuda"):
@@ -141,7 +143,7 @@ def autotune(images, curves: bs.CurveSet, target: torch.Tensor, arrs=None, rule:
     or "fidelity"), then the tile side for that sampling.  Returns
     (images, tile, report)."""
     if rule == "spacing":
-        tuned = _with_sampling(images, spacing_sampling(images, arrs, max_spacing))
+        tuned = with_sampling(images, spacing_sampling(images, arrs, max_spacing))
         table = {}
     else:
         tuned, table = pick_sampling(images, curves, psnr_min, device=device)

@@ -263,7 +263,7 @@ def main():
     layout = synth.batch_layout(W["seed"], W["n_images"], W["side"], W["aspect"], W["curves"])
     arrs, cat, targets = synth.batch_inputs(layout, W["n_shapes"])
     base = [BatchImage(e["W"], e["H"], e["n_open"], e["n_closed"], bs.SampleCfg()) for e in layout]
-    images = autotune._with_sampling(base, autotune.spacing_sampling(base, arrs))
+    images = autotune.with_sampling(base, autotune.spacing_sampling(base, arrs))
     target = torch.as_tensor(np.concatenate([t.reshape(-1) for t in targets]), device=dev)
     curves = CurveSet.from_arrays(cat, device=dev)
     rast = BatchRasterizer(images, tile=args.tile, pair_capacity=1 << 24, device=dev)
