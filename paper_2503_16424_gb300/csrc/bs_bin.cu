@@ -86,6 +86,22 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
   return v;
 }
 
+// The four corner updates of a rectangle [tx0, tx1] x [ty0, ty1] in a 2D
+// difference array of row stride `stride`; the lanes of `active` (all
+// calling, with this warp's other lanes not) that update the same cell add
+// once, through the lowest of them.
+__device__ __forceinline__ void add_corners(unsigned active, int *d, int stride, const Rect &r) {
+  const int lane = threadIdx.x & 31;
+  int *const cell[4] = {d + r.ty0 * stride + r.tx0, d + r.ty0 * stride + r.tx1 + 1, d + (r.ty1 + 1) * stride + r.tx0,
+                        d + (r.ty1 + 1) * stride + r.tx1 + 1};
+  const int sign[4] = {1, -1, -1, 1};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned peers = __match_any_sync(active, (unsigned long long)(uintptr_t)cell[k]);
+    if (lane == __ffs(peers) - 1) atomicAdd(cell[k], sign[k] * __popc(peers));
+  }
+}
+
 __global__ void zero_kernel(uint32_t *a, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = 0u;
@@ -102,20 +118,19 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(const float *gauss
   const int64_t g = (int64_t)blockIdx.x * kCountThreads + threadIdx.x;
   uint32_t cnt = 0;
   Rect r;
+  bool ok = false;
   if (g < n_gauss) {
     uint2 packed = make_uint2(0u, 0u);
-    if (tile_rect(gauss, g, W, H, tile, &r)) {
+    ok = tile_rect(gauss, g, W, H, tile, &r);
+    if (ok) {
       const uint32_t w = (uint32_t)(r.tx1 - r.tx0 + 1), h = (uint32_t)(r.ty1 - r.ty0 + 1);
       cnt = w * h;
       packed = make_uint2((uint32_t)r.tx0 | ((uint32_t)r.ty0 << 16), w | (h << 16));
-      const int stride = tiles_x + 1;
-      atomicAdd(diff + r.ty0 * stride + r.tx0, 1);
-      atomicAdd(diff + r.ty0 * stride + r.tx1 + 1, -1);
-      atomicAdd(diff + (r.ty1 + 1) * stride + r.tx0, -1);
-      atomicAdd(diff + (r.ty1 + 1) * stride + r.tx1 + 1, 1);
     }
     rects[g] = packed;
   }
+  const unsigned active = __ballot_sync(0xffffffffu, ok);
+  if (ok) add_corners(active, diff, tiles_x + 1, r);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t incl = warp_incl_scan(cnt, lane);
   if (lane == 31) s_warp[warp] = incl;
@@ -693,23 +708,25 @@ __global__ void __launch_bounds__(kCountThreads) batch_count_kernel(const float 
   __shared__ uint32_t s_warp[kCountThreads / 32];
   const int64_t g = (int64_t)blockIdx.x * kCountThreads + threadIdx.x;
   uint32_t cnt = 0;
+  Rect r;
+  bool ok = false;
+  int *d = nullptr;
+  int stride = 0;
   if (g < n_gauss) {
     const BatchImage &im = tab[last_image_le<&BatchImage::gauss0>(tab, n_images, g)];
     uint4 packed = make_uint4(0u, 0u, 0u, 0u);
-    Rect r;
-    if (tile_rect(gauss, g, im.W, im.H, tile, &r)) {
+    ok = tile_rect(gauss, g, im.W, im.H, tile, &r);
+    if (ok) {
       const uint32_t w = (uint32_t)(r.tx1 - r.tx0 + 1), h = (uint32_t)(r.ty1 - r.ty0 + 1);
       cnt = w * h;
       packed = make_uint4((uint32_t)(im.tile0 + (int64_t)r.ty0 * im.tiles_x + r.tx0), (uint32_t)im.tiles_x, w, h);
-      const int stride = im.tiles_x + 1;
-      int *d = diff + im.diff0;
-      atomicAdd(d + r.ty0 * stride + r.tx0, 1);
-      atomicAdd(d + r.ty0 * stride + r.tx1 + 1, -1);
-      atomicAdd(d + (r.ty1 + 1) * stride + r.tx0, -1);
-      atomicAdd(d + (r.ty1 + 1) * stride + r.tx1 + 1, 1);
+      stride = im.tiles_x + 1;
+      d = diff + im.diff0;
     }
     rects[g] = packed;
   }
+  const unsigned active = __ballot_sync(0xffffffffu, ok);
+  if (ok) add_corners(active, d, stride, r);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t incl = warp_incl_scan(cnt, lane);
   if (lane == 31) s_warp[warp] = incl;
