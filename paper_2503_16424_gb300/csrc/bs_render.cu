@@ -170,34 +170,20 @@ __device__ __forceinline__ Staged stage_slot(const StageBuf<kBatch> &buf, uint32
   return stage_rec(buf.rec[0][threadIdx.x], buf.rec[1][threadIdx.x], buf.rec[2][threadIdx.x]);
 }
 
-// Smallest t1^2 + t2^2 over the rectangle [dx0, dx1] x [dy0, dy1] of offsets
-// from the mean: 0 if the mean is inside, else the least value on the four
-// edges (a convex quadratic restricted to a segment, minimised in closed
-// form and clamped).  r_axx = -axy / axx and r_byy = -axy / byy give the
-// minimising coordinate on an edge; any point of the edge bounds the minimum
-// from above, so rounding in them only makes the test more conservative.
-__device__ __forceinline__ float min_q_rect(float A1, float B1, float A2, float B2, float r_axx, float r_byy,
-                                            float dx0, float dx1, float dy0, float dy1) {
-  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
-  float best = INFINITY;
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const float X = e ? dx1 : dx0;
-    const float y = fminf(fmaxf(r_byy * X, dy0), dy1);
-    const float t1 = A1 * X + B1 * y, t2 = A2 * X + B2 * y;
-    best = fminf(best, t1 * t1 + t2 * t2);
-    const float Y = e ? dy1 : dy0;
-    const float x = fminf(fmaxf(r_axx * Y, dx0), dx1);
-    const float u1 = A1 * x + B1 * Y, u2 = A2 * x + B2 * Y;
-    best = fminf(best, u1 * u1 + u2 * u2);
-  }
-  return best;
-}
-
 // Bit Geo<T>::bit(block_col, block_row) set: the Gaussian can reach alpha
 // >= 1/255 at some pixel centre of the 8x4 block (block_col, block_row) of
 // the tile whose first pixel is (x0, y0).  Blocks outside the Gaussian's box
-// (mean +- ext) are cleared first; the others get the exact ellipse test.
+// (mean +- ext) are cleared first; the others get an exact test by block
+// row.  With q = t1^2 + t2^2 = axx dx^2 + 2 axy dx dy + byy dy^2 and L the
+// threshold, the chord of the ellipse q <= L at height dy is
+//     dx in [r dy - h(dy), r dy + h(dy)],  r = -axy / axx,
+//     h(dy) = sqrt((L - k dy^2) / axx),     k = det / axx,
+// det = axx byy - axy^2 = (A1 B2 - A2 B1)^2.  Over a block row's band of
+// pixel-centre heights the right end r dy + h(dy) is concave in dy, so its
+// largest value is at the band point nearest the height of the ellipse's
+// rightmost point, dy* = -(axy / byy) Xm with Xm = sqrt(L byy / det) (the
+// left end likewise at -dy*): one chord per side and band gives the
+// ellipse's x-extent in the band, tested against each block column.
 // Conservative by a margin far above the float32 error of either side, so a
 // cleared bit only skips pixels that the blend would skip anyway.
 template <int kT>
@@ -219,21 +205,36 @@ __device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, flo
 #pragma unroll
   for (int br = 0; br < kT / 4; ++br)
     if (rows & (1u << br)) cand |= G::row_bits(cols, br);
-  const float lim = thr + (1e-2f + 1e-4f * thr);
+  if (!cand) return 0u;
+  const float L = thr + (1e-2f + 1e-4f * thr);
   const float A1 = s.a.z, B1 = s.a.w, A2 = s.b.x, B2 = s.b.y;
   const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
-  // axx, byy > 0 for a staged Gaussian (isx, isy > 0 and (ux, uy) a unit vector)
-  const float r_axx = axx > 0.f ? -axy * __frcp_rn(axx) : 0.f, r_byy = byy > 0.f ? -axy * __frcp_rn(byy) : 0.f;
+  const float sq = A1 * B2 - A2 * B1, det = sq * sq;
+  // a staged Gaussian has axx, byy, det > 0 (isx, isy > 0, (ux, uy) a unit
+  // vector); anything else keeps the box's blocks
+  if (!(axx > 0.f && byy > 0.f && det > 0.f && det < INFINITY)) return cand;
+  const float inv_axx = __frcp_rn(axx), inv_det = __frcp_rn(det);
+  const float Xm = sqrtf(L * byy * inv_det), Ym = sqrtf(L * axx * inv_det);
+  const float r = -axy * inv_axx, k = det * inv_axx, ys = -axy * __frcp_rn(byy) * Xm;
+  const float pad = 1e-3f + 1e-4f * (Xm + Ym);  // rounding of the chord ends, px
+  const float ox = ((float)x0 + 0.5f) - s.a.x, oy = ((float)y0 + 0.5f) - s.a.y;
   uint32_t bits = 0u;
-  while (cand) {
-    const unsigned b = (unsigned)(__ffs(cand) - 1);
-    cand &= cand - 1;
-    const int br = (int)G::brow(b), bc = (int)G::bcol(b);
-    const float dy0 = ((float)(y0 + 4 * br) + 0.5f) - s.a.y, dy1 = ((float)(y0 + 4 * br) + 3.5f) - s.a.y;
-    const float dx0 = ((float)(x0 + 8 * bc) + 0.5f) - s.a.x, dx1 = ((float)(x0 + 8 * bc) + 7.5f) - s.a.x;
-    if (min_q_rect(A1, B1, A2, B2, r_axx, r_byy, dx0, dx1, dy0, dy1) <= lim) bits |= 1u << b;
+#pragma unroll
+  for (int br = 0; br < kT / 4; ++br) {
+    const float ya = fmaxf(oy + 4.f * br, -Ym), yb = fminf(oy + 4.f * br + 3.f, Ym);
+    if (!(ya <= yb)) continue;
+    const float yr = fminf(fmaxf(ys, ya), yb), yl = fminf(fmaxf(-ys, ya), yb);
+    const float xr = fmaf(r, yr, sqrtf(fmaxf(0.f, fmaf(-k * yr, yr, L)) * inv_axx)) + pad;
+    const float xl = fmaf(r, yl, -sqrtf(fmaxf(0.f, fmaf(-k * yl, yl, L)) * inv_axx)) - pad;
+    uint32_t c = 0u;
+#pragma unroll
+    for (int bc = 0; bc < kT / 8; ++bc) {
+      const float cx0 = ox + 8.f * bc;
+      if (cx0 + 7.f >= xl && cx0 <= xr) c |= 1u << bc;
+    }
+    bits |= G::row_bits(c, br);
   }
-  return bits;
+  return bits & cand;
 }
 
 // log2 of the unclamped alpha at a pixel: dx = px - mx, and the shared
