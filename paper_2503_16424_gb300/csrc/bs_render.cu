@@ -172,9 +172,8 @@ __device__ __forceinline__ Staged stage_slot(const StageBuf<kBatch> &buf, uint32
 
 // Bit Geo<T>::bit(block_col, block_row) set: the Gaussian can reach alpha
 // >= 1/255 at some pixel centre of the 8x4 block (block_col, block_row) of
-// the tile whose first pixel is (x0, y0).  Blocks outside the Gaussian's box
-// (mean +- ext) are cleared first; the others get an exact test by block
-// row.  With q = t1^2 + t2^2 = axx dx^2 + 2 axy dx dy + byy dy^2 and L the
+// the tile whose first pixel is (x0, y0), by an exact test per block row.
+// With q = t1^2 + t2^2 = axx dx^2 + 2 axy dx dy + byy dy^2 and L the
 // threshold, the chord of the ellipse q <= L at height dy is
 //     dx in [r dy - h(dy), r dy + h(dy)],  r = -axy / axx,
 //     h(dy) = sqrt((L - k dy^2) / axx),     k = det / axx,
@@ -186,33 +185,35 @@ __device__ __forceinline__ Staged stage_slot(const StageBuf<kBatch> &buf, uint32
 // ellipse's x-extent in the band, tested against each block column.
 // Conservative by a margin far above the float32 error of either side, so a
 // cleared bit only skips pixels that the blend would skip anyway.
+// The blocks whose pixel centres overlap the box mean +- ext (the fallback
+// for a record without a proper frame).
 template <int kT>
-__device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, float ext_y, int x0, int y0) {
+__device__ __forceinline__ uint32_t box_bits(const Staged &s, float ext_x, float ext_y, int x0, int y0) {
   using G = Geo<kT>;
-  const float thr = s.b.z + kLog2_255;
-  if (!(thr >= 0.f)) return 0u;  // o < 1/255 (or not finite): never visible
-  // box test: block columns / rows whose pixel centres overlap the box
   const float bx0 = s.a.x - ext_x - ((float)x0 + 0.5f), bx1 = s.a.x + ext_x - ((float)x0 + 0.5f);
   const float by0 = s.a.y - ext_y - ((float)y0 + 0.5f), by1 = s.a.y + ext_y - ((float)y0 + 0.5f);
-  uint32_t cols = 0u, rows = 0u;
+  uint32_t cols = 0u, cand = 0u;
 #pragma unroll
   for (int bc = 0; bc < kT / 8; ++bc)
     if (bx1 >= 8.f * bc - 0.5f && bx0 <= 8.f * bc + 7.5f) cols |= 1u << bc;
 #pragma unroll
   for (int br = 0; br < kT / 4; ++br)
-    if (by1 >= 4.f * br - 0.5f && by0 <= 4.f * br + 3.5f) rows |= 1u << br;
-  uint32_t cand = 0u;
-#pragma unroll
-  for (int br = 0; br < kT / 4; ++br)
-    if (rows & (1u << br)) cand |= G::row_bits(cols, br);
-  if (!cand) return 0u;
+    if (by1 >= 4.f * br - 0.5f && by0 <= 4.f * br + 3.5f) cand |= G::row_bits(cols, br);
+  return cand;
+}
+
+template <int kT>
+__device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, float ext_y, int x0, int y0) {
+  using G = Geo<kT>;
+  const float thr = s.b.z + kLog2_255;
+  if (!(thr >= 0.f)) return 0u;  // o < 1/255 (or not finite): never visible
   const float L = thr + (1e-2f + 1e-4f * thr);
   const float A1 = s.a.z, B1 = s.a.w, A2 = s.b.x, B2 = s.b.y;
   const float axx = A1 * A1 + A2 * A2, byy = B1 * B1 + B2 * B2, axy = A1 * B1 + A2 * B2;
   const float sq = A1 * B2 - A2 * B1, det = sq * sq;
   // a staged Gaussian has axx, byy, det > 0 (isx, isy > 0, (ux, uy) a unit
-  // vector); anything else keeps the box's blocks
-  if (!(axx > 0.f && byy > 0.f && det > 0.f && det < INFINITY)) return cand;
+  // vector); anything else keeps the blocks of its box
+  if (!(axx > 0.f && byy > 0.f && det > 0.f && det < INFINITY)) return box_bits<kT>(s, ext_x, ext_y, x0, y0);
   const float inv_axx = __frcp_rn(axx), inv_det = __frcp_rn(det);
   const float Xm = sqrtf(L * byy * inv_det), Ym = sqrtf(L * axx * inv_det);
   const float r = -axy * inv_axx, k = det * inv_axx, ys = -axy * __frcp_rn(byy) * Xm;
@@ -234,7 +235,7 @@ __device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, flo
     }
     bits |= G::row_bits(c, br);
   }
-  return bits & cand;
+  return bits;
 }
 
 // log2 of the unclamped alpha at a pixel: dx = px - mx, and the shared
