@@ -71,6 +71,18 @@ constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kKappa = 0.84932180028801907f;      // sqrt(log2(e) / 2)
 constexpr float kLog2_255 = 7.99435343685885793f;   // alpha >= 1/255 <=> t1^2 + t2^2 <= log2(o) + log2(255)
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -214,9 +226,10 @@ __device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, flo
   // a staged Gaussian has axx, byy, det > 0 (isx, isy > 0, (ux, uy) a unit
   // vector); anything else keeps the blocks of its box
   if (!(axx > 0.f && byy > 0.f && det > 0.f && det < INFINITY)) return box_bits<kT>(s, ext_x, ext_y, x0, y0);
-  const float inv_axx = __frcp_rn(axx), inv_det = __frcp_rn(det);
-  const float Xm = sqrtf(L * byy * inv_det), Ym = sqrtf(L * axx * inv_det);
-  const float r = -axy * inv_axx, k = det * inv_axx, ys = -axy * __frcp_rn(byy) * Xm;
+  // approximate reciprocals and roots (relative error ~1e-7): the padding below covers them
+  const float inv_axx = rcp_approx(axx), inv_det = rcp_approx(det);
+  const float Xm = sqrt_approx(L * byy * inv_det), Ym = sqrt_approx(L * axx * inv_det);
+  const float r = -axy * inv_axx, k = det * inv_axx, ys = -axy * rcp_approx(byy) * Xm;
   const float pad = 1e-3f + 1e-4f * (Xm + Ym);  // rounding of the chord ends, px
   const float ox = ((float)x0 + 0.5f) - s.a.x, oy = ((float)y0 + 0.5f) - s.a.y;
   uint32_t bits = 0u;
@@ -225,8 +238,8 @@ __device__ __forceinline__ uint32_t block_bits(const Staged &s, float ext_x, flo
     const float ya = fmaxf(oy + 4.f * br, -Ym), yb = fminf(oy + 4.f * br + 3.f, Ym);
     if (!(ya <= yb)) continue;
     const float yr = fminf(fmaxf(ys, ya), yb), yl = fminf(fmaxf(-ys, ya), yb);
-    const float xr = fmaf(r, yr, sqrtf(fmaxf(0.f, fmaf(-k * yr, yr, L)) * inv_axx)) + pad;
-    const float xl = fmaf(r, yl, -sqrtf(fmaxf(0.f, fmaf(-k * yl, yl, L)) * inv_axx)) - pad;
+    const float xr = fmaf(r, yr, sqrt_approx(fmaxf(0.f, fmaf(-k * yr, yr, L)) * inv_axx)) + pad;
+    const float xl = fmaf(r, yl, -sqrt_approx(fmaxf(0.f, fmaf(-k * yl, yl, L)) * inv_axx)) - pad;
     uint32_t c = 0u;
 #pragma unroll
     for (int bc = 0; bc < kT / 8; ++bc) {
@@ -589,11 +602,6 @@ __global__ void __launch_bounds__(Geo<kT>::kThreads, fwd_min_blocks<kT>()) batch
     atomicAdd(loss + acc_b, acc / (3.0 * (double)tab[acc_b].W * (double)tab[acc_b].H));
 }
 
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 // Number of per-Gaussian sums the backward accumulates (see render_bwd_kernel).
 constexpr int kSums = 9;
