@@ -71,6 +71,12 @@ constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kKappa = 0.84932180028801907f;      // sqrt(log2(e) / 2)
 constexpr float kLog2_255 = 7.99435343685885793f;   // alpha >= 1/255 <=> t1^2 + t2^2 <= log2(o) + log2(255)
 
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -122,7 +128,7 @@ __device__ __forceinline__ Staged stage_rec(const float4 r0, const float4 r1, co
   scaled_axes(r0.z, r0.w, r1.x, r1.y, A1, B1, A2, B2);
   const float o = r1.z;
   s.a = make_float4(r0.x, r0.y, A1, B1);
-  s.b = make_float4(A2, B2, o > 0.f ? log2f(o) : -INFINITY, r1.w);
+  s.b = make_float4(A2, B2, o > 0.f ? lg2_approx(o) : -INFINITY, r1.w);
   s.c = make_float2(r2.x, r2.y);
   s.ext = make_float2(r2.z, r2.w);
   return s;
@@ -693,7 +699,7 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
   __shared__ uint8_t s_list[kW][kW][32];  // [consumer warp][staging warp][k]: entries reaching the warp
   __shared__ uint32_t s_cnt[kW][kW];
   __shared__ uint32_t s_max_last;
-  __shared__ uint32_t s_wlast[kW][kPix];
+  __shared__ __align__(16) uint32_t s_wlast[kW][kPix];
   __shared__ __align__(16) float s_part[kW][kPend * kSums * kRow];
   __shared__ uint32_t s_pend_g[kW][kPend];
   const ThreadPixels<kT> tp = thread_pixels<kT>(v.x0, v.y0, v.W, v.H);
