@@ -267,20 +267,21 @@ __device__ __forceinline__ float pixel_log2_alpha(const float4 &a, const float4 
 }
 
 // Per consumer warp, the staged entries whose block bits reach it, in order:
-// each staging warp writes the indices of its qualifying lanes (ballot +
-// prefix count) into its own part of the consumer's list.  The caller
+// each staging warp writes, for each of its qualifying lanes (ballot +
+// prefix count), the entry's index with the consumer's block bits above it
+// (index | slots << 8) into its own part of the consumer's list.  The caller
 // synchronises before the lists are read.
 template <int kT>
-__device__ __forceinline__ void compact_lists(uint32_t bits, uint8_t (*list)[Geo<kT>::kWarps][32],
+__device__ __forceinline__ void compact_lists(uint32_t bits, uint16_t (*list)[Geo<kT>::kWarps][32],
                                               uint32_t (*cnt)[Geo<kT>::kWarps]) {
   using G = Geo<kT>;
   const int sw = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
   for (int cw = 0; cw < G::kWarps; ++cw) {
-    const bool rel = ((bits >> (G::kPix * cw)) & G::kSlotMask) != 0u;
-    const unsigned m = __ballot_sync(0xffffffffu, rel);
-    if (rel) list[cw][sw][__popc(m & lt)] = (uint8_t)threadIdx.x;
+    const uint32_t slots = (bits >> (G::kPix * cw)) & G::kSlotMask;
+    const unsigned m = __ballot_sync(0xffffffffu, slots != 0u);
+    if (slots) list[cw][sw][__popc(m & lt)] = (uint16_t)(threadIdx.x | (slots << 8));
     if (lane == 0) cnt[cw][sw] = (uint32_t)__popc(m);
   }
 }
@@ -290,7 +291,6 @@ struct ThreadPixels {
   int x[Geo<kT>::kBC], y[2];  // slot q is pixel (x[q % kBC], y[q / kBC])
   float px[Geo<kT>::kBC], py[2];
   unsigned inside;            // bit q: slot q lies on the canvas
-  int shift;                  // this warp's block bits start at bit `shift`
   int tile_x0, tile_y0;
 };
 
@@ -316,7 +316,6 @@ __device__ __forceinline__ ThreadPixels<kT> thread_pixels(int tile_x0, int tile_
 #pragma unroll
   for (int q = 0; q < G::kPix; ++q)
     if (t.x[q % G::kBC] < W && t.y[q / G::kBC] < H) t.inside |= 1u << q;
-  t.shift = G::kPix * warp;
   return t;
 }
 
@@ -353,8 +352,7 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
-  __shared__ uint32_t s_bits[kBatch];
-  __shared__ uint8_t s_list[kW][kW][32];  // [consumer warp][staging warp][k]: entries reaching the warp
+  __shared__ uint16_t s_list[kW][kW][32];  // [consumer warp][staging warp][k]: entries reaching the warp
   __shared__ uint32_t s_cnt[kW][kW];
   uint32_t n_eval = 0, n_blend = 0;
   const ThreadPixels<kT> tp = thread_pixels<kT>(v.x0, v.y0, v.W, v.H);
@@ -396,7 +394,6 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
 #pragma unroll
       for (int w = 0; w < kW; ++w) alive_all |= s_alive[w] << (kPix * w);
       my_bits = block_bits<kT>(s, s.ext.x, s.ext.y, tp.tile_x0, tp.tile_y0) & alive_all;
-      s_bits[threadIdx.x] = my_bits;
     }
     // in flight while this batch blends: the next batch's record, the key after it
     if (i + kBatch < r.y) issue_rec(s_buf, gauss, s_buf.key[kb ^ 1u][threadIdx.x] & gmask, n_gauss);
@@ -408,8 +405,9 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
     for (int sw = 0; sw < kW && alive; ++sw) {
     const int cnt = (int)s_cnt[cw][sw];
     for (int k = 0; k < cnt && alive; ++k) {
-      const int j = s_list[cw][sw][k];
-      const uint32_t bits = (s_bits[j] >> tp.shift) & G::kSlotMask;  // warp-uniform, not 0
+      const uint32_t ent = s_list[cw][sw][k];
+      const int j = (int)(ent & 0xffu);
+      const uint32_t bits = ent >> 8;  // this warp's block bits: warp-uniform, not 0
       const float4 a = s_a[j], b = s_b[j];
       const float2 gb = s_c[j];
       float dx[kBC], b1dy[2], b2dy[2];
@@ -695,8 +693,7 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
   __shared__ float4 s_b[kBatch];
   __shared__ float2 s_c[kBatch];
   __shared__ uint32_t s_g[kBatch];
-  __shared__ uint32_t s_bits[kBatch];
-  __shared__ uint8_t s_list[kW][kW][32];  // [consumer warp][staging warp][k]: entries reaching the warp
+  __shared__ uint16_t s_list[kW][kW][32];  // [consumer warp][staging warp][k]: entries reaching the warp
   __shared__ uint32_t s_cnt[kW][kW];
   __shared__ uint32_t s_max_last;
   __shared__ __align__(16) uint32_t s_wlast[kW][kPix];
@@ -757,16 +754,16 @@ __device__ __forceinline__ void bwd_tile(const TileView &v, const BwdIn &in, con
 #pragma unroll
       for (int b = 0; b < G::kBits; ++b)
         if (i >= s_wlast[b / kPix][b % kPix]) my_bits &= ~(1u << b);
-      s_bits[threadIdx.x] = my_bits;
     }
     compact_lists<kT>(my_bits, s_list, s_cnt);
     __syncthreads();
     const int cw = threadIdx.x >> 5;
     for (int sw = kW - 1; sw >= 0; --sw)
     for (int k = (int)s_cnt[cw][sw] - 1; k >= 0; --k) {
-      const int j = s_list[cw][sw][k];
+      const uint32_t ent = s_list[cw][sw][k];
+      const int j = (int)(ent & 0xffu);
       const uint32_t pos = start + (uint32_t)j;
-      const uint32_t bits = (s_bits[j] >> tp.shift) & G::kSlotMask;  // warp-uniform, not 0
+      const uint32_t bits = ent >> 8;  // this warp's block bits: warp-uniform, not 0
       const float4 a = s_a[j], b = s_b[j];
       const float2 gb = s_c[j];
       float dx[kBC], b1dy[2], b2dy[2];
