@@ -45,7 +45,7 @@ FP32_LANES_PER_SM = 128
 # workload, from one ncu capture of the current kernel
 # (profiles/render_bwd_kernel_hires_2048_4096.md, render_fwd_kernel_hires_2048_4096.md); None where no capture of
 # the current kernel exists.
-DRAM_BYTES_PER_LAUNCH = {"render_bwd_kernel": 130950912, "render_fwd_kernel": 179825664}
+DRAM_BYTES_PER_LAUNCH = {"render_bwd_kernel": 131352832, "render_fwd_kernel": 180358912}
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
