@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsig
   if (n_chunks > 0) fetch(kb);
   for (int c = 0; c < n_chunks; ++c) {
     const int st = c & 1;
-    if (c >= 2) {  // the MMAs that read this stage: thread 0 waits, the CTA follows its verdict
+    if (c >= 2) {  // the MMAs that read this stage: thread 0 waits, the CTA follows its outcome
       const bool w = tid == 0 ? mbar_wait(&bar[st], (uint32_t)(((c - 2) >> 1) & 1)) : true;
       if (!__syncthreads_and(w)) {
         ok = false;
