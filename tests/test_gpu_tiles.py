@@ -38,7 +38,7 @@ def _plain(bs, case, tile):
 
 
 @pytest.mark.parametrize("tile", [8, 32])
-@pytest.mark.parametrize("name", ["ragged", "mixed"])
+@pytest.mark.parametrize("name", ["ragged", "mixed", "dense"])
 def test_plain_path_at_tile_side(bs, name, tile):
     case = CASES[name]
     arr, curves, r = _plain(bs, case, tile)
