@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -544,13 +545,32 @@ __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const K *__restri
   __shared__ uint32_t s_h[kSortWarps][256];
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&s_h[0][0])[i] = 0u;
-  __syncthreads();
   const uint32_t n = (uint32_t)*count, nbins = 1u << bits, dmask = nbins - 1;
   const uint32_t base = blockIdx.x * (uint32_t)kSortTile;
-#pragma unroll 4
-  for (int i = tid; i < kSortTile; i += kSortThreads) {
-    const uint32_t idx = base + (uint32_t)i;
-    if (idx < n) atomicAdd(&s_h[warp][(uint32_t)(in[idx] >> shift) & dmask], 1u);
+  // all of a thread's keys in flight at once, 16 bytes a load when the key
+  // array is 16-byte aligned (partitions start on multiples of kSortTile
+  // keys); the counts do not depend on the order
+  constexpr int kVec = 16 / (int)sizeof(K), kLoads = kSortTile / (kSortThreads * kVec);
+  const bool vec = (reinterpret_cast<uintptr_t>(in) & 15u) == 0u;
+  K key[kLoads][kVec];
+#pragma unroll
+  for (int j = 0; j < kLoads; ++j) {
+    const uint32_t idx = base + (uint32_t)(j * kSortThreads + tid) * kVec;
+    if (vec && idx + kVec <= n) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in + idx));
+      memcpy(&key[j][0], &v, sizeof(v));
+    } else {
+#pragma unroll
+      for (int e = 0; e < kVec; ++e) key[j][e] = idx + e < n ? in[idx + e] : K(0);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kLoads; ++j) {
+    const uint32_t idx = base + (uint32_t)(j * kSortThreads + tid) * kVec;
+#pragma unroll
+    for (int e = 0; e < kVec; ++e)
+      if (idx + e < n) atomicAdd(&s_h[warp][(uint32_t)(key[j][e] >> shift) & dmask], 1u);
   }
   __syncthreads();
   for (uint32_t d = tid; d < nbins; d += kSortThreads) {
