@@ -19,6 +19,9 @@ Modules
   prune_densify  Section 3.5, Algorithm 1, Appendix B: pruning, splitting,
            error regions and circular initialisation of new curves
   adam     Section 4.1: the Adam update (Kingma and Ba), box-projected
+  bounds   the sums of absolute per-pixel terms that scale the float32
+           rounding of the gradients (Section 3.4's reverse walk, carried
+           through the sampling of Section 3.3)
 
 Parity pins: every function is pinned by a test in tests/test_oracle_*.py
 against closed forms, invariants, brute force or finite differences; none is

@@ -72,7 +72,7 @@ def target(case: Case):
     return synth.procedural_target(case.seed + 1000, case.W, case.H, 12)
 
 
-def grad_rel_err(got, exp, floor_frac=1e-3):
+def grad_rel_err(got, exp, floor_frac=1e-6):
     """max_i |got_i - exp_i| / max(|exp_i|, floor_frac * max|exp|)."""
     got = torch.as_tensor(got, dtype=torch.float64).reshape(-1)
     exp = torch.as_tensor(exp, dtype=torch.float64).reshape(-1)
@@ -82,5 +82,66 @@ def grad_rel_err(got, exp, floor_frac=1e-3):
     return float(((got - exp).abs() / torch.clamp(exp.abs(), min=floor)).max())
 
 
-__all__ = ["CASES", "Case", "arrays", "ocfg", "oracle_table", "target", "grad_rel_err", "table_to_f32",
-           "table_from_f32"]
+# Float32 rounding of a gradient entry (see oracle/bounds.py): a sum over
+# pixels of per-pixel terms, bounded by gamma_n * sum |terms| with u = 2^-24.
+# n = DEPTH + the tiles the Gaussian is listed in: about 12 roundings to
+# recompute alpha and its derivative in a term, 3 + 5 + 1 in the in-tile
+# reduction (a lane's four pixels, the warp, the shared-memory rows), 4 in
+# the conversion from eigen-frame sums, one per tile atomic, and room for the
+# transmittance and colour-behind recursions of the reverse walk.
+U32 = 2.0 ** -24
+DEPTH = 32
+
+
+def tiles_per_gaussian(rec, W, H, tile=16):
+    """Tiles listing each Gaussian of the float32 table (its atomics)."""
+    tx0, tx1, ty0, ty1, ok = oracle.tile_rects_f32(rec, W, H, tile)
+    return torch.as_tensor(np.where(ok, (tx1 - tx0 + 1) * (ty1 - ty0 + 1), 0), dtype=torch.float64)
+
+
+def blend_grad_bound(rec, W, H, dC, bg=(0.0, 0.0, 0.0), tile=16, xs=None, ys=None, tab=None):
+    """Per field of the table gradient, the float32 error bound of each entry:
+    (DEPTH + its tiles) u A, A = oracle.bounds.blend_abs at the pixels
+    (xs, ys) (default: the whole W x H canvas) with dL/dC = dC [n, 3]."""
+    from oracle.bounds import blend_abs
+    tab = table_from_f32(rec) if tab is None else tab
+    if xs is None:
+        ys_, xs_ = torch.meshgrid(torch.arange(H, dtype=torch.float64), torch.arange(W, dtype=torch.float64),
+                                  indexing="ij")
+        xs, ys = xs_.reshape(-1), ys_.reshape(-1)
+    A = blend_abs(tab, xs, ys, dC, bg)
+    c = (DEPTH + tiles_per_gaussian(rec, W, H, tile)) * U32
+    return {k: (c[:, None] * v if v.dim() == 2 else c * v) for k, v in A.items()}
+
+
+def curve_grad_bound(arr, cfg, first, gbound, dtab):
+    """The float32 error bound of the curve gradients: the table-gradient
+    bound carried through the sampling's Jacobian in absolute value, plus the
+    sampling backward's own rounding (DEPTH u |dL/dtable|)."""
+    from oracle.bounds import sample_abs_vjp
+    from oracle.raster import GRAD_KEYS
+    scale = {}
+    for k in GRAD_KEYS:
+        d = torch.as_tensor(dtab[k], dtype=torch.float64).abs()
+        g = gbound[k] if gbound is not None else torch.zeros_like(d)
+        scale[k] = g + DEPTH * U32 * d
+    return sample_abs_vjp(as_curves(arr), cfg, scale, first)
+
+
+def grad_check(got, exp, bound=None, rel=1e-3, floor_frac=1e-6):
+    """The gradient bar: |got - exp| <= rel max(|exp|, floor_frac max|exp|)
+    + bound, entry by entry.  Returns the largest ratio of |got - exp| to
+    its allowance (the bar holds when it is <= 1)."""
+    got = torch.as_tensor(got, dtype=torch.float64).reshape(-1)
+    exp = torch.as_tensor(exp, dtype=torch.float64).reshape(-1)
+    if exp.numel() == 0:
+        return 0.0
+    floor = max(float(exp.abs().max()) * floor_frac, 1e-300)
+    allow = rel * torch.clamp(exp.abs(), min=floor)
+    if bound is not None:
+        allow = allow + torch.as_tensor(bound, dtype=torch.float64).reshape(-1)
+    return float(((got - exp).abs() / allow).max())
+
+
+__all__ = ["CASES", "Case", "arrays", "ocfg", "oracle_table", "target", "grad_rel_err", "grad_check",
+           "blend_grad_bound", "curve_grad_bound", "tiles_per_gaussian", "table_to_f32", "table_from_f32"]

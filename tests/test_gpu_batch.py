@@ -18,7 +18,7 @@ import oracle
 from oracle.curves import SampleCfg as OCfg, table_from_f32
 from oracle.pipeline import as_curves, sample_vjp
 from paper_2503_16424_gb300 import synth
-from tests.gpu_cases import grad_rel_err
+from tests.gpu_cases import blend_grad_bound, curve_grad_bound, grad_check, grad_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -155,10 +155,10 @@ def test_batch_forward_matches_oracle_and_single_canvas(bs, ragged):
             assert torch.equal(img, bg.to(torch.float32).double())
         else:
             tab = table_from_f32(gauss[g0:g0 + n])
-            ref = oracle.render_image(tab, im.width, im.height, bg=im.bg, margin=4e-6, margin_T=2e-5)
+            ref = oracle.render_image(tab, im.width, im.height, bg=im.bg, margin=1e-5)
             ok = ~ref["flag"]
             err = (img - ref["img"]).abs().amax(0)
-            assert float((~ok).double().mean()) <= 2e-4 or (~ok).sum() <= 1
+            assert float(((~ok) & (err > 1e-5)).double().mean()) < 1e-4, b   # excused pixels
             assert float(err[ok].max()) <= 1e-5, b
         l_ref, _ = oracle.l2_loss(img, tgt)
         assert abs(loss[b] - float(l_ref)) <= 1e-6 * max(1.0, float(l_ref)), b
@@ -206,6 +206,8 @@ def test_batch_backward_matches_oracle(bs, ragged):
         dC = r.batch.image(dimg, b).cpu().double().permute(1, 2, 0).reshape(-1, 3)
         dtab = oracle.render_grads(tab, xs.reshape(-1), ys.reshape(-1), dC, bg=im.bg)
         dref = sample_vjp(as_curves(arr), oc, dtab, o_first)
+        cb = curve_grad_bound(arr, oc, o_first, blend_grad_bound(gauss[g0:g0 + n], im.width, im.height, dC, im.bg),
+                              dtab)
         for k in KEYS:
             if k in OPEN_KEYS:
                 got = getattr(grad, k)[r.batch.open0[b]:r.batch.open0[b] + im.n_open]
@@ -213,8 +215,8 @@ def test_batch_backward_matches_oracle(bs, ragged):
                 got = getattr(grad, k)[r.batch.closed0[b]:r.batch.closed0[b] + im.n_closed]
             if got.numel() == 0:
                 continue
-            e = grad_rel_err(got.cpu(), dref[k])
-            assert e <= 1e-3, (b, k, e)
+            e = grad_check(got.cpu(), dref[k], cb[k])
+            assert e <= 1.0, (b, k, e)
 
 
 def test_batch_capacity_overflow_renders_nothing_and_reports(bs):

@@ -2,10 +2,13 @@
 the same seeded inputs, element by element.
 
 Bars: integer results (draw order, tile keys, tile ranges) bit-exact;
-forward pixels within 1e-5 absolute except pixels the oracle flags as being
-within 1e-4 (relative) of a threshold decision; per-Gaussian and curve
-gradients within 1e-3 relative error, the relative error of an entry being
-measured against max(|reference|, 1e-3 * max |reference| of that array)."""
+forward pixels within 1e-5 absolute; a pixel whose fp64 threshold decision
+(alpha against 1/255 or 0.99, T against 1e-4) lies within 1e-5 relative of
+its threshold is flagged by the oracle, and the flagged pixels that also
+miss 1e-5 (excused) must be under 1e-4 of the image.  Per-Gaussian and
+curve gradients: |g - g_ref| <= 1e-3 max(|g_ref|, 1e-6 max|g_ref|) plus the
+float32 rounding bound of the entry, (32 + its tiles) 2^-24 sum |terms|
+(tests/gpu_cases.py, oracle/bounds.py)."""
 
 import numpy as np
 import pytest
@@ -13,7 +16,11 @@ import torch
 
 import oracle
 from oracle.pipeline import as_curves, sample_vjp
-from tests.gpu_cases import CASES, arrays, grad_rel_err, ocfg, oracle_table, target, table_to_f32, table_from_f32
+from tests.gpu_cases import (CASES, arrays, blend_grad_bound, grad_check, grad_rel_err, ocfg, oracle_table, target,
+                             table_to_f32, table_from_f32)
+
+MARGIN = 1e-5      # relative distance of a threshold decision that flags a pixel
+EXCUSED_MAX = 1e-4  # flagged pixels that miss the 1e-5 bar, as a fraction of the image
 
 pytestmark = pytest.mark.gpu
 
@@ -136,14 +143,14 @@ def test_render_fwd_matches_oracle(bs, name):
     tab, _, _ = oracle_table(case)
     rec = table_to_f32(tab)
     gauss, b, img, T, nc = _render(bs, case, rec)
-    # flag decisions within 4e-6 (alpha) / 2e-5 (transmittance) of a threshold
-    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg, margin=4e-6, margin_T=2e-5)
+    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg, margin=MARGIN)
     ok = ~ref["flag"].numpy()
     err = np.abs(img.cpu().numpy().astype(np.float64) - ref["img"].numpy()).max(0)
     terr = np.abs(T.cpu().numpy() - ref["T"].numpy())
-    print(f"{name}: flagged {1 - ok.mean():.2e}, max err {err[ok].max():.2e}, "
+    excused = (~ok) & (np.maximum(err, terr) > 1e-5)
+    print(f"{name}: flagged {1 - ok.mean():.2e}, excused {excused.mean():.2e}, max err {err[ok].max():.2e}, "
           f"max err incl. flagged {err.max():.2e}, T err {terr[ok].max():.2e}")
-    assert 1 - ok.mean() <= 2e-4
+    assert excused.mean() < EXCUSED_MAX
     assert err[ok].max() <= 1e-5
     assert terr[ok].max() <= 1e-5
     # the last blended Gaussian of every pixel, through the tile list
@@ -175,13 +182,16 @@ def test_render_bwd_matches_oracle(bs, name):
                             torch.arange(case.W, dtype=torch.float64), indexing="ij")
     dC = dimg.cpu().double().permute(1, 2, 0).reshape(-1, 3)
     ref = oracle.render_grads(table_from_f32(rec), xs.reshape(-1), ys.reshape(-1), dC, bg=case.bg)
+    bound = blend_grad_bound(rec, case.W, case.H, dC, case.bg)
     got = dgauss.cpu().double()
-    errs = {key: grad_rel_err(got[:, col], ref[key]) for key, col in FIELD_SLICES.items()}
-    errs["col"] = grad_rel_err(got[:, 7:10], ref["col"])
+    cols = dict(FIELD_SLICES, col=slice(7, 10))
+    errs = {key: grad_rel_err(got[:, c], ref[key]) for key, c in cols.items()}
+    ratio = {key: grad_check(got[:, c], ref[key], bound[key]) for key, c in cols.items()}
     print(f"{name}: flagged {float(ref_f.double().mean()):.2e}, rel errs " +
-          ", ".join(f"{k} {v:.1e}" for k, v in errs.items()))
-    for key, e in errs.items():
-        assert e <= 1e-3, key
+          ", ".join(f"{k} {v:.1e}" for k, v in errs.items()) +
+          "; of the bar: " + ", ".join(f"{k} {v:.2f}" for k, v in ratio.items()))
+    for key, e in ratio.items():
+        assert e <= 1.0, key
     assert torch.all(got[:, 10:] == 0)
 
 
@@ -252,7 +262,7 @@ def test_work_counters_match_oracle(bs, name):
     gauss = torch.as_tensor(rec, device="cuda")
     b = bs.Binning(_canvas(bs, case), "cuda", pair_capacity=1024).run(gauss)
     st = bs.render_stats(gauss, _canvas(bs, case), b)
-    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg, margin=4e-6, margin_T=2e-5)
+    ref = oracle.render_image(table_from_f32(rec), case.W, case.H, bg=case.bg, margin=MARGIN)
     keys, ranges, _ = oracle.tile_keys(rec, case.W, case.H, 16)
     gbits = max(1, (rec.shape[0] - 1).bit_length())
     tiles_x = -(-case.W // 16)

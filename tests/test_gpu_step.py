@@ -9,7 +9,7 @@ import oracle
 from oracle.curves import SampleCfg as OCfg, table_to_f32, table_from_f32
 from oracle.pipeline import as_curves, loss_only, sample_vjp
 from paper_2503_16424_gb300 import synth
-from tests.gpu_cases import grad_rel_err
+from tests.gpu_cases import blend_grad_bound, curve_grad_bound, grad_check, grad_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -44,12 +44,16 @@ def test_step_matches_oracle_and_fd(bs, seed, W, H, no, nc):
     oc = as_curves(arr)
     _, first = oracle.draw_order(arr["open_ctrl"], arr["open_width"], arr["closed_ctrl"], ocfg)
     tab = oracle.gaussian_table(oc, ocfg, first)
-    ref = oracle.render_image({k: v.detach() for k, v in tab.items()}, W, H, bg=bg, margin=1e-4)
-    ok = ~ref["flag"]
+    ref = oracle.render_image({k: v.detach() for k, v in tab.items()}, W, H, bg=bg, margin=1e-5)
     err = (img.cpu().double() - ref["img"]).abs().amax(0)
-    print(f"step {W}x{H}: flagged {float((~ok).double().mean()):.1e}, pixel err {float(err[ok].max()):.1e}")
-    assert float(err[ok].max()) <= 2e-5
-    # gradients of the L2 loss restricted to unflagged pixels, both sides
+    excused = ref["flag"] & (err > 1e-5)
+    print(f"step {W}x{H}: flagged {float(ref['flag'].double().mean()):.1e}, "
+          f"pixel err {float(err[~ref['flag']].max()):.1e}, excused {int(excused.sum())}")
+    assert float(err[~ref["flag"]].max()) <= 1e-5
+    assert float(excused.double().mean()) < 1e-4
+    # gradients of the L2 loss restricted to pixels with no threshold
+    # decision within 1e-4 (a kink of the blend), on both sides
+    ok = ~oracle.render_image({k: v.detach() for k, v in tab.items()}, W, H, bg=bg, margin=1e-4)["flag"]
     _, dimg = bs.l2_loss_grad(img, tgt)
     dimg = dimg * ok.to("cuda")[None].float()
     grad = r.backward(curves, dimg)
@@ -58,10 +62,14 @@ def test_step_matches_oracle_and_fd(bs, seed, W, H, no, nc):
     dC = dimg.cpu().double().permute(1, 2, 0).reshape(-1, 3)
     dtab = oracle.render_grads({k: v.detach() for k, v in tab.items()}, xs.reshape(-1), ys.reshape(-1), dC, bg=bg)
     dref = sample_vjp(oc, ocfg, dtab, first)
+    gb = blend_grad_bound(r.gauss.cpu().numpy(), W, H, dC, bg, tab={k: v.detach() for k, v in tab.items()})
+    cb = curve_grad_bound(arr, ocfg, first, gb, dtab)
     errs = {k: grad_rel_err(getattr(grad, k).cpu(), dref[k]) for k in KEYS}
-    print("  curve grad rel errs: " + ", ".join(f"{k} {v:.1e}" for k, v in errs.items()))
-    for k, e in errs.items():
-        assert e <= 1e-3, k
+    ratio = {k: grad_check(getattr(grad, k).cpu(), dref[k], cb[k]) for k in KEYS}
+    print("  curve grad rel errs: " + ", ".join(f"{k} {v:.1e}" for k, v in errs.items()) +
+          "; of the bar: " + ", ".join(f"{k} {v:.2f}" for k, v in ratio.items()))
+    for k, e in ratio.items():
+        assert e <= 1.0, k
     # central finite differences of the oracle loss (same mask) for a few parameters
     mask = ok.double()
 
@@ -71,19 +79,26 @@ def test_step_matches_oracle_and_fd(bs, seed, W, H, no, nc):
             im = oracle.render_image(t, W, H, bg=bg)["img"]
             d = (im - torch.as_tensor(tgt_np, dtype=torch.float64)) * mask[None]
             return float((d * d).sum() / d.numel())
+    def central(k, i, h):
+        plus = {kk: v.clone() for kk, v in oc.items()}
+        minus = {kk: v.clone() for kk, v in oc.items()}
+        plus[k].view(-1)[i] += h
+        minus[k].view(-1)[i] -= h
+        return (masked_loss(plus) - masked_loss(minus)) / (2 * h)
+
+    # the bar of the curve gradients, with the finite difference's own error
+    # estimated from a second step (central differences err ~ h^2, so
+    # |fd(h) - fd(2h)| / 3 estimates the error of fd(h))
     rng = np.random.default_rng(seed)
     for k in ("open_ctrl", "closed_ctrl", "open_width", "closed_color"):
         g = getattr(grad, k).cpu().double().reshape(-1)
         gmax = float(g.abs().max())
+        bnd = cb[k].reshape(-1)
         for i in rng.choice(g.numel(), size=4, replace=False):
-            base = float(oc[k].reshape(-1)[i])
-            h = 1e-5 * max(1.0, abs(base))
-            plus = {kk: v.clone() for kk, v in oc.items()}
-            minus = {kk: v.clone() for kk, v in oc.items()}
-            plus[k].view(-1)[i] += h
-            minus[k].view(-1)[i] -= h
-            fd = (masked_loss(plus) - masked_loss(minus)) / (2 * h)
-            assert abs(float(g[i]) - fd) <= 1e-3 * max(abs(fd), 1e-3 * gmax) + 1e-9, (k, i, float(g[i]), fd)
+            h = 1e-5 * max(1.0, abs(float(oc[k].reshape(-1)[i])))
+            fd, fd2 = central(k, i, h), central(k, i, 2 * h)
+            allow = 1e-3 * max(abs(fd), 1e-6 * gmax) + float(bnd[i]) + abs(fd - fd2) / 3
+            assert abs(float(g[i]) - fd) <= allow, (k, i, float(g[i]), fd, fd2)
 
 
 def test_autograd_function_matches_rasterizer(bs):
@@ -143,9 +158,11 @@ def test_degenerate_curves_match_oracle(bs):
     assert np.abs(got[:, 0:2] - ref[:, 0:2]).max() <= 1e-4
     assert np.abs(got[:, 2:4] - ref[:, 2:4]).max() <= 1e-5
     assert (np.abs(got[:, 4:6] - ref[:, 4:6]) / ref[:, 4:6]).max() <= 1e-5
-    refi = oracle.render_image(table_from_f32(r.gauss.cpu().numpy()), W, H, margin=4e-6, margin_T=1e-4)
+    refi = oracle.render_image(table_from_f32(r.gauss.cpu().numpy()), W, H, margin=1e-5)
     ok = ~refi["flag"]
-    assert float((r.img.cpu().double() - refi["img"]).abs().amax(0)[ok].max()) <= 1e-5
+    err = (r.img.cpu().double() - refi["img"]).abs().amax(0)
+    assert float(err[ok].max()) <= 1e-5
+    assert float(((~ok) & (err > 1e-5)).double().mean()) < 1e-4
     # 1x1 canvas
     cfg, curves, r1 = _setup(bs, 1, 1, arr, 7, 3, 5)
     img = r1.forward(curves)
@@ -166,11 +183,17 @@ def test_tile_with_more_than_1e4_gaussians(bs):
     r.forward(curves)
     ranges = r.binning.ranges.cpu().numpy()
     assert (ranges[:, 1] - ranges[:, 0]).max() > 10000
-    refi = oracle.render_image(table_from_f32(r.gauss.cpu().numpy()), W, H, margin=4e-6, margin_T=1e-4)
+    # the float32 transmittance after n factors carries a relative rounding
+    # error that grows with n (about sqrt(n) u in practice, 2 n u at worst:
+    # 1.5e-3 after 12,800 factors), so with lists this long the stop decision
+    # is flagged at 1e-4 relative instead of 1e-5
+    refi = oracle.render_image(table_from_f32(r.gauss.cpu().numpy()), W, H, margin=1e-5, margin_T=1e-4)
     ok = ~refi["flag"]
     err = (r.img.cpu().double() - refi["img"]).abs().amax(0)
-    print(f"pile: list max {(ranges[:, 1] - ranges[:, 0]).max()}, err {float(err[ok].max()):.1e}")
+    print(f"pile: list max {(ranges[:, 1] - ranges[:, 0]).max()}, err {float(err[ok].max()):.1e}, "
+          f"flagged {float((~ok).double().mean()):.1e}")
     assert float(err[ok].max()) <= 1e-5
+    assert float(((~ok) & (err > 1e-5)).double().mean()) < 1e-4
 
 
 def test_sort_over_many_partitions_is_exact(bs):
