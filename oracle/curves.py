@@ -23,6 +23,11 @@ Readings of the paper used here (the paper is silent or garbled):
     segments walked backwards); both run from P0 to P6.
   * interior rows: tau_r = (1 - cos(pi r/(R+1)))/2, r = 0..R+1, a normalized
     CDF (the arcsine law) that is dense near both boundaries (Section 3.3).
+  * the rotation (Eq. 8) comes from the central neighbour difference
+    (tangent_mode 0, the paper's), or from the direction of the derivative
+    B'(t) of the sample's own segment (tangent_mode 1, the reading of the
+    Gaussian's orientation as the curve's tangent); a closed row's
+    derivative is that of its interpolated control points (Eq. 4).
   * sigma at the last sample of a row uses the previous pair; sigma_y of the
     last row uses the previous row; a zero-length neighbour vector gives
     theta = 0 (Eq. 7-8 "nearest available neighbour").
@@ -50,6 +55,7 @@ class SampleCfg:
     k_closed: int = 8       # K samples per row of a closed curve
     rho: float = 1.0        # the density constant of Eq. 7
     eps: float = 0.3        # isotropic covariance floor, px^2
+    tangent_mode: int = 0   # rotation from: 0 the neighbour difference (Eq. 8), 1 the derivative B'(t)
 
     @property
     def per_closed(self) -> int:
@@ -70,6 +76,16 @@ def bezier(P: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
     out = torch.zeros(P.shape[:-2] + (2,), dtype=P.dtype)
     for j in range(M + 1):
         out = out + bernstein(M, j, t)[..., None] * P[..., j, :]
+    return out
+
+
+def bezier_derivative(P: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
+    """dB/dt of Eq. 1, the hodograph: M sum_{j<M} B_j^{M-1}(t) (P_{j+1} - P_j).
+    P [..., M+1, 2], t [...]."""
+    M = P.shape[-2] - 1
+    out = torch.zeros(P.shape[:-2] + (2,), dtype=P.dtype)
+    for j in range(M):
+        out = out + (M * bernstein(M - 1, j, t))[..., None] * (P[..., j + 1, :] - P[..., j, :])
     return out
 
 
@@ -96,6 +112,20 @@ def chain_points(ctrl: torch.Tensor, K: int) -> torch.Tensor:
     return torch.stack(pts, dim=-2)
 
 
+def chain_tangents(ctrl: torch.Tensor, K: int) -> torch.Tensor:
+    """The derivative of each sample's own segment at its local parameter
+    (the samples of chain_points; a sample at a join belongs to the later
+    segment).  ctrl [..., 3S+1, 2] -> [..., K, 2]."""
+    S = (ctrl.shape[-2] - 1) // 3
+    s, t = chain_sample_params(K, S)
+    out = []
+    for k in range(K):
+        seg = ctrl[..., 3 * s[k]: 3 * s[k] + 4, :]
+        tk = torch.full(seg.shape[:-2], float(t[k]), dtype=ctrl.dtype)
+        out.append(bezier_derivative(seg, tk))
+    return torch.stack(out, dim=-2)
+
+
 # --------------------------------------------------------------------------
 # Eq. 7-8 and 11-12
 # --------------------------------------------------------------------------
@@ -115,12 +145,16 @@ def _angle(v: torch.Tensor) -> torch.Tensor:
     return torch.where(zero, torch.zeros_like(vx), torch.atan2(vy, vx))
 
 
-def along_row(X: torch.Tensor, rho: float):
+def along_row(X: torch.Tensor, rho: float, tangents: torch.Tensor = None):
     """sigma_x (Eq. 7, first line) and theta (Eq. 8) for samples X [..., K, 2]
-    ordered along a curve."""
+    ordered along a curve.  With `tangents` given (tangent_mode 1, the
+    reading of the rotation as the direction of B'(t)), theta is their angle
+    instead of the neighbour difference's."""
     nxt = X[..., 1:, :] - X[..., :-1, :]                   # X_{k+1} - X_k
     sx_vec = torch.cat([nxt, nxt[..., -1:, :]], dim=-2)    # last uses (K-2, K-1)
     sigma_x = _norm(sx_vec) / rho
+    if tangents is not None:
+        return sigma_x, _angle(tangents)
     if X.shape[-2] >= 3:
         central = X[..., 2:, :] - X[..., :-2, :]           # X_{k+1} - X_{k-1}
         tang = torch.cat([nxt[..., :1, :], central, nxt[..., -1:, :]], dim=-2)
@@ -150,7 +184,7 @@ def sample_open(ctrl, width, color, opac, cfg: SampleCfg):
     """Gaussians on open curves, [No, K] per field (Section 3.3)."""
     K = cfg.g_open
     X = chain_points(ctrl, K)                                  # [No, K, 2]
-    sigma_x, theta = along_row(X, cfg.rho)
+    sigma_x, theta = along_row(X, cfg.rho, chain_tangents(ctrl, K) if cfg.tangent_mode == 1 else None)
     sigma_y = width[:, None].expand(-1, K)
     seg, _ = chain_sample_params(K, 3)
     o = opac[:, torch.as_tensor(seg)]                          # per-segment opacity
@@ -184,7 +218,7 @@ def sample_closed(ctrl, color, opac, cfg: SampleCfg, color2=None, opac2=None):
     tau = closed_tau(rows)[None, :, None, None]
     Q = (1.0 - tau) * A[:, None] + tau * B[:, None]            # Eq. 4: [Nc, rows, 7, 2]
     X = chain_points(Q, K)                                     # Eq. 5-6: [Nc, rows, K, 2]
-    sigma_x, theta = along_row(X, cfg.rho)
+    sigma_x, theta = along_row(X, cfg.rho, chain_tangents(Q, K) if cfg.tangent_mode == 1 else None)
     nxt = X[:, 1:] - X[:, :-1]                                 # X_{r+1,k} - X_{r,k}
     sy_vec = torch.cat([nxt, nxt[:, -1:]], dim=1)              # last row uses (R, R+1)
     sigma_y = _norm(sy_vec) / cfg.rho                          # Eq. 7, second line

@@ -235,3 +235,87 @@ def test_chain_points_joins_are_shared():
     assert torch.allclose(X[:, 4], ctrl[:, 6], atol=1e-12)
     assert torch.equal(X[:, 0], ctrl[:, 0])
     assert torch.allclose(X[:, 6], ctrl[:, 9], atol=1e-12)
+
+
+# ---- tangent_mode 1: the rotation from the derivative B'(t) ----
+
+def test_bezier_derivative_equals_autograd_and_central_differences():
+    """The hodograph against two independent derivatives of Eq. 1: autograd
+    of bezier() with respect to t, and fp64 central differences."""
+    rng = np.random.default_rng(11)
+    P = torch.as_tensor(rng.uniform(-50, 50, (30, 4, 2)))
+    t = torch.as_tensor(rng.uniform(0.01, 0.99, 30)).requires_grad_(True)
+    d = oracle.curves.bezier_derivative(P, t.detach())
+    B = oracle.bezier(P, t)
+    gx, = torch.autograd.grad(B[:, 0].sum(), t, retain_graph=True)
+    gy, = torch.autograd.grad(B[:, 1].sum(), t)
+    assert torch.allclose(d, torch.stack([gx, gy], 1), rtol=1e-12, atol=1e-10)
+    h = 1e-6
+    td = t.detach()
+    fd = (oracle.bezier(P, td + h) - oracle.bezier(P, td - h)) / (2 * h)
+    assert torch.allclose(d, fd, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("K", [2, 7, 16])
+def test_tangent_mode_on_a_straight_line_equals_eq8(K):
+    """Evenly spaced collinear points: B'(t) points along the line, so both
+    modes give the line's angle, and sigma is unchanged."""
+    ctrl = _line_curve((10.0, 20.0), (130.0, 70.0), 10)[None]
+    args = (ctrl, torch.tensor([2.5], dtype=F64), torch.zeros(1, 3, dtype=F64), torch.tensor([[0.2, 0.5, 0.9]],
+                                                                                            dtype=F64))
+    a = oracle.sample_open(*args, SampleCfg(g_open=K, tangent_mode=0))
+    b = oracle.sample_open(*args, SampleCfg(g_open=K, tangent_mode=1))
+    assert np.allclose(b["theta"][0].numpy(), math.atan2(50, 120), atol=1e-12)
+    assert torch.allclose(a["theta"], b["theta"], atol=1e-12)
+    assert torch.equal(a["sigma_x"], b["sigma_x"]) and torch.equal(a["mu"], b["mu"])
+
+
+def test_tangent_mode_follows_the_curve_direction():
+    """On a random open curve, every sample's theta (mode 1) is the direction
+    of its own segment's chord B(t + h) - B(t - h) (one-sided at a segment's
+    start), a derivative-free estimate of the tangent."""
+    rng = np.random.default_rng(12)
+    ctrl = torch.as_tensor(rng.uniform(0, 100, (3, 10, 2)))
+    K = 13
+    out = oracle.sample_open(ctrl, torch.ones(3, dtype=F64), torch.zeros(3, 3, dtype=F64),
+                             torch.ones(3, 3, dtype=F64), SampleCfg(g_open=K, tangent_mode=1))
+    s, t = oracle.chain_sample_params(K, 3)
+    h = 1e-5
+    for k in range(K):
+        seg = ctrl[:, 3 * s[k]: 3 * s[k] + 4]
+        lo = max(t[k] - h, 0.0)
+        hi = min(t[k] + h, 1.0)
+        chord = oracle.bezier(seg, torch.full((3,), hi, dtype=F64)) - oracle.bezier(seg, torch.full((3,), lo,
+                                                                                                   dtype=F64))
+        ang = torch.atan2(chord[:, 1], chord[:, 0])
+        diff = torch.remainder(out["theta"][:, k] - ang + math.pi, 2 * math.pi) - math.pi
+        assert float(diff.abs().max()) <= 1e-4, k
+
+
+def test_tangent_mode_closed_rows_interpolate_the_boundary_derivatives():
+    """A closed row is (1 - tau) A + tau B (Eq. 4), so its derivative is
+    (1 - tau) A'(t) + tau B'(t) (linearity of Eq. 1): mode 1's theta is the
+    angle of that combination."""
+    rng = np.random.default_rng(13)
+    ctrl = torch.as_tensor(rng.uniform(0, 100, (2, 12, 2)))
+    cfg = SampleCfg(rows_closed=5, k_closed=9, tangent_mode=1)
+    out = oracle.sample_closed(ctrl, torch.zeros(2, 3, dtype=F64), torch.ones(2, dtype=F64), cfg)
+    A, B = oracle.closed_boundaries(ctrl)
+    dA = oracle.curves.chain_tangents(A, 9)
+    dB = oracle.curves.chain_tangents(B, 9)
+    tau = oracle.closed_tau(5)
+    for r in range(5):
+        v = (1 - tau[r]) * dA + tau[r] * dB
+        exp = torch.atan2(v[..., 1], v[..., 0])
+        assert torch.allclose(out["theta"][:, r], exp, atol=1e-10), r
+
+
+def test_tangent_mode_zero_derivative_gives_theta_zero():
+    """Coincident control points: B'(t) = 0, theta = 0 (the zero-vector rule
+    of Eq. 8's reading), with a zero derivative."""
+    ctrl = torch.full((1, 10, 2), 7.0, dtype=F64, requires_grad=True)
+    out = oracle.sample_open(ctrl, torch.ones(1, dtype=F64), torch.zeros(1, 3, dtype=F64),
+                             torch.ones(1, 3, dtype=F64), SampleCfg(g_open=6, tangent_mode=1))
+    assert float(out["theta"].abs().max()) == 0.0
+    g, = torch.autograd.grad(out["theta"].sum(), ctrl)
+    assert float(g.abs().max()) == 0.0
