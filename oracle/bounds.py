@@ -107,7 +107,9 @@ def sample_abs_vjp(curves: dict, cfg: SampleCfg, scale: dict, first=None) -> dic
     (scale[k] >= 0, [Ng], the colour [Ng, 3]).  A Gaussian depends on its
     own curve only, so one forward-mode derivative per parameter slot, with
     the tangent set at that slot of every curve at once, gives every
-    Gaussian's derivative with respect to its own curve's parameter."""
+    Gaussian's derivative with respect to its own curve's parameter; the
+    slots' derivatives are taken together (torch.func.vmap over the
+    tangents)."""
     keys = [k for k in curves]
     vals = tuple(curves[k].detach().to(F64) for k in keys)
 
@@ -115,20 +117,28 @@ def sample_abs_vjp(curves: dict, cfg: SampleCfg, scale: dict, first=None) -> dic
         t = gaussian_table(dict(zip(keys, v)), cfg, first)
         return tuple(t[k] for k in GRAD_KEYS)
 
+    slots = []          # (input index, slot index within a curve's row)
+    for vi, v in enumerate(vals):
+        if v.shape[0]:
+            slots += [(vi, j) for j in range(v[0].numel())]
+    out = {k: torch.zeros_like(v) for k, v in zip(keys, vals)}
+    if not slots:
+        return out
+    tangents = []
+    for vi, v in enumerate(vals):
+        t = torch.zeros((len(slots),) + tuple(v.shape), dtype=F64)
+        for si, (vj, j) in enumerate(slots):
+            if vj == vi:
+                t[si].reshape(v.shape[0], -1)[:, j] = 1.0
+        tangents.append(t)
+    jvps = torch.func.vmap(lambda *tt: torch.func.jvp(table, vals, tt)[1])(*tangents)
     sc = [torch.as_tensor(scale[k], dtype=F64) for k in GRAD_KEYS]
-    out = {}
-    for vi, (k, v) in enumerate(zip(keys, vals)):
-        n = v.shape[0]
-        res = torch.zeros_like(v).reshape(n, -1) if n else torch.zeros_like(v)
-        if n:
-            for j in range(res.shape[1]):
-                tang = tuple(torch.zeros_like(w) for w in vals)
-                tang[vi].reshape(n, -1)[:, j] = 1.0
-                _, jv = torch.func.jvp(table, vals, tang)
-                contrib = sum((d.abs() * s).reshape(d.shape[0], -1).sum(1) for d, s in zip(jv, sc))
-                # Gaussian g belongs to one curve: sum its contributions per curve
-                res[:, j] = _per_curve(contrib, k, curves, cfg, first)
-        out[k] = res.reshape(v.shape)
+    for si, (vi, j) in enumerate(slots):
+        contrib = sum((d[si].abs() * s).reshape(d.shape[1], -1).sum(1) for d, s in zip(jvps, sc))
+        k = keys[vi]
+        n = vals[vi].shape[0]
+        # Gaussian g belongs to one curve: sum its contributions per curve
+        out[k].reshape(n, -1)[:, j] = _per_curve(contrib, k, curves, cfg, first)
     return out
 
 
