@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "bs_internal.cuh"
 
@@ -45,10 +46,15 @@ constexpr int kMaxPasses = 4;
 constexpr int64_t kMaxPairs = (1ll << 30) - 1;
 constexpr int kScanThreads = 1024;
 
+// Header of the binning workspace: status bits (kDevErr*), the pairs the
+// Gaussians' rectangles hold, and the pairs sorted (n_pairs, or 0 when they
+// exceed the capacity: then nothing is emitted or sorted and every tile
+// range is empty).
 struct Hdr {
   uint32_t status;
   uint32_t pad;
   unsigned long long n_pairs;
+  unsigned long long n_sorted;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -147,10 +153,13 @@ __global__ void __launch_bounds__(kCountThreads) count_kernel(const float *gauss
   if (threadIdx.x == kCountThreads - 1) partial[blockIdx.x] = warp_excl + incl;
 }
 
-// Exclusive scan of the per-CTA totals (one CTA); writes the pair count and
-// the sentinel partial[n] = P.
+// Exclusive scan of the per-CTA totals (one CTA); writes the pair count P,
+// the sentinel partial[n] = P, and with a header (one canvas) the count to
+// sort: P, or 0 with the capacity bit of the status word when P exceeds the
+// capacity.
 __global__ void __launch_bounds__(1024) scan_partials_kernel(unsigned long long *partial, int64_t n,
-                                                             unsigned long long *total_out) {
+                                                             unsigned long long *total_out, Hdr *hdr,
+                                                             int64_t capacity) {
   __shared__ unsigned long long s[1024];
   __shared__ unsigned long long carry;
   if (threadIdx.x == 0) carry = 0;
@@ -173,6 +182,11 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(unsigned long long 
   }
   if (threadIdx.x == 0) {
     *total_out = carry;
+    if (hdr) {
+      const bool over = carry > (unsigned long long)capacity;
+      hdr->n_sorted = over ? 0ull : carry;
+      if (over) hdr->status |= kDevErrCapacity;
+    }
     partial[n] = carry;
   }
 }
@@ -236,7 +250,8 @@ __device__ __forceinline__ uint32_t block_excl_scan1024(uint32_t v, uint32_t *s_
 }
 
 __global__ void __launch_bounds__(1024) tile_scan_kernel(const int *counts, int tiles_x, int tiles_y, int passes,
-                                                         int digit_bits, uint2 *ranges, uint32_t *hist) {
+                                                         int digit_bits, const Hdr *hdr, uint2 *ranges,
+                                                         uint32_t *hist) {
   __shared__ uint32_t s_hist[kMaxPasses * 256];
   __shared__ uint32_t s_warp[32];
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) s_hist[i] = 0u;
@@ -256,10 +271,11 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const int *counts, int 
   }
   uint32_t total;
   uint32_t start = block_excl_scan1024(sum, s_warp, &total);
+  const bool over = (hdr->status & kDevErrCapacity) != 0u;  // nothing sorted: every range empty
   for (int t = t0; t < t1; ++t) {
     const int ty = t / tiles_x, tx = t - ty * tiles_x;
     const uint32_t v = (uint32_t)counts[ty * stride + tx];
-    ranges[t] = v ? make_uint2(start, start + v) : make_uint2(0u, 0u);
+    ranges[t] = (v && !over) ? make_uint2(start, start + v) : make_uint2(0u, 0u);
     start += v;
   }
   __syncthreads();
@@ -286,7 +302,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const int *counts, int 
 constexpr int kFusedMaxWords = 48 * 1024;   // ints of array + prefixes in shared memory
 __global__ void __launch_bounds__(1024) fused_tile_scan_kernel(const int *__restrict__ diff, int tiles_x,
                                                                int tiles_y, int passes, int digit_bits,
-                                                               uint2 *__restrict__ ranges, uint32_t *__restrict__ hist) {
+                                                               const Hdr *hdr, uint2 *__restrict__ ranges,
+                                                               uint32_t *__restrict__ hist) {
   extern __shared__ int s_dyn[];
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_dig[kMaxPasses * 256];
@@ -362,11 +379,12 @@ __global__ void __launch_bounds__(1024) fused_tile_scan_kernel(const int *__rest
   }
   if (threadIdx.x == 0) s_pre[n] = total;
   __syncthreads();
-  // ranges, coalesced; pass-0 digit counts
+  // ranges, coalesced (all empty when nothing is sorted); pass-0 digit counts
   const uint32_t dmask = (1u << digit_bits) - 1;
+  const bool over = (hdr->status & kDevErrCapacity) != 0u;
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     const uint32_t pre = s_pre[t], v = s_pre[t + 1] - pre;
-    ranges[t] = v ? make_uint2(pre, pre + v) : make_uint2(0u, 0u);
+    ranges[t] = (v && !over) ? make_uint2(pre, pre + v) : make_uint2(0u, 0u);
     if (passes > 1 && v) atomicAdd(&s_dig[t & dmask], v);
   }
   const int hshift = digit_bits * (passes - 1);
@@ -1075,8 +1093,13 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
   return BS_OK;
 }
 
+// sync: read the pair count back (one stream synchronisation) and size the
+// sort's grids by it; otherwise size them by the capacity and let the
+// kernels read the count to sort from the workspace header (no host
+// dependency, so the binning can be captured in a CUDA graph).
 bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv, void *ws, int64_t *n_pairs,
-                      uint32_t *tile_keys, uint32_t *tile_ranges, cudaStream_t s) {
+                      uint32_t *tile_keys, uint32_t *tile_ranges, cudaStream_t s, bool sync,
+                      int64_t *n_pairs_dev) {
   char *base = static_cast<char *>(ws);
   Hdr *hdr = reinterpret_cast<Hdr *>(base + p.off_hdr);
   uint32_t *local = reinterpret_cast<uint32_t *>(base + p.off_local);
@@ -1089,6 +1112,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   uint32_t *part_offs = reinterpret_cast<uint32_t *>(base + p.off_parts);
   uint2 *ranges = reinterpret_cast<uint2 *>(tile_ranges);
   const int rows = p.tiles_y + 1, cols = p.tiles_x + 1;
+  const unsigned long long *count = &hdr->n_sorted;
 
   {
     const size_t nz = p.zero_bytes / sizeof(uint32_t);
@@ -1100,7 +1124,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     count_kernel<<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(gauss, p.n_gauss, cv.width, cv.height,
                                                                     cv.tile, p.tiles_x, local, partial, rects, diff);
     BS_LAUNCHED("count_kernel");
-    scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, &hdr->n_pairs);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, &hdr->n_pairs, hdr, p.capacity);
     BS_LAUNCHED("scan_partials_kernel");
     chunk_owner_kernel<uint2><<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(
         local, partial, rects, p.n_gauss, (uint32_t)div_up64(p.capacity, kEmitTile), owner);
@@ -1116,26 +1140,36 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
                                    (int)(sizeof(int) * kFusedMaxWords)));
       if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    fused_tile_scan_kernel<<<1, 1024, smem, s>>>(diff, p.tiles_x, p.tiles_y, p.passes, p.digit_bits, ranges, hist);
+    fused_tile_scan_kernel<<<1, 1024, smem, s>>>(diff, p.tiles_x, p.tiles_y, p.passes, p.digit_bits, hdr, ranges,
+                                                 hist);
     BS_LAUNCHED("fused_tile_scan_kernel");
   } else {
     diff_rows_kernel<<<div_up(rows, 8), 256, 0, s>>>(diff, rows, cols);
     BS_LAUNCHED("diff_rows_kernel");
     diff_cols_kernel<<<div_up(cols, 8), 256, 0, s>>>(diff, rows, cols);
     BS_LAUNCHED("diff_cols_kernel");
-    tile_scan_kernel<<<1, 1024, 0, s>>>(diff, p.tiles_x, p.tiles_y, p.passes, p.digit_bits, ranges, hist);
+    tile_scan_kernel<<<1, 1024, 0, s>>>(diff, p.tiles_x, p.tiles_y, p.passes, p.digit_bits, hdr, ranges, hist);
     BS_LAUNCHED("tile_scan_kernel");
   }
-  Hdr h;
-  BS_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(Hdr), cudaMemcpyDeviceToHost, s));
-  BS_CUDA(cudaStreamSynchronize(s));
-  *n_pairs = (int64_t)h.n_pairs;
-  if ((int64_t)h.n_pairs > p.capacity) {
-    set_error("%lld pairs exceed pair_capacity %lld", (long long)h.n_pairs, (long long)p.capacity);
-    return BS_ERR_CAPACITY;
+  if (n_pairs_dev) {
+    BS_CUDA(cudaMemcpyAsync(n_pairs_dev, &hdr->n_pairs, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   }
-  const int64_t P = (int64_t)h.n_pairs;
-  if (P == 0) return BS_OK;
+  // the number of keys the grids below cover: P (read back) or the capacity
+  int64_t P;
+  if (sync) {
+    Hdr h;
+    BS_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(Hdr), cudaMemcpyDeviceToHost, s));
+    BS_CUDA(cudaStreamSynchronize(s));
+    *n_pairs = (int64_t)h.n_pairs;
+    if ((int64_t)h.n_pairs > p.capacity) {
+      set_error("%lld pairs exceed pair_capacity %lld", (long long)h.n_pairs, (long long)p.capacity);
+      return BS_ERR_CAPACITY;
+    }
+    P = (int64_t)h.n_pairs;
+  } else {
+    P = p.capacity;
+  }
+  if (P == 0 || p.n_gauss == 0) return BS_OK;
   const int64_t parts = div_up64(P, kSortTile);
   const int bits0 = std::min(p.digit_bits, p.tbits);
   BS_CUDA(cudaMemsetAsync(part_offs, 0, sizeof(uint32_t) * ((size_t)1 << bits0) * (size_t)parts, s));
@@ -1144,7 +1178,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     auto *k64 = reinterpret_cast<unsigned long long *>(base + p.off_keys_tmp);
     unsigned long long *kb[2] = {k64, k64 + p.capacity};
     emit_kernel<unsigned long long><<<(unsigned)div_up64(P, kEmitTile), kEmitThreads, 0, s>>>(
-        local, partial, p.count_blocks, rects, p.n_gauss, &hdr->n_pairs, p.tiles_x, p.gbits, owner, kb[0], bits0,
+        local, partial, p.count_blocks, rects, p.n_gauss, count, p.tiles_x, p.gbits, owner, kb[0], bits0,
         part_offs, (uint32_t)parts);
     BS_LAUNCHED("emit_kernel");
     int cur = 0;
@@ -1152,19 +1186,19 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
       const int shift = 32 + pass * p.digit_bits;
       const int bits = std::min(p.digit_bits, p.tbits - pass * p.digit_bits);
       if (pass > 0) {
-        upsweep_kernel<unsigned long long><<<(unsigned)parts, kSortThreads, 0, s>>>(kb[cur], &hdr->n_pairs, shift,
-                                                                                   bits, part_offs, (uint32_t)parts);
+        upsweep_kernel<unsigned long long><<<(unsigned)parts, kSortThreads, 0, s>>>(kb[cur], count, shift, bits,
+                                                                                   part_offs, (uint32_t)parts);
         BS_LAUNCHED("upsweep_kernel");
       }
       scan_parts_kernel<<<1u << bits, kScanThreads, 0, s>>>(part_offs, (uint32_t)parts, hist + pass * 256);
       BS_LAUNCHED("scan_parts_kernel");
       if (pass + 1 < p.passes) {
         downsweep_kernel<unsigned long long, unsigned long long><<<(unsigned)parts, kSortThreads, 0, s>>>(
-            kb[cur], kb[1 - cur], &hdr->n_pairs, shift, bits, part_offs, (uint32_t)parts);
+            kb[cur], kb[1 - cur], count, shift, bits, part_offs, (uint32_t)parts);
         cur = 1 - cur;
       } else {
         downsweep_kernel<unsigned long long, uint32_t><<<(unsigned)parts, kSortThreads, 0, s>>>(
-            kb[cur], tile_keys, &hdr->n_pairs, shift, bits, part_offs, (uint32_t)parts);
+            kb[cur], tile_keys, count, shift, bits, part_offs, (uint32_t)parts);
       }
       BS_LAUNCHED("downsweep_kernel");
     }
@@ -1174,7 +1208,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   uint32_t *bufs[2] = {tile_keys, keys_tmp};
   uint32_t *src = (p.passes % 2 == 0) ? tile_keys : keys_tmp;
   emit_kernel<uint32_t><<<(unsigned)div_up64(P, kEmitTile), kEmitThreads, 0, s>>>(local, partial, p.count_blocks, rects,
-                                                                                 p.n_gauss, &hdr->n_pairs, p.tiles_x,
+                                                                                 p.n_gauss, count, p.tiles_x,
                                                                                  p.gbits, owner, src, bits0, part_offs,
                                                                                  (uint32_t)parts);
   BS_LAUNCHED("emit_kernel");
@@ -1183,13 +1217,13 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     const int shift = p.gbits + pass * p.digit_bits;
     const int bits = std::min(p.digit_bits, p.tbits - pass * p.digit_bits);
     if (pass > 0) {  // the first pass's counts come from emit_kernel
-      upsweep_kernel<uint32_t><<<(unsigned)parts, kSortThreads, 0, s>>>(src, &hdr->n_pairs, shift, bits, part_offs,
+      upsweep_kernel<uint32_t><<<(unsigned)parts, kSortThreads, 0, s>>>(src, count, shift, bits, part_offs,
                                                                         (uint32_t)parts);
       BS_LAUNCHED("upsweep_kernel");
     }
     scan_parts_kernel<<<1u << bits, kScanThreads, 0, s>>>(part_offs, (uint32_t)parts, hist + pass * 256);
     BS_LAUNCHED("scan_parts_kernel");
-    downsweep_kernel<uint32_t, uint32_t><<<(unsigned)parts, kSortThreads, 0, s>>>(src, dst, &hdr->n_pairs, shift,
+    downsweep_kernel<uint32_t, uint32_t><<<(unsigned)parts, kSortThreads, 0, s>>>(src, dst, count, shift,
                                                                                    bits, part_offs, (uint32_t)parts);
     BS_LAUNCHED("downsweep_kernel");
     src = dst;
@@ -1223,7 +1257,7 @@ bs_status run_batch_binning(const BatchPlan &p, void *ws, const float *gauss, ui
     batch_count_kernel<<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(gauss, p.n_gauss, tab, p.n_images,
                                                                           p.tile, local, partial, rects, diff);
     BS_LAUNCHED("batch_count_kernel");
-    scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, &hdr->n_pairs);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, &hdr->n_pairs, nullptr, 0);
     BS_LAUNCHED("scan_partials_kernel");
     chunk_owner_kernel<uint4><<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(
         local, partial, rects, p.n_gauss, (uint32_t)div_up64(p.capacity, kEmitTile), owner);
@@ -1236,7 +1270,7 @@ bs_status run_batch_binning(const BatchPlan &p, void *ws, const float *gauss, ui
   batch_tile_reduce_kernel<<<(unsigned)p.tile_blocks, kTileThreads, 0, s>>>(diff, tab, p.n_images, p.n_tiles,
                                                                             p.passes, p.digit_bits, tsum, hist);
   BS_LAUNCHED("batch_tile_reduce_kernel");
-  scan_partials_kernel<<<1, 1024, 0, s>>>(tsum, p.tile_blocks, &hdr->tile_total);
+  scan_partials_kernel<<<1, 1024, 0, s>>>(tsum, p.tile_blocks, &hdr->tile_total, nullptr, 0);
   BS_LAUNCHED("scan_partials_kernel");
   batch_digits_kernel<<<1, 32 * kMaxPasses, 0, s>>>(hdr, p.capacity, p.passes, hist);
   BS_LAUNCHED("batch_digits_kernel");
@@ -1294,12 +1328,16 @@ bs_status read_batch_status(const BatchPlan &p, const void *ws, int32_t *status,
 // which every GPU that loads the library holds until the process exits.
 // Host code may not pass the array's name to a kernel (on the host it only
 // names a stand-in); its device address is looked up once per device, with
-// that device current, and cached.
+// that device current, under a per-device once flag (so concurrent first
+// calls from several host threads are safe), and kept.  A device reset
+// (cudaDeviceReset) unloads the module and makes that address stale.
 namespace {
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
 void *g_static_scratch_ptr[kMaxDevices] = {};
+cudaError_t g_static_scratch_err[kMaxDevices] = {};
+std::once_flag g_static_scratch_once[kMaxDevices];
 }  // namespace
 
 bs_status static_scratch(void **ptr) {
@@ -1309,16 +1347,17 @@ bs_status static_scratch(void **ptr) {
     set_error("device %d: at most %d devices supported", dev, kMaxDevices);
     return BS_ERR_UNSUPPORTED;
   }
-  if (!g_static_scratch_ptr[dev]) {
+  std::call_once(g_static_scratch_once[dev], [dev] {
     void *p = nullptr;
-    BS_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_scratch_err[dev] = cudaGetSymbolAddress(&p, g_static_scratch);
     g_static_scratch_ptr[dev] = p;
-  }
+  });
+  BS_CUDA(g_static_scratch_err[dev]);
   *ptr = g_static_scratch_ptr[dev];
   return BS_OK;
 }
 
-bs_status read_device_status(const void *ws, size_t ws_bytes, int32_t *out, cudaStream_t s) {
+bs_status read_device_status(const void *ws, size_t ws_bytes, int32_t *out, cudaStream_t s, int64_t *n_pairs) {
   if (ws_bytes < sizeof(Hdr)) {
     set_error("workspace too small");
     return BS_ERR_INVALID_ARG;
@@ -1327,6 +1366,7 @@ bs_status read_device_status(const void *ws, size_t ws_bytes, int32_t *out, cuda
   BS_CUDA(cudaMemcpyAsync(&h, ws, sizeof(Hdr), cudaMemcpyDeviceToHost, s));
   BS_CUDA(cudaStreamSynchronize(s));
   *out = (h.status & kDevErrTimeout) ? BS_ERR_TIMEOUT : (h.status ? BS_ERR_CAPACITY : BS_OK);
+  if (n_pairs) *n_pairs = (int64_t)h.n_pairs;
   return BS_OK;
 }
 

@@ -69,3 +69,32 @@ def test_static_scratch_refuses_oversized_requests(bs):
                                     ctypes.c_void_p(ranges.data_ptr()), None)
     assert st == bs.BS_ERR_INVALID_ARG
     assert b"fixed scratch" in bs.lib.bs_last_error()
+
+
+def test_static_scratch_allocates_no_device_memory(bs):
+    """The defining property: after a first call on the device (which looks
+    up the array's address and loads the kernels), repeated calls change
+    neither the device's free memory (cudaMemGetInfo) nor the counts of
+    torch's caching allocator."""
+    canvas = bs.Canvas(300, 200)
+    gauss = torch.as_tensor(_table(3, 300, 200, 4000), device="cuda")
+    keys = torch.empty(1 << 18, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(canvas.n_tiles, 2, dtype=torch.int32, device="cuda")
+    cv = canvas.c()
+    n_pairs = ctypes.c_int64(0)
+    args = (ctypes.c_void_p(gauss.data_ptr()), 4000, ctypes.byref(cv), keys.numel(), ctypes.byref(n_pairs),
+            ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(ranges.data_ptr()), None)
+    assert bs.lib.bs_bin_tiles_static(*args) == bs.BS_OK     # warm-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    first = n_pairs.value
+    for _ in range(5):
+        assert bs.lib.bs_bin_tiles_static(*args) == bs.BS_OK
+        assert n_pairs.value == first
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    for k in ("allocation.all.allocated", "segment.all.allocated", "allocated_bytes.all.allocated"):
+        assert stats1.get(k, 0) == stats0.get(k, 0), k
