@@ -13,16 +13,21 @@
  *     parameter says "host".  The library never allocates device memory.
  *   - Calls are asynchronous on the given stream (a cudaStream_t; NULL is
  *     the legacy default stream).  The calls that synchronise are
- *     bs_bin_tiles and bs_bin_tiles_static (one 8-byte read-back of the pair
+ *     bs_bin_tiles and bs_bin_tiles_static (one read-back of the pair
  *     count), bs_prune_densify (its counts), bs_batch_setup (the copy of the
- *     layout table), and the status reads bs_device_status and
- *     bs_batch_status.
+ *     layout table), and the status reads bs_device_status,
+ *     bs_bin_tiles_result, bs_batch_status and bs_sync_status.  Every other
+ *     call (bs_bin_tiles_async for the binning) can be captured in a CUDA
+ *     graph.
  *   - Every call returns a bs_status.  Arguments are validated on the host
  *     before anything is launched; an invalid argument returns
  *     BS_ERR_INVALID_ARG and launches nothing.  bs_last_error() gives a
  *     thread-local message for the last non-OK status.
- *   - Errors found by a kernel (a count that overflowed) are recorded in a
- *     status word inside the binning workspace; bs_device_status reads it.
+ *   - Errors found by a kernel are recorded in device status words and read
+ *     later, so that no call waits on them: a count that overflowed in the
+ *     binning workspace's word (bs_device_status, bs_bin_tiles_result), a
+ *     non-finite Gaussian record or gradient in the library's own word of
+ *     each device (bs_sync_status).
  *   - Coordinates are pixels: pixel (x, y) covers [x, x+1) x [y, y+1) and
  *     its centre is (x + 0.5, y + 0.5).  Colours and opacities are the
  *     activated values in [0, 1].
@@ -48,7 +53,7 @@ typedef enum {
   BS_ERR_CUDA = 2,          /* a CUDA runtime call failed (message in bs_last_error) */
   BS_ERR_CAPACITY = 3,      /* pair_capacity too small; *n_pairs_out holds the need  */
   BS_ERR_TIMEOUT = 4,       /* a bounded device-side retry loop ran out              */
-  BS_ERR_NOT_FINITE = 5,    /* reserved: non-finite values detected                 */
+  BS_ERR_NOT_FINITE = 5,    /* a kernel wrote a non-finite record or gradient (bs_sync_status) */
   BS_ERR_UNSUPPORTED = 6    /* device or configuration the library does not support */
 } bs_status;
 
@@ -101,6 +106,11 @@ typedef struct {
                           rows_closed * k_closed <= 3072                           */
   float rho;           /* the density constant of Eq. 7, > 0                      */
   float cov_eps;       /* isotropic covariance floor in px^2 (Sigma += eps I), >= 0 */
+  int32_t tangent_mode;/* the Gaussian's rotation (Eq. 8): 0 from the neighbour
+                          difference X_{k+1} - X_{k-1} (one-sided at the ends), as
+                          the paper; 1 from the derivative B'(t) of the sample's own
+                          segment (a closed row's: (1 - tau) A'(t) + tau B'(t)).
+                          A zero vector gives theta = 0 either way.               */
 } bs_sample_cfg;
 
 /* The canvas and its tiling (Section 3.4). */
@@ -150,7 +160,8 @@ bs_status bs_curve_order(const bs_curves *curves, const bs_sample_cfg *cfg,
  * Sample Gaussians on curves (Section 3.3, Eq. 3-8; covariance Eq. 11-12).
  * Open curve: K samples uniform in u = k/(K-1) over the 3-segment chain;
  * sigma_x = |X_{k+1} - X_k| / rho (last sample: previous pair),
- * sigma_y = width, theta from the central difference (ends: one-sided).
+ * sigma_y = width, theta from the central difference (ends: one-sided), or
+ * with tangent_mode 1 from the derivative of the sample's segment.
  * Closed curve: rows r = 0..R+1 interpolate the control points of boundary
  * A = P0..P6 and boundary B = P0,P11,...,P7,P6 with weights
  * tau_r = (1 - cos(pi r/(R+1)))/2; K samples per row; sigma_y is the distance
@@ -204,6 +215,28 @@ bs_status bs_bin_tiles(const float *gauss, int64_t n_gauss, const bs_canvas *can
                        bs_stream stream);
 
 /*
+ * bs_bin_tiles without the read-back (the tile pipeline of Section 3.4, the
+ * rules of bs_bin_tiles): every grid of the sort is sized by pair_capacity
+ * (>= 1) and the kernels read the pair count P from the workspace, so the
+ * call never waits on the host and can be captured in a CUDA graph.
+ *   n_pairs_dev  (device int64, may be NULL) receives P, stream-ordered
+ *   tile_keys, tile_ranges  as bs_bin_tiles
+ * When P > pair_capacity nothing is emitted or sorted, every range is (0, 0)
+ * (a blend then draws only the background), and the workspace's status word
+ * records BS_ERR_CAPACITY: bs_bin_tiles_result (or bs_device_status) reports
+ * it together with P, for a retry with a larger capacity.
+ */
+bs_status bs_bin_tiles_async(const float *gauss, int64_t n_gauss, const bs_canvas *canvas,
+                             void *ws, size_t ws_bytes, int64_t pair_capacity, int64_t *n_pairs_dev,
+                             uint32_t *tile_keys, uint32_t *tile_ranges, bs_stream stream);
+
+/* Synchronise the stream and read the outcome of the last binning in `ws`:
+ * *status_out = BS_OK or BS_ERR_CAPACITY (BS_ERR_TIMEOUT is reserved), and
+ * *n_pairs_out (HOST, may be NULL) = the pairs that binning found. */
+bs_status bs_bin_tiles_result(const void *ws, size_t ws_bytes, int32_t *status_out, int64_t *n_pairs_out,
+                              bs_stream stream);
+
+/*
  * bs_bin_tiles for callers that cannot allocate device memory: the same
  * binning, with its scratch in one fixed array of 32 MiB that the library
  * keeps in device memory (every GPU that loads the library holds it until the
@@ -217,7 +250,11 @@ bs_status bs_bin_tiles(const float *gauss, int64_t n_gauss, const bs_canvas *can
  *     BS_ERR_INVALID_ARG with the size it needs; nothing is launched.
  *   - No allocation is made: no cudaMalloc, cudaFree or allocating library
  *     routine.  The first call on a device looks up the array's device
- *     address, so make that first call before any stream capture.
+ *     address (once per device, safe from several host threads), so make
+ *     that first call before any stream capture.  A device reset
+ *     (cudaDeviceReset) unloads the array and leaves that address stale: do
+ *     not call this entry point on a device after resetting it in the same
+ *     process.
  *   - All calls share the one array and it keeps the last call's contents
  *     (each call clears what it needs cleared): calls that overlap on the GPU,
  *     on any streams, race with each other.  bs_device_status does not read it.
@@ -669,6 +706,17 @@ bs_status bs_device_status(const void *ws, size_t ws_bytes, int32_t *status_out,
  * this process.  No device loop is unbounded either way, and no kernel of
  * the library waits on another thread. */
 bs_status bs_debug_retry_limit(int64_t max_attempts);
+
+/* Synchronise the stream and read the library's status word of the current
+ * device: *status_out = BS_ERR_NOT_FINITE when, since the word was last
+ * cleared, the sampling (bs_sample_curves, bs_batch_sample_curves) wrote a
+ * non-finite Gaussian record (mean, direction, inverse scales, opacity or
+ * colour; e.g. from NaN control points, or eps = 0 with coincident samples),
+ * or a backward (bs_render_bwd, bs_batch_render_bwd, bs_sample_curves_bwd)
+ * wrote a non-finite per-Gaussian or curve gradient; else BS_OK.  With
+ * clear != 0 the word is reset after the read (stream-ordered).  The word
+ * is shared by every stream and caller on the device. */
+bs_status bs_sync_status(int32_t clear, int32_t *status_out, bs_stream stream);
 
 /* Message of the last non-OK status on this thread ("" if none). */
 const char *bs_last_error(void);

@@ -45,7 +45,7 @@ class bs_curves_grad(ctypes.Structure):
 
 class bs_sample_cfg(ctypes.Structure):
     _fields_ = [("g_open", c_int32), ("rows_closed", c_int32), ("k_closed", c_int32),
-                ("rho", c_float), ("cov_eps", c_float)]
+                ("rho", c_float), ("cov_eps", c_float), ("tangent_mode", c_int32)]
 
 
 class bs_canvas(ctypes.Structure):
@@ -128,6 +128,9 @@ _sig("bs_bin_tiles_workspace", c_int64, POINTER(bs_canvas), c_int64, POINTER(c_s
 _sig("bs_bin_tiles", _P, c_int64, POINTER(bs_canvas), _P, c_size_t, c_int64, POINTER(c_int64), _P, _P, _P)
 _sig("bs_render_fwd", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P)
 _sig("bs_bin_tiles_static", _P, c_int64, POINTER(bs_canvas), c_int64, POINTER(c_int64), _P, _P, _P)
+_sig("bs_bin_tiles_async", _P, c_int64, POINTER(bs_canvas), _P, c_size_t, c_int64, _P, _P, _P, _P)
+_sig("bs_bin_tiles_result", _P, c_size_t, POINTER(c_int32), POINTER(c_int64), _P)
+_sig("bs_sync_status", c_int32, POINTER(c_int32), _P)
 _sig("bs_render_fwd_l2", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P, _P, _P, _P)
 _sig("bs_l2_loss_grad", _P, _P, c_int64, _P, _P, _P)
 _sig("bs_render_stats", _P, c_int64, POINTER(bs_canvas), _P, _P, _P, _P, _P, _P, _P)
@@ -199,9 +202,11 @@ class SampleCfg:
     k_closed: int = 8
     rho: float = 1.0
     cov_eps: float = 0.3
+    tangent_mode: int = 0   # 0: Eq. 8's neighbour difference; 1: the derivative B'(t)
 
     def c(self):
-        return bs_sample_cfg(self.g_open, self.rows_closed, self.k_closed, self.rho, self.cov_eps)
+        return bs_sample_cfg(self.g_open, self.rows_closed, self.k_closed, self.rho, self.cov_eps,
+                             self.tangent_mode)
 
 
 @dataclass
@@ -288,13 +293,19 @@ def num_gaussians(n_open, n_closed, cfg: SampleCfg) -> int:
     return int(n)
 
 
-def curve_order(curves: CurveSet, cfg: SampleCfg):
-    """rank [N] (0 = front) and first [N] Gaussian index, uint32 as int32."""
+def curve_order(curves: CurveSet, cfg: SampleCfg, out=None):
+    """rank [N] (0 = front) and first [N] Gaussian index, uint32 as int32
+    (into out = (rank, first) when given)."""
     curves.check()
     n = curves.n_open + curves.n_closed
     dev = curves.open_ctrl.device
-    rank = torch.empty(n, dtype=torch.int32, device=dev)
-    first = torch.empty(n, dtype=torch.int32, device=dev)
+    if out is None:
+        rank = torch.empty(n, dtype=torch.int32, device=dev)
+        first = torch.empty(n, dtype=torch.int32, device=dev)
+    else:
+        rank, first = out
+        _want(rank, torch.int32, (n,), "rank")
+        _want(first, torch.int32, (n,), "first")
     c, k = curves.c(), cfg.c()
     _check("bs_curve_order", lib.bs_curve_order(ctypes.byref(c), ctypes.byref(k), _ptr(rank), _ptr(first),
                                                  _stream()))
@@ -370,11 +381,54 @@ class Binning:
             return self
         raise BSError("bs_bin_tiles", BS_ERR_CAPACITY)
 
+    def prepare(self, n_gauss: int, capacity: int = None):
+        """Allocate the workspace and key buffer for n_gauss Gaussians and
+        `capacity` pairs (default: the current wish), once, ahead of run_async."""
+        capacity = max(self._want_capacity, self.capacity) if capacity is None else capacity
+        if self.ws is None or n_gauss != self.n_gauss or self.capacity < capacity:
+            self._alloc(n_gauss, capacity)
+        return self
+
+    def run_async(self, gauss: torch.Tensor, n_pairs_dev: torch.Tensor = None):
+        """bs_bin_tiles_async: the binning with no read-back, graph-capturable.
+        The buffers must have been sized (prepare) beforehand; an overflow
+        shows in result().  n_pairs_dev: optional device int64 [1] for P."""
+        n_gauss = int(gauss.shape[0])
+        _want(gauss, torch.float32, (n_gauss, GAUSS_FLOATS), "gauss")
+        if self.ws is None or n_gauss != self.n_gauss:
+            raise RuntimeError("Binning.run_async needs prepare(n_gauss) first (no allocation while capturing)")
+        if n_pairs_dev is not None:
+            _want(n_pairs_dev, torch.int64, (1,), "n_pairs_dev")
+        cv = self.canvas.c()
+        _check("bs_bin_tiles_async", lib.bs_bin_tiles_async(_ptr(gauss), n_gauss, ctypes.byref(cv), _ptr(self.ws),
+                                                             self.ws.numel(), self.capacity, _ptr(n_pairs_dev),
+                                                             _ptr(self.keys), _ptr(self.ranges), _stream()))
+        self.n_pairs = None
+        return self
+
+    def result(self):
+        """(status, P) of the last binning (synchronises): BS_OK or
+        BS_ERR_CAPACITY, and the pairs it found; sets n_pairs."""
+        st, n = c_int32(0), c_int64(0)
+        _check("bs_bin_tiles_result", lib.bs_bin_tiles_result(_ptr(self.ws), self.ws.numel(), ctypes.byref(st),
+                                                               ctypes.byref(n), _stream()))
+        self.n_pairs = int(n.value)
+        return int(st.value), int(n.value)
+
     def device_status(self) -> int:
         out = c_int32(0)
         _check("bs_device_status", lib.bs_device_status(_ptr(self.ws), self.ws.numel(), ctypes.byref(out),
                                                          _stream()))
         return int(out.value)
+
+
+def sync_status(clear: bool = True) -> int:
+    """bs_sync_status: BS_OK, or BS_ERR_NOT_FINITE when a sampling or
+    backward kernel wrote a non-finite record or gradient since the last
+    clear (synchronises the current stream)."""
+    out = c_int32(0)
+    _check("bs_sync_status", lib.bs_sync_status(1 if clear else 0, ctypes.byref(out), _stream()))
+    return int(out.value)
 
 
 def bin_tiles_static(gauss: torch.Tensor, canvas: Canvas, tile_keys: torch.Tensor, tile_ranges: torch.Tensor):

@@ -5,6 +5,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string.h>
 
 #include <string>
@@ -56,6 +57,33 @@ bs_status check_device() {
 void debug_set_retry_limit(int64_t max_attempts);
 const char *last_error_cstr();
 
+// The library's own status word on each device (kDevErrNotFinite); its
+// device address is looked up once per device with that device current.
+namespace {
+__device__ uint32_t g_lib_status;
+constexpr int kMaxStatusDevices = 64;
+uint32_t *g_lib_status_ptr[kMaxStatusDevices] = {};
+cudaError_t g_lib_status_err[kMaxStatusDevices] = {};
+std::once_flag g_lib_status_once[kMaxStatusDevices];
+}  // namespace
+
+bs_status lib_status_word(uint32_t **ptr) {
+  int dev = 0;
+  BS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxStatusDevices) {
+    set_error("device %d: at most %d devices supported", dev, kMaxStatusDevices);
+    return BS_ERR_UNSUPPORTED;
+  }
+  std::call_once(g_lib_status_once[dev], [dev] {
+    void *p = nullptr;
+    g_lib_status_err[dev] = cudaGetSymbolAddress(&p, g_lib_status);
+    g_lib_status_ptr[dev] = static_cast<uint32_t *>(p);
+  });
+  BS_CUDA(g_lib_status_err[dev]);
+  *ptr = g_lib_status_ptr[dev];
+  return BS_OK;
+}
+
 }  // namespace bs
 
 using namespace bs;
@@ -78,6 +106,7 @@ bs_status check_cfg(const bs_sample_cfg *cfg) {
   if (cfg->rows_closed < 2 || cfg->k_closed < 2) return invalid("rows_closed and k_closed must be >= 2");
   if ((int64_t)cfg->rows_closed * cfg->k_closed > kMaxSamplesPerCurve)
     return invalid("rows_closed * k_closed > %d", kMaxSamplesPerCurve);
+  if (cfg->tangent_mode != 0 && cfg->tangent_mode != 1) return invalid("tangent_mode %d not 0 or 1", cfg->tangent_mode);
   if (!(cfg->rho > 0.f)) return invalid("rho must be > 0");
   if (!(cfg->cov_eps >= 0.f)) return invalid("cov_eps must be >= 0");
   return BS_OK;
@@ -362,6 +391,32 @@ bs_status bs_bin_tiles(const float *gauss, int64_t n_gauss, const bs_canvas *can
   return run_binning(p, gauss, *canvas, ws, n_pairs_out, tile_keys, tile_ranges, (cudaStream_t)stream);
 }
 
+bs_status bs_bin_tiles_async(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, void *ws, size_t ws_bytes,
+                             int64_t pair_capacity, int64_t *n_pairs_dev, uint32_t *tile_keys, uint32_t *tile_ranges,
+                             bs_stream stream) {
+  BS_TRY(check_canvas(canvas));
+  if (pair_capacity < 1) return invalid("pair_capacity must be >= 1");
+  BinPlan p;
+  BS_TRY(plan_binning(n_gauss, *canvas, pair_capacity, &p));
+  if (!ws || ws_bytes < p.bytes || !aligned16(ws))
+    return invalid("workspace needs %zu bytes (16-byte aligned), got %zu", p.bytes, ws_bytes);
+  if (n_gauss > 0 && (!gauss || !aligned16(gauss))) return invalid("gauss must be a 16-byte aligned device pointer");
+  if (!tile_ranges || !aligned16(tile_ranges)) return invalid("tile_ranges must be an 8-byte aligned device pointer");
+  if (!tile_keys) return invalid("tile_keys is NULL");
+  if (n_pairs_dev && (reinterpret_cast<uintptr_t>(n_pairs_dev) & 7u))
+    return invalid("n_pairs_dev must be 8-byte aligned");
+  BS_TRY(check_device());
+  int64_t unused = 0;
+  return run_binning(p, gauss, *canvas, ws, &unused, tile_keys, tile_ranges, (cudaStream_t)stream, false,
+                     n_pairs_dev);
+}
+
+bs_status bs_bin_tiles_result(const void *ws, size_t ws_bytes, int32_t *status_out, int64_t *n_pairs_out,
+                              bs_stream stream) {
+  if (!ws || !status_out) return invalid("NULL pointer");
+  return read_device_status(ws, ws_bytes, status_out, (cudaStream_t)stream, n_pairs_out);
+}
+
 bs_status bs_bin_tiles_static(const float *gauss, int64_t n_gauss, const bs_canvas *canvas, int64_t pair_capacity,
                               int64_t *n_pairs_out, uint32_t *tile_keys, uint32_t *tile_ranges, bs_stream stream) {
   BS_TRY(check_canvas(canvas));
@@ -631,6 +686,20 @@ bs_status bs_prune_densify(const bs_curves_mut *curves, const bs_pd_cfg *cfg, co
 bs_status bs_device_status(const void *ws, size_t ws_bytes, int32_t *status_out, bs_stream stream) {
   if (!ws || !status_out) return invalid("NULL pointer");
   return read_device_status(ws, ws_bytes, status_out, (cudaStream_t)stream);
+}
+
+bs_status bs_sync_status(int32_t clear, int32_t *status_out, bs_stream stream) {
+  if (!status_out) return invalid("status_out is NULL");
+  BS_TRY(check_device());
+  uint32_t *word = nullptr;
+  BS_TRY(lib_status_word(&word));
+  const cudaStream_t s = (cudaStream_t)stream;
+  uint32_t h = 0;
+  BS_CUDA(cudaMemcpyAsync(&h, word, sizeof(h), cudaMemcpyDeviceToHost, s));
+  BS_CUDA(cudaStreamSynchronize(s));
+  if (clear) BS_CUDA(cudaMemsetAsync(word, 0, sizeof(uint32_t), s));
+  *status_out = (h & kDevErrNotFinite) ? BS_ERR_NOT_FINITE : BS_OK;
+  return BS_OK;
 }
 
 bs_status bs_debug_retry_limit(int64_t max_attempts) {

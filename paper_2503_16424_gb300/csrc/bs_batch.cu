@@ -153,6 +153,7 @@ void fill_batch_table(const bs_batch_image *images, const BatchPlan &p, BatchIma
     e.kc = im.sample.k_closed;
     e.rho = im.sample.rho;
     e.eps = im.sample.cov_eps;
+    e.tmode = im.sample.tangent_mode;
     for (int c = 0; c < 3; ++c) e.bg[c] = im.bg[c];
     e.l2_scale = (float)(2.0 / (3.0 * (double)im.width * (double)im.height));
     const int64_t nc = (int64_t)im.n_open + im.n_closed;

@@ -38,6 +38,7 @@ __host__ __device__ inline int curve_threads(int n_max) { return n_max >= kWideS
 struct Cfg {
   int g_open, rows, kc;
   float rho, eps;
+  int tmode;  // 0: rotation from the neighbour difference (Eq. 8); 1: from B'(t)
 };
 
 // ---- float-float arithmetic: x = hi + lo, |lo| <= ulp(hi) / 2 ----
@@ -194,6 +195,31 @@ __device__ __forceinline__ float4 boundary_point(const float4 *Q, const ff w[4],
   return make_float4(x.hi, x.lo, y.hi, y.lo);
 }
 
+// Derivative weights of the cubic Bernstein basis at t (d/dt of Eq. 2):
+// dB/dt = sum_i dw_i Q_i.
+__device__ __forceinline__ float4 bern3_dt(float t) {
+  const float u = 1.f - t;
+  return make_float4(-3.f * u * u, 3.f * u * u - 6.f * u * t, 6.f * u * t - 3.f * t * t, 3.f * t * t);
+}
+
+// tangent_mode 1: dX/dt of a boundary at column k, the hodograph of its
+// segment, 3 (u^2 (Q1 - Q0) + 2 u t (Q2 - Q1) + t^2 (Q3 - Q2)), u = 1 - t, from
+// control-point differences taken in float-float (the same vector as
+// sum_i dw_i Q_i, since the dw_i sum to 0).
+__device__ __forceinline__ float2 boundary_tangent(const float4 *Q, int k, int K, int S, bool b_side) {
+  const int s = chain_seg(k, K, S);
+  const float t = ff_round(chain_t(k, K, S, s)), u = 1.f - t;
+  float2 d[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int j0 = b_side ? closed_b_index(3 * s + i) : 3 * s + i;
+    const int j1 = b_side ? closed_b_index(3 * s + i + 1) : 3 * s + i + 1;
+    d[i] = ff2_diff(Q[j1], Q[j0]);
+  }
+  const float a = 3.f * u * u, b = 6.f * u * t, c = 3.f * t * t;
+  return make_float2(a * d[0].x + b * d[1].x + c * d[2].x, a * d[0].y + b * d[1].y + c * d[2].y);
+}
+
 // Along-row difference e_k and tangent difference t_k of a column table X
 // (one-sided at both ends), each rounded to float from float-float.
 __device__ __forceinline__ float4 column_diffs(const float4 *X, int k, int K) {
@@ -233,9 +259,21 @@ __device__ int eval_samples(const bs_curves &c, const Cfg &cfg, int curve, const
   }
   __syncthreads();
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    m.EA[k] = column_diffs(m.XA, k, K);
+    float4 ea = column_diffs(m.XA, k, K);
+    if (cfg.tmode) {  // the tangent from B'(t) instead of the neighbour difference
+      const float2 ta = boundary_tangent(m.Q, k, K, S, false);
+      ea.z = ta.x;
+      ea.w = ta.y;
+    }
+    m.EA[k] = ea;
     if (closed) {
-      m.EB[k] = column_diffs(m.XB, k, K);
+      float4 eb = column_diffs(m.XB, k, K);
+      if (cfg.tmode) {
+        const float2 tb = boundary_tangent(m.Q, k, K, S, true);
+        eb.z = tb.x;
+        eb.w = tb.y;
+      }
+      m.EB[k] = eb;
       m.D[k] = ff2_diff(m.XB[k], m.XA[k]);
     }
   }
@@ -334,13 +372,14 @@ __device__ __forceinline__ Cfg batch_cfg(const BatchImage *__restrict__ tab, int
   const int b = curve < c.n_open ? last_image_le<&BatchImage::open0>(tab, n_images, curve)
                                  : last_image_le<&BatchImage::closed0>(tab, n_images, curve - c.n_open);
   const BatchImage &im = tab[b];
-  return Cfg{im.g_open, im.rows, im.kc, im.rho, im.eps};
+  return Cfg{im.g_open, im.rows, im.kc, im.rho, im.eps, im.tmode};
 }
 
 // tab == nullptr: one canvas, sampling cfg, CTA b samples curve b; else a
 // batch, CTA b samples curve curve_ids[b] with its image's sampling
 // (dynamic shared memory sized for the largest curve of the launch).
 __global__ void __launch_bounds__(kCurveThreadsWide) sample_fwd_kernel(bs_curves c, Cfg cfg, float *gauss,
+                                                                   uint32_t *status,
                                                                    const BatchImage *tab = nullptr,
                                                                    int n_images = 0,
                                                                    const int32_t *curve_ids = nullptr) {
@@ -369,9 +408,15 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_fwd_kernel(bs_curves
       ey = sqrtf(2.0f * lth * syy) + kExtPad;
     }
     float4 *rec = reinterpret_cast<float4 *>(gauss + (size_t)(first + idx) * BS_GAUSS_FLOATS);
-    rec[0] = make_float4(P[0] + L.mx, P[1] + L.my, L.ux, L.uy);
-    rec[1] = make_float4(rsqrtf(lx), rsqrtf(ly), at.opac, at.col.x);
+    const float4 r0 = make_float4(P[0] + L.mx, P[1] + L.my, L.ux, L.uy);
+    const float4 r1 = make_float4(rsqrtf(lx), rsqrtf(ly), at.opac, at.col.x);
+    rec[0] = r0;
+    rec[1] = r1;
     rec[2] = make_float4(at.col.y, at.col.z, ex, ey);
+    // a non-finite record (0 * x is NaN exactly when x is not finite)
+    const float probe = 0.f * r0.x + 0.f * r0.y + 0.f * r0.z + 0.f * r0.w + 0.f * r1.x + 0.f * r1.y + 0.f * r1.z +
+                        0.f * r1.w + 0.f * at.col.y + 0.f * at.col.z;
+    if (probe != 0.f) atomicOr(status, kDevErrNotFinite);
   }
 }
 
@@ -391,7 +436,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // coordinate gathers the Bernstein-weighted (and, for closed rows,
 // tau-weighted, Eq. 4) gradients of the sample points it moves.
 __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves c, Cfg cfg, const float *dgauss,
-                                                                   bs_curves_grad g,
+                                                                   bs_curves_grad g, uint32_t *status,
                                                                    const BatchImage *tab = nullptr,
                                                                    int n_images = 0,
                                                                    const int32_t *curve_ids = nullptr) {
@@ -496,11 +541,14 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
     if (k == K - 1) { d.x += GE[mi].x; d.y += GE[mi].y; }
     if (k < K - 1) { d.x -= GE[mi].x; d.y -= GE[mi].y; }
     if (k == K - 2) { d.x -= GE[mi + 1].x; d.y -= GE[mi + 1].y; }
-    // t_k = X_{k+1} - X_{k-1}, one-sided at both ends
-    if (k >= 1) { d.x += GT[mi - 1].x; d.y += GT[mi - 1].y; }
-    if (k == K - 1) { d.x += GT[mi].x; d.y += GT[mi].y; }
-    if (k <= K - 2) { d.x -= GT[mi + 1].x; d.y -= GT[mi + 1].y; }
-    if (k == 0) { d.x -= GT[mi].x; d.y -= GT[mi].y; }
+    // t_k = X_{k+1} - X_{k-1}, one-sided at both ends (tangent_mode 0; in
+    // mode 1 t_k is B'(t), which phase 3 takes to the control points)
+    if (!cfg.tmode) {
+      if (k >= 1) { d.x += GT[mi - 1].x; d.y += GT[mi - 1].y; }
+      if (k == K - 1) { d.x += GT[mi].x; d.y += GT[mi].y; }
+      if (k <= K - 2) { d.x -= GT[mi + 1].x; d.y -= GT[mi + 1].y; }
+      if (k == 0) { d.x -= GT[mi].x; d.y -= GT[mi].y; }
+    }
     if (closed) {
       // f_k = X_{r+1,k} - X_{r,k} (r < R2-1), X_{r,k} - X_{r-1,k} (last row)
       if (r >= 1) { d.x += GF[mi - K].x; d.y += GF[mi - K].y; }
@@ -521,10 +569,18 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
   // (boundary B): those column sums first (one thread per column), kept in
   // the no longer needed GE / GT planes, then every control point runs over
   // the K columns only.
-  float2 *colA = GE, *colB = GT;
+  // With tangent_mode 1 the row tangents t_rk = (1 - tau_r) tA_k + tau_r tB_k
+  // (local_geometry) are summed the same way into tangent columns (the GF
+  // plane, free after phase 2; GT is then still read, so the point columns
+  // go to the GE plane alone: R2 >= 2, so it holds both).  Open curves use
+  // dX and GT as their columns.
+  float2 *colA = GE, *colB = cfg.tmode ? GE + K : GT;
+  const float2 *colTA = GT, *colTB = GT;
   if (closed) {
+    float2 *tA = GF, *tB = GF + K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
       float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+      float2 ta = make_float2(0.f, 0.f), tb = make_float2(0.f, 0.f);
       for (int r = 0; r < R2; ++r) {
         const float tau = m.tau[r].x;
         const float2 dx = dX[r * K + k];
@@ -532,11 +588,24 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
         a.y += (1.f - tau) * dx.y;
         b.x += tau * dx.x;
         b.y += tau * dx.y;
+        if (cfg.tmode) {
+          const float2 gt = GT[r * K + k];
+          ta.x += (1.f - tau) * gt.x;
+          ta.y += (1.f - tau) * gt.y;
+          tb.x += tau * gt.x;
+          tb.y += tau * gt.y;
+        }
+      }
+      if (cfg.tmode) {
+        tA[k] = ta;
+        tB[k] = tb;
       }
       colA[k] = a;
       colB[k] = b;
     }
     __syncthreads();
+    colTA = tA;
+    colTB = tB;
   }
   // Each (control point, segment it shapes, coordinate) item sums over that
   // segment's samples only (a contiguous k range, no division per sample);
@@ -550,7 +619,7 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
   for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
     const int comp = it & 1, q = it >> 1;
     int j, sg;
-    const float2 *src = dX;
+    const float2 *src = dX, *srcT = colTA;
     if (!closed) {
       j = q < 10 ? q : (q == 10 ? 3 : 6);
       sg = q < 10 ? min(q / 3, 2) : (q == 10 ? 0 : 1);
@@ -559,11 +628,18 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
       j = r < 7 ? r : 3;
       sg = r < 7 ? min(r / 3, 1) : 0;
       src = q < 8 ? colA : colB;
+      srcT = q < 8 ? colTA : colTB;
     }
     const int i = j - 3 * sg;
     const int k0 = seg_first(sg, K, S), k1 = seg_first(sg + 1, K, S);
     float acc = 0.f;
     for (int k = k0; k < k1; ++k) acc += w_at(m.W[k], i) * (comp ? src[k].y : src[k].x);
+    if (cfg.tmode) {  // t_k = sum_i dw_i(t_k) Q_i (Eq. 1 differentiated)
+      for (int k = k0; k < k1; ++k) {
+        const float4 dw = bern3_dt(ff_round(chain_t(k, K, S, sg)));
+        acc += w_at(dw, i) * (comp ? srcT[k].y : srcT[k].x);
+      }
+    }
     s_item[it] = acc;
   }
   __syncthreads();
@@ -582,7 +658,9 @@ __global__ void __launch_bounds__(kCurveThreadsWide) sample_bwd_kernel(bs_curves
     }
     if (!closed) g.open_ctrl[(size_t)curve * 20 + t] = acc;
     else g.closed_ctrl[(size_t)(curve - c.n_open) * 24 + t] = acc;
+    if (0.f * acc != 0.f) atomicOr(status, kDevErrNotFinite);
   }
+  if (threadIdx.x < 11 && 0.f * sAttr[threadIdx.x] != 0.f) atomicOr(status, kDevErrNotFinite);
   if (!closed) {
     if (threadIdx.x < 3) {
       g.open_opac[curve * 3 + threadIdx.x] = sAttr[threadIdx.x];
@@ -754,7 +832,9 @@ __global__ void xing_kernel(const float *__restrict__ ctrl, int n_closed, float 
   }
 }
 
-Cfg to_cfg(const bs_sample_cfg &s) { return Cfg{s.g_open, s.rows_closed, s.k_closed, s.rho, s.cov_eps}; }
+Cfg to_cfg(const bs_sample_cfg &s) {
+  return Cfg{s.g_open, s.rows_closed, s.k_closed, s.rho, s.cov_eps, s.tangent_mode};
+}
 
 int max_samples(const bs_curves &c, const bs_sample_cfg &cfg) {
   int m = 0;
@@ -823,7 +903,9 @@ bs_status launch_sample_fwd(const bs_curves &c, const bs_sample_cfg &cfg, float 
   if (n == 0) return BS_OK;
   const size_t smem = launch_smem(c, cfg, false);
   BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-  sample_fwd_kernel<<<n, curve_threads(max_samples(c, cfg)), smem, s>>>(c, to_cfg(cfg), gauss);
+  uint32_t *status = nullptr;
+  BS_TRY(lib_status_word(&status));
+  sample_fwd_kernel<<<n, curve_threads(max_samples(c, cfg)), smem, s>>>(c, to_cfg(cfg), gauss, status);
   BS_LAUNCHED("sample_fwd_kernel");
   return BS_OK;
 }
@@ -834,7 +916,9 @@ bs_status launch_sample_bwd(const bs_curves &c, const bs_sample_cfg &cfg, const 
   if (n == 0) return BS_OK;
   const size_t smem = launch_smem(c, cfg, true);
   BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-  sample_bwd_kernel<<<n, curve_threads(max_samples(c, cfg)), smem, s>>>(c, to_cfg(cfg), dgauss, g);
+  uint32_t *status = nullptr;
+  BS_TRY(lib_status_word(&status));
+  sample_bwd_kernel<<<n, curve_threads(max_samples(c, cfg)), smem, s>>>(c, to_cfg(cfg), dgauss, g, status);
   BS_LAUNCHED("sample_bwd_kernel");
   return BS_OK;
 }
@@ -857,17 +941,20 @@ bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, c
   // curves below kWideSamples samples on narrow CTAs, the rest on wide ones
   // (curve_ids lists the narrow curves, then the wide ones), each launch
   // with the shared memory of its own largest curves
+  uint32_t *status = nullptr;
+  BS_TRY(lib_status_word(&status));
   if (p.narrow.n_curves > 0) {
     const size_t smem = launch_smem(p.narrow, false);
     BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-    sample_fwd_kernel<<<(unsigned)p.narrow.n_curves, kCurveThreads, smem, s>>>(c, Cfg{}, gauss, table, p.n_images,
-                                                                               curve_ids);
+    sample_fwd_kernel<<<(unsigned)p.narrow.n_curves, kCurveThreads, smem, s>>>(c, Cfg{}, gauss, status, table,
+                                                                               p.n_images, curve_ids);
     BS_LAUNCHED("sample_fwd_kernel");
   }
   if (p.wide.n_curves > 0) {
     const size_t smem = launch_smem(p.wide, false);
     BS_TRY(raise_smem(sample_fwd_kernel, smem, 0));
-    sample_fwd_kernel<<<(unsigned)p.wide.n_curves, kCurveThreadsWide, smem, s>>>(c, Cfg{}, gauss, table, p.n_images,
+    sample_fwd_kernel<<<(unsigned)p.wide.n_curves, kCurveThreadsWide, smem, s>>>(c, Cfg{}, gauss, status, table,
+                                                                                 p.n_images,
                                                                                  curve_ids + p.narrow.n_curves);
     BS_LAUNCHED("sample_fwd_kernel");
   }
@@ -877,18 +964,20 @@ bs_status launch_batch_sample_fwd(const BatchPlan &p, const BatchImage *table, c
 bs_status launch_batch_sample_bwd(const BatchPlan &p, const BatchImage *table, const int32_t *curve_ids,
                                   const bs_curves &c, const float *dgauss, const bs_curves_grad &g,
                                   cudaStream_t s) {
+  uint32_t *status = nullptr;
+  BS_TRY(lib_status_word(&status));
   if (p.narrow.n_curves > 0) {
     const size_t smem = launch_smem(p.narrow, true);
     BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-    sample_bwd_kernel<<<(unsigned)p.narrow.n_curves, kCurveThreads, smem, s>>>(c, Cfg{}, dgauss, g, table,
+    sample_bwd_kernel<<<(unsigned)p.narrow.n_curves, kCurveThreads, smem, s>>>(c, Cfg{}, dgauss, g, status, table,
                                                                                p.n_images, curve_ids);
     BS_LAUNCHED("sample_bwd_kernel");
   }
   if (p.wide.n_curves > 0) {
     const size_t smem = launch_smem(p.wide, true);
     BS_TRY(raise_smem(sample_bwd_kernel, smem, 1));
-    sample_bwd_kernel<<<(unsigned)p.wide.n_curves, kCurveThreadsWide, smem, s>>>(c, Cfg{}, dgauss, g, table,
-                                                                                 p.n_images,
+    sample_bwd_kernel<<<(unsigned)p.wide.n_curves, kCurveThreadsWide, smem, s>>>(c, Cfg{}, dgauss, g, status,
+                                                                                 table, p.n_images,
                                                                                  curve_ids + p.narrow.n_curves);
     BS_LAUNCHED("sample_bwd_kernel");
   }

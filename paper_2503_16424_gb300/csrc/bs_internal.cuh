@@ -38,10 +38,17 @@ bs_status check_device();
 
 #define BS_LAUNCHED(what) BS_TRY(::bs::cuda_status(cudaGetLastError(), what))
 
-// ---- device status word (inside the binning workspace) ----
+// ---- device status words ----
+// Inside the binning and batch workspaces:
 constexpr uint32_t kDevErrTimeout = 1u;
 constexpr uint32_t kDevErrCapacity = 2u;
 constexpr uint32_t kDevErrCounts = 4u;   // batch binning: pair totals disagree (never expected)
+// The library's own word on each device (bs_sync_status): a sampling or
+// backward kernel wrote a non-finite table record or gradient.
+constexpr uint32_t kDevErrNotFinite = 8u;
+// Device address of the current device's library status word, looked up
+// once per device (thread-safe).
+bs_status lib_status_word(uint32_t **ptr);
 
 // ---- small math helpers usable on host and device ----
 __host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
@@ -130,8 +137,9 @@ struct BinPlan {
 bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, BinPlan *p);
 bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv, void *ws,
                       int64_t *n_pairs, uint32_t *tile_keys, uint32_t *tile_ranges,
-                      cudaStream_t s);
-bs_status read_device_status(const void *ws, size_t ws_bytes, int32_t *out, cudaStream_t s);
+                      cudaStream_t s, bool sync = true, int64_t *n_pairs_dev = nullptr);
+bs_status read_device_status(const void *ws, size_t ws_bytes, int32_t *out, cudaStream_t s,
+                             int64_t *n_pairs = nullptr);
 // Fixed scratch of bs_bin_tiles_static: 32 MiB of device memory per GPU.
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;
 bs_status static_scratch(void **ptr);
@@ -163,7 +171,7 @@ struct BatchImage {
   float bg[3];
   float l2_scale;       // 2 / (3 W H)
   int order_chunks;     // ceil((n_open + n_closed) / 256)
-  int pad;
+  int tmode;            // its sampling's tangent_mode
   int64_t open0, closed0;  // first open / closed curve
   int64_t gauss0, n_gauss; // first Gaussian and count
   int64_t pix0;            // first pixel

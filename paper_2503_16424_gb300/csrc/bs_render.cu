@@ -880,7 +880,9 @@ __global__ void __launch_bounds__(Geo<kT>::kThreads, bwd_min_blocks<kT>()) batch
 //   d/dM = -2 ln2 sum dq t d^T = -2 ln2 Tm M^-T = -(2 ln2 / k) Tm D^-1 R^T,
 //   A1 = k isx ux, B1 = k isx uy, A2 = -k isy uy, B2 = k isy ux,
 //   d/do = s5 / o,   d/dcolour = s6..s8.   In place, one thread per Gaussian.
-__global__ void grads_from_sums_kernel(const float *__restrict__ gauss, float *__restrict__ dgauss, int64_t n) {
+// A non-finite gradient sets kDevErrNotFinite in the library status word.
+__global__ void grads_from_sums_kernel(const float *__restrict__ gauss, float *__restrict__ dgauss, int64_t n,
+                                       uint32_t *status) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
   const float4 *rec = reinterpret_cast<const float4 *>(gauss + g * BS_GAUSS_FLOATS);
@@ -899,10 +901,18 @@ __global__ void grads_from_sums_kernel(const float *__restrict__ gauss, float *_
   const float X10 = p10 * ux - p11 * uy, X11 = p10 * uy + p11 * ux;
   const float f = -c / kKappa;
   const float dA1 = f * X00, dB1 = f * X01, dA2 = f * X10, dB2 = f * X11;
-  d[0] = make_float4(c * (A1 * T1 + A2 * T2), c * (B1 * T1 + B2 * T2),
-                     kKappa * (isx * dA1 + isy * dB2), kKappa * (isx * dB1 - isy * dA2));
-  d[1] = make_float4(kKappa * (ux * dA1 + uy * dB1), kKappa * (ux * dB2 - uy * dA2), o > 0.f ? S / o : 0.f, s1.z);
-  d[2] = make_float4(s1.w, s2.x, 0.f, 0.f);
+  const float4 o0 = make_float4(c * (A1 * T1 + A2 * T2), c * (B1 * T1 + B2 * T2),
+                                kKappa * (isx * dA1 + isy * dB2), kKappa * (isx * dB1 - isy * dA2));
+  const float4 o1 = make_float4(kKappa * (ux * dA1 + uy * dB1), kKappa * (ux * dB2 - uy * dA2), o > 0.f ? S / o : 0.f,
+                                s1.z);
+  const float4 o2 = make_float4(s1.w, s2.x, 0.f, 0.f);
+  d[0] = o0;
+  d[1] = o1;
+  d[2] = o2;
+  // 0 * x is 0 for a finite x and NaN otherwise
+  const float probe = 0.f * o0.x + 0.f * o0.y + 0.f * o0.z + 0.f * o0.w + 0.f * o1.x + 0.f * o1.y + 0.f * o1.z +
+                      0.f * o1.w + 0.f * o2.x + 0.f * o2.y;
+  if (probe != 0.f) atomicOr(status, kDevErrNotFinite);
 }
 
 // L2 loss and its gradient, float4 at a time; per-thread float partial sums
@@ -1017,7 +1027,9 @@ bs_status launch_render_bwd(const float *gauss, int64_t n_gauss, const bs_canvas
   BS_BY_TILE(cv.tile, (bwd_plain<kT>(gauss, n_gauss, cv, gauss_mask(gbits), keys, rg, T_final, n_contrib, dL_dimg,
                                      dgauss, s)));
   BS_LAUNCHED("render_bwd_kernel");
-  grads_from_sums_kernel<<<(unsigned)div_up64(n_gauss, 256), 256, 0, s>>>(gauss, dgauss, n_gauss);
+  uint32_t *status = nullptr;
+  BS_TRY(lib_status_word(&status));
+  grads_from_sums_kernel<<<(unsigned)div_up64(n_gauss, 256), 256, 0, s>>>(gauss, dgauss, n_gauss, status);
   BS_LAUNCHED("grads_from_sums_kernel");
   return BS_OK;
 }
@@ -1125,7 +1137,9 @@ bs_status launch_batch_render_bwd(const BatchPlan &p, void *ws, const float *gau
   BS_BY_TILE(p.tile, BS_TRY((bwd_batch<kT>(p, ws, gauss, vals, rg, T_final, n_contrib, dimg, dgauss, s))));
   BS_LAUNCHED("batch_render_bwd_kernel");
   if (p.n_gauss > 0) {
-    grads_from_sums_kernel<<<(unsigned)div_up64(p.n_gauss, 256), 256, 0, s>>>(gauss, dgauss, p.n_gauss);
+    uint32_t *status = nullptr;
+    BS_TRY(lib_status_word(&status));
+    grads_from_sums_kernel<<<(unsigned)div_up64(p.n_gauss, 256), 256, 0, s>>>(gauss, dgauss, p.n_gauss, status);
     BS_LAUNCHED("grads_from_sums_kernel");
   }
   return BS_OK;

@@ -56,13 +56,13 @@ def arrays(case: Case):
     return a
 
 
-def ocfg(case: Case):
-    return OCfg(g_open=case.g_open, rows_closed=case.rows, k_closed=case.kc)
+def ocfg(case: Case, tangent_mode: int = 0):
+    return OCfg(g_open=case.g_open, rows_closed=case.rows, k_closed=case.kc, tangent_mode=tangent_mode)
 
 
-def oracle_table(case: Case, arr=None):
+def oracle_table(case: Case, arr=None, tangent_mode: int = 0):
     arr = arr if arr is not None else arrays(case)
-    cfg = ocfg(case)
+    cfg = ocfg(case, tangent_mode)
     rank, first = oracle.draw_order(arr["open_ctrl"], arr["open_width"], arr["closed_ctrl"], cfg)
     tab = oracle.gaussian_table(as_curves(arr), cfg, first)
     return tab, rank, first

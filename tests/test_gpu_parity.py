@@ -37,8 +37,8 @@ def _gpu_curves(bs, arr):
     return bs.CurveSet.from_arrays(arr, device="cuda")
 
 
-def _cfg(bs, case):
-    return bs.SampleCfg(g_open=case.g_open, rows_closed=case.rows, k_closed=case.kc)
+def _cfg(bs, case, tangent_mode=0):
+    return bs.SampleCfg(g_open=case.g_open, rows_closed=case.rows, k_closed=case.kc, tangent_mode=tangent_mode)
 
 
 def _canvas(bs, case):
@@ -55,14 +55,17 @@ def test_curve_order_bit_exact(bs, name):
     assert np.array_equal(first.cpu().numpy(), o_first)
 
 
+@pytest.mark.parametrize("tmode", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
-def test_sample_matches_oracle(bs, name):
+def test_sample_matches_oracle(bs, name, tmode):
+    """Both rotations: Eq. 8's neighbour difference (tangent_mode 0) and the
+    derivative B'(t) (tangent_mode 1)."""
     case = CASES[name]
     arr = arrays(case)
     curves = _gpu_curves(bs, arr)
-    _, first = bs.curve_order(curves, _cfg(bs, case))
-    gauss = bs.sample_curves(curves, _cfg(bs, case), first).cpu().numpy().astype(np.float64)
-    tab, _, _ = oracle_table(case, arr)
+    _, first = bs.curve_order(curves, _cfg(bs, case, tmode))
+    gauss = bs.sample_curves(curves, _cfg(bs, case, tmode), first).cpu().numpy().astype(np.float64)
+    tab, _, _ = oracle_table(case, arr, tmode)
     ref = table_to_f32(tab).astype(np.float64)
     ref64 = np.stack([tab[k].detach().numpy() for k in ("mx", "my", "ux", "uy", "isx", "isy")], 1)
     # positions relative to the canvas size, the rest relative to 1 (the
@@ -195,11 +198,12 @@ def test_render_bwd_matches_oracle(bs, name):
     assert torch.all(got[:, 10:] == 0)
 
 
+@pytest.mark.parametrize("tmode", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
-def test_sample_bwd_matches_oracle(bs, name):
+def test_sample_bwd_matches_oracle(bs, name, tmode):
     case = CASES[name]
     arr = arrays(case)
-    tab, _, first = oracle_table(case, arr)
+    tab, _, first = oracle_table(case, arr, tmode)
     rng = np.random.default_rng(case.seed)
     n = tab["mx"].shape[0]
     dg = np.zeros((n, 12), dtype=np.float32)
@@ -208,9 +212,10 @@ def test_sample_bwd_matches_oracle(bs, name):
     dtab = dict(mx=dg[:, 0], my=dg[:, 1], ux=dg[:, 2], uy=dg[:, 3], isx=dg[:, 4], isy=dg[:, 5], o=dg[:, 6],
                 col=dg[:, 7:10])
     dtab = {k: torch.as_tensor(v.astype(np.float64)) for k, v in dtab.items()}
-    ref = sample_vjp(as_curves(arr), ocfg(case), dtab, first)
+    ref = sample_vjp(as_curves(arr), ocfg(case, tmode), dtab, first)
     curves = _gpu_curves(bs, arr)
-    grad = bs.sample_curves_bwd(curves, _cfg(bs, case), torch.as_tensor(first.astype(np.int32), device="cuda"),
+    grad = bs.sample_curves_bwd(curves, _cfg(bs, case, tmode),
+                                torch.as_tensor(first.astype(np.int32), device="cuda"),
                                 torch.as_tensor(dg, device="cuda"))
     errs = {k: grad_rel_err(getattr(grad, k).cpu(), ref[k]) for k in
             ("open_ctrl", "open_width", "open_color", "open_opac", "closed_ctrl", "closed_color", "closed_opac")}

@@ -22,21 +22,22 @@ def bs():
     return _bs
 
 
-def _setup(bs, W, H, arr, g_open, rows, kc, bg=(0.0, 0.0, 0.0)):
+def _setup(bs, W, H, arr, g_open, rows, kc, bg=(0.0, 0.0, 0.0), tangent_mode=0):
     from paper_2503_16424_gb300.raster import Rasterizer
-    cfg = bs.SampleCfg(g_open=g_open, rows_closed=rows, k_closed=kc)
+    cfg = bs.SampleCfg(g_open=g_open, rows_closed=rows, k_closed=kc, tangent_mode=tangent_mode)
     curves = bs.CurveSet.from_arrays(arr, device="cuda")
     r = Rasterizer(bs.Canvas(W, H, 16, bg), cfg, curves.n_open, curves.n_closed, pair_capacity=2048)
     return cfg, curves, r
 
 
-@pytest.mark.parametrize("seed,W,H,no,nc", [(5, 64, 48, 6, 3), (6, 96, 80, 10, 5)])
-def test_step_matches_oracle_and_fd(bs, seed, W, H, no, nc):
+@pytest.mark.parametrize("seed,W,H,no,nc,tmode", [(5, 64, 48, 6, 3, 0), (6, 96, 80, 10, 5, 0),
+                                                   (7, 80, 64, 8, 4, 1)])
+def test_step_matches_oracle_and_fd(bs, seed, W, H, no, nc, tmode):
     bg = (0.1, 0.2, 0.3)
     arr = synth.make_curves(seed, W, H, no, nc, style="local").as_dict()
     g_open, rows, kc = 10, 4, 6
-    cfg, curves, r = _setup(bs, W, H, arr, g_open, rows, kc, bg)
-    ocfg = OCfg(g_open=g_open, rows_closed=rows, k_closed=kc)
+    cfg, curves, r = _setup(bs, W, H, arr, g_open, rows, kc, bg, tangent_mode=tmode)
+    ocfg = OCfg(g_open=g_open, rows_closed=rows, k_closed=kc, tangent_mode=tmode)
     tgt_np = synth.procedural_target(seed, W, H, 6)
     tgt = torch.as_tensor(tgt_np, device="cuda")
     img = r.forward(curves)
