@@ -135,3 +135,134 @@ def test_full_backward_crop(problem):
           "; of the bar: " + ", ".join(f"{k} {v:.2f}" for k, v in ratio.items()))
     for k, e in ratio.items():
         assert e <= 1.0, k
+
+
+def test_full_crop_curve_gradients_match_finite_differences(problem):
+    """The 2048 x 2048 workload's curve gradients of an L2 loss on the 32 x 32
+    crop at (1008, 1008), against fp64 central differences of the oracle's
+    crop loss: the perturbed curve is re-sampled by the oracle, every other
+    Gaussian that reaches the crop is the GPU's record, and the crop is
+    blended by brute force in draw order.  Pixels with a threshold decision
+    within 1e-4 (a kink of the blend) are masked on both sides.  Bar: 1e-3
+    relative (floor 1e-6 max|g|) plus the entry's float32 rounding bound plus
+    the difference quotient's own error, estimated from a second step."""
+    from oracle.bounds import blend_abs, sample_abs_vjp
+    from tests.gpu_cases import DEPTH, U32, tiles_per_gaussian
+    p = problem
+    bs, r, w, arr = p["bs"], p["r"], p["w"], p["arr"]
+    r.forward(p["curves"])
+    rec = r.gauss.cpu().numpy()
+    first = r.first.cpu().numpy().astype(np.int64)
+    n_open, per_open, per_closed = w["n_open"], w["g_open"], w["rows_closed"] * w["k_closed"]
+    ocfg = OCfg(g_open=w["g_open"], rows_closed=w["rows_closed"], k_closed=w["k_closed"])
+    x0 = y0 = 1008
+    side = 32
+    yy, xx = torch.meshgrid(torch.arange(y0, y0 + side, dtype=torch.float64),
+                            torch.arange(x0, x0 + side, dtype=torch.float64), indexing="ij")
+    xs, ys = xx.reshape(-1), yy.reshape(-1)
+    tgt = synth.procedural_target(w["seed"] + 1, 2048, 2048, w["n_shapes"])
+    t_crop = torch.as_tensor(tgt[:, y0:y0 + side, x0:x0 + side]).permute(1, 2, 0).reshape(-1, 3).double()
+    tab = table_from_f32(rec)
+    ex, ey = tab["ext_x"], tab["ext_y"]
+    near = ((ex >= 0) & (tab["mx"] + ex >= x0 + 0.5) & (tab["mx"] - ex <= x0 + side - 0.5)
+            & (tab["my"] + ey >= y0 + 0.5) & (tab["my"] - ey <= y0 + side - 0.5)).numpy()
+    # the curve owning each Gaussian (curves are draw-ordered runs from first)
+    order = np.argsort(first)
+    owner = np.empty(rec.shape[0], np.int64)
+    for c in order:
+        n = per_open if c < n_open else per_closed
+        owner[first[c]:first[c] + n] = c
+    counts = np.bincount(owner[near], minlength=first.shape[0])
+    opens = [int(c) for c in np.argsort(-counts[:n_open])[:2] if counts[c] > 0]
+    closeds = [int(c) + n_open for c in np.argsort(-counts[n_open:])[:2] if counts[c + n_open] > 0]
+    chosen = opens + closeds
+    assert len(chosen) == 4
+    rows = {c: np.arange(first[c], first[c] + (per_open if c < n_open else per_closed)) for c in chosen}
+    sub_idx = np.unique(np.concatenate([np.nonzero(near)[0]] + list(rows.values())))
+    pos = {g: i for i, g in enumerate(sub_idx)}
+    sub = {k: v[torch.as_tensor(sub_idx)] for k, v in tab.items()}
+    mask = ~oracle.render_pixels(sub, xs, ys, margin=1e-4)["flag"]
+    img = r.img[:, y0:y0 + side, x0:x0 + side].cpu().double().permute(1, 2, 0).reshape(-1, 3)
+    n_crop = 3 * side * side
+    dC = (2.0 * (img - t_crop) / n_crop) * mask[:, None].double()
+    dimg = torch.zeros(3, 2048, 2048, dtype=torch.float32)
+    dimg[:, y0:y0 + side, x0:x0 + side] = dC.float().reshape(side, side, 3).permute(2, 0, 1)
+    grad = r.backward(p["curves"], dimg.cuda())
+
+    def one_curve(c, a):
+        """The oracle's records of curve c of the arrays a, alone."""
+        one = {k: v[c:c + 1] if k.startswith("open") else v[:0] for k, v in a.items() if k.startswith("open")}
+        one.update({k: (v[c - n_open:c - n_open + 1] if c >= n_open else v[:0]) for k, v in a.items()
+                    if k.startswith("closed")})
+        if c < n_open:
+            one.update({k: v[:0] for k, v in a.items() if k.startswith("closed")})
+        with torch.no_grad():
+            return oracle.gaussian_table(as_curves(one), ocfg, np.array([0]))
+
+    def crop_loss(c, a):
+        t1 = one_curve(c, a)
+        s = {k: v.clone() for k, v in sub.items()}
+        ix = torch.as_tensor([pos[g] for g in rows[c]])
+        for k in ("mx", "my", "ux", "uy", "isx", "isy", "o", "col"):
+            s[k][ix] = t1[k]
+        C = oracle.render_pixels(s, xs, ys)["C"]
+        d = (C - t_crop) * mask[:, None].double()
+        return float((d * d).sum()) / n_crop
+
+    loss0 = float(((img - t_crop) ** 2 * mask[:, None].double()).sum()) / n_crop
+    keys0 = oracle.area_keys_f32(arr["open_ctrl"], arr["open_width"], arr["closed_ctrl"])
+    in_crop = np.unique(owner[near])
+
+    def central(c, k, i, h):
+        vals = []
+        for sgn in (1.0, -1.0):
+            a = {kk: np.array(v, dtype=np.float64) for kk, v in arr.items()}
+            row = c if k.startswith("open") else c - n_open
+            a[k].reshape(a[k].shape[0], -1)[row, i] += sgn * h
+            keys = oracle.area_keys_f32(a["open_ctrl"].astype(np.float32), a["open_width"].astype(np.float32),
+                                        a["closed_ctrl"].astype(np.float32))
+            # the draw order among the curves reaching the crop is unchanged
+            assert np.array_equal(np.argsort(keys[in_crop], kind="stable"), np.argsort(keys0[in_crop], kind="stable"))
+            vals.append(crop_loss(c, a))
+        return (vals[0] - vals[1]) / (2 * h)
+
+    # the float32 rounding bound of the chosen curves' gradients
+    A = blend_abs(sub, xs, ys, dC)
+    dtab = oracle.render_grads(sub, xs, ys, dC)
+    ntile = tiles_per_gaussian(rec[sub_idx], 2048, 2048)
+    cf = (DEPTH + ntile) * U32
+    checked = 0
+    for c in chosen:
+        kind = "open" if c < n_open else "closed"
+        ix = torch.as_tensor([pos[g] for g in rows[c]])
+        one = {k: v[c:c + 1] for k, v in arr.items() if k.startswith("open")} if kind == "open" else \
+            {k: v[c - n_open:c - n_open + 1] for k, v in arr.items() if k.startswith("closed")}
+        other = "closed" if kind == "open" else "open"
+        one.update({k: v[:0] for k, v in arr.items() if k.startswith(other)})
+        gb = {k: (cf[ix][:, None] * A[k][ix] if A[k].dim() == 2 else cf[ix] * A[k][ix]) for k in A}
+        dtab_c = {k: v[ix] for k, v in dtab.items()}
+        scale = {k: gb[k] + DEPTH * U32 * dtab_c[k].abs() for k in gb}
+        bound = sample_abs_vjp(as_curves(one), ocfg, scale, np.array([0]))
+        # the two control coordinates with the largest gradient, and the attributes
+        ck = kind + "_ctrl"
+        gc = getattr(grad, ck).cpu().double()[c if kind == "open" else c - n_open].reshape(-1)
+        top = [int(i) for i in torch.argsort(gc.abs(), descending=True)[:2]]
+        params = [(ck, top[0]), (ck, top[1])] + ([("open_width", 0), ("open_color", 1)] if kind == "open"
+                                                 else [("closed_color", 2), ("closed_opac", 0)])
+        for k, i in params:
+            row = c if kind == "open" else c - n_open
+            g_all = getattr(grad, k).cpu().double()
+            g = float(g_all[row].reshape(-1)[i])
+            gmax = float(g_all.abs().max())
+            base = float(np.asarray(arr[k])[row].reshape(-1)[i])
+            # px for positions: small enough that no unmasked threshold decision moves across
+            h = 1e-5 if k.endswith("ctrl") else 1e-5 * max(1.0, abs(base))
+            fd, fd2 = central(c, k, i, h), central(c, k, i, 2 * h)
+            b = float(bound[k][0].reshape(-1)[i])
+            # the quotient's own error: truncation (from the second step) and the
+            # fp64 rounding of the two crop losses (64 eps |L| each, over 2h)
+            allow = 1e-3 * max(abs(fd), 1e-6 * gmax) + b + abs(fd - fd2) / 3 + 64 * 2.2e-16 * loss0 / h
+            print(f"crop FD: curve {c} {k}[{i}]: gpu {g:.6e} fd {fd:.6e} (2h {fd2:.6e}), allowance {allow:.2e}")
+            assert abs(g - fd) <= allow, (c, k, i, g, fd, fd2)
+            checked += 1
+    assert checked == 16
