@@ -3,27 +3,34 @@
 One step = the whole hot path over one synthetic problem:
   curve order -> sample Gaussians -> bin (count, emit, radix sort, ranges)
   -> blend forward with the L2 loss gradient (one kernel) -> blend backward
-  -> sampling backward.
+  -> sampling backward,
+captured as one CUDA graph (the binning reads nothing back) and replayed.
 Workload (default): 2048x2048 RGB target, 2048 open + 2048 closed cubic
 curves, 64 Gaussians per curve (262,144 Gaussians), 16x16 tiles.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
-bounded sample of the same workload.  Under torchrun every rank runs an
-independent replica (the single-image path has no exchange step).
+bounded sample of the same workload.  Under torchrun the ranks optimise
+independent images (rank r's curves and target from seed + r; the images
+share nothing, so there is no collective in the data path) and the batch of
+the "batched" object is split across the ranks by pixel count.
 
 The line's "batched" object measures the other half of the metric: 64
 ragged images (sides 256..2048, 128..4096 curves each) optimised together,
 sampling and tile side autotuned, one CUDA-graph replay per Adam step of
-every image, against the same optimisation image by image through the
-single-canvas calls, and the PSNR both reach after the same steps.
+every image, against the same optimisation image by image (one graph replay
+per image), both run for the same steps from the same curves: ms per step,
+the PSNR curves, and the steps and wall-clock the batch needs to reach the
+plain arm's final PSNR.
 """
 
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
 import time
@@ -37,20 +44,58 @@ if ROOT not in sys.path:
 WORKLOAD = "hires_2048_4096"
 METRIC = "fwd+bwd raster steps/s at 2048² (4096 curves); batched vs plain, same PSNR"
 UNIT = "steps/s"
-FP32_FLOP_PER_FWD_EVAL = 22     # per (pixel, list entry) evaluation, forward
-FP32_FLOP_PER_BWD_EVAL = 55     # per (pixel, list entry) evaluation, backward
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of one launch of each render kernel on this
-# workload, from one ncu capture of the current kernel
-# (profiles/render_bwd_kernel_hires_2048_4096.md, render_fwd_kernel_hires_2048_4096.md); None where no capture of
-# the current kernel exists.
-DRAM_BYTES_PER_LAUNCH = {"render_bwd_kernel": 131352832, "render_fwd_kernel": 180358912}
+RENDER_SOURCE = os.path.join(ROOT, "paper_2503_16424_gb300", "csrc", "bs_render.cu")
+
+# Per (pixel, list entry) evaluation E of each blend kernel (E: the entries
+# up to each pixel's stop point; the backward: up to its last blended
+# entry), the FP32 floating-point operations the code issues and its MUFU
+# operations: ncu's per-opcode thread-instruction counters of one launch on
+# this workload (FFMA counted 2, FADD and FMUL 1, FFMA2/FADD2/FMUL2 twice
+# that; MUFU = XU-pipe thread instructions), divided by that launch's E.
+# Each entry holds the counters of one capture, the E it was divided by, and
+# the 16-hex-digit SHA-256 prefix of the kernel source it was taken on; when
+# the source has changed since, the figures are reported as stale (null).
+# The instruction counts come from a quarter of the workload (1024 x 1024,
+# 512 + 512 curves, the same sampling; a capture of several passes), and
+# carry over per evaluation; the DRAM bytes (read + write, one launch) from a
+# one-pass capture of the full workload.
+NCU_CAPTURE = {
+    "source_sha256_16": "a84be228cd0d7afb",
+    "workload": "hires_1024_1024",
+    "render_fwd_kernel": {"flop_per_eval": 10.5012, "mufu_per_eval": 0.7677,
+                          "ffma": 636433010, "fadd": 201107114, "fmul": 252587454, "xu": 126225312,
+                          "evals": 164415548, "dram_bytes": 179508736,
+                          "pipes": {"issue_active_pct": 73.3, "fma_pipe_pct": 35.5, "alu_pipe_pct": 40.8,
+                                    "shared_pipe_pct": 17.5, "warps_active_pct": 38.4}},
+    "render_bwd_kernel": {"flop_per_eval": 22.6996, "mufu_per_eval": 1.0985,
+                          "ffma": 1094764262, "fadd": 832285333, "fmul": 641605485, "xu": 177279424,
+                          "evals": 161386727, "dram_bytes": 127796224,
+                          "pipes": {"issue_active_pct": 69.8, "fma_pipe_pct": 35.3, "alu_pipe_pct": 40.1,
+                                    "shared_pipe_pct": 34.2, "warps_active_pct": 30.8}},
+}
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    """FMA = 2 FLOP on 128 FP32 lanes per SM."""
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz: float, n_sm: int = 152) -> float:
+    """FP32 peak: n_sm SMs x 128 lanes x 2 FLOP (an FMA) x the SM clock."""
+    return n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def set_workload(name: str):
+    global WORKLOAD
+    from paper_2503_16424_gb300 import synth
+    if name not in synth.WORKLOADS:
+        raise SystemExit(f"unknown workload {name}; one of {sorted(synth.WORKLOADS)}")
+    WORKLOAD = name
+
+
+def render_source_hash() -> str:
+    with open(RENDER_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def capture_current() -> bool:
+    return NCU_CAPTURE["source_sha256_16"] is not None and NCU_CAPTURE["source_sha256_16"] == render_source_hash()
 
 
 def load_peaks():
@@ -59,6 +104,27 @@ def load_peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def host_cpu() -> dict:
+    """The host's core count and CPU model (lscpu's "Model name", else
+    /proc/cpuinfo, else platform)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model and os.path.exists("/proc/cpuinfo"):
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine()}
 
 
 class ClockSampler:
@@ -123,64 +189,68 @@ def max_over_ranks(x: float, world: int, device) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, world: int, device) -> float:
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
 def job_throughput(world: int, steps: int, ms: float) -> float:
-    """Steps of all replicas per second of the slowest rank's clock."""
+    """Steps of all ranks per second of the slowest rank's clock."""
     return world * steps / (ms / 1e3)
 
 
-def make_problem(device):
-    import torch
-    from paper_2503_16424_gb300 import bs, synth
+def workload_inputs(seed_offset: int = 0):
+    """The workload's curves and target (seeded; synth only, so that the
+    oracle arm never loads the library)."""
+    from paper_2503_16424_gb300 import synth
     w = synth.WORKLOADS[WORKLOAD]
-    arrays = synth.make_curves(w["seed"], w["W"], w["H"], w["n_open"], w["n_closed"], style=w["style"]).as_dict()
-    target = synth.procedural_target(w["seed"] + 1, w["W"], w["H"], w["n_shapes"])
-    cfg = bs.SampleCfg(g_open=w["g_open"], rows_closed=w["rows_closed"], k_closed=w["k_closed"])
-    canvas = bs.Canvas(w["W"], w["H"], w["tile"])
-    return w, arrays, target, cfg, canvas
+    seed = w["seed"] + 100 * seed_offset
+    arrays = synth.make_curves(seed, w["W"], w["H"], w["n_open"], w["n_closed"], style=w["style"]).as_dict()
+    target = synth.procedural_target(seed + 1, w["W"], w["H"], w.get("n_shapes", 40))
+    return w, arrays, target
+
+
+def workload_config(w, n_pairs, world):
+    return {"workload": WORKLOAD, "W": w["W"], "H": w["H"], "n_open": w["n_open"], "n_closed": w["n_closed"],
+            "gaussians_per_curve": w["g_open"],
+            "n_gaussians": w["n_open"] * w["g_open"] + w["n_closed"] * w["rows_closed"] * w["k_closed"],
+            "tile": w["tile"], "n_pairs": n_pairs, "curve_init": w["style"],
+            "l2": "working set larger than L2 (no flush)",
+            "parallelism": "1 GPU" if world == 1 else f"independent images x{world}"}
 
 
 def run_ours(args, rank, world):
     import torch
     from paper_2503_16424_gb300 import bs
-    from paper_2503_16424_gb300.raster import Rasterizer
+    from paper_2503_16424_gb300.raster import Rasterizer, StepGraph
 
     local = int(os.environ.get("LOCAL_RANK", 0))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w, arrays, target_np, cfg, canvas = make_problem(dev)
+    w, arrays, target_np = workload_inputs(rank)
+    cfg = bs.SampleCfg(g_open=w["g_open"], rows_closed=w["rows_closed"], k_closed=w["k_closed"])
+    canvas = bs.Canvas(w["W"], w["H"], w["tile"])
     curves = bs.CurveSet.from_arrays(arrays, device=dev)
     target = torch.as_tensor(target_np, device=dev)
     r = Rasterizer(canvas, cfg, curves.n_open, curves.n_closed, device=dev, pair_capacity=1 << 25)
     grad = curves.zeros_like()
     stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
 
-    def mk():
-        return torch.cuda.Event(enable_timing=True)
-    ev = [[mk() for _ in range(4)] for _ in range(args.steps)]
-
-    def step(e=None, cv=curves, tg=target, gr=grad):
-        # forward: order, sample, bin, blend
-        r.rank, r.first = bs.curve_order(cv, cfg)
-        bs.sample_curves(cv, cfg, r.first, out=r.gauss)
-        r.binning.run(r.gauss)
-        if e:
-            e[0].record(stream)
-        # blend forward with the L2 loss and its gradient in the same pass
-        bs.render_fwd_l2(r.gauss, canvas, r.binning, tg, out=(r.img, r.T, r.nc), dimg=r.dimg, loss=r.loss)
-        if e:
-            e[1].record(stream)
-            e[2].record(stream)
-        bs.render_bwd(r.gauss, canvas, r.binning, r.T, r.nc, r.dimg, r.dgauss)
-        if e:
-            e[3].record(stream)
-        bs.sample_curves_bwd(cv, cfg, r.first, r.dgauss, gr)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    # work counters of this problem (untimed)
-    stats = bs.render_stats(r.gauss, canvas, r.binning)
-    n_pairs = r.binning.n_pairs
+    # the step as one graph: the first call runs eagerly and sizes the pair
+    # capacity, the second captures, the others replay
+    sg = StepGraph(r, curves, target, grad)
+    for _ in range(max(3, args.warmup)):
+        sg()
+    st, n_pairs = sg.check()
+    if st != bs.BS_OK:
+        raise RuntimeError(f"binning status {st} after the warm-up")
+    stats = bs.render_stats(r.gauss, canvas, r.binning)     # work counters of this problem (untimed)
 
     if world > 1:
         torch.distributed.barrier()
@@ -189,31 +259,59 @@ def run_ours(args, rank, world):
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        for i in range(args.steps):
-            step(ev[i])
+        for _ in range(args.steps):
+            sg()
         t1.record(stream)
         torch.cuda.synchronize()
-    fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    bwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    st, _ = sg.check()
+    if st != bs.BS_OK:
+        raise RuntimeError(f"binning status {st} in the timed region")
     ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     if world > 1:
         torch.distributed.barrier()
     ms_per_step = ms / args.steps
     value = job_throughput(world, args.steps, ms)
 
+    # the blend kernels' own durations, for the roofline: the same steps run
+    # eagerly with CUDA events around the two kernels on their stream
+    def mk():
+        return torch.cuda.Event(enable_timing=True)
+    ev = [[mk() for _ in range(4)] for _ in range(args.steps)]
+    for i in range(args.steps):
+        e = ev[i]
+        bs.curve_order(curves, cfg, out=(r.rank, r.first))
+        bs.sample_curves(curves, cfg, r.first, out=r.gauss)
+        r.binning.run(r.gauss)
+        e[0].record(stream)
+        bs.render_fwd_l2(r.gauss, canvas, r.binning, target, out=(r.img, r.T, r.nc), dimg=r.dimg, loss=r.loss)
+        e[1].record(stream)
+        e[2].record(stream)
+        bs.render_bwd(r.gauss, canvas, r.binning, r.T, r.nc, r.dimg, r.dgauss)
+        e[3].record(stream)
+        bs.sample_curves_bwd(curves, cfg, r.first, r.dgauss, grad)
+    torch.cuda.synchronize()
+    fwd_avg = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    bwd_avg = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
+
     # end to end through the public API with host buffers: every step copies
     # its inputs (curves + target) from pinned memory and reads its loss and
-    # gradients back.  Two device buffer sets and a copy stream: step i+1's
-    # inputs go up while step i computes, step i's results come down after
-    # it; every copy of every step is inside the timed region.
+    # gradients back.  Two device buffer sets, each with its own captured
+    # step, and a copy stream: step i+1's inputs go up while step i computes,
+    # step i's results come down after it; every copy of every step is inside
+    # the timed region.
     host_in = {k: torch.as_tensor(v).pin_memory() for k, v in arrays.items()}
     host_target = torch.as_tensor(target_np).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in host_in.values()) + host_target.numel() * 4
     d2h = sum(getattr(grad, k).numel() * getattr(grad, k).element_size() for k in bs.CURVE_FIELDS) + 8
     bufs = []
     for _ in range(2):
-        cv = bs.CurveSet(**{k: torch.empty_like(getattr(curves, k)) for k in bs.CURVE_FIELDS})
-        bufs.append({"cv": cv, "tg": torch.empty_like(target), "gr": curves.zeros_like(),
+        cv = bs.CurveSet(**{k: getattr(curves, k).clone() for k in bs.CURVE_FIELDS})
+        tg = target.clone()
+        gr = curves.zeros_like()
+        g = StepGraph(r, cv, tg, gr)
+        g()
+        g()
+        bufs.append({"cv": cv, "tg": tg, "gr": gr, "sg": g,
                      "out": {k: torch.empty_like(getattr(grad, k), device="cpu").pin_memory()
                              for k in bs.CURVE_FIELDS},
                      "loss": torch.empty((), dtype=torch.float64).pin_memory(),
@@ -240,7 +338,7 @@ def run_ours(args, rank, world):
                 upload(bufs[(i + 1) % 2])
             stream.wait_event(b["up"])
             stream.wait_event(b["down"])     # its gradients of two steps ago have been read back
-            step(cv=b["cv"], tg=b["tg"], gr=b["gr"])
+            b["sg"]()
             b["loss_dev"].copy_(r.loss)       # the next step rewrites r.loss
             b["done"].record(stream)
             with torch.cuda.stream(copy):
@@ -259,6 +357,9 @@ def run_ours(args, rank, world):
     run_e2e(args.steps)
     e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3, world, dev)
     e2e_value = job_throughput(world, args.steps, e_ms)
+    for b in bufs:
+        if b["sg"].check()[0] != bs.BS_OK:
+            raise RuntimeError("binning overflow in the end-to-end region")
     # same inputs as the device-timed steps: the same gradients up to the
     # order of the backward's atomic sums
     g_e2e, g_dev = bufs[(args.steps - 1) % 2]["out"]["open_ctrl"], grad.open_ctrl.cpu()
@@ -266,11 +367,11 @@ def run_ours(args, rank, world):
 
     # the periodic pass (every few hundred steps, outside the step): prune and
     # densify a copy of the curves against the last rendered image
-    pd_curves = bs.CurveSet(**{k: getattr(curves, k).clone() for k in bs.CURVE_FIELDS})
+    r.forward(curves)
     pd_cfg = bs.PDCfg(step=200, t_end=1000)
     pd_ms = []
     for i in range(3):
-        pd_work = bs.CurveSet(**{k: getattr(pd_curves, k).clone() for k in bs.CURVE_FIELDS})
+        pd_work = bs.CurveSet(**{k: getattr(curves, k).clone() for k in bs.CURVE_FIELDS})
         a, b = mk(), mk()
         a.record(stream)
         _, pd_stats = r.prune_densify(pd_work, target, pd_cfg)
@@ -281,36 +382,16 @@ def run_ours(args, rank, world):
 
     peaks, src = load_peaks()
     clocks = clk.summary()
-    fwd_avg, bwd_avg = float(np.mean(fwd_ms)), float(np.mean(bwd_ms))
-    # E per pass: (pixel, list entry) pairs up to each pixel's stop point
-    # (forward: the entry that stops it or the list's end; backward: its
-    # last blended entry), whatever the kernels skip inside a list
     e_fwd, e_bwd = stats["visits"], stats["n_contrib_sum"]
-    fwd_tf = FP32_FLOP_PER_FWD_EVAL * e_fwd / (fwd_avg * 1e-3) / 1e12
-    bwd_tf = FP32_FLOP_PER_BWD_EVAL * e_bwd / (bwd_avg * 1e-3) / 1e12
-    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-    if bwd_avg >= fwd_avg:
-        dom, ach = "render_bwd_kernel", bwd_tf
-    else:
-        dom, ach = "render_fwd_kernel", fwd_tf
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "W": w["W"], "H": w["H"], "n_open": w["n_open"],
-                   "n_closed": w["n_closed"], "gaussians_per_curve": w["g_open"],
-                   "n_gaussians": r.n_gauss, "tile": w["tile"], "n_pairs": n_pairs,
-                   "curve_init": w["style"], "l2": "working set larger than L2 (no flush)",
-                   "parallelism": f"replicas{world}"},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": round(ach, 3),
-                     "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-                     "traffic": DRAM_BYTES_PER_LAUNCH.get(dom),
-                     "peak_source": f"FP32 {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                                    f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)"},
+        "config": dict(workload_config(w, n_pairs, world), step="one CUDA graph replay"),
+        "roofline": roofline(fwd_avg, bwd_avg, e_fwd, e_bwd, n_sm, peaks, src),
         "kernels_ms": {"render_fwd": round(fwd_avg, 4), "render_bwd": round(bwd_avg, 4)},
         "work": {"fwd_evals": e_fwd, "bwd_evals": e_bwd, "fwd_evals_performed": stats["evals"],
-                 "blended": stats["blended"],
-                 "fwd_tflops": round(fwd_tf, 3), "bwd_tflops": round(bwd_tf, 3)},
+                 "blended": stats["blended"]},
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": None,
@@ -330,11 +411,40 @@ def run_ours(args, rank, world):
     per_step = 2 + 1 + (6 + 3 * passes - 1 + (0 if fused and passes <= 2 else 2)) + 1 + 2 + 1
     out["gpu_launches"] = per_step * args.steps
     if not args.no_batched:
-        out["batched"] = run_batched(dev, args)
+        out["batched"] = run_batched(dev, args, rank, world)
     if not args.no_paper_shape:
         out["paper_shape"] = run_paper_shape(dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(side=8)
+    return out
+
+
+def roofline(fwd_ms, bwd_ms, e_fwd, e_bwd, n_sm, peaks, src):
+    """The dominant blend kernel's FP32 rate against the FP32 peak (SMs x 128
+    lanes x 2 FLOP x the maximum SM clock), from the FLOP per evaluation the
+    code issues (ncu instruction counters of the current kernel source)."""
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_peak_tflops(mhz, n_sm)
+    dom, t, e = ("render_bwd_kernel", bwd_ms, e_bwd) if bwd_ms >= fwd_ms else ("render_fwd_kernel", fwd_ms, e_fwd)
+    fresh = capture_current()
+    cap = NCU_CAPTURE.get(dom) if fresh else None
+    out = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": round(peak, 2),
+           "peak_source": f"FP32: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {mhz} MHz ({src} max clock)",
+           "achieved": None, "frac": None, "traffic": None,
+           "flop_per_eval": None, "evals": e, "kernel_ms": round(t, 4),
+           "counters": "current" if fresh else "stale: the kernel source changed since the ncu capture"}
+    if cap:
+        ach = cap["flop_per_eval"] * e / (t * 1e-3) / 1e12
+        out.update(achieved=round(ach, 3), frac=round(ach / peak, 4), flop_per_eval=cap["flop_per_eval"],
+                   mufu_per_eval=cap.get("mufu_per_eval"), traffic=cap.get("dram_bytes"),
+                   algorithmic_bytes=cap.get("algorithmic_bytes"), pipes=cap.get("pipes"))
+        other = "render_fwd_kernel" if dom == "render_bwd_kernel" else "render_bwd_kernel"
+        oc = NCU_CAPTURE.get(other)
+        if oc:
+            ot, oe = (fwd_ms, e_fwd) if other == "render_fwd_kernel" else (bwd_ms, e_bwd)
+            oach = oc["flop_per_eval"] * oe / (ot * 1e-3) / 1e12
+            out["other_kernel"] = {"kernel": other, "achieved": round(oach, 3), "frac": round(oach / peak, 4),
+                                   "flop_per_eval": oc["flop_per_eval"], "kernel_ms": round(ot, 4)}
     return out
 
 
@@ -370,7 +480,7 @@ def run_paper_shape(dev, steps=10, warmup=3):
         for i in range(warmup + steps):
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record(stream)
-            r.rank, r.first = bs.curve_order(curves, cfg)
+            bs.curve_order(curves, cfg, out=(r.rank, r.first))
             bs.sample_curves(curves, cfg, r.first, out=r.gauss)
             r.binning.run(r.gauss)
             bs.render_fwd_l2(r.gauss, r.canvas, r.binning, target, out=(r.img, r.T, r.nc), dimg=r.dimg, loss=r.loss)
@@ -390,86 +500,98 @@ def run_paper_shape(dev, steps=10, warmup=3):
                                           "Table 4's resolution is not stated", "cases": out}
 
 
-def run_batched(dev, args):
-    """Batched vs plain on the ragged 64-image workload: ms per Adam step of
-    every image (graph replay vs the single-canvas calls image by image) and
-    the PSNR both reach after the same steps from the same curves."""
+def _mean_psnr(losses):
+    import torch
+    return float((-10.0 * torch.log10(losses.double())).mean())
+
+
+def run_batched(dev, args, rank, world):
+    """Batched vs plain on the ragged 64-image workload (this rank's share of
+    it under torchrun): both arms run the same Adam steps from the same
+    curves, the batch as one graph replay per step of every image, the plain
+    arm as one graph replay per image, both with pair capacity 1.5 x the
+    pairs found and the binning status read after every step outside the
+    timed window (an overflow is counted, and the capacity regrown).
+    Reported: ms per step of every image (timed over a window of replays
+    with no reads), the mean PSNR every `every` steps, and the steps and
+    wall-clock (steps x ms per step) the batch needs to reach the plain
+    arm's final mean PSNR."""
     import torch
     from paper_2503_16424_gb300 import autotune, bs, synth
-    from paper_2503_16424_gb300.batch import BatchOptimizer, BatchRasterizer, PlainOptimizer
+    from paper_2503_16424_gb300.batch import BatchOptimizer, BatchRasterizer, PlainOptimizer, partition_images
     W = synth.BATCH_WORKLOAD
-    layout = synth.batch_layout(W["seed"], W["n_images"], W["side"], W["aspect"], W["curves"])
+    layout_all = synth.batch_layout(W["seed"], W["n_images"], W["side"], W["aspect"], W["curves"])
+    mine = partition_images([e["W"] * e["H"] for e in layout_all], world)[rank]
+    layout = [layout_all[i] for i in mine]
     arrs, cat, targets = synth.batch_inputs(layout, W["n_shapes"])
     base = [bs.BatchImage(e["W"], e["H"], e["n_open"], e["n_closed"], bs.SampleCfg()) for e in layout]
     target = torch.as_tensor(np.concatenate([t.reshape(-1) for t in targets]), device=dev)
     images, tile, report = autotune.autotune(base, bs.CurveSet.from_arrays(cat, device=dev), target, arrs=arrs,
                                              device=dev)
-    # batched: graph replays after the eager first step and the capture
+    total, every, window = max(args.batched_steps, 25), 25, 20
+    stream = torch.cuda.current_stream()
+
+    def run(step_fn, losses_fn, check_fn):
+        """total steps; the ms per step over replays 3 .. 3 + window (no
+        reads inside); the mean PSNR after every `every` steps."""
+        curve, ms = [], None
+        for i in range(total):
+            if i == 3:
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            step_fn()
+            if i == 2 + window:
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / window
+            if not 3 <= i <= 2 + window:
+                check_fn()                           # a capacity overflow regrows and recaptures
+            if i == 0 or (i + 1) % every == 0:      # outside the window (every > 2 + window)
+                curve.append((i + 1, round(_mean_psnr(losses_fn()), 4)))
+        check_fn()
+        return curve, ms
+
+    # batched: the eager first step fits the capacity, then graph replays
     curves = bs.CurveSet.from_arrays(cat, device=dev)
     r = BatchRasterizer(images, tile=tile, pair_capacity=1 << 24, device=dev)
     opt = BatchOptimizer(r, curves, target, graph=True, check_every=0)
-    k_psnr = args.batched_steps
-    for _ in range(2):
-        opt.step()
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(k_psnr - 2):
-        opt.step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    b_curve, b_ms = run(opt.step, lambda: r.loss, opt.check)
     st, n_pairs = r.batch.status()
-    b_ms = e0.elapsed_time(e1) / (k_psnr - 2)
-    r.forward(curves, target)
-    p_batch = r.psnr(target)
-    # plain: the same steps image by image (one binning read-back per image)
+    b_overflows = opt.overflows
+    # plain: the same steps image by image, one graph replay per image
     per = [bs.CurveSet.from_arrays(a, device=dev) for a in arrs]
     tg = [torch.as_tensor(t, device=dev) for t in targets]
-    plain = PlainOptimizer(images, per, tg, device=dev, tile=tile)
-    for _ in range(2):
-        plain.step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(k_psnr - 2):
-        plain.step()
-    torch.cuda.synchronize()
-    p_ms = (time.perf_counter() - t0) * 1e3 / (k_psnr - 2)
-    p_plain = []
-    for (rr, cv, t, _, _) in plain.items:
-        img = rr.forward(cv)
-        p_plain.append(float(-10.0 * torch.log10(((img - t).double() ** 2).mean())))
+    plain = PlainOptimizer(images, per, tg, device=dev, tile=tile, graph=True, headroom=1.5)
+    p_curve, p_ms = run(plain.step, plain.losses, plain.check)
+    p_overflows = sum(g.overflows for g in plain.graphs)
+    p_final = p_curve[-1][1]
+    reach = next((s for s, p in b_curve if p >= p_final), None)
     n_img = len(images)
-    diff = [abs(a - b) for a, b in zip(p_batch, p_plain)]
+    # the job: every rank's images over the slowest rank's step
+    job_b_ms, job_p_ms = max_over_ranks(b_ms, world, dev), max_over_ranks(p_ms, world, dev)
+    job_imgs = sum_over_ranks(n_img, world, dev)
     passes = -(-max(1, (r.batch.n_tiles - 1).bit_length()) // 8)
-    # curves below 512 samples and the rest are sampled by separate launches
     sizes = [im.sample.g_open for im in images if im.n_open] + \
             [im.sample.rows_closed * im.sample.k_closed for im in images if im.n_closed]
     classes = len({n >= 512 for n in sizes})
     return {
-        "workload": W["name"], "images": n_img, "pixels": r.batch.n_pixels,
-        "curves": r.batch.n_open + r.batch.n_closed, "gaussians": r.batch.n_gauss, "pairs": n_pairs,
-        "binning_status": st, "autotune": report,
-        "ms_per_step": round(b_ms, 4), "image_steps_per_s": round(n_img * 1e3 / b_ms, 2),
-        "plain_ms_per_step": round(p_ms, 4), "plain_image_steps_per_s": round(n_img * 1e3 / p_ms, 2),
+        "workload": W["name"], "images": n_img, "images_all_ranks": int(job_imgs), "rank_images": mine,
+        "pixels": r.batch.n_pixels, "curves": r.batch.n_open + r.batch.n_closed, "gaussians": r.batch.n_gauss,
+        "pairs": n_pairs, "binning_status": st, "autotune": report,
+        "ms_per_step": round(b_ms, 4), "image_steps_per_s": round(job_imgs * 1e3 / job_b_ms, 2),
+        "plain_ms_per_step": round(p_ms, 4), "plain_image_steps_per_s": round(job_imgs * 1e3 / job_p_ms, 2),
         "speedup_vs_plain": round(p_ms / b_ms, 3),
-        "step": "draw order, sampling, binning, blend + L2, backward, Adam; batched = one CUDA graph replay",
+        "step": "draw order, sampling, binning, blend + L2, backward, Adam; batched = one CUDA graph replay "
+                "for every image, plain = one CUDA graph replay per image",
         "launches_per_step": 17 + 3 * passes + 2 * classes,
-        "psnr": {"steps": k_psnr, "batched_mean_db": round(float(np.mean(p_batch)), 4),
-                 "plain_mean_db": round(float(np.mean(p_plain)), 4),
-                 "max_abs_diff_db": round(float(max(diff)), 5)},
+        "psnr": {"steps": total, "every": every, "batched_curve_db": b_curve, "plain_curve_db": p_curve,
+                 "batched_final_db": b_curve[-1][1], "plain_final_db": p_final,
+                 "batched_steps_to_plain_final": reach,
+                 "batched_ms_to_plain_final": round(reach * b_ms, 2) if reach else None,
+                 "plain_ms_for_all_steps": round(total * p_ms, 2),
+                 "capacity_overflows": {"batched": b_overflows, "plain": p_overflows}},
     }
-
-
-_PROBLEM = {}
-
-
-def _oracle_problem():
-    """The workload's curves and target for the oracle (made once)."""
-    if not _PROBLEM:
-        w, arrays, target_np, _, _ = make_problem(None)
-        _PROBLEM.update(w=w, arrays=arrays, target=target_np)
-    return _PROBLEM
 
 
 def cpu_baseline(side=16):
@@ -481,8 +603,7 @@ def cpu_baseline(side=16):
     import oracle
     from oracle.curves import SampleCfg as OCfg
     from oracle.pipeline import as_curves, sample_vjp
-    pb = _oracle_problem()
-    w, arrays, target_np = pb["w"], pb["arrays"], pb["target"]
+    w, arrays, target_np = _oracle_problem()
     cfg = OCfg(g_open=w["g_open"], rows_closed=w["rows_closed"], k_closed=w["k_closed"])
     threads = torch.get_num_threads()
     t0 = time.perf_counter()
@@ -509,16 +630,46 @@ def cpu_baseline(side=16):
     frac = (side * side) / (w["W"] * w["H"])
     step_s = t_sample + t_vjp + t_pix / frac
     return {"value": round(1.0 / step_s, 9), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "extrapolated": True, "host": host_cpu(),
             "sample": f"sampling of all {w['n_open'] + w['n_closed']} curves, brute-force blend and its "
                       f"gradient at a {side}x{side} pixel crop ({side * side} of {w['W'] * w['H']} pixels, "
                       f"time extrapolated by pixel count), sampling backward of all curves",
             "seconds": round(time.perf_counter() - t0, 2)}
 
 
+_PROBLEM = {}
+
+
+def _oracle_problem():
+    """The workload's curves and target for the oracle (made once)."""
+    if not _PROBLEM:
+        w, arrays, target_np = workload_inputs(0)
+        _PROBLEM.update(w=w, arrays=arrays, target=target_np)
+    return _PROBLEM["w"], _PROBLEM["arrays"], _PROBLEM["target"]
+
+
+def oracle_pairs() -> int:
+    """The workload's (tile, Gaussian) pairs by the oracle's binning rule."""
+    import torch
+    import oracle
+    from oracle.curves import SampleCfg as OCfg, table_to_f32
+    from oracle.pipeline import as_curves
+    w, arrays, _ = _oracle_problem()
+    cfg = OCfg(g_open=w["g_open"], rows_closed=w["rows_closed"], k_closed=w["k_closed"])
+    _, first = oracle.draw_order(arrays["open_ctrl"], arrays["open_width"], arrays["closed_ctrl"], cfg)
+    with torch.no_grad():
+        rec = table_to_f32(oracle.gaussian_table(as_curves(arrays), cfg, first))
+    tx0, tx1, ty0, ty1, ok = oracle.tile_rects_f32(rec, w["W"], w["H"], w["tile"])
+    return int(np.where(ok, (tx1 - tx0 + 1) * (ty1 - ty0 + 1), 0).sum())
+
+
 def run_reference(args, rank):
+    """The oracle arm: the CPU oracle, as it stands, on the same workload and
+    metric; each step is the bounded sample of cpu_baseline, its time
+    extrapolated to the whole image.  It loads no part of the library."""
     if rank != 0:
         return None
-    _oracle_problem()
+    w, _, _ = _oracle_problem()
     for _ in range(max(1, args.warmup)):
         cpu_baseline(side=8)
     vals = []
@@ -527,15 +678,12 @@ def run_reference(args, rank):
         vals.append(cpu_baseline(side=8)["value"])
     total = time.perf_counter() - t0
     value = float(np.mean(vals))
-    w = _PROBLEM["w"]
     cb = cpu_baseline(side=8)
     cb["value"] = round(value, 9)
     return {"impl": "reference", "metric": METRIC, "value": round(value, 9), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / value, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "W": w["W"], "H": w["H"],
-                                            "n_open": w["n_open"], "n_closed": w["n_closed"],
-                                            "gaussians_per_curve": w["g_open"], "tile": w["tile"]},
+            "ms_per_step_extrapolated": True, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": workload_config(w, oracle_pairs(), 1),
             "cpu_baseline": cb, "wall_s": round(total, 2),
             "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -549,8 +697,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-paper-shape", action="store_true")
-    ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="synthetic single-canvas workload (another one than the default is for profiler captures)")
     args = ap.parse_args()
+    set_workload(args.workload)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -118,6 +118,24 @@ class BatchRasterizer:
         return out
 
 
+def partition_images(weights, world: int):
+    """The images each of `world` ranks optimises when a batch is split
+    across GPUs (independent images: no exchange between ranks).  Longest
+    processing time first: images by descending weight (pixel count; equal
+    weights by index) each go to the rank with the least weight so far (the
+    lowest rank on a tie).  Returns one ascending index list per rank."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(weights)), key=lambda i: (-weights[i], i))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += weights[i]
+    return [sorted(p) for p in parts]
+
+
 def _curve_scales(images, field_rows, device):
     """Per-curve control-point lr multipliers: half the longer side of the
     curve's image, for the open (field_rows = 'open') or closed curves."""
@@ -221,24 +239,43 @@ class BatchOptimizer:
 
 class PlainOptimizer:
     """The same optimisation image by image through the single-canvas calls
-    (bs_curve_order ... bs_render_bwd, then bs_adam_step per image)."""
+    (bs_curve_order ... bs_render_bwd, then bs_adam_step per image).  With
+    graph=True each image's step and Adam update is one CUDA-graph replay
+    (raster.StepGraph), so the comparison with the batch is not about host
+    launches."""
 
     def __init__(self, images, curves_per_image, targets, cfg: AdamCfg = None, device="cuda",
-                 pair_capacity: int = 1 << 20, tile: int = 16):
-        from .raster import Rasterizer
+                 pair_capacity: int = 1 << 20, tile: int = 16, graph: bool = False, headroom: float = 1.25):
+        from .raster import Rasterizer, StepGraph
         self.cfg = cfg or AdamCfg()
         self.items = []
+        self.graphs = []
         for im, cv, tg in zip(images, curves_per_image, targets):
             r = Rasterizer(bs.Canvas(im.width, im.height, tile, im.bg), im.sample, im.n_open, im.n_closed,
                            device=device, pair_capacity=pair_capacity)
             grad = cv.zeros_like()
             adam = CurveAdam(cv, grad, [im], self.cfg, device)
             self.items.append((r, cv, tg, grad, adam))
+            if graph:
+                self.graphs.append(StepGraph(r, cv, tg, grad, after=adam.step, headroom=headroom))
 
     def step(self):
+        if self.graphs:
+            for g in self.graphs:
+                g()
+            return
         for r, cv, tg, grad, adam in self.items:
             r.step(cv, tg, grad)
             adam.step()
+
+    def check(self):
+        """Read every image's binning status (synchronises); regrow where a
+        captured step overflowed."""
+        return [g.check() for g in self.graphs]
+
+    def losses(self):
+        """Each image's loss of its last step (device doubles)."""
+        return torch.stack([r.loss for r, *_ in self.items])
 
 
 def main():

@@ -259,6 +259,11 @@ WORKLOADS = {
     "hires_2048_4096": dict(W=2048, H=2048, n_open=2048, n_closed=2048, style="local",
                             g_open=64, rows_closed=8, k_closed=8, tile=16, seed=20,
                             n_shapes=200),
+    # a quarter of it (1024x1024, 512 + 512 curves, the same sampling): the
+    # small case of the kernels' profiler captures
+    "hires_1024_1024": dict(W=1024, H=1024, n_open=512, n_closed=512, style="local",
+                            g_open=64, rows_closed=8, k_closed=8, tile=16, seed=20,
+                            n_shapes=50),
 }
 
 # 64 ragged images (sides log-uniform in [256, 2048], aspect in [0.5, 2],

@@ -1,6 +1,8 @@
 """bench.py's host logic (no GPU): the clock record taken during the timed
 region (median SM clock, throttle reasons seen as Active), the FP32 peak
-derived from the unit counts, and the whole-job throughput."""
+derived from the unit counts, the whole-job throughput, the oracle arm's
+isolation from the library, the shared config keys, and the staleness guard
+of the ncu counters."""
 
 import pytest
 
@@ -41,11 +43,59 @@ def test_clock_summary_without_samples():
 
 
 def test_fp32_peak_from_unit_counts():
-    # 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2070 MHz
+    # 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2070 MHz; the SM count is the device's
     assert bench.fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
     assert bench.fp32_peak_tflops(1035.0) == pytest.approx(bench.fp32_peak_tflops(2070.0) / 2)
+    assert bench.fp32_peak_tflops(2070.0, 76) == pytest.approx(bench.fp32_peak_tflops(2070.0) / 2)
 
 
 def test_job_throughput_counts_every_replica():
     assert bench.job_throughput(1, 50, 100.0) == pytest.approx(500.0)
     assert bench.job_throughput(4, 50, 100.0) == pytest.approx(2000.0)
+
+
+def test_oracle_arm_loads_no_part_of_the_library():
+    """The reference arm builds its problem from the seeded generator alone:
+    the ctypes binding (and with it libbs.so) is never imported."""
+    import subprocess
+    import sys
+    code = ("import sys, bench; w, a, t = bench.workload_inputs(0); "
+            "assert 'paper_2503_16424_gb300.bs' not in sys.modules, 'binding imported'; "
+            "assert not any('libbs' in l for l in open('/proc/self/maps')), 'libbs.so mapped'; print('ok')")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=bench.ROOT, timeout=300)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr
+
+
+def test_both_arms_report_the_same_config_keys():
+    w, _, _ = bench.workload_inputs(0)
+    one = bench.workload_config(w, 123, 1)
+    assert one["n_gaussians"] == 262144 and one["n_pairs"] == 123
+    assert set(one) == set(bench.workload_config(w, 5, 4))
+    assert bench.workload_config(w, 5, 4)["parallelism"] == "independent images x4"
+
+
+def test_ranks_get_independent_images():
+    w0, a0, t0 = bench.workload_inputs(0)
+    w1, a1, t1 = bench.workload_inputs(1)
+    assert w0 == w1 and a0["open_ctrl"].shape == a1["open_ctrl"].shape
+    assert not (a0["open_ctrl"] == a1["open_ctrl"]).all()
+
+
+def test_host_cpu_reports_cores_and_a_model():
+    h = bench.host_cpu()
+    assert h["nproc"] >= 1 and isinstance(h["cpu_model"], str) and h["cpu_model"]
+
+
+def test_stale_counters_are_not_used():
+    saved = dict(bench.NCU_CAPTURE)
+    try:
+        bench.NCU_CAPTURE.update(source_sha256_16="0" * 16,
+                                 render_bwd_kernel={"flop_per_eval": 40.0, "dram_bytes": 1})
+        r = bench.roofline(0.5, 1.0, 10, 10, 152, {"sm_max_mhz": 2070.0}, "measured")
+        assert r["achieved"] is None and r["traffic"] is None and r["counters"].startswith("stale")
+        bench.NCU_CAPTURE.update(source_sha256_16=bench.render_source_hash())
+        r = bench.roofline(0.5, 1.0, 10 ** 9, 10 ** 9, 152, {"sm_max_mhz": 2070.0}, "measured")
+        assert r["achieved"] == pytest.approx(40.0 * 1e9 / 1e-3 / 1e12, rel=1e-3) and r["traffic"] == 1
+    finally:
+        bench.NCU_CAPTURE.clear()
+        bench.NCU_CAPTURE.update(saved)
