@@ -666,6 +666,10 @@ bs_status bs_net_sync_weights(const bs_net *net, bs_stream stream);
  * Writes (device, each may be NULL) the head outputs head_out [n][cells][32],
  * and the proposed curves: ctrl [n][cells][12][2] patch pixels, color
  * [n][cells][3], opac [n][cells]; cells = (side / 32)^2, row-major.
+ * Synchronises the stream once, at the end, to read how many tensor-core
+ * tiles gave up their bounded wait for their MMAs: any such tile left its
+ * outputs unwritten, and the call returns BS_ERR_TIMEOUT (never expected;
+ * the test hook bs_debug_umma_wait makes it happen).
  */
 bs_status bs_net_forward(const bs_net *net, const float *patches, int32_t n, int32_t side, void *ws,
                          size_t ws_bytes, float *head_out, float *ctrl, float *color, float *opac,
@@ -676,7 +680,8 @@ bs_status bs_net_forward(const bs_net *net, const float *patches, int32_t n, int
  * [n][cells][12][2], t_color [n][cells][3], t_opac [n][cells] (device): the
  * loss L = mean over cells of sum_j |P_j - P*_j|^2 / BS_NET_REACH^2 +
  * |colour - colour*|^2 + (opacity - opacity*)^2 to loss_out (device double),
- * and dL/d(master weights) to grad (zeroed and written).
+ * and dL/d(master weights) to grad (zeroed and written).  Synchronises and
+ * reports BS_ERR_TIMEOUT as bs_net_forward does.
  */
 bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, int32_t side,
                             const float *t_ctrl, const float *t_color, const float *t_opac, void *ws,
@@ -690,6 +695,14 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
  * how many tcgen05 tiles so far gave up a bounded wait on their MMAs (their
  * results were not stored; 0 expected). */
 bs_status bs_debug_gemm_engine(int32_t engine, int64_t *timeouts_out);
+
+/* Test hook: the tries of the tcgen05 GEMM's wait for its last MMA commit
+ * before the read-back, for later calls in this process (< 0: the default,
+ * 2^24; 0: the wait gives up at once).  A tile whose wait gave up waits
+ * again with the full bound before it releases its tensor memory, stores
+ * nothing, and makes bs_net_forward / bs_net_train_step return
+ * BS_ERR_TIMEOUT.  No wait of the library is unbounded either way. */
+bs_status bs_debug_umma_wait(int64_t first_wait);
 
 /* Synchronise the stream and read the device status word of a binning
  * workspace: BS_OK or the first kernel-side error recorded since the

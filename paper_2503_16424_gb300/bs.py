@@ -161,6 +161,7 @@ _sig("bs_net_forward", POINTER(bs_net), _P, c_int32, c_int32, _P, c_size_t, _P, 
 _sig("bs_net_train_step", POINTER(bs_net), _P, c_int32, c_int32, _P, _P, _P, _P, c_size_t, POINTER(bs_net_grad),
      _P, _P)
 _sig("bs_debug_retry_limit", c_int64)
+_sig("bs_debug_umma_wait", c_int64)
 
 
 class BSError(RuntimeError):
@@ -581,6 +582,13 @@ def prune_densify(curves: CurveSet, img: torch.Tensor, target: torch.Tensor, cfg
     return changed[:n], {f: int(getattr(st, f)) for f, _ in bs_pd_stats._fields_}
 
 
+def debug_umma_wait(first_wait: int = -1):
+    """Test hook: the tries of the tensor-core GEMM's wait for its last MMA
+    commit (< 0 restores the default; 0 gives up at once, which makes the
+    network calls return BS_ERR_TIMEOUT)."""
+    _check("bs_debug_umma_wait", lib.bs_debug_umma_wait(first_wait))
+
+
 def debug_retry_limit(max_attempts: int = -1):
     """Test hook: bound the device-side retry loops (the union step of the
     region labelling) to max_attempts linking attempts (< 0 restores the
@@ -604,6 +612,16 @@ class BatchImage:
     def c(self):
         return bs_batch_image(self.width, self.height, self.n_open, self.n_closed, self.sample.c(),
                               (c_float * 3)(*self.bg))
+
+
+def batch_sizes(images, tile: int = 16, pair_capacity: int = 1 << 20) -> dict:
+    """bs_batch_plan (host arithmetic only, no device needed): the totals of
+    a batch of BatchImage and its workspace bytes."""
+    arr = (bs_batch_image * len(images))(*(im.c() for im in images))
+    b = bs_batch(ctypes.cast(arr, c_void_p), len(images), int(tile), int(pair_capacity), None, 0)
+    sz = bs_batch_sizes()
+    _check("bs_batch_plan", lib.bs_batch_plan(ctypes.byref(b), ctypes.byref(sz)))
+    return {f: int(getattr(sz, f)) for f, _ in bs_batch_sizes._fields_}
 
 
 class Batch:

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "bs_internal.cuh"
 
@@ -166,11 +167,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// Wait until the phase of `parity` of the barrier completed; false when the
-// bounded wait gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait until the phase of `parity` of the barrier completed, trying at most
+// `limit` times; false when the bounded wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kWaitLimit) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -198,8 +199,13 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
 // byte offset of the 16-byte vector (row r, columns 8j..8j+7) in a stage
 __device__ __forceinline__ uint32_t core_off(int r, int j) { return (uint32_t)((r >> 3) * kUmmaSbo + j * kUmmaLbo + (r & 7) * 16); }
 
+// err[0]: tiles whose wait gave up, cumulative; err[1]: the same, for the
+// current library call (zeroed at its start).  first_wait: the tries of the
+// wait for the last commit before the read-back (kWaitLimit; lowered only by
+// the test hook bs_debug_umma_wait); every other wait, and the draining wait
+// before the tensor memory is released, keep kWaitLimit.
 template <class Op>
-__global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsigned int *err) {
+__global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsigned int *err, uint32_t first_wait) {
   __shared__ __align__(128) uint8_t sA[2][kUM * kUK * 2];
   __shared__ __align__(128) uint8_t sB[2][kUN * kUK * 2];
   __shared__ __align__(8) uint64_t bar[2];
@@ -239,6 +245,7 @@ __global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsig
   };
   const int n_chunks = ke > kb ? (ke - kb + kUK - 1) / kUK : 0;
   bool ok = true;
+  int last = n_chunks - 1;  // the last chunk whose MMAs were committed
   if (n_chunks > 0) fetch(kb);
   for (int c = 0; c < n_chunks; ++c) {
     const int st = c & 1;
@@ -246,6 +253,7 @@ __global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsig
       const bool w = tid == 0 ? mbar_wait(&bar[st], (uint32_t)(((c - 2) >> 1) & 1)) : true;
       if (!__syncthreads_and(w)) {
         ok = false;
+        last = c - 1;
         break;
       }
     }
@@ -271,15 +279,15 @@ __global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsig
   }
   if (n_chunks > 0) {
     // thread 0 waits for the last commit, which covers every MMA it issued;
-    // after a wait that gave up, a second bounded wait before the tensor
-    // memory is released, and the tile is not stored
-    const int last = n_chunks - 1;
+    // after a wait that gave up, a second bounded wait (full limit) before
+    // the tensor memory is released, and the tile is not stored
     bool w = true;
     if (tid == 0) {
-      w = ok && mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1));
+      w = ok && mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), first_wait);
       if (!w) {
         mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1));
         atomicAdd(err, 1u);
+        atomicAdd(err + 1, 1u);
       }
     }
     ok = __syncthreads_and(w) && ok;
@@ -511,20 +519,50 @@ struct WgradOp {
 // bs_debug_gemm_engine selects them).
 int g_gemm_engine = 1;
 constexpr int kUmmaMinK = 1024;
-__device__ unsigned int g_umma_timeouts;
+// [0] tiles whose wait gave up since the process started, [1] in the
+// current library call
+__device__ unsigned int g_umma_timeouts[2];
+uint32_t g_first_wait = kWaitLimit;
 
 // The device address of g_umma_timeouts, looked up once per device.
 bs_status umma_err_ptr(unsigned int **out) {
   constexpr int kMaxDev = 64;
   static unsigned int *cache[kMaxDev] = {};
+  static std::once_flag once[kMaxDev];
+  static cudaError_t err[kMaxDev] = {};
   int dev = 0;
   BS_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDev) {
     set_error("device %d: at most %d devices supported", dev, kMaxDev);
     return BS_ERR_UNSUPPORTED;
   }
-  if (!cache[dev]) BS_CUDA(cudaGetSymbolAddress((void **)&cache[dev], g_umma_timeouts));
+  std::call_once(once[dev], [dev] { err[dev] = cudaGetSymbolAddress((void **)&cache[dev], g_umma_timeouts); });
+  BS_CUDA(err[dev]);
   *out = cache[dev];
+  return BS_OK;
+}
+
+// Start of a network call: zero its count of tensor-core waits that gave up.
+bs_status call_timeouts_reset(cudaStream_t s) {
+  unsigned int *err = nullptr;
+  BS_TRY(umma_err_ptr(&err));
+  BS_CUDA(cudaMemsetAsync(err + 1, 0, sizeof(unsigned int), s));
+  return BS_OK;
+}
+
+// End of a network call: read that count (one synchronisation); a wait that
+// gave up left its tile's outputs unwritten, so the call fails.
+bs_status call_timeouts_check(cudaStream_t s, const char *what) {
+  unsigned int *err = nullptr;
+  BS_TRY(umma_err_ptr(&err));
+  unsigned int n = 0;
+  BS_CUDA(cudaMemcpyAsync(&n, err + 1, sizeof(n), cudaMemcpyDeviceToHost, s));
+  BS_CUDA(cudaStreamSynchronize(s));
+  if (n) {
+    set_error("%s: %u tensor-core tile(s) gave up a bounded wait on their MMAs; their outputs were not written",
+              what, n);
+    return BS_ERR_TIMEOUT;
+  }
   return BS_OK;
 }
 
@@ -534,7 +572,7 @@ bs_status run_gemm(const Op &op, int M, int N, int K, int splits, cudaStream_t s
     unsigned int *err = nullptr;
     BS_TRY(umma_err_ptr(&err));
     const dim3 grid((unsigned)div_up(M, kUM), (unsigned)div_up(N, kUN), (unsigned)splits);
-    umma_gemm_kernel<Op><<<grid, kUThreads, 0, s>>>(op, err);
+    umma_gemm_kernel<Op><<<grid, kUThreads, 0, s>>>(op, err, g_first_wait);
     BS_LAUNCHED("umma_gemm_kernel");
     return BS_OK;
   }
@@ -769,10 +807,15 @@ bs_status bs_debug_gemm_engine(int32_t engine, int64_t *timeouts_out) {
   if (engine < 0 || engine > 2) return net_invalid("engine must be 0 (mma.sync), 1 (by reduction length) or 2 (tcgen05)");
   g_gemm_engine = engine;
   if (timeouts_out) {
-    unsigned int t = 0;
-    BS_CUDA(cudaMemcpyFromSymbol(&t, g_umma_timeouts, sizeof(t)));
-    *timeouts_out = t;
+    unsigned int t[2] = {0, 0};
+    BS_CUDA(cudaMemcpyFromSymbol(t, g_umma_timeouts, sizeof(t)));
+    *timeouts_out = t[0];
   }
+  return BS_OK;
+}
+
+bs_status bs_debug_umma_wait(int64_t first_wait) {
+  g_first_wait = first_wait < 0 ? kWaitLimit : (uint32_t)std::min<int64_t>(first_wait, kWaitLimit);
   return BS_OK;
 }
 
@@ -812,13 +855,14 @@ bs_status bs_net_forward(const bs_net *net, const float *patches, int32_t n, int
   if (!patches) return net_invalid("patches is NULL");
   BS_TRY(check_device());
   const cudaStream_t s = (cudaStream_t)stream;
+  BS_TRY(call_timeouts_reset(s));
   BS_TRY(net_forward(net, patches, n, side, w, s));
   const int grid = side >> 5, cells = n * grid * grid;
   net_head_kernel<<<div_up(cells, 128), 128, 0, s>>>(w.head, cells, grid, 32.f, BS_NET_REACH, ctrl, color, opac,
                                                      nullptr, nullptr, nullptr, nullptr, nullptr);
   BS_LAUNCHED("net_head_kernel");
   if (head_out) BS_CUDA(cudaMemcpyAsync(head_out, w.head, sizeof(float) * cells * kHeadOut, cudaMemcpyDeviceToDevice, s));
-  return BS_OK;
+  return call_timeouts_check(s, "bs_net_forward");
 }
 
 bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, int32_t side, const float *t_ctrl,
@@ -833,6 +877,7 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
   if (!patches) return net_invalid("patches is NULL");
   BS_TRY(check_device());
   const cudaStream_t s = (cudaStream_t)stream;
+  BS_TRY(call_timeouts_reset(s));
   BS_TRY(net_forward(net, patches, n, side, w, s));
   const int grid = side >> 5, cells = n * grid * grid;
   BS_CUDA(cudaMemsetAsync(loss_out, 0, sizeof(double), s));
@@ -873,7 +918,7 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
       BS_TRY(run_gemm(dop, g.N * (g.Hi / 2) * (g.Wi / 2), g.Cin, 4 * g.Cout, 1, s));
     }
   }
-  return BS_OK;
+  return call_timeouts_check(s, "bs_net_train_step");
 }
 
 }  // extern "C"

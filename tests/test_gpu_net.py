@@ -145,3 +145,47 @@ def test_tcgen05_and_mma_sync_engines_agree(learned):
         cos = float(g1[l] @ g0[l] / (g1[l].norm() * g0[l].norm()))
         print(f"layer {l}: tcgen05 vs mma.sync rel {err:.2e}, cosine {cos:.7f}")
         assert err <= 2e-2 and cos >= 0.9999, l
+
+
+def test_a_tensor_core_wait_that_gives_up_fails_the_call_and_the_next_call_is_exact(learned):
+    """The bounded wait for the last MMA commit, made to give up at once by
+    the test hook: the tile waits again (full bound) before it frees its
+    tensor memory, stores nothing, and the call returns BS_ERR_TIMEOUT.  With
+    the default bound restored, the next calls equal the calls made before."""
+    import paper_2503_16424_gb300.bs as bs
+    net = _rand_net(learned, 7)
+    rng = np.random.default_rng(12)
+    n, side = 2, 64
+    x = torch.as_tensor(rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32), device="cuda")
+    cells = (side // 32) ** 2
+    t_ctrl = torch.as_tensor(rng.uniform(0, side, (n, cells, 12, 2)).astype(np.float32), device="cuda")
+    t_color = torch.as_tensor(rng.uniform(0, 1, (n, cells, 3)).astype(np.float32), device="cuda")
+    t_opac = torch.as_tensor(rng.uniform(0, 1, (n, cells)).astype(np.float32), device="cuda")
+    bs.debug_gemm_engine(2)                      # every GEMM on tcgen05
+    try:
+        ref = torch.empty(n, cells, 32, device="cuda")
+        bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), ref)
+        loss = torch.zeros((), dtype=torch.float64, device="cuda")
+        bs.net_train_step(net.w, net.w_bf16, net.g, x, t_ctrl, t_color, t_opac, net.ws(n, side), loss)
+        ref_g = [g.clone() for g in net.g]
+        before = bs.debug_gemm_engine(2)
+        bs.debug_umma_wait(0)
+        try:
+            with pytest.raises(bs.BSError) as e:
+                bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), torch.empty(n, cells, 32, device="cuda"))
+            assert e.value.status == bs.BS_ERR_TIMEOUT
+            with pytest.raises(bs.BSError) as e:
+                bs.net_train_step(net.w, net.w_bf16, net.g, x, t_ctrl, t_color, t_opac, net.ws(n, side), loss)
+            assert e.value.status == bs.BS_ERR_TIMEOUT
+        finally:
+            bs.debug_umma_wait(-1)
+        assert bs.debug_gemm_engine(2) > before
+        head = torch.empty(n, cells, 32, device="cuda")
+        bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), head)
+        bs.net_train_step(net.w, net.w_bf16, net.g, x, t_ctrl, t_color, t_opac, net.ws(n, side), loss)
+        torch.cuda.synchronize()
+        assert torch.equal(head, ref)
+        for a, b in zip(net.g, ref_g):
+            assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(b.abs().max()) + 1e-30)
+    finally:
+        bs.debug_gemm_engine(1)
