@@ -19,6 +19,8 @@ Modules
   prune_densify  Section 3.5, Algorithm 1, Appendix B: pruning, splitting,
            error regions and circular initialisation of new curves
   adam     Section 4.1: the Adam update (Kingma and Ba), box-projected
+  cull     Section 3.4's blend and its hand-derived backward in C (OpenMP,
+           exact box culling): the multi-core CPU baseline
   bounds   the sums of absolute per-pixel terms that scale the float32
            rounding of the gradients (Section 3.4's reverse walk, carried
            through the sampling of Section 3.3)
