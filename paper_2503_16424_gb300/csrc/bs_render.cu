@@ -422,7 +422,7 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
       const auto blend = [&](const int q, const float al) {
         if (kStats) ++n_eval;
         if (al < kAlphaMin) return;
-        const float Tn = T[q] * (1.f - al);
+        const float Tn = __fmaf_rn(-T[q], al, T[q]);
         if (Tn < kTMin) {
           alive &= ~(1u << q);
           if (kStats) stop[q] = base - r.x + (uint32_t)j + 1;
@@ -441,15 +441,24 @@ __device__ __forceinline__ float fwd_tile(const TileView &v, const FwdOut &o, co
         return fminf(kAlphaMax,
                      ex2_approx(pixel_log2_alpha(a, b, dx[q % kBC], b1dy[q / kBC], b2dy[q / kBC], t1, t2)));
       };
-      {  // the alphas of all slots first, in one straight run whose chains interleave (a slot the
-         // entry does not reach costs one evaluation; its alpha is not used)
+      // T (1 - alpha) as one FMA; when the entry reaches every block of the
+      // warp, the four alphas in one straight run whose chains interleave,
+      // otherwise only the reached blocks' alphas, each behind its
+      // warp-uniform bit (0.541 -> 0.515 ms at 2048^2)
+      if (bits == G::kSlotMask) {  // every block reached: the alphas in one straight run
         float al[kPix];
 #pragma unroll
         for (int q = 0; q < kPix; ++q) al[q] = alpha(q);
-        const uint32_t go = bits & alive;
 #pragma unroll
         for (int q = 0; q < kPix; ++q)
-          if (go & (1u << q)) blend(q, al[q]);
+          if (alive & (1u << q)) blend(q, al[q]);
+      } else {  // each reached block behind its warp-uniform bit
+#pragma unroll
+        for (int q = 0; q < kPix; ++q)
+          if (bits & (1u << q)) {
+            const float al = alpha(q);
+            if (alive & (1u << q)) blend(q, al);
+          }
       }
     }
     }
