@@ -18,6 +18,7 @@
 //             float32 atomics)
 // Operands are gathered into shared memory 8 bf16 (16 bytes) at a time by
 // the op's load functions; a 64 x 64 tile per CTA, four warps of 32 x 32.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -321,6 +322,181 @@ __global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsig
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kUmmaCols) : "memory");
 }
 
+// ---- forward convolutions fed by the tensor memory accelerator ----
+// For the 4 x 4, stride-2 convolutions whose input has 64 or more channels
+// (and output channels a multiple of 128): a CTA computes a 128 x 128 tile
+// (output pixels x output channels) over K = 16 taps x Cin, in chunks of 64
+// input channels of one tap.  Per chunk one thread issues two TMA loads
+// into a ring of kTStages shared-memory stages:
+//   A: an im2col load of the NHWC input: 128 output pixels (the tile's
+//      rows, traversed W, H, N with stride 2 inside the box [-1, dim - 3],
+//      the padding zero-filled) x 64 channels of the tap (ky, kx), given as
+//      im2col offsets; 128-byte rows, 128-byte swizzle;
+//   B: a tiled load of the weights [Cout][K] (K-major): 128 rows x 64.
+// Both land in the canonical K-major layout with 128-byte swizzle (8-row
+// groups of 1024 bytes), which the tcgen05 descriptors read directly.
+// Another thread waits for each stage, issues four tcgen05.mma (M 128, N
+// 128, K 16; the descriptor's start advances 32 bytes per K step inside the
+// swizzled row) and commits them to the stage's "empty" barrier, which frees
+// it for the next load.  The accumulator (128 x 128 float32) lives in tensor
+// memory; the epilogue reads it back (warp w: lanes 32 w ..), adds the bias,
+// applies ReLU and stores bf16 NHWC rows.  Every mbarrier wait is bounded: a
+// wait that gives up counts in err[0] and err[1] and the tile is not stored.
+constexpr int kTM = 128, kTN = 128, kTK = 64, kTStages = 3, kTThreads = 128;
+constexpr uint32_t kTStageA = kTM * kTK * 2, kTStageB = kTN * kTK * 2;   // bytes
+constexpr uint32_t kTSmem = kTStages * (kTStageA + kTStageB) + 1024;   // + alignment slack
+constexpr uint32_t kTIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                             ((uint32_t)(kTM >> 4) << 24);
+
+// K-major operand descriptor with 128-byte swizzle: start address, stride
+// between 8-row groups 1024 bytes, version 1, layout type 2 (128B swizzle).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_im2col_4d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int c, int w, int h,
+                                              int n, uint16_t off_w, uint16_t off_h) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.im2col.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6], {%7, %8};" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(w), "r"(h), "r"(n), "r"(smem_u32(bar)), "h"(off_w), "h"(off_h)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_tile_2d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16_n128(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kTIdesc), "r"(accumulate)
+      : "memory");
+}
+
+// M = N Ho Wo output pixels, Cout a multiple of kTN, Cin a multiple of kTK;
+// grid (ceil(M / kTM), Cout / kTN).
+__global__ void __launch_bounds__(kTThreads) conv_tma_kernel(const __grid_constant__ CUtensorMap map_in,
+                                                             const __grid_constant__ CUtensorMap map_w, int M, int Ho,
+                                                             int Wo, int Cin, int Cout, const float *__restrict__ bias,
+                                                             __nv_bfloat16 *__restrict__ out, unsigned int *err,
+                                                             uint32_t first_wait) {
+  extern __shared__ uint8_t t_smem[];
+  __shared__ __align__(8) uint64_t full[kTStages], empty[kTStages], done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t base = (smem_u32(t_smem) + 1023u) & ~1023u;   // 1024-byte aligned stages
+  const uint32_t sA = base, sB = base + kTStages * kTStageA;
+  const int m0 = blockIdx.x * kTM, co0 = blockIdx.y * kTN;
+  const int per_tap = Cin / kTK, n_chunks = 16 * per_tap;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"((uint32_t)kTN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kTStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  if (tid == 0) {
+    // producer: the receptive field's corner of the tile's first output pixel
+    const int hw = Ho * Wo, n0 = m0 / hw, r0 = m0 - n0 * hw, oy = r0 / Wo, ox = r0 - oy * Wo;
+    const int w0 = 2 * ox - 1, h0 = 2 * oy - 1;
+    for (int c = 0; c < n_chunks; ++c) {
+      const int st = c % kTStages;
+      if (c >= kTStages && !mbar_wait(&empty[st], (uint32_t)((c / kTStages - 1) & 1))) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      const int tap = c / per_tap, cb = (c - tap * per_tap) * kTK;
+      mbar_expect_tx(&full[st], kTStageA + kTStageB);
+      tma_im2col_4d(sA + st * kTStageA, &map_in, &full[st], cb, w0, h0, n0, (uint16_t)(tap & 3), (uint16_t)(tap >> 2));
+      tma_tile_2d(sB + st * kTStageB, &map_w, &full[st], tap * Cin + cb, co0);
+    }
+  } else if (tid == 32) {
+    // MMA issuer
+    for (int c = 0; c < n_chunks; ++c) {
+      const int st = c % kTStages;
+      if (!mbar_wait(&full[st], (uint32_t)((c / kTStages) & 1))) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < kTK / 16; ++ks) {
+        const uint64_t da = umma_desc_sw128(sA + st * kTStageA + 32u * ks);
+        const uint64_t db = umma_desc_sw128(sB + st * kTStageB + 32u * ks);
+        umma_bf16_n128(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
+      }
+      umma_commit(&empty[st]);
+    }
+    umma_commit(&done);  // arrives once every MMA issued before it has completed
+  }
+  // epilogue: every thread waits for the last commit (bounded; after a wait
+  // that gave up, a second wait with the full bound before the tensor memory
+  // is released), then reads its row of the accumulator
+  bool w = mbar_wait(&done, 0u, first_wait);
+  if (!w) {
+    mbar_wait(&done, 0u);
+    if (tid == 0) {
+      atomicAdd(err, 1u);
+      atomicAdd(err + 1, 1u);
+    }
+  }
+  const bool store = __syncthreads_and(w) && s_fail == 0;
+  if (!store && tid == 0 && w) {
+    atomicAdd(err, 1u);
+    atomicAdd(err + 1, 1u);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (store) {
+    const int m = m0 + 32 * warp + lane;
+#pragma unroll 4
+    for (int col = 0; col < kTN; col += 8) {
+      uint32_t v[8];
+      const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+          "tcgen05.wait::ld.sync.aligned;\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+          : "r"(ta)
+          : "memory");
+      if (m < M) {
+        __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          o[j] = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[2 * j]) + bias[co0 + col + 2 * j], 0.f),
+                                       fmaxf(__uint_as_float(v[2 * j + 1]) + bias[co0 + col + 2 * j + 1], 0.f));
+        *reinterpret_cast<uint4 *>(out + (size_t)m * Cout + co0 + col) = *reinterpret_cast<const uint4 *>(o);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kTN) : "memory");
+}
+
 // ---- the operations ----
 // lcin, lcout, lks: log2 of Cin, Cout, KS (all powers of two here)
 struct Geom {
@@ -517,7 +693,7 @@ struct WgradOp {
 // tensor memory, barriers and read-back, which a few K chunks do not
 // amortise); 2 = tcgen05 always, 0 = mma.sync always (the test hook
 // bs_debug_gemm_engine selects them).
-int g_gemm_engine = 1;
+int g_gemm_engine = 1;   // 3: tcgen05 with thread-gathered operands for every GEMM
 constexpr int kUmmaMinK = 1024;
 // [0] tiles whose wait gave up since the process started, [1] in the
 // current library call
@@ -568,7 +744,7 @@ bs_status call_timeouts_check(cudaStream_t s, const char *what) {
 
 template <class Op>
 bs_status run_gemm(const Op &op, int M, int N, int K, int splits, cudaStream_t s) {
-  if (g_gemm_engine == 2 || (g_gemm_engine == 1 && K >= kUmmaMinK)) {
+  if (g_gemm_engine >= 2 || (g_gemm_engine == 1 && K >= kUmmaMinK)) {
     unsigned int *err = nullptr;
     BS_TRY(umma_err_ptr(&err));
     const dim3 grid((unsigned)div_up(M, kUM), (unsigned)div_up(N, kUN), (unsigned)splits);
@@ -580,6 +756,98 @@ bs_status run_gemm(const Op &op, int M, int N, int K, int splits, cudaStream_t s
   gemm_kernel<Op><<<grid, kGemmThreads, 0, s>>>(op);
   BS_LAUNCHED("gemm_kernel");
   return BS_OK;
+}
+
+// ---- tensor maps for conv_tma_kernel ----
+// The driver's encoders, taken through the runtime's entry-point lookup (the
+// library links no driver library).
+using EncodeIm2col = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const int *, const int *, cuuint32_t, cuuint32_t,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bs_status tma_encoders(EncodeIm2col *im2col, EncodeTiled *tiled) {
+  static std::once_flag once;
+  static void *f_im2col = nullptr, *f_tiled = nullptr;
+  static bool ok = false;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+    const cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeIm2col", &f_im2col, 12000,
+                                                            cudaEnableDefault, &q1);
+    const cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f_tiled, 12000,
+                                                            cudaEnableDefault, &q2);
+    ok = e1 == cudaSuccess && e2 == cudaSuccess && q1 == cudaDriverEntryPointSuccess &&
+         q2 == cudaDriverEntryPointSuccess && f_im2col && f_tiled;
+  });
+  if (!ok) {
+    set_error("the driver's tensor-map encoders are not available");
+    return BS_ERR_UNSUPPORTED;
+  }
+  *im2col = reinterpret_cast<EncodeIm2col>(f_im2col);
+  *tiled = reinterpret_cast<EncodeTiled>(f_tiled);
+  return BS_OK;
+}
+
+// The forward convolution of layer g (4 x 4, stride 2, padding 1; Cin a
+// multiple of 64, Cout of 128) by conv_tma_kernel.
+bs_status run_conv_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias,
+                       __nv_bfloat16 *out, cudaStream_t s) {
+  EncodeIm2col enc_im2col;
+  EncodeTiled enc_tiled;
+  BS_TRY(tma_encoders(&enc_im2col, &enc_tiled));
+  CUtensorMap map_in, map_w;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.Cin, (cuuint64_t)g.Wi, (cuuint64_t)g.Hi, (cuuint64_t)g.N};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.Cin * 2, (cuuint64_t)g.Wi * g.Cin * 2,
+                                 (cuuint64_t)g.Hi * g.Wi * g.Cin * 2};
+  // the receptive field's corner runs over [-P, dim - 1 + P - (KS - 1)]
+  const int lower[2] = {-g.P, -g.P}, upper[2] = {g.P - (g.KS - 1), g.P - (g.KS - 1)};
+  const cuuint32_t estr[4] = {1, (cuuint32_t)g.S, (cuuint32_t)g.S, 1};
+  CUresult r = enc_im2col(&map_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(in), dims, strides,
+                          lower, upper, kTK, kTM, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeIm2col failed (%d) for a %dx%dx%d input", (int)r, g.Hi, g.Wi, g.Cin);
+    return BS_ERR_CUDA;
+  }
+  const cuuint64_t wdims[2] = {(cuuint64_t)g.K(), (cuuint64_t)g.Cout};
+  const cuuint64_t wstrides[1] = {(cuuint64_t)g.K() * 2};
+  const cuuint32_t box[2] = {kTK, kTN}, wes[2] = {1, 1};
+  r = enc_tiled(&map_w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(w), wdims, wstrides, box,
+                wes, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for the %dx%d weights", (int)r, g.Cout, g.K());
+    return BS_ERR_CUDA;
+  }
+  unsigned int *err = nullptr;
+  BS_TRY(umma_err_ptr(&err));
+  {
+    constexpr int kMaxDev = 64;
+    static bool attr[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    BS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDev || !attr[dev]) {
+      BS_CUDA(cudaFuncSetAttribute(conv_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem));
+      if (dev >= 0 && dev < kMaxDev) attr[dev] = true;
+    }
+  }
+  const dim3 grid((unsigned)div_up(g.M(), kTM), (unsigned)(g.Cout / kTN));
+  conv_tma_kernel<<<grid, kTThreads, kTSmem, s>>>(map_in, map_w, g.M(), g.Ho, g.Wo, g.Cin, g.Cout, bias, out, err,
+                                                  g_first_wait);
+  BS_LAUNCHED("conv_tma_kernel");
+  return BS_OK;
+}
+
+// The layers run by conv_tma_kernel: engines 1 and 2, 4 x 4 stride-2
+// convolutions with Cin a multiple of 64 and Cout of 128.
+bool uses_tma(const Geom &g) {
+  return (g_gemm_engine == 1 || g_gemm_engine == 2) && g.KS == 4 && g.S == 2 && g.P == 1 && g.Cin % kTK == 0 &&
+         g.Cout % kTN == 0;
 }
 
 // ---- element-wise pieces ----
@@ -791,7 +1059,12 @@ bs_status net_forward(const bs_net *net, const float *patches, int n, int side, 
   BS_LAUNCHED("net_input_kernel");
   for (int l = 0; l < 5; ++l) {
     const Geom g = net_layer(l, n, side);
-    const FwdOp<true> op{g, ws.act[l], wbf(net, l), net->w[l] + (size_t)g.Cout * g.K(), ws.act[l + 1], nullptr};
+    const float *bias = net->w[l] + (size_t)g.Cout * g.K();
+    if (uses_tma(g)) {
+      BS_TRY(run_conv_tma(g, ws.act[l], wbf(net, l), bias, ws.act[l + 1], s));
+      continue;
+    }
+    const FwdOp<true> op{g, ws.act[l], wbf(net, l), bias, ws.act[l + 1], nullptr};
     BS_TRY(run_gemm(op, g.M(), g.Cout, g.K(), 1, s));
   }
   const Geom g = net_layer(5, n, side);
@@ -804,7 +1077,8 @@ bs_status net_forward(const bs_net *net, const float *patches, int n, int side, 
 extern "C" {
 
 bs_status bs_debug_gemm_engine(int32_t engine, int64_t *timeouts_out) {
-  if (engine < 0 || engine > 2) return net_invalid("engine must be 0 (mma.sync), 1 (by reduction length) or 2 (tcgen05)");
+  if (engine < 0 || engine > 3)
+    return net_invalid("engine must be 0 (mma.sync), 1 (by reduction length), 2 (tcgen05) or 3 (tcgen05, gathered)");
   g_gemm_engine = engine;
   if (timeouts_out) {
     unsigned int t[2] = {0, 0};

@@ -289,9 +289,37 @@ def train_flops(n: int, side: int = SIDE) -> float:
     return tot
 
 
+def time_forward(n: int = 64, side: int = SIDE, reps: int = 20, engines=(0, 3, 1), device="cuda") -> dict:
+    """ms of one forward of n random patches on each GEMM engine (0:
+    mma.sync, 3: tcgen05 with thread-gathered operands, 1: the default, the
+    convolutions of 64 or more input channels TMA-fed), CUDA events."""
+    net = InitNet(device=device, seed=1)
+    rng = np.random.default_rng(0)
+    x = torch.as_tensor(rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32), device=device)
+    head = torch.empty(n, (side // CELL) ** 2, 32, device=device)
+    out = {}
+    try:
+        for engine in engines:
+            bs.debug_gemm_engine(engine)
+            for _ in range(3):
+                bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), head)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), head)
+            e1.record()
+            torch.cuda.synchronize()
+            out[engine] = e0.elapsed_time(e1) / reps
+    finally:
+        bs.debug_gemm_engine(1)
+    return out
+
+
 def main(argv=None):
     """Pairs -> training -> evaluation on 2048 x 2048 targets (64 patches
-    each); prints one JSON line."""
+    each); prints one JSON line.  With --time-forward, only the forward's
+    time on each GEMM engine."""
     import argparse
     import json
     import time
@@ -305,7 +333,14 @@ def main(argv=None):
     ap.add_argument("--side", type=int, default=2048)
     ap.add_argument("--eval-steps", type=int, default=300)
     ap.add_argument("--every", type=int, default=10)
+    ap.add_argument("--time-forward", action="store_true", help="time one forward of --batch patches per engine")
+    ap.add_argument("--engines", default="0,3,1", help="GEMM engines for --time-forward")
+    ap.add_argument("--reps", type=int, default=20)
     a = ap.parse_args(argv)
+    if a.time_forward:
+        ms = time_forward(a.batch, SIDE, a.reps, tuple(int(e) for e in a.engines.split(",")))
+        print(json.dumps({"forward_ms_by_engine": ms, "patches": a.batch, "side": SIDE}))
+        return
     dev = "cuda"
     t0 = time.perf_counter()
     data = make_pairs(a.pairs, seed=1, steps=a.pair_steps, device=dev)

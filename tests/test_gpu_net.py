@@ -189,3 +189,34 @@ def test_a_tensor_core_wait_that_gives_up_fails_the_call_and_the_next_call_is_ex
             assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(b.abs().max()) + 1e-30)
     finally:
         bs.debug_gemm_engine(1)
+
+
+def test_tma_fed_convolutions_agree_with_the_gathered_engines(learned):
+    """The forward convolutions with 64 or more input channels (layers 2-4)
+    on the TMA-fed tcgen05 kernel (engines 1 and 2) against the same
+    network with every GEMM's operands gathered by threads (engine 3,
+    tcgen05; engine 0, mma.sync): the same bf16 products summed in float32
+    in another order, so the head outputs agree to a few float32 ulps of the
+    sums, up to activations whose bf16 rounding flips (bars as above)."""
+    import paper_2503_16424_gb300.bs as bs
+    net = _rand_net(learned, 8)
+    rng = np.random.default_rng(13)
+    for n, side in ((2, 128), (3, 96), (1, 32)):
+        x = torch.as_tensor(rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32), device="cuda")
+        cells = (side // 32) ** 2
+        heads = {}
+        try:
+            for engine in (0, 1, 2, 3):
+                bs.debug_gemm_engine(engine)
+                head = torch.empty(n, cells, 32, device="cuda")
+                bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), head)
+                torch.cuda.synchronize()
+                heads[engine] = head.cpu().double()
+        finally:
+            bs.debug_gemm_engine(1)
+        ref = heads[3]
+        for engine in (0, 1, 2):
+            err = float((heads[engine] - ref).abs().max() / ref.abs().max())
+            print(f"n {n} side {side}: engine {engine} vs gathered tcgen05: rel {err:.2e}")
+            assert err <= 5e-3, (n, side, engine)
+        assert torch.equal(heads[1], heads[2])   # both run layers 2-4 on the TMA kernel, 0-1 and the head alike
