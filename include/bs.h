@@ -688,12 +688,16 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
                             size_t ws_bytes, const bs_net_grad *grad, double *loss_out, bs_stream stream);
 
 /* Test hook: the engine of the network's GEMMs for later calls in this
- * process: 1 (the default) tcgen05 (128 x 64 tiles, accumulators in tensor
- * memory) for GEMMs whose reduction per CTA is at least 1024 long and
- * mma.sync (64 x 64 tiles, accumulators in registers) for the shorter ones;
- * 2 tcgen05 always; 0 mma.sync always.  timeouts_out (HOST, may be NULL):
- * how many tcgen05 tiles so far gave up a bounded wait on their MMAs (their
- * results were not stored; 0 expected). */
+ * process.  1 (the default): the forward convolutions with 64 or more input
+ * channels on the TMA-fed tcgen05 kernel (im2col and tiled TMA loads into
+ * 128-byte-swizzled stages of an mbarrier ring, 128 x 128 tiles accumulated
+ * in tensor memory), the other GEMMs on tcgen05 with thread-gathered
+ * operands (128 x 64 tiles) when their reduction per CTA is at least 1024
+ * long and on mma.sync (64 x 64 tiles, accumulators in registers) below;
+ * 2: as 1, with every other GEMM on the gathered tcgen05 kernel; 3: every
+ * GEMM on the gathered tcgen05 kernel; 0: every GEMM on mma.sync.
+ * timeouts_out (HOST, may be NULL): how many tcgen05 tiles so far gave up a
+ * bounded wait on their MMAs (their results were not stored; 0 expected). */
 bs_status bs_debug_gemm_engine(int32_t engine, int64_t *timeouts_out);
 
 /* Test hook: the tries of the tcgen05 GEMM's wait for its last MMA commit
