@@ -623,21 +623,26 @@ bs_status bs_svg_export(const bs_curves *curves, const uint32_t *rank, int32_t w
 /* ------------------------------------------------------------------------
  * Learned initialisation (not in the paper: a proposal network for initial
  * curves).  A 5-layer convolutional encoder maps a side x side RGB patch
- * (side a multiple of 32) to one closed curve per 32 x 32 cell: five 4 x 4
- * convolutions of stride 2 and padding 1 with ReLU (channels 8 -> 32 -> 64
- * -> 128 -> 256 -> 256, the RGB input padded to 8), then a 1 x 1 head
- * (256 -> 32).  The head's first 28 outputs o of a cell with centre c give
- * the curve: control points P_j = c + BS_NET_REACH tanh(o_{2j}, o_{2j+1})
- * (j = 0..11, patch pixels), colour sigmoid(o_24..26), opacity
- * sigmoid(o_27).  Convolutions run as implicit GEMMs on the bf16 tensor
- * cores with float32 accumulation; activations are bf16.
+ * (side a multiple of 32) to one closed curve and one open stroke (the two
+ * kinds of Section 3.2) per 32 x 32 cell: five 4 x 4 convolutions of stride
+ * 2 and padding 1 with ReLU (channels 8 -> 32 -> 64 -> 128 -> 256 -> 256,
+ * the RGB input padded to 8), then a 1 x 1 head (256 -> 64).  The head's
+ * outputs o of a cell with centre c give (patch pixels):
+ *   closed curve  P_j = c + BS_NET_REACH tanh(o_{2j}, o_{2j+1}) (j = 0..11),
+ *                 colour sigmoid(o_24..26), opacity sigmoid(o_27);
+ *   open stroke   Q_j = c + BS_NET_REACH tanh(o_{28+2j}, o_{29+2j})
+ *                 (j = 0..9), width BS_NET_WIDTH_MAX sigmoid(o_48), colour
+ *                 sigmoid(o_49..51), segment opacities sigmoid(o_52..54);
+ * outputs 55..63 are unused.  Convolutions run as implicit GEMMs on the
+ * bf16 tensor cores with float32 accumulation; activations are bf16.
  * ---------------------------------------------------------------------- */
 #define BS_NET_LAYERS 6
 #define BS_NET_REACH 24.0f
+#define BS_NET_WIDTH_MAX 8.0f
 
 /* Weights of the network (device, caller-owned).  w[l]: float32 master
  * weights of layer l, [Cout][ky][kx][Cin] then the bias [Cout]
- * (bs_net_param_count(l) floats; layer 5 is the head, [32][256] + [32]).
+ * (bs_net_param_count(l) floats; layer 5 is the head, [64][256] + [64]).
  * w_bf16[l]: bfloat16 copy of the weights (without the bias), written by
  * bs_net_sync_weights. */
 typedef struct {
@@ -649,6 +654,19 @@ typedef struct {
 typedef struct {
   float *g[BS_NET_LAYERS];
 } bs_net_grad;
+
+/* Per-cell curves of n patches (device, cells = (side / 32)^2, row-major,
+ * patch after patch): the network's proposals, or the targets of a training
+ * step (then read only). */
+typedef struct {
+  float *ctrl;        /* [n][cells][12][2] closed-curve control points, patch px */
+  float *color;       /* [n][cells][3]                                            */
+  float *opac;        /* [n][cells]                                               */
+  float *open_ctrl;   /* [n][cells][10][2] open-stroke control points, patch px   */
+  float *open_width;  /* [n][cells]        px, in (0, BS_NET_WIDTH_MAX)           */
+  float *open_color;  /* [n][cells][3]                                            */
+  float *open_opac;   /* [n][cells][3]     one per segment                        */
+} bs_net_curves;
 
 /* Floats of layer `layer`'s master array (weights + bias); -1 if out of range. */
 int64_t bs_net_param_count(int32_t layer);
@@ -663,29 +681,30 @@ bs_status bs_net_sync_weights(const bs_net *net, bs_stream stream);
 
 /*
  * Forward of n patches (planar float32 [n][3][side][side], values in [0,1]).
- * Writes (device, each may be NULL) the head outputs head_out [n][cells][32],
- * and the proposed curves: ctrl [n][cells][12][2] patch pixels, color
- * [n][cells][3], opac [n][cells]; cells = (side / 32)^2, row-major.
- * Synchronises the stream once, at the end, to read how many tensor-core
- * tiles gave up their bounded wait for their MMAs: any such tile left its
- * outputs unwritten, and the call returns BS_ERR_TIMEOUT (never expected;
- * the test hook bs_debug_umma_wait makes it happen).
+ * Writes (device, each may be NULL) the head outputs head_out [n][cells][64]
+ * and, when curves is non-NULL, the proposals into those of its arrays that
+ * are non-NULL.  Synchronises the stream once, at the end, to read how many
+ * tensor-core tiles gave up their bounded wait for their MMAs: any such tile
+ * left its outputs unwritten, and the call returns BS_ERR_TIMEOUT (never
+ * expected; the test hook bs_debug_umma_wait makes it happen).
  */
 bs_status bs_net_forward(const bs_net *net, const float *patches, int32_t n, int32_t side, void *ws,
-                         size_t ws_bytes, float *head_out, float *ctrl, float *color, float *opac,
-                         bs_stream stream);
+                         size_t ws_bytes, float *head_out, const bs_net_curves *curves, bs_stream stream);
 
 /*
- * One training step's forward and backward against target curves t_ctrl
- * [n][cells][12][2], t_color [n][cells][3], t_opac [n][cells] (device): the
- * loss L = mean over cells of sum_j |P_j - P*_j|^2 / BS_NET_REACH^2 +
- * |colour - colour*|^2 + (opacity - opacity*)^2 to loss_out (device double),
- * and dL/d(master weights) to grad (zeroed and written).  Synchronises and
- * reports BS_ERR_TIMEOUT as bs_net_forward does.
+ * One training step's forward and backward against the target curves
+ * `target` (device, every array non-NULL): the loss, the mean over cells of
+ *   sum_j |P_j - P*_j|^2 / BS_NET_REACH^2 + |colour - colour*|^2
+ *   + (opacity - opacity*)^2 + sum_j |Q_j - Q*_j|^2 / BS_NET_REACH^2
+ *   + (width - width*)^2 / BS_NET_WIDTH_MAX^2 + |colour' - colour'*|^2
+ *   + sum_s (opacity'_s - opacity'*_s)^2
+ * (primes: the open stroke), to loss_out (device double), and dL/d(master
+ * weights) to grad (zeroed and written).  Synchronises and reports
+ * BS_ERR_TIMEOUT as bs_net_forward does.
  */
 bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, int32_t side,
-                            const float *t_ctrl, const float *t_color, const float *t_opac, void *ws,
-                            size_t ws_bytes, const bs_net_grad *grad, double *loss_out, bs_stream stream);
+                            const bs_net_curves *target, void *ws, size_t ws_bytes, const bs_net_grad *grad,
+                            double *loss_out, bs_stream stream);
 
 /* Test hook: the engine of the network's GEMMs for later calls in this
  * process.  1 (the default): the forward convolutions with 64 or more input

@@ -98,6 +98,8 @@ class bs_adam_cfg(ctypes.Structure):
 ADAM_MAX_GROUPS = 16
 NET_LAYERS = 6
 NET_REACH = 24.0
+NET_WIDTH_MAX = 8.0
+NET_CURVE_KEYS = ("ctrl", "color", "opac", "open_ctrl", "open_width", "open_color", "open_opac")
 
 
 class bs_net(ctypes.Structure):
@@ -106,6 +108,10 @@ class bs_net(ctypes.Structure):
 
 class bs_net_grad(ctypes.Structure):
     _fields_ = [("g", c_void_p * NET_LAYERS)]
+
+
+class bs_net_curves(ctypes.Structure):
+    _fields_ = [(k, c_void_p) for k in NET_CURVE_KEYS]
 
 
 def _sig(name, *args):
@@ -157,8 +163,8 @@ lib.bs_net_param_count.argtypes = [c_int32]
 lib.bs_net_param_count.restype = c_int64
 _sig("bs_net_workspace", c_int32, c_int32, POINTER(c_size_t))
 _sig("bs_net_sync_weights", POINTER(bs_net), _P)
-_sig("bs_net_forward", POINTER(bs_net), _P, c_int32, c_int32, _P, c_size_t, _P, _P, _P, _P, _P)
-_sig("bs_net_train_step", POINTER(bs_net), _P, c_int32, c_int32, _P, _P, _P, _P, c_size_t, POINTER(bs_net_grad),
+_sig("bs_net_forward", POINTER(bs_net), _P, c_int32, c_int32, _P, c_size_t, _P, POINTER(bs_net_curves), _P)
+_sig("bs_net_train_step", POINTER(bs_net), _P, c_int32, c_int32, POINTER(bs_net_curves), _P, c_size_t, POINTER(bs_net_grad),
      _P, _P)
 _sig("bs_debug_retry_limit", c_int64)
 _sig("bs_debug_umma_wait", c_int64)
@@ -798,22 +804,47 @@ def net_sync_weights(w, w_bf16):
     _check("bs_net_sync_weights", lib.bs_net_sync_weights(ctypes.byref(net), _stream()))
 
 
-def net_forward(w, w_bf16, patches, ws, head=None, ctrl=None, color=None, opac=None):
+NET_CURVE_SHAPES = dict(ctrl=(12, 2), color=(3,), opac=(), open_ctrl=(10, 2), open_width=(), open_color=(3,),
+                        open_opac=(3,))
+
+
+def _net_curves_c(curves: dict, n: int, cells: int, need_all: bool):
+    """bs_net_curves of a dict of float32 device tensors [n, cells, ...]
+    (missing keys NULL unless need_all)."""
+    ptrs = {}
+    for k in NET_CURVE_KEYS:
+        t = curves.get(k)
+        if t is None:
+            if need_all:
+                raise ValueError(f"target {k} is missing")
+            ptrs[k] = None
+            continue
+        _want(t, torch.float32, (n, cells) + NET_CURVE_SHAPES[k], k)
+        ptrs[k] = t.data_ptr()
+    return bs_net_curves(**ptrs)
+
+
+def net_forward(w, w_bf16, patches, ws, head=None, curves: dict = None):
+    """Head outputs to `head` [n, cells, 64] and proposals into the tensors
+    of `curves` (keys NET_CURVE_KEYS, any subset)."""
     _want(patches, torch.float32, None, "patches")
     n, side = int(patches.shape[0]), int(patches.shape[-1])
     net = _net_c(w, w_bf16)
+    c = _net_curves_c(curves, n, (side // 32) ** 2, False) if curves else None
     _check("bs_net_forward", lib.bs_net_forward(ctypes.byref(net), _ptr(patches), n, side, _ptr(ws), ws.numel(),
-                                                 _ptr(head), _ptr(ctrl), _ptr(color), _ptr(opac), _stream()))
+                                                 _ptr(head), ctypes.byref(c) if c is not None else None, _stream()))
 
 
-def net_train_step(w, w_bf16, grads, patches, t_ctrl, t_color, t_opac, ws, loss):
+def net_train_step(w, w_bf16, grads, patches, targets: dict, ws, loss):
+    """targets: every key of NET_CURVE_KEYS, float32 device [n, cells, ...]."""
     _want(patches, torch.float32, None, "patches")
     n, side = int(patches.shape[0]), int(patches.shape[-1])
     net = _net_c(w, w_bf16)
-    g = bs_net_grad((c_void_p * NET_LAYERS)(*(t.data_ptr() for t in grads)))
-    _check("bs_net_train_step", lib.bs_net_train_step(ctypes.byref(net), _ptr(patches), n, side, _ptr(t_ctrl),
-                                                       _ptr(t_color), _ptr(t_opac), _ptr(ws), ws.numel(),
-                                                       ctypes.byref(g), c_void_p(loss.data_ptr()), _stream()))
+    t = _net_curves_c(targets, n, (side // 32) ** 2, True)
+    g = bs_net_grad((c_void_p * NET_LAYERS)(*(x.data_ptr() for x in grads)))
+    _check("bs_net_train_step", lib.bs_net_train_step(ctypes.byref(net), _ptr(patches), n, side, ctypes.byref(t),
+                                                       _ptr(ws), ws.numel(), ctypes.byref(g),
+                                                       c_void_p(loss.data_ptr()), _stream()))
 
 
 # ---------------------------------------------------------------------------

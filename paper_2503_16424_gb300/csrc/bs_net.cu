@@ -1,10 +1,11 @@
 // The learned initialiser: a 5-layer convolutional encoder that maps a
-// 256 x 256 RGB patch to 64 closed-curve proposals (one per cell of an 8 x 8
-// grid), trained on curve sets the method itself optimised.
+// 256 x 256 RGB patch to curve proposals, one closed curve and one open
+// stroke per cell of an 8 x 8 grid, trained on curve sets the method itself
+// optimised.
 //
 // Layers: five 4 x 4 convolutions of stride 2 and padding 1 (channels 8 -> 32
 // -> 64 -> 128 -> 256 -> 256; the RGB input is padded to 8 channels), each
-// followed by ReLU, then a 1 x 1 head (256 -> 32, the first 28 used).
+// followed by ReLU, then a 1 x 1 head (256 -> 64, the first 55 used).
 // Activations are NHWC bfloat16, weights bfloat16 copies of float32 master
 // weights, accumulation float32.
 //
@@ -906,55 +907,83 @@ __global__ void net_bias_grad_kernel(const __nv_bfloat16 *__restrict__ dout, int
   atomicAdd(db + co, acc);
 }
 
-// The head's 28 outputs per cell o -> one closed curve (Section 3.2: 12
-// control points, colour, opacity) in the patch's pixel coordinates:
-// P_j = cell centre + reach tanh(o_{2j..2j+1}), colour = sigmoid(o_24..26),
-// opacity = sigmoid(o_27).  Cells are row-major on the grid x grid lattice
-// of cell side `cell`.  With targets: the loss
-//   L = mean over cells of [ sum_j |P_j - P*_j|^2 / reach^2 + |c - c*|^2 + (a - a*)^2 ]
-// (added to *loss, one double atomic per thread with cells) and dL/do (float
-// [cells][32], zero in 28..31) as bf16 for the head's backward and float.
-constexpr int kHeadOut = 32, kCurveOut = 28;
-__global__ void net_head_kernel(const float *__restrict__ o, int n_cells, int grid, float cell, float reach,
-                                float *__restrict__ ctrl, float *__restrict__ color, float *__restrict__ opac,
-                                const float *__restrict__ t_ctrl, const float *__restrict__ t_color,
-                                const float *__restrict__ t_opac, double *__restrict__ loss,
+// The head's 64 outputs per cell o -> one closed curve and one open stroke
+// (the two kinds of Section 3.2) in the patch's pixel coordinates, around the
+// cell centre C (cells row-major on the grid x grid lattice of side `cell`):
+//   closed  P_j = C + reach tanh(o_{2j}, o_{2j+1}) (j < 12), colour
+//           sigmoid(o_24..26), opacity sigmoid(o_27);
+//   open    Q_j = C + reach tanh(o_{28+2j}, o_{29+2j}) (j < 10), width
+//           wmax sigmoid(o_48), colour sigmoid(o_49..51), segment opacities
+//           sigmoid(o_52..54); outputs 55..63 are unused.
+// With targets (tgt.ctrl non-NULL): the loss, the mean over cells of
+//   sum_j |P_j - P*_j|^2 / reach^2 + |c - c*|^2 + (a - a*)^2
+//   + sum_j |Q_j - Q*_j|^2 / reach^2 + (w - w*)^2 / wmax^2 + |c' - c'*|^2 + sum_s (a'_s - a'*_s)^2,
+// added to *loss (one double atomic per cell), and dL/do as bf16 [cells][64]
+// (zero at the unused outputs) for the head's backward.
+constexpr int kHeadOut = 64;
+
+__device__ __forceinline__ float head_sigmoid(float x) { return 1.f / (1.f + __expf(-x)); }
+
+__global__ void net_head_kernel(const float *__restrict__ o, int n_cells, int grid, float cell, float reach, float wmax,
+                                bs_net_curves out, bs_net_curves tgt, double *__restrict__ loss,
                                 __nv_bfloat16 *__restrict__ dout) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
   const float *oc = o + (size_t)c * kHeadOut;
+  const bool train = tgt.ctrl != nullptr;
+  __nv_bfloat16 *dc = train ? dout + (size_t)c * kHeadOut : nullptr;
   const int cc = c % (grid * grid), gy = cc / grid, gx = cc - gy * grid;
   const float cx = (gx + 0.5f) * cell, cy = (gy + 0.5f) * cell;
-  float d[kHeadOut];
   double l = 0.0;
   const float inv = 1.f / (reach * reach), scale = 1.f / (float)n_cells;
-  for (int j = 0; j < 12; ++j) {
-    const float tx = tanhf(oc[2 * j]), ty = tanhf(oc[2 * j + 1]);
-    const float px = cx + reach * tx, py = cy + reach * ty;
-    if (ctrl) {
-      ctrl[(size_t)c * 24 + 2 * j] = px;
-      ctrl[(size_t)c * 24 + 2 * j + 1] = py;
-    }
-    if (t_ctrl) {
-      const float ex = px - t_ctrl[(size_t)c * 24 + 2 * j], ey = py - t_ctrl[(size_t)c * 24 + 2 * j + 1];
-      l += (double)(ex * ex + ey * ey) * inv;
-      d[2 * j] = scale * 2.f * ex * inv * reach * (1.f - tx * tx);
-      d[2 * j + 1] = scale * 2.f * ey * inv * reach * (1.f - ty * ty);
+  // control points: the closed curve's 12 at outputs 0..23, the stroke's 10 at 28..47
+  for (int kind = 0; kind < 2; ++kind) {
+    const int np = kind ? 10 : 12, o0 = kind ? 28 : 0;
+    float *dst = kind ? out.open_ctrl : out.ctrl;
+    const float *t = kind ? tgt.open_ctrl : tgt.ctrl;
+    for (int j = 0; j < np; ++j) {
+      const float tx = tanhf(oc[o0 + 2 * j]), ty = tanhf(oc[o0 + 2 * j + 1]);
+      const float px = cx + reach * tx, py = cy + reach * ty;
+      const size_t e0 = ((size_t)c * np + j) * 2;
+      if (dst) {
+        dst[e0] = px;
+        dst[e0 + 1] = py;
+      }
+      if (train) {
+        const float ex = px - t[e0], ey = py - t[e0 + 1];
+        l += (double)(ex * ex + ey * ey) * inv;
+        dc[o0 + 2 * j] = __float2bfloat16(scale * 2.f * ex * inv * reach * (1.f - tx * tx));
+        dc[o0 + 2 * j + 1] = __float2bfloat16(scale * 2.f * ey * inv * reach * (1.f - ty * ty));
+      }
     }
   }
-  for (int k = 0; k < 4; ++k) {
-    const float s = 1.f / (1.f + __expf(-oc[24 + k]));
-    if (k < 3 && color) color[(size_t)c * 3 + k] = s;
-    if (k == 3 && opac) opac[c] = s;
-    if (t_ctrl) {
-      const float e = s - (k < 3 ? t_color[(size_t)c * 3 + k] : t_opac[c]);
+  // the sigmoid outputs: value s, written to dst[i] and compared with t[i]
+  auto unit = [&](int k, float *dst, const float *t, size_t i) {
+    const float s = head_sigmoid(oc[k]);
+    if (dst) dst[i] = s;
+    if (train) {
+      const float e = s - t[i];
       l += (double)(e * e);
-      d[24 + k] = scale * 2.f * e * s * (1.f - s);
+      dc[k] = __float2bfloat16(scale * 2.f * e * s * (1.f - s));
+    }
+  };
+  for (int k = 0; k < 3; ++k) {
+    unit(24 + k, out.color, tgt.color, (size_t)c * 3 + k);
+    unit(49 + k, out.open_color, tgt.open_color, (size_t)c * 3 + k);
+    unit(52 + k, out.open_opac, tgt.open_opac, (size_t)c * 3 + k);
+  }
+  unit(27, out.opac, tgt.opac, c);
+  {  // width: (w - w*) / wmax = s - w* / wmax, so the term is a unit one in s
+    const float s = head_sigmoid(oc[48]);
+    if (out.open_width) out.open_width[c] = wmax * s;
+    if (train) {
+      const float e = s - tgt.open_width[c] / wmax;
+      l += (double)(e * e);
+      dc[48] = __float2bfloat16(scale * 2.f * e * s * (1.f - s));
     }
   }
-  if (t_ctrl) {
-    for (int k = kCurveOut; k < kHeadOut; ++k) d[k] = 0.f;
-    for (int k = 0; k < kHeadOut; ++k) dout[(size_t)c * kHeadOut + k] = __float2bfloat16(d[k]);
+  if (train) {
+    for (int k = 55; k < kHeadOut; ++k) dc[k] = __float2bfloat16(0.f);
     atomicAdd(loss, l / (double)n_cells);
   }
 }
@@ -1016,7 +1045,7 @@ bs_status check_net(const bs_net *net, int32_t n, int32_t side) {
 }
 
 // Activation buffers inside the workspace: x0 (input, 8 channels) and the
-// outputs of layers 0..4, NHWC bf16; the head output (float [cells][32]).
+// outputs of layers 0..4, NHWC bf16; the head output (float [cells][64]).
 struct NetWs {
   __nv_bfloat16 *act[6];
   float *head;
@@ -1122,7 +1151,7 @@ bs_status bs_net_sync_weights(const bs_net *net, bs_stream stream) {
 }
 
 bs_status bs_net_forward(const bs_net *net, const float *patches, int32_t n, int32_t side, void *ws, size_t ws_bytes,
-                         float *head_out, float *ctrl, float *color, float *opac, bs_stream stream) {
+                         float *head_out, const bs_net_curves *curves, bs_stream stream) {
   BS_TRY(check_net(net, n, side));
   const NetWs w = carve_net(ws, n, side);
   if (!ws || ws_bytes < w.bytes || ((uintptr_t)ws & 255u)) return net_invalid("workspace too small or not 256-byte aligned");
@@ -1132,18 +1161,22 @@ bs_status bs_net_forward(const bs_net *net, const float *patches, int32_t n, int
   BS_TRY(call_timeouts_reset(s));
   BS_TRY(net_forward(net, patches, n, side, w, s));
   const int grid = side >> 5, cells = n * grid * grid;
-  net_head_kernel<<<div_up(cells, 128), 128, 0, s>>>(w.head, cells, grid, 32.f, BS_NET_REACH, ctrl, color, opac,
-                                                     nullptr, nullptr, nullptr, nullptr, nullptr);
+  const bs_net_curves out = curves ? *curves : bs_net_curves{};
+  net_head_kernel<<<div_up(cells, 128), 128, 0, s>>>(w.head, cells, grid, 32.f, BS_NET_REACH, BS_NET_WIDTH_MAX, out,
+                                                     bs_net_curves{}, nullptr, nullptr);
   BS_LAUNCHED("net_head_kernel");
   if (head_out) BS_CUDA(cudaMemcpyAsync(head_out, w.head, sizeof(float) * cells * kHeadOut, cudaMemcpyDeviceToDevice, s));
   return call_timeouts_check(s, "bs_net_forward");
 }
 
-bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, int32_t side, const float *t_ctrl,
-                            const float *t_color, const float *t_opac, void *ws, size_t ws_bytes, const bs_net_grad *grad,
+bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, int32_t side,
+                            const bs_net_curves *target, void *ws, size_t ws_bytes, const bs_net_grad *grad,
                             double *loss_out, bs_stream stream) {
   BS_TRY(check_net(net, n, side));
-  if (!grad || !t_ctrl || !t_color || !t_opac || !loss_out) return net_invalid("NULL target, gradient or loss");
+  if (!grad || !target || !loss_out) return net_invalid("NULL target, gradient or loss");
+  if (!target->ctrl || !target->color || !target->opac || !target->open_ctrl || !target->open_width ||
+      !target->open_color || !target->open_opac)
+    return net_invalid("every target array must be non-NULL");
   for (int l = 0; l < BS_NET_LAYERS; ++l)
     if (!grad->g[l]) return net_invalid("gradient buffers must be non-NULL");
   const NetWs w = carve_net(ws, n, side);
@@ -1155,8 +1188,8 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
   BS_TRY(net_forward(net, patches, n, side, w, s));
   const int grid = side >> 5, cells = n * grid * grid;
   BS_CUDA(cudaMemsetAsync(loss_out, 0, sizeof(double), s));
-  net_head_kernel<<<div_up(cells, 128), 128, 0, s>>>(w.head, cells, grid, 32.f, BS_NET_REACH, nullptr, nullptr,
-                                                     nullptr, t_ctrl, t_color, t_opac, loss_out, w.dhead);
+  net_head_kernel<<<div_up(cells, 128), 128, 0, s>>>(w.head, cells, grid, 32.f, BS_NET_REACH, BS_NET_WIDTH_MAX,
+                                                     bs_net_curves{}, *target, loss_out, w.dhead);
   BS_LAUNCHED("net_head_kernel");
   for (int l = 0; l < BS_NET_LAYERS; ++l)
     BS_CUDA(cudaMemsetAsync(grad->g[l], 0, sizeof(float) * net_param_count(l), s));

@@ -1,23 +1,26 @@
 """Learned initialisation of curves: a convolutional proposal network
 (bs_net_* calls) trained on curve sets the method itself optimised.
 
-Pairs.  A pair is a procedural 256 x 256 patch and the 64 closed curves the
-method reaches on it from the circular initialisation of Section 4.1 (one
-circle of radius 10 px per 32 x 32 cell, the cell's mean target colour,
-opacity 0.8), after `steps` Adam steps of the batched path (64 patches per
-batch, one CUDA-graph replay per step).  Curve i stays the curve of cell i,
-which gives the network a fixed slot per cell.
+Pairs.  A pair is a procedural 256 x 256 patch and the 64 closed curves and
+64 open strokes the method reaches on it from the baseline initialisation,
+one of each per 32 x 32 cell: the circle of Section 4.1 (radius 10 px) and a
+horizontal stroke through the cell centre (20 px long, width 2 px), both in
+the cell's mean target colour at opacity 0.8, after `steps` Adam steps of
+the batched path (64 patches per batch, one CUDA-graph replay per step).
+Curve i of either kind stays the curve of cell i, which gives the network a
+fixed slot per cell.
 
 Network.  bs.h describes it: five stride-2 4 x 4 convolutions and a 1 x 1
 head, bf16 tensor-core GEMMs with float32 accumulation; the head's bias
-starts at the circular initialisation, so an untrained network proposes
-exactly the baseline circles (with colour 0.5).  Training minimises the
+starts at the baseline initialisation, so an untrained network proposes
+exactly the baseline curves (with colour 0.5).  Training minimises the
 mean squared distance to the optimised curves (control points in units of
-the 24 px reach) with Adam (bs_adam_step) on float32 master weights.
+the 24 px reach, widths of the 8 px largest width) with Adam
+(bs_adam_step) on float32 master weights.
 
-Use.  A large target is cut into 256 x 256 patches; each patch's 64
-proposals, shifted to the patch's place, initialise the method on the whole
-image.  Without the network the same image starts from the circles.
+Use.  A large target is cut into 256 x 256 patches; each patch's proposals,
+shifted to the patch's place, initialise the method on the whole image.
+Without the network the same image starts from the baseline curves.
 """
 
 from __future__ import annotations
@@ -36,6 +39,8 @@ GRID = SIDE // CELL
 CELLS = GRID * GRID
 RADIUS = 10.0
 OPACITY = 0.8
+STROKE_HALF = 10.0    # the baseline stroke runs from x - 10 to x + 10 px
+STROKE_WIDTH = 2.0
 # pair generation: a faster control-point step than the paper's 15k-step
 # schedule, so that a few hundred steps move the curves (same for both arms
 # of the evaluation)
@@ -50,29 +55,42 @@ def circle_points(cx, cy, r):
     return np.stack([cx[..., None] + r * np.cos(a), cy[..., None] + r * np.sin(a)], -1)
 
 
-def circle_init(n_patches: int, side: int = SIDE, target: np.ndarray = None):
-    """Closed-curve arrays of the circular initialisation for n patches of
-    side `side` (curves patch by patch, cells row-major), in patch pixels;
-    colours the cells' mean target colours (0.5 without a target)."""
+def stroke_points(cx, cy, half):
+    """10 control points evenly along the horizontal segment from
+    (cx - half, cy) to (cx + half, cy): an open curve of three segments."""
+    x = half * (2.0 * np.arange(10) / 9.0 - 1.0)
+    return np.stack([cx[..., None] + x, np.broadcast_to(cy[..., None], cy.shape + (10,))], -1)
+
+
+def baseline_init(n_patches: int, side: int = SIDE, target: np.ndarray = None) -> dict:
+    """The baseline curves of n patches of side `side` (curves patch by
+    patch, cells row-major; keys bs.NET_CURVE_KEYS, float32 [n cells, ...],
+    patch pixels): per cell a circle and a stroke, colours the cells' mean
+    target colours (0.5 without a target)."""
     g = side // CELL
     gy, gx = np.meshgrid(np.arange(g), np.arange(g), indexing="ij")
     cx = np.broadcast_to((gx.reshape(-1) + 0.5) * CELL, (n_patches, g * g))
     cy = np.broadcast_to((gy.reshape(-1) + 0.5) * CELL, (n_patches, g * g))
-    ctrl = circle_points(cx, cy, RADIUS).reshape(n_patches * g * g, 12, 2).astype(np.float32)
+    m = n_patches * g * g
     if target is None:
-        color = np.full((n_patches * g * g, 3), 0.5, np.float32)
+        color = np.full((m, 3), 0.5, np.float32)
     else:
         t = np.asarray(target, dtype=np.float64).reshape(n_patches, 3, g, CELL, g, CELL)
         color = np.clip(t.mean(axis=(3, 5)), 0.0, 1.0).transpose(0, 2, 3, 1).reshape(-1, 3).astype(np.float32)
-    opac = np.full(n_patches * g * g, OPACITY, np.float32)
-    return ctrl, color, opac
+    return dict(ctrl=circle_points(cx, cy, RADIUS).reshape(m, 12, 2).astype(np.float32), color=color,
+                opac=np.full(m, OPACITY, np.float32),
+                open_ctrl=stroke_points(cx, cy, STROKE_HALF).reshape(m, 10, 2).astype(np.float32),
+                open_width=np.full(m, STROKE_WIDTH, np.float32), open_color=color.copy(),
+                open_opac=np.full((m, 3), OPACITY, np.float32))
 
 
-def _closed_set(ctrl, color, opac, device):
-    z2, z1 = np.zeros((0, 10, 2), np.float32), np.zeros((0,), np.float32)
-    return bs.CurveSet.from_arrays(dict(open_ctrl=z2, open_width=z1, open_color=np.zeros((0, 3), np.float32),
-                                        open_opac=np.zeros((0, 3), np.float32), closed_ctrl=ctrl,
-                                        closed_color=color, closed_opac=opac), device=device)
+def _curve_set(d: dict, device):
+    """CurveSet of a dict of bs.NET_CURVE_KEYS arrays (flat over curves)."""
+    a = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in d.items()}
+    return bs.CurveSet.from_arrays(dict(open_ctrl=a["open_ctrl"], open_width=a["open_width"],
+                                        open_color=a["open_color"], open_opac=a["open_opac"],
+                                        closed_ctrl=a["ctrl"], closed_color=a["color"], closed_opac=a["opac"]),
+                                   device=device)
 
 
 _POOL = None
@@ -95,22 +113,28 @@ def _targets(seeds, n_shapes, workers):
     return np.stack(_POOL.map(_target, [(s, n_shapes) for s in seeds], chunksize=max(1, len(seeds) // workers)))
 
 
+PAIR_KEYS = ("patches",) + bs.NET_CURVE_KEYS
+_FROM_SET = dict(ctrl="closed_ctrl", color="closed_color", opac="closed_opac", open_ctrl="open_ctrl",
+                 open_width="open_width", open_color="open_color", open_opac="open_opac")
+
+
 def make_pairs(n: int, seed: int, steps: int = 200, n_shapes: int = 6, device="cuda", batch: int = 64,
-               sample=(4, 8), workers: int = 0):
+               sample=(4, 8, 8), workers: int = 0):
     """n (patch, optimised curves) pairs.  Returns device tensors patches
-    [n, 3, 256, 256], ctrl [n, 64, 12, 2], color [n, 64, 3], opac [n, 64];
-    control points clamped to the network's reach around their cell.
-    workers: host processes drawing the patches (0: the host's cores)."""
+    [n, 3, 256, 256] and the curves [n, 64, ...] under bs.NET_CURVE_KEYS;
+    control points clamped to the network's reach around their cell, widths
+    into the network's range.  sample: (rows, k) of the closed curves and
+    the samples per open segment.  workers: host processes drawing the
+    patches (0: the host's cores)."""
     import os
     workers = workers or min(16, os.cpu_count() or 1)
-    rows, kc = sample
-    out = {"patches": [], "ctrl": [], "color": [], "opac": []}
+    rows, kc, g_open = sample
+    out = {k: [] for k in PAIR_KEYS}
     for b0 in range(0, n, batch):
         m = min(batch, n - b0)
         tg = _targets([seed * 100003 + b0 + i for i in range(m)], n_shapes, workers)
-        ctrl, color, opac = circle_init(m, SIDE, tg)
-        curves = _closed_set(ctrl, color, opac, device)
-        images = [bs.BatchImage(SIDE, SIDE, 0, CELLS, bs.SampleCfg(g_open=2, rows_closed=rows, k_closed=kc))
+        curves = _curve_set(baseline_init(m, SIDE, tg), device)
+        images = [bs.BatchImage(SIDE, SIDE, CELLS, CELLS, bs.SampleCfg(g_open=g_open, rows_closed=rows, k_closed=kc))
                   for _ in range(m)]
         target = torch.as_tensor(tg.reshape(-1), device=device)
         r = BatchRasterizer(images, pair_capacity=1 << 22, device=device)
@@ -118,16 +142,52 @@ def make_pairs(n: int, seed: int, steps: int = 200, n_shapes: int = 6, device="c
         for _ in range(steps):
             opt.step()
         out["patches"].append(torch.as_tensor(tg, device=device))
-        out["ctrl"].append(curves.closed_ctrl.view(m, CELLS, 12, 2).clone())
-        out["color"].append(curves.closed_color.view(m, CELLS, 3).clone())
-        out["opac"].append(curves.closed_opac.view(m, CELLS).clone())
+        for k in bs.NET_CURVE_KEYS:
+            v = getattr(curves, _FROM_SET[k])
+            out[k].append(v.view((m, CELLS) + tuple(v.shape[1:])).clone())
     res = {k: torch.cat(v, 0) for k, v in out.items()}
     g = torch.arange(GRID, device=device, dtype=torch.float32)
     cy, cx = torch.meshgrid((g + 0.5) * CELL, (g + 0.5) * CELL, indexing="ij")
     centre = torch.stack([cx.reshape(-1), cy.reshape(-1)], -1)[None, :, None, :]
     lim = 0.98 * bs.NET_REACH
-    res["ctrl"] = (centre + (res["ctrl"] - centre).clamp(-lim, lim)).contiguous()
+    for k in ("ctrl", "open_ctrl"):
+        res[k] = (centre + (res[k] - centre).clamp(-lim, lim)).contiguous()
+    res["open_width"] = res["open_width"].clamp(0.02 * bs.NET_WIDTH_MAX, 0.98 * bs.NET_WIDTH_MAX).contiguous()
     return res
+
+
+def initial_weights(seed: int = 0):
+    """The master arrays of the six layers (float32, the library's layout):
+    He-uniform convolutions, a small random head whose bias is the baseline
+    initialisation (so that a zero feature map proposes the baseline curves
+    with colour 0.5)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for l in range(bs.NET_LAYERS):
+        n = bs.net_param_count(l)
+        if l < 5:
+            cin, cout, ks = KERNEL_CH[l], KERNEL_CH[l + 1], 4
+            fan_in = ks * ks * (3 if l == 0 else cin)
+        else:
+            cin, cout, ks, fan_in = 256, 64, 1, 256
+        nw = cout * ks * ks * cin
+        bound = math.sqrt(6.0 / fan_in) * (0.1 if l == 5 else 1.0)
+        w = np.zeros(n, np.float32)
+        w[:nw] = rng.uniform(-bound, bound, nw)
+        if l == 0:   # the padding channels 3..7 of the input carry nothing
+            w[:nw].reshape(cout, ks, ks, cin)[..., 3:] = 0.0
+        if l == 5:
+            a = 2.0 * np.pi * np.arange(12) / 12.0
+            off = RADIUS / bs.NET_REACH
+            b = w[nw:]
+            b[0:24:2] = np.arctanh(off * np.cos(a))
+            b[1:24:2] = np.arctanh(off * np.sin(a))
+            b[27] = math.log(OPACITY / (1.0 - OPACITY))
+            b[28:48:2] = np.arctanh(STROKE_HALF / bs.NET_REACH * (2.0 * np.arange(10) / 9.0 - 1.0))
+            b[48] = math.log(STROKE_WIDTH / (bs.NET_WIDTH_MAX - STROKE_WIDTH))
+            b[52:55] = math.log(OPACITY / (1.0 - OPACITY))
+        out.append(w)
+    return out
 
 
 class InitNet:
@@ -136,31 +196,10 @@ class InitNet:
 
     def __init__(self, device="cuda", seed: int = 0, lr: float = 1e-3):
         self.device = device
-        rng = np.random.default_rng(seed)
-        self.w, self.w_bf16, self.g = [], [], []
-        for l in range(bs.NET_LAYERS):
-            n = bs.net_param_count(l)
-            if l < 5:
-                cin, cout, ks = KERNEL_CH[l], KERNEL_CH[l + 1], 4
-                fan_in = ks * ks * (3 if l == 0 else cin)
-            else:
-                cin, cout, ks, fan_in = 256, 32, 1, 256
-            nw = cout * ks * ks * cin
-            bound = math.sqrt(6.0 / fan_in) * (0.1 if l == 5 else 1.0)
-            w = np.zeros(n, np.float32)
-            w[:nw] = rng.uniform(-bound, bound, nw)
-            if l == 0:   # the padding channels 3..7 of the input carry nothing
-                w[:nw].reshape(cout, ks, ks, cin)[..., 3:] = 0.0
-            if l == 5:   # head bias: the circular initialisation (colour 0.5)
-                a = 2.0 * np.pi * np.arange(12) / 12.0
-                off = RADIUS / bs.NET_REACH
-                b = w[nw:]
-                b[0:24:2] = np.arctanh(off * np.cos(a))
-                b[1:24:2] = np.arctanh(off * np.sin(a))
-                b[27] = math.log(OPACITY / (1.0 - OPACITY))
-            self.w.append(torch.as_tensor(w, device=device))
-            self.w_bf16.append(torch.empty(nw, dtype=torch.int16, device=device))
-            self.g.append(torch.zeros(n, dtype=torch.float32, device=device))
+        self.w = [torch.as_tensor(w, device=device) for w in initial_weights(seed)]
+        self.w_bf16 = [torch.empty(bs.net_param_count(l) - (64 if l == 5 else KERNEL_CH[l + 1]), dtype=torch.int16,
+                                   device=device) for l in range(bs.NET_LAYERS)]
+        self.g = [torch.zeros_like(w) for w in self.w]
         self.m = [torch.zeros_like(x) for x in self.w]
         self.v = [torch.zeros_like(x) for x in self.w]
         self.t = torch.zeros(1, dtype=torch.int32, device=device)
@@ -175,20 +214,19 @@ class InitNet:
             self._ws[key] = torch.empty(bs.net_workspace(n, side), dtype=torch.uint8, device=self.device)
         return self._ws[key]
 
-    def propose(self, patches: torch.Tensor):
-        """ctrl [n, cells, 12, 2] (patch pixels), color [n, cells, 3], opac [n, cells]."""
+    def propose(self, patches: torch.Tensor) -> dict:
+        """The proposals of patches [n, 3, side, side]: bs.NET_CURVE_KEYS ->
+        [n, cells, ...] (patch pixels)."""
         n, side = int(patches.shape[0]), int(patches.shape[-1])
         cells = (side // CELL) ** 2
-        ctrl = torch.empty(n, cells, 12, 2, device=self.device)
-        color = torch.empty(n, cells, 3, device=self.device)
-        opac = torch.empty(n, cells, device=self.device)
-        bs.net_forward(self.w, self.w_bf16, patches.contiguous(), self.ws(n, side), ctrl=ctrl, color=color, opac=opac)
-        return ctrl, color, opac
+        out = {k: torch.empty((n, cells) + shape, device=self.device) for k, shape in bs.NET_CURVE_SHAPES.items()}
+        bs.net_forward(self.w, self.w_bf16, patches.contiguous(), self.ws(n, side), curves=out)
+        return out
 
-    def train_step(self, patches, t_ctrl, t_color, t_opac):
+    def train_step(self, patches, targets: dict):
         """Forward, backward, Adam, bf16 copies; the loss (device double)."""
         n, side = int(patches.shape[0]), int(patches.shape[-1])
-        bs.net_train_step(self.w, self.w_bf16, self.g, patches, t_ctrl, t_color, t_opac, self.ws(n, side), self.loss)
+        bs.net_train_step(self.w, self.w_bf16, self.g, patches, targets, self.ws(n, side), self.loss)
         bs.adam_step(self.groups, self.t)
         bs.net_sync_weights(self.w, self.w_bf16)
         return self.loss
@@ -202,11 +240,8 @@ def train(net: InitNet, data: dict, steps: int, batch: int = 64, seed: int = 0):
     losses = torch.empty(steps, dtype=torch.float64, device=net.device)
     for i in range(steps):
         idx = torch.randint(0, n, (min(batch, n),), generator=gen).to(net.device)
-        p = data["patches"].index_select(0, idx).contiguous()
-        c = data["ctrl"].index_select(0, idx).contiguous()
-        col = data["color"].index_select(0, idx).contiguous()
-        o = data["opac"].index_select(0, idx).contiguous()
-        losses[i] = net.train_step(p, c, col, o)
+        b = {k: data[k].index_select(0, idx).contiguous() for k in PAIR_KEYS}
+        losses[i] = net.train_step(b.pop("patches"), b)
     return losses.cpu().numpy()
 
 
@@ -218,43 +253,44 @@ def image_patches(target: torch.Tensor):
     return p.reshape(-1, 3, SIDE, SIDE).contiguous()
 
 
-def to_image(ctrl, color, opac, H: int, W: int):
-    """Patch proposals [n, cells, ...] -> closed curves of the whole image
-    (patch origins added)."""
-    py, px = torch.meshgrid(torch.arange(H // SIDE, device=ctrl.device), torch.arange(W // SIDE, device=ctrl.device),
-                            indexing="ij")
+def to_image(props: dict, H: int, W: int) -> dict:
+    """Patch proposals [n, cells, ...] -> the curves of the whole image
+    (patch origins added to the control points, flat over curves)."""
+    dev = props["ctrl"].device
+    py, px = torch.meshgrid(torch.arange(H // SIDE, device=dev), torch.arange(W // SIDE, device=dev), indexing="ij")
     origin = torch.stack([px.reshape(-1), py.reshape(-1)], -1).float() * SIDE
-    c = ctrl + origin[:, None, None, :]
-    return c.reshape(-1, 12, 2), color.reshape(-1, 3), opac.reshape(-1)
+    out = {}
+    for k, v in props.items():
+        if k in ("ctrl", "open_ctrl"):
+            v = v + origin[:, None, None, :]
+        out[k] = v.reshape((-1,) + tuple(v.shape[2:]))
+    return out
 
 
 def initial_curves(target: torch.Tensor, net: InitNet = None):
-    """Closed curves initialising the method on target [3, H, W]: the
-    network's proposals, or (net None) the circular initialisation."""
+    """The curves initialising the method on target [3, H, W]: the
+    network's proposals, or (net None) the baseline curves."""
     _, H, W = target.shape
     if net is None:
         n = (H // SIDE) * (W // SIDE)
-        tg = image_patches(target).cpu().numpy()
-        ctrl, color, opac = circle_init(n, SIDE, tg)
-        c, col, o = to_image(torch.as_tensor(ctrl, device=target.device).view(n, CELLS, 12, 2),
-                             torch.as_tensor(color, device=target.device).view(n, CELLS, 3),
-                             torch.as_tensor(opac, device=target.device).view(n, CELLS), H, W)
+        base = baseline_init(n, SIDE, image_patches(target).cpu().numpy())
+        props = {k: torch.as_tensor(v, device=target.device).view((n, CELLS) + v.shape[1:]) for k, v in base.items()}
     else:
-        c, col, o = to_image(*net.propose(image_patches(target)), H, W)
-    return _closed_set(c.cpu().numpy(), col.cpu().numpy(), o.cpu().numpy(), target.device)
+        props = net.propose(image_patches(target))
+    return _curve_set(to_image(props, H, W), target.device)
 
 
-def optimise(target: torch.Tensor, curves: bs.CurveSet, steps: int, sample=(4, 8), every: int = 10,
+def optimise(target: torch.Tensor, curves: bs.CurveSet, steps: int, sample=(4, 8, 8), every: int = 10,
              cfg: AdamCfg = PAIR_ADAM):
     """The method on one image from `curves` (in place): PSNR every `every`
     steps (index 0 = the initial curves) and the ms per step."""
     from .raster import Rasterizer
     _, H, W = target.shape
-    rows, kc = sample
-    r = Rasterizer(bs.Canvas(W, H, 16), bs.SampleCfg(g_open=2, rows_closed=rows, k_closed=kc), 0, curves.n_closed,
-                   device=target.device, pair_capacity=1 << 22)
+    rows, kc, g_open = sample
+    r = Rasterizer(bs.Canvas(W, H, 16), bs.SampleCfg(g_open=g_open, rows_closed=rows, k_closed=kc), curves.n_open,
+                   curves.n_closed, device=target.device, pair_capacity=1 << 22)
     grad = curves.zeros_like()
-    adam = CurveAdam(curves, grad, [bs.BatchImage(W, H, 0, curves.n_closed, r.cfg)], cfg, target.device)
+    adam = CurveAdam(curves, grad, [bs.BatchImage(W, H, curves.n_open, curves.n_closed, r.cfg)], cfg, target.device)
     psnr = []
     t_ms = 0.0
     for i in range(steps + 1):
@@ -283,7 +319,7 @@ def train_flops(n: int, side: int = SIDE) -> float:
             ho = side >> (l + 1)
             m, k, co = n * ho * ho, 16 * KERNEL_CH[l], KERNEL_CH[l + 1]
         else:
-            m, k, co = n * (side // CELL) ** 2, 256, 32
+            m, k, co = n * (side // CELL) ** 2, 256, 64
         f = 2.0 * m * k * co
         tot += f * (2 if l == 0 else 3)
     return tot
@@ -296,7 +332,7 @@ def time_forward(n: int = 64, side: int = SIDE, reps: int = 20, engines=(0, 3, 1
     net = InitNet(device=device, seed=1)
     rng = np.random.default_rng(0)
     x = torch.as_tensor(rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32), device=device)
-    head = torch.empty(n, (side // CELL) ** 2, 32, device=device)
+    head = torch.empty(n, (side // CELL) ** 2, 64, device=device)
     out = {}
     try:
         for engine in engines:
@@ -352,13 +388,14 @@ def main(argv=None):
     t_train = time.perf_counter() - learned_t0
     # the network's tensor-core throughput on one training batch
     idx = torch.arange(min(a.batch, a.pairs), device=dev)
-    p, c, col, o = (data[k].index_select(0, idx).contiguous() for k in ("patches", "ctrl", "color", "opac"))
+    b = {k: data[k].index_select(0, idx).contiguous() for k in PAIR_KEYS}
+    p = b.pop("patches")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(3):
-        net.train_step(p, c, col, o)
+        net.train_step(p, b)
     e0.record()
     for _ in range(10):
-        net.train_step(p, c, col, o)
+        net.train_step(p, b)
     e1.record()
     torch.cuda.synchronize()
     step_ms = e0.elapsed_time(e1) / 10
@@ -366,27 +403,27 @@ def main(argv=None):
     for i in range(a.targets):
         tg = torch.as_tensor(synth.procedural_target(7000 + i, a.side, a.side, 200), device=dev)
         res = {}
-        for name, m in (("circles", None), ("learned", net)):
+        for name, m in (("baseline", None), ("learned", net)):
             s0 = time.perf_counter()
             curves = initial_curves(tg, m)
             torch.cuda.synchronize()
             init_ms = (time.perf_counter() - s0) * 1e3
             psnr, ms = optimise(tg, curves, a.eval_steps, every=a.every)
             res[name] = dict(psnr=[round(x, 3) for x in psnr], ms_per_step=round(ms, 4), init_ms=round(init_ms, 2))
-        goal = res["circles"]["psnr"][-1]
+        goal = res["baseline"]["psnr"][-1]
         hit = next((j for j, x in enumerate(res["learned"]["psnr"]) if x >= goal), None)
         steps_learned = None if hit is None else min(a.eval_steps, hit * a.every)
-        res["circles_final_db"] = goal
-        res["learned_steps_to_circles_final"] = steps_learned
-        res["circles_steps"] = a.eval_steps
+        res["baseline_final_db"] = goal
+        res["learned_steps_to_baseline_final"] = steps_learned
+        res["baseline_steps"] = a.eval_steps
         if steps_learned is not None:
-            t_c = a.eval_steps * res["circles"]["ms_per_step"] + res["circles"]["init_ms"]
+            t_c = a.eval_steps * res["baseline"]["ms_per_step"] + res["baseline"]["init_ms"]
             t_l = steps_learned * res["learned"]["ms_per_step"] + res["learned"]["init_ms"]
-            res["wall_ms_circles"] = round(t_c, 2)
+            res["wall_ms_baseline"] = round(t_c, 2)
             res["wall_ms_learned"] = round(t_l, 2)
         evals.append(res)
     out = {
-        "what": "learned initialisation vs circular initialisation of the method",
+        "what": "learned initialisation vs the baseline initialisation of the method (circles and strokes)",
         "pairs": {"n": a.pairs, "optimiser_steps": a.pair_steps, "seconds": round(t_pairs, 2)},
         "train": {"steps": a.train_steps, "batch": a.batch, "seconds": round(t_train, 2),
                   "loss_first": round(float(losses[:10].mean()), 5), "loss_last": round(float(losses[-10:].mean()), 5),

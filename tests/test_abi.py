@@ -163,3 +163,23 @@ def test_adam_rejects_bad_groups(bs):
     bad = bs.bs_adam_cfg(1.0, 0.999, 1e-8)
     ok = (bs.bs_adam_group * 1)(bs.bs_adam_group(None, None, None, None, 0, 0.1, 0.0, 1.0, None, 1))
     assert bs.lib.bs_adam_step(ok, 1, ctypes.byref(bad), ctypes.c_void_p(256), None) == bs.BS_ERR_INVALID_ARG
+
+
+def test_net_host_arithmetic_and_validation(bs):
+    """The head holds 64 outputs of 256 features; a training step refuses a
+    missing target array before it touches the device."""
+    assert bs.lib.bs_net_param_count(5) == 64 * 256 + 64
+    assert bs.lib.bs_net_param_count(0) == 32 * 16 * 8 + 32
+    assert bs.lib.bs_net_param_count(6) == -1
+    fake = ctypes.c_void_p(256)
+    net = bs.bs_net((ctypes.c_void_p * bs.NET_LAYERS)(*([fake.value] * bs.NET_LAYERS)),
+                    (ctypes.c_void_p * bs.NET_LAYERS)(*([fake.value] * bs.NET_LAYERS)))
+    grad = bs.bs_net_grad((ctypes.c_void_p * bs.NET_LAYERS)(*([fake.value] * bs.NET_LAYERS)))
+    tgt = bs.bs_net_curves(**{k: fake.value for k in bs.NET_CURVE_KEYS})
+    tgt.open_width = None
+    st = bs.lib.bs_net_train_step(ctypes.byref(net), fake, 1, 64, ctypes.byref(tgt), fake, 1 << 30,
+                                  ctypes.byref(grad), fake, None)
+    assert st == bs.BS_ERR_INVALID_ARG and b"target" in bs.lib.bs_last_error()
+    st = bs.lib.bs_net_train_step(ctypes.byref(net), fake, 1, 48, ctypes.byref(tgt), fake, 1 << 30,
+                                  ctypes.byref(grad), fake, None)
+    assert st == bs.BS_ERR_INVALID_ARG    # side not a multiple of 32

@@ -1,6 +1,6 @@
 """The learned initialiser (bs_net_*): forward and gradients of the
 proposal network against the float64 oracle, training, and what the trained
-network gains over the circular initialisation.
+network gains over the baseline initialisation (circles and strokes).
 
 Tolerances.  The library keeps activations and their gradients in bfloat16
 (8 significand bits: a relative rounding step of 2^-8) and sums in float32.
@@ -32,7 +32,7 @@ def _rand_net(learned, seed):
     import paper_2503_16424_gb300.bs as bs
     n = learned.InitNet(seed=seed)
     rng = np.random.default_rng(seed)
-    nw = 32 * 256
+    nw = 64 * 256
     n.w[5][:nw] = torch.as_tensor(rng.normal(0, 0.05, nw).astype(np.float32), device="cuda")
     bs.net_sync_weights(n.w, n.w_bf16)
     return n
@@ -45,21 +45,35 @@ def test_forward_matches_oracle(learned, n, side):
     rng = np.random.default_rng(side)
     x = rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32)
     cells = (side // 32) ** 2
-    head = torch.empty(n, cells, 32, device="cuda")
-    ctrl = torch.empty(n, cells, 12, 2, device="cuda")
-    color = torch.empty(n, cells, 3, device="cuda")
-    opac = torch.empty(n, cells, device="cuda")
-    bs.net_forward(net.w, net.w_bf16, torch.as_tensor(x, device="cuda"), net.ws(n, side), head, ctrl, color, opac)
+    head = torch.empty(n, cells, 64, device="cuda")
+    props = {k: torch.empty((n, cells) + sh, device="cuda") for k, sh in bs.NET_CURVE_SHAPES.items()}
+    bs.net_forward(net.w, net.w_bf16, torch.as_tensor(x, device="cuda"), net.ws(n, side), head, props)
     torch.cuda.synchronize()
     ref, _ = onet.forward(onet.unpack([w.cpu().numpy() for w in net.w], round_bf16=True), x, round_bf16=True)
     got = head.cpu().double()
     err = float((got - ref).abs().max() / ref.abs().max())
     print(f"head rel err {err:.2e}")
     assert err <= 1e-2
-    rc, rcol, rop = onet.head_curves(got, side)      # the mapping of the GPU's own head outputs
-    assert torch.allclose(ctrl.cpu().double(), rc, atol=2e-4)
-    assert torch.allclose(color.cpu().double(), rcol, atol=1e-5)
-    assert torch.allclose(opac.cpu().double(), rop, atol=1e-5)
+    ref_p = onet.head_curves(got, side)      # the mapping of the GPU's own head outputs
+    for k in onet.CURVE_KEYS:    # pixels: a few float32 ulps of 256; units and widths: of 1 and 8
+        atol = {"ctrl": 2e-4, "open_ctrl": 2e-4, "open_width": 1e-5 * onet.WIDTH_MAX}.get(k, 1e-5)
+        assert torch.allclose(props[k].cpu().double(), ref_p[k], atol=atol), k
+    # a subset of outputs: the others stay untouched
+    sub = dict(open_width=torch.full((n, cells), -1.0, device="cuda"))
+    bs.net_forward(net.w, net.w_bf16, torch.as_tensor(x, device="cuda"), net.ws(n, side), None, sub)
+    assert torch.allclose(sub["open_width"].cpu().double(), ref_p["open_width"], atol=1e-5 * onet.WIDTH_MAX)
+
+
+def _targets(rng, n, cells, side):
+    """Random target curves, numpy float32, bs.NET_CURVE_KEYS -> [n, cells, ...]."""
+    return dict(ctrl=rng.uniform(0, side, (n, cells, 12, 2)), color=rng.uniform(0, 1, (n, cells, 3)),
+                opac=rng.uniform(0, 1, (n, cells)), open_ctrl=rng.uniform(0, side, (n, cells, 10, 2)),
+                open_width=rng.uniform(0.5, 7.5, (n, cells)), open_color=rng.uniform(0, 1, (n, cells, 3)),
+                open_opac=rng.uniform(0, 1, (n, cells, 3)))
+
+
+def _dev(t):
+    return {k: torch.as_tensor(np.asarray(v, np.float32), device="cuda") for k, v in t.items()}
 
 
 def test_train_step_gradients_match_oracle(learned):
@@ -68,14 +82,11 @@ def test_train_step_gradients_match_oracle(learned):
     rng = np.random.default_rng(9)
     n, side = 2, 64
     x = rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32)
-    t_ctrl = rng.uniform(0, side, (n, 4, 12, 2)).astype(np.float32)
-    t_color = rng.uniform(0, 1, (n, 4, 3)).astype(np.float32)
-    t_opac = rng.uniform(0, 1, (n, 4)).astype(np.float32)
-    dev = {k: torch.as_tensor(v, device="cuda") for k, v in dict(x=x, c=t_ctrl, col=t_color, o=t_opac).items()}
+    t = {k: np.asarray(v, np.float32) for k, v in _targets(rng, n, 4, side).items()}
     loss = torch.zeros((), dtype=torch.float64, device="cuda")
-    bs.net_train_step(net.w, net.w_bf16, net.g, dev["x"], dev["c"], dev["col"], dev["o"], net.ws(n, side), loss)
+    bs.net_train_step(net.w, net.w_bf16, net.g, torch.as_tensor(x, device="cuda"), _dev(t), net.ws(n, side), loss)
     torch.cuda.synchronize()
-    L, ref = onet.loss_and_grads([w.cpu().numpy() for w in net.w], x, t_ctrl, t_color, t_opac, round_bf16=True)
+    L, ref = onet.loss_and_grads([w.cpu().numpy() for w in net.w], x, t, round_bf16=True)
     assert abs(float(loss) - L) <= 2e-2 * abs(L)
     for l in range(6):
         got = net.g[l].cpu().double().numpy()
@@ -86,10 +97,11 @@ def test_train_step_gradients_match_oracle(learned):
         assert err <= 2e-2 and cos >= 0.9999, l
 
 
-def test_training_fits_pairs_and_beats_the_circles(learned):
+def test_training_fits_pairs_and_beats_the_baseline(learned):
     """Pairs from the batched method, a short training, then on held-out
-    512 x 512 targets: the proposals start and stay above the circular
-    initialisation under the same Adam steps of the method."""
+    512 x 512 targets: the proposals (closed curves and open strokes) start
+    and stay above the baseline initialisation under the same Adam steps of
+    the method."""
     data = learned.make_pairs(256, seed=1, steps=150)
     net = learned.InitNet(seed=0, lr=2e-3)
     losses = learned.train(net, data, steps=300, batch=32)
@@ -100,13 +112,14 @@ def test_training_fits_pairs_and_beats_the_circles(learned):
     for seed in (901, 902):
         tg = torch.as_tensor(synth.procedural_target(seed, 512, 512, 24), device="cuda")
         res = {}
-        for name, m in (("circles", None), ("learned", net)):
+        for name, m in (("baseline", None), ("learned", net)):
             curves = learned.initial_curves(tg, m)
+            assert curves.n_open == curves.n_closed == 256
             psnr, _ = learned.optimise(tg, curves, steps=60, every=30)
             res[name] = psnr
         print(seed, {k: np.round(v, 2) for k, v in res.items()})
-        gains0.append(res["learned"][0] - res["circles"][0])
-        gains.append(res["learned"][-1] - res["circles"][-1])
+        gains0.append(res["learned"][0] - res["baseline"][0])
+        gains.append(res["learned"][-1] - res["baseline"][-1])
     assert min(gains0) > 0.0 and min(gains) > 0.0
 
 
@@ -122,16 +135,14 @@ def test_tcgen05_and_mma_sync_engines_agree(learned):
     n, side = 3, 96
     x = torch.as_tensor(rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32), device="cuda")
     cells = (side // 32) ** 2
-    t_ctrl = torch.as_tensor(rng.uniform(0, side, (n, cells, 12, 2)).astype(np.float32), device="cuda")
-    t_color = torch.as_tensor(rng.uniform(0, 1, (n, cells, 3)).astype(np.float32), device="cuda")
-    t_opac = torch.as_tensor(rng.uniform(0, 1, (n, cells)).astype(np.float32), device="cuda")
+    tg = _dev(_targets(rng, n, cells, side))
     out = {}
     for engine in (0, 2):
         bs.debug_gemm_engine(engine)
-        head = torch.empty(n, cells, 32, device="cuda")
+        head = torch.empty(n, cells, 64, device="cuda")
         bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), head)
         loss = torch.zeros((), dtype=torch.float64, device="cuda")
-        bs.net_train_step(net.w, net.w_bf16, net.g, x, t_ctrl, t_color, t_opac, net.ws(n, side), loss)
+        bs.net_train_step(net.w, net.w_bf16, net.g, x, tg, net.ws(n, side), loss)
         torch.cuda.synchronize()
         out[engine] = (head.cpu().double(), [g.cpu().double() for g in net.g], float(loss))
     timeouts = bs.debug_gemm_engine(1)
@@ -158,31 +169,29 @@ def test_a_tensor_core_wait_that_gives_up_fails_the_call_and_the_next_call_is_ex
     n, side = 2, 64
     x = torch.as_tensor(rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32), device="cuda")
     cells = (side // 32) ** 2
-    t_ctrl = torch.as_tensor(rng.uniform(0, side, (n, cells, 12, 2)).astype(np.float32), device="cuda")
-    t_color = torch.as_tensor(rng.uniform(0, 1, (n, cells, 3)).astype(np.float32), device="cuda")
-    t_opac = torch.as_tensor(rng.uniform(0, 1, (n, cells)).astype(np.float32), device="cuda")
+    tg = _dev(_targets(rng, n, cells, side))
     bs.debug_gemm_engine(2)                      # every GEMM on tcgen05
     try:
-        ref = torch.empty(n, cells, 32, device="cuda")
+        ref = torch.empty(n, cells, 64, device="cuda")
         bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), ref)
         loss = torch.zeros((), dtype=torch.float64, device="cuda")
-        bs.net_train_step(net.w, net.w_bf16, net.g, x, t_ctrl, t_color, t_opac, net.ws(n, side), loss)
+        bs.net_train_step(net.w, net.w_bf16, net.g, x, tg, net.ws(n, side), loss)
         ref_g = [g.clone() for g in net.g]
         before = bs.debug_gemm_engine(2)
         bs.debug_umma_wait(0)
         try:
             with pytest.raises(bs.BSError) as e:
-                bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), torch.empty(n, cells, 32, device="cuda"))
+                bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), torch.empty(n, cells, 64, device="cuda"))
             assert e.value.status == bs.BS_ERR_TIMEOUT
             with pytest.raises(bs.BSError) as e:
-                bs.net_train_step(net.w, net.w_bf16, net.g, x, t_ctrl, t_color, t_opac, net.ws(n, side), loss)
+                bs.net_train_step(net.w, net.w_bf16, net.g, x, tg, net.ws(n, side), loss)
             assert e.value.status == bs.BS_ERR_TIMEOUT
         finally:
             bs.debug_umma_wait(-1)
         assert bs.debug_gemm_engine(2) > before
-        head = torch.empty(n, cells, 32, device="cuda")
+        head = torch.empty(n, cells, 64, device="cuda")
         bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), head)
-        bs.net_train_step(net.w, net.w_bf16, net.g, x, t_ctrl, t_color, t_opac, net.ws(n, side), loss)
+        bs.net_train_step(net.w, net.w_bf16, net.g, x, tg, net.ws(n, side), loss)
         torch.cuda.synchronize()
         assert torch.equal(head, ref)
         for a, b in zip(net.g, ref_g):
@@ -208,7 +217,7 @@ def test_tma_fed_convolutions_agree_with_the_gathered_engines(learned):
         try:
             for engine in (0, 1, 2, 3):
                 bs.debug_gemm_engine(engine)
-                head = torch.empty(n, cells, 32, device="cuda")
+                head = torch.empty(n, cells, 64, device="cuda")
                 bs.net_forward(net.w, net.w_bf16, x, net.ws(n, side), head)
                 torch.cuda.synchronize()
                 heads[engine] = head.cpu().double()
