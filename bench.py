@@ -61,18 +61,18 @@ RENDER_SOURCE = os.path.join(ROOT, "paper_2503_16424_gb300", "csrc", "bs_render.
 # carry over per evaluation; the DRAM bytes (read + write, one launch) from a
 # one-pass capture of the full workload.
 NCU_CAPTURE = {
-    "source_sha256_16": "a84be228cd0d7afb",
+    "source_sha256_16": "8d544da7b8a885f7",
     "workload": "hires_1024_1024",
-    "render_fwd_kernel": {"flop_per_eval": 10.5012, "mufu_per_eval": 0.7677,
-                          "ffma": 636433010, "fadd": 201107114, "fmul": 252587454, "xu": 126225312,
-                          "evals": 164415548, "dram_bytes": 179508736,
-                          "pipes": {"issue_active_pct": 73.3, "fma_pipe_pct": 35.5, "alu_pipe_pct": 40.8,
-                                    "shared_pipe_pct": 17.5, "warps_active_pct": 38.4}},
+    "render_fwd_kernel": {"flop_per_eval": 9.0215, "mufu_per_eval": 0.5828,
+                          "ffma": 569099211, "fadd": 146802257, "fmul": 198282596, "xu": 95816128,
+                          "evals": 164415545, "dram_bytes": 179984384,
+                          "pipes": {"issue_active_pct": 72.0, "fma_pipe_pct": 32.2, "alu_pipe_pct": 41.8,
+                                    "shared_pipe_pct": 18.7, "warps_active_pct": 38.3}},
     "render_bwd_kernel": {"flop_per_eval": 22.6996, "mufu_per_eval": 1.0985,
-                          "ffma": 1094764262, "fadd": 832285333, "fmul": 641605485, "xu": 177279424,
-                          "evals": 161386727, "dram_bytes": 127796224,
-                          "pipes": {"issue_active_pct": 69.8, "fma_pipe_pct": 35.3, "alu_pipe_pct": 40.1,
-                                    "shared_pipe_pct": 34.2, "warps_active_pct": 30.8}},
+                          "ffma": 1094763846, "fadd": 832285173, "fmul": 641605293, "xu": 177278848,
+                          "evals": 161386726, "dram_bytes": 127642112,
+                          "pipes": {"issue_active_pct": 69.9, "fma_pipe_pct": 35.4, "alu_pipe_pct": 40.1,
+                                    "shared_pipe_pct": 35.4, "warps_active_pct": 30.8}},
 }
 
 
