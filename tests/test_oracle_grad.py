@@ -91,3 +91,57 @@ def test_l2_loss_gradient():
     am = a.copy(); am[i] -= h
     fd = (float(oracle.l2_loss(ap, b)[0]) - float(oracle.l2_loss(am, b)[0])) / (2 * h)
     assert abs(fd - float(g[i])) < 1e-8
+
+
+def _conic_blend_loss(curves, cfg, W, H, target, bg):
+    """The loss through a blend written in the conic form of Eq. 11-12,
+    alpha = min(0.99, o exp(-0.5 d^T Sigma^-1 d)) with Sigma^-1 from
+    torch.linalg.inv, walked Gaussian by Gaussian in draw order with the
+    three thresholds (skip below 1/255, stop before T < 1e-4): no use of the
+    eigen-frame fields of the table."""
+    tab = oracle.gaussian_table(curves, cfg)
+    P = torch.linalg.inv(tab["Sigma"])
+    ys, xs = torch.meshgrid(torch.arange(H, dtype=torch.float64), torch.arange(W, dtype=torch.float64),
+                            indexing="ij")
+    px, py = xs.reshape(-1) + 0.5, ys.reshape(-1) + 0.5
+    T = torch.ones_like(px)
+    C = torch.zeros(px.shape[0], 3, dtype=torch.float64)
+    alive = torch.ones_like(px, dtype=torch.bool)
+    for i in range(tab["mx"].shape[0]):
+        dx, dy = px - tab["mx"][i], py - tab["my"][i]
+        q = P[i, 0, 0] * dx * dx + (P[i, 0, 1] + P[i, 1, 0]) * dx * dy + P[i, 1, 1] * dy * dy
+        a = torch.clamp(tab["o"][i] * torch.exp(-0.5 * q), max=0.99)
+        Tn = T * (1.0 - a)
+        use = alive & (a >= 1.0 / 255.0) & (Tn >= 1e-4)
+        alive = alive & ~((a >= 1.0 / 255.0) & (Tn < 1e-4))
+        w = torch.where(use, a * T, torch.zeros_like(a))
+        C = C + w[:, None] * tab["col"][i][None, :]
+        T = torch.where(use, Tn, T)
+    img = (C + T[:, None] * torch.as_tensor(bg, dtype=torch.float64)[None, :]).T.reshape(3, H, W)
+    return ((img - target) ** 2).mean()
+
+
+@pytest.mark.parametrize("seed,W,H,n_open,n_closed", [(3, 10, 9, 2, 1), (4, 12, 8, 1, 2)])
+def test_curve_gradients_match_a_conic_form_blend(seed, W, H, n_open, n_closed):
+    """The oracle stores Gaussians in the eigen-frame (R, S^-1) and takes its
+    table gradients there; the curve gradients must equal those of the
+    conic form of Eq. 11-12 through autograd, which shares none of that
+    parameterisation (the same thresholds, no pixel near one)."""
+    cfg = SampleCfg(g_open=6, rows_closed=3, k_closed=4, eps=0.3)
+    curves, target = _case(seed, W, H, n_open, n_closed, cfg)
+    bg = (0.2, 0.1, 0.4)
+    res = step(curves, cfg, W, H, target, bg)
+    assert not bool(res["flag"].any())
+    leaves = as_curves({k: v.detach().numpy() for k, v in curves.items()}, requires_grad=True)
+    L = _conic_blend_loss(leaves, cfg, W, H, target, bg)
+    assert abs(float(L.detach()) - res["loss"]) <= 1e-12 * abs(res["loss"])
+    gs = torch.autograd.grad(L, [leaves[k] for k in CURVE_KEYS], allow_unused=True)
+    for k, g in zip(CURVE_KEYS, gs):
+        ref = res["dcurves"][k]
+        g = torch.zeros_like(ref) if g is None else g
+        scale = float(ref.abs().max()) if ref.numel() else 0.0
+        if scale == 0.0:
+            assert float(g.abs().max()) == 0.0 if g.numel() else True, k
+            continue
+        assert float((g - ref).abs().max()) <= 1e-9 * scale, k
+    assert float(res["dcurves"]["open_ctrl"].abs().max()) > 0.0
