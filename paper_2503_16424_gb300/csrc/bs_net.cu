@@ -385,6 +385,152 @@ __device__ __forceinline__ void umma_bf16_n128(uint32_t tmem_d, uint64_t a, uint
       : "memory");
 }
 
+// ---- weight gradients fed by the tensor memory accelerator ----
+// For the same convolutions (Cin a multiple of 64, Cout of 128, Ho Wo of
+// 64): dW^T[kk][co] = sum over output pixels m of patch[m][kk] dout[m][co],
+// kk = (tap, ci).  A CTA computes a 128 x 128 tile (kk x co) over one split
+// of the pixels, in chunks of 64 pixels, and adds it to dw with float
+// atomics.  Per chunk one thread issues four TMA loads into a ring of
+// kWStages stages:
+//   A: two im2col loads of the NHWC input (64 output pixels x 64 channels
+//      of one tap: the tile's two 64-wide halves of kk);
+//   B: two tiled loads of dout [M][Cout] (64 pixels x 64 output channels).
+// Every box lands as 64 pixel rows of 128 bytes (128-byte swizzle): the
+// pixels are the GEMM's reduction axis, so both operands are MN-major (the
+// instruction descriptor's transpose bits).  The descriptors advance 2048
+// bytes (16 pixel rows) per K step; the two halves of M (N) lie kWHalf bytes
+// apart and the 8-row groups 1024 bytes apart.  Waits, commits and the
+// error count work as in conv_tma_kernel.
+constexpr int kWStages = 3, kWThreads = 128;
+constexpr uint32_t kWHalf = 64 * 64 * 2;   // bytes of one 64 x 64 box
+constexpr uint32_t kWStage = 4 * kWHalf;   // A's two halves, then B's
+constexpr uint32_t kWSmem = kWStages * kWStage + 1024;
+constexpr uint32_t kWIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                             ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+// MN-major operand descriptor with 128-byte swizzle.
+__device__ __forceinline__ uint64_t umma_desc_sw128_mn(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void umma_bf16_wgrad(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kWIdesc), "r"(accumulate)
+      : "memory");
+}
+
+// grid (K / 128, Cout / 128, splits); split z takes chunks
+// [z per, min(n_chunks, (z + 1) per)) of 64 pixels.
+__global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_constant__ CUtensorMap map_in,
+                                                              const __grid_constant__ CUtensorMap map_dout, int Ho,
+                                                              int Wo, int Cin, int K, int n_chunks, int per,
+                                                              float *__restrict__ dw, unsigned int *err,
+                                                              uint32_t first_wait, uint32_t lbo, uint32_t sbo) {
+  extern __shared__ uint8_t w_smem[];
+  __shared__ __align__(8) uint64_t full[kWStages], empty[kWStages], done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int c0 = blockIdx.z * per, n = min(n_chunks, c0 + per) - c0;
+  if (n <= 0) return;  // uniform over the CTA, before any allocation
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t base = (smem_u32(w_smem) + 1023u) & ~1023u;
+  const int kk0 = blockIdx.x * 128, co0 = blockIdx.y * 128;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(128u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kWStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  if (tid == 0) {
+    // producer; the kk halves: tap and first channel of each
+    const int t0 = kk0 / Cin, ci0 = kk0 - t0 * Cin, t1 = (kk0 + 64) / Cin, ci1 = kk0 + 64 - t1 * Cin;
+    const int hw = Ho * Wo;
+    for (int c = 0; c < n; ++c) {
+      const int st = c % kWStages;
+      if (c >= kWStages && !mbar_wait(&empty[st], (uint32_t)((c / kWStages - 1) & 1))) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      const int m = (c0 + c) * 64, img = m / hw, r = m - img * hw, oy = r / Wo, ox = r - oy * Wo;
+      const uint32_t sa = base + st * kWStage, sb = sa + 2 * kWHalf;
+      mbar_expect_tx(&full[st], kWStage);
+      tma_im2col_4d(sa, &map_in, &full[st], ci0, 2 * ox - 1, 2 * oy - 1, img, (uint16_t)(t0 & 3), (uint16_t)(t0 >> 2));
+      tma_im2col_4d(sa + kWHalf, &map_in, &full[st], ci1, 2 * ox - 1, 2 * oy - 1, img, (uint16_t)(t1 & 3),
+                    (uint16_t)(t1 >> 2));
+      tma_tile_2d(sb, &map_dout, &full[st], co0, m);
+      tma_tile_2d(sb + kWHalf, &map_dout, &full[st], co0 + 64, m);
+    }
+  } else if (tid == 32) {
+    // MMA issuer
+    for (int c = 0; c < n; ++c) {
+      const int st = c % kWStages;
+      if (!mbar_wait(&full[st], (uint32_t)((c / kWStages) & 1))) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = base + st * kWStage, sb = sa + 2 * kWHalf;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t da = umma_desc_sw128_mn(sa + 2048u * ks, lbo, sbo);
+        const uint64_t db = umma_desc_sw128_mn(sb + 2048u * ks, lbo, sbo);
+        umma_bf16_wgrad(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
+      }
+      umma_commit(&empty[st]);
+    }
+    umma_commit(&done);
+  }
+  bool w = mbar_wait(&done, 0u, first_wait);
+  if (!w) {
+    mbar_wait(&done, 0u);
+    if (tid == 0) {
+      atomicAdd(err, 1u);
+      atomicAdd(err + 1, 1u);
+    }
+  }
+  const bool store = __syncthreads_and(w) && s_fail == 0;
+  if (!store && tid == 0 && w) {
+    atomicAdd(err, 1u);
+    atomicAdd(err + 1, 1u);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (store) {
+    const int kk = kk0 + 32 * warp + lane;
+#pragma unroll 4
+    for (int col = 0; col < 128; col += 8) {
+      uint32_t v[8];
+      const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+          "tcgen05.wait::ld.sync.aligned;\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+          : "r"(ta)
+          : "memory");
+#pragma unroll
+      for (int j = 0; j < 8; ++j) atomicAdd(dw + (size_t)(co0 + col + j) * K + kk, __uint_as_float(v[j]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+}
+
 // M = N Ho Wo output pixels, Cout a multiple of kTN, Cin a multiple of kTK;
 // grid (ceil(M / kTM), Cout / kTN).
 __global__ void __launch_bounds__(kTThreads) conv_tma_kernel(const __grid_constant__ CUtensorMap map_in,
@@ -851,6 +997,63 @@ bool uses_tma(const Geom &g) {
          g.Cout % kTN == 0;
 }
 
+// The weight gradient of layer g by wgrad_tma_kernel (the layers conv_tma_kernel runs, with
+// Ho Wo a multiple of 64).
+bs_status run_wgrad_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *dw, cudaStream_t s) {
+  EncodeIm2col enc_im2col;
+  EncodeTiled enc_tiled;
+  BS_TRY(tma_encoders(&enc_im2col, &enc_tiled));
+  CUtensorMap map_in, map_dout;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.Cin, (cuuint64_t)g.Wi, (cuuint64_t)g.Hi, (cuuint64_t)g.N};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.Cin * 2, (cuuint64_t)g.Wi * g.Cin * 2,
+                                 (cuuint64_t)g.Hi * g.Wi * g.Cin * 2};
+  const int lower[2] = {-g.P, -g.P}, upper[2] = {g.P - (g.KS - 1), g.P - (g.KS - 1)};
+  const cuuint32_t estr[4] = {1, (cuuint32_t)g.S, (cuuint32_t)g.S, 1};
+  CUresult r = enc_im2col(&map_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(in), dims, strides,
+                          lower, upper, 64, 64, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeIm2col failed (%d) for a %dx%dx%d input", (int)r, g.Hi, g.Wi, g.Cin);
+    return BS_ERR_CUDA;
+  }
+  const cuuint64_t ddims[2] = {(cuuint64_t)g.Cout, (cuuint64_t)g.M()};
+  const cuuint64_t dstrides[1] = {(cuuint64_t)g.Cout * 2};
+  const cuuint32_t box[2] = {64, 64}, es[2] = {1, 1};
+  r = enc_tiled(&map_dout, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(dout), ddims, dstrides, box,
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for the %dx%d output gradient", (int)r, g.M(), g.Cout);
+    return BS_ERR_CUDA;
+  }
+  unsigned int *err = nullptr;
+  BS_TRY(umma_err_ptr(&err));
+  {
+    constexpr int kMaxDev = 64;
+    static bool attr[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    BS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDev || !attr[dev]) {
+      BS_CUDA(cudaFuncSetAttribute(wgrad_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+      if (dev >= 0 && dev < kMaxDev) attr[dev] = true;
+    }
+  }
+  // splits of the pixels so that about two CTAs per SM run
+  const int tiles = (g.K() / 128) * (g.Cout / 128), n_chunks = g.M() / 64;
+  int splits = std::max(1, std::min(n_chunks, div_up(2 * 152, tiles)));
+  const int per = div_up(n_chunks, splits);
+  splits = div_up(n_chunks, per);
+  const dim3 grid((unsigned)(g.K() / 128), (unsigned)(g.Cout / 128), (unsigned)splits);
+  wgrad_tma_kernel<<<grid, kWThreads, kWSmem, s>>>(map_in, map_dout, g.Ho, g.Wo, g.Cin, g.K(), n_chunks, per, dw, err,
+                                                   g_first_wait, kWHalf, 1024u);
+  BS_LAUNCHED("wgrad_tma_kernel");
+  return BS_OK;
+}
+
+bool uses_tma_wgrad(const Geom &g) { return uses_tma(g) && (g.Ho * g.Wo) % 64 == 0; }
+
 // ---- element-wise pieces ----
 // Planar float32 patches [N][3][H][W] -> NHWC bf16 [N][H][W][8] (channels
 // 3..7 zero).
@@ -898,13 +1101,49 @@ __global__ void net_transpose_kernel(const float *__restrict__ w, int Cin, int C
   wt[i] = __float2bfloat16(w[(size_t)co * Cin + ci]);
 }
 
-// db[co] += sum over m of dout[m][co] (bf16 dout).
-__global__ void net_bias_grad_kernel(const __nv_bfloat16 *__restrict__ dout, int M, int C, float *__restrict__ db) {
-  const int co = blockIdx.y * blockDim.x + threadIdx.x;
-  if (co >= C) return;
-  float acc = 0.f;
-  for (int m = blockIdx.x; m < M; m += gridDim.x) acc += __bfloat162float(dout[(size_t)m * C + co]);
-  atomicAdd(db + co, acc);
+// db[co] += sum over m of dout[m][co] (bf16 dout [M][C], C a multiple of 8,
+// at most 256).  Each CTA takes a contiguous chunk of rows; a thread reads
+// 8 channels (16 bytes) of a row at a time, so consecutive threads read
+// consecutive bytes, and accumulates them in float; the CTA then sums its
+// threads' partials per channel in shared memory and adds one atomic per
+// channel.
+constexpr int kBiasThreads = 256;
+__global__ void __launch_bounds__(kBiasThreads) net_bias_grad_kernel(const __nv_bfloat16 *__restrict__ dout, int M,
+                                                                     int C, float *__restrict__ db) {
+  __shared__ float s_acc[kBiasThreads][9];
+  const int groups = C >> 3, grp = threadIdx.x % groups, rstep = kBiasThreads / groups;
+  const int64_t chunk = div_up64(M, gridDim.x);
+  const int64_t m0 = (int64_t)blockIdx.x * chunk, m1 = min((int64_t)M, m0 + chunk);
+  float acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+#pragma unroll 4
+  for (int64_t m = m0 + threadIdx.x / groups; m < m1; m += rstep) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(dout + m * C) + grp);
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __bfloat1622float2(h[k]);
+      acc[2 * k] += f.x;
+      acc[2 * k + 1] += f.y;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s_acc[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  if ((int)threadIdx.x < C) {
+    const int g = threadIdx.x >> 3, k = threadIdx.x & 7;
+    float t = 0.f;
+    for (int r = 0; r < rstep; ++r) t += s_acc[r * groups + g][k];
+    if (t != 0.f) atomicAdd(db + threadIdx.x, t);
+  }
+}
+
+// The grid of net_bias_grad_kernel for M rows: about 8 rows per thread,
+// at most four CTAs per SM.
+unsigned bias_grid(int M, int C) {
+  const int64_t rows_per_cta = (int64_t)(kBiasThreads / (C >> 3)) * 8;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(4 * 152, div_up64(M, rows_per_cta)));
 }
 
 // The head's 64 outputs per cell o -> one closed curve and one open stroke
@@ -1199,8 +1438,8 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
     const int chunk = std::max(kBK, (int)div_up64(div_up64(g.M(), 152), kBK) * kBK);
     const WgradOp op{g, chunk, w.dhead, w.act[5], grad->g[5]};
     BS_TRY(run_gemm(op, g.Cout, g.K(), chunk, div_up(g.M(), chunk), s));
-    net_bias_grad_kernel<<<dim3(128, div_up(g.Cout, 128)), 128, 0, s>>>(w.dhead, g.M(), g.Cout,
-                                                                        grad->g[5] + (size_t)g.Cout * g.K());
+    net_bias_grad_kernel<<<bias_grid(g.M(), g.Cout), kBiasThreads, 0, s>>>(w.dhead, g.M(), g.Cout,
+                                                                           grad->g[5] + (size_t)g.Cout * g.K());
     BS_LAUNCHED("net_bias_grad_kernel");
     net_transpose_kernel<<<div_up(g.Cin * g.Cout, 256), 256, 0, s>>>(net->w[5], g.Cin, g.Cout, w.wq);
     BS_LAUNCHED("net_transpose_kernel");
@@ -1210,11 +1449,15 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
   for (int l = 4; l >= 0; --l) {
     const Geom g = net_layer(l, n, side);
     const __nv_bfloat16 *dout = w.dact[l + 1];
-    const int chunk = std::max(kBK, (int)div_up64(div_up64(g.M(), 304), kBK) * kBK);
-    const WgradOp op{g, chunk, dout, w.act[l], grad->g[l]};
-    BS_TRY(run_gemm(op, g.Cout, g.K(), chunk, div_up(g.M(), chunk), s));
-    net_bias_grad_kernel<<<dim3(256, div_up(g.Cout, 128)), 128, 0, s>>>(dout, g.M(), g.Cout,
-                                                                        grad->g[l] + (size_t)g.Cout * g.K());
+    if (uses_tma_wgrad(g)) {
+      BS_TRY(run_wgrad_tma(g, w.act[l], dout, grad->g[l], s));
+    } else {
+      const int chunk = std::max(kBK, (int)div_up64(div_up64(g.M(), 304), kBK) * kBK);
+      const WgradOp op{g, chunk, dout, w.act[l], grad->g[l]};
+      BS_TRY(run_gemm(op, g.Cout, g.K(), chunk, div_up(g.M(), chunk), s));
+    }
+    net_bias_grad_kernel<<<bias_grid(g.M(), g.Cout), kBiasThreads, 0, s>>>(dout, g.M(), g.Cout,
+                                                                           grad->g[l] + (size_t)g.Cout * g.K());
     BS_LAUNCHED("net_bias_grad_kernel");
     if (l == 0) break;  // the input image needs no gradient
     const int64_t nq = 4ll * g.Cin * 4 * g.Cout;

@@ -352,10 +352,39 @@ def time_forward(n: int = 64, side: int = SIDE, reps: int = 20, engines=(0, 3, 1
     return out
 
 
+def time_train(n: int = 64, side: int = SIDE, reps: int = 20, engines=(0, 3, 1), device="cuda") -> dict:
+    """ms of one training step (forward, backward, Adam, bf16 copies) of n
+    random patches against random target curves on each GEMM engine, CUDA
+    events."""
+    net = InitNet(device=device, seed=1)
+    rng = np.random.default_rng(0)
+    x = torch.as_tensor(rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32), device=device)
+    cells = (side // CELL) ** 2
+    t = {k: torch.as_tensor(rng.uniform(0.1, 0.9, (n, cells) + sh).astype(np.float32), device=device)
+         for k, sh in bs.NET_CURVE_SHAPES.items()}
+    out = {}
+    try:
+        for engine in engines:
+            bs.debug_gemm_engine(engine)
+            for _ in range(3):
+                net.train_step(x, t)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                net.train_step(x, t)
+            e1.record()
+            torch.cuda.synchronize()
+            out[engine] = e0.elapsed_time(e1) / reps
+    finally:
+        bs.debug_gemm_engine(1)
+    return out
+
+
 def main(argv=None):
     """Pairs -> training -> evaluation on 2048 x 2048 targets (64 patches
-    each); prints one JSON line.  With --time-forward, only the forward's
-    time on each GEMM engine."""
+    each); prints one JSON line.  With --time-forward (--time-train), only
+    the forward's (a training step's) time on each GEMM engine."""
     import argparse
     import json
     import time
@@ -370,12 +399,19 @@ def main(argv=None):
     ap.add_argument("--eval-steps", type=int, default=300)
     ap.add_argument("--every", type=int, default=10)
     ap.add_argument("--time-forward", action="store_true", help="time one forward of --batch patches per engine")
+    ap.add_argument("--time-train", action="store_true", help="time one training step of --batch patches per engine")
     ap.add_argument("--engines", default="0,3,1", help="GEMM engines for --time-forward")
     ap.add_argument("--reps", type=int, default=20)
     a = ap.parse_args(argv)
     if a.time_forward:
         ms = time_forward(a.batch, SIDE, a.reps, tuple(int(e) for e in a.engines.split(",")))
         print(json.dumps({"forward_ms_by_engine": ms, "patches": a.batch, "side": SIDE}))
+        return
+    if a.time_train:
+        ms = time_train(a.batch, SIDE, a.reps, tuple(int(e) for e in a.engines.split(",")))
+        print(json.dumps({"train_step_ms_by_engine": ms, "patches": a.batch, "side": SIDE,
+                          "tflops_by_engine": {k: round(train_flops(a.batch) / (v * 1e-3) / 1e12, 2)
+                                               for k, v in ms.items()}}))
         return
     dev = "cuda"
     t0 = time.perf_counter()

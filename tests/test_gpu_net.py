@@ -76,13 +76,21 @@ def _dev(t):
     return {k: torch.as_tensor(np.asarray(v, np.float32), device="cuda") for k, v in t.items()}
 
 
-def test_train_step_gradients_match_oracle(learned):
+@pytest.mark.parametrize("n,side,bar", [(2, 64, 2e-2), (2, 256, 1e-1)])
+def test_train_step_gradients_match_oracle(learned, n, side, bar):
+    """(2, 64): every GEMM gathers its operands; (2, 256): layers 2-4 take
+    their weight gradients from the TMA-fed tcgen05 kernel (64-pixel
+    chunks: 32, 8 and 2 of them).  The larger case has 16 times the pixels
+    per layer, so more activations and activation gradients round to the
+    other bf16 neighbour under float32 sums than under the oracle's float64
+    ones; each such flip moves its value by one bf16 step (0.4 %) and the
+    change propagates, so the largest entry error grows (measured 5.6 % in
+    layer 4) while the gradients stay aligned (cosine above 0.9999)."""
     import paper_2503_16424_gb300.bs as bs
     net = _rand_net(learned, 4)
     rng = np.random.default_rng(9)
-    n, side = 2, 64
     x = rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32)
-    t = {k: np.asarray(v, np.float32) for k, v in _targets(rng, n, 4, side).items()}
+    t = {k: np.asarray(v, np.float32) for k, v in _targets(rng, n, (side // 32) ** 2, side).items()}
     loss = torch.zeros((), dtype=torch.float64, device="cuda")
     bs.net_train_step(net.w, net.w_bf16, net.g, torch.as_tensor(x, device="cuda"), _dev(t), net.ws(n, side), loss)
     torch.cuda.synchronize()
@@ -94,7 +102,7 @@ def test_train_step_gradients_match_oracle(learned):
         err = np.abs(got - r).max() / np.abs(r).max()
         cos = float(got @ r / (np.linalg.norm(got) * np.linalg.norm(r)))
         print(f"layer {l}: grad rel err {err:.2e}, cosine {cos:.6f}")
-        assert err <= 2e-2 and cos >= 0.9999, l
+        assert err <= bar and cos >= 0.9999, l
 
 
 def test_training_fits_pairs_and_beats_the_baseline(learned):
@@ -229,3 +237,44 @@ def test_tma_fed_convolutions_agree_with_the_gathered_engines(learned):
             print(f"n {n} side {side}: engine {engine} vs gathered tcgen05: rel {err:.2e}")
             assert err <= 5e-3, (n, side, engine)
         assert torch.equal(heads[1], heads[2])   # both run layers 2-4 on the TMA kernel, 0-1 and the head alike
+
+
+def test_tma_weight_gradients_agree_with_the_gathered_engines(learned):
+    """The weight gradients of layers 2-4 on wgrad_tma_kernel (engines 1 and
+    2: both operands MN-major, straight from im2col and tiled TMA loads)
+    against the thread-gathered engines (0: mma.sync, 3: tcgen05), on shapes
+    whose pixel splits leave 1 to 27 chunks per CTA: the same bf16 products
+    summed in float32 in another order, and no tile gave up waiting.  The
+    layers' inputs and output gradients are the same bf16 values on every
+    engine up to rare rounding flips, so the TMA path must agree with
+    mma.sync to 1e-3 of each layer's largest entry (a dropped or repeated
+    64-pixel chunk of a split moves entries by far more; measured 4e-7);
+    engine 3 keeps the bars of the tests above."""
+    import paper_2503_16424_gb300.bs as bs
+    net = _rand_net(learned, 9)
+    rng = np.random.default_rng(14)
+    before = bs.debug_gemm_engine(1)   # tiles that gave up so far in this process
+    for n, side in ((2, 256), (3, 512)):
+        x = torch.as_tensor(rng.uniform(0, 1, (n, 3, side, side)).astype(np.float32), device="cuda")
+        tg = _dev(_targets(rng, n, (side // 32) ** 2, side))
+        loss = torch.zeros((), dtype=torch.float64, device="cuda")
+        grads = {}
+        try:
+            for engine in (0, 3, 1, 2):
+                bs.debug_gemm_engine(engine)
+                bs.net_train_step(net.w, net.w_bf16, net.g, x, tg, net.ws(n, side), loss)
+                torch.cuda.synchronize()
+                grads[engine] = [g.cpu().double() for g in net.g]
+        finally:
+            timeouts = bs.debug_gemm_engine(1)
+        assert timeouts == before
+        for engine in (1, 2, 3):
+            for l in range(6):
+                a, b = grads[engine][l], grads[0][l]
+                err = float((a - b).abs().max() / b.abs().max())
+                cos = float(a @ b / (a.norm() * b.norm()))
+                print(f"n {n} side {side} engine {engine} layer {l}: rel {err:.2e}, cosine {cos:.7f}")
+                if engine == 3:
+                    assert err <= 2e-2 and cos >= 0.9999, (n, side, engine, l)
+                else:
+                    assert err <= 1e-3 and cos >= 0.99999, (n, side, engine, l)
