@@ -385,6 +385,160 @@ __device__ __forceinline__ void umma_bf16_n128(uint32_t tmem_d, uint64_t a, uint
       : "memory");
 }
 
+// ---- input gradients fed by the tensor memory accelerator ----
+// For the 4 x 4 stride-2 convolutions with Cout a multiple of 64 and Cin 32,
+// 64 or a multiple of 128.  An input pixel (2a + qy, 2c + qx) of parity
+// class q = (qy, qx) is reached by the 2 x 2 taps of that parity, so per
+// class the input gradient is a stride-1 2 x 2 correlation over dout:
+//   din[n, 2a + qy, 2c + qx, ci] = relu'(act_in) sum over taps (ta, tb) and co
+//       of dout[n, a + qy - ta, c + qx - tb, co] wq[q][ci][(2 ta + tb) Cout + co]
+// (wq as DgradOp reads it).  A CTA computes a 128 x kN tile (class pixels x
+// ci) over K = 4 Cout in chunks of 64 output channels of one tap:
+//   A: an im2col load of dout with the class's own map (the 2 x 2 window's
+//      corner runs over [q - 1, dim + q - 2] per axis at stride 1; taps as
+//      im2col offsets (1 - tb, 1 - ta); outside dout reads zeros);
+//   B: a tiled load of the rows q Cin + n0 .. of wq (K-major).
+// Stages, descriptors, waits and commits as in conv_tma_kernel (N = kN);
+// the epilogue applies the ReLU mask of act_in and stores bf16 NHWC rows at
+// the class's pixels.  One launch covers the four classes (grid z).
+struct DgradMaps {
+  CUtensorMap a[4];
+  CUtensorMap b;
+};
+
+template <int kN>
+__device__ __forceinline__ void umma_bf16_dgrad(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                             ((uint32_t)(kTM >> 4) << 24);
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+template <int kN> constexpr uint32_t dgrad_smem() { return kTStages * (kTStageA + kN * kTK * 2) + 1024; }
+
+// grid (ceil(M / 128), Cin / kN, 4); M = N Ho Wo pixels per class.
+template <int kN>
+__global__ void __launch_bounds__(kTThreads) dgrad_tma_kernel(const __grid_constant__ DgradMaps maps, int M, int Ho,
+                                                              int Wo, int Cin, int Cout,
+                                                              const __nv_bfloat16 *__restrict__ act_in,
+                                                              __nv_bfloat16 *__restrict__ din, unsigned int *err,
+                                                              uint32_t first_wait) {
+  constexpr uint32_t kStageB = kN * kTK * 2;
+  extern __shared__ uint8_t d_smem[];
+  __shared__ __align__(8) uint64_t full[kTStages], empty[kTStages], done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t base = (smem_u32(d_smem) + 1023u) & ~1023u;
+  const uint32_t sA = base, sB = base + kTStages * kTStageA;
+  const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kN, q = blockIdx.z, qy = q >> 1, qx = q & 1;
+  const int per_tap = Cout / kTK, n_chunks = 4 * per_tap;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"((uint32_t)kN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kTStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  const int hw = Ho * Wo;
+  if (tid == 0) {
+    // producer: the window's corner for the tile's first class pixel
+    const int img = m0 / hw, r0 = m0 - img * hw, a0 = r0 / Wo, c0 = r0 - a0 * Wo;
+    for (int c = 0; c < n_chunks; ++c) {
+      const int st = c % kTStages;
+      if (c >= kTStages && !mbar_wait(&empty[st], (uint32_t)((c / kTStages - 1) & 1))) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      const int tap = c / per_tap, cb = (c - tap * per_tap) * kTK, ta = tap >> 1, tb = tap & 1;
+      mbar_expect_tx(&full[st], kTStageA + kStageB);
+      tma_im2col_4d(sA + st * kTStageA, &maps.a[q], &full[st], cb, c0 + qx - 1, a0 + qy - 1, img, (uint16_t)(1 - tb),
+                    (uint16_t)(1 - ta));
+      tma_tile_2d(sB + st * kStageB, &maps.b, &full[st], tap * Cout + cb, q * Cin + n0);
+    }
+  } else if (tid == 32) {
+    for (int c = 0; c < n_chunks; ++c) {
+      const int st = c % kTStages;
+      if (!mbar_wait(&full[st], (uint32_t)((c / kTStages) & 1))) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < kTK / 16; ++ks) {
+        const uint64_t da = umma_desc_sw128(sA + st * kTStageA + 32u * ks);
+        const uint64_t db = umma_desc_sw128(sB + st * kStageB + 32u * ks);
+        umma_bf16_dgrad<kN>(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
+      }
+      umma_commit(&empty[st]);
+    }
+    umma_commit(&done);
+  }
+  bool w = mbar_wait(&done, 0u, first_wait);
+  if (!w) {
+    mbar_wait(&done, 0u);
+    if (tid == 0) {
+      atomicAdd(err, 1u);
+      atomicAdd(err + 1, 1u);
+    }
+  }
+  const bool store = __syncthreads_and(w) && s_fail == 0;
+  if (!store && tid == 0 && w) {
+    atomicAdd(err, 1u);
+    atomicAdd(err + 1, 1u);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (store) {
+    const int m = m0 + 32 * warp + lane;
+    size_t o = 0;
+    if (m < M) {
+      const int img = m / hw, r = m - img * hw, a = r / Wo, cc = r - a * Wo;
+      o = (((size_t)img * 2 * Ho + 2 * a + qy) * 2 * Wo + 2 * cc + qx) * Cin + n0;
+    }
+#pragma unroll
+    for (int col = 0; col < kN; col += 8) {
+      uint32_t v[8];
+      const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+          "tcgen05.wait::ld.sync.aligned;\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+          : "r"(ta)
+          : "memory");
+      if (m < M) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(act_in + o + col);
+        const __nv_bfloat162 *xh = reinterpret_cast<const __nv_bfloat162 *>(&x);
+        __align__(16) __nv_bfloat162 res[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 xf = __bfloat1622float2(xh[j]);
+          res[j] = __floats2bfloat162_rn(xf.x > 0.f ? __uint_as_float(v[2 * j]) : 0.f,
+                                         xf.y > 0.f ? __uint_as_float(v[2 * j + 1]) : 0.f);
+        }
+        *reinterpret_cast<uint4 *>(din + o + col) = *reinterpret_cast<const uint4 *>(res);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kN) : "memory");
+}
+
 // ---- weight gradients fed by the tensor memory accelerator ----
 // For the same convolutions (Cin a multiple of 64, Cout of 128, Ho Wo of
 // 64): dW^T[kk][co] = sum over output pixels m of patch[m][kk] dout[m][co],
@@ -1053,6 +1207,80 @@ bs_status run_wgrad_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloa
 }
 
 bool uses_tma_wgrad(const Geom &g) { return uses_tma(g) && (g.Ho * g.Wo) % 64 == 0; }
+// The input gradient of layer g by dgrad_tma_kernel: dout [N][Ho][Wo][Cout],
+// wq the four classes' weights [4][Cin][4 Cout] (bf16), act_in / din
+// [N][Hi][Wi][Cin].
+template <int kN>
+bs_status launch_dgrad_tma(const DgradMaps &maps, const Geom &g, const __nv_bfloat16 *act_in, __nv_bfloat16 *din,
+                           unsigned int *err, cudaStream_t s) {
+  constexpr int kMaxDev = 64;
+  static bool attr[kMaxDev] = {};
+  static std::mutex mu;
+  int dev = 0;
+  BS_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDev || !attr[dev]) {
+      BS_CUDA(cudaFuncSetAttribute(dgrad_tma_kernel<kN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)dgrad_smem<kN>()));
+      if (dev >= 0 && dev < kMaxDev) attr[dev] = true;
+    }
+  }
+  const int M = g.N * g.Ho * g.Wo;
+  const dim3 grid((unsigned)div_up(M, kTM), (unsigned)(g.Cin / kN), 4u);
+  dgrad_tma_kernel<kN><<<grid, kTThreads, dgrad_smem<kN>(), s>>>(maps, M, g.Ho, g.Wo, g.Cin, g.Cout, act_in, din, err,
+                                                                 g_first_wait);
+  BS_LAUNCHED("dgrad_tma_kernel");
+  return BS_OK;
+}
+
+bs_status run_dgrad_tma(const Geom &g, const __nv_bfloat16 *dout, const __nv_bfloat16 *wq, const __nv_bfloat16 *act_in,
+                        __nv_bfloat16 *din, cudaStream_t s) {
+  EncodeIm2col enc_im2col;
+  EncodeTiled enc_tiled;
+  BS_TRY(tma_encoders(&enc_im2col, &enc_tiled));
+  const int kN = g.Cin >= 128 ? 128 : g.Cin;
+  DgradMaps maps;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.Cout, (cuuint64_t)g.Wo, (cuuint64_t)g.Ho, (cuuint64_t)g.N};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.Cout * 2, (cuuint64_t)g.Wo * g.Cout * 2,
+                                 (cuuint64_t)g.Ho * g.Wo * g.Cout * 2};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  for (int q = 0; q < 4; ++q) {
+    // the 2 x 2 window's corner runs over [q - 1, dim + q - 2] on each axis
+    const int lower[2] = {(q & 1) - 1, (q >> 1) - 1}, upper[2] = {(q & 1) - 1, (q >> 1) - 1};
+    const CUresult r = enc_im2col(&maps.a[q], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(dout),
+                                  dims, strides, lower, upper, kTK, kTM, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error("cuTensorMapEncodeIm2col failed (%d) for a %dx%dx%d output gradient", (int)r, g.Ho, g.Wo, g.Cout);
+      return BS_ERR_CUDA;
+    }
+  }
+  const cuuint64_t wdims[2] = {(cuuint64_t)4 * g.Cout, (cuuint64_t)4 * g.Cin};
+  const cuuint64_t wstrides[1] = {(cuuint64_t)4 * g.Cout * 2};
+  const cuuint32_t box[2] = {kTK, (cuuint32_t)kN}, wes[2] = {1, 1};
+  const CUresult r = enc_tiled(&maps.b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(wq), wdims,
+                               wstrides, box, wes, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for the %dx%d class weights", (int)r, 4 * g.Cin, 4 * g.Cout);
+    return BS_ERR_CUDA;
+  }
+  unsigned int *err = nullptr;
+  BS_TRY(umma_err_ptr(&err));
+  switch (kN) {
+    case 32: return launch_dgrad_tma<32>(maps, g, act_in, din, err, s);
+    case 64: return launch_dgrad_tma<64>(maps, g, act_in, din, err, s);
+    default: return launch_dgrad_tma<128>(maps, g, act_in, din, err, s);
+  }
+}
+
+// The layers whose input gradient runs on dgrad_tma_kernel.
+bool uses_tma_dgrad(const Geom &g) {
+  return (g_gemm_engine == 1 || g_gemm_engine == 2) && g.KS == 4 && g.S == 2 && g.P == 1 && g.Cout % kTK == 0 &&
+         (g.Cin == 32 || g.Cin == 64 || g.Cin % 128 == 0);
+}
 
 // ---- element-wise pieces ----
 // Planar float32 patches [N][3][H][W] -> NHWC bf16 [N][H][W][8] (channels
@@ -1463,6 +1691,10 @@ bs_status bs_net_train_step(const bs_net *net, const float *patches, int32_t n, 
     const int64_t nq = 4ll * g.Cin * 4 * g.Cout;
     net_dgrad_weights_kernel<<<(unsigned)div_up64(nq, 256), 256, 0, s>>>(net->w[l], g.Cin, g.Cout, w.wq);
     BS_LAUNCHED("net_dgrad_weights_kernel");
+    if (uses_tma_dgrad(g)) {
+      BS_TRY(run_dgrad_tma(g, dout, w.wq, w.act[l], w.dact[l], s));
+      continue;
+    }
     for (int q = 0; q < 4; ++q) {
       const DgradOp dop{g, q >> 1, q & 1, dout, w.wq + (size_t)q * g.Cin * 4 * g.Cout, w.act[l], w.dact[l]};
       BS_TRY(run_gemm(dop, g.N * (g.Hi / 2) * (g.Wi / 2), g.Cin, 4 * g.Cout, 1, s));
