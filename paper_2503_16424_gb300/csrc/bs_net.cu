@@ -327,8 +327,10 @@ __global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsig
 // For the 4 x 4, stride-2 convolutions whose input has 64 or more channels
 // (and output channels a multiple of 128): a CTA computes a 128 x 128 tile
 // (output pixels x output channels) over K = 16 taps x Cin, in chunks of 64
-// input channels of one tap.  Per chunk one thread issues two TMA loads
-// into a ring of kTStages shared-memory stages:
+// input channels of one tap.  (A 32-channel input, output channels a
+// multiple of 64, runs the same way with 32-channel chunks in 64-byte
+// swizzled rows and 128 x 64 tiles.)  Per chunk one thread issues two TMA
+// loads into a ring of kTStages shared-memory stages:
 //   A: an im2col load of the NHWC input: 128 output pixels (the tile's
 //      rows, traversed W, H, N with stride 2 inside the box [-1, dim - 3],
 //      the padding zero-filled) x 64 channels of the tap (ky, kx), given as
@@ -343,17 +345,35 @@ __global__ void __launch_bounds__(kUThreads) umma_gemm_kernel(const Op op, unsig
 // memory; the epilogue reads it back (warp w: lanes 32 w ..), adds the bias,
 // applies ReLU and stores bf16 NHWC rows.  Every mbarrier wait is bounded: a
 // wait that gives up counts in err[0] and err[1] and the tile is not stored.
-constexpr int kTM = 128, kTN = 128, kTK = 64, kTStages = 3, kTThreads = 128;
-constexpr uint32_t kTStageA = kTM * kTK * 2, kTStageB = kTN * kTK * 2;   // bytes
-constexpr uint32_t kTSmem = kTStages * (kTStageA + kTStageB) + 1024;   // + alignment slack
-constexpr uint32_t kTIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
-                             ((uint32_t)(kTM >> 4) << 24);
+constexpr int kTM = 128, kTK = 64, kTStages = 3, kTThreads = 128;
+constexpr uint32_t kTStageA = kTM * kTK * 2;   // bytes of an A stage of 64 channels
 
 // K-major operand descriptor with 128-byte swizzle: start address, stride
 // between 8-row groups 1024 bytes, version 1, layout type 2 (128B swizzle).
 __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// K-major operand descriptor for rows of kRow bytes (128: 128-byte
+// swizzle, layout type 2; 64: 64-byte swizzle, layout type 4): 8-row
+// groups 8 kRow bytes apart.
+template <int kRow>
+__device__ __forceinline__ uint64_t umma_desc_kmajor(uint32_t addr) {
+  static_assert(kRow == 128 || kRow == 64, "128- or 64-byte rows");
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)((8 * kRow) >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)(kRow == 128 ? 2 : 4) << 61);
+}
+
+template <int kN>
+__device__ __forceinline__ void umma_bf16_m128(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
@@ -377,13 +397,6 @@ __device__ __forceinline__ void tma_tile_2d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-__device__ __forceinline__ void umma_bf16_n128(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kTIdesc), "r"(accumulate)
-      : "memory");
-}
 
 // ---- input gradients fed by the tensor memory accelerator ----
 // For the 4 x 4 stride-2 convolutions with Cout a multiple of 64 and Cin 32,
@@ -406,16 +419,6 @@ struct DgradMaps {
   CUtensorMap b;
 };
 
-template <int kN>
-__device__ __forceinline__ void umma_bf16_dgrad(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
-  constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                             ((uint32_t)(kTM >> 4) << 24);
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
 
 template <int kN> constexpr uint32_t dgrad_smem() { return kTStages * (kTStageA + kN * kTK * 2) + 1024; }
 
@@ -483,7 +486,7 @@ __global__ void __launch_bounds__(kTThreads) dgrad_tma_kernel(const __grid_const
       for (int ks = 0; ks < kTK / 16; ++ks) {
         const uint64_t da = umma_desc_sw128(sA + st * kTStageA + 32u * ks);
         const uint64_t db = umma_desc_sw128(sB + st * kStageB + 32u * ks);
-        umma_bf16_dgrad<kN>(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
+        umma_bf16_m128<kN>(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
       }
       umma_commit(&empty[st]);
     }
@@ -540,49 +543,58 @@ __global__ void __launch_bounds__(kTThreads) dgrad_tma_kernel(const __grid_const
 }
 
 // ---- weight gradients fed by the tensor memory accelerator ----
-// For the same convolutions (Cin a multiple of 64, Cout of 128, Ho Wo of
-// 64): dW^T[kk][co] = sum over output pixels m of patch[m][kk] dout[m][co],
-// kk = (tap, ci).  A CTA computes a 128 x 128 tile (kk x co) over one split
+// For the convolutions conv_tma_kernel runs whose Ho Wo is a multiple of 64:
+// dW^T[kk][co] = sum over output pixels m of patch[m][kk] dout[m][co],
+// kk = (tap, ci).  A CTA computes a 128 x kN tile (kk x co) over one split
 // of the pixels, in chunks of 64 pixels, and adds it to dw with float
-// atomics.  Per chunk one thread issues four TMA loads into a ring of
+// atomics.  Per chunk one thread issues its TMA loads into a ring of
 // kWStages stages:
-//   A: two im2col loads of the NHWC input (64 output pixels x 64 channels
-//      of one tap: the tile's two 64-wide halves of kk);
-//   B: two tiled loads of dout [M][Cout] (64 pixels x 64 output channels).
-// Every box lands as 64 pixel rows of 128 bytes (128-byte swizzle): the
-// pixels are the GEMM's reduction axis, so both operands are MN-major (the
-// instruction descriptor's transpose bits).  The descriptors advance 2048
-// bytes (16 pixel rows) per K step; the two halves of M (N) lie kWHalf bytes
-// apart and the 8-row groups 1024 bytes apart.  Waits, commits and the
-// error count work as in conv_tma_kernel.
+//   A: 128 / kACh im2col loads of the NHWC input (64 output pixels x kACh
+//      channels of one tap each: the tile's kk in kACh-wide pieces);
+//   B: kN / 64 tiled loads of dout [M][Cout] (64 pixels x 64 output
+//      channels).
+// Every box lands as 64 pixel rows of 2 kACh (A) or 128 (B) bytes, swizzled
+// at the row width: the pixels are the GEMM's reduction axis, so both
+// operands are MN-major (the instruction descriptor's transpose bits).  The
+// descriptors advance 16 rows per K step; the pieces of M (N) lie one box
+// apart (leading byte offset) and the 8-row groups eight rows apart (stride
+// byte offset).  Waits, commits and the error count work as in
+// conv_tma_kernel.
 constexpr int kWStages = 3, kWThreads = 128;
-constexpr uint32_t kWHalf = 64 * 64 * 2;   // bytes of one 64 x 64 box
-constexpr uint32_t kWStage = 4 * kWHalf;   // A's two halves, then B's
-constexpr uint32_t kWSmem = kWStages * kWStage + 1024;
-constexpr uint32_t kWIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-                             ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t kWBoxB = 64 * 64 * 2;   // bytes of one dout box
+template <int kACh, int kN> constexpr uint32_t wgrad_stage() { return 128 * 64 * 2 + (kN / 64) * kWBoxB; }
+template <int kACh, int kN> constexpr uint32_t wgrad_smem() { return kWStages * wgrad_stage<kACh, kN>() + 1024; }
 
-// MN-major operand descriptor with 128-byte swizzle.
-__device__ __forceinline__ uint64_t umma_desc_sw128_mn(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// MN-major operand descriptor for rows of kRow bytes (128: 128-byte
+// swizzle, layout type 2; 64: 64-byte swizzle, layout type 4).
+template <int kRow>
+__device__ __forceinline__ uint64_t umma_desc_mn(uint32_t addr, uint32_t lbo) {
+  static_assert(kRow == 128 || kRow == 64, "128- or 64-byte rows");
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+         ((uint64_t)((8 * kRow) >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(kRow == 128 ? 2 : 4) << 61);
 }
 
-__device__ __forceinline__ void umma_bf16_wgrad(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+template <int kN>
+__device__ __forceinline__ void umma_bf16_mn(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                             ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kWIdesc), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
-// grid (K / 128, Cout / 128, splits); split z takes chunks
+// grid (K / 128, Cout / kN, splits); split z takes chunks
 // [z per, min(n_chunks, (z + 1) per)) of 64 pixels.
+template <int kACh, int kN>
 __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_constant__ CUtensorMap map_in,
                                                               const __grid_constant__ CUtensorMap map_dout, int Ho,
                                                               int Wo, int Cin, int K, int n_chunks, int per,
                                                               float *__restrict__ dw, unsigned int *err,
-                                                              uint32_t first_wait, uint32_t lbo, uint32_t sbo) {
+                                                              uint32_t first_wait) {
+  constexpr int kRowA = 2 * kACh, kNA = 128 / kACh, kNB = kN / 64;
+  constexpr uint32_t kBoxA = 64 * kRowA, kStage = wgrad_stage<kACh, kN>();
   extern __shared__ uint8_t w_smem[];
   __shared__ __align__(8) uint64_t full[kWStages], empty[kWStages], done;
   __shared__ uint32_t s_tmem;
@@ -591,10 +603,10 @@ __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_const
   if (n <= 0) return;  // uniform over the CTA, before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t base = (smem_u32(w_smem) + 1023u) & ~1023u;
-  const int kk0 = blockIdx.x * 128, co0 = blockIdx.y * 128;
+  const int kk0 = blockIdx.x * 128, co0 = blockIdx.y * kN;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(128u)
+                 "r"((uint32_t)kN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -612,8 +624,7 @@ __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_const
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
   if (tid == 0) {
-    // producer; the kk halves: tap and first channel of each
-    const int t0 = kk0 / Cin, ci0 = kk0 - t0 * Cin, t1 = (kk0 + 64) / Cin, ci1 = kk0 + 64 - t1 * Cin;
+    // producer
     const int hw = Ho * Wo;
     for (int c = 0; c < n; ++c) {
       const int st = c % kWStages;
@@ -622,13 +633,16 @@ __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_const
         break;
       }
       const int m = (c0 + c) * 64, img = m / hw, r = m - img * hw, oy = r / Wo, ox = r - oy * Wo;
-      const uint32_t sa = base + st * kWStage, sb = sa + 2 * kWHalf;
-      mbar_expect_tx(&full[st], kWStage);
-      tma_im2col_4d(sa, &map_in, &full[st], ci0, 2 * ox - 1, 2 * oy - 1, img, (uint16_t)(t0 & 3), (uint16_t)(t0 >> 2));
-      tma_im2col_4d(sa + kWHalf, &map_in, &full[st], ci1, 2 * ox - 1, 2 * oy - 1, img, (uint16_t)(t1 & 3),
-                    (uint16_t)(t1 >> 2));
-      tma_tile_2d(sb, &map_dout, &full[st], co0, m);
-      tma_tile_2d(sb + kWHalf, &map_dout, &full[st], co0 + 64, m);
+      const uint32_t sa = base + st * kStage, sb = sa + kNA * kBoxA;
+      mbar_expect_tx(&full[st], kStage);
+#pragma unroll
+      for (int j = 0; j < kNA; ++j) {
+        const int kk = kk0 + j * kACh, tap = kk / Cin, ci = kk - tap * Cin;
+        tma_im2col_4d(sa + j * kBoxA, &map_in, &full[st], ci, 2 * ox - 1, 2 * oy - 1, img, (uint16_t)(tap & 3),
+                      (uint16_t)(tap >> 2));
+      }
+#pragma unroll
+      for (int j = 0; j < kNB; ++j) tma_tile_2d(sb + j * kWBoxB, &map_dout, &full[st], co0 + 64 * j, m);
     }
   } else if (tid == 32) {
     // MMA issuer
@@ -639,12 +653,12 @@ __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_const
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = base + st * kWStage, sb = sa + 2 * kWHalf;
+      const uint32_t sa = base + st * kStage, sb = sa + kNA * kBoxA;
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
-        const uint64_t da = umma_desc_sw128_mn(sa + 2048u * ks, lbo, sbo);
-        const uint64_t db = umma_desc_sw128_mn(sb + 2048u * ks, lbo, sbo);
-        umma_bf16_wgrad(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
+        const uint64_t da = umma_desc_mn<kRowA>(sa + 16u * kRowA * ks, kBoxA);
+        const uint64_t db = umma_desc_mn<128>(sb + 2048u * ks, kWBoxB);
+        umma_bf16_mn<kN>(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
       }
       umma_commit(&empty[st]);
     }
@@ -667,7 +681,7 @@ __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_const
   if (store) {
     const int kk = kk0 + 32 * warp + lane;
 #pragma unroll 4
-    for (int col = 0; col < 128; col += 8) {
+    for (int col = 0; col < kN; col += 8) {
       uint32_t v[8];
       const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col;
       asm volatile(
@@ -682,28 +696,34 @@ __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_const
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kN) : "memory");
 }
 
-// M = N Ho Wo output pixels, Cout a multiple of kTN, Cin a multiple of kTK;
-// grid (ceil(M / kTM), Cout / kTN).
+// kCh input channels per chunk (64: 128-byte rows and swizzle; 32: 64-byte
+// rows and swizzle, for a 32-channel input), kN output channels per tile.
+// M = N Ho Wo output pixels, Cout a multiple of kN, Cin a multiple of kCh;
+// grid (ceil(M / kTM), Cout / kN).
+template <int kCh, int kN> constexpr uint32_t conv_smem() { return kTStages * (kTM + kN) * kCh * 2 + 1024; }
+
+template <int kCh, int kN>
 __global__ void __launch_bounds__(kTThreads) conv_tma_kernel(const __grid_constant__ CUtensorMap map_in,
                                                              const __grid_constant__ CUtensorMap map_w, int M, int Ho,
                                                              int Wo, int Cin, int Cout, const float *__restrict__ bias,
                                                              __nv_bfloat16 *__restrict__ out, unsigned int *err,
                                                              uint32_t first_wait) {
+  constexpr uint32_t kStageA = kTM * kCh * 2, kStageB = kN * kCh * 2;
   extern __shared__ uint8_t t_smem[];
   __shared__ __align__(8) uint64_t full[kTStages], empty[kTStages], done;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t base = (smem_u32(t_smem) + 1023u) & ~1023u;   // 1024-byte aligned stages
-  const uint32_t sA = base, sB = base + kTStages * kTStageA;
-  const int m0 = blockIdx.x * kTM, co0 = blockIdx.y * kTN;
-  const int per_tap = Cin / kTK, n_chunks = 16 * per_tap;
+  const uint32_t sA = base, sB = base + kTStages * kStageA;
+  const int m0 = blockIdx.x * kTM, co0 = blockIdx.y * kN;
+  const int per_tap = Cin / kCh, n_chunks = 16 * per_tap;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"((uint32_t)kTN)
+                 "r"((uint32_t)kN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -730,10 +750,10 @@ __global__ void __launch_bounds__(kTThreads) conv_tma_kernel(const __grid_consta
         atomicExch(&s_fail, 1);
         break;
       }
-      const int tap = c / per_tap, cb = (c - tap * per_tap) * kTK;
-      mbar_expect_tx(&full[st], kTStageA + kTStageB);
-      tma_im2col_4d(sA + st * kTStageA, &map_in, &full[st], cb, w0, h0, n0, (uint16_t)(tap & 3), (uint16_t)(tap >> 2));
-      tma_tile_2d(sB + st * kTStageB, &map_w, &full[st], tap * Cin + cb, co0);
+      const int tap = c / per_tap, cb = (c - tap * per_tap) * kCh;
+      mbar_expect_tx(&full[st], kStageA + kStageB);
+      tma_im2col_4d(sA + st * kStageA, &map_in, &full[st], cb, w0, h0, n0, (uint16_t)(tap & 3), (uint16_t)(tap >> 2));
+      tma_tile_2d(sB + st * kStageB, &map_w, &full[st], tap * Cin + cb, co0);
     }
   } else if (tid == 32) {
     // MMA issuer
@@ -745,10 +765,10 @@ __global__ void __launch_bounds__(kTThreads) conv_tma_kernel(const __grid_consta
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int ks = 0; ks < kTK / 16; ++ks) {
-        const uint64_t da = umma_desc_sw128(sA + st * kTStageA + 32u * ks);
-        const uint64_t db = umma_desc_sw128(sB + st * kTStageB + 32u * ks);
-        umma_bf16_n128(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
+      for (int ks = 0; ks < kCh / 16; ++ks) {
+        const uint64_t da = umma_desc_kmajor<kCh * 2>(sA + st * kStageA + 32u * ks);
+        const uint64_t db = umma_desc_kmajor<kCh * 2>(sB + st * kStageB + 32u * ks);
+        umma_bf16_m128<kN>(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
       }
       umma_commit(&empty[st]);
     }
@@ -774,7 +794,7 @@ __global__ void __launch_bounds__(kTThreads) conv_tma_kernel(const __grid_consta
   if (store) {
     const int m = m0 + 32 * warp + lane;
 #pragma unroll 4
-    for (int col = 0; col < kTN; col += 8) {
+    for (int col = 0; col < kN; col += 8) {
       uint32_t v[8];
       const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col;
       asm volatile(
@@ -795,7 +815,7 @@ __global__ void __launch_bounds__(kTThreads) conv_tma_kernel(const __grid_consta
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kTN) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kN) : "memory");
 }
 
 // ---- the operations ----
@@ -1092,10 +1112,46 @@ bs_status tma_encoders(EncodeIm2col *im2col, EncodeTiled *tiled) {
   return BS_OK;
 }
 
-// The forward convolution of layer g (4 x 4, stride 2, padding 1; Cin a
-// multiple of 64, Cout of 128) by conv_tma_kernel.
+template <int kCh, int kN>
+bs_status launch_conv_tma(const CUtensorMap &map_in, const CUtensorMap &map_w, const Geom &g, const float *bias,
+                          __nv_bfloat16 *out, unsigned int *err, cudaStream_t s) {
+  constexpr int kMaxDev = 64;
+  static bool attr[kMaxDev] = {};
+  static std::mutex mu;
+  int dev = 0;
+  BS_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDev || !attr[dev]) {
+      BS_CUDA(cudaFuncSetAttribute(conv_tma_kernel<kCh, kN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)conv_smem<kCh, kN>()));
+      if (dev >= 0 && dev < kMaxDev) attr[dev] = true;
+    }
+  }
+  const dim3 grid((unsigned)div_up(g.M(), kTM), (unsigned)(g.Cout / kN));
+  conv_tma_kernel<kCh, kN><<<grid, kTThreads, conv_smem<kCh, kN>(), s>>>(map_in, map_w, g.M(), g.Ho, g.Wo, g.Cin,
+                                                                         g.Cout, bias, out, err, g_first_wait);
+  BS_LAUNCHED("conv_tma_kernel");
+  return BS_OK;
+}
+
+// The TMA forward's chunk width for layer g: 64 channels (Cin a multiple
+// of 64, Cout of 128) or 32 (a 32-channel input, Cout a multiple of 64);
+// 0: the layer runs on the gathered engines.
+int conv_tma_channels(const Geom &g) {
+  if (!(g_gemm_engine == 1 || g_gemm_engine == 2) || g.KS != 4 || g.S != 2 || g.P != 1) return 0;
+  if (g.Cin % 64 == 0 && g.Cout % 128 == 0) return 64;
+  if (g.Cin == 32 && g.Cout % 64 == 0) return 32;
+  return 0;
+}
+
+// The forward convolution of layer g (4 x 4, stride 2, padding 1) by
+// conv_tma_kernel, with the chunk width of conv_tma_channels.
 bs_status run_conv_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias,
                        __nv_bfloat16 *out, cudaStream_t s) {
+  const int ch = conv_tma_channels(g);
+  const int nt = ch == 64 ? 128 : 64;
+  const CUtensorMapSwizzle swz = ch == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   EncodeIm2col enc_im2col;
   EncodeTiled enc_tiled;
   BS_TRY(tma_encoders(&enc_im2col, &enc_tiled));
@@ -1107,7 +1163,7 @@ bs_status run_conv_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloat
   const int lower[2] = {-g.P, -g.P}, upper[2] = {g.P - (g.KS - 1), g.P - (g.KS - 1)};
   const cuuint32_t estr[4] = {1, (cuuint32_t)g.S, (cuuint32_t)g.S, 1};
   CUresult r = enc_im2col(&map_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(in), dims, strides,
-                          lower, upper, kTK, kTM, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          lower, upper, (cuuint32_t)ch, kTM, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeIm2col failed (%d) for a %dx%dx%d input", (int)r, g.Hi, g.Wi, g.Cin);
@@ -1115,9 +1171,9 @@ bs_status run_conv_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloat
   }
   const cuuint64_t wdims[2] = {(cuuint64_t)g.K(), (cuuint64_t)g.Cout};
   const cuuint64_t wstrides[1] = {(cuuint64_t)g.K() * 2};
-  const cuuint32_t box[2] = {kTK, kTN}, wes[2] = {1, 1};
+  const cuuint32_t box[2] = {(cuuint32_t)ch, (cuuint32_t)nt}, wes[2] = {1, 1};
   r = enc_tiled(&map_w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(w), wdims, wstrides, box,
-                wes, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                wes, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d) for the %dx%d weights", (int)r, g.Cout, g.K());
@@ -1125,35 +1181,47 @@ bs_status run_conv_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloat
   }
   unsigned int *err = nullptr;
   BS_TRY(umma_err_ptr(&err));
+  if (ch == 64) return launch_conv_tma<64, 128>(map_in, map_w, g, bias, out, err, s);
+  return launch_conv_tma<32, 64>(map_in, map_w, g, bias, out, err, s);
+}
+
+// The layers run by conv_tma_kernel.
+bool uses_tma(const Geom &g) { return conv_tma_channels(g) != 0; }
+
+template <int kACh, int kN>
+bs_status launch_wgrad_tma(const CUtensorMap &map_in, const CUtensorMap &map_dout, const Geom &g, float *dw,
+                           unsigned int *err, cudaStream_t s) {
+  constexpr int kMaxDev = 64;
+  static bool attr[kMaxDev] = {};
+  static std::mutex mu;
+  int dev = 0;
+  BS_CUDA(cudaGetDevice(&dev));
   {
-    constexpr int kMaxDev = 64;
-    static bool attr[kMaxDev] = {};
-    static std::mutex mu;
-    int dev = 0;
-    BS_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(mu);
     if (dev < 0 || dev >= kMaxDev || !attr[dev]) {
-      BS_CUDA(cudaFuncSetAttribute(conv_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem));
+      BS_CUDA(cudaFuncSetAttribute(wgrad_tma_kernel<kACh, kN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)wgrad_smem<kACh, kN>()));
       if (dev >= 0 && dev < kMaxDev) attr[dev] = true;
     }
   }
-  const dim3 grid((unsigned)div_up(g.M(), kTM), (unsigned)(g.Cout / kTN));
-  conv_tma_kernel<<<grid, kTThreads, kTSmem, s>>>(map_in, map_w, g.M(), g.Ho, g.Wo, g.Cin, g.Cout, bias, out, err,
-                                                  g_first_wait);
-  BS_LAUNCHED("conv_tma_kernel");
+  // splits of the pixels so that about two CTAs per SM run
+  const int tiles = (g.K() / 128) * (g.Cout / kN), n_chunks = g.M() / 64;
+  int splits = std::max(1, std::min(n_chunks, div_up(2 * 152, tiles)));
+  const int per = div_up(n_chunks, splits);
+  splits = div_up(n_chunks, per);
+  const dim3 grid((unsigned)(g.K() / 128), (unsigned)(g.Cout / kN), (unsigned)splits);
+  wgrad_tma_kernel<kACh, kN><<<grid, kWThreads, wgrad_smem<kACh, kN>(), s>>>(map_in, map_dout, g.Ho, g.Wo, g.Cin,
+                                                                             g.K(), n_chunks, per, dw, err,
+                                                                             g_first_wait);
+  BS_LAUNCHED("wgrad_tma_kernel");
   return BS_OK;
 }
 
-// The layers run by conv_tma_kernel: engines 1 and 2, 4 x 4 stride-2
-// convolutions with Cin a multiple of 64 and Cout of 128.
-bool uses_tma(const Geom &g) {
-  return (g_gemm_engine == 1 || g_gemm_engine == 2) && g.KS == 4 && g.S == 2 && g.P == 1 && g.Cin % kTK == 0 &&
-         g.Cout % kTN == 0;
-}
-
-// The weight gradient of layer g by wgrad_tma_kernel (the layers conv_tma_kernel runs, with
-// Ho Wo a multiple of 64).
+// The weight gradient of layer g by wgrad_tma_kernel (the layers
+// conv_tma_kernel runs, with Ho Wo a multiple of 64): A pieces of the
+// forward's chunk width, co tiles of 128 (64 for a 32-channel input).
 bs_status run_wgrad_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *dw, cudaStream_t s) {
+  const int ch = conv_tma_channels(g);
   EncodeIm2col enc_im2col;
   EncodeTiled enc_tiled;
   BS_TRY(tma_encoders(&enc_im2col, &enc_tiled));
@@ -1164,7 +1232,8 @@ bs_status run_wgrad_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloa
   const int lower[2] = {-g.P, -g.P}, upper[2] = {g.P - (g.KS - 1), g.P - (g.KS - 1)};
   const cuuint32_t estr[4] = {1, (cuuint32_t)g.S, (cuuint32_t)g.S, 1};
   CUresult r = enc_im2col(&map_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(in), dims, strides,
-                          lower, upper, 64, 64, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          lower, upper, (cuuint32_t)ch, 64, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          ch == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeIm2col failed (%d) for a %dx%dx%d input", (int)r, g.Hi, g.Wi, g.Cin);
@@ -1182,31 +1251,11 @@ bs_status run_wgrad_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloa
   }
   unsigned int *err = nullptr;
   BS_TRY(umma_err_ptr(&err));
-  {
-    constexpr int kMaxDev = 64;
-    static bool attr[kMaxDev] = {};
-    static std::mutex mu;
-    int dev = 0;
-    BS_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lock(mu);
-    if (dev < 0 || dev >= kMaxDev || !attr[dev]) {
-      BS_CUDA(cudaFuncSetAttribute(wgrad_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
-      if (dev >= 0 && dev < kMaxDev) attr[dev] = true;
-    }
-  }
-  // splits of the pixels so that about two CTAs per SM run
-  const int tiles = (g.K() / 128) * (g.Cout / 128), n_chunks = g.M() / 64;
-  int splits = std::max(1, std::min(n_chunks, div_up(2 * 152, tiles)));
-  const int per = div_up(n_chunks, splits);
-  splits = div_up(n_chunks, per);
-  const dim3 grid((unsigned)(g.K() / 128), (unsigned)(g.Cout / 128), (unsigned)splits);
-  wgrad_tma_kernel<<<grid, kWThreads, kWSmem, s>>>(map_in, map_dout, g.Ho, g.Wo, g.Cin, g.K(), n_chunks, per, dw, err,
-                                                   g_first_wait, kWHalf, 1024u);
-  BS_LAUNCHED("wgrad_tma_kernel");
-  return BS_OK;
+  if (ch == 64) return launch_wgrad_tma<64, 128>(map_in, map_dout, g, dw, err, s);
+  return launch_wgrad_tma<32, 64>(map_in, map_dout, g, dw, err, s);
 }
 
-bool uses_tma_wgrad(const Geom &g) { return uses_tma(g) && (g.Ho * g.Wo) % 64 == 0; }
+bool uses_tma_wgrad(const Geom &g) { return conv_tma_channels(g) != 0 && (g.Ho * g.Wo) % 64 == 0; }
 // The input gradient of layer g by dgrad_tma_kernel: dout [N][Ho][Wo][Cout],
 // wq the four classes' weights [4][Cin][4 Cout] (bf16), act_in / din
 // [N][Hi][Wi][Cin].
