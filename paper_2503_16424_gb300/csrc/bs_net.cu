@@ -365,6 +365,13 @@ __device__ __forceinline__ uint64_t umma_desc_kmajor(uint32_t addr) {
          ((uint64_t)1 << 46) | ((uint64_t)(kRow == 128 ? 2 : 4) << 61);
 }
 
+// Operand descriptor without swizzle (8-row x 16-byte core matrices): start,
+// leading and stride byte offsets given (layout type 0).
+__device__ __forceinline__ uint64_t umma_desc_plain(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
 template <int kN>
 __device__ __forceinline__ void umma_bf16_m128(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
   constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
@@ -553,20 +560,24 @@ __global__ void __launch_bounds__(kTThreads) dgrad_tma_kernel(const __grid_const
 //      channels of one tap each: the tile's kk in kACh-wide pieces);
 //   B: kN / 64 tiled loads of dout [M][Cout] (64 pixels x 64 output
 //      channels).
-// Every box lands as 64 pixel rows of 2 kACh (A) or 128 (B) bytes, swizzled
-// at the row width: the pixels are the GEMM's reduction axis, so both
-// operands are MN-major (the instruction descriptor's transpose bits).  The
-// descriptors advance 16 rows per K step; the pieces of M (N) lie one box
-// apart (leading byte offset) and the 8-row groups eight rows apart (stride
-// byte offset).  Waits, commits and the error count work as in
-// conv_tma_kernel.
+// Every box lands as 64 pixel rows of 2 kACh (A) or up to 128 (B) bytes,
+// swizzled at the row width (16-byte rows: unswizzled core matrices): the
+// pixels are the GEMM's reduction axis, so both operands are MN-major (the
+// instruction descriptor's transpose bits).  The descriptors advance 16
+// rows per K step; with swizzle the pieces of M (N) lie one box apart
+// (leading byte offset) and the 8-row groups eight rows apart (stride byte
+// offset); without, the two offsets trade places.  Waits, commits and the
+// error count work as in conv_tma_kernel.
 constexpr int kWStages = 3, kWThreads = 128;
 constexpr uint32_t kWBoxB = 64 * 64 * 2;   // bytes of one dout box
-template <int kACh, int kN> constexpr uint32_t wgrad_stage() { return 128 * 64 * 2 + (kN / 64) * kWBoxB; }
+template <int kACh, int kN> constexpr uint32_t wgrad_stage() {
+  return 128 * 64 * 2 + (kN >= 64 ? (kN / 64) * kWBoxB : 64 * kN * 2);
+}
 template <int kACh, int kN> constexpr uint32_t wgrad_smem() { return kWStages * wgrad_stage<kACh, kN>() + 1024; }
 
 // MN-major operand descriptor for rows of kRow bytes (128: 128-byte
-// swizzle, layout type 2; 64: 64-byte swizzle, layout type 4).
+// swizzle, layout type 2; 64: 64-byte swizzle, layout type 4); the 8-row
+// groups eight rows apart.
 template <int kRow>
 __device__ __forceinline__ uint64_t umma_desc_mn(uint32_t addr, uint32_t lbo) {
   static_assert(kRow == 128 || kRow == 64, "128- or 64-byte rows");
@@ -593,8 +604,9 @@ __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_const
                                                               int Wo, int Cin, int K, int n_chunks, int per,
                                                               float *__restrict__ dw, unsigned int *err,
                                                               uint32_t first_wait) {
-  constexpr int kRowA = 2 * kACh, kNA = 128 / kACh, kNB = kN / 64;
+  constexpr int kRowA = 2 * kACh, kNA = 128 / kACh, kNB = kN >= 64 ? kN / 64 : 1;
   constexpr uint32_t kBoxA = 64 * kRowA, kStage = wgrad_stage<kACh, kN>();
+  constexpr uint32_t kBoxB = kN >= 64 ? kWBoxB : 64 * kN * 2;  // B: 64-channel boxes, or one of kN < 64
   extern __shared__ uint8_t w_smem[];
   __shared__ __align__(8) uint64_t full[kWStages], empty[kWStages], done;
   __shared__ uint32_t s_tmem;
@@ -635,14 +647,14 @@ __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_const
       const int m = (c0 + c) * 64, img = m / hw, r = m - img * hw, oy = r / Wo, ox = r - oy * Wo;
       const uint32_t sa = base + st * kStage, sb = sa + kNA * kBoxA;
       mbar_expect_tx(&full[st], kStage);
-#pragma unroll
+#pragma unroll 4
       for (int j = 0; j < kNA; ++j) {
         const int kk = kk0 + j * kACh, tap = kk / Cin, ci = kk - tap * Cin;
         tma_im2col_4d(sa + j * kBoxA, &map_in, &full[st], ci, 2 * ox - 1, 2 * oy - 1, img, (uint16_t)(tap & 3),
                       (uint16_t)(tap >> 2));
       }
 #pragma unroll
-      for (int j = 0; j < kNB; ++j) tma_tile_2d(sb + j * kWBoxB, &map_dout, &full[st], co0 + 64 * j, m);
+      for (int j = 0; j < kNB; ++j) tma_tile_2d(sb + j * kBoxB, &map_dout, &full[st], co0 + 64 * j, m);
     }
   } else if (tid == 32) {
     // MMA issuer
@@ -656,8 +668,14 @@ __global__ void __launch_bounds__(kWThreads) wgrad_tma_kernel(const __grid_const
       const uint32_t sa = base + st * kStage, sb = sa + kNA * kBoxA;
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
-        const uint64_t da = umma_desc_mn<kRowA>(sa + 16u * kRowA * ks, kBoxA);
-        const uint64_t db = umma_desc_mn<128>(sb + 2048u * ks, kWBoxB);
+        // A: 16-byte rows (8 channels) use core matrices without swizzle;
+        // for this MN-major form the leading byte offset steps along the
+        // pixels (eight rows, 128 bytes) and the stride byte offset along
+        // kk (one tap's box), the reverse of the swizzled forms
+        const uint64_t da = kRowA == 16 ? umma_desc_plain(sa + 256u * ks, 128, kBoxA)
+                                        : umma_desc_mn<kRowA == 16 ? 64 : kRowA>(sa + 16u * kRowA * ks, kBoxA);
+        constexpr int kRowB = kN >= 64 ? 128 : 2 * kN;
+        const uint64_t db = umma_desc_mn<kRowB>(sb + 16u * kRowB * ks, kBoxB);
         umma_bf16_mn<kN>(tmem, da, db, (c > 0 || ks > 0) ? 1u : 0u);
       }
       umma_commit(&empty[st]);
@@ -1135,13 +1153,16 @@ bs_status launch_conv_tma(const CUtensorMap &map_in, const CUtensorMap &map_w, c
   return BS_OK;
 }
 
-// The TMA forward's chunk width for layer g: 64 channels (Cin a multiple
-// of 64, Cout of 128) or 32 (a 32-channel input, Cout a multiple of 64);
-// 0: the layer runs on the gathered engines.
+// The TMA box width for layer g: 64 channels (Cin a multiple of 64, Cout of
+// 128), 32 (a 32-channel input, Cout a multiple of 64) or 8 (an 8-channel
+// input, Cout a multiple of 32; the weight gradient only: as a forward its
+// tiles are too small to pay for sixteen loads each); 0: the gathered
+// engines.
 int conv_tma_channels(const Geom &g) {
   if (!(g_gemm_engine == 1 || g_gemm_engine == 2) || g.KS != 4 || g.S != 2 || g.P != 1) return 0;
   if (g.Cin % 64 == 0 && g.Cout % 128 == 0) return 64;
   if (g.Cin == 32 && g.Cout % 64 == 0) return 32;
+  if (g.Cin == 8 && g.Cout % 32 == 0) return 8;
   return 0;
 }
 
@@ -1185,8 +1206,8 @@ bs_status run_conv_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloat
   return launch_conv_tma<32, 64>(map_in, map_w, g, bias, out, err, s);
 }
 
-// The layers run by conv_tma_kernel.
-bool uses_tma(const Geom &g) { return conv_tma_channels(g) != 0; }
+// The layers whose forward runs on conv_tma_kernel.
+bool uses_tma(const Geom &g) { return conv_tma_channels(g) >= 32; }
 
 template <int kACh, int kN>
 bs_status launch_wgrad_tma(const CUtensorMap &map_in, const CUtensorMap &map_dout, const Geom &g, float *dw,
@@ -1219,7 +1240,8 @@ bs_status launch_wgrad_tma(const CUtensorMap &map_in, const CUtensorMap &map_dou
 
 // The weight gradient of layer g by wgrad_tma_kernel (the layers
 // conv_tma_kernel runs, with Ho Wo a multiple of 64): A pieces of the
-// forward's chunk width, co tiles of 128 (64 for a 32-channel input).
+// forward's box width, co tiles of 128 (64 for a 32-channel input, 32 for
+// an 8-channel one).
 bs_status run_wgrad_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *dw, cudaStream_t s) {
   const int ch = conv_tma_channels(g);
   EncodeIm2col enc_im2col;
@@ -1233,7 +1255,8 @@ bs_status run_wgrad_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloa
   const cuuint32_t estr[4] = {1, (cuuint32_t)g.S, (cuuint32_t)g.S, 1};
   CUresult r = enc_im2col(&map_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(in), dims, strides,
                           lower, upper, (cuuint32_t)ch, 64, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          ch == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          ch == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                   : (ch == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE),
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeIm2col failed (%d) for a %dx%dx%d input", (int)r, g.Hi, g.Wi, g.Cin);
@@ -1241,10 +1264,11 @@ bs_status run_wgrad_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloa
   }
   const cuuint64_t ddims[2] = {(cuuint64_t)g.Cout, (cuuint64_t)g.M()};
   const cuuint64_t dstrides[1] = {(cuuint64_t)g.Cout * 2};
-  const cuuint32_t box[2] = {64, 64}, es[2] = {1, 1};
+  const int nb = g.Cout >= 64 ? 64 : g.Cout;   // dout box width: 64 channels, or all of fewer
+  const cuuint32_t box[2] = {(cuuint32_t)nb, 64}, es[2] = {1, 1};
   r = enc_tiled(&map_dout, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(dout), ddims, dstrides, box,
-                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, nb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d) for the %dx%d output gradient", (int)r, g.M(), g.Cout);
     return BS_ERR_CUDA;
@@ -1252,7 +1276,8 @@ bs_status run_wgrad_tma(const Geom &g, const __nv_bfloat16 *in, const __nv_bfloa
   unsigned int *err = nullptr;
   BS_TRY(umma_err_ptr(&err));
   if (ch == 64) return launch_wgrad_tma<64, 128>(map_in, map_dout, g, dw, err, s);
-  return launch_wgrad_tma<32, 64>(map_in, map_dout, g, dw, err, s);
+  if (ch == 32) return launch_wgrad_tma<32, 64>(map_in, map_dout, g, dw, err, s);
+  return launch_wgrad_tma<8, 32>(map_in, map_dout, g, dw, err, s);
 }
 
 bool uses_tma_wgrad(const Geom &g) { return conv_tma_channels(g) != 0 && (g.Ho * g.Wo) % 64 == 0; }
