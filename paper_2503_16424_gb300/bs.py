@@ -360,6 +360,9 @@ class Binning:
         self.ranges = torch.empty(canvas.n_tiles, 2, dtype=torch.int32, device=device)
         self._want_capacity = pair_capacity
         self.n_pairs = 0
+        # allocations so far: a captured graph holds the addresses of the
+        # buffers of one allocation, so it is stale once this count moves
+        self.allocations = 0
 
     def _alloc(self, n_gauss, capacity):
         nbytes = bin_tiles_workspace(n_gauss, self.canvas, capacity)
@@ -367,6 +370,7 @@ class Binning:
         self.keys = torch.empty(max(1, capacity), dtype=torch.int32, device=self.device)
         self.capacity = capacity
         self.n_gauss = n_gauss
+        self.allocations += 1
 
     def run(self, gauss: torch.Tensor):
         n_gauss = int(gauss.shape[0])
@@ -394,6 +398,15 @@ class Binning:
         capacity = max(self._want_capacity, self.capacity) if capacity is None else capacity
         if self.ws is None or n_gauss != self.n_gauss or self.capacity < capacity:
             self._alloc(n_gauss, capacity)
+        return self
+
+    def fit(self, n_gauss: int, capacity: int):
+        """prepare() for `capacity` pairs, also shrinking a capacity more than
+        1.5 times that: the graph-safe binning sizes its grids by the
+        capacity, so idle room costs launches of empty partitions."""
+        if self.ws is None or n_gauss != self.n_gauss or self.capacity < capacity or self.capacity > 1.5 * capacity:
+            self._alloc(n_gauss, capacity)
+        self._want_capacity = capacity
         return self
 
     def run_async(self, gauss: torch.Tensor, n_pairs_dev: torch.Tensor = None):

@@ -96,10 +96,9 @@ def fit(rast: Rasterizer, curves: bs.CurveSet, target: torch.Tensor, cfg: FitCfg
             _reset_moments(adam, changed, rast.n_open)
             passes.append(dict(step=step, **stats))
             rast.forward(curves)                           # the new curves' pairs, read back
-            need = int(rast.binning.n_pairs * cfg.headroom) + 1024
-            if need > rast.binning.capacity:
-                rast.binning.prepare(rast.n_gauss, need)
-                sg.graph = None                            # captured again at the next step
+            # room for the new curves' pairs (new buffers: the step graph
+            # captures again at its next call)
+            rast.binning.fit(rast.n_gauss, int(rast.binning.n_pairs * cfg.headroom) + 1024)
             if pass_hook:
                 pass_hook(step, before, img_host, changed.cpu().numpy().copy(), stats, host(curves))
     torch.cuda.synchronize()

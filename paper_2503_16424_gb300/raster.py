@@ -102,12 +102,16 @@ class StepGraph:
     instance an Adam step) if given.
 
     The first call runs the step eagerly with the synchronising binning and
-    sizes the pair capacity to `headroom` times the pairs found; the graph is
+    fits the pair capacity to `headroom` times the pairs found (growing or
+    shrinking it: the captured binning's grids are sized by it); the graph is
     captured on the second call and replayed from then on.  check() reads the
     binning's outcome (one synchronisation): a replay whose pairs overflowed
     the capacity blended nothing, so the capacity is grown and the graph
-    captured again at the next call.  Curves, target and grad must keep their
-    storage (the graph holds their addresses)."""
+    captured again at the next call; so is it whenever the binning's buffers
+    were allocated anew since the capture (a synchronising call in between,
+    Rasterizer.forward for instance, grows them when its pairs overflow).
+    Curves, target and grad must keep their storage (the graph holds their
+    addresses)."""
 
     def __init__(self, rast: Rasterizer, curves: CurveSet, target: torch.Tensor, grad: CurveSet, after=None,
                  headroom: float = 1.25):
@@ -116,19 +120,17 @@ class StepGraph:
         self.graph = None
         self.calls = 0
         self.overflows = 0
+        self._allocations = None   # the binning's allocation count the graph was captured with
 
     def _eager_fit(self):
         r = self.r
         r.step(self.curves, self.target, self.grad)
-        want = int(r.binning.n_pairs * self.headroom) + 1024
-        if r.binning.capacity < want:
-            r.binning.prepare(r.n_gauss, want)
-        else:
-            r.binning.prepare(r.n_gauss)
+        r.binning.fit(r.n_gauss, int(r.binning.n_pairs * self.headroom) + 1024)
         if self.after is not None:
             self.after()
 
     def _capture(self):
+        self._allocations = self.r.binning.allocations
         self.graph = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
@@ -143,7 +145,7 @@ class StepGraph:
         if self.calls == 0:
             self._eager_fit()
         else:
-            if self.graph is None:
+            if self.graph is None or self._allocations != self.r.binning.allocations:
                 self._capture()
             self.graph.replay()
         self.calls += 1
@@ -155,7 +157,7 @@ class StepGraph:
         if st == bs.BS_ERR_CAPACITY:
             self.overflows += 1
             self.r.binning.prepare(self.r.n_gauss, int(n_pairs * 1.5) + 4096)
-            self.graph = None
+            self.graph = None   # captured again at the next call
         return st, n_pairs
 
 

@@ -181,3 +181,29 @@ def test_autograd_function_twice_before_one_backward(bs):
         for k in KEYS:
             a, b = getattr(p, k).grad, getattr(g, k)
             assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * float(b.abs().max()) + 1e-30), k
+
+
+def test_step_graph_captures_again_after_the_binning_buffers_move(bs):
+    """A synchronising call between replays (here a forward whose pairs
+    overflow the capacity, so the binning grows its buffers) leaves the
+    captured graph pointing at freed buffers: the next call must capture
+    again, and its step must equal the eager one."""
+    from paper_2503_16424_gb300.raster import StepGraph
+    make, tgt = _problem(bs)
+    r, curves = make()
+    grad = curves.zeros_like()
+    sg = StepGraph(r, curves, tgt, grad, headroom=1.0)
+    sg()
+    sg()
+    before = r.binning.allocations
+    curves.open_width.mul_(20.0)         # 485 -> 2531 pairs: the forward's binning grows its buffers
+    r.forward(curves)
+    assert r.binning.allocations > before
+    sg()
+    assert sg.check()[0] == bs.BS_OK and sg.overflows == 0
+    e, ce = make()
+    ce.open_width.mul_(20.0)
+    loss, _ = e.step(ce, tgt)
+    torch.cuda.synchronize()
+    assert torch.equal(r.img, e.img) and torch.equal(r.gauss, e.gauss)
+    assert abs(float(r.loss) - float(loss)) <= 1e-12 * float(loss)
