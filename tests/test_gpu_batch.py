@@ -69,7 +69,8 @@ def image_curve_slices(batch, b):
 
 
 def ocfg_of(im):
-    return OCfg(g_open=im.sample.g_open, rows_closed=im.sample.rows_closed, k_closed=im.sample.k_closed)
+    return OCfg(g_open=im.sample.g_open, rows_closed=im.sample.rows_closed, k_closed=im.sample.k_closed,
+                tangent_mode=im.sample.tangent_mode)
 
 
 @pytest.fixture(scope="module")
@@ -205,6 +206,64 @@ def test_batch_backward_matches_oracle(bs, ragged):
                                 torch.arange(im.width, dtype=torch.float64), indexing="ij")
         dC = r.batch.image(dimg, b).cpu().double().permute(1, 2, 0).reshape(-1, 3)
         dtab = oracle.render_grads(tab, xs.reshape(-1), ys.reshape(-1), dC, bg=im.bg)
+        dref = sample_vjp(as_curves(arr), oc, dtab, o_first)
+        cb = curve_grad_bound(arr, oc, o_first, blend_grad_bound(gauss[g0:g0 + n], im.width, im.height, dC, im.bg),
+                              dtab)
+        for k in KEYS:
+            if k in OPEN_KEYS:
+                got = getattr(grad, k)[r.batch.open0[b]:r.batch.open0[b] + im.n_open]
+            else:
+                got = getattr(grad, k)[r.batch.closed0[b]:r.batch.closed0[b] + im.n_closed]
+            if got.numel() == 0:
+                continue
+            e = grad_check(got.cpu(), dref[k], cb[k])
+            assert e <= 1.0, (b, k, e)
+
+
+def test_batch_with_mixed_tangent_modes_matches_oracle_and_single_canvas(bs):
+    """Images of one batch may take their rotations from different rules:
+    Eq. 8's neighbour difference (tangent_mode 0) beside the derivative
+    B'(t) (tangent_mode 1).  Per image: the table against the oracle and bit
+    for bit against the single-canvas call with the same mode, and the curve
+    gradients against the oracle (bars as above)."""
+    from paper_2503_16424_gb300.batch import BatchRasterizer
+    specs = SPECS[:3] + SPECS[5:6]
+    modes = (1, 0, 1, 1)
+    images, arrs, targets, curves, target = make_batch(bs, specs)
+    for im, m in zip(images, modes):
+        im.sample = bs.SampleCfg(g_open=im.sample.g_open, rows_closed=im.sample.rows_closed,
+                                 k_closed=im.sample.k_closed, tangent_mode=m)
+    r = BatchRasterizer(images, pair_capacity=1 << 16)
+    r.fit_capacity(curves)
+    r.forward(curves, target)
+    torch.cuda.synchronize()
+    assert r.batch.status()[0] == bs.BS_OK
+    gauss = r.gauss.cpu().numpy()
+    dimg = r.dimg.clone()
+    for b, im in enumerate(images):
+        g0, n = r.batch.gauss0[b], r.batch.n_gauss_of[b]
+        ref = oracle.render_image(table_from_f32(gauss[g0:g0 + n]), im.width, im.height, bg=im.bg)
+        r.batch.image(dimg, b).mul_((~ref["flag"]).to("cuda")[None].float())
+    grad = curves.zeros_like()
+    r.backward(curves, dimg, grad)
+    for b, (im, arr) in enumerate(zip(images, arrs)):
+        g0, n = r.batch.gauss0[b], r.batch.n_gauss_of[b]
+        oc = ocfg_of(im)
+        _, o_first = oracle.draw_order(arr["open_ctrl"], arr["open_width"], arr["closed_ctrl"], oc)
+        tab = oracle.gaussian_table(as_curves(arr), oc, o_first)
+        mine = gauss[g0:g0 + n].astype(np.float64)
+        ref = np.stack([tab[k].detach().numpy() for k in ("mx", "my", "ux", "uy", "isx", "isy")], 1)
+        assert np.abs(mine[:, 0:2] - ref[:, 0:2]).max() / max(im.width, im.height) <= 1e-5, b
+        assert np.abs(mine[:, 2:4] - ref[:, 2:4]).max() <= 1e-5, b
+        assert (np.abs(mine[:, 4:6] - ref[:, 4:6]) / ref[:, 4:6]).max() <= 1e-5, b
+        cv = bs.CurveSet.from_arrays(arr, device="cuda")
+        _, first1 = bs.curve_order(cv, im.sample)
+        assert np.array_equal(bs.sample_curves(cv, im.sample, first1).cpu().numpy(), gauss[g0:g0 + n]), b
+        ftab = table_from_f32(gauss[g0:g0 + n])
+        ys, xs = torch.meshgrid(torch.arange(im.height, dtype=torch.float64),
+                                torch.arange(im.width, dtype=torch.float64), indexing="ij")
+        dC = r.batch.image(dimg, b).cpu().double().permute(1, 2, 0).reshape(-1, 3)
+        dtab = oracle.render_grads(ftab, xs.reshape(-1), ys.reshape(-1), dC, bg=im.bg)
         dref = sample_vjp(as_curves(arr), oc, dtab, o_first)
         cb = curve_grad_bound(arr, oc, o_first, blend_grad_bound(gauss[g0:g0 + n], im.width, im.height, dC, im.bg),
                               dtab)
