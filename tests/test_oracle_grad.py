@@ -145,3 +145,63 @@ def test_curve_gradients_match_a_conic_form_blend(seed, W, H, n_open, n_closed):
             continue
         assert float((g - ref).abs().max()) <= 1e-9 * scale, k
     assert float(res["dcurves"]["open_ctrl"].abs().max()) > 0.0
+
+
+def test_colour_gradient_is_the_sum_of_alpha_t():
+    """With dL/dC = 1 in every channel, dL/dc_i = sum over pixels of
+    alpha_i T_i (Eq. 9 is linear in the colours), written out from the
+    forward's alphas in draw order."""
+    cfg = SampleCfg(g_open=6, rows_closed=3, k_closed=4, eps=0.3)
+    curves, _ = _case(7, 10, 9, 2, 1, cfg)
+    with torch.no_grad():
+        tab = oracle.gaussian_table({k: v.detach() for k, v in curves.items()}, cfg)
+    ys, xs = torch.meshgrid(torch.arange(9, dtype=torch.float64), torch.arange(10, dtype=torch.float64), indexing="ij")
+    xs, ys = xs.reshape(-1), ys.reshape(-1)
+    g = oracle.render_grads(tab, xs, ys, torch.ones(xs.shape[0], 3, dtype=torch.float64))
+    # alpha_i T_i per pixel, the walk written out with the three thresholds
+    from oracle.raster import ALPHA_MAX, ALPHA_MIN, T_MIN
+    w = torch.zeros(xs.shape[0], tab["mx"].shape[0], dtype=torch.float64)
+    for p in range(xs.shape[0]):
+        T = 1.0
+        for i in range(tab["mx"].shape[0]):
+            dx, dy = float(xs[p]) + 0.5 - float(tab["mx"][i]), float(ys[p]) + 0.5 - float(tab["my"][i])
+            a1 = float(tab["isx"][i]) * (float(tab["ux"][i]) * dx + float(tab["uy"][i]) * dy)
+            a2 = float(tab["isy"][i]) * (-float(tab["uy"][i]) * dx + float(tab["ux"][i]) * dy)
+            a = min(ALPHA_MAX, float(tab["o"][i]) * np.exp(-0.5 * (a1 * a1 + a2 * a2)))
+            if a < ALPHA_MIN:
+                continue
+            if T * (1 - a) < T_MIN:
+                break
+            w[p, i] = a * T
+            T *= 1 - a
+    exp = w.sum(0)
+    assert float(exp.max()) > 0.1
+    for ch in range(3):
+        assert torch.allclose(g["col"][:, ch], exp, atol=1e-12)
+
+
+def test_curve_gradients_rotate_with_the_scene():
+    """Rotating the curves and the target by 90 degrees rotates the image,
+    so the control-point gradients rotate with it: g'(x, y) = (g_y, -g_x)
+    at the rotated points (x, y) -> (y, W - x); the other gradients are
+    unchanged.  Catches a transposed or sign-flipped conic in the backward."""
+    cfg = SampleCfg(g_open=6, rows_closed=3, k_closed=4, eps=0.3)
+    W = 10
+    curves, target = _case(8, W, W, 2, 1, cfg)
+    rot = dict(curves)
+    for k in ("open_ctrl", "closed_ctrl"):
+        P = curves[k].detach()
+        rot[k] = torch.stack([P[..., 1], W - P[..., 0]], -1)
+    rot = as_curves({k: v.detach().numpy() for k, v in rot.items()})
+    # image pixel (x, y) moves to (y, W - 1 - x): rotate the target alike
+    target_r = torch.rot90(target, k=1, dims=(1, 2))
+    bg = (0.2, 0.1, 0.4)
+    a = step(curves, cfg, W, W, target, bg)
+    b = step(rot, cfg, W, W, target_r, bg)
+    assert abs(a["loss"] - b["loss"]) < 1e-12
+    for k in ("open_ctrl", "closed_ctrl"):
+        ga, gb = a["dcurves"][k], b["dcurves"][k]
+        assert torch.allclose(gb[..., 0], ga[..., 1], atol=1e-10)
+        assert torch.allclose(gb[..., 1], -ga[..., 0], atol=1e-10)
+    for k in ("open_width", "open_color", "open_opac", "closed_color", "closed_opac"):
+        assert torch.allclose(a["dcurves"][k], b["dcurves"][k], atol=1e-10), k

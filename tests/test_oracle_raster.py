@@ -167,3 +167,37 @@ def test_render_of_f32_table_roundtrip():
     rec = np.random.default_rng(9).uniform(0, 1, (5, 12)).astype(np.float32)
     t = table_from_f32(rec)
     assert t["mx"].dtype == F64 and np.array_equal(t["col"].numpy().astype(np.float32), rec[:, 7:10])
+
+
+def test_two_gaussians_at_a_pixel_closed_form():
+    """Two Gaussians over one pixel: C = c1 a1 + c2 a2 (1 - a1) + bg (1 - a1)
+    (1 - a2), T = (1 - a1)(1 - a2), with a_i = o_i exp(-d^T Sigma_i^-1 d / 2)
+    written out from the densities (Eq. 9-10), both above 1/255 and below
+    the clamp."""
+    S1 = np.array([[6.0, 1.5], [1.5, 3.0]])
+    S2 = np.array([[2.0, -0.4], [-0.4, 5.0]])
+    mu = np.array([[3.2, 2.9], [4.1, 3.6]])
+    o = np.array([0.7, 0.55])
+    col = np.array([[0.9, 0.1, 0.2], [0.2, 0.6, 0.95]])
+    bg = np.array([0.05, 0.3, 0.7])
+    tab = _table(mu[:, 0], mu[:, 1], np.stack([S1, S2]), o, col)
+    px, py = 3.5, 3.5
+    a = [o[i] * math.exp(-0.5 * (np.array([px, py]) - mu[i]) @ np.linalg.solve(S, np.array([px, py]) - mu[i]))
+         for i, S in enumerate((S1, S2))]
+    assert all(1 / 255 < x < 0.99 for x in a)
+    exp_C = col[0] * a[0] + col[1] * a[1] * (1 - a[0]) + bg * (1 - a[0]) * (1 - a[1])
+    r = oracle.render_pixels(tab, torch.tensor([3.0], dtype=F64), torch.tensor([3.0], dtype=F64), bg=tuple(bg))
+    assert np.allclose(r["C"][0].numpy(), exp_C, atol=1e-13)
+    assert abs(float(r["T"][0]) - (1 - a[0]) * (1 - a[1])) < 1e-13
+
+
+def test_clamp_bounds_the_transmittance_below():
+    """n opaque coincident Gaussians: each alpha is clamped to 0.99, so
+    before the stop rule T falls by 0.01 per Gaussian, and the pixel stops
+    at the Gaussian that would take T below 1e-4: T_final = 0.01^2."""
+    n = 5
+    tab = _table([4.0] * n, [4.0] * n, np.tile(np.eye(2) * 50.0, (n, 1, 1)), [1.0] * n, np.ones((n, 3)))
+    r = oracle.render_pixels(tab, torch.tensor([3.5], dtype=F64), torch.tensor([3.5], dtype=F64))
+    # centre pixel (4, 4) is at the mean: alpha = min(0.99, 1) = 0.99
+    assert abs(float(r["T"][0]) - 0.01 ** 2) < 1e-15
+    assert int(r["last"][0]) == 1
