@@ -363,6 +363,10 @@ class Binning:
         # allocations so far: a captured graph holds the addresses of the
         # buffers of one allocation, so it is stale once this count moves
         self.allocations = 0
+        # whether the current workspace holds a binning (a new one holds none
+        # until the next run), and the pairs of the last synchronising run
+        self._binned = False
+        self._last_pairs = 0
 
     def _alloc(self, n_gauss, capacity):
         nbytes = bin_tiles_workspace(n_gauss, self.canvas, capacity)
@@ -371,6 +375,7 @@ class Binning:
         self.capacity = capacity
         self.n_gauss = n_gauss
         self.allocations += 1
+        self._binned = False
 
     def run(self, gauss: torch.Tensor):
         n_gauss = int(gauss.shape[0])
@@ -389,6 +394,8 @@ class Binning:
                 continue
             _check("bs_bin_tiles", st)
             self.n_pairs = int(n_pairs.value)
+            self._last_pairs = self.n_pairs
+            self._binned = True
             return self
         raise BSError("bs_bin_tiles", BS_ERR_CAPACITY)
 
@@ -424,11 +431,18 @@ class Binning:
                                                              self.ws.numel(), self.capacity, _ptr(n_pairs_dev),
                                                              _ptr(self.keys), _ptr(self.ranges), _stream()))
         self.n_pairs = None
+        self._binned = True
         return self
 
     def result(self):
         """(status, P) of the last binning (synchronises): BS_OK or
-        BS_ERR_CAPACITY, and the pairs it found; sets n_pairs."""
+        BS_ERR_CAPACITY, and the pairs it found; sets n_pairs.  When the
+        buffers were allocated anew since the last binning (prepare, fit),
+        the workspace holds none: the last synchronising run's pairs are
+        reported against the new capacity."""
+        if not self._binned:
+            self.n_pairs = self._last_pairs
+            return (BS_OK if self._last_pairs <= self.capacity else BS_ERR_CAPACITY), self._last_pairs
         st, n = c_int32(0), c_int64(0)
         _check("bs_bin_tiles_result", lib.bs_bin_tiles_result(_ptr(self.ws), self.ws.numel(), ctypes.byref(st),
                                                                ctypes.byref(n), _stream()))
@@ -436,6 +450,8 @@ class Binning:
         return int(st.value), int(n.value)
 
     def device_status(self) -> int:
+        if not self._binned:   # buffers allocated anew since the last binning: nothing recorded
+            return BS_OK
         out = c_int32(0)
         _check("bs_device_status", lib.bs_device_status(_ptr(self.ws), self.ws.numel(), ctypes.byref(out),
                                                          _stream()))

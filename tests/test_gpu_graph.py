@@ -207,3 +207,24 @@ def test_step_graph_captures_again_after_the_binning_buffers_move(bs):
     torch.cuda.synchronize()
     assert torch.equal(r.img, e.img) and torch.equal(r.gauss, e.gauss)
     assert abs(float(r.loss) - float(loss)) <= 1e-12 * float(loss)
+
+
+def test_step_graph_check_right_after_a_shrinking_fit(bs):
+    """A rasterizer made with a large capacity: the first (eager) call fits
+    the capacity down, which allocates a workspace no binning has written
+    yet; check() at once must report the eager run's pairs, not read the
+    fresh workspace, and the replays that follow must match."""
+    from paper_2503_16424_gb300.raster import Rasterizer, StepGraph
+    make, tgt = _problem(bs)
+    _, curves = make()
+    r = Rasterizer(bs.Canvas(96, 80, 16, (0.1, 0.2, 0.3)), bs.SampleCfg(g_open=10, rows_closed=4, k_closed=6),
+                   curves.n_open, curves.n_closed, pair_capacity=1 << 20)
+    grad = curves.zeros_like()
+    sg = StepGraph(r, curves, tgt, grad)
+    sg()
+    before = r.binning.allocations
+    st, n = sg.check()
+    assert st == bs.BS_OK and 0 < n < r.binning.capacity < (1 << 20) and r.binning.allocations == before
+    assert r.binning.device_status() == bs.BS_OK
+    sg()
+    assert sg.check() == (bs.BS_OK, n) and sg.overflows == 0
