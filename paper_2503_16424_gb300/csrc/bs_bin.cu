@@ -292,105 +292,170 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const int *counts, int 
   }
 }
 
-// The difference array's row and column scans, the tile scan and the digit
-// starts in one CTA, with the whole (tiles_y + 1) x (tiles_x + 1) array and
-// the per-tile prefixes in shared memory (used when they fit; at most two
-// sort passes).  Digit counts: pass 0 (digit t mod 2^digit_bits) by
-// shared-memory adds from consecutive tiles, which hit distinct digits; the
-// last pass's digit d covers the tile range [d 2^shift, (d + 1) 2^shift),
-// whose count is a difference of two prefixes.
-constexpr int kFusedMaxWords = 48 * 1024;   // ints of array + prefixes in shared memory
+// The difference array's scans, the tile ranges and the digit starts in one
+// CTA of 1024 threads, with the per-tile counts in shared memory (used when
+// they fit; at most two sort passes).  Only the tiles' own part of the
+// difference array matters (a count sums the array above and left of its
+// tile), so shared memory holds tiles_y rows of ldc = tiles_x rounded up to
+// 4 ints, read and written 16 bytes a lane:
+//   1. row scans, one warp per row, 4 consecutive entries a lane, fused with
+//      the load from global memory;
+//   2. column scans in row blocks: a thread sums its column over its block,
+//      then adds the blocks above and rewrites the block as running sums;
+//   3. per row the total, a block scan of the totals (each row's first
+//      pair), then per row an exclusive scan of its counts, written as the
+//      ranges of its tiles.
+// Digit counts: pass 0 (digit t mod 2^digit_bits) by shared-memory adds
+// from consecutive tiles, which hit distinct digits; the last pass's digit
+// d covers the tile range [d 2^shift, (d + 1) 2^shift), whose count is the
+// difference of the prefixes at its two ends (kept as marks).
+constexpr int kFusedMaxWords = 48 * 1024;   // ints of dynamic shared memory
+__host__ __device__ constexpr int fused_ldc(int tiles_x) { return (tiles_x + 3) & ~3; }
+// row blocks of the column scans: about one column block per thread, at most 64 blocks
+__host__ __device__ constexpr int fused_row_blocks(int tiles_x, int tiles_y) {
+  return tiles_x >= 1024 ? 1 : ((1024 / tiles_x < 64 ? 1024 / tiles_x : 64) < tiles_y
+                                    ? (1024 / tiles_x < 64 ? 1024 / tiles_x : 64) : tiles_y);
+}
+// ints of dynamic shared memory: the counts, the column block totals, the row starts
+__host__ __device__ constexpr int64_t fused_words(int tiles_x, int tiles_y) {
+  return (int64_t)tiles_y * fused_ldc(tiles_x) + (int64_t)fused_row_blocks(tiles_x, tiles_y) * tiles_x + tiles_y;
+}
+
 __global__ void __launch_bounds__(1024) fused_tile_scan_kernel(const int *__restrict__ diff, int tiles_x,
                                                                int tiles_y, int passes, int digit_bits,
                                                                const Hdr *hdr, uint2 *__restrict__ ranges,
                                                                uint32_t *__restrict__ hist) {
-  extern __shared__ int s_dyn[];
+  extern __shared__ __align__(16) int s_dyn[];
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_dig[kMaxPasses * 256];
-  const int rows = tiles_y + 1, cols = tiles_x + 1;
-  const int n = tiles_x * tiles_y;
-  int *s_cnt = s_dyn;                                        // [rows][cols]
-  uint32_t *s_pre = reinterpret_cast<uint32_t *>(s_dyn + rows * cols);  // [n + 1]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) s_dig[i] = 0u;
-  {
-    const int m = rows * cols;
-    constexpr int kU = 8;
-    for (int i0 = 0; i0 < m; i0 += kU * 1024) {
-      int v[kU];
+  __shared__ uint32_t s_mark[257];
+  const int W = tiles_x, H = tiles_y, cols = tiles_x + 1;
+  const int ldc = fused_ldc(W), nb = fused_row_blocks(W, H);
+  int *s_c = s_dyn;                              // [H][ldc]
+  int *s_bt = s_dyn + (size_t)H * ldc;           // [nb][W]
+  uint32_t *s_row = reinterpret_cast<uint32_t *>(s_bt + (size_t)nb * W);  // [H]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < kMaxPasses * 256; i += blockDim.x) s_dig[i] = 0u;
+  // 1. row scans, four rows of a warp (rg + 32 j) at a time, their loads issued together
+  for (int rg = warp; rg < H; rg += 128) {
+    int carry[4] = {0, 0, 0, 0};
+    for (int c0 = 0; c0 < W; c0 += 128) {
+      const int c = c0 + 4 * lane;
+      int v[4][4];
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int i = i0 + u * 1024 + threadIdx.x;
-        v[u] = i < m ? diff[i] : 0;
+      for (int j = 0; j < 4; ++j) {
+        const int r = rg + 32 * j;
+        const int *src = diff + (size_t)r * cols;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[j][i] = (r < H && c + i < W) ? src[c + i] : 0;
       }
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int i = i0 + u * 1024 + threadIdx.x;
-        if (i < m) s_cnt[i] = v[u];
+      for (int j = 0; j < 4; ++j) {
+        const int r = rg + 32 * j;
+        v[j][1] += v[j][0];
+        v[j][2] += v[j][1];
+        v[j][3] += v[j][2];
+        const int incl = (int)warp_incl_scan((uint32_t)v[j][3], lane);
+        const int off = carry[j] + incl - v[j][3];
+        if (r < H && c < ldc)
+          *reinterpret_cast<int4 *>(s_c + (size_t)r * ldc + c) =
+              make_int4(off + v[j][0], off + v[j][1], off + v[j][2], off + v[j][3]);
+        carry[j] += __shfl_sync(0xffffffffu, incl, 31);
       }
     }
   }
   __syncthreads();
-  for (int r = warp; r < rows; r += 32) {      // row scans
-    int carry = 0;
-    for (int c0 = 0; c0 < cols; c0 += 32) {
-      const int c = c0 + lane;
-      int v = c < cols ? s_cnt[r * cols + c] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-      }
-      if (c < cols) s_cnt[r * cols + c] = carry + v;
-      carry += __shfl_sync(0xffffffffu, v, 31);
+  // 2. column scans: thread (b, x) owns rows [b rb, (b + 1) rb) of column x
+  const int rb = (H + nb - 1) / nb;
+  for (int task = tid; task < nb * W; task += blockDim.x) {
+    const int b = task / W, x = task - b * W;
+    const int r1 = min(H, (b + 1) * rb);
+    int s = 0;
+    for (int r = b * rb; r < r1; ++r) s += s_c[(size_t)r * ldc + x];
+    s_bt[task] = s;
+  }
+  __syncthreads();
+  for (int task = tid; task < nb * W; task += blockDim.x) {
+    const int b = task / W, x = task - b * W;
+    const int r1 = min(H, (b + 1) * rb);
+    int s = 0;
+    for (int q = 0; q < b; ++q) s += s_bt[q * W + x];
+    for (int r = b * rb; r < r1; ++r) {
+      s += s_c[(size_t)r * ldc + x];
+      s_c[(size_t)r * ldc + x] = s;
     }
   }
   __syncthreads();
-  for (int c = warp; c < cols; c += 32) {      // column scans
-    int carry = 0;
-    for (int r0 = 0; r0 < rows; r0 += 32) {
-      const int r = r0 + lane;
-      int v = r < rows ? s_cnt[r * cols + c] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
+  // 3a. row totals (counts of the columns x < W only: the padding holds partial sums)
+  for (int r = warp; r < H; r += 32) {
+    uint32_t s = 0;
+    for (int c0 = 0; c0 < W; c0 += 128) {
+      const int c = c0 + 4 * lane;
+      if (c < W) {
+        const int4 v = *reinterpret_cast<const int4 *>(s_c + (size_t)r * ldc + c);
+        s += (uint32_t)v.x + (c + 1 < W ? (uint32_t)v.y : 0u) + (c + 2 < W ? (uint32_t)v.z : 0u) +
+             (c + 3 < W ? (uint32_t)v.w : 0u);
       }
-      if (r < rows) s_cnt[r * cols + c] = carry + v;
-      carry += __shfl_sync(0xffffffffu, v, 31);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) s_row[r] = s;
   }
   __syncthreads();
-  // exclusive prefix over tiles: thread i sums tiles [i run, (i + 1) run)
-  const int run = (n + 1023) / 1024;
-  const int t0 = min(n, (int)threadIdx.x * run), t1 = min(n, t0 + run);
-  const int ty0 = t0 / tiles_x, tx0 = t0 - ty0 * tiles_x;
-  uint32_t sum = 0;
-  for (int t = t0, ty = ty0, tx = tx0; t < t1; ++t) {
-    sum += (uint32_t)s_cnt[ty * cols + tx];
-    if (++tx == tiles_x) tx = 0, ++ty;
-  }
+  // 3b. each row's first pair: thread i sums rows [i run, (i + 1) run)
   uint32_t total;
-  uint32_t start = block_excl_scan1024(sum, s_warp, &total);
-  for (int t = t0, ty = ty0, tx = tx0; t < t1; ++t) {
-    s_pre[t] = start;
-    start += (uint32_t)s_cnt[ty * cols + tx];
-    if (++tx == tiles_x) tx = 0, ++ty;
+  {
+    const int run = (H + 1023) / 1024;
+    const int r0 = min(H, tid * run), r1 = min(H, r0 + run);
+    uint32_t sum = 0;
+    for (int r = r0; r < r1; ++r) sum += s_row[r];
+    uint32_t start = block_excl_scan1024(sum, s_warp, &total);
+    for (int r = r0; r < r1; ++r) {
+      const uint32_t v = s_row[r];
+      s_row[r] = start;
+      start += v;
+    }
   }
-  if (threadIdx.x == 0) s_pre[n] = total;
   __syncthreads();
-  // ranges, coalesced (all empty when nothing is sorted); pass-0 digit counts
+  // 3c. per row: the exclusive scan of its counts, the ranges, the digit counts
   const uint32_t dmask = (1u << digit_bits) - 1;
-  const bool over = (hdr->status & kDevErrCapacity) != 0u;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    const uint32_t pre = s_pre[t], v = s_pre[t + 1] - pre;
-    ranges[t] = (v && !over) ? make_uint2(pre, pre + v) : make_uint2(0u, 0u);
-    if (passes > 1 && v) atomicAdd(&s_dig[t & dmask], v);
-  }
   const int hshift = digit_bits * (passes - 1);
+  const uint32_t hmask = (1u << hshift) - 1;
+  const bool over = (hdr->status & kDevErrCapacity) != 0u;  // nothing sorted: every range empty
+  for (int r = warp; r < H; r += 32) {
+    uint32_t carry = s_row[r];
+    for (int c0 = 0; c0 < W; c0 += 128) {
+      const int c = c0 + 4 * lane;
+      uint32_t v[4] = {0u, 0u, 0u, 0u};
+      if (c < W) {
+        const int4 q = *reinterpret_cast<const int4 *>(s_c + (size_t)r * ldc + c);
+        v[0] = (uint32_t)q.x;
+        v[1] = c + 1 < W ? (uint32_t)q.y : 0u;
+        v[2] = c + 2 < W ? (uint32_t)q.z : 0u;
+        v[3] = c + 3 < W ? (uint32_t)q.w : 0u;
+      }
+      const uint32_t lsum = v[0] + v[1] + v[2] + v[3];
+      const uint32_t incl = warp_incl_scan(lsum, lane);
+      uint32_t pre = carry + incl - lsum;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (c + i < W) {
+          const uint32_t t = (uint32_t)r * (uint32_t)W + (uint32_t)(c + i);
+          ranges[t] = (v[i] && !over) ? make_uint2(pre, pre + v[i]) : make_uint2(0u, 0u);
+          if (passes > 1 && v[i]) atomicAdd(&s_dig[t & dmask], v[i]);
+          if ((t & hmask) == 0u) s_mark[t >> hshift] = pre;
+        }
+        pre += v[i];
+      }
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  __syncthreads();
+  // the last pass's digit counts: prefix differences between marks
+  const int n = W * H;
   const int nmark = (n + (1 << hshift) - 1) >> hshift;
-  for (int d = threadIdx.x; d < nmark; d += blockDim.x)   // last pass: prefix differences
-    s_dig[(passes - 1) * 256 + d] = s_pre[min(n, (d + 1) << hshift)] - s_pre[d << hshift];
+  for (int d = tid; d < nmark; d += blockDim.x)
+    s_dig[(passes - 1) * 256 + d] = (d + 1 < nmark ? s_mark[d + 1] : total) - s_mark[d];
   __syncthreads();
   if (warp < passes) {  // per pass, the exclusive prefix over digits
     uint32_t carry = 0;
@@ -1130,8 +1195,8 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
         local, partial, rects, p.n_gauss, (uint32_t)div_up64(p.capacity, kEmitTile), owner);
     BS_LAUNCHED("chunk_owner_kernel");
   }
-  if ((int64_t)rows * cols + p.n_tiles + 1 <= kFusedMaxWords && p.passes <= 2) {
-    const size_t smem = sizeof(int) * ((size_t)rows * cols + (size_t)p.n_tiles + 1);
+  if (fused_words(p.tiles_x, p.tiles_y) <= kFusedMaxWords && p.passes <= 2) {
+    const size_t smem = sizeof(int) * (size_t)fused_words(p.tiles_x, p.tiles_y);
     static bool attr_set[64] = {};
     int dev = 0;
     BS_CUDA(cudaGetDevice(&dev));

@@ -684,12 +684,44 @@ __device__ __forceinline__ float area_key(const bs_curves &c, int i) {
 constexpr int kOrderThreads = 256;
 constexpr int kOrderChunk = 256;  // keys compared per CTA
 
+// The keys among sk[q0, q1) below `mine` (kLe: or equal to it), four at a
+// time from the first multiple of 4 (sk 16-byte aligned).
+template <bool kLe>
+__device__ __forceinline__ uint32_t count_keys(const uint32_t *sk, int q0, int q1, uint32_t mine) {
+  uint32_t c = 0;
+  int q = q0;
+  for (; q < q1 && (q & 3); ++q) c += kLe ? sk[q] <= mine : sk[q] < mine;
+  for (; q + 4 <= q1; q += 4) {
+    const uint4 k = *reinterpret_cast<const uint4 *>(sk + q);
+    c += kLe ? (uint32_t)(k.x <= mine) + (k.y <= mine) + (k.z <= mine) + (k.w <= mine)
+             : (uint32_t)(k.x < mine) + (k.y < mine) + (k.z < mine) + (k.w < mine);
+  }
+  for (; q < q1; ++q) c += kLe ? sk[q] <= mine : sk[q] < mine;
+  return c;
+}
+
+// Of the chunk entries q < m (curve base + q, key sk[q]), those preceding
+// curve i (key mine): an entry before i precedes it when its key is <= mine,
+// one at or after i when its key is < mine.  `before` counts them all, `ob`
+// those with q < open_end (the open curves).
+__device__ __forceinline__ void count_preceding(const uint32_t *sk, int m, int base, int i, uint32_t mine,
+                                                int open_end, uint32_t &before, uint32_t &ob) {
+  const int e = min(max(i - base, 0), m), oe = min(max(open_end, 0), m);
+  const int lo = min(e, oe), hi = max(e, oe);
+  const uint32_t a = count_keys<true>(sk, 0, lo, mine);     // before i, open
+  const uint32_t b = count_keys<true>(sk, lo, e, mine);     // before i, closed (oe < e)
+  const uint32_t d = count_keys<false>(sk, e, hi, mine);    // after i, open (oe > e)
+  const uint32_t f = count_keys<false>(sk, hi, m, mine);    // after i, closed
+  before = a + b + d + f;
+  ob = a + d;
+}
+
 // Rank by counting: rank_i = #{j : key_j < key_i or (key_j == key_i, j < i)}.
 // CTA (x, y) compares its 256 curves against the keys of chunk y and adds its
 // counts (rank, and how many of the preceding curves are open) atomically.
 __global__ void __launch_bounds__(kOrderThreads) curve_order_count_kernel(bs_curves c, uint32_t *rank,
                                                                          uint32_t *open_before) {
-  __shared__ uint32_t sk[kOrderChunk];
+  __shared__ __align__(16) uint32_t sk[kOrderChunk];
   const int n = c.n_open + c.n_closed;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int base = blockIdx.y * kOrderChunk;
@@ -698,14 +730,8 @@ __global__ void __launch_bounds__(kOrderThreads) curve_order_count_kernel(bs_cur
   const uint32_t mine = i < n ? key_order(area_key(c, i)) : 0u;
   __syncthreads();
   if (i >= n) return;
-  uint32_t before = 0, ob = 0;
-  const int open_end = c.n_open - base;  // chunk entries q < open_end are open curves
-  for (int q = 0; q < m; ++q) {
-    const uint32_t kq = sk[q];
-    const bool prec = kq < mine || (kq == mine && base + q < i);
-    before += prec;
-    ob += prec && q < open_end;
-  }
+  uint32_t before, ob;
+  count_preceding(sk, m, base, i, mine, c.n_open - base, before, ob);  // entries q < n_open - base are open
   if (before) atomicAdd(&rank[i], before);
   if (ob) atomicAdd(&open_before[i], ob);
 }
@@ -731,7 +757,7 @@ __global__ void __launch_bounds__(kOrderThreads) batch_curve_order_count_kernel(
                                                                                const BatchImage *__restrict__ tab,
                                                                                int n_images, uint32_t *rank,
                                                                                uint32_t *open_before) {
-  __shared__ uint32_t sk[kOrderChunk];
+  __shared__ __align__(16) uint32_t sk[kOrderChunk];
   const int b = last_image_le<&BatchImage::order0>(tab, n_images, blockIdx.x);
   const BatchImage &im = tab[b];
   const int local = blockIdx.x - (int)im.order0;
@@ -745,14 +771,8 @@ __global__ void __launch_bounds__(kOrderThreads) batch_curve_order_count_kernel(
   const uint32_t mine = i < n ? key_order(area_key(c, gi)) : 0u;
   __syncthreads();
   if (i >= n) return;
-  uint32_t before = 0, ob = 0;
-  const int open_end = im.n_open - base;  // chunk entries q < open_end are open curves
-  for (int q = 0; q < m; ++q) {
-    const uint32_t kq = sk[q];
-    const bool prec = kq < mine || (kq == mine && base + q < i);
-    before += prec;
-    ob += prec && q < open_end;
-  }
+  uint32_t before, ob;
+  count_preceding(sk, m, base, i, mine, im.n_open - base, before, ob);  // entries q < n_open - base are open
   if (before) atomicAdd(&rank[gi], before);
   if (ob) atomicAdd(&open_before[gi], ob);
 }
