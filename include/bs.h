@@ -33,6 +33,12 @@
  *     activated values in [0, 1].
  *   - Images are planar float32 [3][H][W]; per-pixel maps are [H][W].
  *   - Only sm_103a is supported; other devices return BS_ERR_UNSUPPORTED.
+ *   - The calls may be made from several host threads.  Per device, the
+ *     library raises some kernels' dynamic shared-memory limits once (under
+ *     a lock) and keeps a status word and the addresses of its device
+ *     arrays; a device reset (cudaDeviceReset) discards all of them, so do
+ *     not call the library on a device after resetting it in the same
+ *     process.
  */
 #ifndef BEZIER_SPLATTING_BS_H
 #define BEZIER_SPLATTING_BS_H

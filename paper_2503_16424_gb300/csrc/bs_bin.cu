@@ -1197,13 +1197,17 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
   }
   if (fused_words(p.tiles_x, p.tiles_y) <= kFusedMaxWords && p.passes <= 2) {
     const size_t smem = sizeof(int) * (size_t)fused_words(p.tiles_x, p.tiles_y);
-    static bool attr_set[64] = {};
+    static bool attr_set[64] = {};  // per device, under attr_mu
+    static std::mutex attr_mu;
     int dev = 0;
     BS_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-      BS_CUDA(cudaFuncSetAttribute(fused_tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(int) * kFusedMaxWords)));
-      if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    {
+      std::lock_guard<std::mutex> lock(attr_mu);
+      if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        BS_CUDA(cudaFuncSetAttribute(fused_tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(int) * kFusedMaxWords)));
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+      }
     }
     fused_tile_scan_kernel<<<1, 1024, smem, s>>>(diff, p.tiles_x, p.tiles_y, p.passes, p.digit_bits, hdr, ranges,
                                                  hist);

@@ -27,6 +27,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "bs_internal.cuh"
 
@@ -890,13 +891,15 @@ size_t launch_smem(const bs_curves &c, const bs_sample_cfg &cfg, bool with_grad)
 template <typename Kernel>
 bs_status raise_smem(Kernel k, size_t smem, int slot) {
   constexpr int kMaxDev = 64;
-  static size_t done[kMaxDev][2] = {};
+  static size_t done[kMaxDev][2] = {};  // per device and slot, under mu
+  static std::mutex mu;
   int dev = 0;
   BS_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDev) {
     set_error("device %d: at most %d devices supported", dev, kMaxDev);
     return BS_ERR_UNSUPPORTED;
   }
+  std::lock_guard<std::mutex> lock(mu);
   if (smem > done[dev][slot]) {
     BS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     done[dev][slot] = smem;
