@@ -399,16 +399,9 @@ def run_ours(args, rank, world):
         "periodic": {"prune_densify_ms": round(float(np.mean(pd_ms)), 4), "not_in_step": True, **pd_stats},
     }
     # kernels launched per step: curve_order 2 (count, first), sample 1,
-    # binning 6 + 3 per sort pass - 1 (zero, count, scan_partials,
-    # chunk_owner, fused_tile_scan, emit; upsweep, scan_parts, downsweep per
-    # pass, the first pass's counts coming from emit; a tile grid too large
-    # for one CTA's shared memory takes 2 more), render_fwd with the L2 term
-    # 1, render_bwd 2 (blend backward, grads_from_sums), sample_bwd 1;
-    # memsets are not kernels
-    passes = -(-max(1, (canvas.n_tiles - 1).bit_length()) // 8)
-    tiles_x, tiles_y = -(-canvas.width // canvas.tile), -(-canvas.height // canvas.tile)
-    fused = (tiles_x + 1) * (tiles_y + 1) + canvas.n_tiles + 1 <= 48 * 1024
-    per_step = 2 + 1 + (6 + 3 * passes - 1 + (0 if fused and passes <= 2 else 2)) + 1 + 2 + 1
+    # binning (binning_launches), render_fwd with the L2 term 1, render_bwd 2
+    # (blend backward, grads_from_sums), sample_bwd 1; memsets are not kernels
+    per_step = 2 + 1 + binning_launches(canvas, r.n_gauss) + 1 + 2 + 1
     out["gpu_launches"] = per_step * args.steps
     if not args.no_batched:
         out["batched"] = run_batched(dev, args, rank, world)
@@ -418,6 +411,27 @@ def run_ours(args, rank, world):
         out["cpu_baseline"] = cpu_baseline_culled()
         out["cpu_baseline_brute_force"] = cpu_baseline(side=8)
     return out
+
+
+def binning_launches(canvas, n_gauss: int) -> int:
+    """Kernels one bs_bin_tiles call launches on one canvas: zero, count,
+    scan_partials and the tile scan (one CTA when the tile counts fit its
+    shared memory, else row scans, column scans and the scan), then either
+    the two-level counting sort (32-bit keys, at most 512 x 512 tiles: 7
+    kernels) or the key emission and the radix passes (chunk_owner, emit,
+    then upsweep, scan_parts and downsweep per pass, the first pass's counts
+    coming from emit)."""
+    tx, ty = -(-canvas.width // canvas.tile), -(-canvas.height // canvas.tile)
+    n_tiles = tx * ty
+    tbits = max(1, (n_tiles - 1).bit_length())
+    gbits = max(1, (max(n_gauss, 1) - 1).bit_length())
+    passes = -(-tbits // 8)
+    ldc, nb = (tx + 3) & ~3, (1 if tx >= 1024 else min(min(1024 // tx, 64), ty))
+    fused = ty * ldc + nb * tx + ty <= 48 * 1024 and passes <= 2
+    n_g1 = -(-max(n_gauss, 1) // 256)
+    rows = gbits + tbits <= 32 and ty <= 512 and tx <= 512 and ty * n_g1 <= (1 << 24)
+    sort = 7 if rows else 2 + 3 * passes - 1
+    return 3 + (1 if fused else 3) + sort
 
 
 def roofline(fwd_ms, bwd_ms, e_fwd, e_bwd, n_sm, peaks, src):

@@ -423,7 +423,7 @@ bs_status bs_bin_tiles_static(const float *gauss, int64_t n_gauss, const bs_canv
   if (!n_pairs_out) return invalid("n_pairs_out is NULL");
   *n_pairs_out = 0;
   BinPlan p;
-  BS_TRY(plan_binning(n_gauss, *canvas, pair_capacity, &p));
+  BS_TRY(plan_binning(n_gauss, *canvas, pair_capacity, &p, false));
   if (p.bytes > kStaticScratchBytes)
     return invalid("this binning needs %zu bytes of scratch; the fixed scratch of bs_bin_tiles_static holds %zu "
                    "(lower pair_capacity or n_gauss, or use bs_bin_tiles with a workspace)",

@@ -1109,9 +1109,333 @@ __global__ void __launch_bounds__(kEmitThreads) batch_emit_kernel(const uint32_t
     if (s_h[d]) atomicAdd(&hist1[(size_t)d * parts + (blockIdx.x >> 1)], s_h[d]);
 }
 
+// ---- two-level binning (one canvas, 32-bit keys) ----
+// A stable counting sort that uses the rectangles' shape instead of sorting
+// the keys.  Level 1 puts every Gaussian into the list of each tile row its
+// rectangle covers, in ascending index.  Per chunk of 256 Gaussians: a bit
+// per (row, Gaussian), one 32-bit ballot per warp and row, gives the chunk's
+// count per row (row_count_kernel); their exclusive scan over the chunks of
+// each row (row_scan_kernel) and the rows' starts (row_starts_kernel) give
+// where each chunk's Gaussians of a row begin; a Gaussian's rank among them
+// is the population count of the row's bits below its own
+// (row_scatter_kernel).  Level 2 does the same for the columns of each
+// row's list, cut into chunks of 256 entries (col_count_kernel with a
+// difference array per chunk, col_scan_kernel, col_scatter_kernel): a pair's
+// place is its tile's first pair, plus the tile's pairs in the row's earlier
+// chunks, plus its rank among the chunk's entries covering the tile.  The
+// keys come out as the radix sort writes them, (tile << gbits) | g in
+// (tile, g) order.
+constexpr int kRowChunk = 256;   // Gaussians per level-1 chunk (8 words of bits per row)
+constexpr int kColChunk = 256;   // row-list entries per level-2 chunk (8 words of bits per column)
+constexpr int kRowsMax = 512, kColsMax = 512;
+constexpr int kColGrid = 152 * 8;  // CTAs of the level-2 kernels (eight per SM)
+static_assert(kRowChunk == 256 && kColChunk == 256, "eight 32-bit words of bits per line");
+
+// The 32 items of a warp (item = lane) over lines [a, b] (valid items only):
+// bm[l * 8 + warp] = the ballot of the items covering line l, for every line
+// some item of the warp covers.  Lines no item covers are left as they are.
+__device__ __forceinline__ void warp_line_bits(uint32_t *bm, bool valid, int a, int b, int warp) {
+  const unsigned lo = __reduce_min_sync(0xffffffffu, valid ? (unsigned)a : 0xffffffffu);
+  const unsigned hi = __reduce_max_sync(0xffffffffu, valid ? (unsigned)b : 0u);
+  for (unsigned l = lo; l <= hi && lo != 0xffffffffu; ++l) {
+    const unsigned bits = __ballot_sync(0xffffffffu, valid && (int)l >= a && (int)l <= b);
+    if ((threadIdx.x & 31) == 0) bm[l * 8 + warp] = bits;
+  }
+}
+
+__device__ __forceinline__ uint32_t line_count(const uint32_t *bm, int l) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) c += __popc(bm[l * 8 + w]);
+  return c;
+}
+
+// Exclusive scan of one value per thread over a CTA of kThreads (a multiple
+// of 32, at most 1024); *total gets the sum.  Starts and ends with a barrier
+// crossed by every thread, so s_warp can be reused right after.
+template <int kThreads>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+  constexpr int kWarps = kThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  const uint32_t incl = warp_incl_scan(v, lane);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = warp_incl_scan(lane < kWarps ? s_warp[lane] : 0u, lane);
+    if (lane < kWarps) s_warp[lane] = w;
+  }
+  __syncthreads();
+  *total = s_warp[kWarps - 1];
+  const uint32_t ex = (warp ? s_warp[warp - 1] : 0u) + incl - v;
+  __syncthreads();
+  return ex;
+}
+
+// Level 1: the bits of chunk blockIdx.x's Gaussians over the rows.
+__device__ __forceinline__ void gauss_row_bits(const uint2 *__restrict__ rects, int64_t n_gauss, int H, uint32_t *s_bm) {
+  for (int i = threadIdx.x; i < H * 8; i += kRowChunk) s_bm[i] = 0u;
+  __syncthreads();
+  const int64_t g = (int64_t)blockIdx.x * kRowChunk + threadIdx.x;
+  const uint2 rc = g < n_gauss ? rects[g] : make_uint2(0u, 0u);
+  const int h = (int)(rc.y >> 16), ty0 = (int)(rc.x >> 16);
+  warp_line_bits(s_bm, (rc.y & 0xffffu) != 0u && h != 0, ty0, ty0 + h - 1, threadIdx.x >> 5);
+  __syncthreads();
+}
+
+// t1[row][chunk] = the chunk's Gaussians covering the row.  Dynamic shared
+// memory: 8 H words.
+__global__ void __launch_bounds__(kRowChunk) row_count_kernel(const uint2 *__restrict__ rects, int64_t n_gauss,
+                                                              int H, int n_g1, const unsigned long long *count,
+                                                              uint32_t *__restrict__ t1) {
+  extern __shared__ uint32_t s_rows[];
+  if (*count == 0) return;  // nothing to sort (no pairs, or more than the capacity)
+  gauss_row_bits(rects, n_gauss, H, s_rows);
+  for (int r = threadIdx.x; r < H; r += kRowChunk) t1[(size_t)r * n_g1 + blockIdx.x] = line_count(s_rows, r);
+}
+
+// One CTA per row: t1[row][.] becomes its exclusive scan over the chunks,
+// rowcnt[row] the row's total.
+__global__ void __launch_bounds__(1024) row_scan_kernel(uint32_t *__restrict__ t1, int n_g1,
+                                                        const unsigned long long *count,
+                                                        uint32_t *__restrict__ rowcnt) {
+  __shared__ uint32_t s_warp[32];
+  if (*count == 0) return;
+  uint32_t *row = t1 + (size_t)blockIdx.x * n_g1;
+  uint32_t carry = 0;
+  for (int base = 0; base < n_g1; base += 1024) {
+    const int i = base + threadIdx.x;
+    const uint32_t v = i < n_g1 ? row[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_excl_scan<1024>(v, s_warp, &total);
+    if (i < n_g1) row[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) rowcnt[blockIdx.x] = carry;
+}
+
+// One CTA: rowstart[r] = the list entries of rows < r (rowstart[H] = all),
+// chstart[r] = the level-2 chunks of rows < r (chstart[H] = all).
+__global__ void __launch_bounds__(1024) row_starts_kernel(const uint32_t *__restrict__ rowcnt, int H,
+                                                          const unsigned long long *count,
+                                                          uint32_t *__restrict__ rowstart,
+                                                          uint32_t *__restrict__ chstart) {
+  __shared__ uint32_t s_warp[32];
+  if (*count == 0) return;
+  const int run = (H + 1023) / 1024;
+  const int r0 = min(H, (int)threadIdx.x * run), r1 = min(H, r0 + run);
+  uint32_t s = 0, c = 0;
+  for (int r = r0; r < r1; ++r) {
+    s += rowcnt[r];
+    c += (rowcnt[r] + kColChunk - 1) / kColChunk;
+  }
+  uint32_t tot_s, tot_c;
+  uint32_t ps = block_excl_scan<1024>(s, s_warp, &tot_s);
+  uint32_t pc = block_excl_scan<1024>(c, s_warp, &tot_c);
+  for (int r = r0; r < r1; ++r) {
+    rowstart[r] = ps;
+    chstart[r] = pc;
+    ps += rowcnt[r];
+    pc += (rowcnt[r] + kColChunk - 1) / kColChunk;
+  }
+  if (threadIdx.x == 0) {
+    rowstart[H] = tot_s;
+    chstart[H] = tot_c;
+  }
+}
+
+// Per line of a CTA's bits (8 words, one per warp of 32 items): the set bits
+// of its earlier words, pre[l * 8 + w].
+__device__ __forceinline__ void word_prefixes(const uint32_t *bm, int n, uint32_t *pre, int threads) {
+  for (int l = threadIdx.x; l < n; l += threads) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      pre[l * 8 + w] = acc;
+      acc += __popc(bm[l * 8 + w]);
+    }
+  }
+}
+
+// Item e (= threadIdx.x, valid, covering lines [a, b]) writes v (kTileKey:
+// ((tile0 + l) << gbits) | v) to out[base[l] + its rank among the items
+// covering l] for each of its lines l.  A warp whose lines span at most 64
+// walks them in step, so each store instruction writes one line's
+// consecutive ranks; a wider warp walks each item's own lines.
+template <bool kTileKey>
+__device__ __forceinline__ void scatter_ranks(const uint32_t *bm, const uint32_t *pre, const uint32_t *base,
+                                              bool valid, int a, int b, uint32_t v, uint32_t tile0, int gbits,
+                                              uint32_t *__restrict__ out, uint32_t cap) {
+  const int e = threadIdx.x, we = e >> 5;
+  const uint32_t below = (1u << (e & 31)) - 1u;
+  const unsigned lo = __reduce_min_sync(0xffffffffu, valid ? (unsigned)a : 0xffffffffu);
+  const unsigned hi = __reduce_max_sync(0xffffffffu, valid ? (unsigned)b : 0u);
+  if (lo == 0xffffffffu) return;
+  const bool step = hi - lo < 64u;
+  const int l0 = step ? (int)lo : a, l1 = step ? (int)hi : (valid ? b : a - 1);
+  for (int l = l0; l <= l1; ++l) {
+    if (valid && l >= a && l <= b) {
+      const uint32_t pos = base[l] + pre[l * 8 + we] + (uint32_t)__popc(bm[l * 8 + we] & below);
+      if (pos < cap) out[pos] = kTileKey ? ((tile0 + (uint32_t)l) << gbits) | v : v;
+    }
+  }
+}
+
+// The chunk's Gaussians into the row lists: Gaussian g of the chunk goes to
+// rowlist[rowstart[row] + t1[row][chunk] + its rank among the chunk's
+// Gaussians covering the row] for each row it covers.  Dynamic shared
+// memory: 17 H words.
+__global__ void __launch_bounds__(kRowChunk) row_scatter_kernel(const uint2 *__restrict__ rects, int64_t n_gauss,
+                                                                int H, int n_g1, const unsigned long long *count,
+                                                                const uint32_t *__restrict__ t1,
+                                                                const uint32_t *__restrict__ rowstart,
+                                                                uint32_t *__restrict__ rowlist, uint32_t cap) {
+  extern __shared__ uint32_t s_rows[];  // [H][8] bits, [H][8] word prefixes, [H] bases
+  if (*count == 0) return;
+  uint32_t *s_pre = s_rows + H * 8, *s_base = s_pre + H * 8;
+  for (int r = threadIdx.x; r < H; r += kRowChunk) s_base[r] = rowstart[r] + t1[(size_t)r * n_g1 + blockIdx.x];
+  gauss_row_bits(rects, n_gauss, H, s_rows);
+  word_prefixes(s_rows, H, s_pre, kRowChunk);
+  __syncthreads();
+  const int64_t g = (int64_t)blockIdx.x * kRowChunk + threadIdx.x;
+  const uint2 rc = g < n_gauss ? rects[g] : make_uint2(0u, 0u);
+  const int h = (int)(rc.y >> 16), ty0 = (int)(rc.x >> 16);
+  scatter_ranks<false>(s_rows, s_pre, s_base, (rc.y & 0xffffu) != 0u && h != 0, ty0, ty0 + h - 1, (uint32_t)g, 0u,
+                       0, rowlist, cap);
+}
+
+// Level 2: chunk ch of the row lists (its row, its first entry and its
+// entries m).  The level-2 kernels loop over the chunks (CTA b takes b, b +
+// gridDim.x, ...: their number is known only on the device, below
+// chstart[H]); thread e holds entry e of the chunk.
+struct ColChunk {
+  int row;
+  uint32_t e0, m;
+};
+
+__device__ __forceinline__ void col_chunk(const uint32_t *__restrict__ rowcnt, const uint32_t *__restrict__ chstart,
+                                          int H, uint32_t ch, ColChunk *c) {
+  int lo = 0, hi = H;  // the last row whose first chunk is <= ch (a row with chunks)
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (chstart[mid] <= ch) lo = mid + 1;
+    else hi = mid;
+  }
+  c->row = lo - 1;
+  c->e0 = (ch - chstart[c->row]) * kColChunk;
+  c->m = min((uint32_t)kColChunk, rowcnt[c->row] - c->e0);
+}
+
+// t2[chunk][tx] = the chunk's entries covering column tx: each entry adds
+// +1 / -1 at the ends of its columns in a difference array, then a scan.
+// Dynamic shared memory: W + 1 words.
+__global__ void __launch_bounds__(kColChunk) col_count_kernel(const uint2 *__restrict__ rects,
+                                                              const uint32_t *__restrict__ rowlist,
+                                                              const uint32_t *__restrict__ rowcnt,
+                                                              const uint32_t *__restrict__ rowstart,
+                                                              const uint32_t *__restrict__ chstart, int H, int W,
+                                                              const unsigned long long *count,
+                                                              uint32_t *__restrict__ t2) {
+  extern __shared__ int s_diff[];
+  __shared__ uint32_t s_warp[32];
+  if (*count == 0) return;
+  const uint32_t n_ch = chstart[H];
+  const int run = (W + kColChunk - 1) / kColChunk;
+  const int x0 = min(W, (int)threadIdx.x * run), x1 = min(W, x0 + run);
+  for (uint32_t ch = blockIdx.x; ch < n_ch; ch += gridDim.x) {
+    ColChunk c;
+    col_chunk(rowcnt, chstart, H, ch, &c);
+    for (int i = threadIdx.x; i <= W; i += kColChunk) s_diff[i] = 0;
+    __syncthreads();
+    if (threadIdx.x < c.m) {
+      const uint2 rc = rects[rowlist[rowstart[c.row] + c.e0 + threadIdx.x]];
+      const int tx0 = (int)(rc.x & 0xffffu), w = (int)(rc.y & 0xffffu);
+      atomicAdd(&s_diff[tx0], 1);
+      atomicSub(&s_diff[tx0 + w], 1);
+    }
+    __syncthreads();
+    int sum = 0;
+    for (int x = x0; x < x1; ++x) sum += s_diff[x];
+    uint32_t total;
+    int acc = (int)block_excl_scan<kColChunk>((uint32_t)sum, s_warp, &total);
+    for (int x = x0; x < x1; ++x) {
+      acc += s_diff[x];
+      t2[(size_t)ch * W + x] = (uint32_t)acc;
+    }
+    __syncthreads();  // before the next chunk clears s_diff
+  }
+}
+
+// Thread per (row, column): t2[.][tx] over the row's chunks becomes its
+// exclusive scan (eight chunks' counts loaded at a time).
+__global__ void col_scan_kernel(uint32_t *__restrict__ t2, const uint32_t *__restrict__ chstart, int H, int W,
+                                const unsigned long long *count) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)H * W || *count == 0) return;
+  const int row = (int)(idx / W), tx = (int)(idx - (int64_t)row * W);
+  const uint32_t c1 = chstart[row + 1];
+  uint32_t s = 0;
+  for (uint32_t c0 = chstart[row]; c0 < c1; c0 += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = c0 + k < c1 ? t2[(size_t)(c0 + k) * W + tx] : 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (c0 + k < c1) {
+        t2[(size_t)(c0 + k) * W + tx] = s;
+        s += v[k];
+      }
+  }
+}
+
+// Each entry of the chunk writes its pairs: in column tx, its rank is the
+// chunk's entries before it covering tx (a bit per (column, entry), the
+// population counts of the column's earlier words kept as prefixes), and
+// its key (tile << gbits) | g goes to ranges[tile].x + t2[chunk][tx] + rank
+// (the sum of the first two kept per column).  Dynamic shared memory:
+// 17 W words.
+__global__ void __launch_bounds__(kColChunk) col_scatter_kernel(const uint2 *__restrict__ rects,
+                                                                const uint32_t *__restrict__ rowlist,
+                                                                const uint32_t *__restrict__ rowcnt,
+                                                                const uint32_t *__restrict__ rowstart,
+                                                                const uint32_t *__restrict__ chstart, int H, int W,
+                                                                const unsigned long long *count,
+                                                                const uint32_t *__restrict__ t2,
+                                                                const uint2 *__restrict__ ranges, int gbits,
+                                                                uint32_t *__restrict__ keys, uint32_t cap) {
+  extern __shared__ uint32_t s_cols[];  // [W][8] bits, [W][8] word prefixes, [W] bases
+  if (*count == 0) return;
+  uint32_t *s_wpre = s_cols + W * 8, *s_base = s_wpre + W * 8;
+  const uint32_t n_ch = chstart[H];
+  const int e = threadIdx.x, we = e >> 5;
+  for (uint32_t ch = blockIdx.x; ch < n_ch; ch += gridDim.x) {
+    ColChunk c;
+    col_chunk(rowcnt, chstart, H, ch, &c);
+    for (int i = threadIdx.x; i < W * 8; i += kColChunk) s_cols[i] = 0u;
+    for (int tx = threadIdx.x; tx < W; tx += kColChunk)
+      s_base[tx] = ranges[c.row * W + tx].x + t2[(size_t)ch * W + tx];
+    __syncthreads();
+    const bool valid = (uint32_t)e < c.m;
+    uint32_t g = 0;
+    int tx0 = 0, tx1 = -1;
+    if (valid) {
+      g = rowlist[rowstart[c.row] + c.e0 + e];
+      const uint2 rc = rects[g];
+      tx0 = (int)(rc.x & 0xffffu);
+      tx1 = tx0 + (int)(rc.y & 0xffffu) - 1;
+      for (int tx = tx0; tx <= tx1; ++tx) atomicOr(&s_cols[tx * 8 + we], 1u << (e & 31));
+    }
+    __syncthreads();
+    word_prefixes(s_cols, W, s_wpre, kColChunk);
+    __syncthreads();
+    scatter_ranks<true>(s_cols, s_wpre, s_base, valid, tx0, tx1, g, (uint32_t)c.row * (uint32_t)W, gbits, keys, cap);
+    __syncthreads();  // before the next chunk rewrites the shared tables
+  }
+}
+
 }  // namespace
 
-bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, BinPlan *p) {
+bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, BinPlan *p, bool allow_rows) {
   if (n_gauss < 0 || n_gauss > (1ll << 31) - 1) {
     set_error("n_gauss %lld out of range", (long long)n_gauss);
     return BS_ERR_INVALID_ARG;
@@ -1154,6 +1478,20 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
   p->off_owner = o;      o = align256(o + sizeof(uint32_t) * (size_t)(div_up64(capacity, kEmitTile) + 1));
   p->off_keys_tmp = o;
   o = align256(o + (p->wide ? 2 * sizeof(unsigned long long) : sizeof(uint32_t)) * (size_t)(capacity > 0 ? capacity : 1));
+  // the two-level counting sort (32-bit keys, up to 512 tile rows and 512
+  // tile columns); its row lists use keys_tmp
+  p->n_g1 = (int)div_up64(n_gauss > 0 ? n_gauss : 1, kRowChunk);
+  p->rows = allow_rows && !p->wide && p->tiles_y <= kRowsMax && p->tiles_x <= kColsMax &&
+            (int64_t)p->tiles_y * p->n_g1 <= (int64_t(1) << 24);
+  p->n_ch_max = div_up64(capacity > 0 ? capacity : 1, kColChunk) + p->tiles_y;
+  p->off_t1 = p->off_rowcnt = p->off_rowstart = p->off_chstart = p->off_t2 = 0;
+  if (p->rows) {
+    p->off_t1 = o;       o = align256(o + sizeof(uint32_t) * (size_t)p->tiles_y * (size_t)p->n_g1);
+    p->off_rowcnt = o;   o = align256(o + sizeof(uint32_t) * (size_t)(p->tiles_y + 1));
+    p->off_rowstart = o; o = align256(o + sizeof(uint32_t) * (size_t)(p->tiles_y + 1));
+    p->off_chstart = o;  o = align256(o + sizeof(uint32_t) * (size_t)(p->tiles_y + 1));
+    p->off_t2 = o;       o = align256(o + sizeof(uint32_t) * (size_t)p->n_ch_max * (size_t)p->tiles_x);
+  }
   p->bytes = o;
   return BS_OK;
 }
@@ -1191,9 +1529,11 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     BS_LAUNCHED("count_kernel");
     scan_partials_kernel<<<1, 1024, 0, s>>>(partial, p.count_blocks, &hdr->n_pairs, hdr, p.capacity);
     BS_LAUNCHED("scan_partials_kernel");
-    chunk_owner_kernel<uint2><<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(
-        local, partial, rects, p.n_gauss, (uint32_t)div_up64(p.capacity, kEmitTile), owner);
-    BS_LAUNCHED("chunk_owner_kernel");
+    if (!p.rows) {
+      chunk_owner_kernel<uint2><<<(unsigned)p.count_blocks, kCountThreads, 0, s>>>(
+          local, partial, rects, p.n_gauss, (uint32_t)div_up64(p.capacity, kEmitTile), owner);
+      BS_LAUNCHED("chunk_owner_kernel");
+    }
   }
   if (fused_words(p.tiles_x, p.tiles_y) <= kFusedMaxWords && p.passes <= 2) {
     const size_t smem = sizeof(int) * (size_t)fused_words(p.tiles_x, p.tiles_y);
@@ -1239,6 +1579,38 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     P = p.capacity;
   }
   if (P == 0 || p.n_gauss == 0) return BS_OK;
+  if (p.rows) {
+    const int H = p.tiles_y, W = p.tiles_x;
+    uint32_t *t1 = reinterpret_cast<uint32_t *>(base + p.off_t1);
+    uint32_t *rowcnt = reinterpret_cast<uint32_t *>(base + p.off_rowcnt);
+    uint32_t *rowstart = reinterpret_cast<uint32_t *>(base + p.off_rowstart);
+    uint32_t *chstart = reinterpret_cast<uint32_t *>(base + p.off_chstart);
+    uint32_t *t2 = reinterpret_cast<uint32_t *>(base + p.off_t2);
+    uint32_t *rowlist = keys_tmp;
+    const uint32_t cap = (uint32_t)p.capacity;
+    row_count_kernel<<<(unsigned)p.n_g1, kRowChunk, sizeof(uint32_t) * 8 * H, s>>>(rects, p.n_gauss, H, p.n_g1,
+                                                                                   count, t1);
+    BS_LAUNCHED("row_count_kernel");
+    row_scan_kernel<<<(unsigned)H, 1024, 0, s>>>(t1, p.n_g1, count, rowcnt);
+    BS_LAUNCHED("row_scan_kernel");
+    row_starts_kernel<<<1, 1024, 0, s>>>(rowcnt, H, count, rowstart, chstart);
+    BS_LAUNCHED("row_starts_kernel");
+    row_scatter_kernel<<<(unsigned)p.n_g1, kRowChunk, sizeof(uint32_t) * 17 * (size_t)H, s>>>(
+        rects, p.n_gauss, H, p.n_g1, count, t1, rowstart, rowlist, cap);
+    BS_LAUNCHED("row_scatter_kernel");
+    // the row lists hold at most P entries, so at most P / 256 + H chunks;
+    // the level-2 kernels loop over the chunks there are
+    const int64_t n_ch = std::min<int64_t>(std::min(p.n_ch_max, div_up64(P, kColChunk) + H), kColGrid);
+    col_count_kernel<<<(unsigned)n_ch, kColChunk, sizeof(int) * ((size_t)W + 1), s>>>(rects, rowlist, rowcnt, rowstart,
+                                                                                 chstart, H, W, count, t2);
+    BS_LAUNCHED("col_count_kernel");
+    col_scan_kernel<<<(unsigned)div_up64((int64_t)H * W, 256), 256, 0, s>>>(t2, chstart, H, W, count);
+    BS_LAUNCHED("col_scan_kernel");
+    col_scatter_kernel<<<(unsigned)n_ch, kColChunk, sizeof(uint32_t) * 17 * (size_t)W, s>>>(
+        rects, rowlist, rowcnt, rowstart, chstart, H, W, count, t2, ranges, p.gbits, tile_keys, cap);
+    BS_LAUNCHED("col_scatter_kernel");
+    return BS_OK;
+  }
   const int64_t parts = div_up64(P, kSortTile);
   const int bits0 = std::min(p.digit_bits, p.tbits);
   BS_CUDA(cudaMemsetAsync(part_offs, 0, sizeof(uint32_t) * ((size_t)1 << bits0) * (size_t)parts, s));

@@ -132,9 +132,17 @@ struct BinPlan {
   // byte offsets inside the workspace
   size_t off_hdr, off_hist, off_diff, zero_bytes, off_parts;
   size_t off_local, off_partial, off_rects, off_owner, off_keys_tmp;  // keys_tmp: u32 [capacity], or u64 [2][capacity] when wide
+  // the two-level counting sort instead of the radix passes (rows): level-1
+  // chunks of 256 Gaussians, the most level-2 chunks, and its tables
+  bool rows;
+  int n_g1;
+  int64_t n_ch_max;
+  size_t off_t1, off_rowcnt, off_rowstart, off_chstart, off_t2;
   size_t bytes;
 };
-bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, BinPlan *p);
+// allow_rows = false keeps the radix passes (the fixed scratch of
+// bs_bin_tiles_static is sized for them).
+bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, BinPlan *p, bool allow_rows = true);
 bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv, void *ws,
                       int64_t *n_pairs, uint32_t *tile_keys, uint32_t *tile_ranges,
                       cudaStream_t s, bool sync = true, int64_t *n_pairs_dev = nullptr);
