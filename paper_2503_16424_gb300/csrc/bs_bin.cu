@@ -1215,11 +1215,13 @@ __global__ void __launch_bounds__(1024) row_scan_kernel(uint32_t *__restrict__ t
 }
 
 // One CTA: rowstart[r] = the list entries of rows < r (rowstart[H] = all),
-// chstart[r] = the level-2 chunks of rows < r (chstart[H] = all).
+// chstart[r] = the level-2 chunks of rows < r (chstart[H] = all), and
+// chrow[ch] = the row of level-2 chunk ch (at most n_ch_max chunks).
 __global__ void __launch_bounds__(1024) row_starts_kernel(const uint32_t *__restrict__ rowcnt, int H,
                                                           const unsigned long long *count,
                                                           uint32_t *__restrict__ rowstart,
-                                                          uint32_t *__restrict__ chstart) {
+                                                          uint32_t *__restrict__ chstart,
+                                                          uint32_t *__restrict__ chrow, uint32_t n_ch_max) {
   __shared__ uint32_t s_warp[32];
   if (*count == 0) return;
   const int run = (H + 1023) / 1024;
@@ -1233,10 +1235,12 @@ __global__ void __launch_bounds__(1024) row_starts_kernel(const uint32_t *__rest
   uint32_t ps = block_excl_scan<1024>(s, s_warp, &tot_s);
   uint32_t pc = block_excl_scan<1024>(c, s_warp, &tot_c);
   for (int r = r0; r < r1; ++r) {
+    const uint32_t nc = (rowcnt[r] + kColChunk - 1) / kColChunk;
     rowstart[r] = ps;
     chstart[r] = pc;
+    for (uint32_t k = 0; k < nc && pc + k < n_ch_max; ++k) chrow[pc + k] = (uint32_t)r;
     ps += rowcnt[r];
-    pc += (rowcnt[r] + kColChunk - 1) / kColChunk;
+    pc += nc;
   }
   if (threadIdx.x == 0) {
     rowstart[H] = tot_s;
@@ -1314,14 +1318,8 @@ struct ColChunk {
 };
 
 __device__ __forceinline__ void col_chunk(const uint32_t *__restrict__ rowcnt, const uint32_t *__restrict__ chstart,
-                                          int H, uint32_t ch, ColChunk *c) {
-  int lo = 0, hi = H;  // the last row whose first chunk is <= ch (a row with chunks)
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (chstart[mid] <= ch) lo = mid + 1;
-    else hi = mid;
-  }
-  c->row = lo - 1;
+                                          const uint32_t *__restrict__ chrow, uint32_t ch, ColChunk *c) {
+  c->row = (int)chrow[ch];
   c->e0 = (ch - chstart[c->row]) * kColChunk;
   c->m = min((uint32_t)kColChunk, rowcnt[c->row] - c->e0);
 }
@@ -1333,7 +1331,8 @@ __global__ void __launch_bounds__(kColChunk) col_count_kernel(const uint2 *__res
                                                               const uint32_t *__restrict__ rowlist,
                                                               const uint32_t *__restrict__ rowcnt,
                                                               const uint32_t *__restrict__ rowstart,
-                                                              const uint32_t *__restrict__ chstart, int H, int W,
+                                                              const uint32_t *__restrict__ chstart,
+                                                              const uint32_t *__restrict__ chrow, int H, int W,
                                                               const unsigned long long *count,
                                                               uint32_t *__restrict__ t2) {
   extern __shared__ int s_diff[];
@@ -1344,7 +1343,7 @@ __global__ void __launch_bounds__(kColChunk) col_count_kernel(const uint2 *__res
   const int x0 = min(W, (int)threadIdx.x * run), x1 = min(W, x0 + run);
   for (uint32_t ch = blockIdx.x; ch < n_ch; ch += gridDim.x) {
     ColChunk c;
-    col_chunk(rowcnt, chstart, H, ch, &c);
+    col_chunk(rowcnt, chstart, chrow, ch, &c);
     for (int i = threadIdx.x; i <= W; i += kColChunk) s_diff[i] = 0;
     __syncthreads();
     if (threadIdx.x < c.m) {
@@ -1398,7 +1397,8 @@ __global__ void __launch_bounds__(kColChunk) col_scatter_kernel(const uint2 *__r
                                                                 const uint32_t *__restrict__ rowlist,
                                                                 const uint32_t *__restrict__ rowcnt,
                                                                 const uint32_t *__restrict__ rowstart,
-                                                                const uint32_t *__restrict__ chstart, int H, int W,
+                                                                const uint32_t *__restrict__ chstart,
+                                                                const uint32_t *__restrict__ chrow, int H, int W,
                                                                 const unsigned long long *count,
                                                                 const uint32_t *__restrict__ t2,
                                                                 const uint2 *__restrict__ ranges, int gbits,
@@ -1410,7 +1410,7 @@ __global__ void __launch_bounds__(kColChunk) col_scatter_kernel(const uint2 *__r
   const int e = threadIdx.x, we = e >> 5;
   for (uint32_t ch = blockIdx.x; ch < n_ch; ch += gridDim.x) {
     ColChunk c;
-    col_chunk(rowcnt, chstart, H, ch, &c);
+    col_chunk(rowcnt, chstart, chrow, ch, &c);
     for (int i = threadIdx.x; i < W * 8; i += kColChunk) s_cols[i] = 0u;
     for (int tx = threadIdx.x; tx < W; tx += kColChunk)
       s_base[tx] = ranges[c.row * W + tx].x + t2[(size_t)ch * W + tx];
@@ -1484,13 +1484,14 @@ bs_status plan_binning(int64_t n_gauss, const bs_canvas &cv, int64_t capacity, B
   p->rows = allow_rows && !p->wide && p->tiles_y <= kRowsMax && p->tiles_x <= kColsMax &&
             (int64_t)p->tiles_y * p->n_g1 <= (int64_t(1) << 24);
   p->n_ch_max = div_up64(capacity > 0 ? capacity : 1, kColChunk) + p->tiles_y;
-  p->off_t1 = p->off_rowcnt = p->off_rowstart = p->off_chstart = p->off_t2 = 0;
+  p->off_t1 = p->off_rowcnt = p->off_rowstart = p->off_chstart = p->off_t2 = p->off_chrow = 0;
   if (p->rows) {
     p->off_t1 = o;       o = align256(o + sizeof(uint32_t) * (size_t)p->tiles_y * (size_t)p->n_g1);
     p->off_rowcnt = o;   o = align256(o + sizeof(uint32_t) * (size_t)(p->tiles_y + 1));
     p->off_rowstart = o; o = align256(o + sizeof(uint32_t) * (size_t)(p->tiles_y + 1));
     p->off_chstart = o;  o = align256(o + sizeof(uint32_t) * (size_t)(p->tiles_y + 1));
     p->off_t2 = o;       o = align256(o + sizeof(uint32_t) * (size_t)p->n_ch_max * (size_t)p->tiles_x);
+    p->off_chrow = o;    o = align256(o + sizeof(uint32_t) * (size_t)p->n_ch_max);
   }
   p->bytes = o;
   return BS_OK;
@@ -1586,6 +1587,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     uint32_t *rowstart = reinterpret_cast<uint32_t *>(base + p.off_rowstart);
     uint32_t *chstart = reinterpret_cast<uint32_t *>(base + p.off_chstart);
     uint32_t *t2 = reinterpret_cast<uint32_t *>(base + p.off_t2);
+    uint32_t *chrow = reinterpret_cast<uint32_t *>(base + p.off_chrow);
     uint32_t *rowlist = keys_tmp;
     const uint32_t cap = (uint32_t)p.capacity;
     row_count_kernel<<<(unsigned)p.n_g1, kRowChunk, sizeof(uint32_t) * 8 * H, s>>>(rects, p.n_gauss, H, p.n_g1,
@@ -1593,7 +1595,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     BS_LAUNCHED("row_count_kernel");
     row_scan_kernel<<<(unsigned)H, 1024, 0, s>>>(t1, p.n_g1, count, rowcnt);
     BS_LAUNCHED("row_scan_kernel");
-    row_starts_kernel<<<1, 1024, 0, s>>>(rowcnt, H, count, rowstart, chstart);
+    row_starts_kernel<<<1, 1024, 0, s>>>(rowcnt, H, count, rowstart, chstart, chrow, (uint32_t)p.n_ch_max);
     BS_LAUNCHED("row_starts_kernel");
     row_scatter_kernel<<<(unsigned)p.n_g1, kRowChunk, sizeof(uint32_t) * 17 * (size_t)H, s>>>(
         rects, p.n_gauss, H, p.n_g1, count, t1, rowstart, rowlist, cap);
@@ -1602,12 +1604,12 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     // the level-2 kernels loop over the chunks there are
     const int64_t n_ch = std::min<int64_t>(std::min(p.n_ch_max, div_up64(P, kColChunk) + H), kColGrid);
     col_count_kernel<<<(unsigned)n_ch, kColChunk, sizeof(int) * ((size_t)W + 1), s>>>(rects, rowlist, rowcnt, rowstart,
-                                                                                 chstart, H, W, count, t2);
+                                                                                 chstart, chrow, H, W, count, t2);
     BS_LAUNCHED("col_count_kernel");
     col_scan_kernel<<<(unsigned)div_up64((int64_t)H * W, 256), 256, 0, s>>>(t2, chstart, H, W, count);
     BS_LAUNCHED("col_scan_kernel");
     col_scatter_kernel<<<(unsigned)n_ch, kColChunk, sizeof(uint32_t) * 17 * (size_t)W, s>>>(
-        rects, rowlist, rowcnt, rowstart, chstart, H, W, count, t2, ranges, p.gbits, tile_keys, cap);
+        rects, rowlist, rowcnt, rowstart, chstart, chrow, H, W, count, t2, ranges, p.gbits, tile_keys, cap);
     BS_LAUNCHED("col_scatter_kernel");
     return BS_OK;
   }

@@ -137,7 +137,7 @@ struct BinPlan {
   bool rows;
   int n_g1;
   int64_t n_ch_max;
-  size_t off_t1, off_rowcnt, off_rowstart, off_chstart, off_t2;
+  size_t off_t1, off_rowcnt, off_rowstart, off_chstart, off_t2, off_chrow;
   size_t bytes;
 };
 // allow_rows = false keeps the radix passes (the fixed scratch of
