@@ -198,9 +198,13 @@ bs_status bs_bin_tiles_workspace(int64_t n_gauss, const bs_canvas *canvas,
  * x0 = max(ceil(xlo), 0), x1 = min(floor(xhi), W - 1) (same for y).  Keys are
  *     key = tile_id << gbits | g,  tile_id = ty * tiles_x + tx,
  *     gbits = max(1, bit length of n_gauss - 1),
- * and are sorted ascending by a hand-written stable LSD radix sort of the
- * tile bits (per pass: digit counts per partition, their scan, a stable
- * scatter), so each tile's list is front to back.
+ * and are put in ascending order, so each tile's list is front to back.
+ * With 32-bit keys on a grid of at most 512 x 512 tiles this is a two-level
+ * stable counting sort over the Gaussians' tile rectangles (every Gaussian
+ * into the list of each tile row it covers, then each row list into its
+ * tiles, ranks from per-chunk bit tables); otherwise a hand-written stable
+ * LSD radix sort of the tile bits (per pass: digit counts per partition,
+ * their scan, a stable scatter).  Both give the same keys.
  * When tile bits + gbits exceed 32 ("wide" keys), the keys are 64-bit
  * (tile << 32 | g) inside the workspace and tile_keys receives only g for
  * each pair, in the same order; the blend calls tell the two apart from
@@ -250,9 +254,11 @@ bs_status bs_bin_tiles_result(const void *ws, size_t ws_bytes, int32_t *status_o
  * allocator, for instance a host that hands this library a fixed memory
  * budget, or a callback that must not allocate.  The caller still provides
  * gauss, tile_keys and tile_ranges.  The paper has no counterpart of this call.
- *   - A request whose scratch would exceed 32 MiB (a pair_capacity above
- *     about 7.1 M for 262,144 Gaussians on a 2048 x 2048 canvas; see
- *     bs_bin_tiles_workspace for the size of a request) returns
+ *   - It always sorts with the radix passes, whose scratch is smaller than
+ *     the two-level sort's tables (bs_bin_tiles_workspace reports the
+ *     larger of the two where bs_bin_tiles would use the two-level sort).
+ *     A request whose scratch would exceed 32 MiB (a pair_capacity above
+ *     about 7.1 M for 262,144 Gaussians on a 2048 x 2048 canvas) returns
  *     BS_ERR_INVALID_ARG with the size it needs; nothing is launched.
  *   - No allocation is made: no cudaMalloc, cudaFree or allocating library
  *     routine.  The first call on a device looks up the array's device

@@ -1,6 +1,10 @@
 // Tile binning (Section 3.4): per-Gaussian tile rectangles, (tile, depth)
-// keys, a hand-written stable LSD radix sort of the tile bits, and
-// per-tile ranges.
+// keys in ascending order, and per-tile ranges.  The order comes from one of
+// two sorts with the same result: on one canvas with 32-bit keys and at most
+// 512 x 512 tiles, a two-level stable counting sort over the rectangles
+// (rows, then columns; see "two-level binning" below); otherwise (wider
+// grids, 64-bit keys, batches, the fixed scratch of bs_bin_tiles_static) a
+// hand-written stable LSD radix sort of the tile bits:
 //
 // The keys are emitted Gaussian by Gaussian, so the emitted array is already
 // ordered by the Gaussian index (the depth, since the table is in draw
