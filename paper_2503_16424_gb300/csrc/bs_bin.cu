@@ -1123,17 +1123,19 @@ __global__ void __launch_bounds__(kEmitThreads) batch_emit_kernel(const uint32_t
 // where each chunk's Gaussians of a row begin; a Gaussian's rank among them
 // is the population count of the row's bits below its own
 // (row_scatter_kernel).  Level 2 does the same for the columns of each
-// row's list, cut into chunks of 256 entries (col_count_kernel with a
+// row's list, cut into chunks of 128 entries (col_count_kernel with a
 // difference array per chunk, col_scan_kernel, col_scatter_kernel): a pair's
 // place is its tile's first pair, plus the tile's pairs in the row's earlier
 // chunks, plus its rank among the chunk's entries covering the tile.  The
 // keys come out as the radix sort writes them, (tile << gbits) | g in
 // (tile, g) order.
 constexpr int kRowChunk = 256;   // Gaussians per level-1 chunk (8 words of bits per row)
-constexpr int kColChunk = 256;   // row-list entries per level-2 chunk (8 words of bits per column)
+constexpr int kColChunk = 128;   // row-list entries per level-2 chunk (one 32-bit word of bits per warp and column)
+constexpr int kColWords = kColChunk / 32;
 constexpr int kRowsMax = 512, kColsMax = 512;
-constexpr int kColGrid = 152 * 8;  // CTAs of the level-2 kernels (eight per SM)
-static_assert(kRowChunk == 256 && kColChunk == 256, "eight 32-bit words of bits per line");
+constexpr int kColGrid = 152 * (2048 / kColChunk);  // CTAs of the level-2 kernels (2,048 threads per SM)
+static_assert(kRowChunk == 256, "eight 32-bit words of bits per row");
+static_assert(kColChunk % 32 == 0 && kColChunk <= 1024, "whole warps per level-2 chunk");
 
 // The 32 items of a warp (item = lane) over lines [a, b] (valid items only):
 // bm[l * 8 + warp] = the ballot of the items covering line l, for every line
@@ -1252,15 +1254,16 @@ __global__ void __launch_bounds__(1024) row_starts_kernel(const uint32_t *__rest
   }
 }
 
-// Per line of a CTA's bits (8 words, one per warp of 32 items): the set bits
-// of its earlier words, pre[l * 8 + w].
+// Per line of a CTA's bits (kWords words, one per warp of 32 items): the set
+// bits of its earlier words, pre[l * kWords + w].
+template <int kWords>
 __device__ __forceinline__ void word_prefixes(const uint32_t *bm, int n, uint32_t *pre, int threads) {
   for (int l = threadIdx.x; l < n; l += threads) {
     uint32_t acc = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      pre[l * 8 + w] = acc;
-      acc += __popc(bm[l * 8 + w]);
+    for (int w = 0; w < kWords; ++w) {
+      pre[l * kWords + w] = acc;
+      acc += __popc(bm[l * kWords + w]);
     }
   }
 }
@@ -1270,7 +1273,7 @@ __device__ __forceinline__ void word_prefixes(const uint32_t *bm, int n, uint32_
 // covering l] for each of its lines l.  A warp whose lines span at most 64
 // walks them in step, so each store instruction writes one line's
 // consecutive ranks; a wider warp walks each item's own lines.
-template <bool kTileKey>
+template <bool kTileKey, int kWords>
 __device__ __forceinline__ void scatter_ranks(const uint32_t *bm, const uint32_t *pre, const uint32_t *base,
                                               bool valid, int a, int b, uint32_t v, uint32_t tile0, int gbits,
                                               uint32_t *__restrict__ out, uint32_t cap) {
@@ -1283,7 +1286,7 @@ __device__ __forceinline__ void scatter_ranks(const uint32_t *bm, const uint32_t
   const int l0 = step ? (int)lo : a, l1 = step ? (int)hi : (valid ? b : a - 1);
   for (int l = l0; l <= l1; ++l) {
     if (valid && l >= a && l <= b) {
-      const uint32_t pos = base[l] + pre[l * 8 + we] + (uint32_t)__popc(bm[l * 8 + we] & below);
+      const uint32_t pos = base[l] + pre[l * kWords + we] + (uint32_t)__popc(bm[l * kWords + we] & below);
       if (pos < cap) out[pos] = kTileKey ? ((tile0 + (uint32_t)l) << gbits) | v : v;
     }
   }
@@ -1303,12 +1306,12 @@ __global__ void __launch_bounds__(kRowChunk) row_scatter_kernel(const uint2 *__r
   uint32_t *s_pre = s_rows + H * 8, *s_base = s_pre + H * 8;
   for (int r = threadIdx.x; r < H; r += kRowChunk) s_base[r] = rowstart[r] + t1[(size_t)r * n_g1 + blockIdx.x];
   gauss_row_bits(rects, n_gauss, H, s_rows);
-  word_prefixes(s_rows, H, s_pre, kRowChunk);
+  word_prefixes<8>(s_rows, H, s_pre, kRowChunk);
   __syncthreads();
   const int64_t g = (int64_t)blockIdx.x * kRowChunk + threadIdx.x;
   const uint2 rc = g < n_gauss ? rects[g] : make_uint2(0u, 0u);
   const int h = (int)(rc.y >> 16), ty0 = (int)(rc.x >> 16);
-  scatter_ranks<false>(s_rows, s_pre, s_base, (rc.y & 0xffffu) != 0u && h != 0, ty0, ty0 + h - 1, (uint32_t)g, 0u,
+  scatter_ranks<false, 8>(s_rows, s_pre, s_base, (rc.y & 0xffffu) != 0u && h != 0, ty0, ty0 + h - 1, (uint32_t)g, 0u,
                        0, rowlist, cap);
 }
 
@@ -1396,7 +1399,7 @@ __global__ void col_scan_kernel(uint32_t *__restrict__ t2, const uint32_t *__res
 // population counts of the column's earlier words kept as prefixes), and
 // its key (tile << gbits) | g goes to ranges[tile].x + t2[chunk][tx] + rank
 // (the sum of the first two kept per column).  Dynamic shared memory:
-// 17 W words.
+// (2 kColWords + 1) W words.
 __global__ void __launch_bounds__(kColChunk) col_scatter_kernel(const uint2 *__restrict__ rects,
                                                                 const uint32_t *__restrict__ rowlist,
                                                                 const uint32_t *__restrict__ rowcnt,
@@ -1409,13 +1412,13 @@ __global__ void __launch_bounds__(kColChunk) col_scatter_kernel(const uint2 *__r
                                                                 uint32_t *__restrict__ keys, uint32_t cap) {
   extern __shared__ uint32_t s_cols[];  // [W][8] bits, [W][8] word prefixes, [W] bases
   if (*count == 0) return;
-  uint32_t *s_wpre = s_cols + W * 8, *s_base = s_wpre + W * 8;
+  uint32_t *s_wpre = s_cols + W * kColWords, *s_base = s_wpre + W * kColWords;
   const uint32_t n_ch = chstart[H];
   const int e = threadIdx.x, we = e >> 5;
   for (uint32_t ch = blockIdx.x; ch < n_ch; ch += gridDim.x) {
     ColChunk c;
     col_chunk(rowcnt, chstart, chrow, ch, &c);
-    for (int i = threadIdx.x; i < W * 8; i += kColChunk) s_cols[i] = 0u;
+    for (int i = threadIdx.x; i < W * kColWords; i += kColChunk) s_cols[i] = 0u;
     for (int tx = threadIdx.x; tx < W; tx += kColChunk)
       s_base[tx] = ranges[c.row * W + tx].x + t2[(size_t)ch * W + tx];
     __syncthreads();
@@ -1427,12 +1430,12 @@ __global__ void __launch_bounds__(kColChunk) col_scatter_kernel(const uint2 *__r
       const uint2 rc = rects[g];
       tx0 = (int)(rc.x & 0xffffu);
       tx1 = tx0 + (int)(rc.y & 0xffffu) - 1;
-      for (int tx = tx0; tx <= tx1; ++tx) atomicOr(&s_cols[tx * 8 + we], 1u << (e & 31));
+      for (int tx = tx0; tx <= tx1; ++tx) atomicOr(&s_cols[tx * kColWords + we], 1u << (e & 31));
     }
     __syncthreads();
-    word_prefixes(s_cols, W, s_wpre, kColChunk);
+    word_prefixes<kColWords>(s_cols, W, s_wpre, kColChunk);
     __syncthreads();
-    scatter_ranks<true>(s_cols, s_wpre, s_base, valid, tx0, tx1, g, (uint32_t)c.row * (uint32_t)W, gbits, keys, cap);
+    scatter_ranks<true, kColWords>(s_cols, s_wpre, s_base, valid, tx0, tx1, g, (uint32_t)c.row * (uint32_t)W, gbits, keys, cap);
     __syncthreads();  // before the next chunk rewrites the shared tables
   }
 }
@@ -1612,7 +1615,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     BS_LAUNCHED("col_count_kernel");
     col_scan_kernel<<<(unsigned)div_up64((int64_t)H * W, 256), 256, 0, s>>>(t2, chstart, H, W, count);
     BS_LAUNCHED("col_scan_kernel");
-    col_scatter_kernel<<<(unsigned)n_ch, kColChunk, sizeof(uint32_t) * 17 * (size_t)W, s>>>(
+    col_scatter_kernel<<<(unsigned)n_ch, kColChunk, sizeof(uint32_t) * (2 * kColWords + 1) * (size_t)W, s>>>(
         rects, rowlist, rowcnt, rowstart, chstart, chrow, H, W, count, t2, ranges, p.gbits, tile_keys, cap);
     BS_LAUNCHED("col_scatter_kernel");
     return BS_OK;

@@ -72,7 +72,7 @@ def test_two_level_at_its_largest_grid(bs):
 
 def test_two_level_with_long_row_lists(bs):
     """A 2048 x 48 canvas (128 x 3 tiles of 16 px) with 6,000 Gaussians in
-    its band: each row list holds about 6,000 entries (24 level-2 chunks) and
+    its band: each row list holds about 6,000 entries (47 level-2 chunks) and
     a tile up to about a thousand pairs."""
     W, H = 2048, 48
     rec = _table(8, W, H, 6000, ext=(10.0, 300.0), y_band=(0.0, 48.0))
