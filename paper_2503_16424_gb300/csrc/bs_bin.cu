@@ -1229,6 +1229,7 @@ __global__ void __launch_bounds__(1024) row_starts_kernel(const uint32_t *__rest
                                                           uint32_t *__restrict__ chstart,
                                                           uint32_t *__restrict__ chrow, uint32_t n_ch_max) {
   __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_ch[kRowsMax + 1];
   if (*count == 0) return;
   const int run = (H + 1023) / 1024;
   const int r0 = min(H, (int)threadIdx.x * run), r1 = min(H, r0 + run);
@@ -1241,16 +1242,27 @@ __global__ void __launch_bounds__(1024) row_starts_kernel(const uint32_t *__rest
   uint32_t ps = block_excl_scan<1024>(s, s_warp, &tot_s);
   uint32_t pc = block_excl_scan<1024>(c, s_warp, &tot_c);
   for (int r = r0; r < r1; ++r) {
-    const uint32_t nc = (rowcnt[r] + kColChunk - 1) / kColChunk;
     rowstart[r] = ps;
     chstart[r] = pc;
-    for (uint32_t k = 0; k < nc && pc + k < n_ch_max; ++k) chrow[pc + k] = (uint32_t)r;
+    s_ch[r] = pc;
     ps += rowcnt[r];
-    pc += nc;
+    pc += (rowcnt[r] + kColChunk - 1) / kColChunk;
   }
   if (threadIdx.x == 0) {
     rowstart[H] = tot_s;
     chstart[H] = tot_c;
+    s_ch[H] = tot_c;
+  }
+  __syncthreads();
+  // the row of every chunk: the last row whose first chunk is <= it
+  for (uint32_t ch = threadIdx.x; ch < tot_c && ch < n_ch_max; ch += blockDim.x) {
+    int lo = 0, hi = H;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (s_ch[mid] <= ch) lo = mid + 1;
+      else hi = mid;
+    }
+    chrow[ch] = (uint32_t)(lo - 1);
   }
 }
 
@@ -1372,24 +1384,45 @@ __global__ void __launch_bounds__(kColChunk) col_count_kernel(const uint2 *__res
   }
 }
 
-// Thread per (row, column): t2[.][tx] over the row's chunks becomes its
-// exclusive scan (eight chunks' counts loaded at a time).
-__global__ void col_scan_kernel(uint32_t *__restrict__ t2, const uint32_t *__restrict__ chstart, int H, int W,
-                                const unsigned long long *count) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)H * W || *count == 0) return;
-  const int row = (int)(idx / W), tx = (int)(idx - (int64_t)row * W);
-  const uint32_t c1 = chstart[row + 1];
+// One CTA of 1024 threads per row: t2[.][tx] over the row's chunks becomes
+// its exclusive scan.  Thread (seg, tx) owns segment seg of the row's chunks
+// (1024 / W segments): it sums its segment, then adds the segments before it
+// and rewrites its segment as running sums (eight chunks' counts loaded at a
+// time).
+__global__ void __launch_bounds__(1024) col_scan_kernel(uint32_t *__restrict__ t2,
+                                                        const uint32_t *__restrict__ chstart, int W,
+                                                        const unsigned long long *count) {
+  __shared__ uint32_t s_tot[1024];
+  if (*count == 0) return;
+  const int row = blockIdx.x, n_seg = 1024 / W;
+  const int seg = threadIdx.x / W, tx = threadIdx.x - seg * W;
+  const uint32_t c0 = chstart[row], c1 = chstart[row + 1];
+  const uint32_t per = (c1 - c0 + n_seg - 1) / n_seg;
+  const uint32_t a = min(c1, c0 + (uint32_t)seg * per), b = min(c1, a + per);
+  const bool mine = seg < n_seg;
   uint32_t s = 0;
-  for (uint32_t c0 = chstart[row]; c0 < c1; c0 += 8) {
+  if (mine)
+    for (uint32_t c = a; c < b; c += 8) {
+      uint32_t v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = c + k < b ? t2[(size_t)(c + k) * W + tx] : 0u;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s += v[k];
+    }
+  s_tot[threadIdx.x] = s;
+  __syncthreads();
+  if (!mine) return;
+  uint32_t off = 0;
+  for (int q = 0; q < seg; ++q) off += s_tot[q * W + tx];
+  for (uint32_t c = a; c < b; c += 8) {
     uint32_t v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = c0 + k < c1 ? t2[(size_t)(c0 + k) * W + tx] : 0u;
+    for (int k = 0; k < 8; ++k) v[k] = c + k < b ? t2[(size_t)(c + k) * W + tx] : 0u;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-      if (c0 + k < c1) {
-        t2[(size_t)(c0 + k) * W + tx] = s;
-        s += v[k];
+      if (c + k < b) {
+        t2[(size_t)(c + k) * W + tx] = off;
+        off += v[k];
       }
   }
 }
@@ -1613,7 +1646,7 @@ bs_status run_binning(const BinPlan &p, const float *gauss, const bs_canvas &cv,
     col_count_kernel<<<(unsigned)n_ch, kColChunk, sizeof(int) * ((size_t)W + 1), s>>>(rects, rowlist, rowcnt, rowstart,
                                                                                  chstart, chrow, H, W, count, t2);
     BS_LAUNCHED("col_count_kernel");
-    col_scan_kernel<<<(unsigned)div_up64((int64_t)H * W, 256), 256, 0, s>>>(t2, chstart, H, W, count);
+    col_scan_kernel<<<(unsigned)H, 1024, 0, s>>>(t2, chstart, W, count);
     BS_LAUNCHED("col_scan_kernel");
     col_scatter_kernel<<<(unsigned)n_ch, kColChunk, sizeof(uint32_t) * (2 * kColWords + 1) * (size_t)W, s>>>(
         rects, rowlist, rowcnt, rowstart, chstart, chrow, H, W, count, t2, ranges, p.gbits, tile_keys, cap);
