@@ -897,7 +897,6 @@ __global__ void batch_diff_cols_kernel(int *diff, const BatchImage *__restrict__
 // [(c 256 + i) 8, +8), which may cross into the next image.
 constexpr int kTileThreads = 256;
 constexpr int kTileItems = 8;
-constexpr int kTilesPerCta = kTileThreads * kTileItems;
 
 struct TileWalk {
   int b, tiles_x, tx, ty;

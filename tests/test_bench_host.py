@@ -99,3 +99,16 @@ def test_stale_counters_are_not_used():
     finally:
         bench.NCU_CAPTURE.clear()
         bench.NCU_CAPTURE.update(saved)
+
+
+def test_binning_launch_counts_follow_the_library_plan():
+    """Kernels one binning call launches: the two-level sort where it applies
+    (32-bit keys, at most 512 x 512 tiles), else key emission and the radix
+    passes; the tile scan in one CTA when the counts fit its shared memory."""
+    from paper_2503_16424_gb300 import bs
+    # 2048^2, 16 px tiles, 262,144 Gaussians: 14 + 18 key bits, 128 x 128 tiles
+    assert bench.binning_launches(bs.Canvas(2048, 2048, 16), 262144) == 4 + 7
+    # 513 tile columns: the radix passes (2 of 7 bits), chunk owners and emission
+    assert bench.binning_launches(bs.Canvas(4104, 64, 8), 6000) == 4 + 2 + 3 * 2 - 1
+    # 64-bit keys on a 32768^2 canvas: radix passes, tile scan in three kernels
+    assert bench.binning_launches(bs.Canvas(32768, 32768, 16), 1536) == 3 + 3 + 2 + 3 * 3 - 1
