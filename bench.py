@@ -61,18 +61,18 @@ RENDER_SOURCE = os.path.join(ROOT, "paper_2503_16424_gb300", "csrc", "bs_render.
 # carry over per evaluation; the DRAM bytes (read + write, one launch) from a
 # one-pass capture of the full workload.
 NCU_CAPTURE = {
-    "source_sha256_16": "e4c8cdcb414ff7b0",
+    "source_sha256_16": "6d4f75d78482383e",
     "workload": "hires_1024_1024",
     "render_fwd_kernel": {"flop_per_eval": 9.0216, "mufu_per_eval": 0.5828,
-                          "ffma": 569099211, "fadd": 146802257, "fmul": 198282596, "xu": 95815232,
-                          "evals": 164415545, "dram_bytes": 179385856,
-                          "pipes": {"issue_active_pct": 72.0, "fma_pipe_pct": 32.2, "alu_pipe_pct": 41.8,
-                                    "shared_pipe_pct": 18.7, "warps_active_pct": 38.3}},
+                          "ffma": 569099211, "fadd": 146802257, "fmul": 198282596, "xu": 95815936,
+                          "evals": 164415545, "dram_bytes": 179548928,
+                          "pipes": {"issue_active_pct": 71.8, "fma_pipe_pct": 32.1, "alu_pipe_pct": 41.7,
+                                    "shared_pipe_pct": 17.7, "warps_active_pct": 38.3}},
     "render_bwd_kernel": {"flop_per_eval": 22.7272, "mufu_per_eval": 1.0985,
-                          "ffma": 1094763846, "fadd": 836737013, "fmul": 641605293, "xu": 177279456,
-                          "evals": 161386726, "dram_bytes": 127687680,
-                          "pipes": {"issue_active_pct": 70.9, "fma_pipe_pct": 35.7, "alu_pipe_pct": 38.3,
-                                    "shared_pipe_pct": 34.7, "warps_active_pct": 30.9}},
+                          "ffma": 1094763846, "fadd": 836737013, "fmul": 641605293, "xu": 177278880,
+                          "evals": 161386726, "dram_bytes": 127760896,
+                          "pipes": {"issue_active_pct": 70.5, "fma_pipe_pct": 35.6, "alu_pipe_pct": 38.0,
+                                    "shared_pipe_pct": 33.5, "warps_active_pct": 30.9}},
 }
 
 
